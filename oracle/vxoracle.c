@@ -1,0 +1,1018 @@
+/*
+ * vxoracle.c -- plain, slow CPU oracle for the voxelization + LoD + SGGX-H path of
+ * "Fast Voxelization and Level of Detail for Microgeometry Rendering" (Fabre et al.).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the bench's CPU
+ * baseline leg may load this library.  It shares no code, header or table with the
+ * CUDA library; both implement the same written definitions independently.
+ *
+ * What it computes (the plain definition, evaluated per primitive over its bounding
+ * box, then grouped per voxel):
+ *   - grid coordinates u = (p - origin) * (1/h)                     (Sec. 3.1, P_volume)
+ *   - per voxel and per 8^3 sub-cell: closed-box overlap with each primitive
+ *     (capsule = segment inflated by its radius; triangle = separating axes)
+ *     -> 512-bit mask, occupancy O = popcount/512                     (Sec. 3.5, Eq. for O)
+ *     -> projected occupancies along x, y, z                          (Sec. 3.5, projections)
+ *   - per voxel mass m = sum_p w_p mu_p(v) and second moment M = sum_p w_p mu_p d_p d_p^T
+ *     (mu = clipped length * pi r^2 for fibers, clipped area for triangles; d = tangent
+ *     or face normal; symmetric sign-free second moment)              (Sec. 4.1, covariance)
+ *   - SGGX S = M/m and its compact parameters                        (Sec. 4.1, Eq. compact-sggx)
+ *   - LoD: 2x2x2 aggregation of m, M, OR-downsampled masks           (Sec. 4.2, 4.3)
+ *   - SGGX-H: agglomerative merging of sampled-histogram lobes       (Sec. 4.4, Eq. similarity)
+ *
+ * Precision: every quantity that decides an integer result (sub-cell bits, histogram
+ * bins, merge argmins) is evaluated in IEEE FP32 with the operation order written
+ * here, no contraction (build with -ffp-contract=off), exactly as the kernels take
+ * those decisions.  Mass and moment are also accumulated in FP64, as the reference
+ * value for the attribute tolerances: the exact (FP64) measures of the geometry after
+ * its FP32 normalisation to grid coordinates (the normalised positions are the
+ * method's input, Sec. 3.1).
+ *
+ * Parity unpinned: none of the functions here; see tests/test_oracle_pins.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_API __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------------- */
+/* small helpers                                                             */
+/* ------------------------------------------------------------------------- */
+static float fmin2(float a, float b) { return (b < a) ? b : a; }
+static float fmax2(float a, float b) { return (b > a) ? b : a; }
+
+/* Morton key: x bit in position 0, y in 1, z in 2 of each bit triple. */
+ORC_API uint64_t vxo_morton(uint32_t x, uint32_t y, uint32_t z) {
+    uint64_t k = 0;
+    for (int b = 0; b < 21; ++b) {
+        k |= (uint64_t)((x >> b) & 1u) << (3 * b);
+        k |= (uint64_t)((y >> b) & 1u) << (3 * b + 1);
+        k |= (uint64_t)((z >> b) & 1u) << (3 * b + 2);
+    }
+    return k;
+}
+
+ORC_API void vxo_demorton(uint64_t k, uint32_t* x, uint32_t* y, uint32_t* z) {
+    uint32_t a = 0, b = 0, c = 0;
+    for (int i = 0; i < 21; ++i) {
+        a |= (uint32_t)((k >> (3 * i)) & 1u) << i;
+        b |= (uint32_t)((k >> (3 * i + 1)) & 1u) << i;
+        c |= (uint32_t)((k >> (3 * i + 2)) & 1u) << i;
+    }
+    *x = a; *y = b; *z = c;
+}
+
+/* sub-cell index inside a voxel: sx + 8*sy + 64*sz; word = sz, bit = sx + 8*sy */
+static void mask_set(uint64_t* m, int sx, int sy, int sz) { m[sz] |= 1ull << (sx + 8 * sy); }
+static int mask_get(const uint64_t* m, int sx, int sy, int sz) { return (int)((m[sz] >> (sx + 8 * sy)) & 1ull); }
+
+static int popcount64(uint64_t v) { int c = 0; while (v) { v &= v - 1; ++c; } return c; }
+
+/* ------------------------------------------------------------------------- */
+/* Capsule (segment a-b inflated by radius r) vs closed box [lo,hi]           */
+/* a, b in voxel-local grid coordinates; d = b - a; rr = r*r.                */
+/* Three steps, each an exact geometric statement:                           */
+/*   1. lower bound: squared gaps between the segment's extent and the box   */
+/*   2. an endpoint within r of the box                                      */
+/*   3. min over t in [0,1] of squared distance from a + t d to the box,     */
+/*      evaluated at the stationary points of the active quadratic pieces.   */
+/* ------------------------------------------------------------------------- */
+static float box_sqdist_point(const float* p, const float* lo, const float* hi) {
+    float e[3];
+    for (int i = 0; i < 3; ++i) {
+        if (p[i] < lo[i]) e[i] = lo[i] - p[i];
+        else if (p[i] > hi[i]) e[i] = p[i] - hi[i];
+        else e[i] = 0.0f;
+    }
+    return (e[0] * e[0] + e[1] * e[1]) + e[2] * e[2];
+}
+
+static float seg_box_g(const float* a, const float* d, float t, const float* lo, const float* hi) {
+    float p[3];
+    if (!(t >= 0.0f)) t = 0.0f;      /* also maps a NaN (0/0 from underflow) to 0 */
+    else if (t > 1.0f) t = 1.0f;
+    for (int i = 0; i < 3; ++i) p[i] = a[i] + t * d[i];
+    return box_sqdist_point(p, lo, hi);
+}
+
+ORC_API int vxo_capsule_box(const float* a, const float* b, float rr, const float* lo, const float* hi) {
+    float d[3];
+    for (int i = 0; i < 3; ++i) d[i] = b[i] - a[i];
+    /* step 1 */
+    float g[3];
+    for (int i = 0; i < 3; ++i) {
+        float mn = fmin2(a[i], b[i]), mx = fmax2(a[i], b[i]);
+        if (lo[i] > mx) g[i] = lo[i] - mx;
+        else if (mn > hi[i]) g[i] = mn - hi[i];
+        else g[i] = 0.0f;
+    }
+    float G = (g[0] * g[0] + g[1] * g[1]) + g[2] * g[2];
+    if (G > rr) return 0;
+    /* step 2 */
+    if (box_sqdist_point(a, lo, hi) <= rr) return 1;
+    if (box_sqdist_point(b, lo, hi) <= rr) return 1;
+    /* step 3 */
+    float L = -INFINITY, U = INFINITY;
+    int iL = -1, jU = -1, moving = 0;
+    float plo[3], phi[3];       /* plane giving the lower / upper end of the t-interval */
+    for (int i = 0; i < 3; ++i) {
+        if (d[i] != 0.0f) {
+            ++moving;
+            plo[i] = (d[i] > 0.0f) ? lo[i] : hi[i];
+            phi[i] = (d[i] > 0.0f) ? hi[i] : lo[i];
+            float jl = (plo[i] - a[i]) / d[i];
+            float jh = (phi[i] - a[i]) / d[i];
+            if (jl > L) { L = jl; iL = i; }
+            if (jh < U) { U = jh; jU = i; }
+        }
+    }
+    if (moving == 0) return 0;
+    float gmin;
+    if (L <= U) {
+        float t;
+        if (U < 0.0f) t = 0.0f;
+        else if (L > 1.0f) t = 1.0f;
+        else t = fmax2(L, 0.0f);
+        gmin = seg_box_g(a, d, t, lo, hi);
+    } else {
+        /* iL is below its slab, jU above it, on the whole bracket [U, L] */
+        float beta[3];
+        int use[3] = {0, 0, 0};
+        beta[iL] = plo[iL]; use[iL] = 1;
+        beta[jU] = phi[jU]; use[jU] = 1;
+        float num = 0.0f, den = 0.0f;
+        int first = 1;
+        for (int i = 0; i < 3; ++i) {
+            if (!use[i]) continue;
+            float ti = d[i] * (beta[i] - a[i]);
+            float di = d[i] * d[i];
+            if (first) { num = ti; den = di; first = 0; }
+            else { num = num + ti; den = den + di; }
+        }
+        gmin = seg_box_g(a, d, num / den, lo, hi);
+        int k = 3 - iL - jU;
+        if (d[k] != 0.0f) {
+            for (int side = 0; side < 2; ++side) {
+                beta[k] = side == 0 ? plo[k] : phi[k];
+                float n3 = 0.0f, d3 = 0.0f;
+                for (int i = 0; i < 3; ++i) {
+                    float ti = d[i] * (beta[i] - a[i]);
+                    float di = d[i] * d[i];
+                    if (i == 0) { n3 = ti; d3 = di; }
+                    else { n3 = n3 + ti; d3 = d3 + di; }
+                }
+                float gc = seg_box_g(a, d, n3 / d3, lo, hi);
+                if (gc < gmin) gmin = gc;
+            }
+        }
+    }
+    return gmin <= rr ? 1 : 0;
+}
+
+/* 512-bit sub-cell mask of a capsule in voxel (vi,vj,vk); A,B grid coordinates. */
+ORC_API int vxo_capsule_mask(const float* A, const float* B, float rg,
+                             int vi, int vj, int vk, uint64_t* mask) {
+    float a[3] = {A[0] - (float)vi, A[1] - (float)vj, A[2] - (float)vk};
+    float b[3] = {B[0] - (float)vi, B[1] - (float)vj, B[2] - (float)vk};
+    float rr = rg * rg;
+    int any = 0;
+    for (int w = 0; w < 8; ++w) mask[w] = 0;
+    for (int sz = 0; sz < 8; ++sz)
+        for (int sy = 0; sy < 8; ++sy)
+            for (int sx = 0; sx < 8; ++sx) {
+                float lo[3] = {(float)sx * 0.125f, (float)sy * 0.125f, (float)sz * 0.125f};
+                float hi[3] = {(float)(sx + 1) * 0.125f, (float)(sy + 1) * 0.125f, (float)(sz + 1) * 0.125f};
+                if (vxo_capsule_box(a, b, rr, lo, hi)) { mask_set(mask, sx, sy, sz); any = 1; }
+            }
+    return any;
+}
+
+/* Fiber measure in a voxel: pi r^2 * length of the axis clipped to the closed voxel. */
+ORC_API float vxo_capsule_measure(const float* A, const float* B, float rg, int vi, int vj, int vk) {
+    float a[3] = {A[0] - (float)vi, A[1] - (float)vj, A[2] - (float)vk};
+    float b[3] = {B[0] - (float)vi, B[1] - (float)vj, B[2] - (float)vk};
+    float d[3];
+    for (int i = 0; i < 3; ++i) d[i] = b[i] - a[i];
+    float t0 = 0.0f, t1 = 1.0f;
+    for (int i = 0; i < 3; ++i) {
+        if (d[i] == 0.0f) {
+            if (a[i] < 0.0f || a[i] > 1.0f) return 0.0f;
+        } else {
+            float ta = (0.0f - a[i]) / d[i];
+            float tb = (1.0f - a[i]) / d[i];
+            float tn = d[i] > 0.0f ? ta : tb;
+            float tf = d[i] > 0.0f ? tb : ta;
+            if (tn > t0) t0 = tn;
+            if (tf < t1) t1 = tf;
+        }
+    }
+    if (t1 <= t0) return 0.0f;
+    float dn = sqrtf((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+    float len = (t1 - t0) * dn;
+    float rr = rg * rg;
+    return (3.14159265358979f * rr) * len;
+}
+
+static double capsule_measure64(const double* A, const double* B, double rg, int vi, int vj, int vk) {
+    double a[3] = {A[0] - vi, A[1] - vj, A[2] - vk};
+    double d[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+    double t0 = 0.0, t1 = 1.0;
+    for (int i = 0; i < 3; ++i) {
+        if (d[i] == 0.0) {
+            if (a[i] < 0.0 || a[i] > 1.0) return 0.0;
+        } else {
+            double ta = -a[i] / d[i], tb = (1.0 - a[i]) / d[i];
+            double tn = d[i] > 0 ? ta : tb, tf = d[i] > 0 ? tb : ta;
+            if (tn > t0) t0 = tn;
+            if (tf < t1) t1 = tf;
+        }
+    }
+    if (t1 <= t0) return 0.0;
+    double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    return 3.14159265358979323846 * rg * rg * (t1 - t0) * dn;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Triangle vs closed axis-aligned box: separating axis theorem with the 13   */
+/* axes (3 box normals, 9 edge cross products, the face normal).             */
+/* v: voxel-local vertices; f: the three edges f0=v1-v0, f1=v2-v1, f2=v0-v2; */
+/* box given by centre c and half extent e.                                  */
+/* ------------------------------------------------------------------------- */
+static int tri_box(const float v[3][3], const float f[3][3], const float* c, float e) {
+    float w[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < 3; ++i) w[k][i] = v[k][i] - c[i];
+    /* box normals */
+    for (int i = 0; i < 3; ++i) {
+        float mn = fmin2(fmin2(w[0][i], w[1][i]), w[2][i]);
+        float mx = fmax2(fmax2(w[0][i], w[1][i]), w[2][i]);
+        if (mn > e || mx < -e) return 0;
+    }
+    /* e_x x f, e_y x f, e_z x f */
+    for (int j = 0; j < 3; ++j) {
+        const float* fj = f[j];
+        float p[3], rad, mn, mx;
+        for (int k = 0; k < 3; ++k) p[k] = fj[1] * w[k][2] - fj[2] * w[k][1];
+        rad = e * (fabsf(fj[1]) + fabsf(fj[2]));
+        mn = fmin2(fmin2(p[0], p[1]), p[2]); mx = fmax2(fmax2(p[0], p[1]), p[2]);
+        if (mn > rad || mx < -rad) return 0;
+        for (int k = 0; k < 3; ++k) p[k] = fj[2] * w[k][0] - fj[0] * w[k][2];
+        rad = e * (fabsf(fj[0]) + fabsf(fj[2]));
+        mn = fmin2(fmin2(p[0], p[1]), p[2]); mx = fmax2(fmax2(p[0], p[1]), p[2]);
+        if (mn > rad || mx < -rad) return 0;
+        for (int k = 0; k < 3; ++k) p[k] = fj[0] * w[k][1] - fj[1] * w[k][0];
+        rad = e * (fabsf(fj[0]) + fabsf(fj[1]));
+        mn = fmin2(fmin2(p[0], p[1]), p[2]); mx = fmax2(fmax2(p[0], p[1]), p[2]);
+        if (mn > rad || mx < -rad) return 0;
+    }
+    /* face normal n = f0 x f1, plane through v0 */
+    float n[3];
+    n[0] = f[0][1] * f[1][2] - f[0][2] * f[1][1];
+    n[1] = f[0][2] * f[1][0] - f[0][0] * f[1][2];
+    n[2] = f[0][0] * f[1][1] - f[0][1] * f[1][0];
+    float p = (n[0] * w[0][0] + n[1] * w[0][1]) + n[2] * w[0][2];
+    float rad = e * ((fabsf(n[0]) + fabsf(n[1])) + fabsf(n[2]));
+    if (p > rad || p < -rad) return 0;
+    return 1;
+}
+
+static void tri_local(const float* U, int vi, int vj, int vk, float v[3][3], float f[3][3]) {
+    /* U: 9 floats, grid coordinates of v0, v1, v2 */
+    for (int k = 0; k < 3; ++k) {
+        v[k][0] = U[3 * k + 0] - (float)vi;
+        v[k][1] = U[3 * k + 1] - (float)vj;
+        v[k][2] = U[3 * k + 2] - (float)vk;
+    }
+    for (int i = 0; i < 3; ++i) {
+        f[0][i] = U[3 + i] - U[i];
+        f[1][i] = U[6 + i] - U[3 + i];
+        f[2][i] = U[i] - U[6 + i];
+    }
+}
+
+ORC_API int vxo_tri_mask(const float* U, int vi, int vj, int vk, uint64_t* mask) {
+    float v[3][3], f[3][3];
+    tri_local(U, vi, vj, vk, v, f);
+    int any = 0;
+    for (int w = 0; w < 8; ++w) mask[w] = 0;
+    for (int sz = 0; sz < 8; ++sz)
+        for (int sy = 0; sy < 8; ++sy)
+            for (int sx = 0; sx < 8; ++sx) {
+                float c[3] = {(float)(2 * sx + 1) * 0.0625f, (float)(2 * sy + 1) * 0.0625f,
+                              (float)(2 * sz + 1) * 0.0625f};
+                if (tri_box((const float(*)[3])v, (const float(*)[3])f, c, 0.0625f)) {
+                    mask_set(mask, sx, sy, sz);
+                    any = 1;
+                }
+            }
+    return any;
+}
+
+/* Sutherland-Hodgman clip of a polygon against the plane x_axis >= c (keep_ge=1) or <= c. */
+static int clip_plane(const float in[][3], int n, float out[][3], int axis, float c, int keep_ge) {
+    int m = 0;
+    for (int k = 0; k < n; ++k) {
+        const float* S = in[k];
+        const float* E = in[(k + 1) % n];
+        int sin_ = keep_ge ? (S[axis] >= c) : (S[axis] <= c);
+        int ein = keep_ge ? (E[axis] >= c) : (E[axis] <= c);
+        if (ein) {
+            if (!sin_) {
+                float s = (c - S[axis]) / (E[axis] - S[axis]);
+                for (int j = 0; j < 3; ++j) out[m][j] = (j == axis) ? c : S[j] + s * (E[j] - S[j]);
+                ++m;
+            }
+            for (int j = 0; j < 3; ++j) out[m][j] = E[j];
+            ++m;
+        } else if (sin_) {
+            float s = (c - S[axis]) / (E[axis] - S[axis]);
+            for (int j = 0; j < 3; ++j) out[m][j] = (j == axis) ? c : S[j] + s * (E[j] - S[j]);
+            ++m;
+        }
+    }
+    return m;
+}
+
+/* Triangle measure in a voxel: area (voxel units^2) of the triangle clipped to the voxel. */
+ORC_API float vxo_tri_measure(const float* U, int vi, int vj, int vk) {
+    float v[3][3], f[3][3];
+    tri_local(U, vi, vj, vk, v, f);
+    float A[16][3], B[16][3];
+    int n = 3;
+    for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 3; ++j) A[k][j] = v[k][j];
+    for (int axis = 0; axis < 3 && n > 0; ++axis) {
+        n = clip_plane((const float(*)[3])A, n, B, axis, 0.0f, 1);
+        if (n == 0) break;
+        n = clip_plane((const float(*)[3])B, n, A, axis, 1.0f, 0);
+    }
+    if (n < 3) return 0.0f;
+    float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+    for (int k = 1; k + 1 < n; ++k) {
+        float e1[3], e2[3];
+        for (int j = 0; j < 3; ++j) { e1[j] = A[k][j] - A[0][j]; e2[j] = A[k + 1][j] - A[0][j]; }
+        cx = cx + (e1[1] * e2[2] - e1[2] * e2[1]);
+        cy = cy + (e1[2] * e2[0] - e1[0] * e2[2]);
+        cz = cz + (e1[0] * e2[1] - e1[1] * e2[0]);
+    }
+    return 0.5f * sqrtf((cx * cx + cy * cy) + cz * cz);
+}
+
+static int clip_plane64(const double in[][3], int n, double out[][3], int axis, double c, int keep_ge) {
+    int m = 0;
+    for (int k = 0; k < n; ++k) {
+        const double* S = in[k];
+        const double* E = in[(k + 1) % n];
+        int sin_ = keep_ge ? (S[axis] >= c) : (S[axis] <= c);
+        int ein = keep_ge ? (E[axis] >= c) : (E[axis] <= c);
+        if (ein) {
+            if (!sin_) {
+                double s = (c - S[axis]) / (E[axis] - S[axis]);
+                for (int j = 0; j < 3; ++j) out[m][j] = (j == axis) ? c : S[j] + s * (E[j] - S[j]);
+                ++m;
+            }
+            for (int j = 0; j < 3; ++j) out[m][j] = E[j];
+            ++m;
+        } else if (sin_) {
+            double s = (c - S[axis]) / (E[axis] - S[axis]);
+            for (int j = 0; j < 3; ++j) out[m][j] = (j == axis) ? c : S[j] + s * (E[j] - S[j]);
+            ++m;
+        }
+    }
+    return m;
+}
+
+ORC_API double vxo_tri_measure64(const double* U, int vi, int vj, int vk) {
+    double A[16][3], B[16][3];
+    int n = 3;
+    for (int k = 0; k < 3; ++k) {
+        A[k][0] = U[3 * k] - vi; A[k][1] = U[3 * k + 1] - vj; A[k][2] = U[3 * k + 2] - vk;
+    }
+    for (int axis = 0; axis < 3 && n > 0; ++axis) {
+        n = clip_plane64((const double(*)[3])A, n, B, axis, 0.0, 1);
+        if (n == 0) break;
+        n = clip_plane64((const double(*)[3])B, n, A, axis, 1.0, 0);
+    }
+    if (n < 3) return 0.0;
+    double cx = 0, cy = 0, cz = 0;
+    for (int k = 1; k + 1 < n; ++k) {
+        double e1[3], e2[3];
+        for (int j = 0; j < 3; ++j) { e1[j] = A[k][j] - A[0][j]; e2[j] = A[k + 1][j] - A[0][j]; }
+        cx += e1[1] * e2[2] - e1[2] * e2[1];
+        cy += e1[2] * e2[0] - e1[0] * e2[2];
+        cz += e1[0] * e2[1] - e1[1] * e2[0];
+    }
+    return 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Voxelization: per primitive, over its bounding box; then grouped per key   */
+/* in primitive order.                                                        */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    uint64_t key;
+    int64_t prim;
+    uint64_t mask[8];
+    float c;          /* w * mu   (FP32) */
+    float dir[3];     /* unit orientation (FP32) */
+    double c64;       /* w * mu   (FP64) */
+    double dir64[3];
+} rec_t;
+
+typedef struct {
+    rec_t* r;
+    int64_t n, cap;
+} recs_t;
+
+static void recs_push(recs_t* R, const rec_t* x) {
+    if (R->n == R->cap) {
+        R->cap = R->cap ? 2 * R->cap : 4096;
+        R->r = (rec_t*)realloc(R->r, (size_t)R->cap * sizeof(rec_t));
+    }
+    R->r[R->n++] = *x;
+}
+
+static int rec_cmp(const void* pa, const void* pb) {
+    const rec_t* a = (const rec_t*)pa;
+    const rec_t* b = (const rec_t*)pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    if (a->prim != b->prim) return a->prim < b->prim ? -1 : 1;
+    return 0;
+}
+
+/* A level of the pyramid as the oracle returns it (arrays malloc'ed here). */
+typedef struct {
+    int64_t n;
+    int32_t K;
+    uint64_t* keys;
+    uint64_t* mask;      /* [n][8] */
+    float* mass;         /* [n] FP32 chain */
+    float* moment;       /* [n][6] xx,yy,zz,xy,xz,yz */
+    double* mass64;      /* [n] */
+    double* moment64;    /* [n][6] */
+    uint16_t* occ;       /* [n] */
+    uint8_t* proj;       /* [n][3] yz (along x), xz (along y), xy (along z) */
+    uint8_t* lobe_count; /* [n] */
+    float* lobes;        /* [n][K][7] S6 + weight */
+    float* compact;      /* [n][K][6] */
+} vxo_level;
+
+ORC_API void vxo_level_free(vxo_level* L) {
+    free(L->keys); free(L->mask); free(L->mass); free(L->moment); free(L->mass64);
+    free(L->moment64); free(L->occ); free(L->proj); free(L->lobe_count); free(L->lobes);
+    free(L->compact);
+    memset(L, 0, sizeof(*L));
+}
+
+static void level_alloc(vxo_level* L, int64_t n, int K) {
+    memset(L, 0, sizeof(*L));
+    L->n = n; L->K = K;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    L->keys = (uint64_t*)calloc(nn, 8);
+    L->mask = (uint64_t*)calloc(nn * 8, 8);
+    L->mass = (float*)calloc(nn, 4);
+    L->moment = (float*)calloc(nn * 6, 4);
+    L->mass64 = (double*)calloc(nn, 8);
+    L->moment64 = (double*)calloc(nn * 6, 8);
+    L->occ = (uint16_t*)calloc(nn, 2);
+    L->proj = (uint8_t*)calloc(nn * 3, 1);
+    L->lobe_count = (uint8_t*)calloc(nn, 1);
+    L->lobes = (float*)calloc(nn * (size_t)K * 7, 4);
+    L->compact = (float*)calloc(nn * (size_t)K * 6, 4);
+}
+
+/* occupancy O (as a count of hit sub-cells) and the three projected counts */
+static void mask_stats(const uint64_t* m, uint16_t* occ, uint8_t* proj) {
+    int o = 0;
+    for (int w = 0; w < 8; ++w) o += popcount64(m[w]);
+    int yz = 0, xz = 0, xy = 0;
+    for (int sz = 0; sz < 8; ++sz)
+        for (int sy = 0; sy < 8; ++sy) {
+            int any = 0;
+            for (int sx = 0; sx < 8; ++sx) any |= mask_get(m, sx, sy, sz);
+            yz += any;
+        }
+    for (int sz = 0; sz < 8; ++sz)
+        for (int sx = 0; sx < 8; ++sx) {
+            int any = 0;
+            for (int sy = 0; sy < 8; ++sy) any |= mask_get(m, sx, sy, sz);
+            xz += any;
+        }
+    for (int sy = 0; sy < 8; ++sy)
+        for (int sx = 0; sx < 8; ++sx) {
+            int any = 0;
+            for (int sz = 0; sz < 8; ++sz) any |= mask_get(m, sx, sy, sz);
+            xy += any;
+        }
+    *occ = (uint16_t)o;
+    proj[0] = (uint8_t)yz; proj[1] = (uint8_t)xz; proj[2] = (uint8_t)xy;
+}
+
+/* Compact SGGX parameters (Eq. compact-sggx): sigma = sqrt(S_ii), r_ij = S_ij / sqrt(S_ii S_jj). */
+ORC_API void vxo_compact(const float* S, float* out) {
+    out[0] = sqrtf(S[0]);
+    out[1] = sqrtf(S[1]);
+    out[2] = sqrtf(S[2]);
+    float pxy = S[0] * S[1], pxz = S[0] * S[2], pyz = S[1] * S[2];
+    out[3] = pxy > 0.0f ? S[3] / sqrtf(pxy) : 0.0f;
+    out[4] = pxz > 0.0f ? S[4] / sqrtf(pxz) : 0.0f;
+    out[5] = pyz > 0.0f ? S[5] / sqrtf(pyz) : 0.0f;
+}
+
+/* single normalised lobe from (m, M): S = M / m, weight m */
+static void single_lobe(vxo_level* L, int64_t v) {
+    float m = L->mass[v];
+    if (m > 0.0f) {
+        float* lo = L->lobes + (size_t)v * L->K * 7;
+        for (int c = 0; c < 6; ++c) lo[c] = L->moment[6 * v + c] / m;
+        lo[6] = m;
+        vxo_compact(lo, L->compact + (size_t)v * L->K * 6);
+        L->lobe_count[v] = 1;
+    } else {
+        L->lobe_count[v] = 0;
+    }
+}
+
+static void reduce_records(recs_t* R, vxo_level* out, int K) {
+    qsort(R->r, (size_t)R->n, sizeof(rec_t), rec_cmp);
+    /* count keys with a non-zero mask */
+    int64_t nv = 0;
+    for (int64_t i = 0; i < R->n;) {
+        int64_t j = i;
+        uint64_t any = 0;
+        while (j < R->n && R->r[j].key == R->r[i].key) {
+            for (int w = 0; w < 8; ++w) any |= R->r[j].mask[w];
+            ++j;
+        }
+        if (any) ++nv;
+        i = j;
+    }
+    level_alloc(out, nv, K);
+    int64_t v = 0;
+    for (int64_t i = 0; i < R->n;) {
+        int64_t j = i;
+        uint64_t m8[8] = {0};
+        float m = 0.0f, M[6] = {0, 0, 0, 0, 0, 0};
+        double m64 = 0.0, M64[6] = {0, 0, 0, 0, 0, 0};
+        while (j < R->n && R->r[j].key == R->r[i].key) {
+            const rec_t* x = &R->r[j];
+            for (int w = 0; w < 8; ++w) m8[w] |= x->mask[w];
+            float c = x->c;
+            const float* t = x->dir;
+            m = m + c;
+            M[0] = M[0] + c * (t[0] * t[0]);
+            M[1] = M[1] + c * (t[1] * t[1]);
+            M[2] = M[2] + c * (t[2] * t[2]);
+            M[3] = M[3] + c * (t[0] * t[1]);
+            M[4] = M[4] + c * (t[0] * t[2]);
+            M[5] = M[5] + c * (t[1] * t[2]);
+            const double* t6 = x->dir64;
+            m64 += x->c64;
+            M64[0] += x->c64 * t6[0] * t6[0];
+            M64[1] += x->c64 * t6[1] * t6[1];
+            M64[2] += x->c64 * t6[2] * t6[2];
+            M64[3] += x->c64 * t6[0] * t6[1];
+            M64[4] += x->c64 * t6[0] * t6[2];
+            M64[5] += x->c64 * t6[1] * t6[2];
+            ++j;
+        }
+        uint64_t any = 0;
+        for (int w = 0; w < 8; ++w) any |= m8[w];
+        if (any) {
+            out->keys[v] = R->r[i].key;
+            memcpy(out->mask + 8 * v, m8, sizeof(m8));
+            out->mass[v] = m;
+            memcpy(out->moment + 6 * v, M, sizeof(M));
+            out->mass64[v] = m64;
+            memcpy(out->moment64 + 6 * v, M64, sizeof(M64));
+            mask_stats(m8, &out->occ[v], &out->proj[3 * v]);
+            single_lobe(out, v);
+            ++v;
+        }
+        i = j;
+    }
+}
+
+typedef struct {
+    float origin[3];
+    float voxel_size;
+    int32_t resolution;
+} vxo_grid;
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Fibers: ctrl [P][4] (xyz, radius), offsets [F+1]; segment s of fiber f joins
+ * ctrl[off[f]+s] and ctrl[off[f]+s+1]; primitive ids count segments fiber by fiber. */
+ORC_API int vxo_voxelize_fibers(const float* ctrl, const int64_t* offsets, int64_t F,
+                                const float* weights, const vxo_grid* g, int K, vxo_level* out) {
+    const float s = 1.0f / g->voxel_size;
+    const int R = g->resolution;
+    recs_t recs = {0, 0, 0};
+    int64_t prim = 0;
+    for (int64_t f = 0; f < F; ++f) {
+        for (int64_t c = offsets[f]; c + 1 < offsets[f + 1]; ++c, ++prim) {
+            const float* pa = ctrl + 4 * c;
+            const float* pb = ctrl + 4 * (c + 1);
+            float A[3], B[3];
+            double A64[3], B64[3];
+            for (int i = 0; i < 3; ++i) {
+                A[i] = (pa[i] - g->origin[i]) * s;
+                B[i] = (pb[i] - g->origin[i]) * s;
+                A64[i] = (double)A[i];
+                B64[i] = (double)B[i];
+            }
+            float rg = ((pa[3] + pb[3]) * 0.5f) * s;
+            double rg64 = (double)rg;
+            float w = weights ? weights[prim] : 1.0f;
+            float d[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+            float dn = sqrtf((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+            float t[3] = {0, 0, 0};
+            if (dn > 0.0f) { t[0] = d[0] / dn; t[1] = d[1] / dn; t[2] = d[2] / dn; }
+            double d64[3] = {B64[0] - A64[0], B64[1] - A64[1], B64[2] - A64[2]};
+            double dn64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
+            double t64[3] = {0, 0, 0};
+            if (dn64 > 0) { t64[0] = d64[0] / dn64; t64[1] = d64[1] / dn64; t64[2] = d64[2] / dn64; }
+            int lo[3], hi[3];
+            for (int i = 0; i < 3; ++i) {
+                double mn = fmin(A64[i], B64[i]) - rg64, mx = fmax(A64[i], B64[i]) + rg64;
+                lo[i] = clampi((int)floor(mn) - 1, 0, R - 1);
+                hi[i] = clampi((int)floor(mx) + 1, 0, R - 1);
+                if (mx < -1.0 || mn > (double)R + 1.0) { lo[i] = 1; hi[i] = 0; }
+            }
+            for (int vk = lo[2]; vk <= hi[2]; ++vk)
+                for (int vj = lo[1]; vj <= hi[1]; ++vj)
+                    for (int vi = lo[0]; vi <= hi[0]; ++vi) {
+                        rec_t x;
+                        int any = vxo_capsule_mask(A, B, rg, vi, vj, vk, x.mask);
+                        float mu = vxo_capsule_measure(A, B, rg, vi, vj, vk);
+                        if (!any && mu == 0.0f) continue;
+                        x.key = vxo_morton((uint32_t)vi, (uint32_t)vj, (uint32_t)vk);
+                        x.prim = prim;
+                        x.c = w * mu;
+                        x.dir[0] = t[0]; x.dir[1] = t[1]; x.dir[2] = t[2];
+                        x.c64 = (double)w * capsule_measure64(A64, B64, rg64, vi, vj, vk);
+                        x.dir64[0] = t64[0]; x.dir64[1] = t64[1]; x.dir64[2] = t64[2];
+                        recs_push(&recs, &x);
+                    }
+        }
+    }
+    reduce_records(&recs, out, K);
+    free(recs.r);
+    return 0;
+}
+
+/* Triangles: tri [T][3][4] (xyz, w unused). */
+ORC_API int vxo_voxelize_tris(const float* tri, int64_t T, const float* weights,
+                              const vxo_grid* g, int K, vxo_level* out) {
+    const float s = 1.0f / g->voxel_size;
+    const int R = g->resolution;
+    recs_t recs = {0, 0, 0};
+    for (int64_t p = 0; p < T; ++p) {
+        float U[9];
+        double U64[9];
+        for (int k = 0; k < 3; ++k)
+            for (int i = 0; i < 3; ++i) {
+                float x = tri[12 * p + 4 * k + i];
+                U[3 * k + i] = (x - g->origin[i]) * s;
+                U64[3 * k + i] = (double)U[3 * k + i];
+            }
+        float w = weights ? weights[p] : 1.0f;
+        float f0[3], f1[3];
+        for (int i = 0; i < 3; ++i) { f0[i] = U[3 + i] - U[i]; f1[i] = U[6 + i] - U[3 + i]; }
+        float n[3];
+        n[0] = f0[1] * f1[2] - f0[2] * f1[1];
+        n[1] = f0[2] * f1[0] - f0[0] * f1[2];
+        n[2] = f0[0] * f1[1] - f0[1] * f1[0];
+        float nn = sqrtf((n[0] * n[0] + n[1] * n[1]) + n[2] * n[2]);
+        float t[3] = {0, 0, 0};
+        if (nn > 0.0f) { t[0] = n[0] / nn; t[1] = n[1] / nn; t[2] = n[2] / nn; }
+        double e0[3], e1[3], n64[3], t64[3] = {0, 0, 0};
+        for (int i = 0; i < 3; ++i) { e0[i] = U64[3 + i] - U64[i]; e1[i] = U64[6 + i] - U64[3 + i]; }
+        n64[0] = e0[1] * e1[2] - e0[2] * e1[1];
+        n64[1] = e0[2] * e1[0] - e0[0] * e1[2];
+        n64[2] = e0[0] * e1[1] - e0[1] * e1[0];
+        double nn64 = sqrt(n64[0] * n64[0] + n64[1] * n64[1] + n64[2] * n64[2]);
+        if (nn64 > 0) { t64[0] = n64[0] / nn64; t64[1] = n64[1] / nn64; t64[2] = n64[2] / nn64; }
+        int lo[3], hi[3];
+        for (int i = 0; i < 3; ++i) {
+            double mn = fmin(fmin(U64[i], U64[3 + i]), U64[6 + i]);
+            double mx = fmax(fmax(U64[i], U64[3 + i]), U64[6 + i]);
+            lo[i] = clampi((int)floor(mn) - 1, 0, R - 1);
+            hi[i] = clampi((int)floor(mx) + 1, 0, R - 1);
+            if (mx < -1.0 || mn > (double)R + 1.0) { lo[i] = 1; hi[i] = 0; }
+        }
+        for (int vk = lo[2]; vk <= hi[2]; ++vk)
+            for (int vj = lo[1]; vj <= hi[1]; ++vj)
+                for (int vi = lo[0]; vi <= hi[0]; ++vi) {
+                    rec_t x;
+                    int any = vxo_tri_mask(U, vi, vj, vk, x.mask);
+                    float mu = vxo_tri_measure(U, vi, vj, vk);
+                    if (!any && mu == 0.0f) continue;
+                    x.key = vxo_morton((uint32_t)vi, (uint32_t)vj, (uint32_t)vk);
+                    x.prim = p;
+                    x.c = w * mu;
+                    x.dir[0] = t[0]; x.dir[1] = t[1]; x.dir[2] = t[2];
+                    x.c64 = (double)w * vxo_tri_measure64(U64, vi, vj, vk);
+                    x.dir64[0] = t64[0]; x.dir64[1] = t64[1]; x.dir64[2] = t64[2];
+                    recs_push(&recs, &x);
+                }
+    }
+    reduce_records(&recs, out, K);
+    free(recs.r);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* SGGX-H (Sec. 4.4)                                                          */
+/* ------------------------------------------------------------------------- */
+
+/* Symmetric square root of a 3x3 SPD matrix by cyclic Jacobi rotations (FP32,
+ * 6 sweeps over the pairs (0,1),(0,2),(1,2)); S packed xx,yy,zz,xy,xz,yz,
+ * R full row-major 3x3. */
+ORC_API void vxo_sqrtm3(const float* S, float* Rm) {
+    float a[3][3] = {{S[0], S[3], S[4]}, {S[3], S[1], S[5]}, {S[4], S[5], S[2]}};
+    float V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    static const int PQ[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (int sweep = 0; sweep < 6; ++sweep) {
+        for (int r = 0; r < 3; ++r) {
+            int p = PQ[r][0], q = PQ[r][1];
+            float apq = a[p][q];
+            if (apq == 0.0f) continue;
+            float app = a[p][p], aqq = a[q][q];
+            float theta = (aqq - app) / (2.0f * apq);
+            float t = 1.0f / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+            if (theta < 0.0f) t = -t;
+            float c = 1.0f / sqrtf(t * t + 1.0f);
+            float sn = t * c;
+            a[p][p] = app - t * apq;
+            a[q][q] = aqq + t * apq;
+            a[p][q] = 0.0f;
+            a[q][p] = 0.0f;
+            int o = 3 - p - q;
+            float arp = a[o][p], arq = a[o][q];
+            float nrp = c * arp - sn * arq;
+            float nrq = sn * arp + c * arq;
+            a[o][p] = nrp; a[p][o] = nrp;
+            a[o][q] = nrq; a[q][o] = nrq;
+            for (int i = 0; i < 3; ++i) {
+                float vp = V[i][p], vq = V[i][q];
+                V[i][p] = c * vp - sn * vq;
+                V[i][q] = sn * vp + c * vq;
+            }
+        }
+    }
+    float sg[3];
+    for (int i = 0; i < 3; ++i) sg[i] = sqrtf(a[i][i] > 0.0f ? a[i][i] : 0.0f);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            Rm[3 * i + j] = ((V[i][0] * sg[0]) * V[j][0] + (V[i][1] * sg[1]) * V[j][1]) +
+                            (V[i][2] * sg[2]) * V[j][2];
+}
+
+/* Histogram + empirical second moment of the N directions drawn from a lobe S.
+ * omega_k = normalize(S'^(1/2) u_k), S' = S + 1e-6 tr(S) I, u_k the fixed direction set.
+ * Histogram (5 bins per axis over [-1,1], omega and -omega both counted): stored as
+ * hist[a] = #(omega_a^2 >= 0.36 |v|^2), hist[3+a] = #(omega_a^2 >= 0.04 |v|^2).
+ * Second moment: each product omega_a omega_b rounded to the 2^-20 grid, summed exactly
+ * in integers, divided by N. */
+ORC_API void vxo_sample_lobe(const float* S, const float* dirs, int N, int32_t* hist, float* Mhat) {
+    float tr = (S[0] + S[1]) + S[2];
+    float eps = 1e-6f * tr;
+    float Sp[6] = {S[0] + eps, S[1] + eps, S[2] + eps, S[3], S[4], S[5]};
+    float Rm[9];
+    vxo_sqrtm3(Sp, Rm);
+    int32_t h[6] = {0, 0, 0, 0, 0, 0};
+    int64_t Q[6] = {0, 0, 0, 0, 0, 0};
+    int64_t cnt = 0;
+    for (int k = 0; k < N; ++k) {
+        const float* u = dirs + 3 * k;
+        float v[3];
+        for (int i = 0; i < 3; ++i) v[i] = (Rm[3 * i] * u[0] + Rm[3 * i + 1] * u[1]) + Rm[3 * i + 2] * u[2];
+        float n2 = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
+        if (!(n2 > 0.0f)) continue;
+        ++cnt;
+        float t6 = 0.36f * n2, t2 = 0.04f * n2;
+        for (int a = 0; a < 3; ++a) {
+            float c2 = v[a] * v[a];
+            if (c2 >= t6) h[a] += 1;
+            if (c2 >= t2) h[3 + a] += 1;
+        }
+        float inv = 1.0f / n2;
+        float s20 = inv * 1048576.0f;
+        static const int AB[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+        for (int c = 0; c < 6; ++c) {
+            float x = (v[AB[c][0]] * v[AB[c][1]]) * s20;
+            Q[c] += (int64_t)nearbyintf(x);
+        }
+    }
+    for (int c = 0; c < 6; ++c) hist[c] = h[c];
+    for (int c = 0; c < 6; ++c)
+        Mhat[c] = cnt > 0 ? (float)((double)Q[c] / ((double)cnt * 1048576.0)) : 0.0f;
+}
+
+/* integer sliced-Wasserstein distance between two lobe histograms (units of 0.4/N) */
+ORC_API int64_t vxo_hist_dist(const int32_t* a, const int32_t* b) {
+    int64_t d = 0;
+    for (int c = 0; c < 6; ++c) d += llabs((long long)a[c] - (long long)b[c]);
+    return d;
+}
+
+/* Agglomerative SGGX-H of n candidate lobes (S6 + weight each, in candidate order) to at
+ * most K lobes.  Output lobes sorted by weight (descending), ties by creation index.
+ * Returns the output count; merges_out (optional) receives (i, j) creation ids per merge. */
+ORC_API int vxo_sggx_h(const float* cand, int n, int K, const float* dirs, int N,
+                       float* out, int32_t* merges_out) {
+    int cap = 2 * n + 1;
+    float* S = (float*)malloc(sizeof(float) * 6 * (size_t)cap);
+    float* wgt = (float*)malloc(sizeof(float) * (size_t)cap);
+    float* Mh = (float*)malloc(sizeof(float) * 6 * (size_t)cap);
+    int32_t* H = (int32_t*)malloc(sizeof(int32_t) * 6 * (size_t)cap);
+    int* alive = (int*)calloc((size_t)cap, sizeof(int));
+    for (int i = 0; i < n; ++i) {
+        memcpy(S + 6 * i, cand + 7 * i, 6 * sizeof(float));
+        wgt[i] = cand[7 * i + 6];
+        alive[i] = 1;
+    }
+    int count = n, next = n, nm = 0;
+    if (n > K) {
+        for (int i = 0; i < n; ++i) vxo_sample_lobe(S + 6 * i, dirs, N, H + 6 * i, Mh + 6 * i);
+        while (count > K) {
+            int bi = -1, bj = -1;
+            int64_t best = 0;
+            for (int i = 0; i < next; ++i) {
+                if (!alive[i]) continue;
+                for (int j = 0; j < i; ++j) {
+                    if (!alive[j]) continue;
+                    int64_t dd = vxo_hist_dist(H + 6 * i, H + 6 * j);
+                    if (bi < 0 || dd < best) { best = dd; bi = i; bj = j; }
+                }
+            }
+            for (int c = 0; c < 6; ++c) S[6 * next + c] = (Mh[6 * bi + c] + Mh[6 * bj + c]) * 0.5f;
+            wgt[next] = wgt[bi] + wgt[bj];
+            vxo_sample_lobe(S + 6 * next, dirs, N, H + 6 * next, Mh + 6 * next);
+            alive[bi] = 0; alive[bj] = 0; alive[next] = 1;
+            if (merges_out) { merges_out[2 * nm] = bi; merges_out[2 * nm + 1] = bj; }
+            ++nm; ++next; --count;
+        }
+    }
+    /* gather alive ids in creation order, then stable selection by weight desc */
+    int ids[64 * 2 + 1];
+    int na = 0;
+    for (int i = 0; i < next; ++i) if (alive[i]) ids[na++] = i;
+    for (int a = 1; a < na; ++a) {         /* insertion sort: stable */
+        int x = ids[a], b = a - 1;
+        while (b >= 0 && wgt[ids[b]] < wgt[x]) { ids[b + 1] = ids[b]; --b; }
+        ids[b + 1] = x;
+    }
+    for (int a = 0; a < na; ++a) {
+        memcpy(out + 7 * a, S + 6 * ids[a], 6 * sizeof(float));
+        out[7 * a + 6] = wgt[ids[a]];
+    }
+    free(S); free(wgt); free(Mh); free(H); free(alive);
+    return na;
+}
+
+/* ------------------------------------------------------------------------- */
+/* LoD: level l -> l+1 (Sec. 4.2 density by projection, 4.3 2x2x2, 4.4 SGGX-H) */
+/* ------------------------------------------------------------------------- */
+ORC_API int vxo_lod_step(const vxo_level* in, int K, const float* dirs, int N, vxo_level* out) {
+    int64_t np = 0;
+    for (int64_t i = 0; i < in->n; ++i)
+        if (i == 0 || (in->keys[i] >> 3) != (in->keys[i - 1] >> 3)) ++np;
+    level_alloc(out, np, K);
+    float cand[8 * 16 * 7];
+    int64_t v = 0;
+    for (int64_t i = 0; i < in->n;) {
+        int64_t j = i;
+        uint64_t pk = in->keys[i] >> 3;
+        float m = 0.0f, M[6] = {0, 0, 0, 0, 0, 0};
+        double m64 = 0.0, M64[6] = {0, 0, 0, 0, 0, 0};
+        uint64_t pm[8] = {0};
+        int nc = 0;
+        while (j < in->n && (in->keys[j] >> 3) == pk) {
+            int oct = (int)(in->keys[j] & 7ull);
+            int ox = oct & 1, oy = (oct >> 1) & 1, oz = (oct >> 2) & 1;
+            m = m + in->mass[j];
+            m64 += in->mass64[j];
+            for (int c = 0; c < 6; ++c) {
+                M[c] = M[c] + in->moment[6 * j + c];
+                M64[c] += in->moment64[6 * j + c];
+            }
+            const uint64_t* cm = in->mask + 8 * j;
+            for (int pz = 4 * oz; pz < 4 * oz + 4; ++pz)
+                for (int py = 4 * oy; py < 4 * oy + 4; ++py)
+                    for (int px = 4 * ox; px < 4 * ox + 4; ++px) {
+                        int bit = 0;
+                        for (int dz = 0; dz < 2; ++dz)
+                            for (int dy = 0; dy < 2; ++dy)
+                                for (int dx = 0; dx < 2; ++dx)
+                                    bit |= mask_get(cm, 2 * (px & 3) + dx, 2 * (py & 3) + dy, 2 * (pz & 3) + dz);
+                        if (bit) mask_set(pm, px, py, pz);
+                    }
+            const float* cl = in->lobes + (size_t)j * in->K * 7;
+            for (int l = 0; l < in->lobe_count[j]; ++l) {
+                memcpy(cand + 7 * nc, cl + 7 * l, 7 * sizeof(float));
+                ++nc;
+            }
+            ++j;
+        }
+        out->keys[v] = pk;
+        memcpy(out->mask + 8 * v, pm, sizeof(pm));
+        out->mass[v] = m;
+        memcpy(out->moment + 6 * v, M, sizeof(M));
+        out->mass64[v] = m64;
+        memcpy(out->moment64 + 6 * v, M64, sizeof(M64));
+        mask_stats(pm, &out->occ[v], &out->proj[3 * v]);
+        if (K == 1) {
+            single_lobe(out, v);
+        } else {
+            float res[16 * 7];
+            int nl = vxo_sggx_h(cand, nc, K, dirs, N, res, NULL);
+            float* lo = out->lobes + (size_t)v * K * 7;
+            memcpy(lo, res, (size_t)nl * 7 * sizeof(float));
+            for (int l = 0; l < nl; ++l) vxo_compact(lo + 7 * l, out->compact + ((size_t)v * K + l) * 6);
+            out->lobe_count[v] = (uint8_t)nl;
+        }
+        ++v;
+        i = j;
+    }
+    return 0;
+}
+
+/* Attributes of a given list of voxels, computed from all fiber primitives by brute
+ * force (used to check full-size runs on sampled voxels).  Outputs per key: mask[8],
+ * mass, moment[6] (FP32 chain) and mass64, moment64[6]. */
+ORC_API int vxo_fiber_voxels(const float* ctrl, const int64_t* offsets, int64_t F,
+                             const float* weights, const vxo_grid* g,
+                             const uint64_t* keys, int64_t nk,
+                             uint64_t* mask, float* mass, float* moment,
+                             double* mass64, double* moment64) {
+    const float s = 1.0f / g->voxel_size;
+    for (int64_t q = 0; q < nk; ++q) {
+        uint32_t vi, vj, vk;
+        vxo_demorton(keys[q], &vi, &vj, &vk);
+        uint64_t m8[8] = {0};
+        float m = 0.0f, M[6] = {0, 0, 0, 0, 0, 0};
+        double m64 = 0.0, M64[6] = {0, 0, 0, 0, 0, 0};
+        int64_t prim = 0;
+        for (int64_t f = 0; f < F; ++f) {
+            for (int64_t c = offsets[f]; c + 1 < offsets[f + 1]; ++c, ++prim) {
+                const float* pa = ctrl + 4 * c;
+                const float* pb = ctrl + 4 * (c + 1);
+                float A[3], B[3];
+                double A64[3], B64[3];
+                for (int i = 0; i < 3; ++i) {
+                    A[i] = (pa[i] - g->origin[i]) * s;
+                    B[i] = (pb[i] - g->origin[i]) * s;
+                    A64[i] = (double)A[i];
+                    B64[i] = (double)B[i];
+                }
+                float rg = ((pa[3] + pb[3]) * 0.5f) * s;
+                double rg64 = (double)rg;
+                double vv[3] = {(double)vi, (double)vj, (double)vk};
+                int skip = 0;
+                for (int i = 0; i < 3; ++i) {
+                    double mn = fmin(A64[i], B64[i]) - rg64 - 1.0, mx = fmax(A64[i], B64[i]) + rg64 + 1.0;
+                    if (vv[i] + 1.0 < mn || vv[i] > mx) skip = 1;
+                }
+                if (skip) continue;
+                uint64_t pm[8];
+                vxo_capsule_mask(A, B, rg, (int)vi, (int)vj, (int)vk, pm);
+                for (int w = 0; w < 8; ++w) m8[w] |= pm[w];
+                float mu = vxo_capsule_measure(A, B, rg, (int)vi, (int)vj, (int)vk);
+                if (mu == 0.0f) continue;
+                float w = weights ? weights[prim] : 1.0f;
+                float d[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+                float dn = sqrtf((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+                float t[3] = {d[0] / dn, d[1] / dn, d[2] / dn};
+                float cc = w * mu;
+                m = m + cc;
+                M[0] = M[0] + cc * (t[0] * t[0]);
+                M[1] = M[1] + cc * (t[1] * t[1]);
+                M[2] = M[2] + cc * (t[2] * t[2]);
+                M[3] = M[3] + cc * (t[0] * t[1]);
+                M[4] = M[4] + cc * (t[0] * t[2]);
+                M[5] = M[5] + cc * (t[1] * t[2]);
+                double d64[3] = {B64[0] - A64[0], B64[1] - A64[1], B64[2] - A64[2]};
+                double dn64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
+                double t64[3] = {d64[0] / dn64, d64[1] / dn64, d64[2] / dn64};
+                double c64 = (double)w * capsule_measure64(A64, B64, rg64, (int)vi, (int)vj, (int)vk);
+                m64 += c64;
+                M64[0] += c64 * t64[0] * t64[0];
+                M64[1] += c64 * t64[1] * t64[1];
+                M64[2] += c64 * t64[2] * t64[2];
+                M64[3] += c64 * t64[0] * t64[1];
+                M64[4] += c64 * t64[0] * t64[2];
+                M64[5] += c64 * t64[1] * t64[2];
+            }
+        }
+        memcpy(mask + 8 * q, m8, sizeof(m8));
+        mass[q] = m;
+        memcpy(moment + 6 * q, M, sizeof(M));
+        mass64[q] = m64;
+        memcpy(moment64 + 6 * q, M64, sizeof(M64));
+    }
+    return 0;
+}
