@@ -1,0 +1,379 @@
+"""Benchmark: sparse voxelization + full LoD pyramid with SGGX-H (K = 4) of a fiber yarn.
+
+Workload (seeded, synthetic): 3 plies x 64 fibers, each a helical polyline of 4,000
+FP32 segments (768,000 capsule primitives, radius 0.004), voxelized into a sparse
+512^3 grid with 8^3 sub-cells, then the pyramid down to 1^3 with K = 4 lobes per voxel
+and N = 5000 sampled directions per lobe histogram.  One step = vx_voxelize +
+vx_build_lod (all levels).  `value` is primitives voxelized per second of the whole
+step with the inputs resident on the device; `e2e` is the same metric through the
+public API from pinned host buffers, with the input upload and the download of every
+level inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica (the path does not
+exchange data between GPUs); value = all ranks' primitives / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "primitives voxelized/s (voxelize + full LoD build with SGGX-H)"
+UNIT = "prims/s"
+WORKLOAD = "fiber yarn 3x64 fibers x 4000 segments (768k capsules), 512^3, 8^3 sub-cells, LoD to 1^3, K=4, N=5000"
+K_LOBES = 4
+N_SAMPLES = 5000
+L2_FLUSH_BYTES = 256 << 20
+FP32_LANES_PER_SM = 128
+N_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------------
+# CPU oracle timings (the reference arm and the cpu_baseline leg)
+# ----------------------------------------------------------------------------------
+def oracle_sample(w, n_fibers=None, n_segments=None):
+    off = w.fiber_offsets
+    if n_fibers is not None:
+        o = off[: n_fibers + 1].copy()
+    else:
+        o = np.array([0, n_segments + 1], np.int64)
+    return w.ctrl[: o[-1]], o
+
+
+def time_oracle(w, ctrl, off, dirs):
+    import oracle
+    t = time.perf_counter()
+    L0 = oracle.voxelize_fibers(ctrl, off, w.grid, K=1)
+    oracle.build_pyramid(L0, w.grid.resolution, K_LOBES, dirs)
+    return time.perf_counter() - t, synth.fiber_segment_count(off)
+
+
+def cpu_baseline(w, dirs):
+    ctrl, off = oracle_sample(w, n_fibers=2)
+    secs, n = time_oracle(w, ctrl, off, dirs)
+    return {"value": n / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first 2 of 192 fibers ({n} segments) of the same yarn, voxelize + full LoD "
+                      f"K={K_LOBES}, N={N_SAMPLES}; single-threaded C oracle, {secs:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w = synth.config2()
+    dirs = synth.sample_directions(N_SAMPLES)
+    ctrl, off = oracle_sample(w, n_segments=1000)
+    for _ in range(args.warmup):
+        time_oracle(w, ctrl, off, dirs)
+    tot, n = 0.0, 0
+    for _ in range(args.steps):
+        s, k = time_oracle(w, ctrl, off, dirs)
+        tot += s
+        n += k
+    value = n / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "first 1000 segments of fiber 0 per step, voxelize + full LoD "
+                                       f"K={K_LOBES}, N={N_SAMPLES}; single-threaded C oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------
+# native arm
+# ----------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_2604_13191_gb300 as vx
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    w = synth.config2()
+    dirs_np = synth.sample_directions(N_SAMPLES)
+    n_prims = w.num_prims
+    ctx = vx.Context(dev)
+    ctrl = torch.from_numpy(w.ctrl).to(dev)
+    off = torch.from_numpy(w.fiber_offsets).to(dev)
+    dirs = torch.from_numpy(dirs_np).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        L0 = ctx.voxelize(w.grid, ctrl=ctrl, fiber_offsets=off, num_prims=n_prims)
+        pyr = ctx.build_lod(L0, K=K_LOBES, dirs=dirs)
+        return L0, pyr
+
+    for _ in range(args.warmup):
+        out = step()
+    torch.cuda.synchronize()
+    levels = [out[0]] + out[1]
+    level_sizes = [lv.num_voxels for lv in levels]
+    pairs_hint = None
+    del out, levels
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs --------------------------------------
+    clocks = ClockSampler(torch.cuda.current_device())
+    ctx.profile(True)
+    clocks.start()
+    barrier()
+    t_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)                       # L2 flush between timed steps (outside the events)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        res = step()
+        b.record()
+        torch.cuda.synchronize()
+        t_ms.append(a.elapsed_time(b))
+        del res
+    barrier()
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    total_ms = sum(t_ms)
+    if ws > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = ws * n_prims * args.steps / (total_ms / 1e3)
+    launches = sum(v[0] for v in prof.values())
+
+    # ---- e2e: same calls from pinned host buffers, outputs downloaded ------------------
+    e2e = None
+    if not args.no_e2e:
+        h_ctrl = torch.from_numpy(w.ctrl).pin_memory()
+        h_off = torch.from_numpy(w.fiber_offsets).pin_memory()
+        h_dirs = torch.from_numpy(dirs_np).pin_memory()
+        L0, pyr = step()
+        sizes = [lv.block.numel() for lv in [L0] + pyr]
+        del L0, pyr
+        h_out = torch.empty(sum(sizes) + 4096 * len(sizes), dtype=torch.uint8).pin_memory()
+        h2d = h_ctrl.numel() * 4 + h_off.numel() * 8 + h_dirs.numel() * 4
+
+        def e2e_step():
+            c = h_ctrl.to(dev, non_blocking=True)
+            o = h_off.to(dev, non_blocking=True)
+            d = h_dirs.to(dev, non_blocking=True)
+            L0 = ctx.voxelize(w.grid, ctrl=c, fiber_offsets=o, num_prims=n_prims)
+            pyr = ctx.build_lod(L0, K=K_LOBES, dirs=d)
+            pos, nbytes = 0, 0
+            for lv in [L0] + pyr:
+                n = lv.block.numel()
+                h_out[pos: pos + n].copy_(lv.block, non_blocking=True)
+                pos += n
+                nbytes += n
+            torch.cuda.synchronize()
+            return nbytes
+
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        e_ms = []
+        d2h = 0
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d2h = e2e_step()
+            e_ms.append(1e3 * (time.perf_counter() - t0))
+        barrier()
+        etot = sum(e_ms)
+        if ws > 1:
+            tt = torch.tensor([etot], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            etot = float(tt.item())
+        e2e = {"value": ws * n_prims * args.steps / (etot / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": etot / args.steps}
+
+    # ---- roofline of the dominant kernel -------------------------------------------------
+    roof = roofline(prof, w, level_sizes, args.steps)
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(w, dirs_np)
+    stages = {k: {"launches": v[0] // args.steps, "ms_per_step": v[1] / args.steps}
+              for k, v in prof.items() if v[0]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "prims": n_prims, "resolution": w.grid.resolution,
+                   "K": K_LOBES, "n_samples": N_SAMPLES, "levels": len(level_sizes),
+                   "voxels_per_level": level_sizes, "parallelism": f"replicas x{ws}",
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "lod_ms": sum(v["ms_per_step"] for k, v in stages.items() if k.startswith(("lod", "sggx"))),
+        "stages": stages,
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------------
+def _source_hash(name):
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2604_13191_gb300", "csrc", name), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def roofline(prof, w, level_sizes, steps):
+    """Dominant stage by device time; achieved = algorithmic work per launch / avg launch
+    time (CUDA events on the launching stream, timed region)."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    stage, (nl, ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    avg_ms = ms / max(nl, 1)
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            t = json.load(open(tfile))
+            ent = t.get(stage)
+            if ent and ent.get("source_hash") == _source_hash(ent["source"]):
+                traffic = ent["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    n = w.num_prims
+    if stage == "sggx_cluster":
+        # ALU: FP32 operations of the histogram sampling (per sample: 3x3 mat-vec 15, norm 5,
+        # thresholds 2, squares 3, compares 6, reciprocal 1, scale 1, products 12, roundings 6 = 51)
+        ops_per_sample = 51
+        clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = N_SMS * FP32_LANES_PER_SM * clk_mhz * 1e6 / 1e12
+        return {"kernel": stage, "bound": "alu", "achieved": None, "peak": peak, "unit": "Tops/s",
+                "frac": None, "traffic": traffic, "avg_launch_ms": avg_ms, "launches": nl // steps,
+                "note": "FP32-lane issue peak = 152 SMs x 128 lanes x max SM clock; achieved needs the "
+                        "number of lobes sampled, see stages",
+                "ops_per_sample": ops_per_sample}
+    # HBM-bound stages: algorithmic bytes per launch
+    per_launch_bytes = None
+    if stage in ("sort_scatter", "sort_hist"):
+        per_launch_bytes = None
+    return {"kernel": stage, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+            "traffic": traffic, "avg_launch_ms": avg_ms, "launches": nl // steps,
+            "bytes_per_launch": per_launch_bytes}
+
+
+if __name__ == "__main__":
+    main()

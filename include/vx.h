@@ -1,0 +1,201 @@
+/*
+ * vx.h -- C ABI of the GB300 (sm_103a) sparse microgeometry voxelizer.
+ *
+ * The library turns triangles or explicit fiber segments into a sparse voxel grid with
+ * per-voxel occupancy, mass and SGGX second moments, and builds the bottom-up LoD
+ * pyramid with hierarchical SGGX clustering (SGGX-H).  Paper: Fabre, Castillo,
+ * Rodriguez-Pardo, Lopez-Moreno, "Fast Voxelization and Level of Detail for
+ * Microgeometry Rendering": Sec. 3 (voxelization for data aggregation), Sec. 4
+ * (SGGX fit, density LoD, SGGX-H), Eq. compact-sggx, Eq. similarity.
+ *
+ * Conventions for every entry point:
+ *   - All pointer arguments named "device" are device (GPU) pointers of the current
+ *     device; "host" pointers are CPU memory.  Inputs are read-only and owned by the
+ *     caller; they must stay valid until the work on `stream` has completed.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - Outputs of a level are carved from ONE block obtained from the context's
+ *     allocator; the caller owns it and returns it with vx_level_release().
+ *   - Every call returns a vx_status; nothing aborts or traps.  On an error the
+ *     outputs are left unallocated (block == NULL).
+ *   - Calls are deterministic: the same inputs give bit-identical outputs.
+ *   - A context is not thread-safe: use one context per host thread / stream.
+ */
+#ifndef VX_H_
+#define VX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VX_API __attribute__((visibility("default")))
+#else
+#define VX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VX_OK = 0,
+    VX_ERR_INVALID_ARG = 1,   /* bad pointer, size, alignment or inconsistent counts   */
+    VX_ERR_OUT_OF_MEMORY = 2, /* the allocator returned NULL                           */
+    VX_ERR_CAPACITY = 3,      /* an internal 32-bit index range would overflow         */
+    VX_ERR_CUDA = 4,          /* a CUDA runtime call failed (see vx_last_cuda_error)   */
+    VX_ERR_TIMEOUT = 5,       /* a bounded wait gave up                                */
+    VX_ERR_UNSUPPORTED = 6    /* a parameter outside the supported range               */
+} vx_status;
+
+/* Device-memory allocator used for workspace and outputs.  alloc(ctx, bytes, stream)
+ * returns a device pointer aligned to at least 256 bytes, or NULL; free(ctx, p, stream)
+ * releases it (stream-ordered).  A NULL allocator means cudaMallocAsync/cudaFreeAsync. */
+typedef struct {
+    void* ctx;
+    void* (*alloc)(void* ctx, size_t bytes, void* stream);
+    void (*free)(void* ctx, void* p, void* stream);
+} vx_allocator;
+
+/* Cubic grid (Sec. 3.1: positions normalised to [0, Resolution) per axis).  Voxel (i,j,k)
+ * covers origin + voxel_size * [i,i+1] x [j,j+1] x [k,k+1].  Grid coordinates are
+ * u = (p - origin) * (1 / voxel_size), evaluated in FP32.
+ * resolution: power of two, 1..1024.  sub_res: sub-cells per voxel edge; 8 (the paper's
+ * third-level resolution, Sec. 3.1) is the supported value. */
+typedef struct {
+    float origin[3];
+    float voxel_size;
+    uint32_t resolution;
+    uint32_t sub_res;
+} vx_grid;
+
+enum { VX_TRIANGLES = 0, VX_FIBERS = 1 };
+
+/* Primitives (Sec. 3.1 node records; Sec. 3.2 splines and triangles).
+ * VX_TRIANGLES: tri_verts (device) [num_prims][3][4] float, xyz + unused w, 16-byte
+ *   aligned; triangles do not share vertices.
+ * VX_FIBERS: ctrl (device) [num_ctrl][4] float, xyz + radius, 16-byte aligned;
+ *   fiber_offsets (device) [num_fibers+1] int64, fiber f owns ctrl[off[f] .. off[f+1]-1];
+ *   segment s of fiber f joins ctrl[off[f]+s] and ctrl[off[f]+s+1] and is a capsule whose
+ *   radius is the mean of its two control-point radii.  Primitive ids count segments
+ *   fiber by fiber; num_prims must equal sum_f max(off[f+1]-off[f]-1, 0) (checked on the
+ *   device; a mismatch returns VX_ERR_INVALID_ARG).
+ * weights (device) [num_prims] float >= 0, or NULL for all ones. */
+typedef struct {
+    int32_t kind;
+    int64_t num_prims;
+    const float* tri_verts;
+    const float* ctrl;
+    int64_t num_ctrl;
+    const int64_t* fiber_offsets;
+    int64_t num_fibers;
+    const float* weights;
+} vx_primitives;
+
+/* One level of the pyramid, all arrays device pointers into `block`, rows sorted by key.
+ *   keys       [n]      uint64 Morton key (x bit 0, y bit 1, z bit 2 of each triple);
+ *                        the parent of key k is k >> 3.
+ *   mask       [n][8]   uint64 8^3 sub-cell occupancy; word z, bit x + 8*y.
+ *   mass       [n]      float  m = sum of w * mu over the voxel (mu: clipped fiber volume
+ *                        pi r^2 * length, or clipped triangle area, in voxel units of
+ *                        level 0).
+ *   moment     [n][6]   float  M = sum w * mu * d d^T (d: unit tangent / face normal),
+ *                        order xx, yy, zz, xy, xz, yz.
+ *   occ        [n]      uint16 number of occupied sub-cells (O = occ / 512, Sec. 3.5).
+ *   occ_proj   [n][3]   uint8  occupied cells of the projections along x, y, z
+ *                        (the YZ, XZ, XY planes of Sec. 3.5), each of 64.
+ *   lobe_count [n]      uint8  number of SGGX lobes (<= K).
+ *   lobes      [n][K][7] float S (xx,yy,zz,xy,xz,yz, trace 1) + weight, sorted by
+ *                        weight (descending).
+ *   compact    [n][K][6] float sigma_x, sigma_y, sigma_z, r_xy, r_xz, r_yz of each lobe
+ *                        (Eq. compact-sggx). */
+typedef struct {
+    int32_t level;
+    int32_t resolution;
+    int64_t num_voxels;
+    int32_t K;
+    void* block;
+    uint64_t* keys;
+    uint64_t* mask;
+    float* mass;
+    float* moment;
+    uint16_t* occ;
+    uint8_t* occ_proj;
+    uint8_t* lobe_count;
+    float* lobes;
+    float* compact;
+} vx_level;
+
+typedef struct vx_context vx_context;
+
+/* Creates a context holding the allocator and a reusable workspace.  alloc may be NULL.
+ * Errors: VX_ERR_INVALID_ARG (out == NULL), VX_ERR_OUT_OF_MEMORY. */
+VX_API vx_status vx_context_create(const vx_allocator* alloc, vx_context** out);
+
+/* Releases the workspace and the context (after synchronising its last stream). */
+VX_API void vx_context_destroy(vx_context* ctx);
+
+/* Sparse voxelization (Sec. 3.1-3.5, Sec. 4.1): level 0 of the pyramid.
+ * For every voxel v and sub-cell c: bit(c) = closed-box overlap of c with some primitive
+ * (capsule: segment inflated by its radius; triangle: separating-axis test).  A voxel is
+ * output iff its mask is non-zero.  mass / moment sum the primitives in increasing id
+ * order; lobes hold the single normalised lobe S = M / m (weight m) when m > 0 (K = 1).
+ * Voxels outside [0, resolution)^3 are dropped.  Synchronises the stream three times to size
+ * its outputs.  Errors: VX_ERR_INVALID_ARG, VX_ERR_UNSUPPORTED (resolution > 1024 or
+ * sub_res != 8), VX_ERR_OUT_OF_MEMORY, VX_ERR_CAPACITY (more than 2^32-1 candidate
+ * voxel/primitive pairs), VX_ERR_CUDA. */
+VX_API vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
+                      void* stream, vx_level* out0);
+
+/* LoD parameters (Sec. 4.2-4.4).
+ *   num_levels: number of coarser levels to build; 0 = down to 1^3 (log2 resolution).
+ *   K: lobe cap per voxel, 1..8 (1 = the plain 2x2x2 moment aggregation of Sec. 4.3).
+ *   n_samples, dirs: the N fixed unit directions (device, [n_samples][3] float) each SGGX
+ *     lobe is sampled with for its histogram (Sec. 4.4, N = 5000 in the paper); only read
+ *     when K > 1.  1 <= n_samples <= 65536. */
+typedef struct {
+    int32_t num_levels;
+    int32_t K;
+    int32_t n_samples;
+    const float* dirs;
+} vx_lod_params;
+
+/* Bottom-up pyramid from level `in` (usually level 0): out[0..L-1] are levels
+ * in->level+1 .. in->level+L.  Per parent (key >> 3): mass and moment are the sums of
+ * its children in key order; the mask is the OR of each child's 2x2x2 sub-cell groups
+ * placed in the child's octant; occ / occ_proj are recounted (Sec. 4.2).  Lobes: K = 1
+ * gives S = M / m.  K > 1 runs SGGX-H (Sec. 4.4, Eq. similarity) on the children's lobes:
+ * every lobe gets a 5-bin-per-axis histogram of N sampled directions, the pair with the
+ * smallest sliced Wasserstein-1 distance is merged (pooled-sample second moment, weights
+ * added) until at most K remain.  Synchronises the stream once to size the levels.
+ * Errors: VX_ERR_INVALID_ARG, VX_ERR_UNSUPPORTED (K out of range), VX_ERR_OUT_OF_MEMORY,
+ * VX_ERR_CUDA. */
+VX_API vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_lod_params* params,
+                       void* stream, vx_level* out);
+
+/* Returns a level's block to the context's allocator and clears the struct. */
+VX_API void vx_level_release(vx_context* ctx, vx_level* level, void* stream);
+
+/* Per-stage timing (opt-in).  With profiling enabled, every kernel launch of the
+ * library is bracketed by CUDA events on its stream; vx_profile_read synchronises
+ * those events and returns, per stage, the number of launches and their summed device
+ * time.  Launch counts are kept even when timing is disabled.  enable != 0 also resets
+ * the counters.  out may be NULL to query the number of stages. */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} vx_stage_time;
+
+VX_API vx_status vx_profile_enable(vx_context* ctx, int enable);
+VX_API vx_status vx_profile_read(vx_context* ctx, vx_stage_time* out, int max_stages, int* num_stages);
+
+/* Static description of a status code. */
+VX_API const char* vx_status_string(vx_status s);
+
+/* The last CUDA error string seen by this context ("" if none). */
+VX_API const char* vx_last_cuda_error(const vx_context* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VX_H_ */

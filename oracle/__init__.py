@@ -96,6 +96,8 @@ def _load():
             lib.vxo_fiber_voxels.restype = C.c_int
             lib.vxo_fiber_voxels.argtypes = [P, P, C.c_int64, P, C.POINTER(_Grid), P, C.c_int64,
                                              P, P, P, P, P]
+            lib.vxo_level_from_voxels.restype = C.c_int
+            lib.vxo_level_from_voxels.argtypes = [P, P, P, P, P, P, C.c_int64, C.POINTER(_Level)]
             _lib = lib
     return _lib
 
@@ -304,3 +306,17 @@ def fiber_voxels(ctrl, offsets, grid, keys, weights=None) -> dict:
                              C.byref(G), _ptr(keys), nk, _ptr(mask), _ptr(mass), _ptr(mom),
                              _ptr(mass64), _ptr(mom64))
     return {"mask": mask, "mass": mass, "moment": mom, "mass64": mass64, "moment64": mom64}
+
+
+def level_from_voxels(keys, vox: dict) -> dict:
+    """Level-0 dict (oracle layout) from brute-force voxel attributes (fiber_voxels);
+    keys must be sorted; voxels with an empty mask are dropped."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    order = np.argsort(keys, kind="stable")
+    keys = keys[order]
+    arrs = [np.ascontiguousarray(vox[k][order]) for k in ("mask", "mass", "moment", "mass64", "moment64")]
+    L = _Level()
+    _load().vxo_level_from_voxels(_ptr(keys), *[_ptr(a) for a in arrs], int(keys.shape[0]), C.byref(L))
+    d = _level_to_dict(L)
+    _load().vxo_level_free(C.byref(L))
+    return d

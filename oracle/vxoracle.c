@@ -1016,3 +1016,33 @@ ORC_API int vxo_fiber_voxels(const float* ctrl, const int64_t* offsets, int64_t 
     }
     return 0;
 }
+
+/* A level from per-voxel primaries (keys sorted, non-zero masks): recomputes occupancy,
+ * projections and the single normalised lobe exactly as the voxelization does. */
+ORC_API int vxo_level_from_voxels(const uint64_t* keys, const uint64_t* mask, const float* mass,
+                                  const float* moment, const double* mass64, const double* moment64,
+                                  int64_t n, vxo_level* out) {
+    int64_t nv = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t any = 0;
+        for (int w = 0; w < 8; ++w) any |= mask[8 * i + w];
+        if (any) ++nv;
+    }
+    level_alloc(out, nv, 1);
+    int64_t v = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t any = 0;
+        for (int w = 0; w < 8; ++w) any |= mask[8 * i + w];
+        if (!any) continue;
+        out->keys[v] = keys[i];
+        memcpy(out->mask + 8 * v, mask + 8 * i, 64);
+        out->mass[v] = mass[i];
+        memcpy(out->moment + 6 * v, moment + 6 * i, 24);
+        out->mass64[v] = mass64[i];
+        memcpy(out->moment64 + 6 * v, moment64 + 6 * i, 48);
+        mask_stats(out->mask + 8 * v, &out->occ[v], &out->proj[3 * v]);
+        single_lobe(out, v);
+        ++v;
+    }
+    return 0;
+}

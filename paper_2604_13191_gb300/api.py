@@ -1,0 +1,320 @@
+"""Thin Python binding of the C ABI in include/vx.h (argument marshalling only).
+
+Every step of the voxelization / LoD path runs in the CUDA library libvx.so; this
+module passes device pointers of torch tensors, supplies torch's caching allocator as
+the library's allocator, and wraps the returned level blocks as typed tensor views.
+There is no CPU fallback: if the library cannot be loaded the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+VX_TRIANGLES, VX_FIBERS = 0, 1
+STATUS = {0: "VX_OK", 1: "VX_ERR_INVALID_ARG", 2: "VX_ERR_OUT_OF_MEMORY", 3: "VX_ERR_CAPACITY",
+          4: "VX_ERR_CUDA", 5: "VX_ERR_TIMEOUT", 6: "VX_ERR_UNSUPPORTED"}
+
+
+class VxError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+class VxGrid(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("voxel_size", C.c_float), ("resolution", C.c_uint32),
+                ("sub_res", C.c_uint32)]
+
+
+class VxPrimitives(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("num_prims", C.c_int64), ("tri_verts", C.c_void_p),
+                ("ctrl", C.c_void_p), ("num_ctrl", C.c_int64), ("fiber_offsets", C.c_void_p),
+                ("num_fibers", C.c_int64), ("weights", C.c_void_p)]
+
+
+class VxLevel(C.Structure):
+    _fields_ = [("level", C.c_int32), ("resolution", C.c_int32), ("num_voxels", C.c_int64),
+                ("K", C.c_int32), ("block", C.c_void_p), ("keys", C.c_void_p), ("mask", C.c_void_p),
+                ("mass", C.c_void_p), ("moment", C.c_void_p), ("occ", C.c_void_p),
+                ("occ_proj", C.c_void_p), ("lobe_count", C.c_void_p), ("lobes", C.c_void_p),
+                ("compact", C.c_void_p)]
+
+
+class VxLodParams(C.Structure):
+    _fields_ = [("num_levels", C.c_int32), ("K", C.c_int32), ("n_samples", C.c_int32),
+                ("dirs", C.c_void_p)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class VxAllocator(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN)]
+
+
+EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_lod",
+           "vx_level_release", "vx_status_string", "vx_last_cuda_error", "vx_profile_enable",
+           "vx_profile_read"]
+
+
+class VxStageTime(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Loads libvx.so (building it in-tree first if needed and nvcc exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"CUDA library not built: {_build.LIB} (run __graft_entry__.build())")
+        lib = C.CDLL(_build.LIB)
+        P = C.c_void_p
+        lib.vx_context_create.restype = C.c_int
+        lib.vx_context_create.argtypes = [C.POINTER(VxAllocator), C.POINTER(C.c_void_p)]
+        lib.vx_context_destroy.restype = None
+        lib.vx_context_destroy.argtypes = [P]
+        lib.vx_voxelize.restype = C.c_int
+        lib.vx_voxelize.argtypes = [P, C.POINTER(VxPrimitives), C.POINTER(VxGrid), P, C.POINTER(VxLevel)]
+        lib.vx_build_lod.restype = C.c_int
+        lib.vx_build_lod.argtypes = [P, C.POINTER(VxLevel), C.POINTER(VxLodParams), P, C.POINTER(VxLevel)]
+        lib.vx_level_release.restype = None
+        lib.vx_level_release.argtypes = [P, C.POINTER(VxLevel), P]
+        lib.vx_status_string.restype = C.c_char_p
+        lib.vx_status_string.argtypes = [C.c_int]
+        lib.vx_last_cuda_error.restype = C.c_char_p
+        lib.vx_last_cuda_error.argtypes = [P]
+        lib.vx_profile_enable.restype = C.c_int
+        lib.vx_profile_enable.argtypes = [P, C.c_int]
+        lib.vx_profile_read.restype = C.c_int
+        lib.vx_profile_read.argtypes = [P, C.POINTER(VxStageTime), C.c_int, C.POINTER(C.c_int)]
+        _lib = lib
+        return lib
+
+
+class _TorchAllocator:
+    """Device memory for the library from torch's caching allocator (current stream)."""
+
+    def __init__(self, device):
+        self.device = device
+        self.live = {}
+        self._a = ALLOC_FN(self._alloc)
+        self._f = FREE_FN(self._free)
+        self.struct = VxAllocator(None, self._a, self._f)
+
+    def _alloc(self, ctx, nbytes, stream):
+        try:
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        except Exception:      # out of memory: the library reports VX_ERR_OUT_OF_MEMORY
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _free(self, ctx, p, stream):
+        self.live.pop(p, None)
+
+    def take(self, p):
+        return self.live.pop(p, None)
+
+
+@dataclass
+class Level:
+    """One pyramid level: typed views of a block owned by this object."""
+    level: int
+    resolution: int
+    num_voxels: int
+    K: int
+    keys: torch.Tensor        # int64 [n] (Morton keys, bit pattern of uint64)
+    mask: torch.Tensor        # int64 [n, 8] (bit patterns of uint64 words)
+    mass: torch.Tensor        # float32 [n]
+    moment: torch.Tensor      # float32 [n, 6]
+    occ: torch.Tensor         # int16 [n] (uint16 values <= 512)
+    occ_proj: torch.Tensor    # uint8 [n, 3]
+    lobe_count: torch.Tensor  # uint8 [n]
+    lobes: torch.Tensor       # float32 [n, K, 7]
+    compact: torch.Tensor     # float32 [n, K, 6]
+    block: torch.Tensor
+    _c: VxLevel
+
+    def host(self) -> dict:
+        """Copies every array to host numpy arrays (uint64 views restored)."""
+        import numpy as np
+        d = {}
+        for k in ("keys", "mask", "mass", "moment", "occ", "occ_proj", "lobe_count", "lobes", "compact"):
+            d[k] = getattr(self, k).cpu().numpy()
+        d["keys"] = d["keys"].view(np.uint64)
+        d["mask"] = d["mask"].view(np.uint64)
+        d["occ"] = d["occ"].view(np.uint16)
+        d["proj"] = d.pop("occ_proj")
+        d["K"] = self.K
+        return d
+
+
+def _view(block: torch.Tensor, base: int, ptr: int, nbytes: int, dtype, shape):
+    off = ptr - base
+    return block[off: off + nbytes].view(dtype).view(*shape)
+
+
+class Context:
+    """A library context (allocator + reusable device workspace) on one CUDA device."""
+
+    def __init__(self, device=None):
+        self.lib = load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.alloc = _TorchAllocator(self.device)
+        h = C.c_void_p()
+        st = self.lib.vx_context_create(C.byref(self.alloc.struct), C.byref(h))
+        if st != 0:
+            raise VxError(st, "vx_context_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vx_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def profile(self, enable: bool = True):
+        """vx_profile_enable: per-launch CUDA-event timing of every library kernel."""
+        st = self.lib.vx_profile_enable(self.h, 1 if enable else 0)
+        if st != 0:
+            raise self._err(st, "vx_profile_enable")
+
+    def profile_read(self) -> dict:
+        """vx_profile_read: {stage: (launches, total device ms)} (synchronises)."""
+        n = C.c_int()
+        buf = (VxStageTime * 64)()
+        st = self.lib.vx_profile_read(self.h, buf, 64, C.byref(n))
+        if st != 0:
+            raise self._err(st, "vx_profile_read")
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(n.value)}
+
+    def _err(self, st, what):
+        detail = self.lib.vx_last_cuda_error(self.h).decode() if st == 4 else ""
+        return VxError(st, what, detail)
+
+    def _wrap(self, L: VxLevel) -> Level:
+        n, K = int(L.num_voxels), int(L.K)
+        block = self.alloc.take(L.block)
+        if block is None:
+            raise RuntimeError("level block was not allocated through this context")
+        base = block.data_ptr()
+        return Level(
+            level=int(L.level), resolution=int(L.resolution), num_voxels=n, K=K,
+            keys=_view(block, base, L.keys, n * 8, torch.int64, (n,)),
+            mask=_view(block, base, L.mask, n * 64, torch.int64, (n, 8)),
+            mass=_view(block, base, L.mass, n * 4, torch.float32, (n,)),
+            moment=_view(block, base, L.moment, n * 24, torch.float32, (n, 6)),
+            occ=_view(block, base, L.occ, n * 2, torch.int16, (n,)),
+            occ_proj=_view(block, base, L.occ_proj, n * 3, torch.uint8, (n, 3)),
+            lobe_count=_view(block, base, L.lobe_count, n, torch.uint8, (n,)),
+            lobes=_view(block, base, L.lobes, n * K * 28, torch.float32, (n, K, 7)),
+            compact=_view(block, base, L.compact, n * K * 24, torch.float32, (n, K, 6)),
+            block=block, _c=L)
+
+    def voxelize(self, grid, *, tri_verts=None, ctrl=None, fiber_offsets=None, weights=None,
+                 num_prims=None, stream=None) -> Level:
+        """vx_voxelize: level 0 from triangles ([T,3,4] float32) or fibers (ctrl [P,4]
+        float32, fiber_offsets [F+1] int64), all CUDA tensors on this context's device."""
+        P = VxPrimitives()
+        keep = []
+        if tri_verts is not None:
+            t = tri_verts.contiguous()
+            _check(t, torch.float32, self.device, "tri_verts")
+            keep.append(t)
+            P.kind = VX_TRIANGLES
+            P.num_prims = t.shape[0]
+            P.tri_verts = t.data_ptr()
+        else:
+            c = ctrl.contiguous()
+            o = fiber_offsets.contiguous()
+            _check(c, torch.float32, self.device, "ctrl")
+            _check(o, torch.int64, self.device, "fiber_offsets")
+            keep += [c, o]
+            P.kind = VX_FIBERS
+            P.ctrl = c.data_ptr()
+            P.num_ctrl = c.shape[0]
+            P.fiber_offsets = o.data_ptr()
+            P.num_fibers = o.shape[0] - 1
+            if num_prims is None:
+                oc = o.cpu()
+                num_prims = int(torch.clamp(oc[1:] - oc[:-1] - 1, min=0).sum())
+            P.num_prims = int(num_prims)
+        if weights is not None:
+            w = weights.contiguous()
+            _check(w, torch.float32, self.device, "weights")
+            keep.append(w)
+            P.weights = w.data_ptr()
+        G = _grid(grid)
+        L = VxLevel()
+        s = _stream(stream)
+        st = self.lib.vx_voxelize(self.h, C.byref(P), C.byref(G), s, C.byref(L))
+        if st != 0:
+            raise self._err(st, "vx_voxelize")
+        return self._wrap(L)
+
+    def build_lod(self, level: Level, *, K: int = 1, dirs=None, num_levels: int = 0,
+                  stream=None) -> list:
+        """vx_build_lod: levels level+1 .. level+L (L = num_levels, 0 = down to 1^3)."""
+        prm = VxLodParams()
+        prm.num_levels = int(num_levels)
+        prm.K = int(K)
+        if dirs is not None:
+            d = dirs.contiguous()
+            _check(d, torch.float32, self.device, "dirs")
+            prm.dirs = d.data_ptr()
+            prm.n_samples = d.shape[0]
+        R = level.resolution
+        L = int(num_levels) if num_levels else int(R).bit_length() - 1
+        outs = (VxLevel * max(L, 1))()
+        st = self.lib.vx_build_lod(self.h, C.byref(level._c), C.byref(prm), _stream(stream), outs)
+        if st != 0:
+            raise self._err(st, "vx_build_lod")
+        return [self._wrap(outs[i]) for i in range(L)]
+
+
+def _check(t, dtype, device, name):
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if t.device != device:
+        raise ValueError(f"{name}: expected a tensor on {device}, got {t.device}")
+
+
+def _grid(g) -> VxGrid:
+    G = VxGrid()
+    for i in range(3):
+        G.origin[i] = float(g.origin[i])
+    G.voxel_size = float(g.voxel_size)
+    G.resolution = int(g.resolution)
+    G.sub_res = int(getattr(g, "sub_res", 8))
+    return G
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)

@@ -1,0 +1,205 @@
+// vx_api.cu -- context, allocator plumbing and status strings of the C ABI.
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <new>
+
+#include "vx_internal.cuh"
+
+const char* const kStageNames[ST_NSTAGES] = {
+    "prep", "candidates_count", "candidates_emit", "scan", "sort_hist", "sort_scatter", "segment_heads",
+    "reduce_fibers", "reduce_tris", "finalize", "lod_counts", "lod_heads", "lod_reduce", "sggx_cluster"};
+
+static void vx_prof_drain(vx_context* ctx) {
+    for (int i = 0; i < ctx->nev; ++i) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(ctx->ev[i].b) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, ctx->ev[i].a, ctx->ev[i].b) == cudaSuccess)
+            ctx->stage_ms[ctx->ev[i].stage] += ms;
+    }
+    ctx->nev = 0;
+}
+
+void vx_stage_begin(vx_context* ctx, int stage, cudaStream_t s) {
+    ctx->launches[stage] += 1;
+    if (!ctx->prof || !ctx->ev) return;
+    if (ctx->nev == vx::kEventPool) vx_prof_drain(ctx);
+    vx::EventRec& r = ctx->ev[ctx->nev];
+    r.stage = stage;
+    cudaEventRecord(r.a, s);
+}
+
+void vx_stage_end(vx_context* ctx, cudaStream_t s) {
+    if (!ctx->prof || !ctx->ev) return;
+    cudaEventRecord(ctx->ev[ctx->nev].b, s);
+    ++ctx->nev;
+}
+
+void vx_record_cuda_error(vx_context* ctx, cudaError_t e, const char* what) {
+    if (!ctx) return;
+    snprintf(ctx->last_err, sizeof(ctx->last_err), "%s: %s", what, cudaGetErrorString(e));
+}
+
+void* vx_dev_alloc(vx_context* ctx, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 256;
+    if (ctx->own_alloc) {
+        void* p = nullptr;
+        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        if (e != cudaSuccess) {
+            vx_record_cuda_error(ctx, e, "cudaMallocAsync");
+            return nullptr;
+        }
+        return p;
+    }
+    return ctx->alloc.alloc(ctx->alloc.ctx, bytes, (void*)s);
+}
+
+void vx_dev_free(vx_context* ctx, void* p, cudaStream_t s) {
+    if (!p) return;
+    if (ctx->own_alloc) {
+        cudaFreeAsync(p, s);
+        return;
+    }
+    ctx->alloc.free(ctx->alloc.ctx, p, (void*)s);
+}
+
+vx_status vx_ws_ensure(vx_context* ctx, int slot, size_t bytes, cudaStream_t s) {
+    vx::Buf& b = ctx->ws[slot];
+    if (b.cap >= bytes && b.p) return VX_OK;
+    size_t want = bytes + bytes / 8 + 4096;   // a little headroom against regrowth
+    void* p = vx_dev_alloc(ctx, want, s);
+    if (!p) return VX_ERR_OUT_OF_MEMORY;
+    if (b.p) vx_dev_free(ctx, b.p, s);
+    b.p = p;
+    b.cap = want;
+    return VX_OK;
+}
+
+vx_status vx_level_alloc(vx_context* ctx, vx_level* L, int64_t n, int K, int level, int res,
+                         cudaStream_t s) {
+    memset(L, 0, sizeof(*L));
+    LevelLayout lay = vx_level_layout(n, K);
+    char* base = (char*)vx_dev_alloc(ctx, lay.total, s);
+    if (!base) return VX_ERR_OUT_OF_MEMORY;
+    L->level = level;
+    L->resolution = res;
+    L->num_voxels = n;
+    L->K = K;
+    L->block = base;
+    L->keys = (uint64_t*)(base + lay.keys);
+    L->mask = (uint64_t*)(base + lay.mask);
+    L->mass = (float*)(base + lay.mass);
+    L->moment = (float*)(base + lay.moment);
+    L->occ = (uint16_t*)(base + lay.occ);
+    L->occ_proj = (uint8_t*)(base + lay.proj);
+    L->lobe_count = (uint8_t*)(base + lay.lobe_count);
+    L->lobes = (float*)(base + lay.lobes);
+    L->compact = (float*)(base + lay.compact);
+    return VX_OK;
+}
+
+extern "C" {
+
+vx_status vx_context_create(const vx_allocator* alloc, vx_context** out) {
+    if (!out) return VX_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (alloc && (!alloc->alloc || !alloc->free)) return VX_ERR_INVALID_ARG;
+    vx_context* ctx = new (std::nothrow) vx_context();
+    if (!ctx) return VX_ERR_OUT_OF_MEMORY;
+    if (alloc) {
+        ctx->alloc = *alloc;
+        ctx->own_alloc = false;
+    } else {
+        memset(&ctx->alloc, 0, sizeof(ctx->alloc));
+        ctx->own_alloc = true;
+    }
+    cudaError_t e = cudaMallocHost((void**)&ctx->host_pin, 64 * sizeof(uint64_t));
+    if (e != cudaSuccess) {
+        vx_record_cuda_error(ctx, e, "cudaMallocHost");
+        delete ctx;
+        return VX_ERR_CUDA;
+    }
+    *out = ctx;
+    return VX_OK;
+}
+
+void vx_context_destroy(vx_context* ctx) {
+    if (!ctx) return;
+    cudaStream_t s = ctx->last_stream;
+    cudaStreamSynchronize(s);
+    for (int i = 0; i < WS_NSLOTS; ++i) {
+        if (ctx->ws[i].p) vx_dev_free(ctx, ctx->ws[i].p, s);
+        ctx->ws[i].p = nullptr;
+        ctx->ws[i].cap = 0;
+    }
+    cudaStreamSynchronize(s);
+    if (ctx->host_pin) cudaFreeHost(ctx->host_pin);
+    if (ctx->ev) {
+        for (int i = 0; i < vx::kEventPool; ++i) {
+            cudaEventDestroy(ctx->ev[i].a);
+            cudaEventDestroy(ctx->ev[i].b);
+        }
+        delete[] ctx->ev;
+    }
+    delete ctx;
+}
+
+vx_status vx_profile_enable(vx_context* ctx, int enable) {
+    if (!ctx) return VX_ERR_INVALID_ARG;
+    if (enable && !ctx->ev) {
+        ctx->ev = new (std::nothrow) vx::EventRec[vx::kEventPool];
+        if (!ctx->ev) return VX_ERR_OUT_OF_MEMORY;
+        for (int i = 0; i < vx::kEventPool; ++i) {
+            cudaError_t e1 = cudaEventCreate(&ctx->ev[i].a);
+            cudaError_t e2 = cudaEventCreate(&ctx->ev[i].b);
+            if (e1 != cudaSuccess || e2 != cudaSuccess) {
+                vx_record_cuda_error(ctx, e1 != cudaSuccess ? e1 : e2, "cudaEventCreate");
+                return VX_ERR_CUDA;
+            }
+        }
+    }
+    if (enable) {
+        vx_prof_drain(ctx);
+        for (int i = 0; i < ST_NSTAGES; ++i) { ctx->launches[i] = 0; ctx->stage_ms[i] = 0.0; }
+    }
+    ctx->prof = enable != 0;
+    return VX_OK;
+}
+
+vx_status vx_profile_read(vx_context* ctx, vx_stage_time* out, int max_stages, int* num_stages) {
+    if (!ctx || !num_stages) return VX_ERR_INVALID_ARG;
+    vx_prof_drain(ctx);
+    *num_stages = ST_NSTAGES;
+    if (out) {
+        for (int i = 0; i < ST_NSTAGES && i < max_stages; ++i) {
+            memset(out[i].name, 0, sizeof(out[i].name));
+            strncpy(out[i].name, kStageNames[i], sizeof(out[i].name) - 1);
+            out[i].launches = ctx->launches[i];
+            out[i].total_ms = ctx->stage_ms[i];
+        }
+    }
+    return VX_OK;
+}
+
+void vx_level_release(vx_context* ctx, vx_level* level, void* stream) {
+    if (!ctx || !level) return;
+    if (level->block) vx_dev_free(ctx, level->block, (cudaStream_t)stream);
+    memset(level, 0, sizeof(*level));
+}
+
+const char* vx_status_string(vx_status s) {
+    switch (s) {
+        case VX_OK: return "ok";
+        case VX_ERR_INVALID_ARG: return "invalid argument";
+        case VX_ERR_OUT_OF_MEMORY: return "out of device memory (allocator returned NULL)";
+        case VX_ERR_CAPACITY: return "capacity exceeded (more than 2^32-1 candidate pairs)";
+        case VX_ERR_CUDA: return "CUDA runtime error";
+        case VX_ERR_TIMEOUT: return "bounded wait timed out";
+        case VX_ERR_UNSUPPORTED: return "unsupported parameter";
+    }
+    return "unknown status";
+}
+
+const char* vx_last_cuda_error(const vx_context* ctx) { return ctx ? ctx->last_err : ""; }
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+// vx_internal.cuh -- shared declarations of the CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/vx.h"
+
+#define VX_CUDA_TRY(expr)                                                   \
+    do {                                                                    \
+        cudaError_t e_ = (expr);                                            \
+        if (e_ != cudaSuccess) {                                            \
+            vx_record_cuda_error(ctx, e_, #expr);                           \
+            return VX_ERR_CUDA;                                             \
+        }                                                                   \
+    } while (0)
+
+#define VX_TRY(expr)                    \
+    do {                                \
+        vx_status s_ = (expr);          \
+        if (s_ != VX_OK) return s_;     \
+    } while (0)
+
+namespace vx {
+
+constexpr int kWarp = 32;
+constexpr int kSMs = 152;        // GB300: 152 SMs on two dies
+constexpr int kMaxK = 8;         // lobe cap
+constexpr int kMaxCand = 8 * kMaxK;
+
+struct Buf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace vx
+
+// Pipeline stages (for launch counts and optional event timing).
+enum VxStage {
+    ST_PREP = 0, ST_COUNT, ST_EMIT, ST_SCAN, ST_SORT_HIST, ST_SORT_SCATTER, ST_HEADS,
+    ST_REDUCE_FIBERS, ST_REDUCE_TRIS, ST_FINALIZE, ST_LOD_COUNTS, ST_LOD_HEADS, ST_LOD_REDUCE,
+    ST_SGGX_CLUSTER, ST_NSTAGES
+};
+extern const char* const kStageNames[ST_NSTAGES];
+
+namespace vx {
+constexpr int kEventPool = 4096;
+struct EventRec {
+    int stage;
+    cudaEvent_t a, b;
+};
+}  // namespace vx
+
+struct vx_context {
+    vx_allocator alloc;
+    bool own_alloc;               // NULL allocator given: cudaMallocAsync
+    cudaStream_t last_stream = nullptr;
+    char last_err[256] = {0};
+    // workspace slots (grow-only)
+    vx::Buf ws[24];
+    uint64_t* host_pin = nullptr; // pinned readback buffer (64 words)
+    // profiling
+    bool prof = false;
+    int64_t launches[ST_NSTAGES] = {0};
+    double stage_ms[ST_NSTAGES] = {0};
+    vx::EventRec* ev = nullptr;   // pool of kEventPool records
+    int nev = 0;
+};
+
+// Brackets one kernel launch: counts it and, with profiling on, records events.
+void vx_stage_begin(vx_context* ctx, int stage, cudaStream_t s);
+void vx_stage_end(vx_context* ctx, cudaStream_t s);
+#define VX_LAUNCH(ctx, stage, s, ...)          \
+    do {                                       \
+        vx_stage_begin((ctx), (stage), (s));   \
+        __VA_ARGS__;                           \
+        vx_stage_end((ctx), (s));              \
+    } while (0)
+
+enum WsSlot {
+    WS_REC_A = 0, WS_REC_B, WS_REC_C, WS_COUNT, WS_OFFS, WS_SCAN_TMP,
+    WS_KEYS0, WS_VALS0, WS_KEYS1, WS_VALS1, WS_SORT_HIST,
+    WS_FLAGS, WS_SEGIDX, WS_STARTS, WS_SEG_OUT, WS_MISC, WS_FIBER_START,
+    WS_LOD_FLAGS, WS_LOD_IDX, WS_LOD_STARTS, WS_LOD_WORK, WS_LOD_TMP,
+    WS_NSLOTS
+};
+
+void vx_record_cuda_error(vx_context* ctx, cudaError_t e, const char* what);
+vx_status vx_ws_ensure(vx_context* ctx, int slot, size_t bytes, cudaStream_t s);
+void* vx_dev_alloc(vx_context* ctx, size_t bytes, cudaStream_t s);
+void vx_dev_free(vx_context* ctx, void* p, cudaStream_t s);
+
+// ---- scan / sort primitives (vx_sort.cu) -----------------------------------
+// Exclusive prefix sum of n uint32 values; out may alias in.  total (device, may be
+// NULL) receives the sum.  Needs scan workspace slot WS_SCAN_TMP.
+vx_status vx_scan_u32(vx_context* ctx, const uint32_t* in, uint32_t* out, uint32_t n,
+                      uint32_t* total, cudaStream_t s);
+// Stable LSD radix sort of (key, value) uint32 pairs on the low `bits` bits.  The
+// function ping-pongs between the two buffer pairs and leaves *keys / *vals pointing
+// at the sorted data.
+vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, uint32_t** keys_alt,
+                            uint32_t** vals_alt, uint32_t n, int bits, cudaStream_t s);
+
+// ---- Morton ------------------------------------------------------------------
+__host__ __device__ inline uint32_t vx_part1by2(uint32_t x) {
+    x &= 0x000003ffu;
+    x = (x | (x << 16)) & 0xff0000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+__host__ __device__ inline uint32_t vx_compact1by2(uint32_t x) {
+    x &= 0x09249249u;
+    x = (x | (x >> 2)) & 0x030c30c3u;
+    x = (x | (x >> 4)) & 0x0300f00fu;
+    x = (x | (x >> 8)) & 0xff0000ffu;
+    x = (x | (x >> 16)) & 0x000003ffu;
+    return x;
+}
+__host__ __device__ inline uint32_t vx_morton3(uint32_t x, uint32_t y, uint32_t z) {
+    return vx_part1by2(x) | (vx_part1by2(y) << 1) | (vx_part1by2(z) << 2);
+}
+
+// ---- level layout --------------------------------------------------------------
+// Byte offsets of each array inside one level block (256-byte aligned sections).
+struct LevelLayout {
+    size_t keys, mask, mass, moment, occ, proj, lobe_count, lobes, compact, total;
+};
+inline size_t vx_align256(size_t x) { return (x + 255) & ~size_t(255); }
+inline LevelLayout vx_level_layout(int64_t n, int K) {
+    LevelLayout L;
+    size_t o = 0;
+    size_t nn = (size_t)n;
+    L.keys = o; o += vx_align256(nn * 8);
+    L.mask = o; o += vx_align256(nn * 64);
+    L.mass = o; o += vx_align256(nn * 4);
+    L.moment = o; o += vx_align256(nn * 24);
+    L.occ = o; o += vx_align256(nn * 2);
+    L.proj = o; o += vx_align256(nn * 3);
+    L.lobe_count = o; o += vx_align256(nn);
+    L.lobes = o; o += vx_align256(nn * (size_t)K * 28);
+    L.compact = o; o += vx_align256(nn * (size_t)K * 24);
+    L.total = o;
+    return L;
+}
+vx_status vx_level_alloc(vx_context* ctx, vx_level* L, int64_t n, int K, int level, int res,
+                         cudaStream_t s);

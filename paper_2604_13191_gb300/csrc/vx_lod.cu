@@ -1,0 +1,480 @@
+// vx_lod.cu -- bottom-up LoD pyramid (Sec. 4.2-4.4): 2x2x2 aggregation of mass and
+// second moments, OR-downsampled sub-cell masks, and SGGX-H lobe clustering.
+//
+// Per level l -> l+1 (children are contiguous in Morton order, the parent key is
+// key >> 3, so no re-sort is needed):
+//   heads     parent segment starts where key >> 3 changes
+//   reduce    thread per parent: sums in child order, mask downsample, occupancy,
+//             K = 1 lobe S = M / m, or the children's lobes when at most K of them
+//   cluster   warp per parent with more than K candidate lobes: sampled histograms,
+//             sliced Wasserstein-1 distances, agglomerative merges (Eq. similarity)
+//
+// SGGX-H arithmetic: every lobe S is sampled with the N given unit directions u_k as
+// omega_k = normalize(S'^(1/2) u_k), S' = S + 1e-6 tr(S) I, S'^(1/2) by cyclic Jacobi
+// (FP32, 6 sweeps).  Histograms are integer counts; the sample second moment sums the
+// products omega_a omega_b rounded to the 2^-20 grid in integers.  Both are therefore
+// independent of the order in which the warp visits the samples.
+#include <math.h>
+
+#include <algorithm>
+
+#include "vx_internal.cuh"
+
+namespace {
+
+constexpr int CL_WARPS = 4;                 // warps per block in the cluster kernel
+constexpr int MAX_SLOTS = 2 * vx::kMaxCand; // candidates + merged lobes
+
+struct LevelIn {
+    const uint64_t* keys;
+    const uint64_t* mask;
+    const float* mass;
+    const float* moment;
+    const uint8_t* lobe_count;
+    const float* lobes;
+    int K;
+};
+
+__global__ void k_level_counts(const uint64_t* __restrict__ keys, uint32_t n, int L, uint32_t* __restrict__ counts) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        uint32_t i = base + threadIdx.x;
+        uint64_t k = (i < n) ? keys[i] : 0ull;
+        uint64_t kp = (i < n && i > 0) ? keys[i - 1] : 0ull;
+        for (int l = 1; l <= L; ++l) {
+            bool head = (i < n) && (i == 0 || (k >> (3 * l)) != (kp >> (3 * l)));
+            uint32_t b = __ballot_sync(0xffffffffu, head);
+            if (lane == 0 && b) atomicAdd(&counts[l], (uint32_t)__popc(b));
+        }
+    }
+}
+
+__global__ void k_parent_flags(const uint64_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ flags) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flags[i] = (i == 0 || (keys[i] >> 3) != (keys[i - 1] >> 3)) ? 1u : 0u;
+}
+
+__global__ void k_parent_starts(const uint64_t* __restrict__ keys, uint32_t n, const uint32_t* __restrict__ idx,
+                                uint32_t np, uint32_t* __restrict__ starts) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && (i == 0 || (keys[i] >> 3) != (keys[i - 1] >> 3))) starts[idx[i]] = i;
+    if (i == 0) starts[np] = n;
+}
+
+__device__ __forceinline__ void mask_counts(const uint64_t* m, uint16_t& occ, uint8_t* proj) {
+    int o = 0, yz = 0, xz = 0;
+    uint64_t orz = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        uint64_t x = m[w];
+        o += __popcll(x);
+        orz |= x;
+        uint64_t t = x | (x >> 4);
+        t |= t >> 2;
+        t |= t >> 1;
+        yz += __popcll(t & 0x0101010101010101ull);
+        uint64_t r = x | (x >> 32);
+        r |= r >> 16;
+        r |= r >> 8;
+        xz += __popc((uint32_t)(r & 0xffu));
+    }
+    occ = (uint16_t)o;
+    proj[0] = (uint8_t)yz;
+    proj[1] = (uint8_t)xz;
+    proj[2] = (uint8_t)__popcll(orz);
+}
+
+// 2x2x2 OR-downsample of a child mask into octant (ox,oy,oz) of the parent mask
+__device__ __forceinline__ void downsample_into(const uint64_t* cm, int oct, uint64_t* pm) {
+    const int ox = oct & 1, oy = (oct >> 1) & 1, oz = (oct >> 2) & 1;
+#pragma unroll
+    for (int qz = 0; qz < 4; ++qz) {
+        uint64_t f = cm[2 * qz] | cm[2 * qz + 1];        // fold z pairs
+        f |= f >> 8;                                      // fold y pairs (rows 2qy, 2qy+1)
+        f |= f >> 1;                                      // fold x pairs
+        uint64_t out = 0;
+#pragma unroll
+        for (int qy = 0; qy < 4; ++qy) {
+            uint32_t b = (uint32_t)(f >> (16 * qy)) & 0x55u;  // bits 0,2,4,6
+            b = (b | (b >> 1)) & 0x33u;
+            b = (b | (b >> 2)) & 0x0fu;
+            out |= (uint64_t)b << (4 * ox + 8 * (4 * oy + qy));
+        }
+        pm[4 * oz + qz] |= out;
+    }
+}
+
+__device__ __forceinline__ void compact_params(const float* S, float* c) {
+    c[0] = sqrtf(S[0]);
+    c[1] = sqrtf(S[1]);
+    c[2] = sqrtf(S[2]);
+    float pxy = S[0] * S[1], pxz = S[0] * S[2], pyz = S[1] * S[2];
+    c[3] = pxy > 0.0f ? S[3] / sqrtf(pxy) : 0.0f;
+    c[4] = pxz > 0.0f ? S[4] / sqrtf(pxz) : 0.0f;
+    c[5] = pyz > 0.0f ? S[5] / sqrtf(pyz) : 0.0f;
+}
+
+// thread per parent
+__global__ void k_lod_reduce(LevelIn in, const uint32_t* __restrict__ starts, uint32_t np, vx_level out, int K,
+                             uint32_t* __restrict__ work, uint32_t* __restrict__ nwork) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+        const uint32_t beg = starts[p], end = starts[p + 1];
+        float m = 0.0f;
+        float M[6] = {0, 0, 0, 0, 0, 0};
+        uint64_t pm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int ncand = 0;
+        for (uint32_t c = beg; c < end; ++c) {
+            m = m + in.mass[c];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) M[j] = M[j] + in.moment[(size_t)c * 6 + j];
+            uint64_t cm[8];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) cm[w] = in.mask[(size_t)c * 8 + w];
+            downsample_into(cm, (int)(in.keys[c] & 7ull), pm);
+            ncand += in.lobe_count[c];
+        }
+        out.keys[p] = in.keys[beg] >> 3;
+        out.mass[p] = m;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) out.moment[(size_t)p * 6 + j] = M[j];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) out.mask[(size_t)p * 8 + w] = pm[w];
+        uint16_t occ;
+        uint8_t pj[3];
+        mask_counts(pm, occ, pj);
+        out.occ[p] = occ;
+        out.occ_proj[(size_t)p * 3 + 0] = pj[0];
+        out.occ_proj[(size_t)p * 3 + 1] = pj[1];
+        out.occ_proj[(size_t)p * 3 + 2] = pj[2];
+        float* lo = out.lobes + (size_t)p * K * 7;
+        float* co = out.compact + (size_t)p * K * 6;
+        if (K == 1) {
+            if (m > 0.0f) {
+                float S[6];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) S[j] = M[j] / m;
+#pragma unroll
+                for (int j = 0; j < 6; ++j) lo[j] = S[j];
+                lo[6] = m;
+                compact_params(S, co);
+                out.lobe_count[p] = 1;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 7; ++j) lo[j] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 6; ++j) co[j] = 0.0f;
+                out.lobe_count[p] = 0;
+            }
+        } else if (ncand <= K) {
+            // copy the children's lobes, ordered by weight (descending), ties by candidate order
+            for (int j = 0; j < K * 7; ++j) lo[j] = 0.0f;
+            for (int j = 0; j < K * 6; ++j) co[j] = 0.0f;
+            int idx = 0;
+            for (uint32_t c = beg; c < end; ++c) {
+                for (int l = 0; l < in.lobe_count[c]; ++l, ++idx) {
+                    const float* src = in.lobes + ((size_t)c * in.K + l) * 7;
+                    const float wx = src[6];
+                    int rank = 0, idy = 0;
+                    for (uint32_t c2 = beg; c2 < end; ++c2)
+                        for (int l2 = 0; l2 < in.lobe_count[c2]; ++l2, ++idy) {
+                            const float wy = in.lobes[((size_t)c2 * in.K + l2) * 7 + 6];
+                            if (wy > wx || (wy == wx && idy < idx)) ++rank;
+                        }
+                    for (int j = 0; j < 7; ++j) lo[rank * 7 + j] = src[j];
+                    compact_params(src, co + rank * 6);
+                }
+            }
+            out.lobe_count[p] = (uint8_t)ncand;
+        } else {
+            out.lobe_count[p] = 0;
+            uint32_t slot = atomicAdd(nwork, 1u);
+            work[slot] = p;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// SGGX-H
+// ------------------------------------------------------------------------------------
+// S'^(1/2) of a symmetric 3x3 matrix (packed xx,yy,zz,xy,xz,yz) by cyclic Jacobi
+__device__ void sqrtm3(const float* S, float* Rm) {
+    float a[3][3] = {{S[0], S[3], S[4]}, {S[3], S[1], S[5]}, {S[4], S[5], S[2]}};
+    float V[3][3] = {{1.0f, 0.0f, 0.0f}, {0.0f, 1.0f, 0.0f}, {0.0f, 0.0f, 1.0f}};
+    for (int sweep = 0; sweep < 6; ++sweep) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int p = (r == 2) ? 1 : 0;
+            const int q = (r == 0) ? 1 : 2;
+            const int o = 3 - p - q;
+            const float apq = a[p][q];
+            if (apq == 0.0f) continue;
+            const float app = a[p][p], aqq = a[q][q];
+            const float theta = (aqq - app) / (2.0f * apq);
+            float t = 1.0f / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+            if (theta < 0.0f) t = -t;
+            const float c = 1.0f / sqrtf(t * t + 1.0f);
+            const float sn = t * c;
+            a[p][p] = app - t * apq;
+            a[q][q] = aqq + t * apq;
+            a[p][q] = 0.0f;
+            a[q][p] = 0.0f;
+            const float arp = a[o][p], arq = a[o][q];
+            const float nrp = c * arp - sn * arq;
+            const float nrq = sn * arp + c * arq;
+            a[o][p] = nrp; a[p][o] = nrp;
+            a[o][q] = nrq; a[q][o] = nrq;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float vp = V[i][p], vq = V[i][q];
+                V[i][p] = c * vp - sn * vq;
+                V[i][q] = sn * vp + c * vq;
+            }
+        }
+    }
+    float sg[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) sg[i] = sqrtf(a[i][i] > 0.0f ? a[i][i] : 0.0f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Rm[3 * i + j] = ((V[i][0] * sg[0]) * V[j][0] + (V[i][1] * sg[1]) * V[j][1]) + (V[i][2] * sg[2]) * V[j][2];
+}
+
+struct LobeStats {
+    int32_t h[6];
+    float Mh[6];
+};
+
+// warp-collective: histogram and sample second moment of lobe S (result valid in all lanes)
+__device__ LobeStats sample_lobe(const float* S, const float* __restrict__ dirs, int N) {
+    const float tr = (S[0] + S[1]) + S[2];
+    const float eps = 1e-6f * tr;
+    const float Sp[6] = {S[0] + eps, S[1] + eps, S[2] + eps, S[3], S[4], S[5]};
+    float Rm[9];
+    sqrtm3(Sp, Rm);
+    int32_t h[6] = {0, 0, 0, 0, 0, 0};
+    long long Q[6] = {0, 0, 0, 0, 0, 0};
+    int cnt = 0;
+    const int lane = threadIdx.x & 31;
+    for (int k = lane; k < N; k += 32) {
+        const float u0 = __ldg(dirs + 3 * k), u1 = __ldg(dirs + 3 * k + 1), u2 = __ldg(dirs + 3 * k + 2);
+        float v[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) v[i] = (Rm[3 * i] * u0 + Rm[3 * i + 1] * u1) + Rm[3 * i + 2] * u2;
+        const float n2 = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
+        if (!(n2 > 0.0f)) continue;
+        ++cnt;
+        const float t6 = 0.36f * n2, t2 = 0.04f * n2;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float c2 = v[a] * v[a];
+            h[a] += (c2 >= t6) ? 1 : 0;
+            h[3 + a] += (c2 >= t2) ? 1 : 0;
+        }
+        const float inv = 1.0f / n2;
+        const float s20 = inv * 1048576.0f;
+        Q[0] += __float2int_rn((v[0] * v[0]) * s20);
+        Q[1] += __float2int_rn((v[1] * v[1]) * s20);
+        Q[2] += __float2int_rn((v[2] * v[2]) * s20);
+        Q[3] += __float2int_rn((v[0] * v[1]) * s20);
+        Q[4] += __float2int_rn((v[0] * v[2]) * s20);
+        Q[5] += __float2int_rn((v[1] * v[2]) * s20);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            h[c] += __shfl_xor_sync(0xffffffffu, h[c], o);
+            Q[c] += __shfl_xor_sync(0xffffffffu, Q[c], o);
+        }
+    }
+    LobeStats st;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        st.h[c] = h[c];
+        st.Mh[c] = cnt > 0 ? (float)((double)Q[c] / ((double)cnt * 1048576.0)) : 0.0f;
+    }
+    return st;
+}
+
+struct ClusterSmem {
+    float S[MAX_SLOTS][6];
+    float w[MAX_SLOTS];
+    float Mh[MAX_SLOTS][6];
+    int32_t H[MAX_SLOTS][6];
+    uint8_t alive[MAX_SLOTS];
+};
+
+// warp per parent listed in `work`
+__global__ void __launch_bounds__(CL_WARPS * 32) k_sggx_cluster(LevelIn in, const uint32_t* __restrict__ starts,
+                                                                const uint32_t* __restrict__ work,
+                                                                const uint32_t* __restrict__ nwork_p, vx_level out,
+                                                                int K, const float* __restrict__ dirs, int N) {
+    extern __shared__ unsigned char smem_raw[];
+    ClusterSmem& sm = ((ClusterSmem*)smem_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwork = *nwork_p;
+    const uint32_t warps = gridDim.x * CL_WARPS;
+    for (uint32_t it = blockIdx.x * CL_WARPS + (threadIdx.x >> 5); it < nwork; it += warps) {
+        const uint32_t p = work[it];
+        const uint32_t beg = starts[p], end = starts[p + 1];
+        // gather candidates in (child, lobe) order
+        int n = 0;
+        for (uint32_t c = beg; c < end; ++c) {
+            const int lc = in.lobe_count[c];
+            for (int l = lane; l < lc * 7; l += 32) {
+                const int li = l / 7, j = l % 7;
+                const float x = in.lobes[((size_t)c * in.K + li) * 7 + j];
+                if (j < 6) sm.S[n + li][j] = x; else sm.w[n + li] = x;
+            }
+            n += lc;
+        }
+        for (int l = lane; l < MAX_SLOTS; l += 32) sm.alive[l] = (l < n) ? 1 : 0;
+        __syncwarp();
+        for (int l = 0; l < n; ++l) {
+            LobeStats st = sample_lobe(sm.S[l], dirs, N);
+            if (lane < 6) {
+                sm.H[l][lane] = st.h[lane];
+                sm.Mh[l][lane] = st.Mh[lane];
+            }
+        }
+        __syncwarp();
+        int count = n, next = n;
+        while (count > K) {
+            // argmin over alive pairs (i > j) of (distance, i, j)
+            unsigned long long best = ~0ull;
+            const int npairs = next * (next - 1) / 2;
+            for (int q = lane; q < npairs; q += 32) {
+                // q -> (i, j), i > j, ordered by i then j
+                int i = (int)((sqrtf(8.0f * (float)q + 1.0f) + 1.0f) * 0.5f);
+                while (i * (i - 1) / 2 > q) --i;
+                while ((i + 1) * i / 2 <= q) ++i;
+                const int j = q - i * (i - 1) / 2;
+                if (!sm.alive[i] || !sm.alive[j]) continue;
+                long long d = 0;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) d += llabs((long long)sm.H[i][c] - (long long)sm.H[j][c]);
+                unsigned long long key = ((unsigned long long)d << 16) | ((unsigned long long)i << 8) | (unsigned long long)j;
+                if (key < best) best = key;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+                if (other < best) best = other;
+            }
+            const int bi = (int)((best >> 8) & 0xffull), bj = (int)(best & 0xffull);
+            if (lane < 6) sm.S[next][lane] = (sm.Mh[bi][lane] + sm.Mh[bj][lane]) * 0.5f;
+            if (lane == 0) {
+                sm.w[next] = sm.w[bi] + sm.w[bj];
+                sm.alive[bi] = 0;
+                sm.alive[bj] = 0;
+                sm.alive[next] = 1;
+            }
+            __syncwarp();
+            LobeStats st = sample_lobe(sm.S[next], dirs, N);
+            if (lane < 6) {
+                sm.H[next][lane] = st.h[lane];
+                sm.Mh[next][lane] = st.Mh[lane];
+            }
+            __syncwarp();
+            ++next;
+            --count;
+        }
+        // output: alive lobes by weight (descending), ties by creation index
+        float* lo = out.lobes + (size_t)p * K * 7;
+        float* co = out.compact + (size_t)p * K * 6;
+        for (int x = lane; x < next; x += 32) {
+            if (!sm.alive[x]) continue;
+            const float wx = sm.w[x];
+            int rank = 0;
+            for (int y = 0; y < next; ++y)
+                if (sm.alive[y] && (sm.w[y] > wx || (sm.w[y] == wx && y < x))) ++rank;
+            for (int j = 0; j < 6; ++j) lo[rank * 7 + j] = sm.S[x][j];
+            lo[rank * 7 + 6] = wx;
+            compact_params(sm.S[x], co + rank * 6);
+        }
+        if (lane == 0) out.lobe_count[p] = (uint8_t)count;
+        __syncwarp();
+    }
+}
+
+inline unsigned grid_for(size_t n, int threads) {
+    size_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (unsigned)std::min<size_t>(b, 0x7fffffff);
+}
+
+}  // namespace
+
+extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_lod_params* params, void* stream,
+                                  vx_level* out) {
+    if (!ctx || !in || !params || !out) return VX_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    const int R = in->resolution;
+    if (R <= 0 || (R & (R - 1)) != 0 || in->num_voxels < 0 || in->num_voxels > 0xffffffffll) return VX_ERR_INVALID_ARG;
+    int maxL = 0;
+    while ((1 << maxL) < R) ++maxL;
+    const int L = params->num_levels == 0 ? maxL : params->num_levels;
+    if (L < 0 || L > maxL) return VX_ERR_INVALID_ARG;
+    const int K = params->K;
+    if (K < 1 || K > vx::kMaxK) return VX_ERR_UNSUPPORTED;
+    if (in->K < 1 || in->K > vx::kMaxK) return VX_ERR_INVALID_ARG;
+    if (K > 1 && (!params->dirs || params->n_samples < 1 || params->n_samples > 65536)) return VX_ERR_INVALID_ARG;
+    for (int l = 0; l < L; ++l) memset(&out[l], 0, sizeof(vx_level));
+    if (L == 0) return VX_OK;
+    const uint32_t n0 = (uint32_t)in->num_voxels;
+
+    // ---- all level sizes in one pass + one readback ---------------------------------
+    VX_TRY(vx_ws_ensure(ctx, WS_MISC, 256, s));
+    uint32_t* misc = (uint32_t*)ctx->ws[WS_MISC].p;
+    VX_CUDA_TRY(cudaMemsetAsync(misc, 0, 128, s));
+    if (n0 > 0)
+        VX_LAUNCH(ctx, ST_LOD_COUNTS, s, k_level_counts<<<(unsigned)std::min<size_t>(grid_for(n0, 256), (size_t)vx::kSMs * 16), 256, 0, s>>>(
+            in->keys, n0, L, misc));
+    VX_CUDA_TRY(cudaGetLastError());
+    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 4 * (L + 1), cudaMemcpyDeviceToHost, s));
+    VX_CUDA_TRY(cudaStreamSynchronize(s));
+    uint32_t counts[32];
+    memcpy(counts, ctx->host_pin, 4 * (L + 1));
+    for (int l = 1; l <= L; ++l) {
+        vx_status st = vx_level_alloc(ctx, &out[l - 1], counts[l], K, in->level + l, R >> l, s);
+        if (st != VX_OK) {
+            for (int j = 0; j < l - 1; ++j) vx_level_release(ctx, &out[j], s);
+            return st;
+        }
+    }
+    // ---- per level ------------------------------------------------------------------------
+    VX_TRY(vx_ws_ensure(ctx, WS_LOD_FLAGS, (size_t)std::max<uint32_t>(n0, 1) * 4, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_LOD_STARTS, (size_t)std::max<uint32_t>(n0, 1) * 4 + 8, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_LOD_WORK, (size_t)std::max<uint32_t>(n0, 1) * 4, s));
+    uint32_t* flags = (uint32_t*)ctx->ws[WS_LOD_FLAGS].p;
+    uint32_t* starts = (uint32_t*)ctx->ws[WS_LOD_STARTS].p;
+    uint32_t* work = (uint32_t*)ctx->ws[WS_LOD_WORK].p;
+    const size_t cl_smem = sizeof(ClusterSmem) * CL_WARPS;
+    if (K > 1) VX_CUDA_TRY(cudaFuncSetAttribute(k_sggx_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl_smem));
+    for (int l = 1; l <= L; ++l) {
+        const vx_level* prev = (l == 1) ? in : &out[l - 2];
+        const uint32_t nprev = (uint32_t)prev->num_voxels, ncur = counts[l];
+        if (ncur == 0) continue;
+        LevelIn li;
+        li.keys = prev->keys; li.mask = prev->mask; li.mass = prev->mass; li.moment = prev->moment;
+        li.lobe_count = prev->lobe_count; li.lobes = prev->lobes; li.K = prev->K;
+        VX_LAUNCH(ctx, ST_LOD_HEADS, s, k_parent_flags<<<grid_for(nprev, 256), 256, 0, s>>>(prev->keys, nprev, flags));
+        VX_TRY(vx_scan_u32(ctx, flags, flags, nprev, nullptr, s));
+        VX_LAUNCH(ctx, ST_LOD_HEADS, s, k_parent_starts<<<grid_for(nprev, 256), 256, 0, s>>>(prev->keys, nprev, flags, ncur, starts));
+        VX_CUDA_TRY(cudaMemsetAsync(misc + 40, 0, 4, s));
+        VX_LAUNCH(ctx, ST_LOD_REDUCE, s, k_lod_reduce<<<(unsigned)std::min<size_t>(grid_for(ncur, 128), (size_t)vx::kSMs * 32), 128, 0, s>>>(
+            li, starts, ncur, out[l - 1], K, work, misc + 40));
+        VX_CUDA_TRY(cudaGetLastError());
+        if (K > 1) {
+            const unsigned cb = (unsigned)std::min<size_t>((ncur + CL_WARPS - 1) / CL_WARPS, (size_t)vx::kSMs * 16);
+            VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, k_sggx_cluster<<<cb, CL_WARPS * 32, cl_smem, s>>>(li, starts, work, misc + 40, out[l - 1], K,
+                                                              params->dirs, params->n_samples));
+            VX_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    return VX_OK;
+}

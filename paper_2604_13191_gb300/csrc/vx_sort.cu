@@ -1,0 +1,224 @@
+// vx_sort.cu -- device prefix sum and stable LSD radix sort of (uint32 key, uint32 value).
+//
+// The sort orders candidate (voxel key, primitive id) pairs by Morton key, keeping
+// primitive-id order inside each key (stability), which is what makes the per-voxel
+// reductions order-deterministic (the paper sorts samples by block id, Sec. 3.3).
+#include "vx_internal.cuh"
+
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int RADIX = 256;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread (256 threads); returns the block total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* smem, uint32_t& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = warp_incl_scan(v);
+    if (lane == 31) smem[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t x = (lane < SCAN_THREADS / 32) ? smem[lane] : 0u;
+        uint32_t xi = warp_incl_scan(x);
+        if (lane < SCAN_THREADS / 32) smem[lane] = xi - x;
+        if (lane == SCAN_THREADS / 32 - 1) smem[SCAN_THREADS / 32] = xi;
+    }
+    __syncthreads();
+    uint32_t r = smem[w] + inc - v;
+    total = smem[SCAN_THREADS / 32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __restrict__ in,
+                                                              uint32_t n, uint32_t* __restrict__ part) {
+    __shared__ uint32_t sm[SCAN_THREADS / 32 + 1];
+    const size_t base = (size_t)blockIdx.x * SCAN_TILE;
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        size_t e = base + (size_t)j * SCAN_THREADS + threadIdx.x;
+        if (e < n) s += in[e];
+    }
+    uint32_t tot;
+    block_excl_scan(s, sm, tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// Single-block exclusive scan of the block partials (any length).
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_partials(uint32_t* part, uint32_t nb,
+                                                                uint32_t* total) {
+    __shared__ uint32_t sm[SCAN_THREADS / 32 + 1];
+    uint32_t carry = 0;
+    for (uint32_t b = 0; b < nb; b += SCAN_TILE) {
+        uint32_t v[SCAN_ITEMS];
+        uint32_t s = 0;
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) {
+            uint32_t e = b + threadIdx.x * SCAN_ITEMS + j;
+            v[j] = (e < nb) ? part[e] : 0u;
+            s += v[j];
+        }
+        uint32_t tot;
+        uint32_t off = block_excl_scan(s, sm, tot);
+        uint32_t run = carry + off;
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) {
+            uint32_t e = b + threadIdx.x * SCAN_ITEMS + j;
+            if (e < nb) part[e] = run;
+            run += v[j];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* in, uint32_t* out, uint32_t n,
+                                                            const uint32_t* __restrict__ part) {
+    __shared__ uint32_t sm[SCAN_THREADS / 32 + 1];
+    const size_t base = (size_t)blockIdx.x * SCAN_TILE;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        size_t e = base + (size_t)threadIdx.x * SCAN_ITEMS + j;
+        v[j] = (e < n) ? in[e] : 0u;
+        s += v[j];
+    }
+    uint32_t tot;
+    uint32_t run = block_excl_scan(s, sm, tot) + part[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        size_t e = base + (size_t)threadIdx.x * SCAN_ITEMS + j;
+        if (e < n) out[e] = run;
+        run += v[j];
+    }
+}
+
+// ---- radix sort ----------------------------------------------------------------
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n,
+                                                             int shift, uint32_t dmask, uint32_t nt,
+                                                             uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[RADIX];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const size_t base = (size_t)blockIdx.x * SORT_TILE;
+#pragma unroll 4
+    for (int j = 0; j < SORT_ITEMS; ++j) {
+        size_t e = base + (size_t)j * SORT_THREADS + threadIdx.x;
+        if (e < n) atomicAdd(&h[(keys[e] >> shift) & dmask], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nt + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint32_t* __restrict__ keys,
+                                                                const uint32_t* __restrict__ vals, uint32_t n,
+                                                                int shift, uint32_t dmask, uint32_t nt,
+                                                                const uint32_t* __restrict__ hist,
+                                                                uint32_t* __restrict__ okeys,
+                                                                uint32_t* __restrict__ ovals) {
+    __shared__ uint32_t wcnt[SORT_WARPS][RADIX];
+    __shared__ uint32_t gofs[RADIX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&wcnt[0][0])[i] = 0;
+    gofs[threadIdx.x] = hist[(size_t)threadIdx.x * nt + blockIdx.x];
+    __syncthreads();
+    const size_t base = (size_t)blockIdx.x * SORT_TILE + (size_t)w * (32 * SORT_ITEMS);
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t k[SORT_ITEMS], v[SORT_ITEMS], rk[SORT_ITEMS];
+#pragma unroll
+    for (int j = 0; j < SORT_ITEMS; ++j) {
+        size_t e = base + (size_t)j * 32 + lane;
+        bool valid = e < n;
+        k[j] = valid ? keys[e] : 0u;
+        v[j] = valid ? vals[e] : 0u;
+        uint32_t d = valid ? ((k[j] >> shift) & dmask) : (uint32_t)RADIX;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t r = 0;
+        if (valid) r = wcnt[w][d] + __popc(peers & lt);
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wcnt[w][d] += __popc(peers);
+        __syncwarp();
+        rk[j] = r;
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < SORT_WARPS; ++ww) {
+            uint32_t t = wcnt[ww][d];
+            wcnt[ww][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < SORT_ITEMS; ++j) {
+        size_t e = base + (size_t)j * 32 + lane;
+        if (e < n) {
+            uint32_t d = (k[j] >> shift) & dmask;
+            uint32_t pos = gofs[d] + wcnt[w][d] + rk[j];
+            okeys[pos] = k[j];
+            ovals[pos] = v[j];
+        }
+    }
+}
+
+}  // namespace
+
+vx_status vx_scan_u32(vx_context* ctx, const uint32_t* in, uint32_t* out, uint32_t n,
+                      uint32_t* total, cudaStream_t s) {
+    uint32_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb == 0) nb = 1;
+    VX_TRY(vx_ws_ensure(ctx, WS_SCAN_TMP, (size_t)nb * 4 + 256, s));
+    uint32_t* part = (uint32_t*)ctx->ws[WS_SCAN_TMP].p;
+    if (n == 0) {
+        if (total) VX_CUDA_TRY(cudaMemsetAsync(total, 0, 4, s));
+        return VX_OK;
+    }
+    VX_LAUNCH(ctx, ST_SCAN, s, k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(in, n, part));
+    VX_LAUNCH(ctx, ST_SCAN, s, k_scan_partials<<<1, SCAN_THREADS, 0, s>>>(part, nb, total));
+    VX_LAUNCH(ctx, ST_SCAN, s, k_scan_down<<<nb, SCAN_THREADS, 0, s>>>(in, out, n, part));
+    VX_CUDA_TRY(cudaGetLastError());
+    return VX_OK;
+}
+
+vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, uint32_t** keys_alt,
+                            uint32_t** vals_alt, uint32_t n, int bits, cudaStream_t s) {
+    if (n <= 1 || bits <= 0) return VX_OK;
+    uint32_t nt = (n + SORT_TILE - 1) / SORT_TILE;
+    size_t hn = (size_t)RADIX * nt;
+    if (hn > 0xffffffffull) return VX_ERR_CAPACITY;
+    VX_TRY(vx_ws_ensure(ctx, WS_SORT_HIST, hn * 4, s));
+    uint32_t* hist = (uint32_t*)ctx->ws[WS_SORT_HIST].p;
+    for (int shift = 0; shift < bits; shift += 8) {
+        int nb = bits - shift < 8 ? bits - shift : 8;
+        uint32_t dmask = (1u << nb) - 1u;
+        VX_LAUNCH(ctx, ST_SORT_HIST, s, k_radix_hist<<<nt, SORT_THREADS, 0, s>>>(*keys, n, shift, dmask, nt, hist));
+        VX_TRY(vx_scan_u32(ctx, hist, hist, (uint32_t)hn, nullptr, s));
+        VX_LAUNCH(ctx, ST_SORT_SCATTER, s, k_radix_scatter<<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, shift, dmask, nt, hist, *keys_alt,
+                                                   *vals_alt));
+        VX_CUDA_TRY(cudaGetLastError());
+        uint32_t* t = *keys; *keys = *keys_alt; *keys_alt = t;
+        t = *vals; *vals = *vals_alt; *vals_alt = t;
+    }
+    return VX_OK;
+}

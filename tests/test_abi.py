@@ -1,0 +1,91 @@
+"""The C-ABI library builds, loads without a GPU and exports every declared entry point;
+the ctypes mirrors of the structs match the header's layout (checked with a C compiler)."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "vx.h")
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"VX_API\s+[\w\s\*]+?\b(vx_\w+)\s*\(", txt)))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ("vx_voxelize", "vx_build_lod", "vx_context_create", "vx_context_destroy",
+              "vx_level_release", "vx_status_string", "vx_last_cuda_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2604_13191_gb300 import _build
+    lib_path = _build.build()
+    lib = C.CDLL(lib_path)
+    for n in declared_functions():
+        assert hasattr(lib, n), f"{n} declared in vx.h but not exported"
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (vx_\w+)", out))
+    assert exported == set(declared_functions())
+
+
+def test_status_strings_without_gpu():
+    import paper_2604_13191_gb300 as vx
+    lib = vx.load()
+    for s in range(7):
+        assert lib.vx_status_string(s)
+    assert b"unknown" in lib.vx_status_string(99)
+
+
+def test_ctypes_layout_matches_header():
+    gcc = "gcc"
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "vx.h"
+#define P(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
+int main(void) {
+  printf("vx_grid %zu\n", sizeof(vx_grid));
+  printf("vx_primitives %zu\n", sizeof(vx_primitives));
+  printf("vx_level %zu\n", sizeof(vx_level));
+  printf("vx_lod_params %zu\n", sizeof(vx_lod_params));
+  printf("vx_allocator %zu\n", sizeof(vx_allocator));
+  P(vx_primitives, weights) P(vx_primitives, fiber_offsets) P(vx_level, compact) P(vx_level, block)
+  P(vx_level, num_voxels) P(vx_lod_params, dirs) P(vx_grid, resolution)
+  return 0;
+}
+"""
+    from paper_2604_13191_gb300 import api
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "l.c")
+        exe = os.path.join(d, "l")
+        open(src, "w").write(prog)
+        subprocess.check_call([gcc, "-I", os.path.join(ROOT, "include"), src, "-o", exe])
+        got = dict(line.split() for line in subprocess.check_output([exe], text=True).splitlines())
+    assert int(got["vx_grid"]) == C.sizeof(api.VxGrid)
+    assert int(got["vx_primitives"]) == C.sizeof(api.VxPrimitives)
+    assert int(got["vx_level"]) == C.sizeof(api.VxLevel)
+    assert int(got["vx_lod_params"]) == C.sizeof(api.VxLodParams)
+    assert int(got["vx_allocator"]) == C.sizeof(api.VxAllocator)
+    assert int(got["vx_primitives.weights"]) == api.VxPrimitives.weights.offset
+    assert int(got["vx_primitives.fiber_offsets"]) == api.VxPrimitives.fiber_offsets.offset
+    assert int(got["vx_level.compact"]) == api.VxLevel.compact.offset
+    assert int(got["vx_level.block"]) == api.VxLevel.block.offset
+    assert int(got["vx_level.num_voxels"]) == api.VxLevel.num_voxels.offset
+    assert int(got["vx_lod_params.dirs"]) == api.VxLodParams.dirs.offset
+    assert int(got["vx_grid.resolution"]) == api.VxGrid.resolution.offset
+
+
+def test_product_path_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_2604_13191_gb300")
+    for dp, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dp, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "vxoracle" not in txt

@@ -1,0 +1,126 @@
+"""Full-size parity: the 768k-segment yarn at 512^3 with K = 4, in the launch
+configuration the bench times.
+
+The oracle cannot voxelize the whole yarn in test time, so it checks sampled outputs
+one by one: level-0 voxels (occupied ones and empty neighbours) by brute force over
+all primitives, and level-1 / level-2 parents rebuilt from brute-force children.
+Properties that hold at any size are checked on every level.  Tolerances as in
+test_parity_gpu.py.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2604_13191_gb300 as vx  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+
+def demorton(k):
+    k = np.asarray(k, np.uint64)
+    out = []
+    for s in range(3):
+        v = np.zeros_like(k)
+        for b in range(21):
+            v |= ((k >> np.uint64(3 * b + s)) & np.uint64(1)) << np.uint64(b)
+        out.append(v)
+    return out
+
+
+def morton(x, y, z):
+    x, y, z = (np.asarray(a, np.uint64) for a in (x, y, z))
+    k = np.zeros_like(x)
+    for b in range(21):
+        k |= ((x >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b)
+        k |= ((y >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + 1)
+        k |= ((z >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + 2)
+    return k
+
+
+@pytest.fixture(scope="module")
+def yarn_run(dirs5000):
+    w = synth.config2()
+    ctx = vx.Context(DEV)
+    L0 = ctx.voxelize(w.grid, ctrl=torch.from_numpy(w.ctrl).to(DEV),
+                      fiber_offsets=torch.from_numpy(w.fiber_offsets).to(DEV), num_prims=w.num_prims)
+    pyr = ctx.build_lod(L0, K=4, dirs=torch.from_numpy(dirs5000).to(DEV))
+    torch.cuda.synchronize()
+    levels = [L0.host()] + [p.host() for p in pyr]
+    yield w, levels
+    ctx.close()
+
+
+def test_sampled_level0_voxels(yarn_run):
+    w, levels = yarn_run
+    L0 = levels[0]
+    n = L0["keys"].shape[0]
+    assert n > 1_000_000
+    rng = np.random.default_rng(20)
+    idx = np.sort(rng.choice(n, 40, replace=False))
+    keys = L0["keys"][idx]
+    # empty neighbours: +-1 in x of occupied voxels, not in the key set
+    x, y, z = demorton(L0["keys"][rng.choice(n, 400, replace=False)])
+    cand = morton(np.minimum(x + np.uint64(1), np.uint64(511)), y, z)
+    empty = np.setdiff1d(cand, L0["keys"])[:16]
+    ref = oracle.fiber_voxels(w.ctrl, w.fiber_offsets, w.grid, np.concatenate([keys, empty]))
+    assert np.array_equal(ref["mask"][:40], L0["mask"][idx])
+    assert not ref["mask"][40:].any(), "a voxel the GPU left empty is occupied in the oracle"
+    assert np.array_equal(ref["mass"][:40].view(np.uint32), L0["mass"][idx].view(np.uint32))
+    assert np.array_equal(ref["moment"][:40].view(np.uint32), L0["moment"][idx].view(np.uint32))
+    m64 = ref["mass64"][:40]
+    floor = 1e-6 * float(L0["mass"].max())
+    assert np.all(np.abs(L0["mass"][idx] - m64) <= 1e-5 * m64 + floor)
+
+
+@pytest.mark.parametrize("lvl", [1, 2])
+def test_sampled_parents(yarn_run, dirs5000, lvl):
+    w, levels = yarn_run
+    P = levels[lvl]
+    rng = np.random.default_rng(30 + lvl)
+    clustered = np.nonzero(P["lobe_count"] == 4)[0]
+    assert clustered.size > 100
+    pick = rng.choice(clustered, 4 if lvl == 1 else 2, replace=False)
+    for pi in pick:
+        pk = np.uint64(P["keys"][pi])
+        span = np.arange(8 ** lvl, dtype=np.uint64)
+        child_keys = (pk << np.uint64(3 * lvl)) | span
+        vox = oracle.fiber_voxels(w.ctrl, w.fiber_offsets, w.grid, child_keys)
+        cur = oracle.level_from_voxels(child_keys, vox)
+        for _ in range(lvl):
+            cur = oracle.lod_step(cur, 4, dirs5000)
+        assert cur["keys"].shape[0] == 1 and cur["keys"][0] == pk
+        assert np.array_equal(cur["mask"][0], P["mask"][pi])
+        assert cur["occ"][0] == P["occ"][pi] and np.array_equal(cur["proj"][0], P["proj"][pi])
+        assert cur["mass"][0].view(np.uint32) == P["mass"][pi].view(np.uint32)
+        assert np.array_equal(cur["moment"][0].view(np.uint32), P["moment"][pi].view(np.uint32))
+        assert cur["lobe_count"][0] == P["lobe_count"][pi]
+        c = int(cur["lobe_count"][0])
+        assert np.max(np.abs(cur["lobes"][0, :c] - P["lobes"][pi, :c])) <= 1e-5
+
+
+def test_pyramid_properties(yarn_run):
+    w, levels = yarn_run
+    tot = levels[0]["mass"].astype(np.float64).sum()
+    # tube volume in voxel units: the yarn lies inside the grid
+    assert len(levels) == 10
+    for l in range(1, len(levels)):
+        a, b = levels[l - 1], levels[l]
+        assert np.array_equal(np.unique(a["keys"] >> np.uint64(3)), b["keys"])
+        assert b["mass"].astype(np.float64).sum() == pytest.approx(tot, rel=1e-5)
+        assert np.all(b["lobe_count"] <= 4)
+        has = b["lobe_count"] > 0
+        wsum = b["lobes"][has, :, 6].astype(np.float64).sum(1)
+        assert np.allclose(wsum, b["mass"][has], rtol=1e-5, atol=1e-6 * float(b["mass"].max()))
+        S = b["lobes"][has, 0, :6].astype(np.float64)
+        assert np.allclose(S[:, :3].sum(1), 1.0, atol=2e-3)
+        assert np.all(b["occ"] <= 8 * b["proj"].min(1).astype(int))
+        assert np.all(b["proj"].max(1) <= b["occ"])
+    assert levels[-1]["keys"].shape[0] == 1

@@ -1,0 +1,224 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bar: keys, sub-cell masks, occupancy, projections and lobe counts bit-exact; mass and
+moments bit-exact with the oracle's FP32 chain and within the stated tolerance of its
+FP64 reference; lobes (S, weight) within 1e-5 (trace-1 matrices, so absolute).
+Tolerance (FP32 vs FP64 reference):
+    |m - m64| <= 1e-5 |m64| + 1e-6 max(m64)        (mass)
+    |M - M64| <= 1e-5 tr(M64) + 1e-6 max(m64)      (moment entries)
+The absolute floor covers FP32 clipping of tiny pieces: a clip parameter carries an
+absolute error of a few 2^-24 of the whole primitive, so a sliver's measure is exact
+only to ~1e-7 of the primitive's measure, which is below 1e-6 of the largest voxel mass.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2604_13191_gb300 as vx  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+LOBE_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = vx.Context(DEV)
+    yield c
+    c.close()
+
+
+def run_gpu(ctx, w, K=None, dirs=None, num_levels=0, lod=True):
+    K = w.K if K is None else K
+    if w.kind == "triangles":
+        L0 = ctx.voxelize(w.grid, tri_verts=torch.from_numpy(w.tri_verts).to(DEV),
+                          weights=None if w.weights is None else torch.from_numpy(w.weights).to(DEV))
+    else:
+        L0 = ctx.voxelize(w.grid, ctrl=torch.from_numpy(w.ctrl).to(DEV),
+                          fiber_offsets=torch.from_numpy(w.fiber_offsets).to(DEV),
+                          weights=None if w.weights is None else torch.from_numpy(w.weights).to(DEV))
+    pyr = []
+    if lod:
+        d = None if dirs is None else torch.from_numpy(dirs).to(DEV)
+        pyr = ctx.build_lod(L0, K=K, dirs=d, num_levels=num_levels)
+    torch.cuda.synchronize()
+    return [L0.host()] + [p.host() for p in pyr]
+
+
+def compare_level(g, r, name="", lobes=True):
+    assert np.array_equal(g["keys"], r["keys"]), f"{name}: keys differ ({g['keys'].shape} vs {r['keys'].shape})"
+    assert np.array_equal(g["mask"], r["mask"]), f"{name}: masks differ"
+    assert np.array_equal(g["occ"], r["occ"]), f"{name}: occ differs"
+    assert np.array_equal(g["proj"], r["proj"]), f"{name}: projections differ"
+    m64, M64 = r["mass64"], r["moment64"]
+    if m64.size:
+        floor = 1e-6 * max(float(m64.max()), 1e-30)
+        assert np.all(np.abs(g["mass"] - m64) <= 1e-5 * np.abs(m64) + floor), f"{name}: mass tolerance"
+        tr = M64[:, :3].sum(1)
+        assert np.all(np.abs(g["moment"] - M64) <= (1e-5 * tr + floor)[:, None]), f"{name}: moment tolerance"
+    # the FP32 chain is evaluated in the same order on both sides
+    assert np.array_equal(g["mass"].view(np.uint32), r["mass"].view(np.uint32)), f"{name}: FP32 mass not bit-exact"
+    assert np.array_equal(g["moment"].view(np.uint32), r["moment"].view(np.uint32)), f"{name}: FP32 moment not bit-exact"
+    if lobes:
+        assert np.array_equal(g["lobe_count"], r["lobe_count"]), f"{name}: lobe counts differ"
+        K = r["lobes"].shape[1]
+        for k in range(K):
+            sel = r["lobe_count"] > k
+            if not sel.any():
+                continue
+            gl, rl = g["lobes"][sel, k], r["lobes"][sel, k]
+            assert np.max(np.abs(gl[:, :6] - rl[:, :6])) <= LOBE_TOL, f"{name}: lobe {k} S"
+            assert np.all(np.abs(gl[:, 6] - rl[:, 6]) <= 1e-5 * np.abs(rl[:, 6]) + 1e-30), f"{name}: lobe {k} weight"
+            gc, rc = g["compact"][sel, k], r["compact"][sel, k]
+            assert np.max(np.abs(gc - rc)) <= 1e-5, f"{name}: compact params of lobe {k}"
+
+
+# ----------------------------------------------------------------------------
+# heightfield (7,938 triangles, 128^3, K = 1): the whole pyramid
+# ----------------------------------------------------------------------------
+def test_heightfield_full_pyramid(ctx, dirs5000):
+    w = synth.config1()
+    got = run_gpu(ctx, w, dirs=dirs5000)
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, 128, 1, dirs5000)
+    assert len(got) == len(refs) == 8
+    for lvl, (g, r) in enumerate(zip(got, refs)):
+        compare_level(g, r, f"level {lvl}")
+    # mass conservation across the pyramid (FP64 sums of FP32 outputs)
+    tot = got[0]["mass"].astype(np.float64).sum()
+    for g in got[1:]:
+        assert g["mass"].astype(np.float64).sum() == pytest.approx(tot, rel=1e-5)
+
+
+@pytest.mark.parametrize("seed,R,rad,pts", [(1, 32, (0.05, 0.4), 30), (2, 64, (0.3, 2.5), 20),
+                                            (3, 16, (0.01, 0.2), 30), (4, 128, (1.0, 3.0), 8)])
+def test_random_fibers(ctx, dirs5000, seed, R, rad, pts):
+    ctrl, off, grid = synth.random_segments(8, pts, R, seed=seed, radius=rad, step=(0.05, 2.0))
+    rng = np.random.default_rng(seed)
+    n = synth.fiber_segment_count(off)
+    w = synth.Workload("rf", "fibers", grid, ctrl=ctrl, fiber_offsets=off,
+                       weights=rng.uniform(0.1, 3.0, n).astype(np.float32), K=1)
+    got = run_gpu(ctx, w, dirs=dirs5000)
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, R, 1, dirs5000)
+    for lvl, (g, r) in enumerate(zip(got, refs)):
+        compare_level(g, r, f"seed {seed} level {lvl}")
+
+
+@pytest.mark.parametrize("seed,R,size", [(1, 16, (0.2, 3.0)), (2, 32, (0.05, 0.5)), (3, 64, (2.0, 12.0))])
+def test_random_triangles(ctx, dirs5000, seed, R, size):
+    tris, grid = synth.random_triangles(60, R, seed=seed, size=size)
+    rng = np.random.default_rng(seed)
+    w = synth.Workload("rt", "triangles", grid, tri_verts=tris,
+                       weights=rng.uniform(0.1, 3.0, tris.shape[0]).astype(np.float32), K=1)
+    got = run_gpu(ctx, w, dirs=dirs5000)
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, R, 1, dirs5000)
+    for lvl, (g, r) in enumerate(zip(got, refs)):
+        compare_level(g, r, f"seed {seed} level {lvl}")
+
+
+def test_yarn_reduced_sggx_h(ctx, dirs5000):
+    """Twisted-ply yarn (3 plies x 8 fibers x 500 segments) at 128^3 with K = 4 SGGX-H."""
+    w = synth.config2(fibers_per_ply=8, segments=500, R=128, K=4)
+    got = run_gpu(ctx, w, dirs=dirs5000)
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, 128, 4, dirs5000)
+    clustered = 0
+    for lvl, (g, r) in enumerate(zip(got, refs)):
+        compare_level(g, r, f"level {lvl}")
+        if lvl:
+            clustered += int((r["lobe_count"] == 4).sum())
+    assert clustered > 100
+
+
+# ----------------------------------------------------------------------------
+# edge cases
+# ----------------------------------------------------------------------------
+def test_empty_and_outside(ctx):
+    grid = synth.Grid((0.0, 0.0, 0.0), 1.0 / 16, 16)
+    ctrl = np.array([[2.0, 2.0, 2.0, 0.01], [2.5, 2.0, 2.0, 0.01]], np.float32)   # outside
+    off = np.array([0, 2], np.int64)
+    w = synth.Workload("out", "fibers", grid, ctrl=ctrl, fiber_offsets=off)
+    got = run_gpu(ctx, w, K=1, lod=True)
+    assert all(g["keys"].shape[0] == 0 for g in got)
+    tris = np.zeros((0, 3, 4), np.float32)
+    w = synth.Workload("none", "triangles", grid, tri_verts=tris)
+    got = run_gpu(ctx, w, K=1, lod=False)
+    assert got[0]["keys"].shape[0] == 0
+
+
+def test_degenerate_primitives(ctx, dirs5000):
+    grid = synth.Grid((0.0, 0.0, 0.0), 1.0 / 8, 8)
+    # zero-length segment (a sphere), a segment along a grid line, fibers with 1 point
+    ctrl = np.array([[0.3, 0.3, 0.3, 0.05], [0.3, 0.3, 0.3, 0.05],
+                     [0.5, 0.5, 0.1, 0.02], [0.5, 0.5, 0.9, 0.02],
+                     [0.7, 0.7, 0.7, 0.1]], np.float32)
+    off = np.array([0, 2, 4, 5], np.int64)
+    w = synth.Workload("deg", "fibers", grid, ctrl=ctrl, fiber_offsets=off)
+    got = run_gpu(ctx, w, K=1, dirs=dirs5000)
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, 8, 1, dirs5000)
+    for lvl, (g, r) in enumerate(zip(got, refs)):
+        compare_level(g, r, f"level {lvl}")
+    # degenerate triangles: a line and a point, plus a triangle in a grid plane
+    tris = np.zeros((3, 3, 4), np.float32)
+    tris[0, :, :3] = [[0.1, 0.1, 0.1], [0.6, 0.6, 0.6], [0.35, 0.35, 0.35]]
+    tris[1, :, :3] = [[0.4, 0.2, 0.7]] * 3
+    tris[2, :, :3] = [[0.1, 0.1, 0.5], [0.9, 0.1, 0.5], [0.1, 0.9, 0.5]]
+    w = synth.Workload("degt", "triangles", grid, tri_verts=tris)
+    got = run_gpu(ctx, w, K=1, dirs=dirs5000)
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, 8, 1, dirs5000)
+    for lvl, (g, r) in enumerate(zip(got, refs)):
+        compare_level(g, r, f"tri level {lvl}")
+
+
+def test_single_voxel_grid_and_max_resolution(ctx, dirs5000):
+    for R in (1, 1024):
+        # radii and steps in voxel units of the grid itself: a few voxels per primitive
+        ctrl, off, grid = synth.random_segments(2, 5, R, seed=9, radius=(0.1, 1.5), step=(0.3, 2.0))
+        w = synth.Workload("r", "fibers", grid, ctrl=ctrl, fiber_offsets=off, K=1)
+        got = run_gpu(ctx, w, K=1, dirs=dirs5000, num_levels=min(3, int(np.log2(R))))
+        ref0 = oracle.voxelize(w)
+        refs = [ref0] + (oracle.build_pyramid(ref0, R, 1, dirs5000, num_levels=3) if R > 1 else [])
+        for lvl, (g, r) in enumerate(zip(got, refs)):
+            compare_level(g, r, f"R={R} level {lvl}")
+
+
+def test_invalid_arguments(ctx):
+    grid = synth.Grid((0.0, 0.0, 0.0), 1.0 / 16, 16)
+    ctrl = torch.zeros((4, 4), dtype=torch.float32, device=DEV)
+    off = torch.tensor([0, 4], dtype=torch.int64, device=DEV)
+    with pytest.raises(vx.VxError) as e:
+        ctx.voxelize(grid, ctrl=ctrl, fiber_offsets=off, num_prims=7)   # wrong segment count
+    assert e.value.status == 1
+    with pytest.raises(vx.VxError) as e:
+        ctx.voxelize(synth.Grid((0.0, 0.0, 0.0), 1.0 / 12, 12), ctrl=ctrl, fiber_offsets=off)
+    assert e.value.status == 1
+    with pytest.raises(vx.VxError) as e:
+        ctx.voxelize(synth.Grid((0.0, 0.0, 0.0), 1.0 / 2048, 2048), ctrl=ctrl, fiber_offsets=off)
+    assert e.value.status == 6
+    L0 = ctx.voxelize(grid, ctrl=ctrl, fiber_offsets=off)
+    with pytest.raises(vx.VxError) as e:
+        ctx.build_lod(L0, K=9)
+    assert e.value.status == 6
+    with pytest.raises(vx.VxError) as e:
+        ctx.build_lod(L0, K=4)          # K > 1 needs the direction set
+    assert e.value.status == 1
+
+
+def test_deterministic(ctx, dirs5000):
+    w = synth.config2(fibers_per_ply=4, segments=400, R=64, K=4)
+    a = run_gpu(ctx, w, dirs=dirs5000)
+    b = run_gpu(ctx, w, dirs=dirs5000)
+    for x, y in zip(a, b):
+        for k in ("keys", "mask", "mass", "moment", "lobes", "lobe_count", "compact"):
+            assert np.array_equal(np.asarray(x[k]).view(np.uint8), np.asarray(y[k]).view(np.uint8)), k
