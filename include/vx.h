@@ -171,6 +171,28 @@ typedef struct {
 VX_API vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_lod_params* params,
                        void* stream, vx_level* out);
 
+/* Adjoint (reverse mode) of a linear loss on the per-voxel mass and second moments of
+ * level 0 and the L coarser levels built from it:
+ *     loss = sum_l sum_v grad_mass[l][v] * m_l(v) + grad_moment[l][v] . M_l(v)
+ * Since m and M of a parent are sums over its children (Sec. 4.3), the coarse adjoints
+ * are broadcast down to level 0 (parents are found from keys0 alone; the coarse levels
+ * themselves are not needed).  Per (segment, voxel) pair the analytic derivative of
+ * w * pi r^2 * clipped length * (gm + gM . T(t)) is taken w.r.t. both endpoints, the
+ * radius and the weight; sub-cell occupancy and the key set are piecewise constant and
+ * carry no gradient.  Candidate pairs are recomputed, not stored.
+ *   prims: the forward's fibers (VX_FIBERS only); grid: the forward's grid.
+ *   keys0 (device) [num_voxels0]: level-0 keys of the forward (sorted).
+ *   grad_mass, grad_moment: HOST arrays of num_levels+1 device pointers; level l has
+ *     as many rows as there are distinct keys0 >> 3l ([V_l] and [V_l][6] floats).
+ *   grad_ctrl (device) [num_ctrl][4]: d loss / d (x, y, z, radius) of every control
+ *     point, world units; grad_weights (device) [num_prims] or NULL.
+ * Deterministic (fixed summation order, no atomics).  Errors: VX_ERR_INVALID_ARG,
+ * VX_ERR_UNSUPPORTED (triangles), VX_ERR_OUT_OF_MEMORY, VX_ERR_CAPACITY, VX_ERR_CUDA. */
+VX_API vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
+                             const uint64_t* keys0, int64_t num_voxels0, int num_levels,
+                             const float* const* grad_mass, const float* const* grad_moment,
+                             void* stream, float* grad_ctrl, float* grad_weights);
+
 /* Returns a level's block to the context's allocator and clears the struct. */
 VX_API void vx_level_release(vx_context* ctx, vx_level* level, void* stream);
 

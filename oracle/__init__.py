@@ -320,3 +320,45 @@ def level_from_voxels(keys, vox: dict) -> dict:
     d = _level_to_dict(L)
     _load().vxo_level_free(C.byref(L))
     return d
+
+
+def fiber_adjoint(ctrl, offsets, grid, keys0, gm0, gM0, weights=None, prims=None):
+    """FP64 loss sum gm*m + gM.M over level-0 voxels and its gradient w.r.t. ctrl
+    ([P,4]: xyz and radius, world units) and the per-segment weights."""
+    lib = _load()
+    if not hasattr(lib, "_adj_ready"):
+        lib.vxo_fiber_adjoint.restype = C.c_double
+        lib.vxo_fiber_adjoint.argtypes = [C.c_void_p] * 4 + [C.c_void_p, C.c_double, C.c_int] + \
+            [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+        lib.vxo_fiber_adjoint.argtypes[2] = C.c_int64
+        lib._adj_ready = True
+    ctrl = np.ascontiguousarray(ctrl, dtype=np.float64).reshape(-1, 4)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    keys0 = np.ascontiguousarray(keys0, dtype=np.uint64)
+    gm0 = np.ascontiguousarray(gm0, dtype=np.float64)
+    gM0 = np.ascontiguousarray(gM0, dtype=np.float64).reshape(-1, 6)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    pr = None if prims is None else np.ascontiguousarray(np.sort(prims), dtype=np.int64)
+    origin = np.ascontiguousarray(grid.origin, dtype=np.float64)
+    nseg = int(np.sum(np.maximum(offsets[1:] - offsets[:-1] - 1, 0)))
+    d_ctrl = np.zeros_like(ctrl)
+    d_w = np.zeros(nseg, dtype=np.float64)
+    loss = lib.vxo_fiber_adjoint(_ptr(ctrl), _ptr(offsets), int(offsets.shape[0] - 1), _ptr(w), _ptr(origin),
+                                 float(grid.voxel_size), int(grid.resolution), _ptr(keys0), int(keys0.shape[0]),
+                                 _ptr(gm0), _ptr(gM0), _ptr(pr), 0 if pr is None else int(pr.shape[0]),
+                                 _ptr(d_ctrl), _ptr(d_w))
+    return float(loss), d_ctrl, d_w
+
+
+def broadcast_adjoints(keys0, level_keys, alphas, betas):
+    """FP64 level-0 adjoints g0 = sum_l alpha_l[parent_l], gM0 = sum_l beta_l[parent_l]
+    (m and M of a parent are sums over its children, Sec. 4.3)."""
+    keys0 = np.asarray(keys0, np.uint64)
+    gm = np.zeros(keys0.shape[0], np.float64)
+    gM = np.zeros((keys0.shape[0], 6), np.float64)
+    for l, (k, a, b) in enumerate(zip(level_keys, alphas, betas)):
+        idx = np.searchsorted(np.asarray(k, np.uint64), keys0 >> np.uint64(3 * l))
+        assert np.array_equal(np.asarray(k, np.uint64)[idx], keys0 >> np.uint64(3 * l))
+        gm += np.asarray(a, np.float64)[idx]
+        gM += np.asarray(b, np.float64)[idx]
+    return gm, gM

@@ -36,6 +36,7 @@
 #include <string.h>
 
 #define ORC_API __attribute__((visibility("default")))
+#define M_PI_D 3.14159265358979323846
 
 /* ------------------------------------------------------------------------- */
 /* small helpers                                                             */
@@ -1045,4 +1046,142 @@ ORC_API int vxo_level_from_voxels(const uint64_t* keys, const uint64_t* mask, co
         ++v;
     }
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of  loss = sum_v gm(v) m(v) + sum_v gM(v) . M(v)  over level-0 voxels      */
+/* (coarser levels enter through gm, gM broadcast down: m and M of a parent are sums  */
+/* of its children).  FP64, for fibers.                                               */
+/* ------------------------------------------------------------------------- */
+
+/* clipped parameter interval of segment a + t d (voxel-local) against [0,1]^3:
+ * returns 0 if empty; t0, t1 and which axis/plane defines each end (-1 = endpoint). */
+static int clip64(const double* a, const double* d, double* t0, double* t1, int* ax0, int* ax1) {
+    double lo = 0.0, hi = 1.0;
+    int alo = -1, ahi = -1;
+    for (int i = 0; i < 3; ++i) {
+        if (d[i] == 0.0) {
+            if (a[i] < 0.0 || a[i] > 1.0) return 0;
+        } else {
+            double ta = -a[i] / d[i], tb = (1.0 - a[i]) / d[i];
+            double tn = d[i] > 0 ? ta : tb, tf = d[i] > 0 ? tb : ta;
+            if (tn > lo) { lo = tn; alo = i; }
+            if (tf < hi) { hi = tf; ahi = i; }
+        }
+    }
+    if (hi <= lo) return 0;
+    *t0 = lo; *t1 = hi; *ax0 = alo; *ax1 = ahi;
+    return 1;
+}
+
+/* gradient of f = w * pi r^2 len * (gm + gM . T(t)) for one (segment, voxel) pair.
+ * A, B grid coordinates, r grid units; outputs d f / d(A, B, r, w) (grid units). */
+ORC_API double vxo_pair_grad64(const double* A, const double* B, double r, double w, int vi, int vj, int vk,
+                               double gm, const double* gM, double* dA, double* dB, double* dr, double* dw) {
+    double a[3] = {A[0] - vi, A[1] - vj, A[2] - vk};
+    double d[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+    for (int i = 0; i < 3; ++i) { dA[i] = 0; dB[i] = 0; }
+    *dr = 0; *dw = 0;
+    double t0, t1;
+    int ax0, ax1;
+    if (!clip64(a, d, &t0, &t1, &ax0, &ax1)) return 0.0;
+    double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double t[3] = {d[0] / dn, d[1] / dn, d[2] / dn};
+    double len = (t1 - t0) * dn;
+    double mu = M_PI_D * r * r * len;
+    double T[6] = {t[0] * t[0], t[1] * t[1], t[2] * t[2], t[0] * t[1], t[0] * t[2], t[1] * t[2]};
+    double G = gm;
+    for (int c = 0; c < 6; ++c) G += gM[c] * T[c];
+    double f = w * mu * G;
+    *dw = mu * G;
+    *dr = w * (2.0 * mu / r) * G;
+    /* d len: len = |Q1 - Q0|, Q = (1-t) A + t B; an end on plane i moves within that plane */
+    double cA[3] = {0, 0, 0}, cB[3] = {0, 0, 0};
+    for (int e = 0; e < 2; ++e) {
+        double te = e == 0 ? t0 : t1;
+        int ax = e == 0 ? ax0 : ax1;
+        double sgn = e == 0 ? -1.0 : 1.0;     /* d len = t . (dQ1 - dQ0) */
+        for (int k = 0; k < 3; ++k) {
+            double gA = (1.0 - te) * t[k], gB = te * t[k];
+            if (ax == k) { gA -= (1.0 - te) * dn / d[k]; gB -= te * dn / d[k]; }
+            cA[k] += sgn * gA;
+            cB[k] += sgn * gB;
+        }
+    }
+    double kmu = w * M_PI_D * r * r * G;     /* d f / d len */
+    /* d T / d d: dT = (I - t t^T)/|d| applied to grad_t (gM . T) */
+    double gt[3];
+    gt[0] = 2 * gM[0] * t[0] + gM[3] * t[1] + gM[4] * t[2];
+    gt[1] = gM[3] * t[0] + 2 * gM[1] * t[1] + gM[5] * t[2];
+    gt[2] = gM[4] * t[0] + gM[5] * t[1] + 2 * gM[2] * t[2];
+    double tg = t[0] * gt[0] + t[1] * gt[1] + t[2] * gt[2];
+    double wm = w * mu;
+    for (int k = 0; k < 3; ++k) {
+        double gd = wm * (gt[k] - t[k] * tg) / dn;   /* d f / d d_k through T */
+        dA[k] = kmu * cA[k] - gd;
+        dB[k] = kmu * cB[k] + gd;
+    }
+    return f;
+}
+
+static int64_t find_key(const uint64_t* keys, int64_t n, uint64_t k) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    return (lo < n && keys[lo] == k) ? lo : -1;
+}
+
+/* Gradients of the loss w.r.t. ctrl [P][4] (xyz world, radius world) and weights [N],
+ * given the broadcast level-0 adjoints gm0 [V], gM0 [V][6] on the sorted keys0.
+ * Only the primitives listed in prims (or all when prims == NULL) are visited;
+ * returns the loss contribution of the visited primitives. */
+ORC_API double vxo_fiber_adjoint(const double* ctrl, const int64_t* offsets, int64_t F, const double* weights,
+                                 const double* origin, double voxel_size, int R,
+                                 const uint64_t* keys0, int64_t V, const double* gm0, const double* gM0,
+                                 const int64_t* prims, int64_t nprims,
+                                 double* d_ctrl, double* d_w) {
+    double s = 1.0 / voxel_size;
+    double loss = 0.0;
+    int64_t prim = 0;
+    int64_t pi = 0;
+    for (int64_t f = 0; f < F; ++f) {
+        for (int64_t c = offsets[f]; c + 1 < offsets[f + 1]; ++c, ++prim) {
+            if (prims) {
+                while (pi < nprims && prims[pi] < prim) ++pi;
+                if (pi >= nprims || prims[pi] != prim) continue;
+            }
+            const double* pa = ctrl + 4 * c;
+            const double* pb = ctrl + 4 * (c + 1);
+            double A[3], B[3];
+            for (int i = 0; i < 3; ++i) { A[i] = (pa[i] - origin[i]) * s; B[i] = (pb[i] - origin[i]) * s; }
+            double r = (pa[3] + pb[3]) * 0.5 * s;
+            double w = weights ? weights[prim] : 1.0;
+            int lo[3], hi[3];
+            for (int i = 0; i < 3; ++i) {
+                lo[i] = clampi((int)floor(fmin(A[i], B[i])) - 1, 0, R - 1);
+                hi[i] = clampi((int)floor(fmax(A[i], B[i])) + 1, 0, R - 1);
+            }
+            double gA[3] = {0, 0, 0}, gB[3] = {0, 0, 0}, gr = 0, gw = 0;
+            for (int vk = lo[2]; vk <= hi[2]; ++vk)
+                for (int vj = lo[1]; vj <= hi[1]; ++vj)
+                    for (int vi = lo[0]; vi <= hi[0]; ++vi) {
+                        int64_t v = find_key(keys0, V, vxo_morton((uint32_t)vi, (uint32_t)vj, (uint32_t)vk));
+                        if (v < 0) continue;
+                        double a3[3], b3[3], dr, dw;
+                        loss += vxo_pair_grad64(A, B, r, w, vi, vj, vk, gm0[v], gM0 + 6 * v, a3, b3, &dr, &dw);
+                        for (int i = 0; i < 3; ++i) { gA[i] += a3[i]; gB[i] += b3[i]; }
+                        gr += dr;
+                        gw += dw;
+                    }
+            if (d_ctrl) {
+                for (int i = 0; i < 3; ++i) { d_ctrl[4 * c + i] += gA[i] * s; d_ctrl[4 * (c + 1) + i] += gB[i] * s; }
+                d_ctrl[4 * c + 3] += gr * 0.5 * s;
+                d_ctrl[4 * (c + 1) + 3] += gr * 0.5 * s;
+            }
+            if (d_w) d_w[prim] += gw;
+        }
+    }
+    return loss;
 }

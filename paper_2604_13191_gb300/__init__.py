@@ -6,6 +6,6 @@ Morton-keyed level 0 with 8^3 sub-cell occupancy, mass and SGGX second moments
 (Sec. 3, 4.1) -> bottom-up pyramid with hierarchical SGGX clustering (Sec. 4.2-4.4).
 The compute runs in hand-written CUDA kernels behind the C ABI of include/vx.h.
 """
-from .api import Context, Level, VxError, load, library_path, EXPORTS  # noqa: F401
+from .api import Context, Level, VxError, VoxelizeLoD, load, library_path, EXPORTS  # noqa: F401
 
-__all__ = ["Context", "Level", "VxError", "load", "library_path", "EXPORTS"]
+__all__ = ["Context", "Level", "VxError", "VoxelizeLoD", "load", "library_path", "EXPORTS"]

@@ -61,7 +61,7 @@ class VxAllocator(C.Structure):
 
 EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_lod",
            "vx_level_release", "vx_status_string", "vx_last_cuda_error", "vx_profile_enable",
-           "vx_profile_read"]
+           "vx_profile_read", "vx_backward"]
 
 
 class VxStageTime(C.Structure):
@@ -105,6 +105,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         lib.vx_profile_enable.argtypes = [P, C.c_int]
         lib.vx_profile_read.restype = C.c_int
         lib.vx_profile_read.argtypes = [P, C.POINTER(VxStageTime), C.c_int, C.POINTER(C.c_int)]
+        lib.vx_backward.restype = C.c_int
+        lib.vx_backward.argtypes = [P, C.POINTER(VxPrimitives), C.POINTER(VxGrid), P, C.c_int64, C.c_int,
+                                    C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), P, P, P]
         _lib = lib
         return lib
 
@@ -277,6 +280,53 @@ class Context:
             raise self._err(st, "vx_voxelize")
         return self._wrap(L)
 
+    def _fiber_prims(self, ctrl, fiber_offsets, weights, num_prims, keep):
+        P = VxPrimitives()
+        c = ctrl.contiguous()
+        o = fiber_offsets.contiguous()
+        _check(c, torch.float32, self.device, "ctrl")
+        _check(o, torch.int64, self.device, "fiber_offsets")
+        keep += [c, o]
+        P.kind = VX_FIBERS
+        P.ctrl = c.data_ptr()
+        P.num_ctrl = c.shape[0]
+        P.fiber_offsets = o.data_ptr()
+        P.num_fibers = o.shape[0] - 1
+        if num_prims is None:
+            oc = o.cpu()
+            num_prims = int(torch.clamp(oc[1:] - oc[:-1] - 1, min=0).sum())
+        P.num_prims = int(num_prims)
+        if weights is not None:
+            w = weights.contiguous()
+            _check(w, torch.float32, self.device, "weights")
+            keep.append(w)
+            P.weights = w.data_ptr()
+        return P
+
+    def backward(self, grid, *, ctrl, fiber_offsets, keys0, grad_mass, grad_moment, weights=None,
+                 num_prims=None, stream=None):
+        """vx_backward: gradients of sum_l <grad_mass[l], m_l> + <grad_moment[l], M_l> w.r.t.
+        the control points ([P,4]: xyz, radius) and the per-segment weights."""
+        keep = []
+        P = self._fiber_prims(ctrl, fiber_offsets, weights, num_prims, keep)
+        L = len(grad_mass) - 1
+        gm = [g.contiguous() for g in grad_mass]
+        gM = [g.contiguous() for g in grad_moment]
+        for g in gm + gM:
+            _check(g, torch.float32, self.device, "grad")
+        k0 = keys0.contiguous()
+        keep += gm + gM + [k0]
+        pm = (C.c_void_p * (L + 1))(*[g.data_ptr() for g in gm])
+        pM = (C.c_void_p * (L + 1))(*[g.data_ptr() for g in gM])
+        g_ctrl = torch.empty((P.num_ctrl, 4), dtype=torch.float32, device=self.device)
+        g_w = torch.empty((P.num_prims,), dtype=torch.float32, device=self.device)
+        G = _grid(grid)
+        st = self.lib.vx_backward(self.h, C.byref(P), C.byref(G), k0.data_ptr(), k0.shape[0], L, pm, pM,
+                                  _stream(stream), g_ctrl.data_ptr(), g_w.data_ptr())
+        if st != 0:
+            raise self._err(st, "vx_backward")
+        return g_ctrl, g_w
+
     def build_lod(self, level: Level, *, K: int = 1, dirs=None, num_levels: int = 0,
                   stream=None) -> list:
         """vx_build_lod: levels level+1 .. level+L (L = num_levels, 0 = down to 1^3)."""
@@ -318,3 +368,36 @@ def _stream(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return C.c_void_p(stream.cuda_stream)
+
+
+class VoxelizeLoD(torch.autograd.Function):
+    """Differentiable fiber voxelization + K = 1 pyramid.
+
+    forward(ctrl [P,4], weights [N], fiber_offsets, grid, num_levels, context) returns
+    (mass_0, moment_0, mass_1, moment_1, ..., mass_L, moment_L).  backward runs
+    vx_backward; it keeps only the level-0 keys (coarse levels are not stored, their
+    parent structure is recomputed from the keys) and recomputes the candidate pairs.
+    """
+
+    @staticmethod
+    def forward(fctx, ctrl, weights, fiber_offsets, grid, num_levels, context):
+        L0 = context.voxelize(grid, ctrl=ctrl, fiber_offsets=fiber_offsets, weights=weights)
+        pyr = context.build_lod(L0, K=1, num_levels=num_levels) if num_levels else []
+        outs = []
+        for lv in [L0] + pyr:
+            outs += [lv.mass.clone(), lv.moment.clone()]
+        fctx.save_for_backward(ctrl, weights, fiber_offsets, L0.keys.clone())
+        fctx.grid = grid
+        fctx.context = context
+        fctx.num_levels = num_levels
+        return tuple(outs)
+
+    @staticmethod
+    def backward(fctx, *grads):
+        ctrl, weights, off, keys0 = fctx.saved_tensors
+        gm = [torch.zeros_like(g) if g is None else g for g in grads[0::2]]
+        gM = [torch.zeros_like(g) if g is None else g for g in grads[1::2]]
+        g_ctrl, g_w = fctx.context.backward(fctx.grid, ctrl=ctrl, fiber_offsets=off, keys0=keys0,
+                                            grad_mass=[g.float() for g in gm],
+                                            grad_moment=[g.float() for g in gM], weights=weights)
+        return g_ctrl, g_w, None, None, None, None

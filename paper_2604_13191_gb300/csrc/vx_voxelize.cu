@@ -962,3 +962,280 @@ extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, co
     }
     return VX_OK;
 }
+
+// =====================================================================================
+// Adjoint (vx_backward)
+// =====================================================================================
+namespace {
+
+__global__ void k_key_shift_flags(const uint64_t* __restrict__ keys, uint32_t n, int shift, uint32_t* __restrict__ flags) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flags[i] = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift)) ? 1u : 0u;
+}
+
+// level-0 adjoints: g = grad_0 (init) or g += grad_l[parent index]
+__global__ void k_bcast(const uint32_t* __restrict__ excl, const uint32_t* __restrict__ flags, uint32_t n,
+                        const float* __restrict__ gmass, const float* __restrict__ gmom, int init,
+                        float* __restrict__ gm, float* __restrict__ gM) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t p = init ? i : excl[i] + flags[i] - 1u;
+    if (init) {
+        gm[i] = gmass[p];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) gM[(size_t)i * 6 + c] = gmom[(size_t)p * 6 + c];
+    } else {
+        gm[i] = gm[i] + gmass[p];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) gM[(size_t)i * 6 + c] = gM[(size_t)i * 6 + c] + gmom[(size_t)p * 6 + c];
+    }
+}
+
+// d/d(A, B, r, w) of  w * pi r^2 len * (gm + gM . T(t))  for one (segment, voxel) pair
+// (grid units); out: dA[3], dB[3], dr, dw
+__device__ __forceinline__ void pair_grad(float4 A, float4 B, int vi, int vj, int vk, float gm, const float* gM,
+                                          float* out) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) out[c] = 0.0f;
+    const float a[3] = {A.x - (float)vi, A.y - (float)vj, A.z - (float)vk};
+    const float d[3] = {B.x - A.x, B.y - A.y, B.z - A.z};
+    float t0 = 0.0f, t1 = 1.0f;
+    int ax0 = -1, ax1 = -1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (d[i] == 0.0f) {
+            if (a[i] < 0.0f || a[i] > 1.0f) return;
+        } else {
+            float ta = (0.0f - a[i]) / d[i], tb = (1.0f - a[i]) / d[i];
+            float tn = d[i] > 0.0f ? ta : tb, tf = d[i] > 0.0f ? tb : ta;
+            if (tn > t0) { t0 = tn; ax0 = i; }
+            if (tf < t1) { t1 = tf; ax1 = i; }
+        }
+    }
+    if (t1 <= t0) return;
+    const float r = A.w, w = B.w;
+    const float dn = sqrtf((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+    const float t[3] = {d[0] / dn, d[1] / dn, d[2] / dn};
+    const float len = (t1 - t0) * dn;
+    const float mu = (kPi * (r * r)) * len;
+    float G = gm;
+    G = G + gM[0] * (t[0] * t[0]);
+    G = G + gM[1] * (t[1] * t[1]);
+    G = G + gM[2] * (t[2] * t[2]);
+    G = G + gM[3] * (t[0] * t[1]);
+    G = G + gM[4] * (t[0] * t[2]);
+    G = G + gM[5] * (t[1] * t[2]);
+    out[7] = mu * G;                       // d/dw
+    out[6] = w * (2.0f * mu / r) * G;      // d/dr
+    float cA[3] = {0.0f, 0.0f, 0.0f}, cB[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float te = e == 0 ? t0 : t1;
+        const int ax = e == 0 ? ax0 : ax1;
+        const float sg = e == 0 ? -1.0f : 1.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float gA = (1.0f - te) * t[k], gB = te * t[k];
+            if (ax == k) {
+                gA -= (1.0f - te) * dn / d[k];
+                gB -= te * dn / d[k];
+            }
+            cA[k] += sg * gA;
+            cB[k] += sg * gB;
+        }
+    }
+    const float kmu = w * (kPi * (r * r)) * G;
+    float gt[3];
+    gt[0] = 2.0f * gM[0] * t[0] + gM[3] * t[1] + gM[4] * t[2];
+    gt[1] = gM[3] * t[0] + 2.0f * gM[1] * t[1] + gM[5] * t[2];
+    gt[2] = gM[4] * t[0] + gM[5] * t[1] + 2.0f * gM[2] * t[2];
+    const float tg = t[0] * gt[0] + t[1] * gt[1] + t[2] * gt[2];
+    const float wm = w * mu;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float gd = wm * (gt[k] - t[k] * tg) / dn;
+        out[k] = kmu * cA[k] - gd;
+        out[3 + k] = kmu * cB[k] + gd;
+    }
+}
+
+__device__ __forceinline__ int64_t find_key64(const uint64_t* __restrict__ keys, uint32_t n, uint64_t k) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (keys[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    return (lo < n && keys[lo] == k) ? (int64_t)lo : -1;
+}
+
+// warp per segment: sum of its pair gradients (lane j takes pairs j, j+32, ...; fixed tree)
+__global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_fibers(const float4* __restrict__ ra,
+                                                                    const float4* __restrict__ rb, uint32_t np,
+                                                                    const uint32_t* __restrict__ offs,
+                                                                    const uint32_t* __restrict__ cnt,
+                                                                    const uint32_t* __restrict__ pkeys,
+                                                                    const uint64_t* __restrict__ keys0, uint32_t V0,
+                                                                    const float* __restrict__ gm,
+                                                                    const float* __restrict__ gM,
+                                                                    float* __restrict__ seg_grad) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * EMIT_WARPS;
+    for (uint32_t p = blockIdx.x * EMIT_WARPS + (threadIdx.x >> 5); p < np; p += warps) {
+        const float4 A = ra[p], B = rb[p];
+        const uint32_t beg = offs[p], n = cnt[p];
+        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (uint32_t j = lane; j < n; j += 32) {
+            const uint32_t key = pkeys[beg + j];
+            const int64_t v = find_key64(keys0, V0, (uint64_t)key);
+            if (v < 0) continue;
+            float g[8];
+            float gMv[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) gMv[c] = gM[(size_t)v * 6 + c];
+            pair_grad(A, B, (int)vx_compact1by2(key), (int)vx_compact1by2(key >> 1), (int)vx_compact1by2(key >> 2),
+                      gm[v], gMv, g);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = acc[c] + g[c];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = acc[c] + __shfl_xor_sync(0xffffffffu, acc[c], o);
+        if (lane < 8) seg_grad[(size_t)p * 8 + lane] = acc[lane];
+    }
+}
+
+// thread per control point: world-unit gradients from the segment before and after it
+__global__ void k_adjoint_ctrl(const int64_t* __restrict__ off, int64_t F, const uint32_t* __restrict__ seg_start,
+                               int64_t P, const float* __restrict__ seg_grad, float s, float4* __restrict__ gctrl) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P) return;
+    int64_t lo = 0, hi = F;       // last fiber with off[f] <= c
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= c) lo = mid + 1; else hi = mid;
+    }
+    const int64_t f = lo - 1;
+    float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (f >= 0 && c < off[f + 1]) {
+        const bool has_prev = c > off[f];
+        const bool has_next = c + 1 < off[f + 1];
+        float px = 0.0f, py = 0.0f, pz = 0.0f, pr = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f, nr = 0.0f;
+        if (has_prev) {
+            const float* q = seg_grad + (size_t)(seg_start[f] + (uint32_t)(c - 1 - off[f])) * 8;
+            px = q[3]; py = q[4]; pz = q[5]; pr = q[6];
+        }
+        if (has_next) {
+            const float* q = seg_grad + (size_t)(seg_start[f] + (uint32_t)(c - off[f])) * 8;
+            nx = q[0]; ny = q[1]; nz = q[2]; nr = q[6];
+        }
+        g.x = (px + nx) * s;
+        g.y = (py + ny) * s;
+        g.z = (pz + nz) * s;
+        g.w = (pr + nr) * (0.5f * s);
+    }
+    gctrl[c] = g;
+}
+
+__global__ void k_adjoint_weights(const float* __restrict__ seg_grad, uint32_t np, float* __restrict__ gw) {
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np) gw[p] = seg_grad[(size_t)p * 8 + 7];
+}
+
+}  // namespace
+
+extern "C" vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
+                                 const uint64_t* keys0, int64_t num_voxels0, int num_levels,
+                                 const float* const* grad_mass, const float* const* grad_moment, void* stream,
+                                 float* grad_ctrl, float* grad_weights) {
+    if (!ctx || !prims || !grid || !grad_mass || !grad_moment || !grad_ctrl) return VX_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    if (prims->kind != VX_FIBERS) return VX_ERR_UNSUPPORTED;
+    const uint32_t R = grid->resolution;
+    if (R == 0 || (R & (R - 1)) != 0) return VX_ERR_INVALID_ARG;
+    if (R > 1024 || grid->sub_res != 8) return VX_ERR_UNSUPPORTED;
+    if (num_voxels0 < 0 || num_voxels0 > 0xffffffffll || num_levels < 0 || num_levels > 11) return VX_ERR_INVALID_ARG;
+    if (prims->num_prims < 0 || prims->num_prims > 0xfffffffell) return VX_ERR_CAPACITY;
+    if (!prims->ctrl || !prims->fiber_offsets || prims->num_fibers <= 0 || ((uintptr_t)prims->ctrl & 15) != 0 ||
+        ((uintptr_t)grad_ctrl & 15) != 0)
+        return VX_ERR_INVALID_ARG;
+    for (int l = 0; l <= num_levels; ++l)
+        if (!grad_mass[l] || !grad_moment[l]) return VX_ERR_INVALID_ARG;
+    const uint32_t np = (uint32_t)prims->num_prims;
+    const uint32_t V0 = (uint32_t)num_voxels0;
+    const int64_t P = prims->num_ctrl, F = prims->num_fibers;
+    GridDev g;
+    g.o[0] = grid->origin[0]; g.o[1] = grid->origin[1]; g.o[2] = grid->origin[2];
+    g.s = 1.0f / grid->voxel_size;
+    g.R = (int)R;
+    VX_CUDA_TRY(cudaMemsetAsync(grad_ctrl, 0, (size_t)P * 16, s));
+    if (grad_weights && np) VX_CUDA_TRY(cudaMemsetAsync(grad_weights, 0, (size_t)np * 4, s));
+    if (np == 0) return VX_OK;
+
+    // ---- level-0 adjoints (coarse adjoints broadcast down) ------------------------------
+    VX_TRY(vx_ws_ensure(ctx, WS_LOD_FLAGS, (size_t)std::max<uint32_t>(V0, 1) * 4, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_LOD_IDX, (size_t)std::max<uint32_t>(V0, 1) * 4, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_LOD_TMP, (size_t)std::max<uint32_t>(V0, 1) * 28, s));
+    uint32_t* flags = (uint32_t*)ctx->ws[WS_LOD_FLAGS].p;
+    uint32_t* excl = (uint32_t*)ctx->ws[WS_LOD_IDX].p;
+    float* gm = (float*)ctx->ws[WS_LOD_TMP].p;
+    float* gM = gm + V0;
+    if (V0) {
+        VX_LAUNCH(ctx, ST_LOD_HEADS, s, k_bcast<<<grid_for(V0, 256), 256, 0, s>>>(excl, flags, V0, grad_mass[0],
+                                                                                 grad_moment[0], 1, gm, gM));
+        for (int l = 1; l <= num_levels; ++l) {
+            VX_LAUNCH(ctx, ST_LOD_HEADS, s, k_key_shift_flags<<<grid_for(V0, 256), 256, 0, s>>>(keys0, V0, 3 * l, flags));
+            VX_TRY(vx_scan_u32(ctx, flags, excl, V0, nullptr, s));
+            VX_LAUNCH(ctx, ST_LOD_HEADS, s, k_bcast<<<grid_for(V0, 256), 256, 0, s>>>(excl, flags, V0, grad_mass[l],
+                                                                                     grad_moment[l], 0, gm, gM));
+        }
+    }
+    // ---- recompute the candidate pairs (primitive-major order) --------------------------
+    VX_TRY(vx_ws_ensure(ctx, WS_REC_A, (size_t)np * 16, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_REC_B, (size_t)np * 16, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_MISC, 256, s));
+    uint32_t* misc = (uint32_t*)ctx->ws[WS_MISC].p;
+    VX_CUDA_TRY(cudaMemsetAsync(misc, 0, 64, s));
+    float4* r0 = (float4*)ctx->ws[WS_REC_A].p;
+    float4* r1 = (float4*)ctx->ws[WS_REC_B].p;
+    if (F > 0x7fffffff) return VX_ERR_CAPACITY;
+    VX_TRY(vx_ws_ensure(ctx, WS_FIBER_START, (size_t)F * 4 + 256, s));
+    uint32_t* fs = (uint32_t*)ctx->ws[WS_FIBER_START].p;
+    VX_LAUNCH(ctx, ST_PREP, s, k_fiber_seg_counts<<<grid_for((size_t)F, 256), 256, 0, s>>>(prims->fiber_offsets, F, fs));
+    VX_TRY(vx_scan_u32(ctx, fs, fs, (uint32_t)F, misc + 4, s));
+    VX_LAUNCH(ctx, ST_PREP, s, k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl,
+                                                                             prims->fiber_offsets, fs, F, misc + 4,
+                                                                             prims->weights, np, g, r0, r1, misc));
+    VX_TRY(vx_ws_ensure(ctx, WS_COUNT, (size_t)np * 4, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_OFFS, (size_t)np * 4, s));
+    uint32_t* cnt = (uint32_t*)ctx->ws[WS_COUNT].p;
+    uint32_t* offs = (uint32_t*)ctx->ws[WS_OFFS].p;
+    const unsigned cblocks = (unsigned)std::min<size_t>((np + EMIT_WARPS - 1) / EMIT_WARPS, (size_t)vx::kSMs * 64);
+    VX_LAUNCH(ctx, ST_COUNT, s, k_candidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                    r0, r1, nullptr, np, (int)R, cnt, nullptr, nullptr, nullptr));
+    VX_TRY(vx_scan_u32(ctx, cnt, offs, np, misc + 1, s));
+    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 8, cudaMemcpyDeviceToHost, s));
+    VX_CUDA_TRY(cudaStreamSynchronize(s));
+    if (((uint32_t*)ctx->host_pin)[0]) return VX_ERR_INVALID_ARG;
+    const uint32_t npairs = ((uint32_t*)ctx->host_pin)[1];
+    if (npairs >= 0x80000000u) return VX_ERR_CAPACITY;
+    VX_TRY(vx_ws_ensure(ctx, WS_KEYS0, (size_t)std::max<uint32_t>(npairs, 1) * 4, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_VALS0, (size_t)std::max<uint32_t>(npairs, 1) * 4, s));
+    uint32_t* k0 = (uint32_t*)ctx->ws[WS_KEYS0].p;
+    uint32_t* v0 = (uint32_t*)ctx->ws[WS_VALS0].p;
+    if (npairs)
+        VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                       r0, r1, nullptr, np, (int)R, nullptr, offs, k0, v0));
+    // ---- per-segment gradients, then the control-point scatter ---------------------------
+    VX_TRY(vx_ws_ensure(ctx, WS_SEG_OUT, (size_t)np * 32, s));
+    float* seg_grad = (float*)ctx->ws[WS_SEG_OUT].p;
+    VX_LAUNCH(ctx, ST_REDUCE_FIBERS, s, k_adjoint_fibers<<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                            r0, r1, np, offs, cnt, k0, keys0, V0, gm, gM, seg_grad));
+    VX_LAUNCH(ctx, ST_FINALIZE, s, k_adjoint_ctrl<<<grid_for((size_t)P, 256), 256, 0, s>>>(
+                                       prims->fiber_offsets, F, fs, P, seg_grad, g.s, (float4*)grad_ctrl));
+    if (grad_weights)
+        VX_LAUNCH(ctx, ST_FINALIZE, s, k_adjoint_weights<<<grid_for(np, 256), 256, 0, s>>>(seg_grad, np, grad_weights));
+    VX_CUDA_TRY(cudaGetLastError());
+    return VX_OK;
+}

@@ -20,7 +20,7 @@ import numpy as np
 __all__ = [
     "Grid", "Workload", "heightfield", "yarn", "woven_patch", "sample_directions",
     "random_segments", "random_triangles", "config1", "config2", "config3",
-    "config4", "config5", "fiber_segment_count",
+    "config4", "config5", "fiber_segment_count", "loss_weights",
 ]
 
 
@@ -293,3 +293,30 @@ def config5(seed: int = 5, R: int = 256, levels: int = 4, n_params: int = 64,
     w.extra["seed"] = seed
     w.extra["n_params"] = n_params
     return w
+
+
+# ----------------------------------------------------------------------------
+# Loss weights of the differentiation workload: U(-1,1) per (level, key, component),
+# from SplitMix64 (Steele, Lea, Flood 2014) of a counter built from the key, the level,
+# the component and the seed, so that any set of voxels gets the same weights
+# regardless of how it is ordered or who enumerated it.
+# ----------------------------------------------------------------------------
+def _splitmix64(x: np.ndarray) -> np.ndarray:
+    x = (x + np.uint64(0x9E3779B97F4A7C15)) & np.uint64(0xFFFFFFFFFFFFFFFF)
+    z = x
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def loss_weights(keys, level: int, seed: int = 5):
+    """(alpha [n] float32, beta [n,6] float32) in U(-1,1) for the voxels `keys` of `level`."""
+    k = np.asarray(keys, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        base = (k << np.uint64(8)) ^ (np.uint64(level) << np.uint64(4)) ^ (np.uint64(seed) << np.uint64(56))
+        cols = []
+        for c in range(7):
+            h = _splitmix64(base + np.uint64(c))
+            u = (h >> np.uint64(40)).astype(np.float64) / float(1 << 24)
+            cols.append((2.0 * u - 1.0).astype(np.float32))
+    return cols[0], np.stack(cols[1:], axis=1)

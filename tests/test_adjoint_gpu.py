@@ -1,0 +1,134 @@
+"""Adjoint (vx_backward / VoxelizeLoD) against the oracle's FP64 analytic gradient and
+FP64 central finite differences.
+
+Loss: sum over levels 0..L and voxels of alpha * m + beta . M with U(-1,1) weights
+drawn per (level, key, component) by a counter-based generator, so both sides draw the
+same weights from their own key sets.  Parameters: control-point xyz, radii, weights.
+Tolerance: |g32 - g64| <= 1e-4 * max(|g64|, median |g64|) (FP32 per-pair terms carry
+~1e-6 relative error; a sum over tens of pairs with mixed signs stays well inside).
+FD: central, h = 1e-4 (world units), FP64; stencils whose clipped pieces change shape
+between -h and +h (FD at h and h/2 disagree) are reported and excluded.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2604_13191_gb300 as vx  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = vx.Context(DEV)
+    yield c
+    c.close()
+
+
+def gpu_forward_backward(ctx, w, levels, weights):
+    ctrl = torch.from_numpy(w.ctrl).to(DEV).requires_grad_(True)
+    wt = torch.from_numpy(weights).to(DEV).requires_grad_(True)
+    off = torch.from_numpy(w.fiber_offsets).to(DEV)
+    outs = vx.VoxelizeLoD.apply(ctrl, wt, off, w.grid, levels, ctx)
+    # level keys for the loss weights: rebuild them from the forward's level 0
+    L0 = ctx.voxelize(w.grid, ctrl=ctrl.detach(), fiber_offsets=off, weights=wt.detach())
+    pyr = ctx.build_lod(L0, K=1, num_levels=levels)
+    keys = [lv.keys.cpu().numpy().view(np.uint64) for lv in [L0] + pyr]
+    loss = 0.0
+    for l in range(levels + 1):
+        a, b = synth.loss_weights(keys[l], l)
+        loss = loss + (outs[2 * l] * torch.from_numpy(a).to(DEV)).sum() + \
+            (outs[2 * l + 1] * torch.from_numpy(b).to(DEV)).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    return ctrl.grad.cpu().numpy(), wt.grad.cpu().numpy(), keys
+
+
+def test_adjoint_matches_oracle_gradient(ctx):
+    w = synth.config2(fibers_per_ply=4, segments=300, R=64, K=1)
+    levels = 4
+    rng = np.random.default_rng(51)
+    weights = rng.uniform(0.5, 2.0, w.num_prims).astype(np.float32)
+    g_ctrl, g_w, keys = gpu_forward_backward(ctx, w, levels, weights)
+    ref0 = oracle.voxelize_fibers(w.ctrl, w.fiber_offsets, w.grid, weights)
+    refs = [ref0] + oracle.build_pyramid(ref0, 64, 1, synth.sample_directions(16), num_levels=levels)
+    for l in range(levels + 1):
+        assert np.array_equal(refs[l]["keys"], keys[l])
+    ab = [synth.loss_weights(r["keys"], l) for l, r in enumerate(refs)]
+    gm0, gM0 = oracle.broadcast_adjoints(ref0["keys"], [r["keys"] for r in refs], [a for a, _ in ab],
+                                         [b for _, b in ab])
+    _, d_ctrl, d_w = oracle.fiber_adjoint(w.ctrl, w.fiber_offsets, w.grid, ref0["keys"], gm0, gM0, weights=weights)
+    scale = np.median(np.abs(d_ctrl[:, :3]))
+    err = np.abs(g_ctrl[:, :3] - d_ctrl[:, :3])
+    assert np.all(err <= 1e-4 * np.maximum(np.abs(d_ctrl[:, :3]), scale)), err.max()
+    rs = np.median(np.abs(d_ctrl[:, 3]))
+    assert np.all(np.abs(g_ctrl[:, 3] - d_ctrl[:, 3]) <= 1e-4 * np.maximum(np.abs(d_ctrl[:, 3]), rs))
+    ws = np.median(np.abs(d_w))
+    assert np.all(np.abs(g_w - d_w) <= 1e-4 * np.maximum(np.abs(d_w), ws))
+
+
+def test_adjoint_finite_differences_yarn_256(ctx):
+    """Config 5: the yarn at 256^3 with 4 LoD levels, 64 random parameters."""
+    w = synth.config5()
+    levels = w.levels
+    weights = np.ones(w.num_prims, np.float32)
+    g_ctrl, g_w, keys = gpu_forward_backward(ctx, w, levels, weights)
+    rng = np.random.default_rng(w.extra["seed"])
+    off = w.fiber_offsets
+    P = w.ctrl.shape[0]
+    c64 = w.ctrl.astype(np.float64)
+    h = 1e-4
+    checked, kinks, worst = 0, 0, 0.0
+    for _ in range(w.extra["n_params"]):
+        c = int(rng.integers(0, P))
+        comp = int(rng.integers(0, 4))
+        f = int(np.searchsorted(off, c, side="right") - 1)
+        # segments touching control point c (segment ids count c - f for >= 1-point fibers)
+        prims = []
+        if c > off[f]:
+            prims.append(c - f - 1)
+        if c + 1 < off[f + 1]:
+            prims.append(c - f)
+        # occupied voxels near the affected segments (brute force over every primitive)
+        s = 1.0 / w.grid.voxel_size
+        pts = c64[max(c - 1, 0): c + 2, :3] * s
+        lo = np.maximum(np.floor(pts.min(0) - 2.5).astype(int), 0)
+        hi = np.minimum(np.floor(pts.max(0) + 2.5).astype(int), w.grid.resolution - 1)
+        g = np.stack(np.meshgrid(*[np.arange(lo[i], hi[i] + 1) for i in range(3)], indexing="ij"), -1).reshape(-1, 3)
+        cand = np.array([oracle.morton(int(x), int(y), int(z)) for x, y, z in g], np.uint64)
+        vox = oracle.fiber_voxels(w.ctrl, off, w.grid, cand)
+        occ = cand[vox["mask"].any(1)]
+        occ.sort()
+        gm0 = np.zeros(occ.shape[0]); gM0 = np.zeros((occ.shape[0], 6))
+        for l in range(levels + 1):
+            a, b = synth.loss_weights(occ >> np.uint64(3 * l), l)
+            gm0 += a; gM0 += b
+
+        def local_loss(cc):
+            return oracle.fiber_adjoint(cc, off, w.grid, occ, gm0, gM0, prims=np.array(prims))[0]
+
+        def fd(step):
+            cp = c64.copy(); cp[c, comp] += step
+            cm = c64.copy(); cm[c, comp] -= step
+            return (local_loss(cp) - local_loss(cm)) / (2 * step)
+        f1, f2 = fd(h), fd(h / 2)
+        _, d_ctrl, _ = oracle.fiber_adjoint(c64, off, w.grid, occ, gm0, gM0, prims=np.array(prims))
+        ref = d_ctrl[c, comp]
+        if abs(f1 - f2) > 1e-5 * max(abs(f1), 1e-3):
+            kinks += 1
+            continue
+        assert abs(ref - f1) <= 1e-4 * max(abs(f1), 1e-3), (c, comp, ref, f1)
+        err = abs(g_ctrl[c, comp] - f1) / max(abs(f1), 1e-3)
+        worst = max(worst, err)
+        assert err <= 1e-4, (c, comp, g_ctrl[c, comp], f1)
+        checked += 1
+    print(f"FD checked {checked}, kinks excluded {kinks}, worst rel {worst:.2e}")
+    assert checked >= 48

@@ -3,12 +3,13 @@
 Bar: keys, sub-cell masks, occupancy, projections and lobe counts bit-exact; mass and
 moments bit-exact with the oracle's FP32 chain and within the stated tolerance of its
 FP64 reference; lobes (S, weight) within 1e-5 (trace-1 matrices, so absolute).
-Tolerance (FP32 vs FP64 reference):
-    |m - m64| <= 1e-5 |m64| + 1e-6 max(m64)        (mass)
-    |M - M64| <= 1e-5 tr(M64) + 1e-6 max(m64)      (moment entries)
-The absolute floor covers FP32 clipping of tiny pieces: a clip parameter carries an
-absolute error of a few 2^-24 of the whole primitive, so a sliver's measure is exact
-only to ~1e-7 of the primitive's measure, which is below 1e-6 of the largest voxel mass.
+Tolerance (FP32 vs FP64 reference), with mu_max the larger of the largest voxel mass
+and the largest whole-primitive measure w * pi r^2 L (fibers) or w * area (triangles):
+    |m - m64| <= 1e-5 |m64| + 1e-6 mu_max          (mass)
+    |M - M64| <= 1e-5 tr(M64) + 1e-6 mu_max        (moment entries)
+The absolute floor covers FP32 clipping: a clip parameter carries an absolute error of a
+few 2^-24 of the primitive's parameter range, so a clipped piece's measure is exact only
+to ~1e-7 of the whole primitive's measure, whatever the size of the piece.
 """
 import numpy as np
 import pytest
@@ -52,14 +53,35 @@ def run_gpu(ctx, w, K=None, dirs=None, num_levels=0, lod=True):
     return [L0.host()] + [p.host() for p in pyr]
 
 
-def compare_level(g, r, name="", lobes=True):
+def prim_measure_max(w) -> float:
+    """Largest whole-primitive measure in level-0 voxel units."""
+    s = 1.0 / w.grid.voxel_size
+    wt = np.ones(w.num_prims) if w.weights is None else w.weights.astype(np.float64)
+    if w.kind == "triangles":
+        U = w.tri_verts[..., :3].astype(np.float64) * s
+        mu = 0.5 * np.linalg.norm(np.cross(U[:, 1] - U[:, 0], U[:, 2] - U[:, 0]), axis=1)
+    else:
+        off = w.fiber_offsets
+        mu = []
+        for f in range(len(off) - 1):
+            c = w.ctrl[off[f]: off[f + 1]].astype(np.float64)
+            if c.shape[0] < 2:
+                continue
+            L = np.linalg.norm(np.diff(c[:, :3], axis=0), axis=1) * s
+            r = 0.5 * (c[:-1, 3] + c[1:, 3]) * s
+            mu.append(np.pi * r * r * L)
+        mu = np.concatenate(mu) if mu else np.zeros(0)
+    return float((wt[: mu.shape[0]] * mu).max()) if mu.size else 0.0
+
+
+def compare_level(g, r, name="", lobes=True, mu_max=0.0):
     assert np.array_equal(g["keys"], r["keys"]), f"{name}: keys differ ({g['keys'].shape} vs {r['keys'].shape})"
     assert np.array_equal(g["mask"], r["mask"]), f"{name}: masks differ"
     assert np.array_equal(g["occ"], r["occ"]), f"{name}: occ differs"
     assert np.array_equal(g["proj"], r["proj"]), f"{name}: projections differ"
     m64, M64 = r["mass64"], r["moment64"]
     if m64.size:
-        floor = 1e-6 * max(float(m64.max()), 1e-30)
+        floor = 1e-6 * max(float(m64.max()), mu_max, 1e-30)
         assert np.all(np.abs(g["mass"] - m64) <= 1e-5 * np.abs(m64) + floor), f"{name}: mass tolerance"
         tr = M64[:, :3].sum(1)
         assert np.all(np.abs(g["moment"] - M64) <= (1e-5 * tr + floor)[:, None]), f"{name}: moment tolerance"
@@ -89,8 +111,9 @@ def test_heightfield_full_pyramid(ctx, dirs5000):
     ref0 = oracle.voxelize(w)
     refs = [ref0] + oracle.build_pyramid(ref0, 128, 1, dirs5000)
     assert len(got) == len(refs) == 8
+    mu = prim_measure_max(w)
     for lvl, (g, r) in enumerate(zip(got, refs)):
-        compare_level(g, r, f"level {lvl}")
+        compare_level(g, r, f"level {lvl}", mu_max=mu)
     # mass conservation across the pyramid (FP64 sums of FP32 outputs)
     tot = got[0]["mass"].astype(np.float64).sum()
     for g in got[1:]:
@@ -109,7 +132,7 @@ def test_random_fibers(ctx, dirs5000, seed, R, rad, pts):
     ref0 = oracle.voxelize(w)
     refs = [ref0] + oracle.build_pyramid(ref0, R, 1, dirs5000)
     for lvl, (g, r) in enumerate(zip(got, refs)):
-        compare_level(g, r, f"seed {seed} level {lvl}")
+        compare_level(g, r, f"seed {seed} level {lvl}", mu_max=prim_measure_max(w))
 
 
 @pytest.mark.parametrize("seed,R,size", [(1, 16, (0.2, 3.0)), (2, 32, (0.05, 0.5)), (3, 64, (2.0, 12.0))])
@@ -122,7 +145,7 @@ def test_random_triangles(ctx, dirs5000, seed, R, size):
     ref0 = oracle.voxelize(w)
     refs = [ref0] + oracle.build_pyramid(ref0, R, 1, dirs5000)
     for lvl, (g, r) in enumerate(zip(got, refs)):
-        compare_level(g, r, f"seed {seed} level {lvl}")
+        compare_level(g, r, f"seed {seed} level {lvl}", mu_max=prim_measure_max(w))
 
 
 def test_yarn_reduced_sggx_h(ctx, dirs5000):
@@ -133,7 +156,7 @@ def test_yarn_reduced_sggx_h(ctx, dirs5000):
     refs = [ref0] + oracle.build_pyramid(ref0, 128, 4, dirs5000)
     clustered = 0
     for lvl, (g, r) in enumerate(zip(got, refs)):
-        compare_level(g, r, f"level {lvl}")
+        compare_level(g, r, f"level {lvl}", mu_max=prim_measure_max(w))
         if lvl:
             clustered += int((r["lobe_count"] == 4).sum())
     assert clustered > 100
@@ -167,7 +190,7 @@ def test_degenerate_primitives(ctx, dirs5000):
     ref0 = oracle.voxelize(w)
     refs = [ref0] + oracle.build_pyramid(ref0, 8, 1, dirs5000)
     for lvl, (g, r) in enumerate(zip(got, refs)):
-        compare_level(g, r, f"level {lvl}")
+        compare_level(g, r, f"level {lvl}", mu_max=prim_measure_max(w))
     # degenerate triangles: a line and a point, plus a triangle in a grid plane
     tris = np.zeros((3, 3, 4), np.float32)
     tris[0, :, :3] = [[0.1, 0.1, 0.1], [0.6, 0.6, 0.6], [0.35, 0.35, 0.35]]
@@ -178,7 +201,7 @@ def test_degenerate_primitives(ctx, dirs5000):
     ref0 = oracle.voxelize(w)
     refs = [ref0] + oracle.build_pyramid(ref0, 8, 1, dirs5000)
     for lvl, (g, r) in enumerate(zip(got, refs)):
-        compare_level(g, r, f"tri level {lvl}")
+        compare_level(g, r, f"tri level {lvl}", mu_max=prim_measure_max(w))
 
 
 def test_single_voxel_grid_and_max_resolution(ctx, dirs5000):
@@ -190,7 +213,7 @@ def test_single_voxel_grid_and_max_resolution(ctx, dirs5000):
         ref0 = oracle.voxelize(w)
         refs = [ref0] + (oracle.build_pyramid(ref0, R, 1, dirs5000, num_levels=3) if R > 1 else [])
         for lvl, (g, r) in enumerate(zip(got, refs)):
-            compare_level(g, r, f"R={R} level {lvl}")
+            compare_level(g, r, f"R={R} level {lvl}", mu_max=prim_measure_max(w))
 
 
 def test_invalid_arguments(ctx):
