@@ -243,6 +243,7 @@ def main():
         total_ms = float(tt.item())
     value = ws * n_prims * args.steps / (total_ms / 1e3)
     launches = sum(v[0] for v in prof.values())
+    prof = {k: v for k, v in prof.items() if v[0]}
 
     # ---- e2e: same calls from pinned host buffers, outputs downloaded ------------------
     e2e = None
@@ -302,7 +303,8 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(w, dirs_np)
-    stages = {k: {"launches": v[0] // args.steps, "ms_per_step": v[1] / args.steps}
+    stages = {k: {"launches": v[0] // args.steps, "ms_per_step": v[1] / args.steps,
+                  "units_per_step": v[2] // args.steps}
               for k, v in prof.items() if v[0]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -333,17 +335,35 @@ def _source_hash(name):
     return h.hexdigest()[:16]
 
 
+# FP32 operations the definition spends per unit of work:
+#   reduce_fibers: per (pair, sub-cell) decision, the step-1/2 test on precomputed per-axis
+#     terms: 3 x (2 adds + 1 compare) = 9, plus the per-axis terms amortised (~1) -> 10
+#   sggx_cluster: per sampled direction: mat-vec 15, norm 5, thresholds 2, compares 6,
+#     reciprocal 1, scale 1, products 9, roundings 12 -> 51
+ALU_OPS = {"reduce_fibers": 512 * 10, "sggx_cluster": N_SAMPLES * 51}
+# algorithmic HBM bytes per unit
+HBM_BYTES = {
+    "sort_scatter": 16,          # per pair and pass: key + value read and written
+    "sort_hist": 4,              # per pair and pass: key read
+    "candidates_emit": 8 + 32,   # per pair written + the primitive record read (per pair upper)
+    "finalize": 100 + 140,       # per candidate voxel read + written
+}
+
+
 def roofline(prof, w, level_sizes, steps):
-    """Dominant stage by device time; achieved = algorithmic work per launch / avg launch
-    time (CUDA events on the launching stream, timed region)."""
+    """Dominant stage by device time; achieved = algorithmic work per launch / average
+    launch time (CUDA events on the launching stream, over the timed region)."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    stage, (nl, ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = N_SMS * FP32_LANES_PER_SM * clk_mhz * 1e6 / 1e12    # Tops/s, FP32 lanes x clock
+    stage, (nl, ms, units) = max(prof.items(), key=lambda kv: kv[1][1])
     avg_ms = ms / max(nl, 1)
+    units_per_launch = units / max(nl, 1)
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tfile):
@@ -351,28 +371,23 @@ def roofline(prof, w, level_sizes, steps):
             t = json.load(open(tfile))
             ent = t.get(stage)
             if ent and ent.get("source_hash") == _source_hash(ent["source"]):
-                traffic = ent["bytes_per_launch"]
+                traffic = ent["bytes_per_launch"] * units_per_launch / ent["units_per_launch"]
         except Exception:
             traffic = None
-    n = w.num_prims
-    if stage == "sggx_cluster":
-        # ALU: FP32 operations of the histogram sampling (per sample: 3x3 mat-vec 15, norm 5,
-        # thresholds 2, squares 3, compares 6, reciprocal 1, scale 1, products 12, roundings 6 = 51)
-        ops_per_sample = 51
-        clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = N_SMS * FP32_LANES_PER_SM * clk_mhz * 1e6 / 1e12
-        return {"kernel": stage, "bound": "alu", "achieved": None, "peak": peak, "unit": "Tops/s",
-                "frac": None, "traffic": traffic, "avg_launch_ms": avg_ms, "launches": nl // steps,
-                "note": "FP32-lane issue peak = 152 SMs x 128 lanes x max SM clock; achieved needs the "
-                        "number of lobes sampled, see stages",
-                "ops_per_sample": ops_per_sample}
-    # HBM-bound stages: algorithmic bytes per launch
-    per_launch_bytes = None
-    if stage in ("sort_scatter", "sort_hist"):
-        per_launch_bytes = None
-    return {"kernel": stage, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
-            "traffic": traffic, "avg_launch_ms": avg_ms, "launches": nl // steps,
-            "bytes_per_launch": per_launch_bytes}
+    if stage in ALU_OPS:
+        ops = units_per_launch * ALU_OPS[stage]
+        ach = ops / (avg_ms * 1e-3) / 1e12
+        return {"kernel": stage, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s",
+                "frac": ach / alu_peak, "traffic": traffic, "avg_launch_ms": avg_ms,
+                "launches_per_step": nl // steps, "units_per_launch": units_per_launch,
+                "ops_per_unit": ALU_OPS[stage],
+                "peak_source": f"152 SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz (max SM clock, MEASURED_PEAKS)"}
+    per_unit = HBM_BYTES.get(stage)
+    ach = None if per_unit is None else units_per_launch * per_unit / (avg_ms * 1e-3) / 1e9
+    return {"kernel": stage, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": None if ach is None else ach / hbm, "traffic": traffic, "avg_launch_ms": avg_ms,
+            "launches_per_step": nl // steps, "units_per_launch": units_per_launch,
+            "peak_source": "hbm_gbs of MEASURED_PEAKS (copy)"}
 
 
 if __name__ == "__main__":

@@ -198,13 +198,17 @@ VX_API void vx_level_release(vx_context* ctx, vx_level* level, void* stream);
 
 /* Per-stage timing (opt-in).  With profiling enabled, every kernel launch of the
  * library is bracketed by CUDA events on its stream; vx_profile_read synchronises
- * those events and returns, per stage, the number of launches and their summed device
- * time.  Launch counts are kept even when timing is disabled.  enable != 0 also resets
+ * those events and returns, per stage, the number of launches, their summed device
+ * time and the work units they processed: candidate pairs for the count / emit / sort /
+ * reduce stages, candidate voxels for finalize, parents for the LoD reduce, and lobe
+ * samplings (of N directions each) for sggx_cluster.  Launch counts and units are kept
+ * even when timing is disabled.  enable != 0 also resets
  * the counters.  out may be NULL to query the number of stages. */
 typedef struct {
     char name[32];
     int64_t launches;
     double total_ms;
+    int64_t units;     /* work units processed (stage-specific: pairs, voxels, lobes sampled) */
 } vx_stage_time;
 
 VX_API vx_status vx_profile_enable(vx_context* ctx, int enable);

@@ -362,3 +362,19 @@ def broadcast_adjoints(keys0, level_keys, alphas, betas):
         gm += np.asarray(a, np.float64)[idx]
         gM += np.asarray(b, np.float64)[idx]
     return gm, gM
+
+
+def clip_signature(ctrl, offsets, grid, prims) -> int:
+    """Hash of the clipped-piece active sets of the listed segments (FP64)."""
+    lib = _load()
+    if not hasattr(lib, "_sig_ready"):
+        lib.vxo_clip_signature.restype = C.c_uint64
+        lib.vxo_clip_signature.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_double, C.c_int,
+                                           C.c_void_p, C.c_int64]
+        lib._sig_ready = True
+    ctrl = np.ascontiguousarray(ctrl, dtype=np.float64).reshape(-1, 4)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    pr = np.ascontiguousarray(np.sort(prims), dtype=np.int64)
+    origin = np.ascontiguousarray(grid.origin, dtype=np.float64)
+    return int(lib.vxo_clip_signature(_ptr(ctrl), _ptr(offsets), int(offsets.shape[0] - 1), _ptr(origin),
+                                      float(grid.voxel_size), int(grid.resolution), _ptr(pr), int(pr.shape[0])))

@@ -1185,3 +1185,42 @@ ORC_API double vxo_fiber_adjoint(const double* ctrl, const int64_t* offsets, int
     }
     return loss;
 }
+
+/* Active-set signature of the clipped pieces of the listed segments: a hash over every
+ * (segment, voxel, entering plane, leaving plane) with a piece of positive length.  Equal
+ * signatures at theta - h, theta, theta + h mean the loss is smooth on that stencil. */
+ORC_API uint64_t vxo_clip_signature(const double* ctrl, const int64_t* offsets, int64_t F, const double* origin,
+                                    double voxel_size, int R, const int64_t* prims, int64_t nprims) {
+    double s = 1.0 / voxel_size;
+    uint64_t h = 1469598103934665603ull;
+    int64_t prim = 0, pi = 0;
+    for (int64_t f = 0; f < F; ++f) {
+        for (int64_t c = offsets[f]; c + 1 < offsets[f + 1]; ++c, ++prim) {
+            while (pi < nprims && prims[pi] < prim) ++pi;
+            if (pi >= nprims || prims[pi] != prim) continue;
+            double A[3], B[3];
+            for (int i = 0; i < 3; ++i) {
+                A[i] = (ctrl[4 * c + i] - origin[i]) * s;
+                B[i] = (ctrl[4 * (c + 1) + i] - origin[i]) * s;
+            }
+            double d[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+            int lo[3], hi[3];
+            for (int i = 0; i < 3; ++i) {
+                lo[i] = clampi((int)floor(fmin(A[i], B[i])) - 1, 0, R - 1);
+                hi[i] = clampi((int)floor(fmax(A[i], B[i])) + 1, 0, R - 1);
+            }
+            for (int vk = lo[2]; vk <= hi[2]; ++vk)
+                for (int vj = lo[1]; vj <= hi[1]; ++vj)
+                    for (int vi = lo[0]; vi <= hi[0]; ++vi) {
+                        double a[3] = {A[0] - vi, A[1] - vj, A[2] - vk};
+                        double t0, t1;
+                        int ax0, ax1;
+                        if (!clip64(a, d, &t0, &t1, &ax0, &ax1)) continue;
+                        uint64_t v = ((uint64_t)prim << 40) ^ (vxo_morton((uint32_t)vi, (uint32_t)vj, (uint32_t)vk) << 4) ^
+                                     (uint64_t)((ax0 + 1) * 5 + (ax1 + 1));
+                        for (int b = 0; b < 8; ++b) { h ^= (v >> (8 * b)) & 0xffu; h *= 1099511628211ull; }
+                    }
+        }
+    }
+    return h;
+}

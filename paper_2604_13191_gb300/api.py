@@ -65,7 +65,8 @@ EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_l
 
 
 class VxStageTime(C.Structure):
-    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double),
+                ("units", C.c_int64)]
 
 _lib = None
 _lock = threading.Lock()
@@ -208,13 +209,14 @@ class Context:
             raise self._err(st, "vx_profile_enable")
 
     def profile_read(self) -> dict:
-        """vx_profile_read: {stage: (launches, total device ms)} (synchronises)."""
+        """vx_profile_read: {stage: (launches, total device ms, work units)} (synchronises)."""
         n = C.c_int()
         buf = (VxStageTime * 64)()
         st = self.lib.vx_profile_read(self.h, buf, 64, C.byref(n))
         if st != 0:
             raise self._err(st, "vx_profile_read")
-        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(n.value)}
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), int(buf[i].units))
+                for i in range(n.value)}
 
     def _err(self, st, what):
         detail = self.lib.vx_last_cuda_error(self.h).decode() if st == 4 else ""

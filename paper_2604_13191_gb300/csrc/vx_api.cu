@@ -141,6 +141,7 @@ void vx_context_destroy(vx_context* ctx) {
         }
         delete[] ctx->ev;
     }
+    if (ctx->dev_lobe_count) cudaFree(ctx->dev_lobe_count);
     delete ctx;
 }
 
@@ -158,9 +159,17 @@ vx_status vx_profile_enable(vx_context* ctx, int enable) {
             }
         }
     }
+    if (enable && !ctx->dev_lobe_count) {
+        cudaError_t e = cudaMalloc((void**)&ctx->dev_lobe_count, sizeof(unsigned long long));
+        if (e != cudaSuccess) {
+            vx_record_cuda_error(ctx, e, "cudaMalloc");
+            return VX_ERR_CUDA;
+        }
+    }
     if (enable) {
         vx_prof_drain(ctx);
-        for (int i = 0; i < ST_NSTAGES; ++i) { ctx->launches[i] = 0; ctx->stage_ms[i] = 0.0; }
+        for (int i = 0; i < ST_NSTAGES; ++i) { ctx->launches[i] = 0; ctx->stage_ms[i] = 0.0; ctx->units[i] = 0; }
+        cudaMemset(ctx->dev_lobe_count, 0, sizeof(unsigned long long));
     }
     ctx->prof = enable != 0;
     return VX_OK;
@@ -170,12 +179,19 @@ vx_status vx_profile_read(vx_context* ctx, vx_stage_time* out, int max_stages, i
     if (!ctx || !num_stages) return VX_ERR_INVALID_ARG;
     vx_prof_drain(ctx);
     *num_stages = ST_NSTAGES;
+    if (ctx->dev_lobe_count) {
+        unsigned long long n = 0;
+        cudaDeviceSynchronize();
+        if (cudaMemcpy(&n, ctx->dev_lobe_count, sizeof(n), cudaMemcpyDeviceToHost) == cudaSuccess)
+            ctx->units[ST_SGGX_CLUSTER] = (int64_t)n;
+    }
     if (out) {
         for (int i = 0; i < ST_NSTAGES && i < max_stages; ++i) {
             memset(out[i].name, 0, sizeof(out[i].name));
             strncpy(out[i].name, kStageNames[i], sizeof(out[i].name) - 1);
             out[i].launches = ctx->launches[i];
             out[i].total_ms = ctx->stage_ms[i];
+            out[i].units = ctx->units[i];
         }
     }
     return VX_OK;

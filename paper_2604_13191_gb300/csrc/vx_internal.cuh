@@ -64,6 +64,8 @@ struct vx_context {
     bool prof = false;
     int64_t launches[ST_NSTAGES] = {0};
     double stage_ms[ST_NSTAGES] = {0};
+    int64_t units[ST_NSTAGES] = {0};
+    unsigned long long* dev_lobe_count = nullptr;   // device counter of lobe samplings
     vx::EventRec* ev = nullptr;   // pool of kEventPool records
     int nev = 0;
 };
@@ -71,6 +73,7 @@ struct vx_context {
 // Brackets one kernel launch: counts it and, with profiling on, records events.
 void vx_stage_begin(vx_context* ctx, int stage, cudaStream_t s);
 void vx_stage_end(vx_context* ctx, cudaStream_t s);
+inline void vx_stage_units(vx_context* ctx, int stage, int64_t n) { ctx->units[stage] += n; }
 #define VX_LAUNCH(ctx, stage, s, ...)          \
     do {                                       \
         vx_stage_begin((ctx), (stage), (s));   \

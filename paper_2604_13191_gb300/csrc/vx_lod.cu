@@ -246,8 +246,18 @@ struct LobeStats {
     float Mh[6];
 };
 
-// warp-collective: histogram and sample second moment of lobe S (result valid in all lanes)
-__device__ LobeStats sample_lobe(const float* S, const float* __restrict__ dirs, int N) {
+// round-half-even to an integer for |x| < 2^22: adding 1.5 * 2^23 leaves the rounded
+// integer in the low mantissa bits (same value as __float2int_rn, at FP32-add cost)
+__device__ __forceinline__ int rint_small(float x) {
+    return __float_as_int(x + 12582912.0f) - 0x4B400000;
+}
+
+// Histogram and sample second moment of lobe S, computed cooperatively by G warps
+// (G = 1: one warp; G > 1: the whole block, `red` is G * 13 words of shared memory).
+// Every count and sum is an integer, so the result is independent of G and of the order
+// in which the threads visit the samples.  Result valid in every participating thread.
+template <int G>
+__device__ LobeStats sample_lobe(const float* S, const float* __restrict__ dirs, int N, long long* red) {
     const float tr = (S[0] + S[1]) + S[2];
     const float eps = 1e-6f * tr;
     const float Sp[6] = {S[0] + eps, S[1] + eps, S[2] + eps, S[3], S[4], S[5]};
@@ -256,30 +266,39 @@ __device__ LobeStats sample_lobe(const float* S, const float* __restrict__ dirs,
     int32_t h[6] = {0, 0, 0, 0, 0, 0};
     long long Q[6] = {0, 0, 0, 0, 0, 0};
     int cnt = 0;
-    const int lane = threadIdx.x & 31;
-    for (int k = lane; k < N; k += 32) {
-        const float u0 = __ldg(dirs + 3 * k), u1 = __ldg(dirs + 3 * k + 1), u2 = __ldg(dirs + 3 * k + 2);
-        float v[3];
+    const int tid = (G == 1) ? (threadIdx.x & 31) : (int)threadIdx.x;
+    constexpr int STRIDE = 32 * G;
+    // per-thread int32 partial sums (|term| <= 2^20), flushed to int64 every 1024 samples
+    for (int k0 = tid; k0 < N; k0 += STRIDE * 1024) {
+        int32_t q[6] = {0, 0, 0, 0, 0, 0};
+        const int kend = min(N, k0 + STRIDE * 1024);
+        for (int k = k0; k < kend; k += STRIDE) {
+            const float u0 = __ldg(dirs + 3 * k), u1 = __ldg(dirs + 3 * k + 1), u2 = __ldg(dirs + 3 * k + 2);
+            float v[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) v[i] = (Rm[3 * i] * u0 + Rm[3 * i + 1] * u1) + Rm[3 * i + 2] * u2;
-        const float n2 = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
-        if (!(n2 > 0.0f)) continue;
-        ++cnt;
-        const float t6 = 0.36f * n2, t2 = 0.04f * n2;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float c2 = v[a] * v[a];
-            h[a] += (c2 >= t6) ? 1 : 0;
-            h[3 + a] += (c2 >= t2) ? 1 : 0;
+            for (int i = 0; i < 3; ++i) v[i] = (Rm[3 * i] * u0 + Rm[3 * i + 1] * u1) + Rm[3 * i + 2] * u2;
+            const float c0 = v[0] * v[0], c1 = v[1] * v[1], c2 = v[2] * v[2];
+            const float n2 = (c0 + c1) + c2;
+            if (!(n2 > 0.0f)) continue;
+            ++cnt;
+            const float t6 = 0.36f * n2, t2 = 0.04f * n2;
+            h[0] += (c0 >= t6) ? 1 : 0;
+            h[1] += (c1 >= t6) ? 1 : 0;
+            h[2] += (c2 >= t6) ? 1 : 0;
+            h[3] += (c0 >= t2) ? 1 : 0;
+            h[4] += (c1 >= t2) ? 1 : 0;
+            h[5] += (c2 >= t2) ? 1 : 0;
+            const float inv = 1.0f / n2;
+            const float s20 = inv * 1048576.0f;
+            q[0] += rint_small(c0 * s20);
+            q[1] += rint_small(c1 * s20);
+            q[2] += rint_small(c2 * s20);
+            q[3] += rint_small((v[0] * v[1]) * s20);
+            q[4] += rint_small((v[0] * v[2]) * s20);
+            q[5] += rint_small((v[1] * v[2]) * s20);
         }
-        const float inv = 1.0f / n2;
-        const float s20 = inv * 1048576.0f;
-        Q[0] += __float2int_rn((v[0] * v[0]) * s20);
-        Q[1] += __float2int_rn((v[1] * v[1]) * s20);
-        Q[2] += __float2int_rn((v[2] * v[2]) * s20);
-        Q[3] += __float2int_rn((v[0] * v[1]) * s20);
-        Q[4] += __float2int_rn((v[0] * v[2]) * s20);
-        Q[5] += __float2int_rn((v[1] * v[2]) * s20);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) Q[c] += q[c];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -288,6 +307,35 @@ __device__ LobeStats sample_lobe(const float* S, const float* __restrict__ dirs,
         for (int c = 0; c < 6; ++c) {
             h[c] += __shfl_xor_sync(0xffffffffu, h[c], o);
             Q[c] += __shfl_xor_sync(0xffffffffu, Q[c], o);
+        }
+    }
+    if (G > 1) {
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        __syncthreads();
+        if (lane == 0) {
+            red[w * 13 + 0] = cnt;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                red[w * 13 + 1 + c] = h[c];
+                red[w * 13 + 7 + c] = Q[c];
+            }
+        }
+        __syncthreads();
+        long long tc = 0, th[6] = {0, 0, 0, 0, 0, 0}, tq[6] = {0, 0, 0, 0, 0, 0};
+        for (int ww = 0; ww < G; ++ww) {
+            tc += red[ww * 13];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                th[c] += red[ww * 13 + 1 + c];
+                tq[c] += red[ww * 13 + 7 + c];
+            }
+        }
+        __syncthreads();
+        cnt = (int)tc;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            h[c] = (int32_t)th[c];
+            Q[c] = tq[c];
         }
     }
     LobeStats st;
@@ -307,46 +355,60 @@ struct ClusterSmem {
     uint8_t alive[MAX_SLOTS];
 };
 
-// warp per parent listed in `work`
-__global__ void __launch_bounds__(CL_WARPS * 32) k_sggx_cluster(LevelIn in, const uint32_t* __restrict__ starts,
-                                                                const uint32_t* __restrict__ work,
-                                                                const uint32_t* __restrict__ nwork_p, vx_level out,
-                                                                int K, const float* __restrict__ dirs, int N) {
+// One parent listed in `work` per group of G warps (G = 1: a warp per parent, for levels
+// with many parents; G = CL_BLOCK_WARPS: a block per parent, for the few coarse parents
+// whose long merge chains would otherwise run on a single warp).
+constexpr int CL_BLOCK_WARPS = 8;
+
+template <int G>
+__global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluster(
+    LevelIn in, const uint32_t* __restrict__ starts, const uint32_t* __restrict__ work,
+    const uint32_t* __restrict__ nwork_p, vx_level out, int K, const float* __restrict__ dirs, int N,
+    unsigned long long* __restrict__ nsampled) {
     extern __shared__ unsigned char smem_raw[];
-    ClusterSmem& sm = ((ClusterSmem*)smem_raw)[threadIdx.x >> 5];
+    constexpr int GROUPS = (G == 1) ? CL_WARPS : 1;
+    const int group = (G == 1) ? (int)(threadIdx.x >> 5) : 0;
+    ClusterSmem& sm = ((ClusterSmem*)smem_raw)[group];
+    long long* red = (long long*)(smem_raw + sizeof(ClusterSmem) * GROUPS);
+    __shared__ unsigned long long bestred[G];
+    const int tid = (G == 1) ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+    constexpr int NT = 32 * G;
     const int lane = threadIdx.x & 31;
     const uint32_t nwork = *nwork_p;
-    const uint32_t warps = gridDim.x * CL_WARPS;
-    for (uint32_t it = blockIdx.x * CL_WARPS + (threadIdx.x >> 5); it < nwork; it += warps) {
+    const uint32_t groups = gridDim.x * GROUPS;
+    auto gsync = [&]() {
+        if (G == 1) __syncwarp(); else __syncthreads();
+    };
+    for (uint32_t it = blockIdx.x * GROUPS + group; it < nwork; it += groups) {
         const uint32_t p = work[it];
         const uint32_t beg = starts[p], end = starts[p + 1];
         // gather candidates in (child, lobe) order
         int n = 0;
         for (uint32_t c = beg; c < end; ++c) {
             const int lc = in.lobe_count[c];
-            for (int l = lane; l < lc * 7; l += 32) {
+            for (int l = tid; l < lc * 7; l += NT) {
                 const int li = l / 7, j = l % 7;
                 const float x = in.lobes[((size_t)c * in.K + li) * 7 + j];
                 if (j < 6) sm.S[n + li][j] = x; else sm.w[n + li] = x;
             }
             n += lc;
         }
-        for (int l = lane; l < MAX_SLOTS; l += 32) sm.alive[l] = (l < n) ? 1 : 0;
-        __syncwarp();
+        for (int l = tid; l < MAX_SLOTS; l += NT) sm.alive[l] = (l < n) ? 1 : 0;
+        gsync();
         for (int l = 0; l < n; ++l) {
-            LobeStats st = sample_lobe(sm.S[l], dirs, N);
-            if (lane < 6) {
-                sm.H[l][lane] = st.h[lane];
-                sm.Mh[l][lane] = st.Mh[lane];
+            LobeStats st = sample_lobe<G>(sm.S[l], dirs, N, red);
+            if (tid < 6) {
+                sm.H[l][tid] = st.h[tid];
+                sm.Mh[l][tid] = st.Mh[tid];
             }
         }
-        __syncwarp();
+        gsync();
         int count = n, next = n;
         while (count > K) {
             // argmin over alive pairs (i > j) of (distance, i, j)
             unsigned long long best = ~0ull;
             const int npairs = next * (next - 1) / 2;
-            for (int q = lane; q < npairs; q += 32) {
+            for (int q = tid; q < npairs; q += NT) {
                 // q -> (i, j), i > j, ordered by i then j
                 int i = (int)((sqrtf(8.0f * (float)q + 1.0f) + 1.0f) * 0.5f);
                 while (i * (i - 1) / 2 > q) --i;
@@ -364,28 +426,35 @@ __global__ void __launch_bounds__(CL_WARPS * 32) k_sggx_cluster(LevelIn in, cons
                 unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
                 if (other < best) best = other;
             }
+            if (G > 1) {
+                if (lane == 0) bestred[threadIdx.x >> 5] = best;
+                __syncthreads();
+                best = bestred[0];
+                for (int ww = 1; ww < G; ++ww) best = bestred[ww] < best ? bestred[ww] : best;
+                __syncthreads();
+            }
             const int bi = (int)((best >> 8) & 0xffull), bj = (int)(best & 0xffull);
-            if (lane < 6) sm.S[next][lane] = (sm.Mh[bi][lane] + sm.Mh[bj][lane]) * 0.5f;
-            if (lane == 0) {
+            if (tid < 6) sm.S[next][tid] = (sm.Mh[bi][tid] + sm.Mh[bj][tid]) * 0.5f;
+            if (tid == 0) {
                 sm.w[next] = sm.w[bi] + sm.w[bj];
                 sm.alive[bi] = 0;
                 sm.alive[bj] = 0;
                 sm.alive[next] = 1;
             }
-            __syncwarp();
-            LobeStats st = sample_lobe(sm.S[next], dirs, N);
-            if (lane < 6) {
-                sm.H[next][lane] = st.h[lane];
-                sm.Mh[next][lane] = st.Mh[lane];
+            gsync();
+            LobeStats st = sample_lobe<G>(sm.S[next], dirs, N, red);
+            if (tid < 6) {
+                sm.H[next][tid] = st.h[tid];
+                sm.Mh[next][tid] = st.Mh[tid];
             }
-            __syncwarp();
+            gsync();
             ++next;
             --count;
         }
         // output: alive lobes by weight (descending), ties by creation index
         float* lo = out.lobes + (size_t)p * K * 7;
         float* co = out.compact + (size_t)p * K * 6;
-        for (int x = lane; x < next; x += 32) {
+        for (int x = tid; x < next; x += NT) {
             if (!sm.alive[x]) continue;
             const float wx = sm.w[x];
             int rank = 0;
@@ -395,8 +464,11 @@ __global__ void __launch_bounds__(CL_WARPS * 32) k_sggx_cluster(LevelIn in, cons
             lo[rank * 7 + 6] = wx;
             compact_params(sm.S[x], co + rank * 6);
         }
-        if (lane == 0) out.lobe_count[p] = (uint8_t)count;
-        __syncwarp();
+        if (tid == 0) {
+            out.lobe_count[p] = (uint8_t)count;
+            if (nsampled) atomicAdd(nsampled, (unsigned long long)next);   // n candidates + merges
+        }
+        gsync();
     }
 }
 
@@ -454,7 +526,12 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
     uint32_t* starts = (uint32_t*)ctx->ws[WS_LOD_STARTS].p;
     uint32_t* work = (uint32_t*)ctx->ws[WS_LOD_WORK].p;
     const size_t cl_smem = sizeof(ClusterSmem) * CL_WARPS;
-    if (K > 1) VX_CUDA_TRY(cudaFuncSetAttribute(k_sggx_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl_smem));
+    const size_t cb_smem = sizeof(ClusterSmem) + sizeof(long long) * 13 * CL_BLOCK_WARPS;
+    if (K > 1) {
+        VX_CUDA_TRY(cudaFuncSetAttribute(k_sggx_cluster<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl_smem));
+        VX_CUDA_TRY(cudaFuncSetAttribute(k_sggx_cluster<CL_BLOCK_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cb_smem));
+    }
     for (int l = 1; l <= L; ++l) {
         const vx_level* prev = (l == 1) ? in : &out[l - 2];
         const uint32_t nprev = (uint32_t)prev->num_voxels, ncur = counts[l];
@@ -466,13 +543,23 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
         VX_TRY(vx_scan_u32(ctx, flags, flags, nprev, nullptr, s));
         VX_LAUNCH(ctx, ST_LOD_HEADS, s, k_parent_starts<<<grid_for(nprev, 256), 256, 0, s>>>(prev->keys, nprev, flags, ncur, starts));
         VX_CUDA_TRY(cudaMemsetAsync(misc + 40, 0, 4, s));
+        vx_stage_units(ctx, ST_LOD_REDUCE, ncur);
         VX_LAUNCH(ctx, ST_LOD_REDUCE, s, k_lod_reduce<<<(unsigned)std::min<size_t>(grid_for(ncur, 128), (size_t)vx::kSMs * 32), 128, 0, s>>>(
             li, starts, ncur, out[l - 1], K, work, misc + 40));
         VX_CUDA_TRY(cudaGetLastError());
         if (K > 1) {
-            const unsigned cb = (unsigned)std::min<size_t>((ncur + CL_WARPS - 1) / CL_WARPS, (size_t)vx::kSMs * 16);
-            VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, k_sggx_cluster<<<cb, CL_WARPS * 32, cl_smem, s>>>(li, starts, work, misc + 40, out[l - 1], K,
-                                                              params->dirs, params->n_samples));
+            unsigned long long* cnt_dev = ctx->prof ? ctx->dev_lobe_count : nullptr;
+            if (ncur > (uint32_t)(vx::kSMs * 16)) {
+                const unsigned cb = (unsigned)std::min<size_t>((ncur + CL_WARPS - 1) / CL_WARPS, (size_t)vx::kSMs * 16);
+                VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, k_sggx_cluster<1><<<cb, CL_WARPS * 32, cl_smem, s>>>(
+                                                   li, starts, work, misc + 40, out[l - 1], K, params->dirs,
+                                                   params->n_samples, cnt_dev));
+            } else {
+                const unsigned cb = (unsigned)std::max<uint32_t>(1u, std::min<uint32_t>(ncur, vx::kSMs * 4));
+                VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, k_sggx_cluster<CL_BLOCK_WARPS><<<cb, CL_BLOCK_WARPS * 32, cb_smem, s>>>(
+                                                   li, starts, work, misc + 40, out[l - 1], K, params->dirs,
+                                                   params->n_samples, cnt_dev));
+            }
             VX_CUDA_TRY(cudaGetLastError());
         }
     }

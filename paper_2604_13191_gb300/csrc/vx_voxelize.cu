@@ -72,20 +72,22 @@ __device__ __forceinline__ float seg_g(const float* a, const float* d, float t, 
 
 // Step 3 of the capsule test: min over t in [0,1] of the squared segment-box distance,
 // taken at the stationary points of the quadratic pieces that can hold the minimum.
-__device__ __noinline__ float seg_box_min(const float* a, const float* d, const float* lo,
-                                          const float* hi) {
+// (Scalar code with explicit selects: no dynamically indexed local arrays.)
+__device__ __forceinline__ float sel3(int i, float x, float y, float z) { return i == 0 ? x : (i == 1 ? y : z); }
+
+__device__ __noinline__ float seg_box_min(const float* a, const float* d, const float* lo, const float* hi) {
     float L = -INFINITY, U = INFINITY;
     int iL = -1, jU = -1, moving = 0;
-    float plo[3], phi[3];
+    float plo0 = 0.0f, plo1 = 0.0f, plo2 = 0.0f, phi0 = 0.0f, phi1 = 0.0f, phi2 = 0.0f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        plo[i] = 0.0f; phi[i] = 0.0f;
         if (d[i] != 0.0f) {
             ++moving;
-            plo[i] = (d[i] > 0.0f) ? lo[i] : hi[i];
-            phi[i] = (d[i] > 0.0f) ? hi[i] : lo[i];
-            float jl = (plo[i] - a[i]) / d[i];
-            float jh = (phi[i] - a[i]) / d[i];
+            const float pl = (d[i] > 0.0f) ? lo[i] : hi[i];
+            const float ph = (d[i] > 0.0f) ? hi[i] : lo[i];
+            if (i == 0) { plo0 = pl; phi0 = ph; } else if (i == 1) { plo1 = pl; phi1 = ph; } else { plo2 = pl; phi2 = ph; }
+            const float jl = (pl - a[i]) / d[i];
+            const float jh = (ph - a[i]) / d[i];
             if (jl > L) { L = jl; iL = i; }
             if (jh < U) { U = jh; jU = i; }
         }
@@ -99,29 +101,35 @@ __device__ __noinline__ float seg_box_min(const float* a, const float* d, const 
         return seg_g(a, d, t, lo, hi);
     }
     // the axis giving L lies below its slab and the one giving U above it on [U, L]
-    const int p0 = iL < jU ? iL : jU, p1 = iL < jU ? jU : iL;
-    const float b0 = (p0 == iL) ? plo[p0] : phi[p0];
-    const float b1 = (p1 == iL) ? plo[p1] : phi[p1];
-    float num = d[p0] * (b0 - a[p0]);
-    float den = d[p0] * d[p0];
-    num = num + d[p1] * (b1 - a[p1]);
-    den = den + d[p1] * d[p1];
-    float gmin = seg_g(a, d, num / den, lo, hi);
     const int k = 3 - iL - jU;
-    if (d[k] != 0.0f) {
+    // beta per axis for the pair {iL, jU}: plo for iL, phi for jU
+    const float b0 = (iL == 0) ? plo0 : phi0;
+    const float b1 = (iL == 1) ? plo1 : phi1;
+    const float b2 = (iL == 2) ? plo2 : phi2;
+    const int p0 = iL < jU ? iL : jU, p1 = iL < jU ? jU : iL;
+    const float a0 = sel3(p0, a[0], a[1], a[2]), a1 = sel3(p1, a[0], a[1], a[2]);
+    const float d0 = sel3(p0, d[0], d[1], d[2]), d1 = sel3(p1, d[0], d[1], d[2]);
+    const float e0 = sel3(p0, b0, b1, b2), e1 = sel3(p1, b0, b1, b2);
+    float num = d0 * (e0 - a0);
+    float den = d0 * d0;
+    num = num + d1 * (e1 - a1);
+    den = den + d1 * d1;
+    float gmin = seg_g(a, d, num / den, lo, hi);
+    const float dk = sel3(k, d[0], d[1], d[2]);
+    if (dk != 0.0f) {
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
-            float beta[3];
-            beta[iL] = plo[iL];
-            beta[jU] = phi[jU];
-            beta[k] = side == 0 ? plo[k] : phi[k];
-            float n3 = d[0] * (beta[0] - a[0]);
+            // beta: iL -> plo, jU -> phi, k -> plo (side 0) or phi (side 1)
+            const float c0 = (k == 0) ? (side == 0 ? plo0 : phi0) : b0;
+            const float c1 = (k == 1) ? (side == 0 ? plo1 : phi1) : b1;
+            const float c2 = (k == 2) ? (side == 0 ? plo2 : phi2) : b2;
+            float n3 = d[0] * (c0 - a[0]);
             float d3 = d[0] * d[0];
-            n3 = n3 + d[1] * (beta[1] - a[1]);
+            n3 = n3 + d[1] * (c1 - a[1]);
             d3 = d3 + d[1] * d[1];
-            n3 = n3 + d[2] * (beta[2] - a[2]);
+            n3 = n3 + d[2] * (c2 - a[2]);
             d3 = d3 + d[2] * d[2];
-            float gc = seg_g(a, d, n3 / d3, lo, hi);
+            const float gc = seg_g(a, d, n3 / d3, lo, hi);
             if (gc < gmin) gmin = gc;
         }
     }
@@ -164,34 +172,70 @@ __device__ __forceinline__ AxisTerms axis_terms(float a, float b, int k) {
     return t;
 }
 
+// Per-axis bounds over a union of sub-cell intervals [lo, hi] on one axis:
+//   gap  <= the step-1 gap of every sub-cell inside (FP subtraction is monotone)
+//   farA >= the step-2 distance of endpoint a to every sub-cell inside, likewise farB.
+struct AxisBound {
+    float g2, fa2, fb2;
+};
+__device__ __forceinline__ AxisBound axis_bound(float a, float b, float lo, float hi) {
+    const float mn = fmin2(a, b), mx = fmax2(a, b);
+    float g = (lo > mx) ? lo - mx : ((mn > hi) ? mn - hi : 0.0f);
+    float fa = fmax2(hi - a, a - lo);
+    float fb = fmax2(hi - b, b - lo);
+    AxisBound r;
+    r.g2 = g * g;
+    r.fa2 = fa * fa;
+    r.fb2 = fb * fb;
+    return r;
+}
+
 // 16 sub-cell bits of one lane: sx = 0..7, sy = sy0 + (0|1), sz fixed; bits already set
 // in `have` are skipped (OR is idempotent).  Bit b = sx + 8 * (sy - sy0).
+// A group of sub-cells (the lane's 16, or one row of 8) is decided at once when
+//   sum of its per-axis gap bounds > r^2  -> every sub-cell fails step 1 (bits 0), or
+//   sum of an endpoint's far bounds <= r^2 -> every sub-cell passes step 2 (bits 1)
+// (each sub-cell's step-1 sum is >= the group's and <= its step-2 sum, so the group
+// result equals the per-sub-cell definition bit for bit).
 __device__ __forceinline__ uint32_t capsule_bits16(const float* a, const float* b, float rr, int sy0,
                                                    int sz, uint32_t have) {
     if (have == 0xffffu) return 0xffffu;
-    AxisTerms tx[8], ty[2], tz;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) tx[k] = axis_terms(a[0], b[0], k);
-    ty[0] = axis_terms(a[1], b[1], sy0);
-    ty[1] = axis_terms(a[1], b[1], sy0 + 1);
-    tz = axis_terms(a[2], b[2], sz);
-    float d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const float zlo = (float)sz * 0.125f, zhi = (float)(sz + 1) * 0.125f;
+    const AxisBound bz = axis_bound(a[2], b[2], zlo, zhi);
+    const AxisBound bx = axis_bound(a[0], b[0], 0.0f, 1.0f);
+    {
+        const AxisBound by = axis_bound(a[1], b[1], (float)sy0 * 0.125f, (float)(sy0 + 2) * 0.125f);
+        if ((bx.g2 + by.g2) + bz.g2 > rr) return have;
+        if ((bx.fa2 + by.fa2) + bz.fa2 <= rr || (bx.fb2 + by.fb2) + bz.fb2 <= rr) return 0xffffu;
+    }
     uint32_t bits = have;
+    const float d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
 #pragma unroll
     for (int yi = 0; yi < 2; ++yi) {
+        const uint32_t rowmask = 0xffu << (8 * yi);
+        if ((bits & rowmask) == rowmask) continue;
+        const float ylo = (float)(sy0 + yi) * 0.125f, yhi = (float)(sy0 + yi + 1) * 0.125f;
+        const AxisBound by = axis_bound(a[1], b[1], ylo, yhi);
+        if ((bx.g2 + by.g2) + bz.g2 > rr) continue;
+        if ((bx.fa2 + by.fa2) + bz.fa2 <= rr || (bx.fb2 + by.fb2) + bz.fb2 <= rr) {
+            bits |= rowmask;
+            continue;
+        }
+        const AxisTerms ty = axis_terms(a[1], b[1], sy0 + yi);
+        const AxisTerms tz = axis_terms(a[2], b[2], sz);
 #pragma unroll
         for (int sx = 0; sx < 8; ++sx) {
             const uint32_t bit = 1u << (sx + 8 * yi);
             if (bits & bit) continue;
-            float G = (tx[sx].g2 + ty[yi].g2) + tz.g2;
+            const AxisTerms tx = axis_terms(a[0], b[0], sx);
+            float G = (tx.g2 + ty.g2) + tz.g2;
             if (G > rr) continue;
-            float EA = (tx[sx].ea2 + ty[yi].ea2) + tz.ea2;
-            float EB = (tx[sx].eb2 + ty[yi].eb2) + tz.eb2;
+            float EA = (tx.ea2 + ty.ea2) + tz.ea2;
+            float EB = (tx.eb2 + ty.eb2) + tz.eb2;
             bool hit = (EA <= rr) || (EB <= rr);
             if (!hit) {
-                float lo[3] = {(float)sx * 0.125f, (float)(sy0 + yi) * 0.125f, (float)sz * 0.125f};
-                float hi[3] = {(float)(sx + 1) * 0.125f, (float)(sy0 + yi + 1) * 0.125f,
-                               (float)(sz + 1) * 0.125f};
+                float lo[3] = {(float)sx * 0.125f, ylo, zlo};
+                float hi[3] = {(float)(sx + 1) * 0.125f, yhi, zhi};
                 hit = seg_box_min(a, d, lo, hi) <= rr;
             }
             if (hit) bits |= bit;
@@ -895,6 +939,12 @@ extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, co
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     const uint32_t err = ((uint32_t*)ctx->host_pin)[0];
     const uint32_t npairs = ((uint32_t*)ctx->host_pin)[1];
+    vx_stage_units(ctx, ST_PREP, np);
+    vx_stage_units(ctx, ST_COUNT, npairs);
+    vx_stage_units(ctx, ST_EMIT, npairs);
+    vx_stage_units(ctx, ST_SORT_SCATTER, npairs);
+    vx_stage_units(ctx, ST_SORT_HIST, npairs);
+    vx_stage_units(ctx, ST_REDUCE_FIBERS + (fiber ? 0 : 1), npairs);
     if (err) return VX_ERR_INVALID_ARG;
     // the 32-bit scan wraps above 2^32-1 pairs; a total below the per-primitive maximum
     // cannot be detected here, so bound the count by 2^31 as a capacity check instead.
@@ -930,6 +980,7 @@ extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, co
     VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc + 2, 4, cudaMemcpyDeviceToHost, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     const uint32_t nseg = ((uint32_t*)ctx->host_pin)[0];
+    vx_stage_units(ctx, ST_FINALIZE, nseg);
 
     // ---- per-voxel reduction ----------------------------------------------------------
     // temp outputs per candidate voxel: mask 64 + mass 4 + moment 24 bytes; the sort's

@@ -6,8 +6,12 @@ drawn per (level, key, component) by a counter-based generator, so both sides dr
 same weights from their own key sets.  Parameters: control-point xyz, radii, weights.
 Tolerance: |g32 - g64| <= 1e-4 * max(|g64|, median |g64|) (FP32 per-pair terms carry
 ~1e-6 relative error; a sum over tens of pairs with mixed signs stays well inside).
-FD: central, h = 1e-4 (world units), FP64; stencils whose clipped pieces change shape
-between -h and +h (FD at h and h/2 disagree) are reported and excluded.
+FD: central, FP64, h = 1e-4 in voxel units (the method's coordinates after the grid
+normalisation of Sec. 3.1; 1e-4 / 256 in world units here), on 64 random parameters whose
+stencil does not cross a kink (a clipped piece changing its entering or leaving plane
+between -h and +h, detected exactly from the oracle's active sets); skipped draws are
+counted and reported.  (A world-unit step of 1e-4 is 1/40 voxel: it rotates the 0.13-voxel
+segments of this yarn by ~0.2 rad, and the central difference's own h^2 error reaches ~0.5%.)
 """
 import numpy as np
 import pytest
@@ -85,9 +89,10 @@ def test_adjoint_finite_differences_yarn_256(ctx):
     off = w.fiber_offsets
     P = w.ctrl.shape[0]
     c64 = w.ctrl.astype(np.float64)
-    h = 1e-4
+    h = 1e-4 * w.grid.voxel_size
     checked, kinks, worst = 0, 0, 0.0
-    for _ in range(w.extra["n_params"]):
+    while checked < w.extra["n_params"]:
+        assert kinks < 10 * w.extra["n_params"], "too many stencils cross a kink"
         c = int(rng.integers(0, P))
         comp = int(rng.integers(0, 4))
         f = int(np.searchsorted(off, c, side="right") - 1)
@@ -97,6 +102,14 @@ def test_adjoint_finite_differences_yarn_256(ctx):
             prims.append(c - f - 1)
         if c + 1 < off[f + 1]:
             prims.append(c - f)
+        # exclude stencils on which a clipped piece changes its entering/leaving plane
+        sig = []
+        for step in (-h, 0.0, h):
+            cc = c64.copy(); cc[c, comp] += step
+            sig.append(oracle.clip_signature(cc, off, w.grid, prims))
+        if len(set(sig)) != 1:
+            kinks += 1
+            continue
         # occupied voxels near the affected segments (brute force over every primitive)
         s = 1.0 / w.grid.voxel_size
         pts = c64[max(c - 1, 0): c + 2, :3] * s
@@ -119,16 +132,12 @@ def test_adjoint_finite_differences_yarn_256(ctx):
             cp = c64.copy(); cp[c, comp] += step
             cm = c64.copy(); cm[c, comp] -= step
             return (local_loss(cp) - local_loss(cm)) / (2 * step)
-        f1, f2 = fd(h), fd(h / 2)
+        f1 = fd(h)
         _, d_ctrl, _ = oracle.fiber_adjoint(c64, off, w.grid, occ, gm0, gM0, prims=np.array(prims))
         ref = d_ctrl[c, comp]
-        if abs(f1 - f2) > 1e-5 * max(abs(f1), 1e-3):
-            kinks += 1
-            continue
         assert abs(ref - f1) <= 1e-4 * max(abs(f1), 1e-3), (c, comp, ref, f1)
         err = abs(g_ctrl[c, comp] - f1) / max(abs(f1), 1e-3)
         worst = max(worst, err)
         assert err <= 1e-4, (c, comp, g_ctrl[c, comp], f1)
         checked += 1
-    print(f"FD checked {checked}, kinks excluded {kinks}, worst rel {worst:.2e}")
-    assert checked >= 48
+    print(f"FD checked {checked}, stencils across a kink skipped {kinks}, worst rel {worst:.2e}")
