@@ -322,14 +322,16 @@ def level_from_voxels(keys, vox: dict) -> dict:
     return d
 
 
-def fiber_adjoint(ctrl, offsets, grid, keys0, gm0, gM0, weights=None, prims=None):
+def fiber_adjoint(ctrl, offsets, grid, keys0, gm0, gM0, weights=None, prims=None, with_abs=False):
     """FP64 loss sum gm*m + gM.M over level-0 voxels and its gradient w.r.t. ctrl
-    ([P,4]: xyz and radius, world units) and the per-segment weights."""
+    ([P,4]: xyz and radius, world units) and the per-segment weights.  With with_abs,
+    also the summed magnitudes of each control-point gradient's per-pair terms."""
     lib = _load()
     if not hasattr(lib, "_adj_ready"):
         lib.vxo_fiber_adjoint.restype = C.c_double
         lib.vxo_fiber_adjoint.argtypes = [C.c_void_p] * 4 + [C.c_void_p, C.c_double, C.c_int] + \
-            [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+            [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+             C.c_void_p]
         lib.vxo_fiber_adjoint.argtypes[2] = C.c_int64
         lib._adj_ready = True
     ctrl = np.ascontiguousarray(ctrl, dtype=np.float64).reshape(-1, 4)
@@ -343,10 +345,13 @@ def fiber_adjoint(ctrl, offsets, grid, keys0, gm0, gM0, weights=None, prims=None
     nseg = int(np.sum(np.maximum(offsets[1:] - offsets[:-1] - 1, 0)))
     d_ctrl = np.zeros_like(ctrl)
     d_w = np.zeros(nseg, dtype=np.float64)
+    d_abs = np.zeros_like(ctrl) if with_abs else None
     loss = lib.vxo_fiber_adjoint(_ptr(ctrl), _ptr(offsets), int(offsets.shape[0] - 1), _ptr(w), _ptr(origin),
                                  float(grid.voxel_size), int(grid.resolution), _ptr(keys0), int(keys0.shape[0]),
                                  _ptr(gm0), _ptr(gM0), _ptr(pr), 0 if pr is None else int(pr.shape[0]),
-                                 _ptr(d_ctrl), _ptr(d_w))
+                                 _ptr(d_ctrl), _ptr(d_w), _ptr(d_abs))
+    if with_abs:
+        return float(loss), d_ctrl, d_w, d_abs
     return float(loss), d_ctrl, d_w
 
 

@@ -1136,12 +1136,13 @@ static int64_t find_key(const uint64_t* keys, int64_t n, uint64_t k) {
 /* Gradients of the loss w.r.t. ctrl [P][4] (xyz world, radius world) and weights [N],
  * given the broadcast level-0 adjoints gm0 [V], gM0 [V][6] on the sorted keys0.
  * Only the primitives listed in prims (or all when prims == NULL) are visited;
- * returns the loss contribution of the visited primitives. */
+ * returns the loss contribution of the visited primitives.  d_abs (optional, [P][4])
+ * receives the summed magnitudes of the per-pair terms of each control-point gradient. */
 ORC_API double vxo_fiber_adjoint(const double* ctrl, const int64_t* offsets, int64_t F, const double* weights,
                                  const double* origin, double voxel_size, int R,
                                  const uint64_t* keys0, int64_t V, const double* gm0, const double* gM0,
                                  const int64_t* prims, int64_t nprims,
-                                 double* d_ctrl, double* d_w) {
+                                 double* d_ctrl, double* d_w, double* d_abs) {
     double s = 1.0 / voxel_size;
     double loss = 0.0;
     int64_t prim = 0;
@@ -1164,6 +1165,7 @@ ORC_API double vxo_fiber_adjoint(const double* ctrl, const int64_t* offsets, int
                 hi[i] = clampi((int)floor(fmax(A[i], B[i])) + 1, 0, R - 1);
             }
             double gA[3] = {0, 0, 0}, gB[3] = {0, 0, 0}, gr = 0, gw = 0;
+            double aA[3] = {0, 0, 0}, aB[3] = {0, 0, 0}, ar = 0;   /* summed |per-pair terms| */
             for (int vk = lo[2]; vk <= hi[2]; ++vk)
                 for (int vj = lo[1]; vj <= hi[1]; ++vj)
                     for (int vi = lo[0]; vi <= hi[0]; ++vi) {
@@ -1171,8 +1173,12 @@ ORC_API double vxo_fiber_adjoint(const double* ctrl, const int64_t* offsets, int
                         if (v < 0) continue;
                         double a3[3], b3[3], dr, dw;
                         loss += vxo_pair_grad64(A, B, r, w, vi, vj, vk, gm0[v], gM0 + 6 * v, a3, b3, &dr, &dw);
-                        for (int i = 0; i < 3; ++i) { gA[i] += a3[i]; gB[i] += b3[i]; }
+                        for (int i = 0; i < 3; ++i) {
+                            gA[i] += a3[i]; gB[i] += b3[i];
+                            aA[i] += fabs(a3[i]); aB[i] += fabs(b3[i]);
+                        }
                         gr += dr;
+                        ar += fabs(dr);
                         gw += dw;
                     }
             if (d_ctrl) {
@@ -1181,6 +1187,11 @@ ORC_API double vxo_fiber_adjoint(const double* ctrl, const int64_t* offsets, int
                 d_ctrl[4 * (c + 1) + 3] += gr * 0.5 * s;
             }
             if (d_w) d_w[prim] += gw;
+            if (d_abs) {
+                for (int i = 0; i < 3; ++i) { d_abs[4 * c + i] += aA[i] * s; d_abs[4 * (c + 1) + i] += aB[i] * s; }
+                d_abs[4 * c + 3] += ar * 0.5 * s;
+                d_abs[4 * (c + 1) + 3] += ar * 0.5 * s;
+            }
         }
     }
     return loss;

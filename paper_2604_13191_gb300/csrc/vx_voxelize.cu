@@ -190,57 +190,99 @@ __device__ __forceinline__ AxisBound axis_bound(float a, float b, float lo, floa
     return r;
 }
 
-// 16 sub-cell bits of one lane: sx = 0..7, sy = sy0 + (0|1), sz fixed; bits already set
-// in `have` are skipped (OR is idempotent).  Bit b = sx + 8 * (sy - sy0).
-// A group of sub-cells (the lane's 16, or one row of 8) is decided at once when
-//   sum of its per-axis gap bounds > r^2  -> every sub-cell fails step 1 (bits 0), or
-//   sum of an endpoint's far bounds <= r^2 -> every sub-cell passes step 2 (bits 1)
-// (each sub-cell's step-1 sum is >= the group's and <= its step-2 sum, so the group
-// result equals the per-sub-cell definition bit for bit).
+// Per-warp shared scratch of the capsule mask: the sub-cells still undecided after steps
+// 1-2 (a task list) and the step-3 results (a 512-bit map).
+struct CapsuleScratch {
+    uint16_t task[512];
+    uint32_t hit[16];
+};
+
+// Warp-collective: 16 sub-cell bits of each lane (sx = 0..7, sy = sy0 + (0|1), sz) for one
+// capsule; bits already set in `have` are skipped (OR is idempotent).  Bit b = sx + 8 (sy - sy0).
+// Steps 1-2 run per lane.  A group of sub-cells (the lane's 16, or one row of 8) is decided
+// at once when
+//   the sum of its per-axis gap bounds > r^2   -> every sub-cell fails step 1 (bits 0), or
+//   the sum of an endpoint's far bounds <= r^2 -> every sub-cell passes step 2 (bits 1)
+// (each sub-cell's step-1 sum is >= the group's and <= its step-2 sum, so the group result
+// equals the per-sub-cell definition bit for bit).  The sub-cells left for step 3 are
+// compacted over the warp and evaluated 32 at a time, so that the exact minimum (the
+// expensive, rare case) runs with all lanes busy.
 __device__ __forceinline__ uint32_t capsule_bits16(const float* a, const float* b, float rr, int sy0,
-                                                   int sz, uint32_t have) {
-    if (have == 0xffffu) return 0xffffu;
-    const float zlo = (float)sz * 0.125f, zhi = (float)(sz + 1) * 0.125f;
-    const AxisBound bz = axis_bound(a[2], b[2], zlo, zhi);
-    const AxisBound bx = axis_bound(a[0], b[0], 0.0f, 1.0f);
-    {
-        const AxisBound by = axis_bound(a[1], b[1], (float)sy0 * 0.125f, (float)(sy0 + 2) * 0.125f);
-        if ((bx.g2 + by.g2) + bz.g2 > rr) return have;
-        if ((bx.fa2 + by.fa2) + bz.fa2 <= rr || (bx.fb2 + by.fb2) + bz.fb2 <= rr) return 0xffffu;
-    }
-    uint32_t bits = have;
-    const float d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+                                                   int sz, uint32_t have, CapsuleScratch& cs) {
+    const int lane = threadIdx.x & 31;
+    uint32_t bits = have, und = 0;
+    if (have != 0xffffu) {
+        const float zlo = (float)sz * 0.125f, zhi = (float)(sz + 1) * 0.125f;
+        const AxisBound bz = axis_bound(a[2], b[2], zlo, zhi);
+        const AxisBound bx = axis_bound(a[0], b[0], 0.0f, 1.0f);
+        const AxisBound bb = axis_bound(a[1], b[1], (float)sy0 * 0.125f, (float)(sy0 + 2) * 0.125f);
+        if ((bx.g2 + bb.g2) + bz.g2 > rr) {
+            // all 16 fail step 1
+        } else if ((bx.fa2 + bb.fa2) + bz.fa2 <= rr || (bx.fb2 + bb.fb2) + bz.fb2 <= rr) {
+            bits = 0xffffu;
+        } else {
+            const AxisTerms tz = axis_terms(a[2], b[2], sz);
 #pragma unroll
-    for (int yi = 0; yi < 2; ++yi) {
-        const uint32_t rowmask = 0xffu << (8 * yi);
-        if ((bits & rowmask) == rowmask) continue;
-        const float ylo = (float)(sy0 + yi) * 0.125f, yhi = (float)(sy0 + yi + 1) * 0.125f;
-        const AxisBound by = axis_bound(a[1], b[1], ylo, yhi);
-        if ((bx.g2 + by.g2) + bz.g2 > rr) continue;
-        if ((bx.fa2 + by.fa2) + bz.fa2 <= rr || (bx.fb2 + by.fb2) + bz.fb2 <= rr) {
-            bits |= rowmask;
-            continue;
-        }
-        const AxisTerms ty = axis_terms(a[1], b[1], sy0 + yi);
-        const AxisTerms tz = axis_terms(a[2], b[2], sz);
+            for (int yi = 0; yi < 2; ++yi) {
+                const uint32_t rowmask = 0xffu << (8 * yi);
+                if ((bits & rowmask) == rowmask) continue;
+                const float ylo = (float)(sy0 + yi) * 0.125f, yhi = (float)(sy0 + yi + 1) * 0.125f;
+                const AxisBound by = axis_bound(a[1], b[1], ylo, yhi);
+                if ((bx.g2 + by.g2) + bz.g2 > rr) continue;
+                if ((bx.fa2 + by.fa2) + bz.fa2 <= rr || (bx.fb2 + by.fb2) + bz.fb2 <= rr) {
+                    bits |= rowmask;
+                    continue;
+                }
+                const AxisTerms ty = axis_terms(a[1], b[1], sy0 + yi);
 #pragma unroll
-        for (int sx = 0; sx < 8; ++sx) {
-            const uint32_t bit = 1u << (sx + 8 * yi);
-            if (bits & bit) continue;
-            const AxisTerms tx = axis_terms(a[0], b[0], sx);
-            float G = (tx.g2 + ty.g2) + tz.g2;
-            if (G > rr) continue;
-            float EA = (tx.ea2 + ty.ea2) + tz.ea2;
-            float EB = (tx.eb2 + ty.eb2) + tz.eb2;
-            bool hit = (EA <= rr) || (EB <= rr);
-            if (!hit) {
-                float lo[3] = {(float)sx * 0.125f, ylo, zlo};
-                float hi[3] = {(float)(sx + 1) * 0.125f, yhi, zhi};
-                hit = seg_box_min(a, d, lo, hi) <= rr;
+                for (int sx = 0; sx < 8; ++sx) {
+                    const uint32_t bit = 1u << (sx + 8 * yi);
+                    const AxisTerms tx = axis_terms(a[0], b[0], sx);
+                    const float G = (tx.g2 + ty.g2) + tz.g2;
+                    const float EA = (tx.ea2 + ty.ea2) + tz.ea2;
+                    const float EB = (tx.eb2 + ty.eb2) + tz.eb2;
+                    const bool todo = !(bits & bit) && !(G > rr);
+                    if (todo && ((EA <= rr) || (EB <= rr))) bits |= bit;
+                    else if (todo) und |= bit;
+                }
             }
-            if (hit) bits |= bit;
         }
     }
+    // step 3 on the compacted undecided sub-cells of the whole warp
+    const uint32_t n = __popc(und);
+    uint32_t off = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, off, 31);
+    if (total == 0) return bits;
+    off -= n;
+    {
+        uint32_t u = und;
+        while (u) {
+            const int bpos = __ffs(u) - 1;
+            u &= u - 1;
+            const int sx = bpos & 7, sy = sy0 + (bpos >> 3);
+            cs.task[off++] = (uint16_t)(sx + 8 * sy + 64 * sz);
+        }
+    }
+    if (lane < 16) cs.hit[lane] = 0u;
+    __syncwarp();
+    const float d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    for (uint32_t t = lane; t < total; t += 32) {
+        const int id = cs.task[t];
+        const int sx = id & 7, sy = (id >> 3) & 7, zz = id >> 6;
+        const float lo[3] = {(float)sx * 0.125f, (float)sy * 0.125f, (float)zz * 0.125f};
+        const float hi[3] = {(float)(sx + 1) * 0.125f, (float)(sy + 1) * 0.125f, (float)(zz + 1) * 0.125f};
+        if (seg_box_min(a, d, lo, hi) <= rr) atomicOr(&cs.hit[id >> 5], 1u << (id & 31));
+    }
+    __syncwarp();
+    // this lane's 16 bits sit at bit 8*sy0 of the 64-bit word sz: u32 word 2 sz + sy0/4
+    const uint32_t w = cs.hit[2 * sz + (sy0 >> 2)];
+    bits |= (w >> ((8 * sy0) & 31)) & 0xffffu;
+    __syncwarp();
     return bits;
 }
 
@@ -668,6 +710,8 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_fibers(const uint32_t
     const uint32_t nseg = *nseg_p;
     const int sz = lane >> 2, sy0 = (lane & 3) * 2;
     const uint32_t warps = gridDim.x * RED_WARPS;
+    __shared__ CapsuleScratch scratch[RED_WARPS];
+    CapsuleScratch& cs = scratch[threadIdx.x >> 5];
     for (uint32_t seg = blockIdx.x * RED_WARPS + (threadIdx.x >> 5); seg < nseg; seg += warps) {
         const uint32_t beg = starts[seg], end = starts[seg + 1];
         const uint32_t key = keys[beg];
@@ -706,7 +750,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_fibers(const uint32_t
                     const float4 A = ra[p], B = rb[p];
                     float a[3] = {A.x - fx, A.y - fy, A.z - fz};
                     float b[3] = {B.x - fx, B.y - fy, B.z - fz};
-                    chunk = capsule_bits16(a, b, A.w * A.w, sy0, sz, chunk);
+                    chunk = capsule_bits16(a, b, A.w * A.w, sy0, sz, chunk, cs);
                     full = __all_sync(0xffffffffu, chunk == 0xffffu);
                 }
             }

@@ -4,8 +4,10 @@ FP64 central finite differences.
 Loss: sum over levels 0..L and voxels of alpha * m + beta . M with U(-1,1) weights
 drawn per (level, key, component) by a counter-based generator, so both sides draw the
 same weights from their own key sets.  Parameters: control-point xyz, radii, weights.
-Tolerance: |g32 - g64| <= 1e-4 * max(|g64|, median |g64|) (FP32 per-pair terms carry
-~1e-6 relative error; a sum over tens of pairs with mixed signs stays well inside).
+Tolerance: |g32 - g64| <= 1e-4 * max(|g64|, median |g64|) against the analytic gradient;
+against FD, 1e-4 relative to max(|FD|, 1% of the summed magnitudes of the parameter's
+per-pair terms) (FP32 per-pair terms carry ~1e-6 relative error, so the rounding of a sum
+of cancelling terms scales with the terms, not with the total).
 FD: central, FP64, h = 1e-4 in voxel units (the method's coordinates after the grid
 normalisation of Sec. 3.1; 1e-4 / 256 in world units here), on 64 random parameters whose
 stencil does not cross a kink (a clipped piece changing its entering or leaving plane
@@ -133,10 +135,14 @@ def test_adjoint_finite_differences_yarn_256(ctx):
             cm = c64.copy(); cm[c, comp] -= step
             return (local_loss(cp) - local_loss(cm)) / (2 * step)
         f1 = fd(h)
-        _, d_ctrl, _ = oracle.fiber_adjoint(c64, off, w.grid, occ, gm0, gM0, prims=np.array(prims))
+        _, d_ctrl, _, d_abs = oracle.fiber_adjoint(c64, off, w.grid, occ, gm0, gM0, prims=np.array(prims),
+                                                   with_abs=True)
         ref = d_ctrl[c, comp]
-        assert abs(ref - f1) <= 1e-4 * max(abs(f1), 1e-3), (c, comp, ref, f1)
-        err = abs(g_ctrl[c, comp] - f1) / max(abs(f1), 1e-3)
+        # scale: |gradient| or 1% of its summed per-pair term magnitudes (FP32 rounding of the
+        # sum scales with the terms, not with their possibly cancelling total)
+        scale = max(abs(f1), 0.01 * d_abs[c, comp], 1e-3)
+        assert abs(ref - f1) <= 1e-4 * scale, (c, comp, ref, f1)
+        err = abs(g_ctrl[c, comp] - f1) / scale
         worst = max(worst, err)
         assert err <= 1e-4, (c, comp, g_ctrl[c, comp], f1)
         checked += 1
