@@ -193,6 +193,26 @@ VX_API vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, const 
                              const float* const* grad_mass, const float* const* grad_moment,
                              void* stream, float* grad_ctrl, float* grad_weights);
 
+/* vx_backward for callers that cannot allocate device memory: for example code running
+ * inside a host application or memory manager that owns all device memory and forbids
+ * cudaMalloc, or a loop in which an allocation would stall the device.  Same arguments
+ * and results as vx_backward (no context: nothing is allocated, not even through an
+ * allocator).  There is no counterpart in the paper.
+ * Scratch: one fixed array of about 39 MB inside the library (a file-scope device
+ * array), which every GPU that loads the library holds until the process exits.
+ * Limits: at most 65,536 segments, 8,192 fibers, 524,288 level-0 voxels and 2,097,152
+ * candidate (voxel, segment) pairs; larger inputs return VX_ERR_CAPACITY (the pair limit
+ * is checked after the candidates are counted, before any gradient is written).
+ * The first call on a device looks up the array's device address and caches it: make
+ * that first call before any stream capture on that device.  Every call uses the same
+ * array, which keeps the previous call's contents (the call clears what must start at
+ * zero); calls that overlap on the GPU (unordered streams or threads) race and give
+ * wrong gradients.  Synchronises `stream` once.  Errors as vx_backward. */
+VX_API vx_status vx_backward_noalloc(const vx_primitives* prims, const vx_grid* grid, const uint64_t* keys0,
+                                     int64_t num_voxels0, int num_levels, const float* const* grad_mass,
+                                     const float* const* grad_moment, void* stream, float* grad_ctrl,
+                                     float* grad_weights);
+
 /* Returns a level's block to the context's allocator and clears the struct. */
 VX_API void vx_level_release(vx_context* ctx, vx_level* level, void* stream);
 

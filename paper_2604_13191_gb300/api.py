@@ -61,7 +61,7 @@ class VxAllocator(C.Structure):
 
 EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_lod",
            "vx_level_release", "vx_status_string", "vx_last_cuda_error", "vx_profile_enable",
-           "vx_profile_read", "vx_backward"]
+           "vx_profile_read", "vx_backward", "vx_backward_noalloc"]
 
 
 class VxStageTime(C.Structure):
@@ -109,6 +109,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         lib.vx_backward.restype = C.c_int
         lib.vx_backward.argtypes = [P, C.POINTER(VxPrimitives), C.POINTER(VxGrid), P, C.c_int64, C.c_int,
                                     C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), P, P, P]
+        lib.vx_backward_noalloc.restype = C.c_int
+        lib.vx_backward_noalloc.argtypes = [C.POINTER(VxPrimitives), C.POINTER(VxGrid), P, C.c_int64, C.c_int,
+                                            C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), P, P, P]
         _lib = lib
         return lib
 
@@ -403,3 +406,44 @@ class VoxelizeLoD(torch.autograd.Function):
                                             grad_mass=[g.float() for g in gm],
                                             grad_moment=[g.float() for g in gM], weights=weights)
         return g_ctrl, g_w, None, None, None, None
+
+
+NOALLOC_LIMITS = {"segments": 65536, "fibers": 8192, "voxels0": 524288, "pairs": 2097152}
+
+
+def backward_noalloc(grid, *, ctrl, fiber_offsets, keys0, grad_mass, grad_moment, grad_ctrl, grad_weights=None,
+                     weights=None, num_prims=None, stream=None):
+    """vx_backward_noalloc: the gradients of Context.backward written into the caller's
+    grad_ctrl [P,4] (and grad_weights [N]) with no device allocation (fixed library
+    scratch; limits in NOALLOC_LIMITS).  Calls that overlap on the GPU race."""
+    lib = load()
+    keep = []
+    c = ctrl.contiguous()
+    o = fiber_offsets.contiguous()
+    P = VxPrimitives()
+    P.kind = VX_FIBERS
+    P.ctrl = c.data_ptr()
+    P.num_ctrl = c.shape[0]
+    P.fiber_offsets = o.data_ptr()
+    P.num_fibers = o.shape[0] - 1
+    if num_prims is None:
+        oc = o.cpu()
+        num_prims = int(torch.clamp(oc[1:] - oc[:-1] - 1, min=0).sum())
+    P.num_prims = int(num_prims)
+    if weights is not None:
+        wt = weights.contiguous()
+        keep.append(wt)
+        P.weights = wt.data_ptr()
+    L = len(grad_mass) - 1
+    gm = [g.contiguous() for g in grad_mass]
+    gM = [g.contiguous() for g in grad_moment]
+    k0 = keys0.contiguous()
+    keep += [c, o, k0] + gm + gM
+    pm = (C.c_void_p * (L + 1))(*[g.data_ptr() for g in gm])
+    pM = (C.c_void_p * (L + 1))(*[g.data_ptr() for g in gM])
+    G = _grid(grid)
+    st = lib.vx_backward_noalloc(C.byref(P), C.byref(G), k0.data_ptr(), k0.shape[0], L, pm, pM, _stream(stream),
+                                 grad_ctrl.data_ptr(), None if grad_weights is None else grad_weights.data_ptr())
+    if st != 0:
+        detail = f"limits {NOALLOC_LIMITS}" if st == 3 else ""
+        raise VxError(st, "vx_backward_noalloc", detail)

@@ -105,6 +105,10 @@ vx_status vx_scan_u32(vx_context* ctx, const uint32_t* in, uint32_t* out, uint32
 vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, uint32_t** keys_alt,
                             uint32_t** vals_alt, uint32_t n, int bits, cudaStream_t s);
 
+// Exclusive prefix sum with caller-provided partials (>= ceil(n / 2048) words).
+cudaError_t vx_scan_u32_scratch(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total,
+                                uint32_t* partials, cudaStream_t s);
+
 // ---- Morton ------------------------------------------------------------------
 __host__ __device__ inline uint32_t vx_part1by2(uint32_t x) {
     x &= 0x000003ffu;

@@ -222,3 +222,15 @@ vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, u
     }
     return VX_OK;
 }
+
+// Exclusive prefix sum with caller-provided partials (at least ceil(n / 2048) words); for
+// code that must not touch the context workspace.  Same kernels as vx_scan_u32.
+cudaError_t vx_scan_u32_scratch(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total,
+                                uint32_t* partials, cudaStream_t s) {
+    if (n == 0) return total ? cudaMemsetAsync(total, 0, 4, s) : cudaSuccess;
+    const uint32_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(in, n, partials);
+    k_scan_partials<<<1, SCAN_THREADS, 0, s>>>(partials, nb, total);
+    k_scan_down<<<nb, SCAN_THREADS, 0, s>>>(in, out, n, partials);
+    return cudaGetLastError();
+}

@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "vx_internal.cuh"
 
@@ -1332,5 +1333,149 @@ extern "C" vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, co
     if (grad_weights)
         VX_LAUNCH(ctx, ST_FINALIZE, s, k_adjoint_weights<<<grid_for(np, 256), 256, 0, s>>>(seg_grad, np, grad_weights));
     VX_CUDA_TRY(cudaGetLastError());
+    return VX_OK;
+}
+
+// =====================================================================================
+// vx_backward_noalloc: the adjoint with its scratch in a fixed device array
+// =====================================================================================
+// For callers that cannot allocate device memory.  The scratch is one file-scope device
+// array, sized for the limits below, held by every device that loads the library until
+// the process exits.  Host code must not pass the array's name to a kernel (on the host
+// it names a host-side stand-in): its device address is fetched once per device with
+// cudaGetSymbolAddress and cached.
+namespace {
+
+constexpr uint32_t NA_MAX_PRIMS = 1u << 16;    // 65,536 segments
+constexpr uint32_t NA_MAX_FIBERS = 1u << 13;   // 8,192 fibers
+constexpr uint32_t NA_MAX_PAIRS = 1u << 21;    // 2,097,152 candidate (voxel, segment) pairs
+constexpr uint32_t NA_MAX_VOXELS = 1u << 19;   // 524,288 level-0 voxels
+
+constexpr size_t na_al(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t NA_RA = 0;
+constexpr size_t NA_RB = NA_RA + na_al(16ull * NA_MAX_PRIMS);
+constexpr size_t NA_CNT = NA_RB + na_al(16ull * NA_MAX_PRIMS);
+constexpr size_t NA_OFFS = NA_CNT + na_al(4ull * NA_MAX_PRIMS);
+constexpr size_t NA_FS = NA_OFFS + na_al(4ull * NA_MAX_PRIMS);
+constexpr size_t NA_MISC = NA_FS + na_al(4ull * NA_MAX_FIBERS + 4);
+constexpr size_t NA_KEYS = NA_MISC + 256;
+constexpr size_t NA_VALS = NA_KEYS + na_al(4ull * NA_MAX_PAIRS);
+constexpr size_t NA_SEG = NA_VALS + na_al(4ull * NA_MAX_PAIRS);
+constexpr size_t NA_FLAGS = NA_SEG + na_al(32ull * NA_MAX_PRIMS);
+constexpr size_t NA_EXCL = NA_FLAGS + na_al(4ull * NA_MAX_VOXELS);
+constexpr size_t NA_GM = NA_EXCL + na_al(4ull * NA_MAX_VOXELS);
+constexpr size_t NA_GMM = NA_GM + na_al(4ull * NA_MAX_VOXELS);
+constexpr size_t NA_PART = NA_GMM + na_al(24ull * NA_MAX_VOXELS);
+constexpr size_t NA_BYTES = NA_PART + na_al(4ull * (NA_MAX_VOXELS / 2048 + 64));   // ~39 MB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+std::mutex g_na_mutex;
+unsigned char* g_na_ptr[256] = {};
+
+// device address of the scratch array on the current device (set up on first use)
+vx_status na_scratch(unsigned char** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return VX_ERR_CUDA;
+    if (dev < 0 || dev >= 256) return VX_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return VX_ERR_CUDA;
+        g_na_ptr[dev] = (unsigned char*)p;
+    }
+    *out = g_na_ptr[dev];
+    return VX_OK;
+}
+
+}  // namespace
+
+#define NA_TRY(expr)                                   \
+    do {                                               \
+        if ((expr) != cudaSuccess) return VX_ERR_CUDA; \
+    } while (0)
+
+extern "C" vx_status vx_backward_noalloc(const vx_primitives* prims, const vx_grid* grid, const uint64_t* keys0,
+                                         int64_t num_voxels0, int num_levels, const float* const* grad_mass,
+                                         const float* const* grad_moment, void* stream, float* grad_ctrl,
+                                         float* grad_weights) {
+    if (!prims || !grid || !grad_mass || !grad_moment || !grad_ctrl) return VX_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prims->kind != VX_FIBERS) return VX_ERR_UNSUPPORTED;
+    const uint32_t R = grid->resolution;
+    if (R == 0 || (R & (R - 1)) != 0) return VX_ERR_INVALID_ARG;
+    if (R > 1024 || grid->sub_res != 8) return VX_ERR_UNSUPPORTED;
+    if (num_voxels0 < 0 || num_levels < 0 || num_levels > 11 || prims->num_prims < 0 || prims->num_fibers <= 0)
+        return VX_ERR_INVALID_ARG;
+    if (prims->num_prims > (int64_t)NA_MAX_PRIMS || prims->num_fibers > (int64_t)NA_MAX_FIBERS ||
+        num_voxels0 > (int64_t)NA_MAX_VOXELS)
+        return VX_ERR_CAPACITY;
+    if (!prims->ctrl || !prims->fiber_offsets || ((uintptr_t)prims->ctrl & 15) != 0 ||
+        ((uintptr_t)grad_ctrl & 15) != 0)
+        return VX_ERR_INVALID_ARG;
+    for (int l = 0; l <= num_levels; ++l)
+        if (!grad_mass[l] || !grad_moment[l]) return VX_ERR_INVALID_ARG;
+    unsigned char* base = nullptr;
+    VX_TRY(na_scratch(&base));
+    const uint32_t np = (uint32_t)prims->num_prims;
+    const uint32_t V0 = (uint32_t)num_voxels0;
+    const int64_t P = prims->num_ctrl, F = prims->num_fibers;
+    GridDev g;
+    g.o[0] = grid->origin[0]; g.o[1] = grid->origin[1]; g.o[2] = grid->origin[2];
+    g.s = 1.0f / grid->voxel_size;
+    g.R = (int)R;
+    float4* r0 = (float4*)(base + NA_RA);
+    float4* r1 = (float4*)(base + NA_RB);
+    uint32_t* cnt = (uint32_t*)(base + NA_CNT);
+    uint32_t* offs = (uint32_t*)(base + NA_OFFS);
+    uint32_t* fs = (uint32_t*)(base + NA_FS);
+    uint32_t* misc = (uint32_t*)(base + NA_MISC);
+    uint32_t* k0 = (uint32_t*)(base + NA_KEYS);
+    uint32_t* v0 = (uint32_t*)(base + NA_VALS);
+    float* seg_grad = (float*)(base + NA_SEG);
+    uint32_t* flags = (uint32_t*)(base + NA_FLAGS);
+    uint32_t* excl = (uint32_t*)(base + NA_EXCL);
+    float* gm = (float*)(base + NA_GM);
+    float* gM = (float*)(base + NA_GMM);
+    uint32_t* part = (uint32_t*)(base + NA_PART);
+
+    // the array keeps the previous call's contents: clear the counters and error flag
+    NA_TRY(cudaMemsetAsync(misc, 0, 64, s));
+    NA_TRY(cudaMemsetAsync(grad_ctrl, 0, (size_t)P * 16, s));
+    if (grad_weights && np) NA_TRY(cudaMemsetAsync(grad_weights, 0, (size_t)np * 4, s));
+    if (np == 0) return VX_OK;
+
+    // level-0 adjoints (coarse adjoints broadcast down)
+    if (V0) {
+        k_bcast<<<grid_for(V0, 256), 256, 0, s>>>(excl, flags, V0, grad_mass[0], grad_moment[0], 1, gm, gM);
+        for (int l = 1; l <= num_levels; ++l) {
+            k_key_shift_flags<<<grid_for(V0, 256), 256, 0, s>>>(keys0, V0, 3 * l, flags);
+            NA_TRY(vx_scan_u32_scratch(flags, excl, V0, nullptr, part, s));
+            k_bcast<<<grid_for(V0, 256), 256, 0, s>>>(excl, flags, V0, grad_mass[l], grad_moment[l], 0, gm, gM);
+        }
+    }
+    // candidate pairs, primitive-major
+    k_fiber_seg_counts<<<grid_for((size_t)F, 256), 256, 0, s>>>(prims->fiber_offsets, F, fs);
+    NA_TRY(vx_scan_u32_scratch(fs, fs, (uint32_t)F, misc + 4, part, s));
+    k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl, prims->fiber_offsets, fs, F, misc + 4,
+                                                     prims->weights, np, g, r0, r1, misc);
+    const unsigned cblocks = (unsigned)std::min<size_t>((np + EMIT_WARPS - 1) / EMIT_WARPS, (size_t)vx::kSMs * 64);
+    k_candidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, nullptr, np, (int)R, cnt, nullptr, nullptr,
+                                                                  nullptr);
+    NA_TRY(vx_scan_u32_scratch(cnt, offs, np, misc + 1, part, s));
+    uint32_t host[2] = {0, 0};
+    NA_TRY(cudaMemcpyAsync(host, misc, 8, cudaMemcpyDeviceToHost, s));
+    NA_TRY(cudaStreamSynchronize(s));
+    if (host[0]) return VX_ERR_INVALID_ARG;
+    const uint32_t npairs = host[1];
+    if (npairs > NA_MAX_PAIRS) return VX_ERR_CAPACITY;
+    if (npairs)
+        k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, nullptr, np, (int)R, nullptr, offs, k0,
+                                                                     v0);
+    k_adjoint_fibers<<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, np, offs, cnt, k0, keys0, V0, gm, gM, seg_grad);
+    k_adjoint_ctrl<<<grid_for((size_t)P, 256), 256, 0, s>>>(prims->fiber_offsets, F, fs, P, seg_grad, g.s,
+                                                             (float4*)grad_ctrl);
+    if (grad_weights) k_adjoint_weights<<<grid_for(np, 256), 256, 0, s>>>(seg_grad, np, grad_weights);
+    NA_TRY(cudaGetLastError());
     return VX_OK;
 }
