@@ -200,7 +200,7 @@ VX_API vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, const 
  * allocator).  There is no counterpart in the paper.
  * Scratch: one fixed array of about 39 MB inside the library (a file-scope device
  * array), which every GPU that loads the library holds until the process exits.
- * Limits: at most 65,536 segments, 8,192 fibers, 524,288 level-0 voxels and 2,097,152
+ * Limits: at most 65,536 segments, 8,192 fibers, 262,144 level-0 voxels and 2,097,152
  * candidate (voxel, segment) pairs; larger inputs return VX_ERR_CAPACITY (the pair limit
  * is checked after the candidates are counted, before any gradient is written).
  * The first call on a device looks up the array's device address and caches it: make

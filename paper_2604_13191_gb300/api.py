@@ -408,7 +408,7 @@ class VoxelizeLoD(torch.autograd.Function):
         return g_ctrl, g_w, None, None, None, None
 
 
-NOALLOC_LIMITS = {"segments": 65536, "fibers": 8192, "voxels0": 524288, "pairs": 2097152}
+NOALLOC_LIMITS = {"segments": 65536, "fibers": 8192, "voxels0": 262144, "pairs": 2097152}
 
 
 def backward_noalloc(grid, *, ctrl, fiber_offsets, keys0, grad_mass, grad_moment, grad_ctrl, grad_weights=None,

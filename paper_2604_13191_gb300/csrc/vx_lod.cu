@@ -272,6 +272,7 @@ __device__ LobeStats sample_lobe(const float* S, const float* __restrict__ dirs,
     for (int k0 = tid; k0 < N; k0 += STRIDE * 1024) {
         int32_t q[6] = {0, 0, 0, 0, 0, 0};
         const int kend = min(N, k0 + STRIDE * 1024);
+#pragma unroll 4
         for (int k = k0; k < kend; k += STRIDE) {
             const float u0 = __ldg(dirs + 3 * k), u1 = __ldg(dirs + 3 * k + 1), u2 = __ldg(dirs + 3 * k + 2);
             float v[3];

@@ -24,894 +24,7 @@
 
 #include "vx_internal.cuh"
 
-namespace {
-
-constexpr float kPi = 3.14159265358979f;
-constexpr int RED_WARPS = 4;        // warps per block in the reduce kernels
-constexpr int EMIT_WARPS = 8;
-
-struct GridDev {
-    float o[3];
-    float s;      // 1 / voxel_size (FP32)
-    int R;
-};
-
-// Per-segment temporary outputs (indexed by candidate-voxel segment id).
-struct SegOut {
-    uint32_t* key;
-    uint64_t* mask;     // [n][8]
-    float* mass;
-    float* moment;      // [n][6]
-    uint32_t* nonzero;
-};
-
-__device__ __forceinline__ float fmin2(float a, float b) { return (b < a) ? b : a; }
-__device__ __forceinline__ float fmax2(float a, float b) { return (b > a) ? b : a; }
-
-// ------------------------------------------------------------------------------------
-// capsule vs closed box [lo, hi]: a, b local endpoints, rr = r^2
-// ------------------------------------------------------------------------------------
-__device__ __forceinline__ float sqdist_point_box(float px, float py, float pz, const float* lo,
-                                                  const float* hi) {
-    float p[3] = {px, py, pz};
-    float e[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        if (p[i] < lo[i]) e[i] = lo[i] - p[i];
-        else if (p[i] > hi[i]) e[i] = p[i] - hi[i];
-        else e[i] = 0.0f;
-    }
-    return (e[0] * e[0] + e[1] * e[1]) + e[2] * e[2];
-}
-
-__device__ __forceinline__ float seg_g(const float* a, const float* d, float t, const float* lo,
-                                       const float* hi) {
-    if (!(t >= 0.0f)) t = 0.0f;
-    else if (t > 1.0f) t = 1.0f;
-    return sqdist_point_box(a[0] + t * d[0], a[1] + t * d[1], a[2] + t * d[2], lo, hi);
-}
-
-// Step 3 of the capsule test: min over t in [0,1] of the squared segment-box distance,
-// taken at the stationary points of the quadratic pieces that can hold the minimum.
-// (Scalar code with explicit selects: no dynamically indexed local arrays.)
-__device__ __forceinline__ float sel3(int i, float x, float y, float z) { return i == 0 ? x : (i == 1 ? y : z); }
-
-__device__ __noinline__ float seg_box_min(const float* a, const float* d, const float* lo, const float* hi) {
-    float L = -INFINITY, U = INFINITY;
-    int iL = -1, jU = -1, moving = 0;
-    float plo0 = 0.0f, plo1 = 0.0f, plo2 = 0.0f, phi0 = 0.0f, phi1 = 0.0f, phi2 = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        if (d[i] != 0.0f) {
-            ++moving;
-            const float pl = (d[i] > 0.0f) ? lo[i] : hi[i];
-            const float ph = (d[i] > 0.0f) ? hi[i] : lo[i];
-            if (i == 0) { plo0 = pl; phi0 = ph; } else if (i == 1) { plo1 = pl; phi1 = ph; } else { plo2 = pl; phi2 = ph; }
-            const float jl = (pl - a[i]) / d[i];
-            const float jh = (ph - a[i]) / d[i];
-            if (jl > L) { L = jl; iL = i; }
-            if (jh < U) { U = jh; jU = i; }
-        }
-    }
-    if (moving == 0) return INFINITY;
-    if (L <= U) {
-        float t;
-        if (U < 0.0f) t = 0.0f;
-        else if (L > 1.0f) t = 1.0f;
-        else t = fmax2(L, 0.0f);
-        return seg_g(a, d, t, lo, hi);
-    }
-    // the axis giving L lies below its slab and the one giving U above it on [U, L]
-    const int k = 3 - iL - jU;
-    // beta per axis for the pair {iL, jU}: plo for iL, phi for jU
-    const float b0 = (iL == 0) ? plo0 : phi0;
-    const float b1 = (iL == 1) ? plo1 : phi1;
-    const float b2 = (iL == 2) ? plo2 : phi2;
-    const int p0 = iL < jU ? iL : jU, p1 = iL < jU ? jU : iL;
-    const float a0 = sel3(p0, a[0], a[1], a[2]), a1 = sel3(p1, a[0], a[1], a[2]);
-    const float d0 = sel3(p0, d[0], d[1], d[2]), d1 = sel3(p1, d[0], d[1], d[2]);
-    const float e0 = sel3(p0, b0, b1, b2), e1 = sel3(p1, b0, b1, b2);
-    float num = d0 * (e0 - a0);
-    float den = d0 * d0;
-    num = num + d1 * (e1 - a1);
-    den = den + d1 * d1;
-    float gmin = seg_g(a, d, num / den, lo, hi);
-    const float dk = sel3(k, d[0], d[1], d[2]);
-    if (dk != 0.0f) {
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            // beta: iL -> plo, jU -> phi, k -> plo (side 0) or phi (side 1)
-            const float c0 = (k == 0) ? (side == 0 ? plo0 : phi0) : b0;
-            const float c1 = (k == 1) ? (side == 0 ? plo1 : phi1) : b1;
-            const float c2 = (k == 2) ? (side == 0 ? plo2 : phi2) : b2;
-            float n3 = d[0] * (c0 - a[0]);
-            float d3 = d[0] * d[0];
-            n3 = n3 + d[1] * (c1 - a[1]);
-            d3 = d3 + d[1] * d[1];
-            n3 = n3 + d[2] * (c2 - a[2]);
-            d3 = d3 + d[2] * d[2];
-            const float gc = seg_g(a, d, n3 / d3, lo, hi);
-            if (gc < gmin) gmin = gc;
-        }
-    }
-    return gmin;
-}
-
-// Full capsule-box predicate (used at voxel level with an inflated radius as a cull).
-__device__ __forceinline__ bool capsule_box(const float* a, const float* b, float rr, const float* lo,
-                                            const float* hi) {
-    float d[3], g[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        d[i] = b[i] - a[i];
-        float mn = fmin2(a[i], b[i]), mx = fmax2(a[i], b[i]);
-        if (lo[i] > mx) g[i] = lo[i] - mx;
-        else if (mn > hi[i]) g[i] = mn - hi[i];
-        else g[i] = 0.0f;
-    }
-    float G = (g[0] * g[0] + g[1] * g[1]) + g[2] * g[2];
-    if (G > rr) return false;
-    if (sqdist_point_box(a[0], a[1], a[2], lo, hi) <= rr) return true;
-    if (sqdist_point_box(b[0], b[1], b[2], lo, hi) <= rr) return true;
-    return seg_box_min(a, d, lo, hi) <= rr;
-}
-
-// Per-axis terms of steps 1 and 2 for the sub-cell interval [k/8, (k+1)/8] of one axis.
-struct AxisTerms {
-    float g2, ea2, eb2;
-};
-__device__ __forceinline__ AxisTerms axis_terms(float a, float b, int k) {
-    const float lo = (float)k * 0.125f, hi = (float)(k + 1) * 0.125f;
-    const float mn = fmin2(a, b), mx = fmax2(a, b);
-    float g = (lo > mx) ? lo - mx : ((mn > hi) ? mn - hi : 0.0f);
-    float ea = (a < lo) ? lo - a : ((a > hi) ? a - hi : 0.0f);
-    float eb = (b < lo) ? lo - b : ((b > hi) ? b - hi : 0.0f);
-    AxisTerms t;
-    t.g2 = g * g;
-    t.ea2 = ea * ea;
-    t.eb2 = eb * eb;
-    return t;
-}
-
-// Per-axis bounds over a union of sub-cell intervals [lo, hi] on one axis:
-//   gap  <= the step-1 gap of every sub-cell inside (FP subtraction is monotone)
-//   farA >= the step-2 distance of endpoint a to every sub-cell inside, likewise farB.
-struct AxisBound {
-    float g2, fa2, fb2;
-};
-__device__ __forceinline__ AxisBound axis_bound(float a, float b, float lo, float hi) {
-    const float mn = fmin2(a, b), mx = fmax2(a, b);
-    float g = (lo > mx) ? lo - mx : ((mn > hi) ? mn - hi : 0.0f);
-    float fa = fmax2(hi - a, a - lo);
-    float fb = fmax2(hi - b, b - lo);
-    AxisBound r;
-    r.g2 = g * g;
-    r.fa2 = fa * fa;
-    r.fb2 = fb * fb;
-    return r;
-}
-
-// Per-warp shared scratch of the capsule mask: the sub-cells still undecided after steps
-// 1-2 (a task list) and the step-3 results (a 512-bit map).
-struct CapsuleScratch {
-    uint16_t task[512];
-    uint32_t hit[16];
-};
-
-// Warp-collective: 16 sub-cell bits of each lane (sx = 0..7, sy = sy0 + (0|1), sz) for one
-// capsule; bits already set in `have` are skipped (OR is idempotent).  Bit b = sx + 8 (sy - sy0).
-// Steps 1-2 run per lane.  A group of sub-cells (the lane's 16, or one row of 8) is decided
-// at once when
-//   the sum of its per-axis gap bounds > r^2   -> every sub-cell fails step 1 (bits 0), or
-//   the sum of an endpoint's far bounds <= r^2 -> every sub-cell passes step 2 (bits 1)
-// (each sub-cell's step-1 sum is >= the group's and <= its step-2 sum, so the group result
-// equals the per-sub-cell definition bit for bit).  The sub-cells left for step 3 are
-// compacted over the warp and evaluated 32 at a time, so that the exact minimum (the
-// expensive, rare case) runs with all lanes busy.
-__device__ __forceinline__ uint32_t capsule_bits16(const float* a, const float* b, float rr, int sy0,
-                                                   int sz, uint32_t have, CapsuleScratch& cs) {
-    const int lane = threadIdx.x & 31;
-    uint32_t bits = have, und = 0;
-    if (have != 0xffffu) {
-        const float zlo = (float)sz * 0.125f, zhi = (float)(sz + 1) * 0.125f;
-        const AxisBound bz = axis_bound(a[2], b[2], zlo, zhi);
-        const AxisBound bx = axis_bound(a[0], b[0], 0.0f, 1.0f);
-        const AxisBound bb = axis_bound(a[1], b[1], (float)sy0 * 0.125f, (float)(sy0 + 2) * 0.125f);
-        if ((bx.g2 + bb.g2) + bz.g2 > rr) {
-            // all 16 fail step 1
-        } else if ((bx.fa2 + bb.fa2) + bz.fa2 <= rr || (bx.fb2 + bb.fb2) + bz.fb2 <= rr) {
-            bits = 0xffffu;
-        } else {
-            const AxisTerms tz = axis_terms(a[2], b[2], sz);
-#pragma unroll
-            for (int yi = 0; yi < 2; ++yi) {
-                const uint32_t rowmask = 0xffu << (8 * yi);
-                if ((bits & rowmask) == rowmask) continue;
-                const float ylo = (float)(sy0 + yi) * 0.125f, yhi = (float)(sy0 + yi + 1) * 0.125f;
-                const AxisBound by = axis_bound(a[1], b[1], ylo, yhi);
-                if ((bx.g2 + by.g2) + bz.g2 > rr) continue;
-                if ((bx.fa2 + by.fa2) + bz.fa2 <= rr || (bx.fb2 + by.fb2) + bz.fb2 <= rr) {
-                    bits |= rowmask;
-                    continue;
-                }
-                const AxisTerms ty = axis_terms(a[1], b[1], sy0 + yi);
-#pragma unroll
-                for (int sx = 0; sx < 8; ++sx) {
-                    const uint32_t bit = 1u << (sx + 8 * yi);
-                    const AxisTerms tx = axis_terms(a[0], b[0], sx);
-                    const float G = (tx.g2 + ty.g2) + tz.g2;
-                    const float EA = (tx.ea2 + ty.ea2) + tz.ea2;
-                    const float EB = (tx.eb2 + ty.eb2) + tz.eb2;
-                    const bool todo = !(bits & bit) && !(G > rr);
-                    if (todo && ((EA <= rr) || (EB <= rr))) bits |= bit;
-                    else if (todo) und |= bit;
-                }
-            }
-        }
-    }
-    // step 3 on the compacted undecided sub-cells of the whole warp
-    const uint32_t n = __popc(und);
-    uint32_t off = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, off, o);
-        if (lane >= o) off += t;
-    }
-    const uint32_t total = __shfl_sync(0xffffffffu, off, 31);
-    if (total == 0) return bits;
-    off -= n;
-    {
-        uint32_t u = und;
-        while (u) {
-            const int bpos = __ffs(u) - 1;
-            u &= u - 1;
-            const int sx = bpos & 7, sy = sy0 + (bpos >> 3);
-            cs.task[off++] = (uint16_t)(sx + 8 * sy + 64 * sz);
-        }
-    }
-    if (lane < 16) cs.hit[lane] = 0u;
-    __syncwarp();
-    const float d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-    for (uint32_t t = lane; t < total; t += 32) {
-        const int id = cs.task[t];
-        const int sx = id & 7, sy = (id >> 3) & 7, zz = id >> 6;
-        const float lo[3] = {(float)sx * 0.125f, (float)sy * 0.125f, (float)zz * 0.125f};
-        const float hi[3] = {(float)(sx + 1) * 0.125f, (float)(sy + 1) * 0.125f, (float)(zz + 1) * 0.125f};
-        if (seg_box_min(a, d, lo, hi) <= rr) atomicOr(&cs.hit[id >> 5], 1u << (id & 31));
-    }
-    __syncwarp();
-    // this lane's 16 bits sit at bit 8*sy0 of the 64-bit word sz: u32 word 2 sz + sy0/4
-    const uint32_t w = cs.hit[2 * sz + (sy0 >> 2)];
-    bits |= (w >> ((8 * sy0) & 31)) & 0xffffu;
-    __syncwarp();
-    return bits;
-}
-
-// pi r^2 * length of the axis a-b clipped to the closed voxel [0,1]^3 (Liang-Barsky)
-__device__ __forceinline__ float capsule_measure(const float* a, const float* b, float rg) {
-    float d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-    float t0 = 0.0f, t1 = 1.0f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        if (d[i] == 0.0f) {
-            if (a[i] < 0.0f || a[i] > 1.0f) return 0.0f;
-        } else {
-            float ta = (0.0f - a[i]) / d[i];
-            float tb = (1.0f - a[i]) / d[i];
-            float tn = d[i] > 0.0f ? ta : tb;
-            float tf = d[i] > 0.0f ? tb : ta;
-            if (tn > t0) t0 = tn;
-            if (tf < t1) t1 = tf;
-        }
-    }
-    if (t1 <= t0) return 0.0f;
-    float dn = sqrtf((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
-    float len = (t1 - t0) * dn;
-    float rr = rg * rg;
-    return (kPi * rr) * len;
-}
-
-// ------------------------------------------------------------------------------------
-// triangle vs closed box: separating axis test (13 axes)
-// ------------------------------------------------------------------------------------
-__device__ __forceinline__ bool sep3(float p0, float p1, float p2, float rad) {
-    float mn = fmin2(fmin2(p0, p1), p2), mx = fmax2(fmax2(p0, p1), p2);
-    return (mn > rad || mx < -rad);
-}
-
-// all 13 axes for a box (centre c, half extent e); v local vertices, f global edges
-__device__ __forceinline__ bool tri_box(const float v[3][3], const float f[3][3], const float* c, float e) {
-    float w[3][3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) w[k][i] = v[k][i] - c[i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-        if (sep3(w[0][i], w[1][i], w[2][i], e)) return false;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const float* q = f[j];
-        if (sep3(q[1] * w[0][2] - q[2] * w[0][1], q[1] * w[1][2] - q[2] * w[1][1], q[1] * w[2][2] - q[2] * w[2][1],
-                 e * (fabsf(q[1]) + fabsf(q[2]))))
-            return false;
-        if (sep3(q[2] * w[0][0] - q[0] * w[0][2], q[2] * w[1][0] - q[0] * w[1][2], q[2] * w[2][0] - q[0] * w[2][2],
-                 e * (fabsf(q[0]) + fabsf(q[2]))))
-            return false;
-        if (sep3(q[0] * w[0][1] - q[1] * w[0][0], q[0] * w[1][1] - q[1] * w[1][0], q[0] * w[2][1] - q[1] * w[2][0],
-                 e * (fabsf(q[0]) + fabsf(q[1]))))
-            return false;
-    }
-    float n0 = f[0][1] * f[1][2] - f[0][2] * f[1][1];
-    float n1 = f[0][2] * f[1][0] - f[0][0] * f[1][2];
-    float n2 = f[0][0] * f[1][1] - f[0][1] * f[1][0];
-    float p = (n0 * w[0][0] + n1 * w[0][1]) + n2 * w[0][2];
-    float rad = e * ((fabsf(n0) + fabsf(n1)) + fabsf(n2));
-    return !(p > rad || p < -rad);
-}
-
-// One edge-family test for the sub-cell pair index q (two sub-cell coordinates (i0,i1)
-// along the axes (ax0, ax1) that the family's axis depends on).
-// family 0: e_x x f (axes y,z), 1: e_y x f (axes x,z), 2: e_z x f (axes x,y)
-__device__ __forceinline__ bool family_pass(int fam, const float v[3][3], const float f[3][3], int i0, int i1) {
-    const float e = 0.0625f;
-    const float c0 = (float)(2 * i0 + 1) * 0.0625f, c1 = (float)(2 * i1 + 1) * 0.0625f;
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const float* q = f[j];
-        float p[3];
-        float rad;
-        if (fam == 0) {          // w_y = v_y - c(i0), w_z = v_z - c(i1)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float wy = v[k][1] - c0, wz = v[k][2] - c1;
-                p[k] = q[1] * wz - q[2] * wy;
-            }
-            rad = e * (fabsf(q[1]) + fabsf(q[2]));
-        } else if (fam == 1) {   // w_x = v_x - c(i0), w_z = v_z - c(i1)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float wx = v[k][0] - c0, wz = v[k][2] - c1;
-                p[k] = q[2] * wx - q[0] * wz;
-            }
-            rad = e * (fabsf(q[0]) + fabsf(q[2]));
-        } else {                 // w_x = v_x - c(i0), w_y = v_y - c(i1)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float wx = v[k][0] - c0, wy = v[k][1] - c1;
-                p[k] = q[0] * wy - q[1] * wx;
-            }
-            rad = e * (fabsf(q[0]) + fabsf(q[1]));
-        }
-        ok = ok && !sep3(p[0], p[1], p[2], rad);
-    }
-    return ok;
-}
-
-// 16 sub-cell bits of one lane (sx 0..7, sy0+{0,1}, sz).  Warp-collective: every lane
-// of the warp must call it with the same triangle.
-__device__ __forceinline__ uint32_t tri_bits16(const float v[3][3], const float f[3][3], int sy0, int sz) {
-    const int lane = threadIdx.x & 31;
-    const float e = 0.0625f;
-    // edge families over the 64 index pairs, two per lane, collected by ballot
-    uint64_t fam[3];
-#pragma unroll
-    for (int fa = 0; fa < 3; ++fa) {
-        bool p_lo = family_pass(fa, v, f, lane & 7, lane >> 3);
-        bool p_hi = family_pass(fa, v, f, (lane + 32) & 7, (lane + 32) >> 3);
-        uint32_t blo = __ballot_sync(0xffffffffu, p_lo);
-        uint32_t bhi = __ballot_sync(0xffffffffu, p_hi);
-        fam[fa] = (uint64_t)blo | ((uint64_t)bhi << 32);
-    }
-    // box normals
-    uint32_t bx = 0, by = 0;
-    bool bz;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        float c = (float)(2 * k + 1) * 0.0625f;
-        if (!sep3(v[0][0] - c, v[1][0] - c, v[2][0] - c, e)) bx |= 1u << k;
-    }
-#pragma unroll
-    for (int yi = 0; yi < 2; ++yi) {
-        float c = (float)(2 * (sy0 + yi) + 1) * 0.0625f;
-        if (!sep3(v[0][1] - c, v[1][1] - c, v[2][1] - c, e)) by |= 1u << yi;
-    }
-    {
-        float c = (float)(2 * sz + 1) * 0.0625f;
-        bz = !sep3(v[0][2] - c, v[1][2] - c, v[2][2] - c, e);
-    }
-    if (!bz || !by || !bx) return 0;
-    // face normal plane
-    float n0 = f[0][1] * f[1][2] - f[0][2] * f[1][1];
-    float n1 = f[0][2] * f[1][0] - f[0][0] * f[1][2];
-    float n2 = f[0][0] * f[1][1] - f[0][1] * f[1][0];
-    float rad = e * ((fabsf(n0) + fabsf(n1)) + fabsf(n2));
-    float cz = (float)(2 * sz + 1) * 0.0625f;
-    float pz = n2 * (v[0][2] - cz);
-    uint32_t bits = 0;
-#pragma unroll
-    for (int yi = 0; yi < 2; ++yi) {
-        const int sy = sy0 + yi;
-        if (!((by >> yi) & 1u)) continue;
-        float cy = (float)(2 * sy + 1) * 0.0625f;
-        float py = n1 * (v[0][1] - cy);
-#pragma unroll
-        for (int sx = 0; sx < 8; ++sx) {
-            if (!((bx >> sx) & 1u)) continue;
-            if (!((fam[0] >> (sy + 8 * sz)) & 1ull)) continue;
-            if (!((fam[1] >> (sx + 8 * sz)) & 1ull)) continue;
-            if (!((fam[2] >> (sx + 8 * sy)) & 1ull)) continue;
-            float cx = (float)(2 * sx + 1) * 0.0625f;
-            float p = (n0 * (v[0][0] - cx) + py) + pz;
-            if (p > rad || p < -rad) continue;
-            bits |= 1u << (sx + 8 * yi);
-        }
-    }
-    return bits;
-}
-
-// Sutherland-Hodgman clip of a polygon against x_axis >= c (ge) or x_axis <= c
-__device__ __forceinline__ int clip_plane(const float (*in)[3], int n, float (*out)[3], int axis, float c, bool ge) {
-    int m = 0;
-    for (int k = 0; k < n; ++k) {
-        const float* S = in[k];
-        const float* E = in[(k + 1) == n ? 0 : k + 1];
-        bool sin_ = ge ? (S[axis] >= c) : (S[axis] <= c);
-        bool ein = ge ? (E[axis] >= c) : (E[axis] <= c);
-        if (ein) {
-            if (!sin_) {
-                float s = (c - S[axis]) / (E[axis] - S[axis]);
-                for (int j = 0; j < 3; ++j) out[m][j] = (j == axis) ? c : S[j] + s * (E[j] - S[j]);
-                ++m;
-            }
-            for (int j = 0; j < 3; ++j) out[m][j] = E[j];
-            ++m;
-        } else if (sin_) {
-            float s = (c - S[axis]) / (E[axis] - S[axis]);
-            for (int j = 0; j < 3; ++j) out[m][j] = (j == axis) ? c : S[j] + s * (E[j] - S[j]);
-            ++m;
-        }
-    }
-    return m;
-}
-
-// area (voxel units^2) of the triangle clipped to the voxel [0,1]^3
-__device__ __noinline__ float tri_measure(const float v[3][3]) {
-    float A[12][3], B[12][3];
-    int n = 3;
-    for (int k = 0; k < 3; ++k)
-        for (int j = 0; j < 3; ++j) A[k][j] = v[k][j];
-    for (int axis = 0; axis < 3 && n > 0; ++axis) {
-        n = clip_plane(A, n, B, axis, 0.0f, true);
-        if (n == 0) break;
-        n = clip_plane(B, n, A, axis, 1.0f, false);
-    }
-    if (n < 3) return 0.0f;
-    float cx = 0.0f, cy = 0.0f, cz = 0.0f;
-    for (int k = 1; k + 1 < n; ++k) {
-        float e1[3], e2[3];
-        for (int j = 0; j < 3; ++j) { e1[j] = A[k][j] - A[0][j]; e2[j] = A[k + 1][j] - A[0][j]; }
-        cx = cx + (e1[1] * e2[2] - e1[2] * e2[1]);
-        cy = cy + (e1[2] * e2[0] - e1[0] * e2[2]);
-        cz = cz + (e1[0] * e2[1] - e1[1] * e2[0]);
-    }
-    return 0.5f * sqrtf((cx * cx + cy * cy) + cz * cz);
-}
-
-// ------------------------------------------------------------------------------------
-// prep kernels
-// ------------------------------------------------------------------------------------
-__global__ void k_fiber_seg_counts(const int64_t* __restrict__ off, int64_t F, uint32_t* __restrict__ cnt) {
-    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f < F) {
-        int64_t c = off[f + 1] - off[f] - 1;
-        cnt[f] = (uint32_t)(c > 0 ? c : 0);
-    }
-}
-
-// rec_a = (A.xyz, r_g), rec_b = (B.xyz, w) in grid coordinates
-__global__ void k_prep_fibers(const float4* __restrict__ ctrl, const int64_t* __restrict__ off,
-                              const uint32_t* __restrict__ seg_start, int64_t F, const uint32_t* __restrict__ seg_total,
-                              const float* __restrict__ weights, uint32_t np, GridDev g, float4* __restrict__ ra,
-                              float4* __restrict__ rb, uint32_t* __restrict__ err) {
-    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p == 0 && *seg_total != np) atomicOr(err, 1u);
-    if (p >= np) return;
-    // last fiber with seg_start <= p (fibers without segments share the next start)
-    int64_t lo = 0, hi = F;   // upper_bound in [0, F)
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (seg_start[mid] <= p) lo = mid + 1; else hi = mid;
-    }
-    int64_t f = lo - 1;
-    if (f < 0) { atomicOr(err, 1u); return; }
-    int64_t c = off[f] + (int64_t)(p - seg_start[f]);
-    if (c + 1 >= off[f + 1]) { atomicOr(err, 1u); return; }
-    float4 pa = ctrl[c], pb = ctrl[c + 1];
-    float4 A, B;
-    A.x = (pa.x - g.o[0]) * g.s; A.y = (pa.y - g.o[1]) * g.s; A.z = (pa.z - g.o[2]) * g.s;
-    B.x = (pb.x - g.o[0]) * g.s; B.y = (pb.y - g.o[1]) * g.s; B.z = (pb.z - g.o[2]) * g.s;
-    A.w = ((pa.w + pb.w) * 0.5f) * g.s;
-    B.w = weights ? weights[p] : 1.0f;
-    ra[p] = A;
-    rb[p] = B;
-}
-
-// tri records: (U0, w), (U1, 0), (U2, 0)
-__global__ void k_prep_tris(const float4* __restrict__ tv, const float* __restrict__ weights, uint32_t np, GridDev g,
-                            float4* __restrict__ r0, float4* __restrict__ r1, float4* __restrict__ r2) {
-    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
-    float4 v0 = tv[3 * (size_t)p], v1 = tv[3 * (size_t)p + 1], v2 = tv[3 * (size_t)p + 2];
-    float4 a, b, c;
-    a.x = (v0.x - g.o[0]) * g.s; a.y = (v0.y - g.o[1]) * g.s; a.z = (v0.z - g.o[2]) * g.s;
-    b.x = (v1.x - g.o[0]) * g.s; b.y = (v1.y - g.o[1]) * g.s; b.z = (v1.z - g.o[2]) * g.s;
-    c.x = (v2.x - g.o[0]) * g.s; c.y = (v2.y - g.o[1]) * g.s; c.z = (v2.z - g.o[2]) * g.s;
-    a.w = weights ? weights[p] : 1.0f;
-    b.w = 0.0f;
-    c.w = 0.0f;
-    r0[p] = a; r1[p] = b; r2[p] = c;
-}
-
-// voxel range of a primitive: [lo, hi] per axis, empty when lo > hi on an axis
-struct Range {
-    int lo[3], n[3];
-    long long total;
-};
-__device__ __forceinline__ Range make_range(const float* mn, const float* mx, int R) {
-    Range r;
-    r.total = 1;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        float fl = floorf(mn[i]), fh = floorf(mx[i]);
-        int lo = fl < 0.0f ? 0 : (fl > (float)(R - 1) ? R : (int)fl);
-        int hi = fh < 0.0f ? -1 : (fh > (float)(R - 1) ? R - 1 : (int)fh);
-        r.lo[i] = lo;
-        r.n[i] = hi >= lo ? hi - lo + 1 : 0;
-        r.total *= r.n[i];
-    }
-    return r;
-}
-
-// conservative voxel-level tests (never reject a voxel with a set sub-cell)
-__device__ __forceinline__ float capsule_margin(float rg) { return 2e-3f * fmax2(1.0f, rg) + 1e-4f; }
-
-__device__ __forceinline__ Range capsule_range(float4 A, float4 B, int R) {
-    const float rc = A.w + capsule_margin(A.w) + 0.01f;
-    float mn[3] = {fmin2(A.x, B.x) - rc, fmin2(A.y, B.y) - rc, fmin2(A.z, B.z) - rc};
-    float mx[3] = {fmax2(A.x, B.x) + rc, fmax2(A.y, B.y) + rc, fmax2(A.z, B.z) + rc};
-    return make_range(mn, mx, R);
-}
-
-__device__ __forceinline__ bool capsule_voxel_candidate(float4 A, float4 B, int vi, int vj, int vk) {
-    float a[3] = {A.x - (float)vi, A.y - (float)vj, A.z - (float)vk};
-    float b[3] = {B.x - (float)vi, B.y - (float)vj, B.z - (float)vk};
-    float r = A.w + capsule_margin(A.w);
-    const float lo[3] = {0.0f, 0.0f, 0.0f}, hi[3] = {1.0f, 1.0f, 1.0f};
-    return capsule_box(a, b, r * r, lo, hi);
-}
-
-__device__ __forceinline__ Range tri_range(float4 a, float4 b, float4 c, int R) {
-    const float m = 0.01f;
-    float mn[3] = {fmin2(fmin2(a.x, b.x), c.x) - m, fmin2(fmin2(a.y, b.y), c.y) - m, fmin2(fmin2(a.z, b.z), c.z) - m};
-    float mx[3] = {fmax2(fmax2(a.x, b.x), c.x) + m, fmax2(fmax2(a.y, b.y), c.y) + m, fmax2(fmax2(a.z, b.z), c.z) + m};
-    return make_range(mn, mx, R);
-}
-
-__device__ __forceinline__ void tri_local(float4 a, float4 b, float4 c, int vi, int vj, int vk, float v[3][3],
-                                          float f[3][3]) {
-    v[0][0] = a.x - (float)vi; v[0][1] = a.y - (float)vj; v[0][2] = a.z - (float)vk;
-    v[1][0] = b.x - (float)vi; v[1][1] = b.y - (float)vj; v[1][2] = b.z - (float)vk;
-    v[2][0] = c.x - (float)vi; v[2][1] = c.y - (float)vj; v[2][2] = c.z - (float)vk;
-    f[0][0] = b.x - a.x; f[0][1] = b.y - a.y; f[0][2] = b.z - a.z;
-    f[1][0] = c.x - b.x; f[1][1] = c.y - b.y; f[1][2] = c.z - b.z;
-    f[2][0] = a.x - c.x; f[2][1] = a.y - c.y; f[2][2] = a.z - c.z;
-}
-
-__device__ __forceinline__ bool tri_voxel_candidate(float4 a, float4 b, float4 c, int vi, int vj, int vk) {
-    float v[3][3], f[3][3];
-    tri_local(a, b, c, vi, vj, vk, v, f);
-    const float ctr[3] = {0.5f, 0.5f, 0.5f};
-    return tri_box(v, f, ctr, 0.5f + 2e-3f);
-}
-
-// ------------------------------------------------------------------------------------
-// count / emit: warp per primitive over its voxel range
-// ------------------------------------------------------------------------------------
-template <bool FIBER, bool EMIT>
-__global__ void __launch_bounds__(EMIT_WARPS * 32) k_candidates(const float4* __restrict__ r0,
-                                                                const float4* __restrict__ r1,
-                                                                const float4* __restrict__ r2, uint32_t np, int R,
-                                                                uint32_t* __restrict__ counts,
-                                                                const uint32_t* __restrict__ offs,
-                                                                uint32_t* __restrict__ keys,
-                                                                uint32_t* __restrict__ vals) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t warps = gridDim.x * EMIT_WARPS;
-    for (uint32_t p = blockIdx.x * EMIT_WARPS + (threadIdx.x >> 5); p < np; p += warps) {
-        float4 a = r0[p], b = r1[p], c;
-        Range rg;
-        if (FIBER) {
-            rg = capsule_range(a, b, R);
-        } else {
-            c = r2[p];
-            rg = tri_range(a, b, c, R);
-        }
-        uint32_t n = 0;
-        uint32_t base = EMIT ? offs[p] : 0u;
-        const long long tot = rg.total;
-        for (long long idx0 = 0; idx0 < tot; idx0 += 32) {
-            long long idx = idx0 + lane;
-            bool hit = false;
-            int vi = 0, vj = 0, vk = 0;
-            if (idx < tot) {
-                int ix = (int)(idx % rg.n[0]);
-                long long t = idx / rg.n[0];
-                int iy = (int)(t % rg.n[1]);
-                int iz = (int)(t / rg.n[1]);
-                vi = rg.lo[0] + ix; vj = rg.lo[1] + iy; vk = rg.lo[2] + iz;
-                hit = FIBER ? capsule_voxel_candidate(a, b, vi, vj, vk) : tri_voxel_candidate(a, b, c, vi, vj, vk);
-            }
-            uint32_t bal = __ballot_sync(0xffffffffu, hit);
-            if (EMIT && hit) {
-                uint32_t pos = base + n + __popc(bal & ((1u << lane) - 1u));
-                keys[pos] = vx_morton3((uint32_t)vi, (uint32_t)vj, (uint32_t)vk);
-                vals[pos] = p;
-            }
-            n += __popc(bal);
-        }
-        if (!EMIT && lane == 0) counts[p] = n;
-    }
-}
-
-// ------------------------------------------------------------------------------------
-// segments
-// ------------------------------------------------------------------------------------
-__global__ void k_head_flags(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ flags) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
-}
-
-__global__ void k_head_starts(const uint32_t* __restrict__ keys, uint32_t n, const uint32_t* __restrict__ idx,
-                              const uint32_t* __restrict__ nseg, uint32_t* __restrict__ starts) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && (i == 0 || keys[i] != keys[i - 1])) starts[idx[i]] = i;
-    if (i == 0) starts[*nseg] = n;
-}
-
-// ------------------------------------------------------------------------------------
-// reduce: warp per candidate voxel
-// lane l owns sub-cells sz = l >> 2, sy = 2 (l & 3) + {0,1}, sx = 0..7 (16 bits)
-// ------------------------------------------------------------------------------------
-__device__ __forceinline__ void write_seg(SegOut out, uint32_t seg, uint32_t key, uint32_t chunk, const float* acc) {
-    const int lane = threadIdx.x & 31;
-    // word sz = lanes 4 sz .. 4 sz + 3, chunk q at bits 16 q
-    uint64_t w = (uint64_t)chunk << (16 * (lane & 3));
-    w |= __shfl_down_sync(0xffffffffu, w, 1);
-    w |= __shfl_down_sync(0xffffffffu, w, 2);
-    bool nz = __any_sync(0xffffffffu, chunk != 0);
-    if ((lane & 3) == 0) out.mask[(size_t)seg * 8 + (lane >> 2)] = w;
-    if (lane == 0) {
-        out.key[seg] = key;
-        out.mass[seg] = acc[0];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) out.moment[(size_t)seg * 6 + c] = acc[1 + c];
-        out.nonzero[seg] = nz ? 1u : 0u;
-    }
-}
-
-__global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_fibers(const uint32_t* __restrict__ keys,
-                                                                  const uint32_t* __restrict__ prims,
-                                                                  const uint32_t* __restrict__ starts,
-                                                                  const uint32_t* __restrict__ nseg_p,
-                                                                  const float4* __restrict__ ra,
-                                                                  const float4* __restrict__ rb, SegOut out) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t nseg = *nseg_p;
-    const int sz = lane >> 2, sy0 = (lane & 3) * 2;
-    const uint32_t warps = gridDim.x * RED_WARPS;
-    __shared__ CapsuleScratch scratch[RED_WARPS];
-    CapsuleScratch& cs = scratch[threadIdx.x >> 5];
-    for (uint32_t seg = blockIdx.x * RED_WARPS + (threadIdx.x >> 5); seg < nseg; seg += warps) {
-        const uint32_t beg = starts[seg], end = starts[seg + 1];
-        const uint32_t key = keys[beg];
-        const float fx = (float)vx_compact1by2(key), fy = (float)vx_compact1by2(key >> 1),
-                    fz = (float)vx_compact1by2(key >> 2);
-        uint32_t chunk = 0;
-        bool full = false;
-        float acc[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (uint32_t base = beg; base < end; base += 32) {
-            const uint32_t cnt = min(32u, end - base);
-            float q[7] = {0, 0, 0, 0, 0, 0, 0};
-            if (lane < cnt) {
-                const uint32_t p = prims[base + lane];
-                const float4 A = ra[p], B = rb[p];
-                float a[3] = {A.x - fx, A.y - fy, A.z - fz};
-                float b[3] = {B.x - fx, B.y - fy, B.z - fz};
-                float mu = capsule_measure(a, b, A.w);
-                float dg[3] = {B.x - A.x, B.y - A.y, B.z - A.z};
-                float dn = sqrtf((dg[0] * dg[0] + dg[1] * dg[1]) + dg[2] * dg[2]);
-                float t[3] = {0.0f, 0.0f, 0.0f};
-                if (dn > 0.0f) { t[0] = dg[0] / dn; t[1] = dg[1] / dn; t[2] = dg[2] / dn; }
-                float c = B.w * mu;
-                q[0] = c;
-                q[1] = c * (t[0] * t[0]);
-                q[2] = c * (t[1] * t[1]);
-                q[3] = c * (t[2] * t[2]);
-                q[4] = c * (t[0] * t[1]);
-                q[5] = c * (t[0] * t[2]);
-                q[6] = c * (t[1] * t[2]);
-            }
-            for (uint32_t j = 0; j < cnt; ++j) {
-#pragma unroll
-                for (int c = 0; c < 7; ++c) acc[c] = acc[c] + __shfl_sync(0xffffffffu, q[c], j);
-                if (!full) {
-                    const uint32_t p = prims[base + j];
-                    const float4 A = ra[p], B = rb[p];
-                    float a[3] = {A.x - fx, A.y - fy, A.z - fz};
-                    float b[3] = {B.x - fx, B.y - fy, B.z - fz};
-                    chunk = capsule_bits16(a, b, A.w * A.w, sy0, sz, chunk, cs);
-                    full = __all_sync(0xffffffffu, chunk == 0xffffu);
-                }
-            }
-        }
-        write_seg(out, seg, key, chunk, acc);
-    }
-}
-
-__global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_tris(const uint32_t* __restrict__ keys,
-                                                                const uint32_t* __restrict__ prims,
-                                                                const uint32_t* __restrict__ starts,
-                                                                const uint32_t* __restrict__ nseg_p,
-                                                                const float4* __restrict__ r0,
-                                                                const float4* __restrict__ r1,
-                                                                const float4* __restrict__ r2, SegOut out) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t nseg = *nseg_p;
-    const int sz = lane >> 2, sy0 = (lane & 3) * 2;
-    const uint32_t warps = gridDim.x * RED_WARPS;
-    for (uint32_t seg = blockIdx.x * RED_WARPS + (threadIdx.x >> 5); seg < nseg; seg += warps) {
-        const uint32_t beg = starts[seg], end = starts[seg + 1];
-        const uint32_t key = keys[beg];
-        const uint32_t ix = vx_compact1by2(key), iy = vx_compact1by2(key >> 1), iz = vx_compact1by2(key >> 2);
-        uint32_t chunk = 0;
-        bool full = false;
-        float acc[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (uint32_t base = beg; base < end; base += 32) {
-            const uint32_t cnt = min(32u, end - base);
-            float q[7] = {0, 0, 0, 0, 0, 0, 0};
-            if (lane < cnt) {
-                const uint32_t p = prims[base + lane];
-                const float4 a = r0[p], b = r1[p], c = r2[p];
-                float v[3][3], f[3][3];
-                tri_local(a, b, c, (int)ix, (int)iy, (int)iz, v, f);
-                float mu = tri_measure(v);
-                float n0 = f[0][1] * f[1][2] - f[0][2] * f[1][1];
-                float n1 = f[0][2] * f[1][0] - f[0][0] * f[1][2];
-                float n2 = f[0][0] * f[1][1] - f[0][1] * f[1][0];
-                float nn = sqrtf((n0 * n0 + n1 * n1) + n2 * n2);
-                float t[3] = {0.0f, 0.0f, 0.0f};
-                if (nn > 0.0f) { t[0] = n0 / nn; t[1] = n1 / nn; t[2] = n2 / nn; }
-                float cc = a.w * mu;
-                q[0] = cc;
-                q[1] = cc * (t[0] * t[0]);
-                q[2] = cc * (t[1] * t[1]);
-                q[3] = cc * (t[2] * t[2]);
-                q[4] = cc * (t[0] * t[1]);
-                q[5] = cc * (t[0] * t[2]);
-                q[6] = cc * (t[1] * t[2]);
-            }
-            for (uint32_t j = 0; j < cnt; ++j) {
-#pragma unroll
-                for (int c = 0; c < 7; ++c) acc[c] = acc[c] + __shfl_sync(0xffffffffu, q[c], j);
-                if (!full) {
-                    const uint32_t p = prims[base + j];
-                    const float4 a = r0[p], b = r1[p], c = r2[p];
-                    float v[3][3], f[3][3];
-                    tri_local(a, b, c, (int)ix, (int)iy, (int)iz, v, f);
-                    chunk |= tri_bits16(v, f, sy0, sz);
-                    full = __all_sync(0xffffffffu, chunk == 0xffffu);
-                }
-            }
-        }
-        write_seg(out, seg, key, chunk, acc);
-    }
-}
-
-// ------------------------------------------------------------------------------------
-// finalize: compaction + occupancy + lobe
-// ------------------------------------------------------------------------------------
-__device__ __forceinline__ void mask_counts(const uint64_t* m, uint16_t& occ, uint8_t* proj) {
-    int o = 0, yz = 0, xz = 0;
-    uint64_t orz = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        uint64_t x = m[w];
-        o += __popcll(x);
-        orz |= x;
-        // along x: a row (byte) is occupied if any of its bits is
-        uint64_t t = x | (x >> 4);
-        t |= t >> 2;
-        t |= t >> 1;
-        yz += __popcll(t & 0x0101010101010101ull);
-        // along y: OR of the 8 rows
-        uint64_t r = x | (x >> 32);
-        r |= r >> 16;
-        r |= r >> 8;
-        xz += __popc((uint32_t)(r & 0xffu));
-    }
-    occ = (uint16_t)o;
-    proj[0] = (uint8_t)yz;
-    proj[1] = (uint8_t)xz;
-    proj[2] = (uint8_t)__popcll(orz);
-}
-
-__device__ __forceinline__ void write_lobe(float m, const float* M, float* lobe, float* comp, uint8_t* cnt) {
-    if (m > 0.0f) {
-        float S[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) S[c] = M[c] / m;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) lobe[c] = S[c];
-        lobe[6] = m;
-        comp[0] = sqrtf(S[0]);
-        comp[1] = sqrtf(S[1]);
-        comp[2] = sqrtf(S[2]);
-        float pxy = S[0] * S[1], pxz = S[0] * S[2], pyz = S[1] * S[2];
-        comp[3] = pxy > 0.0f ? S[3] / sqrtf(pxy) : 0.0f;
-        comp[4] = pxz > 0.0f ? S[4] / sqrtf(pxz) : 0.0f;
-        comp[5] = pyz > 0.0f ? S[5] / sqrtf(pyz) : 0.0f;
-        *cnt = 1;
-    } else {
-#pragma unroll
-        for (int c = 0; c < 7; ++c) lobe[c] = 0.0f;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) comp[c] = 0.0f;
-        *cnt = 0;
-    }
-}
-
-__global__ void k_finalize(SegOut in, const uint32_t* __restrict__ nseg_p, const uint32_t* __restrict__ dst,
-                           vx_level L) {
-    const uint32_t nseg = *nseg_p;
-    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
-        if (!in.nonzero[s]) continue;
-        const uint32_t o = dst[s];
-        L.keys[o] = (uint64_t)in.key[s];
-        uint64_t m[8];
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            m[w] = in.mask[(size_t)s * 8 + w];
-            L.mask[(size_t)o * 8 + w] = m[w];
-        }
-        float mass = in.mass[s];
-        float M[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            M[c] = in.moment[(size_t)s * 6 + c];
-            L.moment[(size_t)o * 6 + c] = M[c];
-        }
-        L.mass[o] = mass;
-        uint16_t occ;
-        uint8_t pj[3];
-        mask_counts(m, occ, pj);
-        L.occ[o] = occ;
-        L.occ_proj[(size_t)o * 3 + 0] = pj[0];
-        L.occ_proj[(size_t)o * 3 + 1] = pj[1];
-        L.occ_proj[(size_t)o * 3 + 2] = pj[2];
-        write_lobe(mass, M, L.lobes + (size_t)o * 7, L.compact + (size_t)o * 6, L.lobe_count + o);
-    }
-}
-
-inline unsigned grid_for(size_t n, int threads) {
-    size_t b = (n + threads - 1) / threads;
-    if (b < 1) b = 1;
-    if (b > 0x7fffffff) b = 0x7fffffff;
-    return (unsigned)b;
-}
-
-}  // namespace
+#include "vx_level0.cuh"
 
 extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
                                  void* stream, vx_level* out0) {
@@ -1069,87 +182,86 @@ __global__ void k_key_shift_flags(const uint64_t* __restrict__ keys, uint32_t n,
     if (i < n) flags[i] = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift)) ? 1u : 0u;
 }
 
-// level-0 adjoints: g = grad_0 (init) or g += grad_l[parent index]
+// level-0 adjoints (FP64): g = grad_0 (init) or g += grad_l[parent index]
 __global__ void k_bcast(const uint32_t* __restrict__ excl, const uint32_t* __restrict__ flags, uint32_t n,
                         const float* __restrict__ gmass, const float* __restrict__ gmom, int init,
-                        float* __restrict__ gm, float* __restrict__ gM) {
+                        double* __restrict__ gm, double* __restrict__ gM) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t p = init ? i : excl[i] + flags[i] - 1u;
     if (init) {
-        gm[i] = gmass[p];
+        gm[i] = (double)gmass[p];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) gM[(size_t)i * 6 + c] = gmom[(size_t)p * 6 + c];
+        for (int c = 0; c < 6; ++c) gM[(size_t)i * 6 + c] = (double)gmom[(size_t)p * 6 + c];
     } else {
-        gm[i] = gm[i] + gmass[p];
+        gm[i] = gm[i] + (double)gmass[p];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) gM[(size_t)i * 6 + c] = gM[(size_t)i * 6 + c] + gmom[(size_t)p * 6 + c];
+        for (int c = 0; c < 6; ++c) gM[(size_t)i * 6 + c] = gM[(size_t)i * 6 + c] + (double)gmom[(size_t)p * 6 + c];
     }
 }
 
 // d/d(A, B, r, w) of  w * pi r^2 len * (gm + gM . T(t))  for one (segment, voxel) pair
-// (grid units); out: dA[3], dB[3], dr, dw
-__device__ __forceinline__ void pair_grad(float4 A, float4 B, int vi, int vj, int vk, float gm, const float* gM,
-                                          float* out) {
+// (grid units); out: dA[3], dB[3], dr, dw.  FP64: the end-point terms of a piece that
+// crosses a plane almost parallel to it are large and cancel between the two voxels
+// sharing the plane, so FP32 would leave an error of a few 1e-6 of their size.
+__device__ __forceinline__ void pair_grad(float4 Af, float4 Bf, int vi, int vj, int vk, double gm, const double* gM,
+                                          double* out) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) out[c] = 0.0f;
-    const float a[3] = {A.x - (float)vi, A.y - (float)vj, A.z - (float)vk};
-    const float d[3] = {B.x - A.x, B.y - A.y, B.z - A.z};
-    float t0 = 0.0f, t1 = 1.0f;
+    for (int c = 0; c < 8; ++c) out[c] = 0.0;
+    const double A[3] = {Af.x, Af.y, Af.z}, B[3] = {Bf.x, Bf.y, Bf.z};
+    const double a[3] = {A[0] - vi, A[1] - vj, A[2] - vk};
+    const double d[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+    double t0 = 0.0, t1 = 1.0;
     int ax0 = -1, ax1 = -1;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        if (d[i] == 0.0f) {
-            if (a[i] < 0.0f || a[i] > 1.0f) return;
+        if (d[i] == 0.0) {
+            if (a[i] < 0.0 || a[i] > 1.0) return;
         } else {
-            float ta = (0.0f - a[i]) / d[i], tb = (1.0f - a[i]) / d[i];
-            float tn = d[i] > 0.0f ? ta : tb, tf = d[i] > 0.0f ? tb : ta;
+            const double ta = -a[i] / d[i], tb = (1.0 - a[i]) / d[i];
+            const double tn = d[i] > 0.0 ? ta : tb, tf = d[i] > 0.0 ? tb : ta;
             if (tn > t0) { t0 = tn; ax0 = i; }
             if (tf < t1) { t1 = tf; ax1 = i; }
         }
     }
     if (t1 <= t0) return;
-    const float r = A.w, w = B.w;
-    const float dn = sqrtf((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
-    const float t[3] = {d[0] / dn, d[1] / dn, d[2] / dn};
-    const float len = (t1 - t0) * dn;
-    const float mu = (kPi * (r * r)) * len;
-    float G = gm;
-    G = G + gM[0] * (t[0] * t[0]);
-    G = G + gM[1] * (t[1] * t[1]);
-    G = G + gM[2] * (t[2] * t[2]);
-    G = G + gM[3] * (t[0] * t[1]);
-    G = G + gM[4] * (t[0] * t[2]);
-    G = G + gM[5] * (t[1] * t[2]);
+    const double r = Af.w, w = Bf.w;
+    const double pi = 3.14159265358979323846;
+    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const double t[3] = {d[0] / dn, d[1] / dn, d[2] / dn};
+    const double len = (t1 - t0) * dn;
+    const double mu = pi * r * r * len;
+    const double G = gm + gM[0] * t[0] * t[0] + gM[1] * t[1] * t[1] + gM[2] * t[2] * t[2] + gM[3] * t[0] * t[1] +
+                     gM[4] * t[0] * t[2] + gM[5] * t[1] * t[2];
     out[7] = mu * G;                       // d/dw
-    out[6] = w * (2.0f * mu / r) * G;      // d/dr
-    float cA[3] = {0.0f, 0.0f, 0.0f}, cB[3] = {0.0f, 0.0f, 0.0f};
+    out[6] = w * (2.0 * mu / r) * G;       // d/dr
+    double cA[3] = {0.0, 0.0, 0.0}, cB[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-        const float te = e == 0 ? t0 : t1;
+        const double te = e == 0 ? t0 : t1;
         const int ax = e == 0 ? ax0 : ax1;
-        const float sg = e == 0 ? -1.0f : 1.0f;
+        const double sg = e == 0 ? -1.0 : 1.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            float gA = (1.0f - te) * t[k], gB = te * t[k];
+            double gA = (1.0 - te) * t[k], gB = te * t[k];
             if (ax == k) {
-                gA -= (1.0f - te) * dn / d[k];
+                gA -= (1.0 - te) * dn / d[k];
                 gB -= te * dn / d[k];
             }
             cA[k] += sg * gA;
             cB[k] += sg * gB;
         }
     }
-    const float kmu = w * (kPi * (r * r)) * G;
-    float gt[3];
-    gt[0] = 2.0f * gM[0] * t[0] + gM[3] * t[1] + gM[4] * t[2];
-    gt[1] = gM[3] * t[0] + 2.0f * gM[1] * t[1] + gM[5] * t[2];
-    gt[2] = gM[4] * t[0] + gM[5] * t[1] + 2.0f * gM[2] * t[2];
-    const float tg = t[0] * gt[0] + t[1] * gt[1] + t[2] * gt[2];
-    const float wm = w * mu;
+    const double kmu = w * pi * r * r * G;
+    double gt[3];
+    gt[0] = 2.0 * gM[0] * t[0] + gM[3] * t[1] + gM[4] * t[2];
+    gt[1] = gM[3] * t[0] + 2.0 * gM[1] * t[1] + gM[5] * t[2];
+    gt[2] = gM[4] * t[0] + gM[5] * t[1] + 2.0 * gM[2] * t[2];
+    const double tg = t[0] * gt[0] + t[1] * gt[1] + t[2] * gt[2];
+    const double wm = w * mu;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float gd = wm * (gt[k] - t[k] * tg) / dn;
+        const double gd = wm * (gt[k] - t[k] * tg) / dn;
         out[k] = kmu * cA[k] - gd;
         out[3 + k] = kmu * cB[k] + gd;
     }
@@ -1171,21 +283,21 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_fibers(const float4
                                                                     const uint32_t* __restrict__ cnt,
                                                                     const uint32_t* __restrict__ pkeys,
                                                                     const uint64_t* __restrict__ keys0, uint32_t V0,
-                                                                    const float* __restrict__ gm,
-                                                                    const float* __restrict__ gM,
-                                                                    float* __restrict__ seg_grad) {
+                                                                    const double* __restrict__ gm,
+                                                                    const double* __restrict__ gM,
+                                                                    double* __restrict__ seg_grad) {
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * EMIT_WARPS;
     for (uint32_t p = blockIdx.x * EMIT_WARPS + (threadIdx.x >> 5); p < np; p += warps) {
         const float4 A = ra[p], B = rb[p];
         const uint32_t beg = offs[p], n = cnt[p];
-        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (uint32_t j = lane; j < n; j += 32) {
             const uint32_t key = pkeys[beg + j];
             const int64_t v = find_key64(keys0, V0, (uint64_t)key);
             if (v < 0) continue;
-            float g[8];
-            float gMv[6];
+            double g[8];
+            double gMv[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c) gMv[c] = gM[(size_t)v * 6 + c];
             pair_grad(A, B, (int)vx_compact1by2(key), (int)vx_compact1by2(key >> 1), (int)vx_compact1by2(key >> 2),
@@ -1203,7 +315,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_fibers(const float4
 
 // thread per control point: world-unit gradients from the segment before and after it
 __global__ void k_adjoint_ctrl(const int64_t* __restrict__ off, int64_t F, const uint32_t* __restrict__ seg_start,
-                               int64_t P, const float* __restrict__ seg_grad, float s, float4* __restrict__ gctrl) {
+                               int64_t P, const double* __restrict__ seg_grad, float s, float4* __restrict__ gctrl) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P) return;
     int64_t lo = 0, hi = F;       // last fiber with off[f] <= c
@@ -1216,26 +328,26 @@ __global__ void k_adjoint_ctrl(const int64_t* __restrict__ off, int64_t F, const
     if (f >= 0 && c < off[f + 1]) {
         const bool has_prev = c > off[f];
         const bool has_next = c + 1 < off[f + 1];
-        float px = 0.0f, py = 0.0f, pz = 0.0f, pr = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f, nr = 0.0f;
+        double px = 0.0, py = 0.0, pz = 0.0, pr = 0.0, nx = 0.0, ny = 0.0, nz = 0.0, nr = 0.0;
         if (has_prev) {
-            const float* q = seg_grad + (size_t)(seg_start[f] + (uint32_t)(c - 1 - off[f])) * 8;
+            const double* q = seg_grad + (size_t)(seg_start[f] + (uint32_t)(c - 1 - off[f])) * 8;
             px = q[3]; py = q[4]; pz = q[5]; pr = q[6];
         }
         if (has_next) {
-            const float* q = seg_grad + (size_t)(seg_start[f] + (uint32_t)(c - off[f])) * 8;
+            const double* q = seg_grad + (size_t)(seg_start[f] + (uint32_t)(c - off[f])) * 8;
             nx = q[0]; ny = q[1]; nz = q[2]; nr = q[6];
         }
-        g.x = (px + nx) * s;
-        g.y = (py + ny) * s;
-        g.z = (pz + nz) * s;
-        g.w = (pr + nr) * (0.5f * s);
+        g.x = (float)((px + nx) * (double)s);
+        g.y = (float)((py + ny) * (double)s);
+        g.z = (float)((pz + nz) * (double)s);
+        g.w = (float)((pr + nr) * (0.5 * (double)s));
     }
     gctrl[c] = g;
 }
 
-__global__ void k_adjoint_weights(const float* __restrict__ seg_grad, uint32_t np, float* __restrict__ gw) {
+__global__ void k_adjoint_weights(const double* __restrict__ seg_grad, uint32_t np, float* __restrict__ gw) {
     uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < np) gw[p] = seg_grad[(size_t)p * 8 + 7];
+    if (p < np) gw[p] = (float)seg_grad[(size_t)p * 8 + 7];
 }
 
 }  // namespace
@@ -1272,11 +384,11 @@ extern "C" vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, co
     // ---- level-0 adjoints (coarse adjoints broadcast down) ------------------------------
     VX_TRY(vx_ws_ensure(ctx, WS_LOD_FLAGS, (size_t)std::max<uint32_t>(V0, 1) * 4, s));
     VX_TRY(vx_ws_ensure(ctx, WS_LOD_IDX, (size_t)std::max<uint32_t>(V0, 1) * 4, s));
-    VX_TRY(vx_ws_ensure(ctx, WS_LOD_TMP, (size_t)std::max<uint32_t>(V0, 1) * 28, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_LOD_TMP, (size_t)std::max<uint32_t>(V0, 1) * 56, s));
     uint32_t* flags = (uint32_t*)ctx->ws[WS_LOD_FLAGS].p;
     uint32_t* excl = (uint32_t*)ctx->ws[WS_LOD_IDX].p;
-    float* gm = (float*)ctx->ws[WS_LOD_TMP].p;
-    float* gM = gm + V0;
+    double* gm = (double*)ctx->ws[WS_LOD_TMP].p;
+    double* gM = gm + V0;
     if (V0) {
         VX_LAUNCH(ctx, ST_LOD_HEADS, s, k_bcast<<<grid_for(V0, 256), 256, 0, s>>>(excl, flags, V0, grad_mass[0],
                                                                                  grad_moment[0], 1, gm, gM));
@@ -1324,8 +436,8 @@ extern "C" vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, co
         VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
                                        r0, r1, nullptr, np, (int)R, nullptr, offs, k0, v0));
     // ---- per-segment gradients, then the control-point scatter ---------------------------
-    VX_TRY(vx_ws_ensure(ctx, WS_SEG_OUT, (size_t)np * 32, s));
-    float* seg_grad = (float*)ctx->ws[WS_SEG_OUT].p;
+    VX_TRY(vx_ws_ensure(ctx, WS_SEG_OUT, (size_t)np * 64, s));
+    double* seg_grad = (double*)ctx->ws[WS_SEG_OUT].p;
     VX_LAUNCH(ctx, ST_REDUCE_FIBERS, s, k_adjoint_fibers<<<cblocks, EMIT_WARPS * 32, 0, s>>>(
                                             r0, r1, np, offs, cnt, k0, keys0, V0, gm, gM, seg_grad));
     VX_LAUNCH(ctx, ST_FINALIZE, s, k_adjoint_ctrl<<<grid_for((size_t)P, 256), 256, 0, s>>>(
@@ -1349,7 +461,7 @@ namespace {
 constexpr uint32_t NA_MAX_PRIMS = 1u << 16;    // 65,536 segments
 constexpr uint32_t NA_MAX_FIBERS = 1u << 13;   // 8,192 fibers
 constexpr uint32_t NA_MAX_PAIRS = 1u << 21;    // 2,097,152 candidate (voxel, segment) pairs
-constexpr uint32_t NA_MAX_VOXELS = 1u << 19;   // 524,288 level-0 voxels
+constexpr uint32_t NA_MAX_VOXELS = 1u << 18;   // 262,144 level-0 voxels
 
 constexpr size_t na_al(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t NA_RA = 0;
@@ -1361,11 +473,11 @@ constexpr size_t NA_MISC = NA_FS + na_al(4ull * NA_MAX_FIBERS + 4);
 constexpr size_t NA_KEYS = NA_MISC + 256;
 constexpr size_t NA_VALS = NA_KEYS + na_al(4ull * NA_MAX_PAIRS);
 constexpr size_t NA_SEG = NA_VALS + na_al(4ull * NA_MAX_PAIRS);
-constexpr size_t NA_FLAGS = NA_SEG + na_al(32ull * NA_MAX_PRIMS);
+constexpr size_t NA_FLAGS = NA_SEG + na_al(64ull * NA_MAX_PRIMS);
 constexpr size_t NA_EXCL = NA_FLAGS + na_al(4ull * NA_MAX_VOXELS);
 constexpr size_t NA_GM = NA_EXCL + na_al(4ull * NA_MAX_VOXELS);
-constexpr size_t NA_GMM = NA_GM + na_al(4ull * NA_MAX_VOXELS);
-constexpr size_t NA_PART = NA_GMM + na_al(24ull * NA_MAX_VOXELS);
+constexpr size_t NA_GMM = NA_GM + na_al(8ull * NA_MAX_VOXELS);
+constexpr size_t NA_PART = NA_GMM + na_al(48ull * NA_MAX_VOXELS);
 constexpr size_t NA_BYTES = NA_PART + na_al(4ull * (NA_MAX_VOXELS / 2048 + 64));   // ~39 MB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
@@ -1432,11 +544,11 @@ extern "C" vx_status vx_backward_noalloc(const vx_primitives* prims, const vx_gr
     uint32_t* misc = (uint32_t*)(base + NA_MISC);
     uint32_t* k0 = (uint32_t*)(base + NA_KEYS);
     uint32_t* v0 = (uint32_t*)(base + NA_VALS);
-    float* seg_grad = (float*)(base + NA_SEG);
+    double* seg_grad = (double*)(base + NA_SEG);
     uint32_t* flags = (uint32_t*)(base + NA_FLAGS);
     uint32_t* excl = (uint32_t*)(base + NA_EXCL);
-    float* gm = (float*)(base + NA_GM);
-    float* gM = (float*)(base + NA_GMM);
+    double* gm = (double*)(base + NA_GM);
+    double* gM = (double*)(base + NA_GMM);
     uint32_t* part = (uint32_t*)(base + NA_PART);
 
     // the array keeps the previous call's contents: clear the counters and error flag
