@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--fibers-per-ply", type=int, default=64,
+                    help="smaller yarns for profiling captures (64 = the benchmark workload)")
     return ap.parse_args()
 
 
@@ -188,7 +191,7 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
-    w = synth.config2()
+    w = synth.config2(fibers_per_ply=args.fibers_per_ply)
     dirs_np = synth.sample_directions(N_SAMPLES)
     n_prims = w.num_prims
     ctx = vx.Context(dev)
@@ -293,6 +296,11 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": etot / args.steps}
 
+    # ---- batched path vs per-instance plain calls (64 instances of uneven size) ------------
+    batched = None
+    if not args.no_batched:
+        batched = batched_vs_plain(ctx, dev, args.steps)
+
     # ---- roofline of the dominant kernel -------------------------------------------------
     roof = roofline(prof, w, level_sizes, args.steps)
 
@@ -310,7 +318,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "prims": n_prims, "resolution": w.grid.resolution,
+        "config": {"workload": WORKLOAD if args.fibers_per_ply == 64 else
+                   f"{WORKLOAD} [profiling variant: {args.fibers_per_ply} fibers per ply]", "prims": n_prims, "resolution": w.grid.resolution,
                    "K": K_LOBES, "n_samples": N_SAMPLES, "levels": len(level_sizes),
                    "voxels_per_level": level_sizes, "parallelism": f"replicas x{ws}",
                    "l2": "flushed between timed steps (256 MiB write)"},
@@ -321,6 +330,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -328,6 +338,62 @@ def main():
 
 
 # ----------------------------------------------------------------------------------
+BATCH_WORKLOAD = ("64 instances: 32 heightfields of 2k-200k triangles and 32 yarn patches of 10k-400k "
+                  "segments (log-uniform), grids 64^3-1024^3, all LoD levels, K=1")
+
+
+def batched_vs_plain(ctx, dev, steps):
+    """One graph replay of the batched path against a loop of plain vx_voxelize +
+    vx_build_lod calls over the same instances (same GPU, CUDA events)."""
+    import torch
+    ws = synth.config4(seed=4, n_instances=64, min_tris=2000, max_tris=200_000, min_segs=10_000,
+                       max_segs=400_000)
+    insts = []
+    for w in ws:
+        if w.kind == "triangles":
+            insts.append({"kind": "triangles", "grid": w.grid, "tri_verts": torch.from_numpy(w.tri_verts).to(dev)})
+        else:
+            insts.append({"kind": "fibers", "grid": w.grid, "ctrl": torch.from_numpy(w.ctrl).to(dev),
+                          "fiber_offsets": torch.from_numpy(w.fiber_offsets).to(dev),
+                          "num_prims": w.num_prims})
+    nprims = sum(w.num_prims for w in ws)
+    b = ctx.batch(insts)
+
+    def run_batch():
+        b.run()
+
+    def run_plain():
+        outs = []
+        for inst in insts:
+            if inst["kind"] == "triangles":
+                L0 = ctx.voxelize(inst["grid"], tri_verts=inst["tri_verts"])
+            else:
+                L0 = ctx.voxelize(inst["grid"], ctrl=inst["ctrl"], fiber_offsets=inst["fiber_offsets"],
+                                  num_prims=inst["num_prims"])
+            outs.append((L0, ctx.build_lod(L0, K=1)))
+        return outs
+
+    def timed(fn, n):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        e.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(e) / n
+
+    tb = timed(run_batch, steps)
+    tp = timed(run_plain, steps)
+    b.close()
+    return {"workload": BATCH_WORKLOAD, "prims": int(nprims), "batched_ms": tb, "plain_ms": tp,
+            "speedup": tp / tb, "batched_prims_per_s": nprims / (tb * 1e-3),
+            "note": "batched = one captured graph per run; plain = per-instance vx_voxelize + vx_build_lod"}
+
+
 def _source_hash(name):
     h = hashlib.sha256()
     with open(os.path.join(ROOT, "paper_2604_13191_gb300", "csrc", name), "rb") as fh:

@@ -213,6 +213,48 @@ VX_API vx_status vx_backward_noalloc(const vx_primitives* prims, const vx_grid* 
                                      const float* const* grad_moment, void* stream, float* grad_ctrl,
                                      float* grad_weights);
 
+/* ---- batched path ------------------------------------------------------------------
+ * Many instances (meshes and fiber patches of uneven size, each with its own grid) go
+ * through ONE pipeline per primitive kind, from the primitives to every pyramid level
+ * (K = 1 lobes), captured once into a CUDA graph and replayed by vx_batch_run.  The
+ * per-instance results are the same as vx_voxelize + vx_build_lod(K = 1) on that
+ * instance alone (Sec. 3-4; no counterpart of batching in the paper). */
+typedef struct {
+    int32_t kind;          /* VX_TRIANGLES or VX_FIBERS */
+    vx_grid grid;          /* this instance's grid (resolution 1..1024, sub_res 8) */
+    int64_t prim_begin;    /* first primitive in the batch's arrays of that kind */
+    int64_t num_prims;     /* instances of a kind are contiguous and in order */
+    int64_t fiber_begin;   /* fibers: first fiber in the batch's fiber_offsets */
+    int64_t num_fibers;
+} vx_instance;
+
+typedef struct vx_batch vx_batch;
+
+/* Plans a batch: `tris` holds every triangle instance's triangles concatenated and
+ * `fibers` every fiber instance's control points, with global fiber_offsets (either may
+ * be NULL when no instance has that kind).  The primitive arrays are re-read on every
+ * run (their addresses are fixed here, their contents may change).  Creation runs the
+ * pipeline once, synchronising after each counting stage, and sizes every buffer at
+ * (1 + headroom) times the measured count; a later run whose counts exceed them is
+ * clamped and reported as VX_ERR_CAPACITY by vx_batch_level.  At most 255 instances of
+ * each kind.  Errors: VX_ERR_INVALID_ARG, VX_ERR_UNSUPPORTED, VX_ERR_OUT_OF_MEMORY,
+ * VX_ERR_CAPACITY, VX_ERR_CUDA. */
+VX_API vx_status vx_batch_create(vx_context* ctx, const vx_primitives* tris, const vx_primitives* fibers,
+                                 const vx_instance* instances, int num_instances, float headroom, void* stream,
+                                 vx_batch** out);
+
+/* Runs the whole batch on `stream` with no host synchronisation: the first call captures
+ * the pipeline into a CUDA graph (on a private stream), every call launches that graph. */
+VX_API vx_status vx_batch_run(vx_batch* batch, void* stream);
+
+/* View of one instance's level (0 = level 0) from the last run: pointers into the batch's
+ * buffers (block = NULL, owned by the batch, valid until the next run).  Synchronises
+ * `stream` on the first call after a run.  VX_ERR_CAPACITY if that run overflowed. */
+VX_API vx_status vx_batch_level(vx_batch* batch, int instance, int level, void* stream, vx_level* view);
+
+/* Frees the batch's buffers and graph. */
+VX_API void vx_batch_destroy(vx_batch* batch);
+
 /* Returns a level's block to the context's allocator and clears the struct. */
 VX_API void vx_level_release(vx_context* ctx, vx_level* level, void* stream);
 

@@ -61,7 +61,13 @@ class VxAllocator(C.Structure):
 
 EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_lod",
            "vx_level_release", "vx_status_string", "vx_last_cuda_error", "vx_profile_enable",
-           "vx_profile_read", "vx_backward", "vx_backward_noalloc"]
+           "vx_profile_read", "vx_backward", "vx_backward_noalloc", "vx_batch_create", "vx_batch_run",
+           "vx_batch_level", "vx_batch_destroy"]
+
+
+class VxInstance(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("grid", VxGrid), ("prim_begin", C.c_int64), ("num_prims", C.c_int64),
+                ("fiber_begin", C.c_int64), ("num_fibers", C.c_int64)]
 
 
 class VxStageTime(C.Structure):
@@ -109,6 +115,15 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         lib.vx_backward.restype = C.c_int
         lib.vx_backward.argtypes = [P, C.POINTER(VxPrimitives), C.POINTER(VxGrid), P, C.c_int64, C.c_int,
                                     C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), P, P, P]
+        lib.vx_batch_create.restype = C.c_int
+        lib.vx_batch_create.argtypes = [P, C.POINTER(VxPrimitives), C.POINTER(VxPrimitives), C.POINTER(VxInstance),
+                                        C.c_int, C.c_float, P, C.POINTER(C.c_void_p)]
+        lib.vx_batch_run.restype = C.c_int
+        lib.vx_batch_run.argtypes = [P, P]
+        lib.vx_batch_level.restype = C.c_int
+        lib.vx_batch_level.argtypes = [P, C.c_int, C.c_int, P, C.POINTER(VxLevel)]
+        lib.vx_batch_destroy.restype = None
+        lib.vx_batch_destroy.argtypes = [P]
         lib.vx_backward_noalloc.restype = C.c_int
         lib.vx_backward_noalloc.argtypes = [C.POINTER(VxPrimitives), C.POINTER(VxGrid), P, C.c_int64, C.c_int,
                                             C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), P, P, P]
@@ -332,6 +347,35 @@ class Context:
             raise self._err(st, "vx_backward")
         return g_ctrl, g_w
 
+    def batch(self, instances, *, headroom: float = 0.125, stream=None) -> "Batch":
+        """vx_batch_create: instances = list of dicts with kind ("triangles" | "fibers"), grid,
+        and tri_verts [T,3,4] or ctrl [P,4] + fiber_offsets [F+1] (+ optional weights), CUDA
+        tensors.  Returns a Batch whose run() replays one captured graph."""
+        return Batch(self, instances, headroom, stream)
+
+    def _view_level(self, L: VxLevel, keep) -> Level:
+        """Typed tensors over a level whose arrays live in blocks of this context's allocator."""
+        n, K = int(L.num_voxels), int(L.K)
+
+        def find(ptr, nbytes):
+            for base, t in self.alloc.live.items():
+                if base <= ptr and ptr + nbytes <= base + t.numel():
+                    return t, base
+            raise RuntimeError("level array outside the context's blocks")
+
+        def v(ptr, nbytes, dtype, shape):
+            if n == 0:
+                return torch.empty(shape, dtype=dtype, device=self.device)
+            t, base = find(ptr, nbytes)
+            return t[ptr - base: ptr - base + nbytes].view(dtype).view(*shape)
+        return Level(level=int(L.level), resolution=int(L.resolution), num_voxels=n, K=K,
+                     keys=v(L.keys, n * 8, torch.int64, (n,)), mask=v(L.mask, n * 64, torch.int64, (n, 8)),
+                     mass=v(L.mass, n * 4, torch.float32, (n,)), moment=v(L.moment, n * 24, torch.float32, (n, 6)),
+                     occ=v(L.occ, n * 2, torch.int16, (n,)), occ_proj=v(L.occ_proj, n * 3, torch.uint8, (n, 3)),
+                     lobe_count=v(L.lobe_count, n, torch.uint8, (n,)),
+                     lobes=v(L.lobes, n * K * 28, torch.float32, (n, K, 7)),
+                     compact=v(L.compact, n * K * 24, torch.float32, (n, K, 6)), block=None, _c=L)
+
     def build_lod(self, level: Level, *, K: int = 1, dirs=None, num_levels: int = 0,
                   stream=None) -> list:
         """vx_build_lod: levels level+1 .. level+L (L = num_levels, 0 = down to 1^3)."""
@@ -447,3 +491,99 @@ def backward_noalloc(grid, *, ctrl, fiber_offsets, keys0, grad_mass, grad_moment
     if st != 0:
         detail = f"limits {NOALLOC_LIMITS}" if st == 3 else ""
         raise VxError(st, "vx_backward_noalloc", detail)
+
+
+class Batch:
+    """A planned batch (vx_batch_*): one captured CUDA graph runs every instance from its
+    primitives to all of its pyramid levels (K = 1)."""
+
+    def __init__(self, ctx: Context, instances, headroom=0.125, stream=None):
+        self.ctx = ctx
+        lib = ctx.lib
+        tris = [i for i in instances if i["kind"] == "triangles"]
+        fibs = [i for i in instances if i["kind"] == "fibers"]
+        self.keep = []
+        tp = fp = None
+        insts = (VxInstance * len(instances))()
+        tb, fb, ffb, cb = 0, 0, 0, 0
+        order = []
+        # instances of a kind keep their relative order; the C side requires contiguous ranges
+        for k, inst in enumerate(instances):
+            I = insts[k]
+            I.grid = _grid(inst["grid"])
+            if inst["kind"] == "triangles":
+                n = int(inst["tri_verts"].shape[0])
+                I.kind, I.prim_begin, I.num_prims, I.fiber_begin, I.num_fibers = VX_TRIANGLES, tb, n, 0, 0
+                tb += n
+            else:
+                o = inst["fiber_offsets"].cpu()
+                n = int(torch.clamp(o[1:] - o[:-1] - 1, min=0).sum())
+                F = int(o.shape[0] - 1)
+                I.kind, I.prim_begin, I.num_prims, I.fiber_begin, I.num_fibers = VX_FIBERS, fb, n, ffb, F
+                fb += n
+                ffb += F
+            order.append(k)
+        if tris:
+            tv = torch.cat([i["tri_verts"].reshape(-1, 3, 4) for i in tris]).contiguous()
+            tw = None
+            if any(i.get("weights") is not None for i in tris):
+                tw = torch.cat([i["weights"] if i.get("weights") is not None else
+                                torch.ones(i["tri_verts"].shape[0], device=ctx.device) for i in tris]).contiguous()
+            self.keep += [tv, tw]
+            tp = VxPrimitives()
+            tp.kind, tp.num_prims, tp.tri_verts = VX_TRIANGLES, tv.shape[0], tv.data_ptr()
+            tp.weights = None if tw is None else tw.data_ptr()
+        if fibs:
+            ctrls, offs, ws = [], [], []
+            base = 0
+            for i in fibs:
+                o = i["fiber_offsets"].to(torch.int64)
+                o0, o1 = int(o[0]), int(o[-1])
+                c = i["ctrl"].reshape(-1, 4)[o0:o1]
+                offs.append(o[:-1] - o0 + base)
+                ctrls.append(c)
+                base += c.shape[0]
+            offs.append(torch.tensor([base], dtype=torch.int64, device=ctx.device))
+            cc = torch.cat(ctrls).contiguous()
+            oo = torch.cat(offs).contiguous()
+            fw = None
+            if any(i.get("weights") is not None for i in fibs):
+                fw = torch.cat([i["weights"] if i.get("weights") is not None else
+                                torch.ones(int(torch.clamp(i["fiber_offsets"][1:] - i["fiber_offsets"][:-1] - 1,
+                                                           min=0).sum()), device=ctx.device)
+                                for i in fibs]).contiguous()
+            self.keep += [cc, oo, fw]
+            fp = VxPrimitives()
+            fp.kind, fp.num_prims = VX_FIBERS, fb
+            fp.ctrl, fp.num_ctrl, fp.fiber_offsets, fp.num_fibers = cc.data_ptr(), cc.shape[0], oo.data_ptr(), oo.shape[0] - 1
+            fp.weights = None if fw is None else fw.data_ptr()
+        h = C.c_void_p()
+        st = lib.vx_batch_create(ctx.h, None if tp is None else C.byref(tp), None if fp is None else C.byref(fp),
+                                 insts, len(instances), float(headroom), _stream(stream), C.byref(h))
+        if st != 0:
+            raise ctx._err(st, "vx_batch_create")
+        self.h = h
+        self.instances = instances
+
+    def run(self, stream=None):
+        st = self.ctx.lib.vx_batch_run(self.h, _stream(stream))
+        if st != 0:
+            raise self.ctx._err(st, "vx_batch_run")
+
+    def level(self, instance: int, level: int, stream=None) -> Level:
+        L = VxLevel()
+        st = self.ctx.lib.vx_batch_level(self.h, int(instance), int(level), _stream(stream), C.byref(L))
+        if st != 0:
+            raise self.ctx._err(st, "vx_batch_level")
+        return self.ctx._view_level(L, self.keep)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.vx_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -8,7 +8,8 @@
 
 const char* const kStageNames[ST_NSTAGES] = {
     "prep", "candidates_count", "candidates_emit", "scan", "sort_hist", "sort_scatter", "segment_heads",
-    "reduce_fibers", "reduce_tris", "finalize", "lod_counts", "lod_heads", "lod_reduce", "sggx_cluster"};
+    "reduce_fibers", "reduce_tris", "finalize", "lod_counts", "lod_heads", "lod_reduce", "sggx_cluster",
+    "batched_graph"};
 
 static void vx_prof_drain(vx_context* ctx) {
     for (int i = 0; i < ctx->nev; ++i) {

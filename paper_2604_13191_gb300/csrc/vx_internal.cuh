@@ -40,7 +40,7 @@ struct Buf {
 enum VxStage {
     ST_PREP = 0, ST_COUNT, ST_EMIT, ST_SCAN, ST_SORT_HIST, ST_SORT_SCATTER, ST_HEADS,
     ST_REDUCE_FIBERS, ST_REDUCE_TRIS, ST_FINALIZE, ST_LOD_COUNTS, ST_LOD_HEADS, ST_LOD_REDUCE,
-    ST_SGGX_CLUSTER, ST_NSTAGES
+    ST_SGGX_CLUSTER, ST_BATCH, ST_NSTAGES
 };
 extern const char* const kStageNames[ST_NSTAGES];
 
@@ -108,6 +108,18 @@ vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, u
 // Exclusive prefix sum with caller-provided partials (>= ceil(n / 2048) words).
 cudaError_t vx_scan_u32_scratch(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total,
                                 uint32_t* partials, cudaStream_t s);
+
+// Stable LSD radix sort with caller-provided scratch (graph-capturable); optional final
+// pass on the digit lut[value] (255 for the padding value 0xffffffff).
+cudaError_t vx_radix_sort_u32_scratch(uint32_t** keys, uint32_t** vals, uint32_t** keys_alt, uint32_t** vals_alt,
+                                      uint32_t n, int bits, const uint8_t* lut, uint32_t* hist,
+                                      uint32_t* partials, cudaStream_t s);
+
+// One batched LoD step (K = 1) with device-side counts (vx_lod.cu); see its definition.
+cudaError_t vx_lod_step_batched(const vx_level* in, const uint16_t* inst_in, const uint32_t* n_dev, uint32_t cap_in,
+                                vx_level* out, uint16_t* inst_out, uint32_t* np_dev, uint32_t cap_out,
+                                uint32_t* flags, uint32_t* idx, uint32_t* starts, uint32_t* partials, uint32_t* tmp,
+                                uint32_t* err, cudaStream_t s);
 
 // ---- Morton ------------------------------------------------------------------
 __host__ __device__ inline uint32_t vx_part1by2(uint32_t x) {

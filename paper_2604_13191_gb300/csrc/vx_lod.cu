@@ -114,9 +114,11 @@ __device__ __forceinline__ void compact_params(const float* S, float* c) {
     c[5] = pyz > 0.0f ? S[5] / sqrtf(pyz) : 0.0f;
 }
 
-// thread per parent
+// thread per parent (np_dev, when given, overrides np with a device-side count)
 __global__ void k_lod_reduce(LevelIn in, const uint32_t* __restrict__ starts, uint32_t np, vx_level out, int K,
-                             uint32_t* __restrict__ work, uint32_t* __restrict__ nwork) {
+                             uint32_t* __restrict__ work, uint32_t* __restrict__ nwork,
+                             const uint32_t* __restrict__ np_dev) {
+    if (np_dev) np = *np_dev;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
         const uint32_t beg = starts[p], end = starts[p + 1];
         float m = 0.0f;
@@ -473,6 +475,40 @@ __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluste
     }
 }
 
+// ---- batched LoD step (several instances, K = 1, counts on the device) ---------------
+__global__ void k_bparent_flags(const uint64_t* __restrict__ keys, const uint16_t* __restrict__ inst,
+                                const uint32_t* __restrict__ n_dev, uint32_t cap, uint32_t* __restrict__ flags) {
+    const uint32_t n = *n_dev;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x)
+        flags[i] = (i < n && (i == 0 || inst[i] != inst[i - 1] || (keys[i] >> 3) != (keys[i - 1] >> 3))) ? 1u : 0u;
+}
+
+// clamp a device count to a capacity, raising the overflow flag
+__global__ void k_clamp_count(const uint32_t* __restrict__ total, uint32_t cap, uint32_t* __restrict__ n_out,
+                              uint32_t* __restrict__ err) {
+    const uint32_t t = *total;
+    *n_out = t < cap ? t : cap;
+    if (t > cap) atomicOr(err, 2u);
+}
+
+__global__ void k_bparent_starts(const uint64_t* __restrict__ keys, const uint16_t* __restrict__ inst,
+                                 const uint32_t* __restrict__ n_dev, const uint32_t* __restrict__ idx,
+                                 const uint32_t* __restrict__ total, uint32_t cap_out, uint32_t* __restrict__ starts) {
+    const uint32_t n = *n_dev;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const bool head = i == 0 || inst[i] != inst[i - 1] || (keys[i] >> 3) != (keys[i - 1] >> 3);
+        if (head && idx[i] <= cap_out) starts[idx[i]] = i;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && *total <= cap_out) starts[*total] = n;
+}
+
+__global__ void k_bparent_inst(const uint16_t* __restrict__ inst_in, const uint32_t* __restrict__ starts,
+                               const uint32_t* __restrict__ np_dev, uint16_t* __restrict__ inst_out) {
+    const uint32_t np = *np_dev;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x)
+        inst_out[p] = inst_in[starts[p]];
+}
+
 inline unsigned grid_for(size_t n, int threads) {
     size_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -546,7 +582,7 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
         VX_CUDA_TRY(cudaMemsetAsync(misc + 40, 0, 4, s));
         vx_stage_units(ctx, ST_LOD_REDUCE, ncur);
         VX_LAUNCH(ctx, ST_LOD_REDUCE, s, k_lod_reduce<<<(unsigned)std::min<size_t>(grid_for(ncur, 128), (size_t)vx::kSMs * 32), 128, 0, s>>>(
-            li, starts, ncur, out[l - 1], K, work, misc + 40));
+            li, starts, ncur, out[l - 1], K, work, misc + 40, nullptr));
         VX_CUDA_TRY(cudaGetLastError());
         if (K > 1) {
             unsigned long long* cnt_dev = ctx->prof ? ctx->dev_lobe_count : nullptr;
@@ -565,4 +601,28 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
         }
     }
     return VX_OK;
+}
+
+// One batched LoD step (K = 1): the parents of `in` (n_dev voxels sorted by (instance, key),
+// instance ids inst_in, capacity cap_in) into `out` (capacity cap_out), their instance ids
+// into inst_out and their count into np_dev; a parent count above cap_out sets bit 2 of err.
+// flags, idx: cap_in words; starts: cap_out + 1 words; partials: ceil(cap_in / 2048) words;
+// tmp: one word.  Only enqueues kernels (graph-capturable).
+cudaError_t vx_lod_step_batched(const vx_level* in, const uint16_t* inst_in, const uint32_t* n_dev, uint32_t cap_in,
+                                vx_level* out, uint16_t* inst_out, uint32_t* np_dev, uint32_t cap_out,
+                                uint32_t* flags, uint32_t* idx, uint32_t* starts, uint32_t* partials, uint32_t* tmp,
+                                uint32_t* err, cudaStream_t s) {
+    const unsigned gb = (unsigned)std::min<size_t>(grid_for(cap_in, 256), (size_t)vx::kSMs * 16);
+    k_bparent_flags<<<gb, 256, 0, s>>>(in->keys, inst_in, n_dev, cap_in, flags);
+    cudaError_t e = vx_scan_u32_scratch(flags, idx, cap_in, tmp, partials, s);
+    if (e != cudaSuccess) return e;
+    k_clamp_count<<<1, 1, 0, s>>>(tmp, cap_out, np_dev, err);
+    k_bparent_starts<<<gb, 256, 0, s>>>(in->keys, inst_in, n_dev, idx, tmp, cap_out, starts);
+    LevelIn li;
+    li.keys = in->keys; li.mask = in->mask; li.mass = in->mass; li.moment = in->moment;
+    li.lobe_count = in->lobe_count; li.lobes = in->lobes; li.K = in->K;
+    const unsigned rb = (unsigned)std::min<size_t>(grid_for(cap_out, 128), (size_t)vx::kSMs * 32);
+    k_lod_reduce<<<rb, 128, 0, s>>>(li, starts, 0u, *out, 1, nullptr, nullptr, np_dev);
+    k_bparent_inst<<<gb, 256, 0, s>>>(inst_in, starts, np_dev, inst_out);
+    return cudaGetLastError();
 }

@@ -112,8 +112,20 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* in, 
 }
 
 // ---- radix sort ----------------------------------------------------------------
-__global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n,
+// Digit of an element: bits [shift, shift + 8) of its key, or (LUT pass) a digit looked
+// up from its value: lut[value], with 255 for the padding value 0xffffffff.
+template <bool LUT>
+__device__ __forceinline__ uint32_t radix_digit(uint32_t k, uint32_t v, int shift, uint32_t dmask,
+                                                const uint8_t* __restrict__ lut) {
+    if (LUT) return v == 0xffffffffu ? 255u : (uint32_t)lut[v];
+    return (k >> shift) & dmask;
+}
+
+template <bool LUT>
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                             const uint32_t* __restrict__ vals, uint32_t n,
                                                              int shift, uint32_t dmask, uint32_t nt,
+                                                             const uint8_t* __restrict__ lut,
                                                              uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[RADIX];
     h[threadIdx.x] = 0;
@@ -122,15 +134,17 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const uint32_t* __r
 #pragma unroll 4
     for (int j = 0; j < SORT_ITEMS; ++j) {
         size_t e = base + (size_t)j * SORT_THREADS + threadIdx.x;
-        if (e < n) atomicAdd(&h[(keys[e] >> shift) & dmask], 1u);
+        if (e < n) atomicAdd(&h[radix_digit<LUT>(LUT ? 0u : keys[e], LUT ? vals[e] : 0u, shift, dmask, lut)], 1u);
     }
     __syncthreads();
     hist[(size_t)threadIdx.x * nt + blockIdx.x] = h[threadIdx.x];
 }
 
+template <bool LUT>
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint32_t* __restrict__ keys,
                                                                 const uint32_t* __restrict__ vals, uint32_t n,
                                                                 int shift, uint32_t dmask, uint32_t nt,
+                                                                const uint8_t* __restrict__ lut,
                                                                 const uint32_t* __restrict__ hist,
                                                                 uint32_t* __restrict__ okeys,
                                                                 uint32_t* __restrict__ ovals) {
@@ -149,7 +163,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint32_t* 
         bool valid = e < n;
         k[j] = valid ? keys[e] : 0u;
         v[j] = valid ? vals[e] : 0u;
-        uint32_t d = valid ? ((k[j] >> shift) & dmask) : (uint32_t)RADIX;
+        uint32_t d = valid ? radix_digit<LUT>(k[j], v[j], shift, dmask, lut) : (uint32_t)RADIX;
         uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t r = 0;
         if (valid) r = wcnt[w][d] + __popc(peers & lt);
@@ -174,7 +188,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint32_t* 
     for (int j = 0; j < SORT_ITEMS; ++j) {
         size_t e = base + (size_t)j * 32 + lane;
         if (e < n) {
-            uint32_t d = (k[j] >> shift) & dmask;
+            uint32_t d = radix_digit<LUT>(k[j], v[j], shift, dmask, lut);
             uint32_t pos = gofs[d] + wcnt[w][d] + rk[j];
             okeys[pos] = k[j];
             ovals[pos] = v[j];
@@ -212,10 +226,11 @@ vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, u
     for (int shift = 0; shift < bits; shift += 8) {
         int nb = bits - shift < 8 ? bits - shift : 8;
         uint32_t dmask = (1u << nb) - 1u;
-        VX_LAUNCH(ctx, ST_SORT_HIST, s, k_radix_hist<<<nt, SORT_THREADS, 0, s>>>(*keys, n, shift, dmask, nt, hist));
+        VX_LAUNCH(ctx, ST_SORT_HIST, s, k_radix_hist<false><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, shift, dmask,
+                                                                                     nt, nullptr, hist));
         VX_TRY(vx_scan_u32(ctx, hist, hist, (uint32_t)hn, nullptr, s));
-        VX_LAUNCH(ctx, ST_SORT_SCATTER, s, k_radix_scatter<<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, shift, dmask, nt, hist, *keys_alt,
-                                                   *vals_alt));
+        VX_LAUNCH(ctx, ST_SORT_SCATTER, s, k_radix_scatter<false><<<nt, SORT_THREADS, 0, s>>>(
+                                               *keys, *vals, n, shift, dmask, nt, nullptr, hist, *keys_alt, *vals_alt));
         VX_CUDA_TRY(cudaGetLastError());
         uint32_t* t = *keys; *keys = *keys_alt; *keys_alt = t;
         t = *vals; *vals = *vals_alt; *vals_alt = t;
@@ -232,5 +247,40 @@ cudaError_t vx_scan_u32_scratch(const uint32_t* in, uint32_t* out, uint32_t n, u
     k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(in, n, partials);
     k_scan_partials<<<1, SCAN_THREADS, 0, s>>>(partials, nb, total);
     k_scan_down<<<nb, SCAN_THREADS, 0, s>>>(in, out, n, partials);
+    return cudaGetLastError();
+}
+
+// Stable LSD radix sort with caller-provided scratch (no context workspace): the `bits`
+// low key bits, then, when lut != NULL, one more stable pass on the digit lut[value]
+// (padding elements carry value 0xffffffff and go last).  hist needs 256 * ceil(n / 4096)
+// words, partials ceil(256 * ceil(n / 4096) / 2048) words.  Enqueues only kernels, so it
+// can be captured in a CUDA graph.  Leaves *keys / *vals pointing at the result.
+cudaError_t vx_radix_sort_u32_scratch(uint32_t** keys, uint32_t** vals, uint32_t** keys_alt, uint32_t** vals_alt,
+                                      uint32_t n, int bits, const uint8_t* lut, uint32_t* hist,
+                                      uint32_t* partials, cudaStream_t s) {
+    if (n <= 1) return cudaSuccess;
+    const uint32_t nt = (n + SORT_TILE - 1) / SORT_TILE;
+    const uint32_t hn = RADIX * nt;
+    const int passes = (bits + 7) / 8 + (lut ? 1 : 0);
+    for (int p = 0; p < passes; ++p) {
+        const bool lutpass = lut && p == passes - 1;
+        const int shift = 8 * p;
+        const int nb = lutpass ? 8 : (bits - shift < 8 ? bits - shift : 8);
+        const uint32_t dmask = (1u << nb) - 1u;
+        if (lutpass)
+            k_radix_hist<true><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, 0, 0xffu, nt, lut, hist);
+        else
+            k_radix_hist<false><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, shift, dmask, nt, nullptr, hist);
+        cudaError_t e = vx_scan_u32_scratch(hist, hist, hn, nullptr, partials, s);
+        if (e != cudaSuccess) return e;
+        if (lutpass)
+            k_radix_scatter<true><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, 0, 0xffu, nt, lut, hist, *keys_alt,
+                                                              *vals_alt);
+        else
+            k_radix_scatter<false><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, shift, dmask, nt, nullptr, hist,
+                                                               *keys_alt, *vals_alt);
+        uint32_t* t = *keys; *keys = *keys_alt; *keys_alt = t;
+        t = *vals; *vals = *vals_alt; *vals_alt = t;
+    }
     return cudaGetLastError();
 }

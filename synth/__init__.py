@@ -257,26 +257,28 @@ def config3(seed: int = 3, n_yarns: int = 16, fibers_per_ply: int = 80,
                     Grid((0.0, 0.0, 0.0), 1.0 / R, R), ctrl=ctrl, fiber_offsets=off, K=K)
 
 
-def config4(seed: int = 4, n_instances: int = 64, max_tris: int = 2_000_000,
-            max_segs: int = 4_000_000):
-    """64 instances of uneven size: half heightfields (2k..max_tris triangles),
-    half yarn patches (10k..max_segs segments), log-uniform sizes, grids 64^3..1024^3."""
+def config4(seed: int = 4, n_instances: int = 64, min_tris: int = 2000, max_tris: int = 2_000_000,
+            min_segs: int = 10_000, max_segs: int = 4_000_000, fiber_radius_voxels: float = 1.5):
+    """Instances of uneven size for the batched path: half heightfields (min_tris..max_tris
+    triangles), half yarn patches (min_segs..max_segs segments), log-uniform sizes, grids
+    64^3..1024^3 drawn independently of the size.  A patch's fibers are fiber_radius_voxels
+    voxels thick at its own resolution (the resolution is chosen to resolve the fibers)."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n_instances):
         R = int(2 ** rng.integers(6, 11))
         if i % 2 == 0:
-            nt = int(math.exp(rng.uniform(math.log(2000), math.log(max_tris))))
+            nt = int(math.exp(rng.uniform(math.log(min_tris), math.log(max_tris))))
             n = max(2, int(round(math.sqrt(nt / 2.0))) + 1)
             tris = heightfield(n, seed * 1000 + i)
             out.append(Workload(f"inst{i}-hf{tris.shape[0]}", "triangles",
                                 Grid((0.0, 0.0, -0.5), 1.0 / R, R), tri_verts=tris, K=1))
         else:
-            ns = int(math.exp(rng.uniform(math.log(10000), math.log(max_segs))))
+            ns = int(math.exp(rng.uniform(math.log(min_segs), math.log(max_segs))))
             fibers = max(3, min(192, ns // 200))
             fpp = max(1, fibers // 3)
             segs = max(4, ns // (3 * fpp))
-            ctrl, off = yarn(3, fpp, segs, seed=seed * 1000 + i)
+            ctrl, off = yarn(3, fpp, segs, fiber_radius=fiber_radius_voxels / R, seed=seed * 1000 + i)
             out.append(Workload(f"inst{i}-yarn{3 * fpp * segs}", "fibers",
                                 Grid((0.0, 0.0, 0.0), 1.0 / R, R), ctrl=ctrl,
                                 fiber_offsets=off, K=1))

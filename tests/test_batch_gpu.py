@@ -1,0 +1,78 @@
+"""Batched path (vx_batch_*): every instance's levels equal the plain path's on that
+instance alone, bit for bit, on the first run and on graph replays; an overflow of the
+planned capacities is reported, not written past."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2604_13191_gb300 as vx  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+FIELDS = ("keys", "mask", "mass", "moment", "occ", "proj", "lobe_count", "lobes", "compact")
+
+
+def instances(seed=4, n=12):
+    ws = synth.config4(seed=seed, n_instances=n, min_tris=200, max_tris=20000, min_segs=500, max_segs=30000)
+    out = []
+    for w in ws:
+        if w.kind == "triangles":
+            out.append({"kind": "triangles", "grid": w.grid, "tri_verts": torch.from_numpy(w.tri_verts).to(DEV)})
+        else:
+            out.append({"kind": "fibers", "grid": w.grid, "ctrl": torch.from_numpy(w.ctrl).to(DEV),
+                        "fiber_offsets": torch.from_numpy(w.fiber_offsets).to(DEV)})
+    return out
+
+
+def plain(ctx, inst):
+    if inst["kind"] == "triangles":
+        L0 = ctx.voxelize(inst["grid"], tri_verts=inst["tri_verts"])
+    else:
+        L0 = ctx.voxelize(inst["grid"], ctrl=inst["ctrl"], fiber_offsets=inst["fiber_offsets"])
+    pyr = ctx.build_lod(L0, K=1)
+    torch.cuda.synchronize()
+    return [L0.host()] + [p.host() for p in pyr]
+
+
+def check_batch(ctx, b, insts):
+    for i, inst in enumerate(insts):
+        ref = plain(ctx, inst)
+        for l, r in enumerate(ref):
+            g = b.level(i, l).host()
+            for f in FIELDS:
+                assert np.array_equal(np.asarray(g[f]).view(np.uint8), np.asarray(r[f]).view(np.uint8)), (i, l, f)
+
+
+def test_batch_matches_plain_instances():
+    ctx = vx.Context(DEV)
+    insts = instances()
+    b = ctx.batch(insts)
+    b.run()
+    check_batch(ctx, b, insts)
+    b.run()          # graph replay
+    b.run()
+    check_batch(ctx, b, insts)
+    b.close()
+    ctx.close()
+
+
+def test_batch_capacity_overflow_is_reported():
+    ctx = vx.Context(DEV)
+    insts = [i for i in instances(seed=5, n=4) if i["kind"] == "fibers"]
+    b = ctx.batch(insts, headroom=0.0)
+    b.run()
+    b.level(0, 0)
+    # thicker fibers produce more candidate pairs than planned
+    b.keep[0][:, 3] *= 4.0
+    b.run()
+    with pytest.raises(vx.VxError) as e:
+        b.level(0, 0)
+    assert e.value.status == 3
+    b.close()
+    ctx.close()
