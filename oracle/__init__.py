@@ -383,3 +383,54 @@ def clip_signature(ctrl, offsets, grid, prims) -> int:
     origin = np.ascontiguousarray(grid.origin, dtype=np.float64)
     return int(lib.vxo_clip_signature(_ptr(ctrl), _ptr(offsets), int(offsets.shape[0] - 1), _ptr(origin),
                                       float(grid.voxel_size), int(grid.resolution), _ptr(pr), int(pr.shape[0])))
+
+
+def tri_adjoint(tris, grid, keys0, gm0, gM0, weights=None, prims=None, with_abs=False):
+    """FP64 loss sum gm*m + gM.M over level-0 voxels and its gradient w.r.t. the triangle
+    vertices ([T,3,3] world units) and the per-triangle weights, by complex-step
+    differentiation of the clipped area and the face normal.  With with_abs, also the
+    summed magnitudes of each vertex coordinate's per-pair terms."""
+    lib = _load()
+    if not hasattr(lib, "_tadj_ready"):
+        lib.vxo_tri_adjoint.restype = C.c_double
+        lib.vxo_tri_adjoint.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                        C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                        C.c_void_p, C.c_void_p, C.c_void_p]
+        lib._tadj_ready = True
+    t = np.asarray(tris, dtype=np.float64)
+    T = t.shape[0]
+    t4 = np.zeros((T, 3, 4), np.float64)
+    t4[:, :, :3] = t.reshape(T, 3, -1)[:, :, :3]
+    keys0 = np.ascontiguousarray(keys0, dtype=np.uint64)
+    gm0 = np.ascontiguousarray(gm0, dtype=np.float64)
+    gM0 = np.ascontiguousarray(gM0, dtype=np.float64).reshape(-1, 6)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    pr = None if prims is None else np.ascontiguousarray(np.sort(prims), dtype=np.int64)
+    origin = np.ascontiguousarray(grid.origin, dtype=np.float64)
+    d_t = np.zeros((T, 3, 3), np.float64)
+    d_w = np.zeros(T, np.float64)
+    d_abs = np.zeros((T, 3, 3), np.float64) if with_abs else None
+    loss = lib.vxo_tri_adjoint(_ptr(t4), T, _ptr(w), _ptr(origin), float(grid.voxel_size), int(grid.resolution),
+                               _ptr(keys0), int(keys0.shape[0]), _ptr(gm0), _ptr(gM0), _ptr(pr),
+                               0 if pr is None else int(pr.shape[0]), _ptr(d_t), _ptr(d_w), _ptr(d_abs))
+    if with_abs:
+        return float(loss), d_t, d_w, d_abs
+    return float(loss), d_t, d_w
+
+
+def tri_clip_signature(tris, grid, prims) -> int:
+    """Hash of the clip structure of the listed triangles' clipped polygons (FP64)."""
+    lib = _load()
+    if not hasattr(lib, "_tsig_ready"):
+        lib.vxo_tri_clip_signature.restype = C.c_uint64
+        lib.vxo_tri_clip_signature.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_double, C.c_int,
+                                               C.c_void_p, C.c_int64]
+        lib._tsig_ready = True
+    t = np.asarray(tris, dtype=np.float64)
+    T = t.shape[0]
+    t4 = np.zeros((T, 3, 4), np.float64)
+    t4[:, :, :3] = t.reshape(T, 3, -1)[:, :, :3]
+    pr = np.ascontiguousarray(np.sort(prims), dtype=np.int64)
+    origin = np.ascontiguousarray(grid.origin, dtype=np.float64)
+    return int(lib.vxo_tri_clip_signature(_ptr(t4), T, _ptr(origin), float(grid.voxel_size),
+                                          int(grid.resolution), _ptr(pr), int(pr.shape[0])))

@@ -28,7 +28,8 @@
  * its FP32 normalisation to grid coordinates (the normalised positions are the
  * method's input, Sec. 3.1).
  *
- * Parity unpinned: none of the functions here; see tests/test_oracle_pins.py.
+ * Parity unpinned: none of the functions here; see tests/test_oracle_pins.py and
+ * tests/test_oracle_adjoint_pins.py.
  */
 #include <math.h>
 #include <stdint.h>
@@ -1232,6 +1233,195 @@ ORC_API uint64_t vxo_clip_signature(const double* ctrl, const int64_t* offsets, 
                         for (int b = 0; b < 8; ++b) { h ^= (v >> (8 * b)) & 0xffu; h *= 1099511628211ull; }
                     }
         }
+    }
+    return h;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Triangle adjoint by complex-step differentiation                           */
+/* ------------------------------------------------------------------------- */
+/* The per-pair term of the loss is f = w * area(T ∩ voxel) * (gm + gM . T(n)), with
+ * n the unit face normal (Sec. 4.1: the triangle's orientation is its normal) and
+ * the area in grid units (Sec. 3.1 coordinates).  Each derivative d f / d U_jk is
+ * Im f(U + i eps e_jk) / eps (complex step, Squire & Trapp 1998): the clip decisions
+ * are taken on the real parts, every other operation (the Sutherland-Hodgman clip of
+ * the triangle to the voxel, the polygon's cross-product sum, the square roots) is
+ * analytic, so the result is the exact derivative of the active piece up to rounding,
+ * with no subtractive cancellation.  This is deliberately a different method from the
+ * analytic reference-domain formula the kernels use. */
+#include <complex.h>
+typedef double complex cplx;
+
+static int clip_plane_c(const cplx in[][3], int n, cplx out[][3], int axis, double c, int keep_ge,
+                        unsigned* inside_bits) {
+    int m = 0;
+    unsigned bits = 0;
+    for (int k = 0; k < n; ++k) {
+        const cplx* S = in[k];
+        const cplx* E = in[(k + 1) % n];
+        int sin_ = keep_ge ? (creal(S[axis]) >= c) : (creal(S[axis]) <= c);
+        int ein = keep_ge ? (creal(E[axis]) >= c) : (creal(E[axis]) <= c);
+        if (sin_) bits |= 1u << k;
+        if (ein) {
+            if (!sin_) {
+                cplx s = (c - S[axis]) / (E[axis] - S[axis]);
+                for (int j = 0; j < 3; ++j) out[m][j] = (j == axis) ? (cplx)c : S[j] + s * (E[j] - S[j]);
+                ++m;
+            }
+            for (int j = 0; j < 3; ++j) out[m][j] = E[j];
+            ++m;
+        } else if (sin_) {
+            cplx s = (c - S[axis]) / (E[axis] - S[axis]);
+            for (int j = 0; j < 3; ++j) out[m][j] = (j == axis) ? (cplx)c : S[j] + s * (E[j] - S[j]);
+            ++m;
+        }
+    }
+    if (inside_bits) *inside_bits = bits;
+    return m;
+}
+
+/* area of the triangle U (complex grid coordinates, [3][3]) clipped to voxel (vi,vj,vk);
+ * sig (optional, [6]) receives (n << 16 | inside-bits) of each of the six clip stages. */
+static cplx tri_area_c(const cplx U[3][3], int vi, int vj, int vk, uint32_t* sig) {
+    cplx A[16][3], B[16][3];
+    int n = 3;
+    for (int k = 0; k < 3; ++k) {
+        A[k][0] = U[k][0] - vi; A[k][1] = U[k][1] - vj; A[k][2] = U[k][2] - vk;
+    }
+    if (sig) for (int q = 0; q < 6; ++q) sig[q] = 0;
+    for (int axis = 0; axis < 3 && n > 0; ++axis) {
+        unsigned b0 = 0, b1 = 0;
+        int n0 = n;
+        n = clip_plane_c((const cplx(*)[3])A, n, B, axis, 0.0, 1, &b0);
+        if (sig) sig[2 * axis] = ((uint32_t)n0 << 16) | b0;
+        if (n == 0) break;
+        int n1 = n;
+        n = clip_plane_c((const cplx(*)[3])B, n, A, axis, 1.0, 0, &b1);
+        if (sig) sig[2 * axis + 1] = ((uint32_t)n1 << 16) | b1;
+    }
+    if (n < 3) return 0.0;
+    cplx cx = 0, cy = 0, cz = 0;
+    for (int k = 1; k + 1 < n; ++k) {
+        cplx e1[3], e2[3];
+        for (int j = 0; j < 3; ++j) { e1[j] = A[k][j] - A[0][j]; e2[j] = A[k + 1][j] - A[0][j]; }
+        cx += e1[1] * e2[2] - e1[2] * e2[1];
+        cy += e1[2] * e2[0] - e1[0] * e2[2];
+        cz += e1[0] * e2[1] - e1[1] * e2[0];
+    }
+    return 0.5 * csqrt(cx * cx + cy * cy + cz * cz);
+}
+
+/* area(T ∩ voxel) * (gm + gM . T(n)) with complex coordinates */
+static cplx tri_pair_value_c(const cplx U[3][3], int vi, int vj, int vk, double gm, const double* gM) {
+    cplx area = tri_area_c(U, vi, vj, vk, NULL);
+    if (creal(area) == 0.0) return 0.0;
+    cplx e0[3], e1[3], n[3];
+    for (int i = 0; i < 3; ++i) { e0[i] = U[1][i] - U[0][i]; e1[i] = U[2][i] - U[1][i]; }
+    n[0] = e0[1] * e1[2] - e0[2] * e1[1];
+    n[1] = e0[2] * e1[0] - e0[0] * e1[2];
+    n[2] = e0[0] * e1[1] - e0[1] * e1[0];
+    cplx nn = csqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (creal(nn) == 0.0) return area * gm;
+    cplx t[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+    cplx G = gm + gM[0] * t[0] * t[0] + gM[1] * t[1] * t[1] + gM[2] * t[2] * t[2] + gM[3] * t[0] * t[1] +
+             gM[4] * t[0] * t[2] + gM[5] * t[1] * t[2];
+    return area * G;
+}
+
+static void tri_grid_coords(const double* tri, const double* origin, double s, double U[3][3]) {
+    for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < 3; ++i) U[k][i] = (tri[4 * k + i] - origin[i]) * s;
+}
+
+static void tri_voxel_range(const double U[3][3], int R, int lo[3], int hi[3]) {
+    for (int i = 0; i < 3; ++i) {
+        double mn = fmin(fmin(U[0][i], U[1][i]), U[2][i]);
+        double mx = fmax(fmax(U[0][i], U[1][i]), U[2][i]);
+        lo[i] = clampi((int)floor(mn) - 1, 0, R - 1);
+        hi[i] = clampi((int)floor(mx) + 1, 0, R - 1);
+        if (mx < -1.0 || mn > (double)R + 1.0) { lo[i] = 1; hi[i] = 0; }
+    }
+}
+
+/* Gradients of the loss w.r.t. the triangle vertices tris [T][3][4] (xyz world; the
+ * fourth component is ignored) and the per-triangle weights [T], given the broadcast
+ * level-0 adjoints gm0 [V], gM0 [V][6] on the sorted keys0.  d_tris [T][3][3] (world
+ * units), d_w [T]; d_abs (optional, [T][3][3]) receives the summed magnitudes of the
+ * per-pair terms.  Only the listed prims (or all, when prims == NULL) are visited;
+ * returns their loss contribution. */
+ORC_API double vxo_tri_adjoint(const double* tris, int64_t T, const double* weights, const double* origin,
+                               double voxel_size, int R, const uint64_t* keys0, int64_t V, const double* gm0,
+                               const double* gM0, const int64_t* prims, int64_t nprims, double* d_tris,
+                               double* d_w, double* d_abs) {
+    const double s = 1.0 / voxel_size;
+    const double eps = 1e-30;
+    double loss = 0.0;
+    int64_t pi = 0;
+    for (int64_t p = 0; p < T; ++p) {
+        if (prims) {
+            while (pi < nprims && prims[pi] < p) ++pi;
+            if (pi >= nprims || prims[pi] != p) continue;
+        }
+        double U[3][3];
+        tri_grid_coords(tris + 12 * p, origin, s, U);
+        const double w = weights ? weights[p] : 1.0;
+        int lo[3], hi[3];
+        tri_voxel_range(U, R, lo, hi);
+        for (int vk = lo[2]; vk <= hi[2]; ++vk)
+            for (int vj = lo[1]; vj <= hi[1]; ++vj)
+                for (int vi = lo[0]; vi <= hi[0]; ++vi) {
+                    int64_t v = find_key(keys0, V, vxo_morton((uint32_t)vi, (uint32_t)vj, (uint32_t)vk));
+                    if (v < 0) continue;
+                    cplx Uc[3][3];
+                    for (int k = 0; k < 3; ++k)
+                        for (int i = 0; i < 3; ++i) Uc[k][i] = U[k][i];
+                    const double f0 = creal(tri_pair_value_c((const cplx(*)[3])Uc, vi, vj, vk, gm0[v], gM0 + 6 * v));
+                    if (f0 == 0.0) continue;
+                    loss += w * f0;
+                    if (d_w) d_w[p] += f0;
+                    for (int k = 0; k < 3; ++k)
+                        for (int i = 0; i < 3; ++i) {
+                            Uc[k][i] = U[k][i] + I * eps;
+                            double g = cimag(tri_pair_value_c((const cplx(*)[3])Uc, vi, vj, vk, gm0[v], gM0 + 6 * v)) /
+                                       eps;
+                            Uc[k][i] = U[k][i];
+                            if (d_tris) d_tris[9 * p + 3 * k + i] += w * g * s;
+                            if (d_abs) d_abs[9 * p + 3 * k + i] += fabs(w * g * s);
+                        }
+                }
+    }
+    return loss;
+}
+
+/* Clip signature of the listed triangles: a hash over every (triangle, voxel) with a
+ * clipped polygon of positive area and the vertex count and inside pattern of each of
+ * its six clip stages.  Equal signatures at theta - h, theta, theta + h mean every
+ * clipped polygon kept its combinatorial structure, so the loss is smooth there. */
+ORC_API uint64_t vxo_tri_clip_signature(const double* tris, int64_t T, const double* origin, double voxel_size,
+                                        int R, const int64_t* prims, int64_t nprims) {
+    const double s = 1.0 / voxel_size;
+    uint64_t h = 1469598103934665603ull;
+    int64_t pi = 0;
+    for (int64_t p = 0; p < T; ++p) {
+        while (pi < nprims && prims[pi] < p) ++pi;
+        if (pi >= nprims || prims[pi] != p) continue;
+        double U[3][3];
+        tri_grid_coords(tris + 12 * p, origin, s, U);
+        int lo[3], hi[3];
+        tri_voxel_range(U, R, lo, hi);
+        cplx Uc[3][3];
+        for (int k = 0; k < 3; ++k)
+            for (int i = 0; i < 3; ++i) Uc[k][i] = U[k][i];
+        for (int vk = lo[2]; vk <= hi[2]; ++vk)
+            for (int vj = lo[1]; vj <= hi[1]; ++vj)
+                for (int vi = lo[0]; vi <= hi[0]; ++vi) {
+                    uint32_t sig[6];
+                    if (creal(tri_area_c((const cplx(*)[3])Uc, vi, vj, vk, sig)) == 0.0) continue;
+                    uint64_t key = ((uint64_t)p << 40) ^ vxo_morton((uint32_t)vi, (uint32_t)vj, (uint32_t)vk);
+                    for (int b = 0; b < 8; ++b) { h ^= (key >> (8 * b)) & 0xffu; h *= 1099511628211ull; }
+                    for (int q = 0; q < 6; ++q)
+                        for (int b = 0; b < 4; ++b) { h ^= (sig[q] >> (8 * b)) & 0xffu; h *= 1099511628211ull; }
+                }
     }
     return h;
 }
