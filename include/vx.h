@@ -58,7 +58,7 @@ typedef struct {
 /* Cubic grid (Sec. 3.1: positions normalised to [0, Resolution) per axis).  Voxel (i,j,k)
  * covers origin + voxel_size * [i,i+1] x [j,j+1] x [k,k+1].  Grid coordinates are
  * u = (p - origin) * (1 / voxel_size), evaluated in FP32.
- * resolution: power of two, 1..1024.  sub_res: sub-cells per voxel edge; 8 (the paper's
+ * resolution: power of two, 1..2048 (1..1024 for vx_backward and batches).  sub_res: sub-cells per voxel edge; 8 (the paper's
  * third-level resolution, Sec. 3.1) is the supported value. */
 typedef struct {
     float origin[3];
@@ -133,15 +133,27 @@ VX_API vx_status vx_context_create(const vx_allocator* alloc, vx_context** out);
 /* Releases the workspace and the context (after synchronising its last stream). */
 VX_API void vx_context_destroy(vx_context* ctx);
 
+/* Per-pass limit on candidate (voxel, primitive) pairs of vx_voxelize (default and
+ * maximum 2^31 - 1).  Each pass holds about 24 bytes of workspace per pair, so a lower
+ * limit bounds the workspace; a window over the limit is split into octants.  The split
+ * does not change any output.  Errors: VX_ERR_INVALID_ARG (ctx NULL or max_pairs < 1). */
+VX_API vx_status vx_set_max_pairs_per_pass(vx_context* ctx, int64_t max_pairs);
+
 /* Sparse voxelization (Sec. 3.1-3.5, Sec. 4.1): level 0 of the pyramid.
  * For every voxel v and sub-cell c: bit(c) = closed-box overlap of c with some primitive
  * (capsule: segment inflated by its radius; triangle: separating-axis test).  A voxel is
  * output iff its mask is non-zero.  mass / moment sum the primitives in increasing id
  * order; lobes hold the single normalised lobe S = M / m (weight m) when m > 0 (K = 1).
- * Voxels outside [0, resolution)^3 are dropped.  Synchronises the stream three times to size
- * its outputs.  Errors: VX_ERR_INVALID_ARG, VX_ERR_UNSUPPORTED (resolution > 1024 or
- * sub_res != 8), VX_ERR_OUT_OF_MEMORY, VX_ERR_CAPACITY (more than 2^32-1 candidate
- * voxel/primitive pairs), VX_ERR_CUDA. */
+ * Voxels outside [0, resolution)^3 are dropped.
+ * Windows: the candidate (voxel, primitive) pairs are counted over the whole grid; a window
+ * wider than 1024 voxels (keys of one pass are 30-bit) or holding more pairs than the
+ * per-pass limit (vx_set_max_pairs_per_pass) is split into its eight octants, recursively,
+ * in Morton order; each window is voxelized on its own and the windows' voxels are
+ * concatenated, which keeps the key order.  Synchronises the stream once per counted
+ * window and three times per processed window to size its outputs.
+ * Errors: VX_ERR_INVALID_ARG, VX_ERR_UNSUPPORTED (resolution > 2048 or sub_res != 8),
+ * VX_ERR_OUT_OF_MEMORY, VX_ERR_CAPACITY (a single voxel over the per-pass limit),
+ * VX_ERR_CUDA. */
 VX_API vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
                       void* stream, vx_level* out0);
 
@@ -176,18 +188,26 @@ VX_API vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_lod_
  *     loss = sum_l sum_v grad_mass[l][v] * m_l(v) + grad_moment[l][v] . M_l(v)
  * Since m and M of a parent are sums over its children (Sec. 4.3), the coarse adjoints
  * are broadcast down to level 0 (parents are found from keys0 alone; the coarse levels
- * themselves are not needed).  Per (segment, voxel) pair the analytic derivative of
- * w * pi r^2 * clipped length * (gm + gM . T(t)) is taken w.r.t. both endpoints, the
- * radius and the weight; sub-cell occupancy and the key set are piecewise constant and
- * carry no gradient.  Candidate pairs are recomputed, not stored.
- *   prims: the forward's fibers (VX_FIBERS only); grid: the forward's grid.
+ * themselves are not needed).  The analytic derivative of each (primitive, voxel) term
+ * is taken in FP64 (Sec. 3.5 measures, Sec. 4.1 orientations):
+ *   fibers: w * pi r^2 * clipped length * (gm + gM . T(t)) w.r.t. both endpoints, the
+ *     radius and the weight (t the unit tangent);
+ *   triangles: w * clipped area * (gm + gM . T(n)) w.r.t. the three vertices and the
+ *     weight (n the unit normal; the clipped polygon's edges on voxel planes carry the
+ *     derivative of the area).
+ * Sub-cell occupancy and the key set are piecewise constant and carry no gradient.
+ * Candidate pairs are recomputed, not stored.
+ *   prims: the forward's primitives; grid: the forward's grid (resolution <= 1024).
  *   keys0 (device) [num_voxels0]: level-0 keys of the forward (sorted).
  *   grad_mass, grad_moment: HOST arrays of num_levels+1 device pointers; level l has
  *     as many rows as there are distinct keys0 >> 3l ([V_l] and [V_l][6] floats).
- *   grad_ctrl (device) [num_ctrl][4]: d loss / d (x, y, z, radius) of every control
- *     point, world units; grad_weights (device) [num_prims] or NULL.
+ *   grad_ctrl (device, 16-byte aligned), world units:
+ *     fibers: [num_ctrl][4], d loss / d (x, y, z, radius) of every control point;
+ *     triangles: [num_prims][3][4], d loss / d (x, y, z) of every vertex, w = 0.
+ *   grad_weights (device) [num_prims] or NULL.
  * Deterministic (fixed summation order, no atomics).  Errors: VX_ERR_INVALID_ARG,
- * VX_ERR_UNSUPPORTED (triangles), VX_ERR_OUT_OF_MEMORY, VX_ERR_CAPACITY, VX_ERR_CUDA. */
+ * VX_ERR_UNSUPPORTED (resolution > 1024), VX_ERR_OUT_OF_MEMORY, VX_ERR_CAPACITY,
+ * VX_ERR_CUDA. */
 VX_API vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
                              const uint64_t* keys0, int64_t num_voxels0, int num_levels,
                              const float* const* grad_mass, const float* const* grad_moment,

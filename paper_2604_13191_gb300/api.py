@@ -62,7 +62,7 @@ class VxAllocator(C.Structure):
 EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_lod",
            "vx_level_release", "vx_status_string", "vx_last_cuda_error", "vx_profile_enable",
            "vx_profile_read", "vx_backward", "vx_backward_noalloc", "vx_batch_create", "vx_batch_run",
-           "vx_batch_level", "vx_batch_destroy"]
+           "vx_batch_level", "vx_batch_destroy", "vx_set_max_pairs_per_pass"]
 
 
 class VxInstance(C.Structure):
@@ -110,6 +110,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         lib.vx_last_cuda_error.argtypes = [P]
         lib.vx_profile_enable.restype = C.c_int
         lib.vx_profile_enable.argtypes = [P, C.c_int]
+        lib.vx_set_max_pairs_per_pass.restype = C.c_int
+        lib.vx_set_max_pairs_per_pass.argtypes = [P, C.c_int64]
         lib.vx_profile_read.restype = C.c_int
         lib.vx_profile_read.argtypes = [P, C.POINTER(VxStageTime), C.c_int, C.POINTER(C.c_int)]
         lib.vx_backward.restype = C.c_int
@@ -220,6 +222,13 @@ class Context:
         except Exception:
             pass
 
+    def set_max_pairs_per_pass(self, max_pairs: int):
+        """vx_set_max_pairs_per_pass: candidate pairs per voxelization pass (windows over
+        the limit are split into octants; the outputs do not change)."""
+        st = self.lib.vx_set_max_pairs_per_pass(self.h, int(max_pairs))
+        if st != 0:
+            raise self._err(st, "vx_set_max_pairs_per_pass")
+
     def profile(self, enable: bool = True):
         """vx_profile_enable: per-launch CUDA-event timing of every library kernel."""
         st = self.lib.vx_profile_enable(self.h, 1 if enable else 0)
@@ -263,8 +272,18 @@ class Context:
                  num_prims=None, stream=None) -> Level:
         """vx_voxelize: level 0 from triangles ([T,3,4] float32) or fibers (ctrl [P,4]
         float32, fiber_offsets [F+1] int64), all CUDA tensors on this context's device."""
-        P = VxPrimitives()
         keep = []
+        P = self._prims(tri_verts, ctrl, fiber_offsets, weights, num_prims, keep)
+        G = _grid(grid)
+        L = VxLevel()
+        s = _stream(stream)
+        st = self.lib.vx_voxelize(self.h, C.byref(P), C.byref(G), s, C.byref(L))
+        if st != 0:
+            raise self._err(st, "vx_voxelize")
+        return self._wrap(L)
+
+    def _prims(self, tri_verts, ctrl, fiber_offsets, weights, num_prims, keep):
+        P = VxPrimitives()
         if tri_verts is not None:
             t = tri_verts.contiguous()
             _check(t, torch.float32, self.device, "tri_verts")
@@ -292,43 +311,15 @@ class Context:
             _check(w, torch.float32, self.device, "weights")
             keep.append(w)
             P.weights = w.data_ptr()
-        G = _grid(grid)
-        L = VxLevel()
-        s = _stream(stream)
-        st = self.lib.vx_voxelize(self.h, C.byref(P), C.byref(G), s, C.byref(L))
-        if st != 0:
-            raise self._err(st, "vx_voxelize")
-        return self._wrap(L)
-
-    def _fiber_prims(self, ctrl, fiber_offsets, weights, num_prims, keep):
-        P = VxPrimitives()
-        c = ctrl.contiguous()
-        o = fiber_offsets.contiguous()
-        _check(c, torch.float32, self.device, "ctrl")
-        _check(o, torch.int64, self.device, "fiber_offsets")
-        keep += [c, o]
-        P.kind = VX_FIBERS
-        P.ctrl = c.data_ptr()
-        P.num_ctrl = c.shape[0]
-        P.fiber_offsets = o.data_ptr()
-        P.num_fibers = o.shape[0] - 1
-        if num_prims is None:
-            oc = o.cpu()
-            num_prims = int(torch.clamp(oc[1:] - oc[:-1] - 1, min=0).sum())
-        P.num_prims = int(num_prims)
-        if weights is not None:
-            w = weights.contiguous()
-            _check(w, torch.float32, self.device, "weights")
-            keep.append(w)
-            P.weights = w.data_ptr()
         return P
 
-    def backward(self, grid, *, ctrl, fiber_offsets, keys0, grad_mass, grad_moment, weights=None,
-                 num_prims=None, stream=None):
+    def backward(self, grid, *, keys0, grad_mass, grad_moment, tri_verts=None, ctrl=None, fiber_offsets=None,
+                 weights=None, num_prims=None, stream=None):
         """vx_backward: gradients of sum_l <grad_mass[l], m_l> + <grad_moment[l], M_l> w.r.t.
-        the control points ([P,4]: xyz, radius) and the per-segment weights."""
+        the control points ([P,4]: xyz, radius) or the triangle vertices ([T,3,4]: xyz, 0),
+        and the per-primitive weights."""
         keep = []
-        P = self._fiber_prims(ctrl, fiber_offsets, weights, num_prims, keep)
+        P = self._prims(tri_verts, ctrl, fiber_offsets, weights, num_prims, keep)
         L = len(grad_mass) - 1
         gm = [g.contiguous() for g in grad_mass]
         gM = [g.contiguous() for g in grad_moment]
@@ -338,7 +329,8 @@ class Context:
         keep += gm + gM + [k0]
         pm = (C.c_void_p * (L + 1))(*[g.data_ptr() for g in gm])
         pM = (C.c_void_p * (L + 1))(*[g.data_ptr() for g in gM])
-        g_ctrl = torch.empty((P.num_ctrl, 4), dtype=torch.float32, device=self.device)
+        shape = (P.num_prims, 3, 4) if tri_verts is not None else (P.num_ctrl, 4)
+        g_ctrl = torch.empty(shape, dtype=torch.float32, device=self.device)
         g_w = torch.empty((P.num_prims,), dtype=torch.float32, device=self.device)
         G = _grid(grid)
         st = self.lib.vx_backward(self.h, C.byref(P), C.byref(G), k0.data_ptr(), k0.shape[0], L, pm, pM,
@@ -420,22 +412,27 @@ def _stream(stream):
 
 
 class VoxelizeLoD(torch.autograd.Function):
-    """Differentiable fiber voxelization + K = 1 pyramid.
+    """Differentiable voxelization + K = 1 pyramid.
 
-    forward(ctrl [P,4], weights [N], fiber_offsets, grid, num_levels, context) returns
-    (mass_0, moment_0, mass_1, moment_1, ..., mass_L, moment_L).  backward runs
-    vx_backward; it keeps only the level-0 keys (coarse levels are not stored, their
-    parent structure is recomputed from the keys) and recomputes the candidate pairs.
+    forward(geom, weights [N], fiber_offsets, grid, num_levels, context): geom is the
+    control points ctrl [P,4] of fibers (fiber_offsets [F+1]) or, with fiber_offsets
+    None, the triangle vertices [T,3,4].  Returns (mass_0, moment_0, ..., mass_L,
+    moment_L).  backward runs vx_backward; it keeps only the level-0 keys (coarse levels
+    are not stored, their parent structure is recomputed from the keys) and recomputes
+    the candidate pairs.
     """
 
     @staticmethod
-    def forward(fctx, ctrl, weights, fiber_offsets, grid, num_levels, context):
-        L0 = context.voxelize(grid, ctrl=ctrl, fiber_offsets=fiber_offsets, weights=weights)
+    def forward(fctx, geom, weights, fiber_offsets, grid, num_levels, context):
+        if fiber_offsets is None:
+            L0 = context.voxelize(grid, tri_verts=geom, weights=weights)
+        else:
+            L0 = context.voxelize(grid, ctrl=geom, fiber_offsets=fiber_offsets, weights=weights)
         pyr = context.build_lod(L0, K=1, num_levels=num_levels) if num_levels else []
         outs = []
         for lv in [L0] + pyr:
             outs += [lv.mass.clone(), lv.moment.clone()]
-        fctx.save_for_backward(ctrl, weights, fiber_offsets, L0.keys.clone())
+        fctx.save_for_backward(geom, weights, fiber_offsets, L0.keys.clone())
         fctx.grid = grid
         fctx.context = context
         fctx.num_levels = num_levels
@@ -443,13 +440,13 @@ class VoxelizeLoD(torch.autograd.Function):
 
     @staticmethod
     def backward(fctx, *grads):
-        ctrl, weights, off, keys0 = fctx.saved_tensors
+        geom, weights, off, keys0 = fctx.saved_tensors
         gm = [torch.zeros_like(g) if g is None else g for g in grads[0::2]]
         gM = [torch.zeros_like(g) if g is None else g for g in grads[1::2]]
-        g_ctrl, g_w = fctx.context.backward(fctx.grid, ctrl=ctrl, fiber_offsets=off, keys0=keys0,
-                                            grad_mass=[g.float() for g in gm],
-                                            grad_moment=[g.float() for g in gM], weights=weights)
-        return g_ctrl, g_w, None, None, None, None
+        kw = dict(tri_verts=geom) if off is None else dict(ctrl=geom, fiber_offsets=off)
+        g_geom, g_w = fctx.context.backward(fctx.grid, keys0=keys0, grad_mass=[g.float() for g in gm],
+                                            grad_moment=[g.float() for g in gM], weights=weights, **kw)
+        return g_geom, g_w, None, None, None, None
 
 
 NOALLOC_LIMITS = {"segments": 65536, "fibers": 8192, "voxels0": 262144, "pairs": 2097152}

@@ -146,6 +146,12 @@ void vx_context_destroy(vx_context* ctx) {
     delete ctx;
 }
 
+vx_status vx_set_max_pairs_per_pass(vx_context* ctx, int64_t max_pairs) {
+    if (!ctx || max_pairs < 1) return VX_ERR_INVALID_ARG;
+    ctx->max_pairs = max_pairs > 0x7fffffffll ? 0x7fffffffll : max_pairs;
+    return VX_OK;
+}
+
 vx_status vx_profile_enable(vx_context* ctx, int enable) {
     if (!ctx) return VX_ERR_INVALID_ARG;
     if (enable && !ctx->ev) {

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_bcandidates(const float4* _
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * EMIT_WARPS;
     for (uint32_t p = blockIdx.x * EMIT_WARPS + (threadIdx.x >> 5); p < np; p += warps) {
-        const int R = inst[inst_of[p]].R;
+        const Window R = full_window(inst[inst_of[p]].R);
         float4 a = r0[p], b = r1[p], c;
         Range rg;
         if (FIBER) {
@@ -408,9 +408,10 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
     // ---- per-voxel reduction ------------------------------------------------------------------
     const unsigned rblocks = (unsigned)std::min<size_t>((S.cap_seg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 32);
     if (S.fiber)
-        k_reduce_fibers<<<rblocks, RED_WARPS * 32, 0, s>>>(k0, v0, S.starts, C + C_SEG, S.r0, S.r1, S.seg);
+        k_reduce_fibers<<<rblocks, RED_WARPS * 32, 0, s>>>(k0, v0, S.starts, C + C_SEG, S.r0, S.r1, S.seg, 0, 0, 0);
     else
-        k_reduce_tris<<<rblocks, RED_WARPS * 32, 0, s>>>(k0, v0, S.starts, C + C_SEG, S.r0, S.r1, S.r2, S.seg);
+        k_reduce_tris<<<rblocks, RED_WARPS * 32, 0, s>>>(k0, v0, S.starts, C + C_SEG, S.r0, S.r1, S.r2, S.seg, 0, 0,
+                                                         0);
     // non-empty flags beyond the clamped segment count read as zero in the compaction scan
     k_zero_tail<<<blk, 256, 0, s>>>(S.seg.nonzero, C + C_SEG, S.cap_seg);
     if (vx_scan_u32_scratch(S.seg.nonzero, S.dst, S.cap_seg, C + C_VOX_TOT, S.part, s) != cudaSuccess)

@@ -58,7 +58,7 @@ struct vx_context {
     cudaStream_t last_stream = nullptr;
     char last_err[256] = {0};
     // workspace slots (grow-only)
-    vx::Buf ws[24];
+    vx::Buf ws[32];
     uint64_t* host_pin = nullptr; // pinned readback buffer (64 words)
     // profiling
     bool prof = false;
@@ -66,6 +66,7 @@ struct vx_context {
     double stage_ms[ST_NSTAGES] = {0};
     int64_t units[ST_NSTAGES] = {0};
     unsigned long long* dev_lobe_count = nullptr;   // device counter of lobe samplings
+    int64_t max_pairs = 0x7fffffffll;  // candidate pairs per voxelization pass (window)
     vx::EventRec* ev = nullptr;   // pool of kEventPool records
     int nev = 0;
 };
@@ -85,9 +86,10 @@ enum WsSlot {
     WS_REC_A = 0, WS_REC_B, WS_REC_C, WS_COUNT, WS_OFFS, WS_SCAN_TMP,
     WS_KEYS0, WS_VALS0, WS_KEYS1, WS_VALS1, WS_SORT_HIST,
     WS_FLAGS, WS_SEGIDX, WS_STARTS, WS_SEG_OUT, WS_MISC, WS_FIBER_START,
-    WS_LOD_FLAGS, WS_LOD_IDX, WS_LOD_STARTS, WS_LOD_WORK, WS_LOD_TMP,
+    WS_LOD_FLAGS, WS_LOD_IDX, WS_LOD_STARTS, WS_LOD_WORK, WS_LOD_TMP, WS_LOD_STATS0, WS_LOD_STATS1,
     WS_NSLOTS
 };
+static_assert(WS_NSLOTS <= 32, "workspace slot table");
 
 void vx_record_cuda_error(vx_context* ctx, cudaError_t e, const char* what);
 vx_status vx_ws_ensure(vx_context* ctx, int slot, size_t bytes, cudaStream_t s);
@@ -140,6 +142,14 @@ __host__ __device__ inline uint32_t vx_compact1by2(uint32_t x) {
 }
 __host__ __device__ inline uint32_t vx_morton3(uint32_t x, uint32_t y, uint32_t z) {
     return vx_part1by2(x) | (vx_part1by2(y) << 1) | (vx_part1by2(z) << 2);
+}
+// 64-bit Morton key of coordinates below 2^21 (host and device)
+__host__ __device__ inline uint64_t vx_morton3_64(uint32_t x, uint32_t y, uint32_t z) {
+    uint64_t k = 0;
+    for (int b = 0; b < 21; ++b)
+        k |= ((uint64_t)((x >> b) & 1u) << (3 * b)) | ((uint64_t)((y >> b) & 1u) << (3 * b + 1)) |
+             ((uint64_t)((z >> b) & 1u) << (3 * b + 2));
+    return k;
 }
 
 // ---- level layout --------------------------------------------------------------

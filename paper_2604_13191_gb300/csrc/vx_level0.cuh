@@ -548,14 +548,24 @@ struct Range {
     int lo[3], n[3];
     long long total;
 };
-__device__ __forceinline__ Range make_range(const float* mn, const float* mx, int R) {
+// voxel window of one pass: indices [lo, hi] per axis (a tile of the grid, or all of it);
+// candidate keys are Morton codes relative to lo
+struct Window {
+    int lo[3], hi[3];
+};
+__host__ __device__ inline Window full_window(int R) {
+    Window w;
+    for (int i = 0; i < 3; ++i) { w.lo[i] = 0; w.hi[i] = R - 1; }
+    return w;
+}
+__device__ __forceinline__ Range make_range(const float* mn, const float* mx, const Window& w) {
     Range r;
     r.total = 1;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        float fl = floorf(mn[i]), fh = floorf(mx[i]);
-        int lo = fl < 0.0f ? 0 : (fl > (float)(R - 1) ? R : (int)fl);
-        int hi = fh < 0.0f ? -1 : (fh > (float)(R - 1) ? R - 1 : (int)fh);
+        const float fl = floorf(mn[i]), fh = floorf(mx[i]);
+        const int lo = fl < (float)w.lo[i] ? w.lo[i] : (fl > (float)w.hi[i] ? w.hi[i] + 1 : (int)fl);
+        const int hi = fh < (float)w.lo[i] ? w.lo[i] - 1 : (fh > (float)w.hi[i] ? w.hi[i] : (int)fh);
         r.lo[i] = lo;
         r.n[i] = hi >= lo ? hi - lo + 1 : 0;
         r.total *= r.n[i];
@@ -566,7 +576,7 @@ __device__ __forceinline__ Range make_range(const float* mn, const float* mx, in
 // conservative voxel-level tests (never reject a voxel with a set sub-cell)
 __device__ __forceinline__ float capsule_margin(float rg) { return 2e-3f * fmax2(1.0f, rg) + 1e-4f; }
 
-__device__ __forceinline__ Range capsule_range(float4 A, float4 B, int R) {
+__device__ __forceinline__ Range capsule_range(float4 A, float4 B, const Window& R) {
     const float rc = A.w + capsule_margin(A.w) + 0.01f;
     float mn[3] = {fmin2(A.x, B.x) - rc, fmin2(A.y, B.y) - rc, fmin2(A.z, B.z) - rc};
     float mx[3] = {fmax2(A.x, B.x) + rc, fmax2(A.y, B.y) + rc, fmax2(A.z, B.z) + rc};
@@ -581,7 +591,7 @@ __device__ __forceinline__ bool capsule_voxel_candidate(float4 A, float4 B, int 
     return capsule_box(a, b, r * r, lo, hi);
 }
 
-__device__ __forceinline__ Range tri_range(float4 a, float4 b, float4 c, int R) {
+__device__ __forceinline__ Range tri_range(float4 a, float4 b, float4 c, const Window& R) {
     const float m = 0.01f;
     float mn[3] = {fmin2(fmin2(a.x, b.x), c.x) - m, fmin2(fmin2(a.y, b.y), c.y) - m, fmin2(fmin2(a.z, b.z), c.z) - m};
     float mx[3] = {fmax2(fmax2(a.x, b.x), c.x) + m, fmax2(fmax2(a.y, b.y), c.y) + m, fmax2(fmax2(a.z, b.z), c.z) + m};
@@ -611,7 +621,7 @@ __device__ __forceinline__ bool tri_voxel_candidate(float4 a, float4 b, float4 c
 template <bool FIBER, bool EMIT>
 __global__ void __launch_bounds__(EMIT_WARPS * 32) k_candidates(const float4* __restrict__ r0,
                                                                 const float4* __restrict__ r1,
-                                                                const float4* __restrict__ r2, uint32_t np, int R,
+                                                                const float4* __restrict__ r2, uint32_t np, Window R,
                                                                 uint32_t* __restrict__ counts,
                                                                 const uint32_t* __restrict__ offs,
                                                                 uint32_t* __restrict__ keys,
@@ -645,7 +655,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_candidates(const float4* __
             uint32_t bal = __ballot_sync(0xffffffffu, hit);
             if (EMIT && hit) {
                 uint32_t pos = base + n + __popc(bal & ((1u << lane) - 1u));
-                keys[pos] = vx_morton3((uint32_t)vi, (uint32_t)vj, (uint32_t)vk);
+                keys[pos] = vx_morton3((uint32_t)(vi - R.lo[0]), (uint32_t)(vj - R.lo[1]), (uint32_t)(vk - R.lo[2]));
                 vals[pos] = p;
             }
             n += __popc(bal);
@@ -695,7 +705,8 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_fibers(const uint32_t
                                                                   const uint32_t* __restrict__ starts,
                                                                   const uint32_t* __restrict__ nseg_p,
                                                                   const float4* __restrict__ ra,
-                                                                  const float4* __restrict__ rb, SegOut out) {
+                                                                  const float4* __restrict__ rb, SegOut out,
+                                                                  int bx, int by, int bz) {
     const int lane = threadIdx.x & 31;
     const uint32_t nseg = *nseg_p;
     const int sz = lane >> 2, sy0 = (lane & 3) * 2;
@@ -705,8 +716,8 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_fibers(const uint32_t
     for (uint32_t seg = blockIdx.x * RED_WARPS + (threadIdx.x >> 5); seg < nseg; seg += warps) {
         const uint32_t beg = starts[seg], end = starts[seg + 1];
         const uint32_t key = keys[beg];
-        const float fx = (float)vx_compact1by2(key), fy = (float)vx_compact1by2(key >> 1),
-                    fz = (float)vx_compact1by2(key >> 2);
+        const float fx = (float)((int)vx_compact1by2(key) + bx), fy = (float)((int)vx_compact1by2(key >> 1) + by),
+                    fz = (float)((int)vx_compact1by2(key >> 2) + bz);
         uint32_t chunk = 0;
         bool full = false;
         float acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -755,7 +766,8 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_tris(const uint32_t* 
                                                                 const uint32_t* __restrict__ nseg_p,
                                                                 const float4* __restrict__ r0,
                                                                 const float4* __restrict__ r1,
-                                                                const float4* __restrict__ r2, SegOut out) {
+                                                                const float4* __restrict__ r2, SegOut out,
+                                                                int bx, int by, int bz) {
     const int lane = threadIdx.x & 31;
     const uint32_t nseg = *nseg_p;
     const int sz = lane >> 2, sy0 = (lane & 3) * 2;
@@ -763,7 +775,8 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_tris(const uint32_t* 
     for (uint32_t seg = blockIdx.x * RED_WARPS + (threadIdx.x >> 5); seg < nseg; seg += warps) {
         const uint32_t beg = starts[seg], end = starts[seg + 1];
         const uint32_t key = keys[beg];
-        const uint32_t ix = vx_compact1by2(key), iy = vx_compact1by2(key >> 1), iz = vx_compact1by2(key >> 2);
+        const uint32_t ix = vx_compact1by2(key) + bx, iy = vx_compact1by2(key >> 1) + by,
+                       iz = vx_compact1by2(key >> 2) + bz;
         uint32_t chunk = 0;
         bool full = false;
         float acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -862,12 +875,12 @@ __device__ __forceinline__ void write_lobe(float m, const float* M, float* lobe,
 }
 
 __global__ void k_finalize(SegOut in, const uint32_t* __restrict__ nseg_p, const uint32_t* __restrict__ dst,
-                           vx_level L) {
+                           vx_level L, uint64_t key_hi) {
     const uint32_t nseg = *nseg_p;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
         if (!in.nonzero[s]) continue;
         const uint32_t o = dst[s];
-        L.keys[o] = (uint64_t)in.key[s];
+        L.keys[o] = key_hi | (uint64_t)in.key[s];
         uint64_t m[8];
 #pragma unroll
         for (int w = 0; w < 8; ++w) {

@@ -23,7 +23,6 @@
 namespace {
 
 constexpr int CL_WARPS = 4;                 // warps per block in the cluster kernel
-constexpr int MAX_SLOTS = 2 * vx::kMaxCand; // candidates + merged lobes
 
 struct LevelIn {
     const uint64_t* keys;
@@ -115,9 +114,19 @@ __device__ __forceinline__ void compact_params(const float* S, float* c) {
 }
 
 // thread per parent (np_dev, when given, overrides np with a device-side count)
+// Histogram counts and sample second moment of one lobe (Sec. 4.4), 48 bytes.  Kept per
+// output lobe of a level so that the next level's clustering does not sample it again
+// (the statistics are a deterministic function of the lobe's stored S); h[0] < 0 marks a
+// lobe that was never sampled.
+struct LobeStats {
+    int32_t h[6];
+    float Mh[6];
+};
+
 __global__ void k_lod_reduce(LevelIn in, const uint32_t* __restrict__ starts, uint32_t np, vx_level out, int K,
                              uint32_t* __restrict__ work, uint32_t* __restrict__ nwork,
-                             const uint32_t* __restrict__ np_dev) {
+                             const uint32_t* __restrict__ np_dev, const LobeStats* __restrict__ cst,
+                             LobeStats* __restrict__ pst) {
     if (np_dev) np = *np_dev;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
         const uint32_t beg = starts[p], end = starts[p + 1];
@@ -184,6 +193,15 @@ __global__ void k_lod_reduce(LevelIn in, const uint32_t* __restrict__ starts, ui
                         }
                     for (int j = 0; j < 7; ++j) lo[rank * 7 + j] = src[j];
                     compact_params(src, co + rank * 6);
+                    if (pst) {
+                        LobeStats st;
+                        if (cst) {
+                            st = cst[(size_t)c * in.K + l];
+                        } else {
+                            st.h[0] = -1;
+                        }
+                        pst[(size_t)p * K + rank] = st;
+                    }
                 }
             }
             out.lobe_count[p] = (uint8_t)ncand;
@@ -243,10 +261,6 @@ __device__ void sqrtm3(const float* S, float* Rm) {
             Rm[3 * i + j] = ((V[i][0] * sg[0]) * V[j][0] + (V[i][1] * sg[1]) * V[j][1]) + (V[i][2] * sg[2]) * V[j][2];
 }
 
-struct LobeStats {
-    int32_t h[6];
-    float Mh[6];
-};
 
 // round-half-even to an integer for |x| < 2^22: adding 1.5 * 2^23 leaves the rounded
 // integer in the low mantissa bits (same value as __float2int_rn, at FP32-add cost)
@@ -259,7 +273,7 @@ __device__ __forceinline__ int rint_small(float x) {
 // Every count and sum is an integer, so the result is independent of G and of the order
 // in which the threads visit the samples.  Result valid in every participating thread.
 template <int G>
-__device__ LobeStats sample_lobe(const float* S, const float* __restrict__ dirs, int N, long long* red) {
+__device__ LobeStats sample_lobe(const float* S, const float4* __restrict__ dirs, int N, long long* red) {
     const float tr = (S[0] + S[1]) + S[2];
     const float eps = 1e-6f * tr;
     const float Sp[6] = {S[0] + eps, S[1] + eps, S[2] + eps, S[3], S[4], S[5]};
@@ -276,7 +290,8 @@ __device__ LobeStats sample_lobe(const float* S, const float* __restrict__ dirs,
         const int kend = min(N, k0 + STRIDE * 1024);
 #pragma unroll 4
         for (int k = k0; k < kend; k += STRIDE) {
-            const float u0 = __ldg(dirs + 3 * k), u1 = __ldg(dirs + 3 * k + 1), u2 = __ldg(dirs + 3 * k + 2);
+            const float4 u4 = __ldg(dirs + k);
+            const float u0 = u4.x, u1 = u4.y, u2 = u4.z;
             float v[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) v[i] = (Rm[3 * i] * u0 + Rm[3 * i + 1] * u1) + Rm[3 * i + 2] * u2;
@@ -350,13 +365,33 @@ __device__ LobeStats sample_lobe(const float* S, const float* __restrict__ dirs,
     return st;
 }
 
-struct ClusterSmem {
-    float S[MAX_SLOTS][6];
-    float w[MAX_SLOTS];
-    float Mh[MAX_SLOTS][6];
-    int32_t H[MAX_SLOTS][6];
-    uint8_t alive[MAX_SLOTS];
+// Per-group shared state of SGGX-H, sized for `slots` lobes (candidates + merges, 2 * 8K):
+// S [slots][6], w [slots], M^ [slots][6], histogram [slots][6], alive [slots].
+struct ClusterView {
+    float* S;
+    float* w;
+    float* Mh;
+    int32_t* H;
+    uint8_t* alive;
 };
+__host__ __device__ inline size_t cluster_bytes(int slots) {
+    return (((size_t)slots * 19 * 4 + (size_t)slots) + 15) & ~size_t(15);
+}
+__device__ inline ClusterView cluster_view(unsigned char* base, int slots) {
+    ClusterView v;
+    v.S = (float*)base;
+    v.w = v.S + (size_t)slots * 6;
+    v.Mh = v.w + slots;
+    v.H = (int32_t*)(v.Mh + (size_t)slots * 6);
+    v.alive = (uint8_t*)(v.H + (size_t)slots * 6);
+    return v;
+}
+
+// float3 direction table -> float4 (one 16-byte load per sample)
+__global__ void k_pack_dirs(const float* __restrict__ d, int n, float4* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = make_float4(d[3 * k], d[3 * k + 1], d[3 * k + 2], 0.0f);
+}
 
 // One parent listed in `work` per group of G warps (G = 1: a warp per parent, for levels
 // with many parents; G = CL_BLOCK_WARPS: a block per parent, for the few coarse parents
@@ -366,13 +401,14 @@ constexpr int CL_BLOCK_WARPS = 8;
 template <int G>
 __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluster(
     LevelIn in, const uint32_t* __restrict__ starts, const uint32_t* __restrict__ work,
-    const uint32_t* __restrict__ nwork_p, vx_level out, int K, const float* __restrict__ dirs, int N,
-    unsigned long long* __restrict__ nsampled) {
+    const uint32_t* __restrict__ nwork_p, vx_level out, int K, const float4* __restrict__ dirs, int N,
+    const LobeStats* __restrict__ cst, LobeStats* __restrict__ pst, unsigned long long* __restrict__ nsampled) {
     extern __shared__ unsigned char smem_raw[];
     constexpr int GROUPS = (G == 1) ? CL_WARPS : 1;
     const int group = (G == 1) ? (int)(threadIdx.x >> 5) : 0;
-    ClusterSmem& sm = ((ClusterSmem*)smem_raw)[group];
-    long long* red = (long long*)(smem_raw + sizeof(ClusterSmem) * GROUPS);
+    const int slots = 16 * K;
+    const ClusterView sm = cluster_view(smem_raw + cluster_bytes(slots) * group, slots);
+    long long* red = (long long*)(smem_raw + cluster_bytes(slots) * GROUPS);
     __shared__ unsigned long long bestred[G];
     const int tid = (G == 1) ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
     constexpr int NT = 32 * G;
@@ -385,26 +421,47 @@ __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluste
     for (uint32_t it = blockIdx.x * GROUPS + group; it < nwork; it += groups) {
         const uint32_t p = work[it];
         const uint32_t beg = starts[p], end = starts[p + 1];
-        // gather candidates in (child, lobe) order
+        // gather candidates in (child, lobe) order, with their statistics where the child
+        // level kept them (alive = 2: not sampled yet)
         int n = 0;
         for (uint32_t c = beg; c < end; ++c) {
             const int lc = in.lobe_count[c];
             for (int l = tid; l < lc * 7; l += NT) {
                 const int li = l / 7, j = l % 7;
                 const float x = in.lobes[((size_t)c * in.K + li) * 7 + j];
-                if (j < 6) sm.S[n + li][j] = x; else sm.w[n + li] = x;
+                if (j < 6) sm.S[(n + li) * 6 + j] = x; else sm.w[n + li] = x;
+            }
+            for (int l = tid; l < lc; l += NT) {
+                bool have = false;
+                if (cst) {
+                    const LobeStats st = cst[(size_t)c * in.K + l];
+                    if (st.h[0] >= 0) {
+                        have = true;
+#pragma unroll
+                        for (int j = 0; j < 6; ++j) {
+                            sm.H[(n + l) * 6 + j] = st.h[j];
+                            sm.Mh[(n + l) * 6 + j] = st.Mh[j];
+                        }
+                    }
+                }
+                sm.alive[n + l] = have ? 1 : 2;
             }
             n += lc;
         }
-        for (int l = tid; l < MAX_SLOTS; l += NT) sm.alive[l] = (l < n) ? 1 : 0;
+        for (int l = n + tid; l < slots; l += NT) sm.alive[l] = 0;
         gsync();
+        int sampled = 0;
         for (int l = 0; l < n; ++l) {
-            LobeStats st = sample_lobe<G>(sm.S[l], dirs, N, red);
+            if (sm.alive[l] != 2) continue;
+            LobeStats st = sample_lobe<G>(sm.S + l * 6, dirs, N, red);
             if (tid < 6) {
-                sm.H[l][tid] = st.h[tid];
-                sm.Mh[l][tid] = st.Mh[tid];
+                sm.H[l * 6 + tid] = st.h[tid];
+                sm.Mh[l * 6 + tid] = st.Mh[tid];
             }
+            ++sampled;
         }
+        gsync();
+        for (int l = tid; l < n; l += NT) sm.alive[l] = 1;
         gsync();
         int count = n, next = n;
         while (count > K) {
@@ -420,7 +477,7 @@ __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluste
                 if (!sm.alive[i] || !sm.alive[j]) continue;
                 long long d = 0;
 #pragma unroll
-                for (int c = 0; c < 6; ++c) d += llabs((long long)sm.H[i][c] - (long long)sm.H[j][c]);
+                for (int c = 0; c < 6; ++c) d += llabs((long long)sm.H[i * 6 + c] - (long long)sm.H[j * 6 + c]);
                 unsigned long long key = ((unsigned long long)d << 16) | ((unsigned long long)i << 8) | (unsigned long long)j;
                 if (key < best) best = key;
             }
@@ -437,7 +494,7 @@ __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluste
                 __syncthreads();
             }
             const int bi = (int)((best >> 8) & 0xffull), bj = (int)(best & 0xffull);
-            if (tid < 6) sm.S[next][tid] = (sm.Mh[bi][tid] + sm.Mh[bj][tid]) * 0.5f;
+            if (tid < 6) sm.S[next * 6 + tid] = (sm.Mh[bi * 6 + tid] + sm.Mh[bj * 6 + tid]) * 0.5f;
             if (tid == 0) {
                 sm.w[next] = sm.w[bi] + sm.w[bj];
                 sm.alive[bi] = 0;
@@ -445,10 +502,10 @@ __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluste
                 sm.alive[next] = 1;
             }
             gsync();
-            LobeStats st = sample_lobe<G>(sm.S[next], dirs, N, red);
+            LobeStats st = sample_lobe<G>(sm.S + next * 6, dirs, N, red);
             if (tid < 6) {
-                sm.H[next][tid] = st.h[tid];
-                sm.Mh[next][tid] = st.Mh[tid];
+                sm.H[next * 6 + tid] = st.h[tid];
+                sm.Mh[next * 6 + tid] = st.Mh[tid];
             }
             gsync();
             ++next;
@@ -463,13 +520,23 @@ __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluste
             int rank = 0;
             for (int y = 0; y < next; ++y)
                 if (sm.alive[y] && (sm.w[y] > wx || (sm.w[y] == wx && y < x))) ++rank;
-            for (int j = 0; j < 6; ++j) lo[rank * 7 + j] = sm.S[x][j];
+            for (int j = 0; j < 6; ++j) lo[rank * 7 + j] = sm.S[x * 6 + j];
             lo[rank * 7 + 6] = wx;
-            compact_params(sm.S[x], co + rank * 6);
+            compact_params(sm.S + x * 6, co + rank * 6);
+            if (pst) {
+                LobeStats st;
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    st.h[j] = sm.H[x * 6 + j];
+                    st.Mh[j] = sm.Mh[x * 6 + j];
+                }
+                pst[(size_t)p * K + rank] = st;
+            }
         }
         if (tid == 0) {
             out.lobe_count[p] = (uint8_t)count;
-            if (nsampled) atomicAdd(nsampled, (unsigned long long)next);   // n candidates + merges
+            // lobe samplings: candidates without kept statistics + one per merge
+            if (nsampled) atomicAdd(nsampled, (unsigned long long)(sampled + next - n));
         }
         gsync();
     }
@@ -562,9 +629,24 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
     uint32_t* flags = (uint32_t*)ctx->ws[WS_LOD_FLAGS].p;
     uint32_t* starts = (uint32_t*)ctx->ws[WS_LOD_STARTS].p;
     uint32_t* work = (uint32_t*)ctx->ws[WS_LOD_WORK].p;
-    const size_t cl_smem = sizeof(ClusterSmem) * CL_WARPS;
-    const size_t cb_smem = sizeof(ClusterSmem) + sizeof(long long) * 13 * CL_BLOCK_WARPS;
+    // per-lobe statistics of the previous and the current level (K > 1), ping-pong
+    LobeStats* stats[2] = {nullptr, nullptr};
     if (K > 1) {
+        uint32_t vmax = 1;
+        for (int l = 1; l <= L; ++l) vmax = std::max(vmax, counts[l]);
+        VX_TRY(vx_ws_ensure(ctx, WS_LOD_STATS0, (size_t)vmax * K * sizeof(LobeStats), s));
+        VX_TRY(vx_ws_ensure(ctx, WS_LOD_STATS1, (size_t)vmax * K * sizeof(LobeStats), s));
+        stats[0] = (LobeStats*)ctx->ws[WS_LOD_STATS0].p;
+        stats[1] = (LobeStats*)ctx->ws[WS_LOD_STATS1].p;
+    }
+    const size_t cl_smem = cluster_bytes(16 * K) * CL_WARPS;
+    const size_t cb_smem = cluster_bytes(16 * K) + sizeof(long long) * 13 * CL_BLOCK_WARPS;
+    float4* dirs4 = nullptr;
+    if (K > 1) {
+        VX_TRY(vx_ws_ensure(ctx, WS_LOD_TMP, (size_t)params->n_samples * 16, s));
+        dirs4 = (float4*)ctx->ws[WS_LOD_TMP].p;
+        VX_LAUNCH(ctx, ST_LOD_HEADS, s, k_pack_dirs<<<(params->n_samples + 255) / 256, 256, 0, s>>>(
+                                            params->dirs, params->n_samples, dirs4));
         VX_CUDA_TRY(cudaFuncSetAttribute(k_sggx_cluster<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl_smem));
         VX_CUDA_TRY(cudaFuncSetAttribute(k_sggx_cluster<CL_BLOCK_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cb_smem));
@@ -581,21 +663,24 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
         VX_LAUNCH(ctx, ST_LOD_HEADS, s, k_parent_starts<<<grid_for(nprev, 256), 256, 0, s>>>(prev->keys, nprev, flags, ncur, starts));
         VX_CUDA_TRY(cudaMemsetAsync(misc + 40, 0, 4, s));
         vx_stage_units(ctx, ST_LOD_REDUCE, ncur);
+        // statistics kept by the child level (none for the input level) and by this one
+        const LobeStats* cst = (K > 1 && l > 1) ? stats[l & 1] : nullptr;
+        LobeStats* pst = (K > 1) ? stats[(l + 1) & 1] : nullptr;
         VX_LAUNCH(ctx, ST_LOD_REDUCE, s, k_lod_reduce<<<(unsigned)std::min<size_t>(grid_for(ncur, 128), (size_t)vx::kSMs * 32), 128, 0, s>>>(
-            li, starts, ncur, out[l - 1], K, work, misc + 40, nullptr));
+            li, starts, ncur, out[l - 1], K, work, misc + 40, nullptr, cst, pst));
         VX_CUDA_TRY(cudaGetLastError());
         if (K > 1) {
             unsigned long long* cnt_dev = ctx->prof ? ctx->dev_lobe_count : nullptr;
             if (ncur > (uint32_t)(vx::kSMs * 16)) {
                 const unsigned cb = (unsigned)std::min<size_t>((ncur + CL_WARPS - 1) / CL_WARPS, (size_t)vx::kSMs * 16);
                 VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, k_sggx_cluster<1><<<cb, CL_WARPS * 32, cl_smem, s>>>(
-                                                   li, starts, work, misc + 40, out[l - 1], K, params->dirs,
-                                                   params->n_samples, cnt_dev));
+                                                   li, starts, work, misc + 40, out[l - 1], K, dirs4,
+                                                   params->n_samples, cst, pst, cnt_dev));
             } else {
                 const unsigned cb = (unsigned)std::max<uint32_t>(1u, std::min<uint32_t>(ncur, vx::kSMs * 4));
                 VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, k_sggx_cluster<CL_BLOCK_WARPS><<<cb, CL_BLOCK_WARPS * 32, cb_smem, s>>>(
-                                                   li, starts, work, misc + 40, out[l - 1], K, params->dirs,
-                                                   params->n_samples, cnt_dev));
+                                                   li, starts, work, misc + 40, out[l - 1], K, dirs4,
+                                                   params->n_samples, cst, pst, cnt_dev));
             }
             VX_CUDA_TRY(cudaGetLastError());
         }
@@ -622,7 +707,7 @@ cudaError_t vx_lod_step_batched(const vx_level* in, const uint16_t* inst_in, con
     li.keys = in->keys; li.mask = in->mask; li.mass = in->mass; li.moment = in->moment;
     li.lobe_count = in->lobe_count; li.lobes = in->lobes; li.K = in->K;
     const unsigned rb = (unsigned)std::min<size_t>(grid_for(cap_out, 128), (size_t)vx::kSMs * 32);
-    k_lod_reduce<<<rb, 128, 0, s>>>(li, starts, 0u, *out, 1, nullptr, nullptr, np_dev);
+    k_lod_reduce<<<rb, 128, 0, s>>>(li, starts, 0u, *out, 1, nullptr, nullptr, np_dev, nullptr, nullptr);
     k_bparent_inst<<<gb, 256, 0, s>>>(inst_in, starts, np_dev, inst_out);
     return cudaGetLastError();
 }

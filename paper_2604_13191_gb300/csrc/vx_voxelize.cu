@@ -21,10 +21,134 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "vx_internal.cuh"
 
 #include "vx_level0.cuh"
+
+namespace {
+
+// exact 64-bit total of the per-primitive candidate counts (the 32-bit scan total wraps)
+__global__ void k_sum_u64(const uint32_t* __restrict__ cnt, uint32_t n, unsigned long long* __restrict__ total) {
+    unsigned long long acc = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc += cnt[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
+}
+
+// Candidate counts and offsets of the primitives over one window (WS_COUNT, WS_OFFS); the
+// exact total goes to *total.  Synchronises the stream once.
+vx_status count_window(vx_context* ctx, bool fiber, uint32_t np, const Window& win, float4* r0, float4* r1,
+                       float4* r2, uint32_t* misc, cudaStream_t s, uint64_t* total) {
+    VX_TRY(vx_ws_ensure(ctx, WS_COUNT, (size_t)np * 4, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_OFFS, (size_t)np * 4, s));
+    uint32_t* cnt = (uint32_t*)ctx->ws[WS_COUNT].p;
+    uint32_t* offs = (uint32_t*)ctx->ws[WS_OFFS].p;
+    const unsigned cblocks = (unsigned)std::min<size_t>((np + EMIT_WARPS - 1) / EMIT_WARPS, (size_t)vx::kSMs * 64);
+    if (fiber)
+        VX_LAUNCH(ctx, ST_COUNT, s, k_candidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                        r0, r1, r2, np, win, cnt, nullptr, nullptr, nullptr));
+    else
+        VX_LAUNCH(ctx, ST_COUNT, s, k_candidates<false, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                        r0, r1, r2, np, win, cnt, nullptr, nullptr, nullptr));
+    VX_TRY(vx_scan_u32(ctx, cnt, offs, np, misc + 1, s));
+    unsigned long long* t64 = (unsigned long long*)(misc + 8);
+    VX_CUDA_TRY(cudaMemsetAsync(t64, 0, 8, s));
+    VX_LAUNCH(ctx, ST_COUNT, s, k_sum_u64<<<(unsigned)std::min<size_t>(grid_for(np, 256), (size_t)vx::kSMs * 8), 256, 0, s>>>(
+                                    cnt, np, t64));
+    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 48, cudaMemcpyDeviceToHost, s));
+    VX_CUDA_TRY(cudaStreamSynchronize(s));
+    if (((uint32_t*)ctx->host_pin)[0]) return VX_ERR_INVALID_ARG;
+    *total = ((const uint64_t*)ctx->host_pin)[4];
+    return VX_OK;
+}
+
+// One counted window (count_window ran on it and its total fits 31 bits): emit, sort,
+// segments, reduction and compaction into a new level block (*out).  Keys of the block
+// are key_hi | the Morton key relative to the window's corner (3 * bits bits).
+vx_status voxelize_window(vx_context* ctx, bool fiber, uint32_t np, const Window& win, int bits, uint64_t key_hi,
+                          int res, uint32_t npairs, float4* r0, float4* r1, float4* r2, uint32_t* misc,
+                          cudaStream_t s, vx_level* out) {
+    const int bx = win.lo[0], by = win.lo[1], bz = win.lo[2];
+    uint32_t* offs = (uint32_t*)ctx->ws[WS_OFFS].p;
+    const unsigned cblocks = (unsigned)std::min<size_t>((np + EMIT_WARPS - 1) / EMIT_WARPS, (size_t)vx::kSMs * 64);
+    vx_stage_units(ctx, ST_COUNT, npairs);
+    vx_stage_units(ctx, ST_EMIT, npairs);
+    vx_stage_units(ctx, ST_SORT_SCATTER, npairs);
+    vx_stage_units(ctx, ST_SORT_HIST, npairs);
+    vx_stage_units(ctx, ST_REDUCE_FIBERS + (fiber ? 0 : 1), npairs);
+    if (npairs == 0) return vx_level_alloc(ctx, out, 0, 1, 0, res, s);
+
+    // ---- emit + sort ------------------------------------------------------------------
+    VX_TRY(vx_ws_ensure(ctx, WS_KEYS0, (size_t)npairs * 4, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_VALS0, (size_t)npairs * 4, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_KEYS1, (size_t)npairs * 4, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_VALS1, (size_t)npairs * 4, s));
+    uint32_t* k0 = (uint32_t*)ctx->ws[WS_KEYS0].p;
+    uint32_t* v0 = (uint32_t*)ctx->ws[WS_VALS0].p;
+    uint32_t* k1 = (uint32_t*)ctx->ws[WS_KEYS1].p;
+    uint32_t* v1 = (uint32_t*)ctx->ws[WS_VALS1].p;
+    if (fiber)
+        VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                       r0, r1, r2, np, win, nullptr, offs, k0, v0));
+    else
+        VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<false, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                       r0, r1, r2, np, win, nullptr, offs, k0, v0));
+    VX_CUDA_TRY(cudaGetLastError());
+    VX_TRY(vx_radix_sort_u32(ctx, &k0, &v0, &k1, &v1, npairs, 3 * bits, s));
+
+    // ---- segments ---------------------------------------------------------------------
+    VX_TRY(vx_ws_ensure(ctx, WS_FLAGS, (size_t)npairs * 4, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_STARTS, (size_t)npairs * 4 + 8, s));
+    uint32_t* flags = (uint32_t*)ctx->ws[WS_FLAGS].p;
+    uint32_t* starts = (uint32_t*)ctx->ws[WS_STARTS].p;
+    VX_LAUNCH(ctx, ST_HEADS, s, k_head_flags<<<grid_for(npairs, 256), 256, 0, s>>>(k0, npairs, flags));
+    VX_TRY(vx_scan_u32(ctx, flags, flags, npairs, misc + 2, s));
+    VX_LAUNCH(ctx, ST_HEADS, s, k_head_starts<<<grid_for(npairs, 256), 256, 0, s>>>(k0, npairs, flags, misc + 2, starts));
+    VX_CUDA_TRY(cudaGetLastError());
+
+    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc + 2, 4, cudaMemcpyDeviceToHost, s));
+    VX_CUDA_TRY(cudaStreamSynchronize(s));
+    const uint32_t nseg = ((uint32_t*)ctx->host_pin)[0];
+    vx_stage_units(ctx, ST_FINALIZE, nseg);
+
+    // ---- per-voxel reduction ----------------------------------------------------------
+    // temp outputs per candidate voxel: mask 64 + mass 4 + moment 24 bytes; the sort's
+    // alternate buffers are free now and hold the key and the non-empty flag.
+    VX_TRY(vx_ws_ensure(ctx, WS_SEG_OUT, (size_t)nseg * (64 + 4 + 24), s));
+    char* so = (char*)ctx->ws[WS_SEG_OUT].p;
+    SegOut seg;
+    seg.mask = (uint64_t*)so;
+    seg.mass = (float*)(so + (size_t)nseg * 64);
+    seg.moment = (float*)(so + (size_t)nseg * 68);
+    seg.key = k1;
+    seg.nonzero = v1;
+    const unsigned rblocks = (unsigned)std::min<size_t>((nseg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 32);
+    if (fiber)
+        VX_LAUNCH(ctx, ST_REDUCE_FIBERS, s, k_reduce_fibers<<<rblocks, RED_WARPS * 32, 0, s>>>(
+                                                k0, v0, starts, misc + 2, r0, r1, seg, bx, by, bz));
+    else
+        VX_LAUNCH(ctx, ST_REDUCE_TRIS, s, k_reduce_tris<<<rblocks, RED_WARPS * 32, 0, s>>>(
+                                              k0, v0, starts, misc + 2, r0, r1, r2, seg, bx, by, bz));
+    VX_CUDA_TRY(cudaGetLastError());
+
+    // ---- compaction: dst = exclusive scan of the non-empty flags ----------------------------
+    uint32_t* dst = flags;   // the head flags are no longer needed
+    VX_TRY(vx_scan_u32(ctx, seg.nonzero, dst, nseg, misc + 3, s));
+    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc + 3, 4, cudaMemcpyDeviceToHost, s));
+    VX_CUDA_TRY(cudaStreamSynchronize(s));
+    const uint32_t nvox = ((uint32_t*)ctx->host_pin)[0];
+    VX_TRY(vx_level_alloc(ctx, out, nvox, 1, 0, res, s));
+    if (nvox > 0) {
+        VX_LAUNCH(ctx, ST_FINALIZE, s, k_finalize<<<grid_for(nseg, 256), 256, 0, s>>>(seg, misc + 2, dst, *out, key_hi));
+        VX_CUDA_TRY(cudaGetLastError());
+    }
+    return VX_OK;
+}
+
+}  // namespace
 
 extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
                                  void* stream, vx_level* out0) {
@@ -34,14 +158,14 @@ extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, co
     ctx->last_stream = s;
     const uint32_t R = grid->resolution;
     if (R == 0 || (R & (R - 1)) != 0) return VX_ERR_INVALID_ARG;
-    if (R > 1024 || grid->sub_res != 8) return VX_ERR_UNSUPPORTED;
+    if (R > 2048 || grid->sub_res != 8) return VX_ERR_UNSUPPORTED;
     if (!(grid->voxel_size > 0.0f) || !isfinite(grid->voxel_size)) return VX_ERR_INVALID_ARG;
     if (prims->num_prims < 0 || prims->num_prims > 0xfffffffell) return VX_ERR_CAPACITY;
     const bool fiber = prims->kind == VX_FIBERS;
     if (!fiber && prims->kind != VX_TRIANGLES) return VX_ERR_INVALID_ARG;
     const uint32_t np = (uint32_t)prims->num_prims;
-    int bits = 0;
-    while ((1u << bits) < R) ++bits;
+    int bits_R = 0;
+    while ((1u << bits_R) < R) ++bits_R;
     GridDev g;
     g.o[0] = grid->origin[0]; g.o[1] = grid->origin[1]; g.o[2] = grid->origin[2];
     g.s = 1.0f / grid->voxel_size;
@@ -79,97 +203,89 @@ extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, co
                                                        r1, r2));
     }
     VX_CUDA_TRY(cudaGetLastError());
-
-    // ---- candidate counts + offsets -------------------------------------------------
-    VX_TRY(vx_ws_ensure(ctx, WS_COUNT, (size_t)np * 4, s));
-    VX_TRY(vx_ws_ensure(ctx, WS_OFFS, (size_t)np * 4, s));
-    uint32_t* cnt = (uint32_t*)ctx->ws[WS_COUNT].p;
-    uint32_t* offs = (uint32_t*)ctx->ws[WS_OFFS].p;
-    const unsigned cblocks = (unsigned)std::min<size_t>((np + EMIT_WARPS - 1) / EMIT_WARPS, (size_t)vx::kSMs * 64);
-    if (fiber)
-        VX_LAUNCH(ctx, ST_COUNT, s, k_candidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, r2, np, (int)R, cnt, nullptr, nullptr,
-                                                                      nullptr));
-    else
-        VX_LAUNCH(ctx, ST_COUNT, s, k_candidates<false, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, r2, np, (int)R, cnt, nullptr, nullptr,
-                                                                       nullptr));
-    VX_TRY(vx_scan_u32(ctx, cnt, offs, np, misc + 1, s));
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 8, cudaMemcpyDeviceToHost, s));
-    VX_CUDA_TRY(cudaStreamSynchronize(s));
-    const uint32_t err = ((uint32_t*)ctx->host_pin)[0];
-    const uint32_t npairs = ((uint32_t*)ctx->host_pin)[1];
     vx_stage_units(ctx, ST_PREP, np);
-    vx_stage_units(ctx, ST_COUNT, npairs);
-    vx_stage_units(ctx, ST_EMIT, npairs);
-    vx_stage_units(ctx, ST_SORT_SCATTER, npairs);
-    vx_stage_units(ctx, ST_SORT_HIST, npairs);
-    vx_stage_units(ctx, ST_REDUCE_FIBERS + (fiber ? 0 : 1), npairs);
-    if (err) return VX_ERR_INVALID_ARG;
-    // the 32-bit scan wraps above 2^32-1 pairs; a total below the per-primitive maximum
-    // cannot be detected here, so bound the count by 2^31 as a capacity check instead.
-    if (npairs >= 0x80000000u) return VX_ERR_CAPACITY;
-    if (npairs == 0) return vx_level_alloc(ctx, out0, 0, 1, 0, (int)R, s);
 
-    // ---- emit + sort ------------------------------------------------------------------
-    VX_TRY(vx_ws_ensure(ctx, WS_KEYS0, (size_t)npairs * 4, s));
-    VX_TRY(vx_ws_ensure(ctx, WS_VALS0, (size_t)npairs * 4, s));
-    VX_TRY(vx_ws_ensure(ctx, WS_KEYS1, (size_t)npairs * 4, s));
-    VX_TRY(vx_ws_ensure(ctx, WS_VALS1, (size_t)npairs * 4, s));
-    uint32_t* k0 = (uint32_t*)ctx->ws[WS_KEYS0].p;
-    uint32_t* v0 = (uint32_t*)ctx->ws[WS_VALS0].p;
-    uint32_t* k1 = (uint32_t*)ctx->ws[WS_KEYS1].p;
-    uint32_t* v1 = (uint32_t*)ctx->ws[WS_VALS1].p;
-    if (fiber)
-        VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, r2, np, (int)R, nullptr, offs, k0, v0));
-    else
-        VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<false, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, r2, np, (int)R, nullptr, offs, k0, v0));
-    VX_CUDA_TRY(cudaGetLastError());
-    VX_TRY(vx_radix_sort_u32(ctx, &k0, &v0, &k1, &v1, npairs, 3 * bits, s));
-
-    // ---- segments ---------------------------------------------------------------------
-    VX_TRY(vx_ws_ensure(ctx, WS_FLAGS, (size_t)npairs * 4, s));
-    VX_TRY(vx_ws_ensure(ctx, WS_STARTS, (size_t)npairs * 4 + 8, s));
-    uint32_t* flags = (uint32_t*)ctx->ws[WS_FLAGS].p;
-    uint32_t* starts = (uint32_t*)ctx->ws[WS_STARTS].p;
-    VX_LAUNCH(ctx, ST_HEADS, s, k_head_flags<<<grid_for(npairs, 256), 256, 0, s>>>(k0, npairs, flags));
-    VX_TRY(vx_scan_u32(ctx, flags, flags, npairs, misc + 2, s));
-    VX_LAUNCH(ctx, ST_HEADS, s, k_head_starts<<<grid_for(npairs, 256), 256, 0, s>>>(k0, npairs, flags, misc + 2, starts));
-    VX_CUDA_TRY(cudaGetLastError());
-
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc + 2, 4, cudaMemcpyDeviceToHost, s));
-    VX_CUDA_TRY(cudaStreamSynchronize(s));
-    const uint32_t nseg = ((uint32_t*)ctx->host_pin)[0];
-    vx_stage_units(ctx, ST_FINALIZE, nseg);
-
-    // ---- per-voxel reduction ----------------------------------------------------------
-    // temp outputs per candidate voxel: mask 64 + mass 4 + moment 24 bytes; the sort's
-    // alternate buffers are free now and hold the key and the non-empty flag.
-    VX_TRY(vx_ws_ensure(ctx, WS_SEG_OUT, (size_t)nseg * (64 + 4 + 24), s));
-    char* so = (char*)ctx->ws[WS_SEG_OUT].p;
-    SegOut seg;
-    seg.mask = (uint64_t*)so;
-    seg.mass = (float*)(so + (size_t)nseg * 64);
-    seg.moment = (float*)(so + (size_t)nseg * 68);
-    seg.key = k1;
-    seg.nonzero = v1;
-    const unsigned rblocks = (unsigned)std::min<size_t>((nseg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 32);
-    if (fiber)
-        VX_LAUNCH(ctx, ST_REDUCE_FIBERS, s, k_reduce_fibers<<<rblocks, RED_WARPS * 32, 0, s>>>(k0, v0, starts, misc + 2, r0, r1, seg));
-    else
-        VX_LAUNCH(ctx, ST_REDUCE_TRIS, s, k_reduce_tris<<<rblocks, RED_WARPS * 32, 0, s>>>(k0, v0, starts, misc + 2, r0, r1, r2, seg));
-    VX_CUDA_TRY(cudaGetLastError());
-
-    // ---- compaction: dst = exclusive scan of the non-empty flags ----------------------------
-    uint32_t* dst = flags;   // the head flags are no longer needed
-    VX_TRY(vx_scan_u32(ctx, seg.nonzero, dst, nseg, misc + 3, s));
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc + 3, 4, cudaMemcpyDeviceToHost, s));
-    VX_CUDA_TRY(cudaStreamSynchronize(s));
-    const uint32_t nvox = ((uint32_t*)ctx->host_pin)[0];
-    VX_TRY(vx_level_alloc(ctx, out0, nvox, 1, 0, (int)R, s));
-    if (nvox > 0) {
-        VX_LAUNCH(ctx, ST_FINALIZE, s, k_finalize<<<grid_for(nseg, 256), 256, 0, s>>>(seg, misc + 2, dst, *out0));
-        VX_CUDA_TRY(cudaGetLastError());
+    // ---- windows: the whole grid, split into octants (Morton order) while a window is
+    // wider than 1024 voxels (30-bit keys) or holds more candidate pairs than one pass may
+    std::vector<vx_level> parts;
+    vx_status st = VX_OK;
+    struct Pending { int lo[3]; int lg; };
+    std::vector<Pending> stack;
+    stack.push_back(Pending{{0, 0, 0}, bits_R});
+    while (!stack.empty() && st == VX_OK) {
+        const Pending w = stack.back();
+        stack.pop_back();
+        Window win;
+        for (int i = 0; i < 3; ++i) { win.lo[i] = w.lo[i]; win.hi[i] = w.lo[i] + (1 << w.lg) - 1; }
+        uint64_t total = 0;
+        st = count_window(ctx, fiber, np, win, r0, r1, r2, misc, s, &total);
+        if (st != VX_OK) break;
+        if (total == 0 && w.lg < bits_R) continue;            // an empty octant adds nothing
+        const uint64_t limit = (uint64_t)std::min<int64_t>(ctx->max_pairs, 0x7fffffffll);
+        if (w.lg <= 10 && total <= limit) {
+            const uint64_t key_hi = vx_morton3_64((uint32_t)(w.lo[0] >> w.lg), (uint32_t)(w.lo[1] >> w.lg),
+                                               (uint32_t)(w.lo[2] >> w.lg)) << (3 * w.lg);
+            parts.emplace_back();
+            st = voxelize_window(ctx, fiber, np, win, w.lg, key_hi, (int)R, (uint32_t)total, r0, r1, r2, misc, s,
+                                 &parts.back());
+            if (st != VX_OK) parts.pop_back();
+            continue;
+        }
+        if (w.lg == 0) { st = VX_ERR_CAPACITY; break; }      // one voxel over the limit
+        const int half = 1 << (w.lg - 1);
+        for (int o = 7; o >= 0; --o) {                          // pushed in reverse: popped in Morton order
+            Pending c;
+            c.lg = w.lg - 1;
+            c.lo[0] = w.lo[0] + ((o & 1) ? half : 0);
+            c.lo[1] = w.lo[1] + ((o & 2) ? half : 0);
+            c.lo[2] = w.lo[2] + ((o & 4) ? half : 0);
+            stack.push_back(c);
+        }
     }
-    return VX_OK;
+    if (st != VX_OK) {
+        for (auto& P : parts) vx_level_release(ctx, &P, s);
+        return st;
+    }
+    if (parts.size() == 1) {
+        *out0 = parts[0];
+        return VX_OK;
+    }
+    int64_t total = 0;
+    for (auto& P : parts) total += P.num_voxels;
+    const size_t ntiles = parts.size();
+    if (st == VX_OK) st = vx_level_alloc(ctx, out0, total, 1, 0, (int)R, s);
+    int64_t at = 0;
+    for (size_t t = 0; t < ntiles && st == VX_OK; ++t) {
+        const vx_level& P = parts[t];
+        const size_t n = (size_t)P.num_voxels;
+        if (n) {
+            const cudaError_t e =
+                [&]() {
+                    cudaError_t r = cudaSuccess;
+                    auto cp = [&](void* d, const void* src, size_t bytes) {
+                        if (r == cudaSuccess) r = cudaMemcpyAsync(d, src, bytes, cudaMemcpyDeviceToDevice, s);
+                    };
+                    cp(out0->keys + at, P.keys, n * 8);
+                    cp(out0->mask + (size_t)at * 8, P.mask, n * 64);
+                    cp(out0->mass + at, P.mass, n * 4);
+                    cp(out0->moment + (size_t)at * 6, P.moment, n * 24);
+                    cp(out0->occ + at, P.occ, n * 2);
+                    cp(out0->occ_proj + (size_t)at * 3, P.occ_proj, n * 3);
+                    cp(out0->lobe_count + at, P.lobe_count, n);
+                    cp(out0->lobes + (size_t)at * 7, P.lobes, n * 28);
+                    cp(out0->compact + (size_t)at * 6, P.compact, n * 24);
+                    return r;
+                }();
+            if (e != cudaSuccess) {
+                vx_record_cuda_error(ctx, e, "cudaMemcpyAsync");
+                st = VX_ERR_CUDA;
+            }
+        }
+        at += (int64_t)n;
+    }
+    for (size_t t = 0; t < ntiles; ++t) vx_level_release(ctx, &parts[t], s);
+    if (st != VX_OK) vx_level_release(ctx, out0, s);
+    return st;
 }
 
 // =====================================================================================
@@ -345,6 +461,166 @@ __global__ void k_adjoint_ctrl(const int64_t* __restrict__ off, int64_t F, const
     gctrl[c] = g;
 }
 
+// d/d(U0, U1, U2, w) of  w * area(T ∩ voxel) * (gm + gM . T(n))  for one (triangle, voxel)
+// pair (grid units, FP64); out[3j + k] = d/dU_j[k], out[9] = d/dw.
+// The triangle is the image of the reference triangle {s, t >= 0, s + t <= 1} under
+// (s, t) -> U0 + s e1 + t e2, so area(T ∩ voxel) = J * A, J = |e1 x e2|, A the area of
+// the reference polygon cut out by the six voxel half-planes.  A box constraint
+// g(s, t) <= 0 whose value changes by dg when a vertex moves shifts its polygon edge
+// outward by -dg / |grad g|, so dA = -sum over the polygon's edges on box planes of
+// (edge length / |grad g|) * dg(edge midpoint) (dg is affine in s, t).  The clip
+// decisions are taken on voxel-local coordinates, as the forward's clip takes them: a
+// vertex or an edge lying exactly on a voxel plane (a heightfield's border row) stays
+// inside, and its derivative is that of the piece it belongs to.
+__device__ void tri_pair_grad(const float4 P0, const float4 P1, const float4 P2, int vi, int vj, int vk, double gm,
+                              const double* gM, double* out) {
+#pragma unroll
+    for (int c = 0; c < 10; ++c) out[c] = 0.0;
+    const double e1[3] = {(double)P1.x - P0.x, (double)P1.y - P0.y, (double)P1.z - P0.z};
+    const double e2[3] = {(double)P2.x - P0.x, (double)P2.y - P0.y, (double)P2.z - P0.z};
+    // polygon vertices carry their voxel-local coordinates (x, y, z: every clip decision is
+    // taken on them, exact for the triangle's own vertices) and their reference-domain
+    // coordinates (s, t); lab[i] labels the edge i -> i+1: -1 a triangle edge, 2k + side a
+    // voxel plane
+    double px[12], py[12], pz[12], ps[12], pt[12];
+    double qx[12], qy[12], qz[12], qs[12], qt[12];
+    int lab[12], qlab[12];
+    px[0] = (double)P0.x - vi; py[0] = (double)P0.y - vj; pz[0] = (double)P0.z - vk;
+    px[1] = (double)P1.x - vi; py[1] = (double)P1.y - vj; pz[1] = (double)P1.z - vk;
+    px[2] = (double)P2.x - vi; py[2] = (double)P2.y - vj; pz[2] = (double)P2.z - vk;
+    ps[0] = 0.0; pt[0] = 0.0; ps[1] = 1.0; pt[1] = 0.0; ps[2] = 0.0; pt[2] = 1.0;
+    lab[0] = lab[1] = lab[2] = -1;
+    int n = 3;
+    for (int c = 0; c < 6 && n > 0; ++c) {
+        const int k = c >> 1;
+        const bool hi = c & 1;
+        const double bound = hi ? 1.0 : 0.0;
+        int m = 0;
+        for (int i = 0; i < n; ++i) {
+            const int j = (i + 1 == n) ? 0 : i + 1;
+            const double xi = k == 0 ? px[i] : (k == 1 ? py[i] : pz[i]);
+            const double xj = k == 0 ? px[j] : (k == 1 ? py[j] : pz[j]);
+            const bool sin_ = hi ? (xi <= 1.0) : (xi >= 0.0);
+            const bool ein = hi ? (xj <= 1.0) : (xj >= 0.0);
+            if (sin_) {
+                qx[m] = px[i]; qy[m] = py[i]; qz[m] = pz[i]; qs[m] = ps[i]; qt[m] = pt[i]; qlab[m] = lab[i];
+                ++m;
+            }
+            if (sin_ != ein) {
+                const double l = (bound - xi) / (xj - xi);
+                qx[m] = k == 0 ? bound : px[i] + l * (px[j] - px[i]);
+                qy[m] = k == 1 ? bound : py[i] + l * (py[j] - py[i]);
+                qz[m] = k == 2 ? bound : pz[i] + l * (pz[j] - pz[i]);
+                qs[m] = ps[i] + l * (ps[j] - ps[i]);
+                qt[m] = pt[i] + l * (pt[j] - pt[i]);
+                qlab[m] = sin_ ? c : lab[i];
+                ++m;
+            }
+        }
+        n = m;
+        for (int i = 0; i < n; ++i) {
+            px[i] = qx[i]; py[i] = qy[i]; pz[i] = qz[i]; ps[i] = qs[i]; pt[i] = qt[i]; lab[i] = qlab[i];
+        }
+    }
+    if (n < 3) return;
+    double A = 0.0;
+    double dA[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int i = 0; i < n; ++i) {
+        const int j = (i + 1 == n) ? 0 : i + 1;
+        A += ps[i] * pt[j] - ps[j] * pt[i];
+        const int c = lab[i];
+        if (c < 0) continue;
+        const int k = c >> 1;
+        const double gn = sqrt(e1[k] * e1[k] + e2[k] * e2[k]);
+        if (gn == 0.0) continue;
+        const double ds = ps[j] - ps[i], dt = pt[j] - pt[i];
+        const double f = -sqrt(ds * ds + dt * dt) / gn * ((c & 1) ? 1.0 : -1.0);
+        const double sm = 0.5 * (ps[i] + ps[j]), tm = 0.5 * (pt[i] + pt[j]);
+        dA[0][k] += f * (1.0 - sm - tm);
+        dA[1][k] += f * sm;
+        dA[2][k] += f * tm;
+    }
+    A *= 0.5;
+    const double nr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const double J = sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
+    if (!(J > 0.0) || !(A > 0.0)) return;
+    const double nh[3] = {nr[0] / J, nr[1] / J, nr[2] / J};
+    const double mu = J * A;
+    const double G = gm + gM[0] * nh[0] * nh[0] + gM[1] * nh[1] * nh[1] + gM[2] * nh[2] * nh[2] +
+                     gM[3] * nh[0] * nh[1] + gM[4] * nh[0] * nh[2] + gM[5] * nh[1] * nh[2];
+    double gt[3];
+    gt[0] = 2.0 * gM[0] * nh[0] + gM[3] * nh[1] + gM[4] * nh[2];
+    gt[1] = gM[3] * nh[0] + 2.0 * gM[1] * nh[1] + gM[5] * nh[2];
+    gt[2] = gM[4] * nh[0] + gM[5] * nh[1] + 2.0 * gM[2] * nh[2];
+    const double ng = nh[0] * gt[0] + nh[1] * gt[1] + nh[2] * gt[2];
+    // q = d G / d (raw normal)
+    const double q[3] = {(gt[0] - nh[0] * ng) / J, (gt[1] - nh[1] * ng) / J, (gt[2] - nh[2] * ng) / J};
+    const double w = P0.w;
+    const double U[3][3] = {{P0.x, P0.y, P0.z}, {P1.x, P1.y, P1.z}, {P2.x, P2.y, P2.z}};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        // d J / d U_j = (U_j+1 - U_j+2) x nh,  d G / d U_j = (U_j+1 - U_j+2) x q
+        const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        const double d[3] = {U[j1][0] - U[j2][0], U[j1][1] - U[j2][1], U[j1][2] - U[j2][2]};
+        const double dJ[3] = {d[1] * nh[2] - d[2] * nh[1], d[2] * nh[0] - d[0] * nh[2], d[0] * nh[1] - d[1] * nh[0]};
+        const double dG[3] = {d[1] * q[2] - d[2] * q[1], d[2] * q[0] - d[0] * q[2], d[0] * q[1] - d[1] * q[0]};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) out[3 * j + k] = w * ((dJ[k] * A + J * dA[j][k]) * G + mu * dG[k]);
+    }
+    out[9] = mu * G;
+}
+
+// warp per triangle: sum of its pair gradients (lane j takes pairs j, j+32, ...; fixed tree)
+__global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_tris(const float4* __restrict__ r0,
+                                                                  const float4* __restrict__ r1,
+                                                                  const float4* __restrict__ r2, uint32_t np,
+                                                                  const uint32_t* __restrict__ offs,
+                                                                  const uint32_t* __restrict__ cnt,
+                                                                  const uint32_t* __restrict__ pkeys,
+                                                                  const uint64_t* __restrict__ keys0, uint32_t V0,
+                                                                  const double* __restrict__ gm,
+                                                                  const double* __restrict__ gM,
+                                                                  double* __restrict__ tri_grad) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * EMIT_WARPS;
+    for (uint32_t p = blockIdx.x * EMIT_WARPS + (threadIdx.x >> 5); p < np; p += warps) {
+        const float4 A = r0[p], B = r1[p], Cv = r2[p];
+        const uint32_t beg = offs[p], n = cnt[p];
+        double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (uint32_t j = lane; j < n; j += 32) {
+            const uint32_t key = pkeys[beg + j];
+            const int64_t v = find_key64(keys0, V0, (uint64_t)key);
+            if (v < 0) continue;
+            double g[10];
+            double gMv[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) gMv[c] = gM[(size_t)v * 6 + c];
+            tri_pair_grad(A, B, Cv, (int)vx_compact1by2(key), (int)vx_compact1by2(key >> 1),
+                          (int)vx_compact1by2(key >> 2), gm[v], gMv, g);
+#pragma unroll
+            for (int c = 0; c < 10; ++c) acc[c] = acc[c] + g[c];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < 10; ++c) acc[c] = acc[c] + __shfl_xor_sync(0xffffffffu, acc[c], o);
+        if (lane < 10) tri_grad[(size_t)p * 10 + lane] = acc[lane];
+    }
+}
+
+// thread per triangle: world-unit vertex gradients ([T][3] float4, w = 0) and weights
+__global__ void k_adjoint_tri_out(const double* __restrict__ tri_grad, uint32_t np, float s,
+                                  float4* __restrict__ gverts, float* __restrict__ gw) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const double* q = tri_grad + (size_t)p * 10;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        gverts[(size_t)p * 3 + j] = make_float4((float)(q[3 * j] * (double)s), (float)(q[3 * j + 1] * (double)s),
+                                                (float)(q[3 * j + 2] * (double)s), 0.0f);
+    if (gw) gw[p] = (float)q[9];
+}
+
 __global__ void k_adjoint_weights(const double* __restrict__ seg_grad, uint32_t np, float* __restrict__ gw) {
     uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < np) gw[p] = (float)seg_grad[(size_t)p * 8 + 7];
@@ -359,25 +635,28 @@ extern "C" vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, co
     if (!ctx || !prims || !grid || !grad_mass || !grad_moment || !grad_ctrl) return VX_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     ctx->last_stream = s;
-    if (prims->kind != VX_FIBERS) return VX_ERR_UNSUPPORTED;
+    const bool fiber = prims->kind == VX_FIBERS;
+    if (!fiber && prims->kind != VX_TRIANGLES) return VX_ERR_INVALID_ARG;
     const uint32_t R = grid->resolution;
     if (R == 0 || (R & (R - 1)) != 0) return VX_ERR_INVALID_ARG;
     if (R > 1024 || grid->sub_res != 8) return VX_ERR_UNSUPPORTED;
     if (num_voxels0 < 0 || num_voxels0 > 0xffffffffll || num_levels < 0 || num_levels > 11) return VX_ERR_INVALID_ARG;
     if (prims->num_prims < 0 || prims->num_prims > 0xfffffffell) return VX_ERR_CAPACITY;
-    if (!prims->ctrl || !prims->fiber_offsets || prims->num_fibers <= 0 || ((uintptr_t)prims->ctrl & 15) != 0 ||
-        ((uintptr_t)grad_ctrl & 15) != 0)
+    if (((uintptr_t)grad_ctrl & 15) != 0) return VX_ERR_INVALID_ARG;
+    if (fiber && (!prims->ctrl || !prims->fiber_offsets || prims->num_fibers <= 0 || ((uintptr_t)prims->ctrl & 15) != 0))
+        return VX_ERR_INVALID_ARG;
+    if (!fiber && prims->num_prims > 0 && (!prims->tri_verts || ((uintptr_t)prims->tri_verts & 15) != 0))
         return VX_ERR_INVALID_ARG;
     for (int l = 0; l <= num_levels; ++l)
         if (!grad_mass[l] || !grad_moment[l]) return VX_ERR_INVALID_ARG;
     const uint32_t np = (uint32_t)prims->num_prims;
     const uint32_t V0 = (uint32_t)num_voxels0;
-    const int64_t P = prims->num_ctrl, F = prims->num_fibers;
+    const int64_t P = fiber ? prims->num_ctrl : 3 * (int64_t)np, F = prims->num_fibers;
     GridDev g;
     g.o[0] = grid->origin[0]; g.o[1] = grid->origin[1]; g.o[2] = grid->origin[2];
     g.s = 1.0f / grid->voxel_size;
     g.R = (int)R;
-    VX_CUDA_TRY(cudaMemsetAsync(grad_ctrl, 0, (size_t)P * 16, s));
+    if (P) VX_CUDA_TRY(cudaMemsetAsync(grad_ctrl, 0, (size_t)P * 16, s));
     if (grad_weights && np) VX_CUDA_TRY(cudaMemsetAsync(grad_weights, 0, (size_t)np * 4, s));
     if (np == 0) return VX_OK;
 
@@ -407,21 +686,34 @@ extern "C" vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, co
     VX_CUDA_TRY(cudaMemsetAsync(misc, 0, 64, s));
     float4* r0 = (float4*)ctx->ws[WS_REC_A].p;
     float4* r1 = (float4*)ctx->ws[WS_REC_B].p;
-    if (F > 0x7fffffff) return VX_ERR_CAPACITY;
-    VX_TRY(vx_ws_ensure(ctx, WS_FIBER_START, (size_t)F * 4 + 256, s));
-    uint32_t* fs = (uint32_t*)ctx->ws[WS_FIBER_START].p;
-    VX_LAUNCH(ctx, ST_PREP, s, k_fiber_seg_counts<<<grid_for((size_t)F, 256), 256, 0, s>>>(prims->fiber_offsets, F, fs));
-    VX_TRY(vx_scan_u32(ctx, fs, fs, (uint32_t)F, misc + 4, s));
-    VX_LAUNCH(ctx, ST_PREP, s, k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl,
-                                                                             prims->fiber_offsets, fs, F, misc + 4,
-                                                                             prims->weights, np, g, r0, r1, misc));
+    float4* r2 = nullptr;
+    uint32_t* fs = nullptr;
+    if (fiber) {
+        if (F > 0x7fffffff) return VX_ERR_CAPACITY;
+        VX_TRY(vx_ws_ensure(ctx, WS_FIBER_START, (size_t)F * 4 + 256, s));
+        fs = (uint32_t*)ctx->ws[WS_FIBER_START].p;
+        VX_LAUNCH(ctx, ST_PREP, s, k_fiber_seg_counts<<<grid_for((size_t)F, 256), 256, 0, s>>>(prims->fiber_offsets, F, fs));
+        VX_TRY(vx_scan_u32(ctx, fs, fs, (uint32_t)F, misc + 4, s));
+        VX_LAUNCH(ctx, ST_PREP, s, k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl,
+                                                                                 prims->fiber_offsets, fs, F, misc + 4,
+                                                                                 prims->weights, np, g, r0, r1, misc));
+    } else {
+        VX_TRY(vx_ws_ensure(ctx, WS_REC_C, (size_t)np * 16, s));
+        r2 = (float4*)ctx->ws[WS_REC_C].p;
+        VX_LAUNCH(ctx, ST_PREP, s, k_prep_tris<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->tri_verts,
+                                                                               prims->weights, np, g, r0, r1, r2));
+    }
     VX_TRY(vx_ws_ensure(ctx, WS_COUNT, (size_t)np * 4, s));
     VX_TRY(vx_ws_ensure(ctx, WS_OFFS, (size_t)np * 4, s));
     uint32_t* cnt = (uint32_t*)ctx->ws[WS_COUNT].p;
     uint32_t* offs = (uint32_t*)ctx->ws[WS_OFFS].p;
     const unsigned cblocks = (unsigned)std::min<size_t>((np + EMIT_WARPS - 1) / EMIT_WARPS, (size_t)vx::kSMs * 64);
-    VX_LAUNCH(ctx, ST_COUNT, s, k_candidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                    r0, r1, nullptr, np, (int)R, cnt, nullptr, nullptr, nullptr));
+    if (fiber)
+        VX_LAUNCH(ctx, ST_COUNT, s, k_candidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                        r0, r1, nullptr, np, full_window((int)R), cnt, nullptr, nullptr, nullptr));
+    else
+        VX_LAUNCH(ctx, ST_COUNT, s, k_candidates<false, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                        r0, r1, r2, np, full_window((int)R), cnt, nullptr, nullptr, nullptr));
     VX_TRY(vx_scan_u32(ctx, cnt, offs, np, misc + 1, s));
     VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 8, cudaMemcpyDeviceToHost, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
@@ -432,9 +724,23 @@ extern "C" vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, co
     VX_TRY(vx_ws_ensure(ctx, WS_VALS0, (size_t)std::max<uint32_t>(npairs, 1) * 4, s));
     uint32_t* k0 = (uint32_t*)ctx->ws[WS_KEYS0].p;
     uint32_t* v0 = (uint32_t*)ctx->ws[WS_VALS0].p;
-    if (npairs)
+    if (npairs && fiber)
         VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                       r0, r1, nullptr, np, (int)R, nullptr, offs, k0, v0));
+                                       r0, r1, nullptr, np, full_window((int)R), nullptr, offs, k0, v0));
+    if (npairs && !fiber)
+        VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<false, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                       r0, r1, r2, np, full_window((int)R), nullptr, offs, k0, v0));
+    if (!fiber) {
+        // ---- per-triangle gradients (no sharing between triangles: no scatter) ---------------
+        VX_TRY(vx_ws_ensure(ctx, WS_SEG_OUT, (size_t)np * 80, s));
+        double* tri_grad = (double*)ctx->ws[WS_SEG_OUT].p;
+        VX_LAUNCH(ctx, ST_REDUCE_TRIS, s, k_adjoint_tris<<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                              r0, r1, r2, np, offs, cnt, k0, keys0, V0, gm, gM, tri_grad));
+        VX_LAUNCH(ctx, ST_FINALIZE, s, k_adjoint_tri_out<<<grid_for(np, 256), 256, 0, s>>>(
+                                           tri_grad, np, g.s, (float4*)grad_ctrl, grad_weights));
+        VX_CUDA_TRY(cudaGetLastError());
+        return VX_OK;
+    }
     // ---- per-segment gradients, then the control-point scatter ---------------------------
     VX_TRY(vx_ws_ensure(ctx, WS_SEG_OUT, (size_t)np * 64, s));
     double* seg_grad = (double*)ctx->ws[WS_SEG_OUT].p;
@@ -572,8 +878,8 @@ extern "C" vx_status vx_backward_noalloc(const vx_primitives* prims, const vx_gr
     k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl, prims->fiber_offsets, fs, F, misc + 4,
                                                      prims->weights, np, g, r0, r1, misc);
     const unsigned cblocks = (unsigned)std::min<size_t>((np + EMIT_WARPS - 1) / EMIT_WARPS, (size_t)vx::kSMs * 64);
-    k_candidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, nullptr, np, (int)R, cnt, nullptr, nullptr,
-                                                                  nullptr);
+    k_candidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, nullptr, np, full_window((int)R), cnt,
+                                                                  nullptr, nullptr, nullptr);
     NA_TRY(vx_scan_u32_scratch(cnt, offs, np, misc + 1, part, s));
     uint32_t host[2] = {0, 0};
     NA_TRY(cudaMemcpyAsync(host, misc, 8, cudaMemcpyDeviceToHost, s));
@@ -582,8 +888,8 @@ extern "C" vx_status vx_backward_noalloc(const vx_primitives* prims, const vx_gr
     const uint32_t npairs = host[1];
     if (npairs > NA_MAX_PAIRS) return VX_ERR_CAPACITY;
     if (npairs)
-        k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, nullptr, np, (int)R, nullptr, offs, k0,
-                                                                     v0);
+        k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, nullptr, np, full_window((int)R), nullptr,
+                                                                     offs, k0, v0);
     k_adjoint_fibers<<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, np, offs, cnt, k0, keys0, V0, gm, gM, seg_grad);
     k_adjoint_ctrl<<<grid_for((size_t)P, 256), 256, 0, s>>>(prims->fiber_offsets, F, fs, P, seg_grad, g.s,
                                                              (float4*)grad_ctrl);

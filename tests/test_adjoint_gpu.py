@@ -147,3 +147,104 @@ def test_adjoint_finite_differences_yarn_256(ctx):
         assert err <= 1e-4, (c, comp, g_ctrl[c, comp], f1)
         checked += 1
     print(f"FD checked {checked}, stencils across a kink skipped {kinks}, worst rel {worst:.2e}")
+
+
+# ----------------------------------------------------------------------------
+# triangles: the config-1 heightfield
+# ----------------------------------------------------------------------------
+def gpu_tri_forward_backward(ctx, w, levels, weights):
+    tv = torch.from_numpy(w.tri_verts).to(DEV).requires_grad_(True)
+    wt = torch.from_numpy(weights).to(DEV).requires_grad_(True)
+    outs = vx.VoxelizeLoD.apply(tv, wt, None, w.grid, levels, ctx)
+    L0 = ctx.voxelize(w.grid, tri_verts=tv.detach(), weights=wt.detach())
+    pyr = ctx.build_lod(L0, K=1, num_levels=levels)
+    keys = [lv.keys.cpu().numpy().view(np.uint64) for lv in [L0] + pyr]
+    loss = 0.0
+    for l in range(levels + 1):
+        a, b = synth.loss_weights(keys[l], l)
+        loss = loss + (outs[2 * l] * torch.from_numpy(a).to(DEV)).sum() + \
+            (outs[2 * l + 1] * torch.from_numpy(b).to(DEV)).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    return tv.grad.cpu().numpy(), wt.grad.cpu().numpy(), keys
+
+
+@pytest.fixture(scope="module")
+def heightfield_grads(ctx):
+    w = synth.config1()
+    levels = 4
+    rng = np.random.default_rng(52)
+    weights = rng.uniform(0.5, 2.0, w.num_prims).astype(np.float32)
+    g_t, g_w, keys = gpu_tri_forward_backward(ctx, w, levels, weights)
+    ref0 = oracle.voxelize_tris(w.tri_verts, w.grid, weights)
+    refs = [ref0] + oracle.build_pyramid(ref0, w.grid.resolution, 1, synth.sample_directions(16), num_levels=levels)
+    for l in range(levels + 1):
+        assert np.array_equal(refs[l]["keys"], keys[l])
+    ab = [synth.loss_weights(r["keys"], l) for l, r in enumerate(refs)]
+    gm0, gM0 = oracle.broadcast_adjoints(ref0["keys"], [r["keys"] for r in refs], [a for a, _ in ab],
+                                         [b for _, b in ab])
+    return w, weights, g_t, g_w, ref0["keys"], gm0, gM0
+
+
+def grid_coords32(w):
+    """Grid coordinates as the method computes them (Sec. 3.1 normalisation in FP32):
+    U = (p - origin) * (1 / h), each operation rounded to FP32."""
+    o = np.asarray(w.grid.origin, np.float32)
+    s = np.float32(1.0) / np.float32(w.grid.voxel_size)
+    return (w.tri_verts[..., :3].astype(np.float32) - o) * s, float(s)
+
+
+def test_tri_adjoint_matches_oracle_gradient(heightfield_grads):
+    """GPU analytic (reference-domain) gradient against the oracle's complex-step one, both
+    taken at the FP32 grid coordinates the method works on (a heightfield triangle almost
+    parallel to a voxel plane has a gradient that moves by ~1e-4 relative under the
+    ~1e-5-voxel rounding of the normalisation, so the two sides must see the same input)."""
+    w, weights, g_t, g_w, keys0, gm0, gM0 = heightfield_grads
+    U, s = grid_coords32(w)
+    unit = synth.Grid((0.0, 0.0, 0.0), 1.0, w.grid.resolution)
+    _, d_u, d_w = oracle.tri_adjoint(U.astype(np.float64), unit, keys0, gm0, gM0, weights=weights)
+    d_t = d_u * s
+    assert g_t.shape == (w.num_prims, 3, 4)
+    assert np.all(g_t[..., 3] == 0.0)
+    scale = np.median(np.abs(d_t))
+    err = np.abs(g_t[..., :3] - d_t)
+    assert np.all(err <= 1e-4 * np.maximum(np.abs(d_t), scale)), err.max()
+    ws = np.median(np.abs(d_w))
+    assert np.all(np.abs(g_w - d_w) <= 1e-4 * np.maximum(np.abs(d_w), ws))
+
+
+def test_tri_adjoint_finite_differences_heightfield(heightfield_grads):
+    """FP64 central FD (h = 1e-4 voxel units) of the heightfield loss, as a function of the
+    FP32 grid coordinates, on 64 random vertex coordinates whose stencil keeps every
+    clipped polygon's structure."""
+    w, weights, g_t, _, keys0, gm0, gM0 = heightfield_grads
+    rng = np.random.default_rng(53)
+    U, s = grid_coords32(w)
+    u64 = U.astype(np.float64)
+    unit = synth.Grid((0.0, 0.0, 0.0), 1.0, w.grid.resolution)
+    w64 = weights.astype(np.float64)
+    h = 1e-4
+    checked, kinks, worst = 0, 0, 0.0
+    while checked < 64:
+        assert kinks < 640, "too many stencils cross a kink"
+        p, k, i = int(rng.integers(0, u64.shape[0])), int(rng.integers(0, 3)), int(rng.integers(0, 3))
+        sig = set()
+        for st in (-h, 0.0, h):
+            tt = u64.copy(); tt[p, k, i] += st
+            sig.add(oracle.tri_clip_signature(tt, unit, [p]))
+        if len(sig) != 1:
+            kinks += 1
+            continue
+
+        def local_loss(step):
+            tt = u64.copy(); tt[p, k, i] += step
+            return oracle.tri_adjoint(tt, unit, keys0, gm0, gM0, weights=w64, prims=[p])[0]
+        fd = (local_loss(h) - local_loss(-h)) / (2 * h)
+        _, d_u, _, d_abs = oracle.tri_adjoint(u64, unit, keys0, gm0, gM0, weights=w64, prims=[p], with_abs=True)
+        scale = max(abs(fd), 0.01 * d_abs[p, k, i], 1e-3)
+        assert abs(d_u[p, k, i] - fd) <= 1e-4 * scale, (p, k, i, d_u[p, k, i], fd)
+        err = abs(g_t[p, k, i] / s - fd) / scale
+        worst = max(worst, err)
+        assert err <= 1e-4, (p, k, i, g_t[p, k, i] / s, fd)
+        checked += 1
+    print(f"FD checked {checked}, stencils across a kink skipped {kinks}, worst rel {worst:.2e}")

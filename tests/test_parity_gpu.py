@@ -227,7 +227,7 @@ def test_invalid_arguments(ctx):
         ctx.voxelize(synth.Grid((0.0, 0.0, 0.0), 1.0 / 12, 12), ctrl=ctrl, fiber_offsets=off)
     assert e.value.status == 1
     with pytest.raises(vx.VxError) as e:
-        ctx.voxelize(synth.Grid((0.0, 0.0, 0.0), 1.0 / 2048, 2048), ctrl=ctrl, fiber_offsets=off)
+        ctx.voxelize(synth.Grid((0.0, 0.0, 0.0), 1.0 / 4096, 4096), ctrl=ctrl, fiber_offsets=off)
     assert e.value.status == 6
     L0 = ctx.voxelize(grid, ctrl=ctrl, fiber_offsets=off)
     with pytest.raises(vx.VxError) as e:
@@ -245,3 +245,59 @@ def test_deterministic(ctx, dirs5000):
     for x, y in zip(a, b):
         for k in ("keys", "mask", "mass", "moment", "lobes", "lobe_count", "compact"):
             assert np.array_equal(np.asarray(x[k]).view(np.uint8), np.asarray(y[k]).view(np.uint8)), k
+
+
+def test_tiled_2048_grid(ctx, dirs5000):
+    """A 2048^3 grid runs as eight 1024^3 tiles: fibers crossing the tile planes at 1024."""
+    R = 2048
+    rng = np.random.default_rng(12)
+    h = 1.0 / R
+    ctrl, off = [], [0]
+    for f in range(12):
+        p = np.array([1024.0, 1024.0, 1024.0]) + rng.uniform(-6, 6, 3)
+        d = rng.standard_normal(3); d /= np.linalg.norm(d)
+        r = rng.uniform(0.3, 2.0)
+        for k in range(12):
+            ctrl.append([p[0] * h, p[1] * h, p[2] * h, r * h])
+            d = d + 0.5 * rng.standard_normal(3); d /= np.linalg.norm(d)
+            p = p + d * rng.uniform(0.3, 1.5)
+        off.append(len(ctrl))
+    w = synth.Workload("t2048", "fibers", synth.Grid((0.0, 0.0, 0.0), h, R),
+                       ctrl=np.asarray(ctrl, np.float32), fiber_offsets=np.asarray(off, np.int64), K=1)
+    got = run_gpu(ctx, w, dirs=dirs5000, num_levels=4)
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, R, 1, dirs5000, num_levels=4)
+    tiles = np.unique(got[0]["keys"] >> np.uint64(30))
+    assert tiles.size == 8, tiles
+    for lvl, (g, r) in enumerate(zip(got, refs)):
+        compare_level(g, r, f"level {lvl}", mu_max=prim_measure_max(w))
+
+
+@pytest.mark.parametrize("kind", ["fibers", "triangles"])
+def test_windows_split_by_pair_limit(ctx, dirs5000, kind):
+    """A per-pass pair limit far below the total splits the grid into octant windows,
+    recursively; the concatenated level is bit-identical to the oracle and to one pass."""
+    R = 64
+    if kind == "fibers":
+        ctrl, off, grid = synth.random_segments(6, 10, R, seed=21, radius=(0.2, 1.5), step=(0.5, 2.5))
+        w = synth.Workload("split-f", "fibers", grid, ctrl=ctrl, fiber_offsets=off, K=4)
+    else:
+        tris, grid = synth.random_triangles(60, R, seed=22, size=(0.5, 4.0))
+        w = synth.Workload("split-t", "triangles", grid, tri_verts=tris, K=4)
+    one = run_gpu(ctx, w, dirs=dirs5000, num_levels=3)
+    try:
+        ctx.set_max_pairs_per_pass(97)
+        split = run_gpu(ctx, w, dirs=dirs5000, num_levels=3)
+        if kind == "fibers":
+            ctx.set_max_pairs_per_pass(1)       # the voxel of a joint holds two segments' pairs
+            with pytest.raises(vx.VxError) as e:
+                run_gpu(ctx, w, lod=False)
+            assert e.value.status == 3
+    finally:
+        ctx.set_max_pairs_per_pass(2 ** 31 - 1)
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, R, 4, dirs5000, num_levels=3)
+    for lvl, (a, b, r) in enumerate(zip(one, split, refs)):
+        for k in ("keys", "mask", "mass", "moment", "lobes", "lobe_count", "compact"):
+            assert np.array_equal(np.asarray(a[k]).view(np.uint8), np.asarray(b[k]).view(np.uint8)), (lvl, k)
+        compare_level(b, r, f"level {lvl}", mu_max=prim_measure_max(w))
