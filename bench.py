@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -52,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--fibers-per-ply", type=int, default=64,
                     help="smaller yarns for profiling captures (64 = the benchmark workload)")
     return ap.parse_args()
@@ -129,7 +131,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the raw samples: VX_CLOCK_LOG if set, else a file in the temporary directory
+        self.path = os.environ.get("VX_CLOCK_LOG") or os.path.join(tempfile.gettempdir(),
+                                                                   f"vx_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
@@ -301,6 +305,11 @@ def main():
     if not args.no_batched:
         batched = batched_vs_plain(ctx, dev, args.steps)
 
+    # ---- adjoint vs forward on the differentiation workload ---------------------------------
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = adjoint_vs_forward(ctx, dev, args.steps)
+
     # ---- roofline of the dominant kernel -------------------------------------------------
     roof = roofline(prof, w, level_sizes, args.steps)
 
@@ -331,6 +340,7 @@ def main():
         "e2e": e2e,
         "clocks": clk,
         "batched": batched,
+        "adjoint": adjoint,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -338,6 +348,8 @@ def main():
 
 
 # ----------------------------------------------------------------------------------
+ADJ_WORKLOAD = ("yarn 3x64 fibers x 4000 segments (768k capsules) at 256^3, level 0 + 4 LoD levels (K=1); "
+                "loss = sum of U(-1,1) weights times every level's m and M")
 BATCH_WORKLOAD = ("64 instances: 32 heightfields of 2k-200k triangles and 32 yarn patches of 10k-400k "
                   "segments (log-uniform), grids 64^3-1024^3, all LoD levels, K=1")
 
@@ -394,6 +406,48 @@ def batched_vs_plain(ctx, dev, steps):
             "note": "batched = one captured graph per run; plain = per-instance vx_voxelize + vx_build_lod"}
 
 
+def adjoint_vs_forward(ctx, dev, steps):
+    """The differentiation workload: the yarn at 256^3 with 4 LoD levels (K = 1); forward
+    (vx_voxelize + vx_build_lod) against the adjoint (vx_backward: level adjoints broadcast
+    to level 0, candidate pairs recomputed, FP64 per-pair derivatives), CUDA events."""
+    import torch
+    w = synth.config5()
+    ctrl = torch.from_numpy(w.ctrl).to(dev)
+    off = torch.from_numpy(w.fiber_offsets).to(dev)
+    L0 = ctx.voxelize(w.grid, ctrl=ctrl, fiber_offsets=off, num_prims=w.num_prims)
+    pyr = ctx.build_lod(L0, K=1, num_levels=w.levels)
+    gen = torch.Generator(device="cpu").manual_seed(5)
+    gm = [torch.rand(lv.num_voxels, generator=gen).mul_(2).sub_(1).to(dev) for lv in [L0] + pyr]
+    gM = [torch.rand(lv.num_voxels, 6, generator=gen).mul_(2).sub_(1).to(dev) for lv in [L0] + pyr]
+    keys0 = L0.keys.clone()
+
+    def fwd():
+        a = ctx.voxelize(w.grid, ctrl=ctrl, fiber_offsets=off, num_prims=w.num_prims)
+        return a, ctx.build_lod(a, K=1, num_levels=w.levels)
+
+    def bwd():
+        return ctx.backward(w.grid, ctrl=ctrl, fiber_offsets=off, keys0=keys0, grad_mass=gm, grad_moment=gM,
+                            num_prims=w.num_prims)
+
+    def timed(fn, n):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        e.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(e) / n
+
+    tf = timed(fwd, steps)
+    tb = timed(bwd, steps)
+    return {"workload": ADJ_WORKLOAD, "prims": int(w.num_prims), "forward_ms": tf, "backward_ms": tb,
+            "backward_over_forward": tb / tf}
+
+
 def _source_hash(name):
     h = hashlib.sha256()
     with open(os.path.join(ROOT, "paper_2604_13191_gb300", "csrc", name), "rb") as fh:
@@ -401,13 +455,13 @@ def _source_hash(name):
     return h.hexdigest()[:16]
 
 
-# FP32 operations the definition spends per unit of work (DESIGN.md section 6):
+# FP32 operations the definition spends per unit of work:
 #   reduce_fibers: per (pair, sub-cell) decision, the step-1/2 test on precomputed per-axis
 #     terms: 3 x (2 adds + 1 compare) = 9, plus the per-axis terms amortised (~1) -> 10
 #   sggx_cluster: per sampled direction: mat-vec 15, norm 5, thresholds 2, compares 6,
 #     reciprocal 1, scale 1, products 9, roundings 12 -> 51
 ALU_OPS = {"reduce_fibers": 512 * 10, "sggx_cluster": N_SAMPLES * 51}
-# algorithmic HBM bytes per unit
+# algorithmic HBM bytes per unit of work
 HBM_BYTES = {
     "sort_scatter": 16,          # per pair and pass: key + value read and written
     "sort_hist": 4,              # per pair and pass: key read

@@ -180,100 +180,94 @@ __device__ __forceinline__ AxisBound axis_bound(float a, float b, float lo, floa
     return r;
 }
 
-// Per-warp shared scratch of the capsule mask: the sub-cells still undecided after steps
-// 1-2 (a task list) and the step-3 results (a 512-bit map).
-struct CapsuleScratch {
-    uint16_t task[512];
-    uint32_t hit[16];
-};
-
-// Warp-collective: 16 sub-cell bits of each lane (sx = 0..7, sy = sy0 + (0|1), sz) for one
-// capsule; bits already set in `have` are skipped (OR is idempotent).  Bit b = sx + 8 (sy - sy0).
-// Steps 1-2 run per lane.  A group of sub-cells (the lane's 16, or one row of 8) is decided
-// at once when
+// Steps 1-2 of the capsule test for the 16 sub-cells of one lane (sx = 0..7,
+// sy = sy0 + (0|1), sz); bit b = sx + 8 (sy - sy0), so lane L holds bits 16L .. 16L+15 of
+// the voxel's 512-bit mask (bit id sx + 8 sy + 64 sz).  Bits already set in `have` are
+// skipped (OR is idempotent).  Returns `have` plus the bits step 1-2 decide set; `und`
+// receives the sub-cells left for step 3.
+// A group of sub-cells (the lane's 16, or one row of 8) is decided at once when
 //   the sum of its per-axis gap bounds > r^2   -> every sub-cell fails step 1 (bits 0), or
 //   the sum of an endpoint's far bounds <= r^2 -> every sub-cell passes step 2 (bits 1)
 // (each sub-cell's step-1 sum is >= the group's and <= its step-2 sum, so the group result
-// equals the per-sub-cell definition bit for bit).  The sub-cells left for step 3 are
-// compacted over the warp and evaluated 32 at a time, so that the exact minimum (the
-// expensive, rare case) runs with all lanes busy.
-__device__ __forceinline__ uint32_t capsule_bits16(const float* a, const float* b, float rr, int sy0,
-                                                   int sz, uint32_t have, CapsuleScratch& cs) {
+// equals the per-sub-cell definition bit for bit).
+__device__ __forceinline__ uint32_t capsule_steps12(const float* a, const float* b, float rr, int sy0, int sz,
+                                                    uint32_t have, uint32_t& und) {
+    uint32_t bits = have;
+    und = 0;
+    if (have == 0xffffu) return bits;
+    const float zlo = (float)sz * 0.125f, zhi = (float)(sz + 1) * 0.125f;
+    const AxisBound bz = axis_bound(a[2], b[2], zlo, zhi);
+    const AxisBound bx = axis_bound(a[0], b[0], 0.0f, 1.0f);
+    const AxisBound bb = axis_bound(a[1], b[1], (float)sy0 * 0.125f, (float)(sy0 + 2) * 0.125f);
+    if ((bx.g2 + bb.g2) + bz.g2 > rr) return bits;                       // all 16 fail step 1
+    if ((bx.fa2 + bb.fa2) + bz.fa2 <= rr || (bx.fb2 + bb.fb2) + bz.fb2 <= rr) return 0xffffu;
+    const AxisTerms tz = axis_terms(a[2], b[2], sz);
+#pragma unroll
+    for (int yi = 0; yi < 2; ++yi) {
+        const uint32_t rowmask = 0xffu << (8 * yi);
+        if ((bits & rowmask) == rowmask) continue;
+        const float ylo = (float)(sy0 + yi) * 0.125f, yhi = (float)(sy0 + yi + 1) * 0.125f;
+        const AxisBound by = axis_bound(a[1], b[1], ylo, yhi);
+        if ((bx.g2 + by.g2) + bz.g2 > rr) continue;
+        if ((bx.fa2 + by.fa2) + bz.fa2 <= rr || (bx.fb2 + by.fb2) + bz.fb2 <= rr) {
+            bits |= rowmask;
+            continue;
+        }
+        const AxisTerms ty = axis_terms(a[1], b[1], sy0 + yi);
+#pragma unroll
+        for (int sx = 0; sx < 8; ++sx) {
+            const uint32_t bit = 1u << (sx + 8 * yi);
+            const AxisTerms tx = axis_terms(a[0], b[0], sx);
+            const float G = (tx.g2 + ty.g2) + tz.g2;
+            const float EA = (tx.ea2 + ty.ea2) + tz.ea2;
+            const float EB = (tx.eb2 + ty.eb2) + tz.eb2;
+            const bool todo = !(bits & bit) && !(G > rr);
+            if (todo && ((EA <= rr) || (EB <= rr))) bits |= bit;
+            else if (todo) und |= bit;
+        }
+    }
+    return bits;
+}
+
+// Per-warp pool of step-3 work of one voxel: (capsule slot, sub-cell) tasks left undecided
+// by steps 1-2 of the voxel's capsules, the local endpoints and r^2 of those capsules, and
+// the voxel's mask while the pool is evaluated.  Tasks of many capsules are evaluated 32 at
+// a time, so that the exact minimum (the expensive case) runs with all lanes busy.
+constexpr int CT_TASKS = 512;
+constexpr int CT_CAPS = 32;
+struct CapsuleTasks {
+    uint32_t task[CT_TASKS];       // slot << 9 | sub-cell id
+    float cap[CT_CAPS][8];         // a.xyz, b.xyz, r^2
+    uint32_t mask[16];             // 512-bit mask, word w = lanes 2w (low half) and 2w+1
+};
+
+// Step 3 of every pooled task whose sub-cell is not set yet (warp-collective); returns the
+// lane's 16 bits of the updated mask.  A task skipped because an earlier task of the same
+// sub-cell set it would have returned a bit that is already 1, so the order of evaluation
+// does not change the mask.
+__device__ __forceinline__ uint32_t capsule_step3_pool(CapsuleTasks& ct, int ntask, uint32_t chunk) {
     const int lane = threadIdx.x & 31;
-    uint32_t bits = have, und = 0;
-    if (have != 0xffffu) {
-        const float zlo = (float)sz * 0.125f, zhi = (float)(sz + 1) * 0.125f;
-        const AxisBound bz = axis_bound(a[2], b[2], zlo, zhi);
-        const AxisBound bx = axis_bound(a[0], b[0], 0.0f, 1.0f);
-        const AxisBound bb = axis_bound(a[1], b[1], (float)sy0 * 0.125f, (float)(sy0 + 2) * 0.125f);
-        if ((bx.g2 + bb.g2) + bz.g2 > rr) {
-            // all 16 fail step 1
-        } else if ((bx.fa2 + bb.fa2) + bz.fa2 <= rr || (bx.fb2 + bb.fb2) + bz.fb2 <= rr) {
-            bits = 0xffffu;
-        } else {
-            const AxisTerms tz = axis_terms(a[2], b[2], sz);
-#pragma unroll
-            for (int yi = 0; yi < 2; ++yi) {
-                const uint32_t rowmask = 0xffu << (8 * yi);
-                if ((bits & rowmask) == rowmask) continue;
-                const float ylo = (float)(sy0 + yi) * 0.125f, yhi = (float)(sy0 + yi + 1) * 0.125f;
-                const AxisBound by = axis_bound(a[1], b[1], ylo, yhi);
-                if ((bx.g2 + by.g2) + bz.g2 > rr) continue;
-                if ((bx.fa2 + by.fa2) + bz.fa2 <= rr || (bx.fb2 + by.fb2) + bz.fb2 <= rr) {
-                    bits |= rowmask;
-                    continue;
-                }
-                const AxisTerms ty = axis_terms(a[1], b[1], sy0 + yi);
-#pragma unroll
-                for (int sx = 0; sx < 8; ++sx) {
-                    const uint32_t bit = 1u << (sx + 8 * yi);
-                    const AxisTerms tx = axis_terms(a[0], b[0], sx);
-                    const float G = (tx.g2 + ty.g2) + tz.g2;
-                    const float EA = (tx.ea2 + ty.ea2) + tz.ea2;
-                    const float EB = (tx.eb2 + ty.eb2) + tz.eb2;
-                    const bool todo = !(bits & bit) && !(G > rr);
-                    if (todo && ((EA <= rr) || (EB <= rr))) bits |= bit;
-                    else if (todo) und |= bit;
-                }
-            }
-        }
-    }
-    // step 3 on the compacted undecided sub-cells of the whole warp
-    const uint32_t n = __popc(und);
-    uint32_t off = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, off, o);
-        if (lane >= o) off += t;
-    }
-    const uint32_t total = __shfl_sync(0xffffffffu, off, 31);
-    if (total == 0) return bits;
-    off -= n;
-    {
-        uint32_t u = und;
-        while (u) {
-            const int bpos = __ffs(u) - 1;
-            u &= u - 1;
-            const int sx = bpos & 7, sy = sy0 + (bpos >> 3);
-            cs.task[off++] = (uint16_t)(sx + 8 * sy + 64 * sz);
-        }
-    }
-    if (lane < 16) cs.hit[lane] = 0u;
+    const uint32_t lo16 = __shfl_sync(0xffffffffu, chunk, (2 * lane) & 31);
+    const uint32_t hi16 = __shfl_sync(0xffffffffu, chunk, (2 * lane + 1) & 31);
+    if (lane < 16) ct.mask[lane] = lo16 | (hi16 << 16);
     __syncwarp();
-    const float d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-    for (uint32_t t = lane; t < total; t += 32) {
-        const int id = cs.task[t];
+    for (int t = lane; t < ntask; t += 32) {
+        const uint32_t task = ct.task[t];
+        const int id = (int)(task & 511u);
+        const uint32_t bit = 1u << (id & 31);
+        if (ct.mask[id >> 5] & bit) continue;
+        const float* c = ct.cap[task >> 9];
+        const float a[3] = {c[0], c[1], c[2]};
+        const float d[3] = {c[3] - c[0], c[4] - c[1], c[5] - c[2]};
         const int sx = id & 7, sy = (id >> 3) & 7, zz = id >> 6;
         const float lo[3] = {(float)sx * 0.125f, (float)sy * 0.125f, (float)zz * 0.125f};
         const float hi[3] = {(float)(sx + 1) * 0.125f, (float)(sy + 1) * 0.125f, (float)(zz + 1) * 0.125f};
-        if (seg_box_min(a, d, lo, hi) <= rr) atomicOr(&cs.hit[id >> 5], 1u << (id & 31));
+        if (seg_box_min(a, d, lo, hi) <= c[6]) atomicOr(&ct.mask[id >> 5], bit);
     }
     __syncwarp();
-    // this lane's 16 bits sit at bit 8*sy0 of the 64-bit word sz: u32 word 2 sz + sy0/4
-    const uint32_t w = cs.hit[2 * sz + (sy0 >> 2)];
-    bits |= (w >> ((8 * sy0) & 31)) & 0xffffu;
+    const uint32_t w = ct.mask[lane >> 1];
     __syncwarp();
-    return bits;
+    return (w >> (16 * (lane & 1))) & 0xffffu;
 }
 
 // pi r^2 * length of the axis a-b clipped to the closed voxel [0,1]^3 (Liang-Barsky)
@@ -700,7 +694,7 @@ __device__ __forceinline__ void write_seg(SegOut out, uint32_t seg, uint32_t key
     }
 }
 
-__global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_fibers(const uint32_t* __restrict__ keys,
+__global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint32_t* __restrict__ keys,
                                                                   const uint32_t* __restrict__ prims,
                                                                   const uint32_t* __restrict__ starts,
                                                                   const uint32_t* __restrict__ nseg_p,
@@ -711,8 +705,8 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_fibers(const uint32_t
     const uint32_t nseg = *nseg_p;
     const int sz = lane >> 2, sy0 = (lane & 3) * 2;
     const uint32_t warps = gridDim.x * RED_WARPS;
-    __shared__ CapsuleScratch scratch[RED_WARPS];
-    CapsuleScratch& cs = scratch[threadIdx.x >> 5];
+    __shared__ CapsuleTasks pool[RED_WARPS];
+    CapsuleTasks& ct = pool[threadIdx.x >> 5];
     for (uint32_t seg = blockIdx.x * RED_WARPS + (threadIdx.x >> 5); seg < nseg; seg += warps) {
         const uint32_t beg = starts[seg], end = starts[seg + 1];
         const uint32_t key = keys[beg];
@@ -720,6 +714,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_fibers(const uint32_t
                     fz = (float)((int)vx_compact1by2(key >> 2) + bz);
         uint32_t chunk = 0;
         bool full = false;
+        int ntask = 0, ncap = 0;
         float acc[7] = {0, 0, 0, 0, 0, 0, 0};
         for (uint32_t base = beg; base < end; base += 32) {
             const uint32_t cnt = min(32u, end - base);
@@ -751,11 +746,48 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_fibers(const uint32_t
                     const float4 A = ra[p], B = rb[p];
                     float a[3] = {A.x - fx, A.y - fy, A.z - fz};
                     float b[3] = {B.x - fx, B.y - fy, B.z - fz};
-                    chunk = capsule_bits16(a, b, A.w * A.w, sy0, sz, chunk, cs);
+                    const float rr = A.w * A.w;
+                    uint32_t und;
+                    chunk = capsule_steps12(a, b, rr, sy0, sz, chunk, und);
+                    // pool the undecided sub-cells as step-3 tasks of this capsule
+                    const uint32_t n = __popc(und);
+                    uint32_t off = n;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t t = __shfl_up_sync(0xffffffffu, off, o);
+                        if (lane >= o) off += t;
+                    }
+                    const int total = (int)__shfl_sync(0xffffffffu, off, 31);
+                    if (total > 0) {
+                        if (ntask + total > CT_TASKS || ncap == CT_CAPS) {
+                            chunk = capsule_step3_pool(ct, ntask, chunk);
+                            ntask = 0;
+                            ncap = 0;
+                        }
+                        float cv = rr;
+                        cv = lane == 0 ? a[0] : cv;
+                        cv = lane == 1 ? a[1] : cv;
+                        cv = lane == 2 ? a[2] : cv;
+                        cv = lane == 3 ? b[0] : cv;
+                        cv = lane == 4 ? b[1] : cv;
+                        cv = lane == 5 ? b[2] : cv;
+                        if (lane < 7) ct.cap[ncap][lane] = cv;
+                        uint32_t pos = (uint32_t)ntask + off - n;
+                        uint32_t u = und;
+                        while (u) {
+                            const int bpos = __ffs(u) - 1;
+                            u &= u - 1;
+                            ct.task[pos++] = ((uint32_t)ncap << 9) | (uint32_t)(16 * lane + bpos);
+                        }
+                        ntask += total;
+                        ++ncap;
+                        __syncwarp();
+                    }
                     full = __all_sync(0xffffffffu, chunk == 0xffffu);
                 }
             }
         }
+        if (ntask > 0) chunk = capsule_step3_pool(ct, ntask, chunk);
         write_seg(out, seg, key, chunk, acc);
     }
 }
@@ -779,6 +811,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_tris(const uint32_t* 
                        iz = vx_compact1by2(key >> 2) + bz;
         uint32_t chunk = 0;
         bool full = false;
+        int ntask = 0, ncap = 0;
         float acc[7] = {0, 0, 0, 0, 0, 0, 0};
         for (uint32_t base = beg; base < end; base += 32) {
             const uint32_t cnt = min(32u, end - base);

@@ -272,8 +272,15 @@ __device__ __forceinline__ int rint_small(float x) {
 // (G = 1: one warp; G > 1: the whole block, `red` is G * 13 words of shared memory).
 // Every count and sum is an integer, so the result is independent of G and of the order
 // in which the threads visit the samples.  Result valid in every participating thread.
+// The part of a lobe's statistics one thread keeps: component `tid` of the histogram and
+// of M^ (threads tid < 6 of the group hold the six components).
+struct LobeOwn {
+    int32_t h;
+    float mh;
+};
+
 template <int G>
-__device__ LobeStats sample_lobe(const float* S, const float4* __restrict__ dirs, int N, long long* red) {
+__device__ LobeOwn sample_lobe(const float* S, const float4* __restrict__ dirs, int N, long long* red) {
     const float tr = (S[0] + S[1]) + S[2];
     const float eps = 1e-6f * tr;
     const float Sp[6] = {S[0] + eps, S[1] + eps, S[2] + eps, S[3], S[4], S[5]};
@@ -356,13 +363,20 @@ __device__ LobeStats sample_lobe(const float* S, const float4* __restrict__ dirs
             Q[c] = tq[c];
         }
     }
-    LobeStats st;
+    // component `tid` (tid < 6) of the histogram and of M^ (one FP64 division per thread)
+    LobeOwn own;
+    own.h = h[0];
+    long long q = Q[0];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        st.h[c] = h[c];
-        st.Mh[c] = cnt > 0 ? (float)((double)Q[c] / ((double)cnt * 1048576.0)) : 0.0f;
+    for (int c = 1; c < 6; ++c) {
+        if (tid == c) {
+            own.h = h[c];
+            q = Q[c];
+        }
     }
-    return st;
+    own.mh = 0.0f;
+    if (tid < 6 && cnt > 0) own.mh = (float)((double)q / ((double)cnt * 1048576.0));
+    return own;
 }
 
 // Per-group shared state of SGGX-H, sized for `slots` lobes (candidates + merges, 2 * 8K):
@@ -397,6 +411,7 @@ __global__ void k_pack_dirs(const float* __restrict__ d, int n, float4* __restri
 // with many parents; G = CL_BLOCK_WARPS: a block per parent, for the few coarse parents
 // whose long merge chains would otherwise run on a single warp).
 constexpr int CL_BLOCK_WARPS = 8;
+constexpr int CL_WIDE_WARPS = 16;   // levels with at most one parent per SM
 
 template <int G>
 __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluster(
@@ -453,10 +468,10 @@ __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluste
         int sampled = 0;
         for (int l = 0; l < n; ++l) {
             if (sm.alive[l] != 2) continue;
-            LobeStats st = sample_lobe<G>(sm.S + l * 6, dirs, N, red);
+            const LobeOwn st = sample_lobe<G>(sm.S + l * 6, dirs, N, red);
             if (tid < 6) {
-                sm.H[l * 6 + tid] = st.h[tid];
-                sm.Mh[l * 6 + tid] = st.Mh[tid];
+                sm.H[l * 6 + tid] = st.h;
+                sm.Mh[l * 6 + tid] = st.mh;
             }
             ++sampled;
         }
@@ -502,10 +517,10 @@ __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluste
                 sm.alive[next] = 1;
             }
             gsync();
-            LobeStats st = sample_lobe<G>(sm.S + next * 6, dirs, N, red);
+            const LobeOwn st = sample_lobe<G>(sm.S + next * 6, dirs, N, red);
             if (tid < 6) {
-                sm.H[next * 6 + tid] = st.h[tid];
-                sm.Mh[next * 6 + tid] = st.Mh[tid];
+                sm.H[next * 6 + tid] = st.h;
+                sm.Mh[next * 6 + tid] = st.mh;
             }
             gsync();
             ++next;
@@ -641,6 +656,7 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
     }
     const size_t cl_smem = cluster_bytes(16 * K) * CL_WARPS;
     const size_t cb_smem = cluster_bytes(16 * K) + sizeof(long long) * 13 * CL_BLOCK_WARPS;
+    const size_t cw_smem = cluster_bytes(16 * K) + sizeof(long long) * 13 * CL_WIDE_WARPS;
     float4* dirs4 = nullptr;
     if (K > 1) {
         VX_TRY(vx_ws_ensure(ctx, WS_LOD_TMP, (size_t)params->n_samples * 16, s));
@@ -650,6 +666,8 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
         VX_CUDA_TRY(cudaFuncSetAttribute(k_sggx_cluster<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl_smem));
         VX_CUDA_TRY(cudaFuncSetAttribute(k_sggx_cluster<CL_BLOCK_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cb_smem));
+        VX_CUDA_TRY(cudaFuncSetAttribute(k_sggx_cluster<CL_WIDE_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cw_smem));
     }
     for (int l = 1; l <= L; ++l) {
         const vx_level* prev = (l == 1) ? in : &out[l - 2];
@@ -676,9 +694,14 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
                 VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, k_sggx_cluster<1><<<cb, CL_WARPS * 32, cl_smem, s>>>(
                                                    li, starts, work, misc + 40, out[l - 1], K, dirs4,
                                                    params->n_samples, cst, pst, cnt_dev));
-            } else {
+            } else if (ncur > (uint32_t)vx::kSMs) {
                 const unsigned cb = (unsigned)std::max<uint32_t>(1u, std::min<uint32_t>(ncur, vx::kSMs * 4));
                 VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, k_sggx_cluster<CL_BLOCK_WARPS><<<cb, CL_BLOCK_WARPS * 32, cb_smem, s>>>(
+                                                   li, starts, work, misc + 40, out[l - 1], K, dirs4,
+                                                   params->n_samples, cst, pst, cnt_dev));
+            } else {
+                const unsigned cb = (unsigned)std::max<uint32_t>(1u, ncur);
+                VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, k_sggx_cluster<CL_WIDE_WARPS><<<cb, CL_WIDE_WARPS * 32, cw_smem, s>>>(
                                                    li, starts, work, misc + 40, out[l - 1], K, dirs4,
                                                    params->n_samples, cst, pst, cnt_dev));
             }
