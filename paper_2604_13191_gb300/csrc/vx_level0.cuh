@@ -149,12 +149,19 @@ __device__ __forceinline__ bool capsule_box(const float* a, const float* b, floa
 struct AxisTerms {
     float g2, ea2, eb2;
 };
+// The gap (lo > mx ? lo - mx : mn > hi ? mn - hi : 0) is written max(lo - mx, mn - hi, 0):
+// at most one of the two differences is positive, and a difference is positive exactly when
+// its comparison holds (FP subtraction of finite values), so the two forms round to the same
+// value up to the sign of a zero, which the square removes.  Likewise the endpoint distances.
+__device__ __forceinline__ float gap3(float lo, float hi, float mn, float mx) {
+    return fmaxf(fmaxf(lo - mx, mn - hi), 0.0f);
+}
 __device__ __forceinline__ AxisTerms axis_terms(float a, float b, int k) {
     const float lo = (float)k * 0.125f, hi = (float)(k + 1) * 0.125f;
-    const float mn = fmin2(a, b), mx = fmax2(a, b);
-    float g = (lo > mx) ? lo - mx : ((mn > hi) ? mn - hi : 0.0f);
-    float ea = (a < lo) ? lo - a : ((a > hi) ? a - hi : 0.0f);
-    float eb = (b < lo) ? lo - b : ((b > hi) ? b - hi : 0.0f);
+    const float mn = fminf(a, b), mx = fmaxf(a, b);
+    const float g = gap3(lo, hi, mn, mx);
+    const float ea = gap3(lo, hi, a, a);
+    const float eb = gap3(lo, hi, b, b);
     AxisTerms t;
     t.g2 = g * g;
     t.ea2 = ea * ea;
@@ -169,10 +176,10 @@ struct AxisBound {
     float g2, fa2, fb2;
 };
 __device__ __forceinline__ AxisBound axis_bound(float a, float b, float lo, float hi) {
-    const float mn = fmin2(a, b), mx = fmax2(a, b);
-    float g = (lo > mx) ? lo - mx : ((mn > hi) ? mn - hi : 0.0f);
-    float fa = fmax2(hi - a, a - lo);
-    float fb = fmax2(hi - b, b - lo);
+    const float mn = fminf(a, b), mx = fmaxf(a, b);
+    const float g = gap3(lo, hi, mn, mx);
+    const float fa = fmaxf(hi - a, a - lo);
+    const float fb = fmaxf(hi - b, b - lo);
     AxisBound r;
     r.g2 = g * g;
     r.fa2 = fa * fa;
@@ -214,18 +221,24 @@ __device__ __forceinline__ uint32_t capsule_steps12(const float* a, const float*
             continue;
         }
         const AxisTerms ty = axis_terms(a[1], b[1], sy0 + yi);
+        // per sub-cell: set when an endpoint passes step 2, open (step 3) when it passes
+        // step 1 only.  EA, EB >= G (an endpoint is no closer to a sub-cell than the
+        // segment's extent, and FP addition is monotone), so min(EA, EB) <= r^2 implies
+        // G <= r^2; bits set before are dropped from `und` at the end.
+        uint32_t row_set = 0, row_open = 0;
 #pragma unroll
         for (int sx = 0; sx < 8; ++sx) {
-            const uint32_t bit = 1u << (sx + 8 * yi);
             const AxisTerms tx = axis_terms(a[0], b[0], sx);
             const float G = (tx.g2 + ty.g2) + tz.g2;
             const float EA = (tx.ea2 + ty.ea2) + tz.ea2;
             const float EB = (tx.eb2 + ty.eb2) + tz.eb2;
-            const bool todo = !(bits & bit) && !(G > rr);
-            if (todo && ((EA <= rr) || (EB <= rr))) bits |= bit;
-            else if (todo) und |= bit;
+            row_set |= (fminf(EA, EB) <= rr ? 1u : 0u) << sx;
+            row_open |= (G <= rr ? 1u : 0u) << sx;
         }
+        bits |= row_set << (8 * yi);
+        und |= row_open << (8 * yi);
     }
+    und &= ~bits;
     return bits;
 }
 
