@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--woven", type=int, default=0,
+                    help="also time the woven patch at 2048^3 with this many warp and weft yarns (16 = the "
+                         "full patch)")
     ap.add_argument("--fibers-per-ply", type=int, default=64,
                     help="smaller yarns for profiling captures (64 = the benchmark workload)")
     return ap.parse_args()
@@ -252,6 +255,22 @@ def main():
     launches = sum(v[0] for v in prof.values())
     prof = {k: v for k, v in prof.items() if v[0]}
 
+    # ---- vx_voxelize alone on a warm stream: median of 10 calls -----------------------------
+    vox_ms = []
+    for _ in range(10):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        L0 = ctx.voxelize(w.grid, ctrl=ctrl, fiber_offsets=off, num_prims=n_prims)
+        b.record()
+        torch.cuda.synchronize()
+        vox_ms.append(a.elapsed_time(b))
+        del L0
+    voxelize = {"median_ms": statistics.median(vox_ms), "prims_per_s": n_prims / (statistics.median(vox_ms) * 1e-3),
+                "calls": len(vox_ms)}
+
     # ---- e2e: same calls from pinned host buffers, outputs downloaded ------------------
     e2e = None
     if not args.no_e2e:
@@ -305,6 +324,11 @@ def main():
     if not args.no_batched:
         batched = batched_vs_plain(ctx, dev, args.steps)
 
+    # ---- the woven patch at 2048^3 (optional) ---------------------------------------------
+    woven = None
+    if args.woven > 0:
+        woven = woven_patch(ctx, dev, args.woven, dirs)
+
     # ---- adjoint vs forward on the differentiation workload ---------------------------------
     adjoint = None
     if not args.no_adjoint:
@@ -333,6 +357,7 @@ def main():
                    "voxels_per_level": level_sizes, "parallelism": f"replicas x{ws}",
                    "l2": "flushed between timed steps (256 MiB write)"},
         "lod_ms": sum(v["ms_per_step"] for k, v in stages.items() if k.startswith(("lod", "sggx"))),
+        "voxelize": voxelize,
         "stages": stages,
         "gpu_launches": int(launches),
         "roofline": roof,
@@ -342,6 +367,8 @@ def main():
         "batched": batched,
         "adjoint": adjoint,
     }
+    if woven is not None:
+        line["woven"] = woven
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -404,6 +431,42 @@ def batched_vs_plain(ctx, dev, steps):
     return {"workload": BATCH_WORKLOAD, "prims": int(nprims), "batched_ms": tb, "plain_ms": tp,
             "speedup": tp / tb, "batched_prims_per_s": nprims / (tb * 1e-3),
             "note": "batched = one captured graph per run; plain = per-instance vx_voxelize + vx_build_lod"}
+
+
+def woven_patch(ctx, dev, n_yarns, dirs):
+    """The woven patch (n_yarns warp x n_yarns weft yarns of 3 x 80 fibers, r = 0.002) at
+    2048^3, K = 4: vx_voxelize + vx_build_lod, one warm-up and two timed steps."""
+    import torch
+    w = synth.config3(n_yarns=n_yarns)
+    ctrl = torch.from_numpy(w.ctrl).to(dev)
+    off = torch.from_numpy(w.fiber_offsets).to(dev)
+    ctx.profile(True)
+    ms, vox, lod = [], [], []
+    for i in range(3):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        m = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        L0 = ctx.voxelize(w.grid, ctrl=ctrl, fiber_offsets=off, num_prims=w.num_prims)
+        m.record()
+        pyr = ctx.build_lod(L0, K=K_LOBES, dirs=dirs)
+        b.record()
+        torch.cuda.synchronize()
+        if i > 0:
+            ms.append(a.elapsed_time(b))
+            vox.append(a.elapsed_time(m))
+            lod.append(m.elapsed_time(b))
+        sizes = [L0.num_voxels] + [p.num_voxels for p in pyr]
+        del L0, pyr
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    pairs = prof.get("reduce_fibers", (0, 0.0, 0))[2] // 3
+    return {"workload": f"woven patch {n_yarns}x{n_yarns} yarns x 3 plies x 80 fibers x 2000 segments "
+                        f"({w.num_prims} capsules, r = 0.002), 2048^3, K=4, N=5000",
+            "prims": int(w.num_prims), "ms_per_step": statistics.mean(ms), "voxelize_ms": statistics.mean(vox),
+            "lod_ms": statistics.mean(lod), "prims_per_s": w.num_prims / (statistics.mean(ms) * 1e-3),
+            "candidate_pairs": int(pairs), "voxels_per_level": sizes}
 
 
 def adjoint_vs_forward(ctx, dev, steps):

@@ -124,3 +124,82 @@ def test_pyramid_properties(yarn_run):
         assert np.all(b["occ"] <= 8 * b["proj"].min(1).astype(int))
         assert np.all(b["proj"].max(1) <= b["occ"])
     assert levels[-1]["keys"].shape[0] == 1
+
+
+# ----------------------------------------------------------------------------
+# the woven patch at 2048^3 (config 3 with 4 warp x 4 weft yarns, 3.84M capsules): several
+# 1024^3 windows, ~2.5e9 candidate pairs.  Level 0 stays on the device; sampled voxels and
+# parents are gathered there and checked one by one.
+# ----------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def woven_run(dirs5000):
+    w = synth.config3(n_yarns=4)
+    ctx = vx.Context(DEV)
+    L0 = ctx.voxelize(w.grid, ctrl=torch.from_numpy(w.ctrl).to(DEV),
+                      fiber_offsets=torch.from_numpy(w.fiber_offsets).to(DEV), num_prims=w.num_prims)
+    pyr = ctx.build_lod(L0, K=4, dirs=torch.from_numpy(dirs5000).to(DEV), num_levels=3)
+    torch.cuda.synchronize()
+    yield w, L0, pyr
+    del L0, pyr
+    ctx.close()
+
+
+def _rows(L, idx):
+    """Host copies of the sampled rows of a device level."""
+    t = torch.from_numpy(idx).to(DEV)
+    return {"keys": L.keys[t].cpu().numpy().view(np.uint64), "mask": L.mask[t].cpu().numpy().view(np.uint64),
+            "mass": L.mass[t].cpu().numpy(), "moment": L.moment[t].cpu().numpy(),
+            "occ": L.occ[t].cpu().numpy().view(np.uint16), "proj": L.occ_proj[t].cpu().numpy(),
+            "lobe_count": L.lobe_count[t].cpu().numpy(), "lobes": L.lobes[t].cpu().numpy()}
+
+
+def test_woven_2048_sampled_level0(woven_run):
+    w, L0, _ = woven_run
+    n = L0.num_voxels
+    assert n > 10_000_000
+    keys = L0.keys
+    # sorted, unique, and spread over more than one 1024^3 window
+    assert bool((keys[1:] > keys[:-1]).all())
+    assert torch.unique(keys >> 30).numel() > 1
+    rng = np.random.default_rng(40)
+    idx = np.sort(rng.choice(n, 48, replace=False))
+    got = _rows(L0, idx)
+    ref = oracle.fiber_voxels(w.ctrl, w.fiber_offsets, w.grid, got["keys"])
+    assert np.array_equal(ref["mask"], got["mask"])
+    assert np.array_equal(ref["mass"].view(np.uint32), got["mass"].view(np.uint32))
+    assert np.array_equal(ref["moment"].view(np.uint32), got["moment"].view(np.uint32))
+    floor = 1e-6 * float(L0.mass.max())
+    assert np.all(np.abs(got["mass"] - ref["mass64"]) <= 1e-5 * ref["mass64"] + floor)
+
+
+def test_woven_2048_sampled_parent(woven_run, dirs5000):
+    w, _, pyr = woven_run
+    P = pyr[0]
+    clustered = torch.nonzero(P.lobe_count == 4).flatten().cpu().numpy()
+    assert clustered.size > 1000
+    rng = np.random.default_rng(41)
+    pick = np.sort(rng.choice(clustered, 3, replace=False))
+    got = _rows(P, pick)
+    for i in range(pick.size):
+        pk = np.uint64(got["keys"][i])
+        child_keys = (pk << np.uint64(3)) | np.arange(8, dtype=np.uint64)
+        vox = oracle.fiber_voxels(w.ctrl, w.fiber_offsets, w.grid, child_keys)
+        cur = oracle.lod_step(oracle.level_from_voxels(child_keys, vox), 4, dirs5000)
+        assert cur["keys"].shape[0] == 1 and cur["keys"][0] == pk
+        assert np.array_equal(cur["mask"][0], got["mask"][i])
+        assert cur["mass"][0].view(np.uint32) == got["mass"][i].view(np.uint32)
+        assert np.array_equal(cur["moment"][0].view(np.uint32), got["moment"][i].view(np.uint32))
+        c = int(cur["lobe_count"][0])
+        assert c == int(got["lobe_count"][i])
+        assert np.max(np.abs(cur["lobes"][0, :c] - got["lobes"][i, :c])) <= 1e-5
+
+
+def test_woven_2048_pyramid_properties(woven_run):
+    _, L0, pyr = woven_run
+    tot = float(L0.mass.double().sum())
+    prev = L0
+    for P in pyr:
+        assert torch.equal(torch.unique(prev.keys >> 3), P.keys)
+        assert float(P.mass.double().sum()) == pytest.approx(tot, rel=1e-5)
+        assert bool((P.lobe_count <= 4).all())
+        prev = P
