@@ -408,7 +408,8 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
     // ---- per-voxel reduction ------------------------------------------------------------------
     const unsigned rblocks = (unsigned)std::min<size_t>((S.cap_seg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 32);
     if (S.fiber)
-        k_reduce_fibers<<<rblocks, RED_WARPS * 32, 0, s>>>(k0, v0, S.starts, C + C_SEG, S.r0, S.r1, S.seg, 0, 0, 0);
+        k_reduce_fibers<<<rblocks, RED_WARPS * 32, 0, s>>>(k0, v0, S.starts, C + C_SEG, S.r0, S.r1, S.seg, 0, 0, 0,
+                                                          nullptr);
     else
         k_reduce_tris<<<rblocks, RED_WARPS * 32, 0, s>>>(k0, v0, S.starts, C + C_SEG, S.r0, S.r1, S.r2, S.seg, 0, 0,
                                                          0);

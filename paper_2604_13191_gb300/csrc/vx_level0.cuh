@@ -713,14 +713,23 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                                                                   const uint32_t* __restrict__ nseg_p,
                                                                   const float4* __restrict__ ra,
                                                                   const float4* __restrict__ rb, SegOut out,
-                                                                  int bx, int by, int bz) {
+                                                                  int bx, int by, int bz,
+                                                                  uint32_t* __restrict__ next) {
     const int lane = threadIdx.x & 31;
     const uint32_t nseg = *nseg_p;
     const int sz = lane >> 2, sy0 = (lane & 3) * 2;
     const uint32_t warps = gridDim.x * RED_WARPS;
     __shared__ CapsuleTasks pool[RED_WARPS];
     CapsuleTasks& ct = pool[threadIdx.x >> 5];
-    for (uint32_t seg = blockIdx.x * RED_WARPS + (threadIdx.x >> 5); seg < nseg; seg += warps) {
+    // voxels are taken from the counter `next` one per warp when it is given (a grid of
+    // resident blocks), else in a fixed grid stride
+    auto take = [&]() -> uint32_t {
+        uint32_t v = 0;
+        if (lane == 0) v = atomicAdd(next, 1u);
+        return __shfl_sync(0xffffffffu, v, 0);
+    };
+    for (uint32_t seg = next ? take() : blockIdx.x * RED_WARPS + (threadIdx.x >> 5); seg < nseg;
+         seg = next ? take() : seg + warps) {
         const uint32_t beg = starts[seg], end = starts[seg + 1];
         const uint32_t key = keys[beg];
         const float fx = (float)((int)vx_compact1by2(key) + bx), fy = (float)((int)vx_compact1by2(key >> 1) + by),

@@ -429,11 +429,25 @@ __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluste
     constexpr int NT = 32 * G;
     const int lane = threadIdx.x & 31;
     const uint32_t nwork = *nwork_p;
-    const uint32_t groups = gridDim.x * GROUPS;
     auto gsync = [&]() {
         if (G == 1) __syncwarp(); else __syncthreads();
     };
-    for (uint32_t it = blockIdx.x * GROUPS + group; it < nwork; it += groups) {
+    // parents are taken one at a time from a shared counter (nwork_p[1]), so that groups
+    // that drew short merge chains take more parents
+    __shared__ uint32_t take[GROUPS];
+    for (;;) {
+        uint32_t it;
+        if (G == 1) {
+            uint32_t v = 0;
+            if (lane == 0) v = atomicAdd(const_cast<uint32_t*>(nwork_p) + 1, 1u);
+            it = __shfl_sync(0xffffffffu, v, 0);
+        } else {
+            if (threadIdx.x == 0) take[0] = atomicAdd(const_cast<uint32_t*>(nwork_p) + 1, 1u);
+            __syncthreads();
+            it = take[0];
+            __syncthreads();
+        }
+        if (it >= nwork) break;
         const uint32_t p = work[it];
         const uint32_t beg = starts[p], end = starts[p + 1];
         // gather candidates in (child, lobe) order, with their statistics where the child
@@ -679,7 +693,7 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
         VX_LAUNCH(ctx, ST_LOD_HEADS, s, k_parent_flags<<<grid_for(nprev, 256), 256, 0, s>>>(prev->keys, nprev, flags));
         VX_TRY(vx_scan_u32(ctx, flags, flags, nprev, nullptr, s));
         VX_LAUNCH(ctx, ST_LOD_HEADS, s, k_parent_starts<<<grid_for(nprev, 256), 256, 0, s>>>(prev->keys, nprev, flags, ncur, starts));
-        VX_CUDA_TRY(cudaMemsetAsync(misc + 40, 0, 4, s));
+        VX_CUDA_TRY(cudaMemsetAsync(misc + 40, 0, 8, s));   // [40] clustered parents, [41] taken
         vx_stage_units(ctx, ST_LOD_REDUCE, ncur);
         // statistics kept by the child level (none for the input level) and by this one
         const LobeStats* cst = (K > 1 && l > 1) ? stats[l & 1] : nullptr;
@@ -690,7 +704,7 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
         if (K > 1) {
             unsigned long long* cnt_dev = ctx->prof ? ctx->dev_lobe_count : nullptr;
             if (ncur > (uint32_t)(vx::kSMs * 16)) {
-                const unsigned cb = (unsigned)std::min<size_t>((ncur + CL_WARPS - 1) / CL_WARPS, (size_t)vx::kSMs * 16);
+                const unsigned cb = (unsigned)std::min<size_t>((ncur + CL_WARPS - 1) / CL_WARPS, (size_t)vx::kSMs * 7);
                 VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, k_sggx_cluster<1><<<cb, CL_WARPS * 32, cl_smem, s>>>(
                                                    li, starts, work, misc + 40, out[l - 1], K, dirs4,
                                                    params->n_samples, cst, pst, cnt_dev));

@@ -126,10 +126,13 @@ vx_status voxelize_window(vx_context* ctx, bool fiber, uint32_t np, const Window
     seg.key = k1;
     seg.nonzero = v1;
     const unsigned rblocks = (unsigned)std::min<size_t>((nseg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 32);
-    if (fiber)
-        VX_LAUNCH(ctx, ST_REDUCE_FIBERS, s, k_reduce_fibers<<<rblocks, RED_WARPS * 32, 0, s>>>(
-                                                k0, v0, starts, misc + 2, r0, r1, seg, bx, by, bz));
-    else
+    if (fiber) {
+        // resident blocks (7 per SM) taking voxels from a counter
+        VX_CUDA_TRY(cudaMemsetAsync(misc + 6, 0, 4, s));
+        const unsigned fblocks = (unsigned)std::min<size_t>((nseg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 7);
+        VX_LAUNCH(ctx, ST_REDUCE_FIBERS, s, k_reduce_fibers<<<fblocks, RED_WARPS * 32, 0, s>>>(
+                                                k0, v0, starts, misc + 2, r0, r1, seg, bx, by, bz, misc + 6));
+    } else
         VX_LAUNCH(ctx, ST_REDUCE_TRIS, s, k_reduce_tris<<<rblocks, RED_WARPS * 32, 0, s>>>(
                                               k0, v0, starts, misc + 2, r0, r1, r2, seg, bx, by, bz));
     VX_CUDA_TRY(cudaGetLastError());
