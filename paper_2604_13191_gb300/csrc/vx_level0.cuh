@@ -821,12 +821,20 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_tris(const uint32_t* 
                                                                 const float4* __restrict__ r0,
                                                                 const float4* __restrict__ r1,
                                                                 const float4* __restrict__ r2, SegOut out,
-                                                                int bx, int by, int bz) {
+                                                                int bx, int by, int bz,
+                                                                uint32_t* __restrict__ next) {
     const int lane = threadIdx.x & 31;
     const uint32_t nseg = *nseg_p;
     const int sz = lane >> 2, sy0 = (lane & 3) * 2;
     const uint32_t warps = gridDim.x * RED_WARPS;
-    for (uint32_t seg = blockIdx.x * RED_WARPS + (threadIdx.x >> 5); seg < nseg; seg += warps) {
+    // voxels from the counter `next` when given (resident blocks), else a fixed grid stride
+    auto take = [&]() -> uint32_t {
+        uint32_t v = 0;
+        if (lane == 0) v = atomicAdd(next, 1u);
+        return __shfl_sync(0xffffffffu, v, 0);
+    };
+    for (uint32_t seg = next ? take() : blockIdx.x * RED_WARPS + (threadIdx.x >> 5); seg < nseg;
+         seg = next ? take() : seg + warps) {
         const uint32_t beg = starts[seg], end = starts[seg + 1];
         const uint32_t key = keys[beg];
         const uint32_t ix = vx_compact1by2(key) + bx, iy = vx_compact1by2(key >> 1) + by,

@@ -121,14 +121,15 @@ __device__ __forceinline__ uint32_t radix_digit(uint32_t k, uint32_t v, int shif
     return (k >> shift) & dmask;
 }
 
-template <bool LUT>
+// RB buckets per pass (256: 8-bit digits; 512: 9-bit digits, three passes for a 27-bit key)
+template <bool LUT, int RB>
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const uint32_t* __restrict__ keys,
                                                              const uint32_t* __restrict__ vals, uint32_t n,
                                                              int shift, uint32_t dmask, uint32_t nt,
                                                              const uint8_t* __restrict__ lut,
                                                              uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[RADIX];
-    h[threadIdx.x] = 0;
+    __shared__ uint32_t h[RB];
+    for (int d = threadIdx.x; d < RB; d += SORT_THREADS) h[d] = 0;
     __syncthreads();
     const size_t base = (size_t)blockIdx.x * SORT_TILE;
 #pragma unroll 4
@@ -137,10 +138,10 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const uint32_t* __r
         if (e < n) atomicAdd(&h[radix_digit<LUT>(LUT ? 0u : keys[e], LUT ? vals[e] : 0u, shift, dmask, lut)], 1u);
     }
     __syncthreads();
-    hist[(size_t)threadIdx.x * nt + blockIdx.x] = h[threadIdx.x];
+    for (int d = threadIdx.x; d < RB; d += SORT_THREADS) hist[(size_t)d * nt + blockIdx.x] = h[d];
 }
 
-template <bool LUT>
+template <bool LUT, int RB>
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint32_t* __restrict__ keys,
                                                                 const uint32_t* __restrict__ vals, uint32_t n,
                                                                 int shift, uint32_t dmask, uint32_t nt,
@@ -148,11 +149,11 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint32_t* 
                                                                 const uint32_t* __restrict__ hist,
                                                                 uint32_t* __restrict__ okeys,
                                                                 uint32_t* __restrict__ ovals) {
-    __shared__ uint32_t wcnt[SORT_WARPS][RADIX];
-    __shared__ uint32_t gofs[RADIX];
+    __shared__ uint32_t wcnt[SORT_WARPS][RB];
+    __shared__ uint32_t gofs[RB];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&wcnt[0][0])[i] = 0;
-    gofs[threadIdx.x] = hist[(size_t)threadIdx.x * nt + blockIdx.x];
+    for (int i = threadIdx.x; i < SORT_WARPS * RB; i += SORT_THREADS) (&wcnt[0][0])[i] = 0;
+    for (int d = threadIdx.x; d < RB; d += SORT_THREADS) gofs[d] = hist[(size_t)d * nt + blockIdx.x];
     __syncthreads();
     const size_t base = (size_t)blockIdx.x * SORT_TILE + (size_t)w * (32 * SORT_ITEMS);
     const uint32_t lt = (1u << lane) - 1u;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint32_t* 
         bool valid = e < n;
         k[j] = valid ? keys[e] : 0u;
         v[j] = valid ? vals[e] : 0u;
-        uint32_t d = valid ? radix_digit<LUT>(k[j], v[j], shift, dmask, lut) : (uint32_t)RADIX;
+        uint32_t d = valid ? radix_digit<LUT>(k[j], v[j], shift, dmask, lut) : (uint32_t)RB;
         uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t r = 0;
         if (valid) r = wcnt[w][d] + __popc(peers & lt);
@@ -173,8 +174,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint32_t* 
         rk[j] = r;
     }
     __syncthreads();
-    {
-        const int d = threadIdx.x;
+    for (int d = threadIdx.x; d < RB; d += SORT_THREADS) {
         uint32_t run = 0;
 #pragma unroll
         for (int ww = 0; ww < SORT_WARPS; ++ww) {
@@ -218,19 +218,32 @@ vx_status vx_scan_u32(vx_context* ctx, const uint32_t* in, uint32_t* out, uint32
 vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, uint32_t** keys_alt,
                             uint32_t** vals_alt, uint32_t n, int bits, cudaStream_t s) {
     if (n <= 1 || bits <= 0) return VX_OK;
+    // as few passes as 9-bit digits allow, digits as even as possible; 512 buckets when a
+    // digit is wider than 8 bits (27-bit keys: three passes of 9 instead of four of 8)
+    const int passes = (bits + 8) / 9;
+    const int width = (bits + passes - 1) / passes;
+    const uint32_t rb = width > 8 ? 512u : 256u;
     uint32_t nt = (n + SORT_TILE - 1) / SORT_TILE;
-    size_t hn = (size_t)RADIX * nt;
+    size_t hn = (size_t)rb * nt;
     if (hn > 0xffffffffull) return VX_ERR_CAPACITY;
     VX_TRY(vx_ws_ensure(ctx, WS_SORT_HIST, hn * 4, s));
     uint32_t* hist = (uint32_t*)ctx->ws[WS_SORT_HIST].p;
-    for (int shift = 0; shift < bits; shift += 8) {
-        int nb = bits - shift < 8 ? bits - shift : 8;
+    for (int shift = 0; shift < bits; shift += width) {
+        int nb = bits - shift < width ? bits - shift : width;
         uint32_t dmask = (1u << nb) - 1u;
-        VX_LAUNCH(ctx, ST_SORT_HIST, s, k_radix_hist<false><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, shift, dmask,
-                                                                                     nt, nullptr, hist));
+        if (rb == 512u)
+            VX_LAUNCH(ctx, ST_SORT_HIST, s, (k_radix_hist<false, 512><<<nt, SORT_THREADS, 0, s>>>(
+                                                *keys, *vals, n, shift, dmask, nt, nullptr, hist)));
+        else
+            VX_LAUNCH(ctx, ST_SORT_HIST, s, (k_radix_hist<false, 256><<<nt, SORT_THREADS, 0, s>>>(
+                                                *keys, *vals, n, shift, dmask, nt, nullptr, hist)));
         VX_TRY(vx_scan_u32(ctx, hist, hist, (uint32_t)hn, nullptr, s));
-        VX_LAUNCH(ctx, ST_SORT_SCATTER, s, k_radix_scatter<false><<<nt, SORT_THREADS, 0, s>>>(
-                                               *keys, *vals, n, shift, dmask, nt, nullptr, hist, *keys_alt, *vals_alt));
+        if (rb == 512u)
+            VX_LAUNCH(ctx, ST_SORT_SCATTER, s, (k_radix_scatter<false, 512><<<nt, SORT_THREADS, 0, s>>>(
+                                                   *keys, *vals, n, shift, dmask, nt, nullptr, hist, *keys_alt, *vals_alt)));
+        else
+            VX_LAUNCH(ctx, ST_SORT_SCATTER, s, (k_radix_scatter<false, 256><<<nt, SORT_THREADS, 0, s>>>(
+                                                   *keys, *vals, n, shift, dmask, nt, nullptr, hist, *keys_alt, *vals_alt)));
         VX_CUDA_TRY(cudaGetLastError());
         uint32_t* t = *keys; *keys = *keys_alt; *keys_alt = t;
         t = *vals; *vals = *vals_alt; *vals_alt = t;
@@ -268,17 +281,17 @@ cudaError_t vx_radix_sort_u32_scratch(uint32_t** keys, uint32_t** vals, uint32_t
         const int nb = lutpass ? 8 : (bits - shift < 8 ? bits - shift : 8);
         const uint32_t dmask = (1u << nb) - 1u;
         if (lutpass)
-            k_radix_hist<true><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, 0, 0xffu, nt, lut, hist);
+            k_radix_hist<true, 256><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, 0, 0xffu, nt, lut, hist);
         else
-            k_radix_hist<false><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, shift, dmask, nt, nullptr, hist);
+            k_radix_hist<false, 256><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, shift, dmask, nt, nullptr, hist);
         cudaError_t e = vx_scan_u32_scratch(hist, hist, hn, nullptr, partials, s);
         if (e != cudaSuccess) return e;
         if (lutpass)
-            k_radix_scatter<true><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, 0, 0xffu, nt, lut, hist, *keys_alt,
-                                                              *vals_alt);
+            k_radix_scatter<true, 256><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, 0, 0xffu, nt, lut, hist,
+                                                                   *keys_alt, *vals_alt);
         else
-            k_radix_scatter<false><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, shift, dmask, nt, nullptr, hist,
-                                                               *keys_alt, *vals_alt);
+            k_radix_scatter<false, 256><<<nt, SORT_THREADS, 0, s>>>(*keys, *vals, n, shift, dmask, nt, nullptr, hist,
+                                                                    *keys_alt, *vals_alt);
         uint32_t* t = *keys; *keys = *keys_alt; *keys_alt = t;
         t = *vals; *vals = *vals_alt; *vals_alt = t;
     }

@@ -132,9 +132,11 @@ vx_status voxelize_window(vx_context* ctx, bool fiber, uint32_t np, const Window
         const unsigned fblocks = (unsigned)std::min<size_t>((nseg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 7);
         VX_LAUNCH(ctx, ST_REDUCE_FIBERS, s, k_reduce_fibers<<<fblocks, RED_WARPS * 32, 0, s>>>(
                                                 k0, v0, starts, misc + 2, r0, r1, seg, bx, by, bz, misc + 6));
-    } else
+    } else {
+        VX_CUDA_TRY(cudaMemsetAsync(misc + 6, 0, 4, s));
         VX_LAUNCH(ctx, ST_REDUCE_TRIS, s, k_reduce_tris<<<rblocks, RED_WARPS * 32, 0, s>>>(
-                                              k0, v0, starts, misc + 2, r0, r1, r2, seg, bx, by, bz));
+                                              k0, v0, starts, misc + 2, r0, r1, r2, seg, bx, by, bz, misc + 6));
+    }
     VX_CUDA_TRY(cudaGetLastError());
 
     // ---- compaction: dst = exclusive scan of the non-empty flags ----------------------------
