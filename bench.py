@@ -70,6 +70,26 @@ def dist_env():
 
 
 # ----------------------------------------------------------------------------------
+# replicas: every rank runs the whole workload on its own GPU; the job's time is the
+# slowest rank's and its throughput counts every rank's primitives
+# ----------------------------------------------------------------------------------
+def max_over_ranks(x, ws, device):
+    """The maximum of x over the ranks of the default process group (x itself when alone)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(ws, prims_per_rank, steps, total_ms):
+    """Primitives of all ranks over `steps` steps divided by the slowest rank's time."""
+    return ws * prims_per_rank * steps / (total_ms / 1e3)
+
+
+# ----------------------------------------------------------------------------------
 # CPU oracle timings (the reference arm and the cpu_baseline leg)
 # ----------------------------------------------------------------------------------
 def oracle_sample(w, n_fibers=None, n_segments=None):
@@ -246,12 +266,8 @@ def main():
     clk = clocks.stop()
     prof = ctx.profile_read()
     ctx.profile(False)
-    total_ms = sum(t_ms)
-    if ws > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = ws * n_prims * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(t_ms), ws, dev)
+    value = replica_throughput(ws, n_prims, args.steps, total_ms)
     launches = sum(v[0] for v in prof.values())
     prof = {k: v for k, v in prof.items() if v[0]}
 
@@ -310,12 +326,8 @@ def main():
             d2h = e2e_step()
             e_ms.append(1e3 * (time.perf_counter() - t0))
         barrier()
-        etot = sum(e_ms)
-        if ws > 1:
-            tt = torch.tensor([etot], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            etot = float(tt.item())
-        e2e = {"value": ws * n_prims * args.steps / (etot / 1e3), "unit": UNIT,
+        etot = max_over_ranks(sum(e_ms), ws, dev)
+        e2e = {"value": replica_throughput(ws, n_prims, args.steps, etot), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": etot / args.steps}
 

@@ -250,7 +250,8 @@ inline unsigned gf(size_t n, int threads, size_t cap_blocks) {
 // counters of one sub-batch (device words)
 enum {
     C_ERR = 0, C_SEGTOT, C_PAIRS_TOT, C_PAIRS, C_SEG_TOT, C_SEG, C_VOX_TOT, C_VOX,
-    C_LVL = 8   // C_LVL + l: parent count of level l (1..kMaxLevels); C_LVL + 16 + l: raw totals
+    C_LVL = 8,  // C_LVL + l: parent count of level l (1..kMaxLevels); C_LVL + 16 + l: raw totals
+    C_TAKE = 48 // work counter of the reduce kernel
 };
 
 struct SubBatch {
@@ -288,6 +289,8 @@ struct vx_batch {
     std::vector<void*> allocs;
     float headroom = 0.125f;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream2 = nullptr;     // the triangle branch of the captured graph
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int num_instances = 0;
@@ -406,13 +409,17 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
     k_bhead_starts<<<gf(S.cap_pairs, 256, blk), 256, 0, s>>>(k0, v0, S.inst_of, C + C_PAIRS, S.idx, C + C_SEG_TOT,
                                                              S.cap_seg, S.starts);
     // ---- per-voxel reduction ------------------------------------------------------------------
-    const unsigned rblocks = (unsigned)std::min<size_t>((S.cap_seg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 32);
-    if (S.fiber)
+    // resident blocks taking voxels from a counter (zeroed by a node of the graph)
+    if (cudaMemsetAsync(C + C_TAKE, 0, 4, s) != cudaSuccess) return VX_ERR_CUDA;
+    if (S.fiber) {
+        const unsigned rblocks = (unsigned)std::min<size_t>((S.cap_seg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 7);
         k_reduce_fibers<<<rblocks, RED_WARPS * 32, 0, s>>>(k0, v0, S.starts, C + C_SEG, S.r0, S.r1, S.seg, 0, 0, 0,
-                                                          nullptr);
-    else
+                                                          C + C_TAKE);
+    } else {
+        const unsigned rblocks = (unsigned)std::min<size_t>((S.cap_seg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 32);
         k_reduce_tris<<<rblocks, RED_WARPS * 32, 0, s>>>(k0, v0, S.starts, C + C_SEG, S.r0, S.r1, S.r2, S.seg, 0, 0,
-                                                         0);
+                                                         0, C + C_TAKE);
+    }
     // non-empty flags beyond the clamped segment count read as zero in the compaction scan
     k_zero_tail<<<blk, 256, 0, s>>>(S.seg.nonzero, C + C_SEG, S.cap_seg);
     if (vx_scan_u32_scratch(S.seg.nonzero, S.dst, S.cap_seg, C + C_VOX_TOT, S.part, s) != cudaSuccess)
@@ -553,6 +560,9 @@ extern "C" vx_status vx_batch_create(vx_context* ctx, const vx_primitives* tris,
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(VX_ERR_CUDA);
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(VX_ERR_CUDA);
+    if (cudaStreamCreateWithFlags(&b->cap_stream2, cudaStreamNonBlocking) != cudaSuccess) return fail(VX_ERR_CUDA);
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return fail(VX_ERR_CUDA);
+    if (cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess) return fail(VX_ERR_CUDA);
     *out = b;
     return VX_OK;
 }
@@ -564,9 +574,18 @@ extern "C" vx_status vx_batch_run(vx_batch* b, void* stream) {
     if (!b->exec) {
         // capture the whole run once on a private stream, then replay it on any stream
         if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return VX_ERR_CUDA;
+        // two branches: the triangle sub-batch forks onto a second stream and joins before
+        // the end, so the graph runs the two pipelines (separate buffers) side by side
         int64_t nl = 0;
         vx_status st = VX_OK;
-        for (int k = 0; k < 2 && st == VX_OK; ++k) st = enqueue(b, b->sb[k], b->cap_stream, false, &nl);
+        if (cudaEventRecord(b->fork, b->cap_stream) != cudaSuccess ||
+            cudaStreamWaitEvent(b->cap_stream2, b->fork, 0) != cudaSuccess)
+            st = VX_ERR_CUDA;
+        if (st == VX_OK) st = enqueue(b, b->sb[0], b->cap_stream2, false, &nl);
+        if (st == VX_OK) st = enqueue(b, b->sb[1], b->cap_stream, false, &nl);
+        if (cudaEventRecord(b->join, b->cap_stream2) != cudaSuccess ||
+            cudaStreamWaitEvent(b->cap_stream, b->join, 0) != cudaSuccess)
+            st = st == VX_OK ? VX_ERR_CUDA : st;
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
         if (st != VX_OK) {
@@ -659,6 +678,9 @@ extern "C" void vx_batch_destroy(vx_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->cap_stream2) cudaStreamDestroy(b->cap_stream2);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
     for (void* p : b->allocs) vx_dev_free(b->ctx, p, s);
     cudaStreamSynchronize(s);
     delete b;
