@@ -236,9 +236,10 @@ VX_API vx_status vx_backward_noalloc(const vx_primitives* prims, const vx_grid* 
 /* ---- batched path ------------------------------------------------------------------
  * Many instances (meshes and fiber patches of uneven size, each with its own grid) go
  * through ONE pipeline per primitive kind, from the primitives to every pyramid level
- * (K = 1 lobes), captured once into a CUDA graph and replayed by vx_batch_run.  The
- * per-instance results are the same as vx_voxelize + vx_build_lod(K = 1) on that
- * instance alone (Sec. 3-4; no counterpart of batching in the paper). */
+ * (K lobes per voxel, SGGX-H clustering when K > 1), captured once into a CUDA graph and
+ * replayed by vx_batch_run.  The per-instance results are the same as vx_voxelize +
+ * vx_build_lod on that instance alone (Sec. 3-4; no counterpart of batching in the
+ * paper). */
 typedef struct {
     int32_t kind;          /* VX_TRIANGLES or VX_FIBERS */
     vx_grid grid;          /* this instance's grid (resolution 1..1024, sub_res 8) */
@@ -262,6 +263,14 @@ typedef struct vx_batch vx_batch;
 VX_API vx_status vx_batch_create(vx_context* ctx, const vx_primitives* tris, const vx_primitives* fibers,
                                  const vx_instance* instances, int num_instances, float headroom, void* stream,
                                  vx_batch** out);
+
+/* vx_batch_create with the pyramid's lobe parameters: lod->K lobes per voxel on every level
+ * above 0 (1..8; K > 1 clusters with SGGX-H over lod->dirs, which are copied here, so every
+ * run uses these directions).  lod->num_levels must be 0 (every instance down to 1^3).
+ * lod == NULL is K = 1.  Errors as vx_batch_create. */
+VX_API vx_status vx_batch_create_lod(vx_context* ctx, const vx_primitives* tris, const vx_primitives* fibers,
+                                     const vx_instance* instances, int num_instances, const vx_lod_params* lod,
+                                     float headroom, void* stream, vx_batch** out);
 
 /* Runs the whole batch on `stream` with no host synchronisation: the first call captures
  * the pipeline into a CUDA graph (on a private stream), every call launches that graph. */

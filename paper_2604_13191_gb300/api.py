@@ -62,7 +62,7 @@ class VxAllocator(C.Structure):
 EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_lod",
            "vx_level_release", "vx_status_string", "vx_last_cuda_error", "vx_profile_enable",
            "vx_profile_read", "vx_backward", "vx_backward_noalloc", "vx_batch_create", "vx_batch_run",
-           "vx_batch_level", "vx_batch_destroy", "vx_set_max_pairs_per_pass"]
+           "vx_batch_level", "vx_batch_destroy", "vx_set_max_pairs_per_pass", "vx_batch_create_lod"]
 
 
 class VxInstance(C.Structure):
@@ -117,6 +117,10 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         lib.vx_backward.restype = C.c_int
         lib.vx_backward.argtypes = [P, C.POINTER(VxPrimitives), C.POINTER(VxGrid), P, C.c_int64, C.c_int,
                                     C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), P, P, P]
+        lib.vx_batch_create_lod.restype = C.c_int
+        lib.vx_batch_create_lod.argtypes = [P, C.POINTER(VxPrimitives), C.POINTER(VxPrimitives),
+                                            C.POINTER(VxInstance), C.c_int, C.POINTER(VxLodParams), C.c_float, P,
+                                            C.POINTER(C.c_void_p)]
         lib.vx_batch_create.restype = C.c_int
         lib.vx_batch_create.argtypes = [P, C.POINTER(VxPrimitives), C.POINTER(VxPrimitives), C.POINTER(VxInstance),
                                         C.c_int, C.c_float, P, C.POINTER(C.c_void_p)]
@@ -339,11 +343,12 @@ class Context:
             raise self._err(st, "vx_backward")
         return g_ctrl, g_w
 
-    def batch(self, instances, *, headroom: float = 0.125, stream=None) -> "Batch":
-        """vx_batch_create: instances = list of dicts with kind ("triangles" | "fibers"), grid,
-        and tri_verts [T,3,4] or ctrl [P,4] + fiber_offsets [F+1] (+ optional weights), CUDA
-        tensors.  Returns a Batch whose run() replays one captured graph."""
-        return Batch(self, instances, headroom, stream)
+    def batch(self, instances, *, K: int = 1, dirs=None, headroom: float = 0.125, stream=None) -> "Batch":
+        """vx_batch_create_lod: instances = list of dicts with kind ("triangles" | "fibers"),
+        grid, and tri_verts [T,3,4] or ctrl [P,4] + fiber_offsets [F+1] (+ optional weights),
+        CUDA tensors; K lobes per voxel above level 0 (dirs [N,3] when K > 1).  Returns a
+        Batch whose run() replays one captured graph."""
+        return Batch(self, instances, headroom, stream, K=K, dirs=dirs)
 
     def _view_level(self, L: VxLevel, keep) -> Level:
         """Typed tensors over a level whose arrays live in blocks of this context's allocator."""
@@ -492,9 +497,9 @@ def backward_noalloc(grid, *, ctrl, fiber_offsets, keys0, grad_mass, grad_moment
 
 class Batch:
     """A planned batch (vx_batch_*): one captured CUDA graph runs every instance from its
-    primitives to all of its pyramid levels (K = 1)."""
+    primitives to all of its pyramid levels (K lobes per voxel above level 0)."""
 
-    def __init__(self, ctx: Context, instances, headroom=0.125, stream=None):
+    def __init__(self, ctx: Context, instances, headroom=0.125, stream=None, K: int = 1, dirs=None):
         self.ctx = ctx
         lib = ctx.lib
         tris = [i for i in instances if i["kind"] == "triangles"]
@@ -554,11 +559,21 @@ class Batch:
             fp.kind, fp.num_prims = VX_FIBERS, fb
             fp.ctrl, fp.num_ctrl, fp.fiber_offsets, fp.num_fibers = cc.data_ptr(), cc.shape[0], oo.data_ptr(), oo.shape[0] - 1
             fp.weights = None if fw is None else fw.data_ptr()
+        lod = VxLodParams()
+        lod.num_levels, lod.K, lod.n_samples, lod.dirs = 0, int(K), 0, None
+        if K > 1:
+            if dirs is None:
+                raise ValueError("K > 1 needs the direction set (dirs [N,3])")
+            d = dirs.contiguous()
+            _check(d, torch.float32, ctx.device, "dirs")
+            self.keep.append(d)
+            lod.n_samples, lod.dirs = int(d.shape[0]), d.data_ptr()
         h = C.c_void_p()
-        st = lib.vx_batch_create(ctx.h, None if tp is None else C.byref(tp), None if fp is None else C.byref(fp),
-                                 insts, len(instances), float(headroom), _stream(stream), C.byref(h))
+        st = lib.vx_batch_create_lod(ctx.h, None if tp is None else C.byref(tp), None if fp is None else C.byref(fp),
+                                     insts, len(instances), C.byref(lod), float(headroom), _stream(stream),
+                                     C.byref(h))
         if st != 0:
-            raise ctx._err(st, "vx_batch_create")
+            raise ctx._err(st, "vx_batch_create_lod")
         self.h = h
         self.instances = instances
 

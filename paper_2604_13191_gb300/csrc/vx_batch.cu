@@ -251,7 +251,8 @@ inline unsigned gf(size_t n, int threads, size_t cap_blocks) {
 enum {
     C_ERR = 0, C_SEGTOT, C_PAIRS_TOT, C_PAIRS, C_SEG_TOT, C_SEG, C_VOX_TOT, C_VOX,
     C_LVL = 8,  // C_LVL + l: parent count of level l (1..kMaxLevels); C_LVL + 16 + l: raw totals
-    C_TAKE = 48 // work counter of the reduce kernel
+    C_TAKE = 48, // work counter of the reduce kernel
+    C_CLUSTER = 50  // [50] parents listed for clustering, [51] their take counter
 };
 
 struct SubBatch {
@@ -278,6 +279,8 @@ struct SubBatch {
     uint32_t* inst_start = nullptr;         // [(Lmax + 1)][ninst + 1]
     vx_level lv[kMaxLevels + 1];
     uint16_t* linst[kMaxLevels + 1];
+    void* stats[kMaxLevels + 1] = {};      // K > 1: lobe statistics of each level (none for 0)
+    uint32_t* work[kMaxLevels + 1] = {};   // K > 1: parents listed for clustering
     uint32_t cap_pairs = 0, cap_seg = 0, cap_v[kMaxLevels + 1];
 };
 
@@ -288,6 +291,9 @@ struct vx_batch {
     SubBatch sb[2];          // 0: triangles, 1: fibers
     std::vector<void*> allocs;
     float headroom = 0.125f;
+    int K = 1;                              // lobes per voxel of the levels above 0
+    int n_dirs = 0;
+    float4* dirs4 = nullptr;                // direction table of the lobe histograms (K > 1)
     cudaStream_t cap_stream = nullptr;
     cudaStream_t cap_stream2 = nullptr;     // the triangle branch of the captured graph
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -449,13 +455,18 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
                 return VX_ERR_CUDA;
             const uint32_t np = readback(C_LVL + 16 + l);
             S.cap_v[l] = with_headroom(np, b->headroom);
-            VX_TRY(vx_level_alloc(ctx, &S.lv[l], S.cap_v[l], 1, l, 0, s));
+            VX_TRY(vx_level_alloc(ctx, &S.lv[l], S.cap_v[l], b->K, l, 0, s));
             b->allocs.push_back(S.lv[l].block);
             VX_TRY(balloc(b, (void**)&S.linst[l], (size_t)S.cap_v[l] * 2 + 16, s));
+            if (b->K > 1) {
+                VX_TRY(balloc(b, &S.stats[l], (size_t)S.cap_v[l] * b->K * kLobeStatsBytes, s));
+                VX_TRY(balloc(b, (void**)&S.work[l], (size_t)S.cap_v[l] * 4 + 16, s));
+            }
         }
         if (vx_lod_step_batched(&S.lv[l - 1], S.linst[l - 1], nprev, S.cap_v[l - 1], &S.lv[l], S.linst[l],
                                 C + C_LVL + l, S.cap_v[l], S.flags, S.idx, S.starts, S.part, C + C_LVL + 16 + l,
-                                C + C_ERR, s) != cudaSuccess)
+                                C + C_ERR, b->dirs4, b->n_dirs, S.work[l], C + C_CLUSTER,
+                                l > 1 ? S.stats[l - 1] : nullptr, S.stats[l], s) != cudaSuccess)
             return VX_ERR_CUDA;
         k_inst_offsets<<<(S.ninst + 1 + 127) / 128, 128, 0, s>>>(S.linst[l], C + C_LVL + l, S.ninst,
                                                                  S.inst_start + (size_t)l * (S.ninst + 1));
@@ -472,14 +483,25 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
 extern "C" vx_status vx_batch_create(vx_context* ctx, const vx_primitives* tris, const vx_primitives* fibers,
                                      const vx_instance* instances, int num_instances, float headroom, void* stream,
                                      vx_batch** out) {
+    return vx_batch_create_lod(ctx, tris, fibers, instances, num_instances, nullptr, headroom, stream, out);
+}
+
+extern "C" vx_status vx_batch_create_lod(vx_context* ctx, const vx_primitives* tris, const vx_primitives* fibers,
+                                         const vx_instance* instances, int num_instances, const vx_lod_params* lod,
+                                         float headroom, void* stream, vx_batch** out) {
     if (!ctx || !instances || num_instances <= 0 || !out || !(headroom >= 0.0f)) return VX_ERR_INVALID_ARG;
     *out = nullptr;
+    const int K = lod ? lod->K : 1;
+    if (K < 1 || K > vx::kMaxK) return VX_ERR_UNSUPPORTED;
+    if (lod && lod->num_levels != 0) return VX_ERR_UNSUPPORTED;
+    if (K > 1 && (!lod->dirs || lod->n_samples < 1 || lod->n_samples > 65536)) return VX_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     ctx->last_stream = s;
     vx_batch* b = new (std::nothrow) vx_batch();
     if (!b) return VX_ERR_OUT_OF_MEMORY;
     b->ctx = ctx;
     b->headroom = headroom;
+    b->K = K;
     b->num_instances = num_instances;
     b->kind_of.resize(num_instances);
     b->local_of.resize(num_instances);
@@ -525,6 +547,12 @@ extern "C" vx_status vx_batch_create(vx_context* ctx, const vx_primitives* tris,
     if (next[1] && (!fibers || fibers->kind != VX_FIBERS || fibers->num_prims != (int64_t)next[1] || !fibers->ctrl ||
                     !fibers->fiber_offsets || fibers->num_fibers != next_fiber || ((uintptr_t)fibers->ctrl & 15)))
         return fail(VX_ERR_INVALID_ARG);
+    if (K > 1) {
+        // the direction table, copied once: runs use the directions given here
+        b->n_dirs = lod->n_samples;
+        if ((st = balloc(b, (void**)&b->dirs4, (size_t)lod->n_samples * 16, s)) != VX_OK) return fail(st);
+        if (vx_lod_batched_prepare(K, lod->dirs, lod->n_samples, b->dirs4, s) != cudaSuccess) return fail(VX_ERR_CUDA);
+    }
     for (int k = 0; k < 2; ++k) {
         SubBatch& S = b->sb[k];
         S.fiber = k == 1;
@@ -657,7 +685,7 @@ extern "C" vx_status vx_batch_level(vx_batch* b, int instance, int level, void* 
     view->level = level;
     view->resolution = I.R >> level;
     view->num_voxels = end - beg;
-    view->K = 1;
+    view->K = L.K;
     view->block = nullptr;
     view->keys = L.keys + beg;
     view->mask = L.mask + (size_t)beg * 8;
@@ -666,8 +694,8 @@ extern "C" vx_status vx_batch_level(vx_batch* b, int instance, int level, void* 
     view->occ = L.occ + beg;
     view->occ_proj = L.occ_proj + (size_t)beg * 3;
     view->lobe_count = L.lobe_count + beg;
-    view->lobes = L.lobes + (size_t)beg * 7;
-    view->compact = L.compact + (size_t)beg * 6;
+    view->lobes = L.lobes + (size_t)beg * L.K * 7;
+    view->compact = L.compact + (size_t)beg * L.K * 6;
     return VX_OK;
 }
 

@@ -121,7 +121,10 @@ cudaError_t vx_radix_sort_u32_scratch(uint32_t** keys, uint32_t** vals, uint32_t
 cudaError_t vx_lod_step_batched(const vx_level* in, const uint16_t* inst_in, const uint32_t* n_dev, uint32_t cap_in,
                                 vx_level* out, uint16_t* inst_out, uint32_t* np_dev, uint32_t cap_out,
                                 uint32_t* flags, uint32_t* idx, uint32_t* starts, uint32_t* partials, uint32_t* tmp,
-                                uint32_t* err, cudaStream_t s);
+                                uint32_t* err, const float4* dirs4, int n_dirs, uint32_t* work, uint32_t* wcnt,
+                                const void* cst, void* pst, cudaStream_t s);
+cudaError_t vx_lod_batched_prepare(int K, const float* dirs, int n, float4* dirs4, cudaStream_t s);
+constexpr size_t kLobeStatsBytes = 48;   // per-lobe histogram + sample moment kept between levels
 
 // ---- Morton ------------------------------------------------------------------
 __host__ __device__ inline uint32_t vx_part1by2(uint32_t x) {

@@ -122,6 +122,7 @@ struct LobeStats {
     int32_t h[6];
     float Mh[6];
 };
+static_assert(sizeof(LobeStats) == kLobeStatsBytes, "lobe statistics record");
 
 __global__ void k_lod_reduce(LevelIn in, const uint32_t* __restrict__ starts, uint32_t np, vx_level out, int K,
                              uint32_t* __restrict__ work, uint32_t* __restrict__ nwork,
@@ -571,7 +572,45 @@ __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluste
     }
 }
 
-// ---- batched LoD step (several instances, K = 1, counts on the device) ---------------
+// Dynamic shared memory of the three clustering tiers for K lobes.
+inline size_t cluster_smem(int G, int K) {
+    return G == 1 ? cluster_bytes(16 * K) * CL_WARPS : cluster_bytes(16 * K) + sizeof(long long) * 13 * G;
+}
+
+cudaError_t cluster_set_smem(int K) {
+    cudaError_t e = cudaFuncSetAttribute(k_sggx_cluster<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cluster_smem(1, K));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sggx_cluster<CL_BLOCK_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cluster_smem(CL_BLOCK_WARPS, K));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sggx_cluster<CL_WIDE_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cluster_smem(CL_WIDE_WARPS, K));
+    return e;
+}
+
+// Clustering of one level.  n, the level's parent count (or an upper bound of it), picks
+// the tier: a warp per parent on wide levels, a block of 8 or 16 warps on narrow ones.
+// wcnt[0] holds the number of listed parents and wcnt[1] (zero) the take counter.
+void launch_cluster(const LevelIn& li, const uint32_t* starts, const uint32_t* work, const uint32_t* wcnt,
+                    const vx_level& out, int K, const float4* dirs4, int N, const LobeStats* cst, LobeStats* pst,
+                    unsigned long long* nsampled, uint32_t n, cudaStream_t s) {
+    if (n > (uint32_t)(vx::kSMs * 16)) {
+        const unsigned cb = (unsigned)std::min<size_t>((n + CL_WARPS - 1) / CL_WARPS, (size_t)vx::kSMs * 7);
+        k_sggx_cluster<1><<<cb, CL_WARPS * 32, cluster_smem(1, K), s>>>(li, starts, work, wcnt, out, K, dirs4, N,
+                                                                          cst, pst, nsampled);
+    } else if (n > (uint32_t)vx::kSMs) {
+        const unsigned cb = (unsigned)std::max<uint32_t>(1u, std::min<uint32_t>(n, vx::kSMs * 4));
+        k_sggx_cluster<CL_BLOCK_WARPS><<<cb, CL_BLOCK_WARPS * 32, cluster_smem(CL_BLOCK_WARPS, K), s>>>(
+            li, starts, work, wcnt, out, K, dirs4, N, cst, pst, nsampled);
+    } else {
+        const unsigned cb = (unsigned)std::max<uint32_t>(1u, n);
+        k_sggx_cluster<CL_WIDE_WARPS><<<cb, CL_WIDE_WARPS * 32, cluster_smem(CL_WIDE_WARPS, K), s>>>(
+            li, starts, work, wcnt, out, K, dirs4, N, cst, pst, nsampled);
+    }
+}
+
+// ---- batched LoD step (several instances, counts on the device) -------------------------
 __global__ void k_bparent_flags(const uint64_t* __restrict__ keys, const uint16_t* __restrict__ inst,
                                 const uint32_t* __restrict__ n_dev, uint32_t cap, uint32_t* __restrict__ flags) {
     const uint32_t n = *n_dev;
@@ -668,20 +707,13 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
         stats[0] = (LobeStats*)ctx->ws[WS_LOD_STATS0].p;
         stats[1] = (LobeStats*)ctx->ws[WS_LOD_STATS1].p;
     }
-    const size_t cl_smem = cluster_bytes(16 * K) * CL_WARPS;
-    const size_t cb_smem = cluster_bytes(16 * K) + sizeof(long long) * 13 * CL_BLOCK_WARPS;
-    const size_t cw_smem = cluster_bytes(16 * K) + sizeof(long long) * 13 * CL_WIDE_WARPS;
     float4* dirs4 = nullptr;
     if (K > 1) {
         VX_TRY(vx_ws_ensure(ctx, WS_LOD_TMP, (size_t)params->n_samples * 16, s));
         dirs4 = (float4*)ctx->ws[WS_LOD_TMP].p;
         VX_LAUNCH(ctx, ST_LOD_HEADS, s, k_pack_dirs<<<(params->n_samples + 255) / 256, 256, 0, s>>>(
                                             params->dirs, params->n_samples, dirs4));
-        VX_CUDA_TRY(cudaFuncSetAttribute(k_sggx_cluster<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl_smem));
-        VX_CUDA_TRY(cudaFuncSetAttribute(k_sggx_cluster<CL_BLOCK_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)cb_smem));
-        VX_CUDA_TRY(cudaFuncSetAttribute(k_sggx_cluster<CL_WIDE_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)cw_smem));
+        VX_CUDA_TRY(cluster_set_smem(K));
     }
     for (int l = 1; l <= L; ++l) {
         const vx_level* prev = (l == 1) ? in : &out[l - 2];
@@ -703,37 +735,36 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
         VX_CUDA_TRY(cudaGetLastError());
         if (K > 1) {
             unsigned long long* cnt_dev = ctx->prof ? ctx->dev_lobe_count : nullptr;
-            if (ncur > (uint32_t)(vx::kSMs * 16)) {
-                const unsigned cb = (unsigned)std::min<size_t>((ncur + CL_WARPS - 1) / CL_WARPS, (size_t)vx::kSMs * 7);
-                VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, k_sggx_cluster<1><<<cb, CL_WARPS * 32, cl_smem, s>>>(
-                                                   li, starts, work, misc + 40, out[l - 1], K, dirs4,
-                                                   params->n_samples, cst, pst, cnt_dev));
-            } else if (ncur > (uint32_t)vx::kSMs) {
-                const unsigned cb = (unsigned)std::max<uint32_t>(1u, std::min<uint32_t>(ncur, vx::kSMs * 4));
-                VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, k_sggx_cluster<CL_BLOCK_WARPS><<<cb, CL_BLOCK_WARPS * 32, cb_smem, s>>>(
-                                                   li, starts, work, misc + 40, out[l - 1], K, dirs4,
-                                                   params->n_samples, cst, pst, cnt_dev));
-            } else {
-                const unsigned cb = (unsigned)std::max<uint32_t>(1u, ncur);
-                VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, k_sggx_cluster<CL_WIDE_WARPS><<<cb, CL_WIDE_WARPS * 32, cw_smem, s>>>(
-                                                   li, starts, work, misc + 40, out[l - 1], K, dirs4,
-                                                   params->n_samples, cst, pst, cnt_dev));
-            }
+            VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, launch_cluster(li, starts, work, misc + 40, out[l - 1], K, dirs4,
+                                                              params->n_samples, cst, pst, cnt_dev, ncur, s));
             VX_CUDA_TRY(cudaGetLastError());
         }
     }
     return VX_OK;
 }
 
-// One batched LoD step (K = 1): the parents of `in` (n_dev voxels sorted by (instance, key),
-// instance ids inst_in, capacity cap_in) into `out` (capacity cap_out), their instance ids
-// into inst_out and their count into np_dev; a parent count above cap_out sets bit 2 of err.
-// flags, idx: cap_in words; starts: cap_out + 1 words; partials: ceil(cap_in / 2048) words;
-// tmp: one word.  Only enqueues kernels (graph-capturable).
+// Direction table and shared-memory limits of batched clustering with K lobes (host side,
+// before any capture): dirs [n][3] -> dirs4 [n] float4.
+cudaError_t vx_lod_batched_prepare(int K, const float* dirs, int n, float4* dirs4, cudaStream_t s) {
+    if (K <= 1) return cudaSuccess;
+    k_pack_dirs<<<(n + 255) / 256, 256, 0, s>>>(dirs, n, dirs4);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? cluster_set_smem(K) : e;
+}
+
+// One batched LoD step: the parents of `in` (n_dev voxels sorted by (instance, key),
+// instance ids inst_in, capacity cap_in) into `out` (capacity cap_out, out->K lobes), their
+// instance ids into inst_out and their count into np_dev; a parent count above cap_out sets
+// bit 2 of err.  flags, idx: cap_in words; starts: cap_out + 1 words; partials:
+// ceil(cap_in / 2048) words; tmp: one word.  With out->K > 1 the parents with more than K
+// candidate lobes are clustered (SGGX-H): work holds cap_out words, wcnt two, cst / pst the
+// lobe statistics of `in` (NULL for level 0) and of `out`.  Only enqueues work
+// (graph-capturable).
 cudaError_t vx_lod_step_batched(const vx_level* in, const uint16_t* inst_in, const uint32_t* n_dev, uint32_t cap_in,
                                 vx_level* out, uint16_t* inst_out, uint32_t* np_dev, uint32_t cap_out,
                                 uint32_t* flags, uint32_t* idx, uint32_t* starts, uint32_t* partials, uint32_t* tmp,
-                                uint32_t* err, cudaStream_t s) {
+                                uint32_t* err, const float4* dirs4, int n_dirs, uint32_t* work, uint32_t* wcnt,
+                                const void* cst, void* pst, cudaStream_t s) {
     const unsigned gb = (unsigned)std::min<size_t>(grid_for(cap_in, 256), (size_t)vx::kSMs * 16);
     k_bparent_flags<<<gb, 256, 0, s>>>(in->keys, inst_in, n_dev, cap_in, flags);
     cudaError_t e = vx_scan_u32_scratch(flags, idx, cap_in, tmp, partials, s);
@@ -744,7 +775,16 @@ cudaError_t vx_lod_step_batched(const vx_level* in, const uint16_t* inst_in, con
     li.keys = in->keys; li.mask = in->mask; li.mass = in->mass; li.moment = in->moment;
     li.lobe_count = in->lobe_count; li.lobes = in->lobes; li.K = in->K;
     const unsigned rb = (unsigned)std::min<size_t>(grid_for(cap_out, 128), (size_t)vx::kSMs * 32);
-    k_lod_reduce<<<rb, 128, 0, s>>>(li, starts, 0u, *out, 1, nullptr, nullptr, np_dev, nullptr, nullptr);
+    const int K = out->K;
+    if (K > 1) {
+        cudaError_t e2 = cudaMemsetAsync(wcnt, 0, 8, s);
+        if (e2 != cudaSuccess) return e2;
+    }
+    k_lod_reduce<<<rb, 128, 0, s>>>(li, starts, 0u, *out, K, K > 1 ? work : nullptr, K > 1 ? wcnt : nullptr, np_dev,
+                                    (const LobeStats*)cst, (LobeStats*)pst);
+    if (K > 1)
+        launch_cluster(li, starts, work, wcnt, *out, K, dirs4, n_dirs, (const LobeStats*)cst, (LobeStats*)pst, nullptr,
+                       cap_out, s);
     k_bparent_inst<<<gb, 256, 0, s>>>(inst_in, starts, np_dev, inst_out);
     return cudaGetLastError();
 }

@@ -1,6 +1,6 @@
 """Batched path (vx_batch_*): every instance's levels equal the plain path's on that
-instance alone, bit for bit, on the first run and on graph replays; an overflow of the
-planned capacities is reported, not written past."""
+instance alone, bit for bit (K = 1 and K = 4 with SGGX-H), on the first run and on graph
+replays; an overflow of the planned capacities is reported, not written past."""
 import numpy as np
 import pytest
 
@@ -30,19 +30,19 @@ def instances(seed=4, n=12):
     return out
 
 
-def plain(ctx, inst):
+def plain(ctx, inst, K=1, dirs=None):
     if inst["kind"] == "triangles":
         L0 = ctx.voxelize(inst["grid"], tri_verts=inst["tri_verts"])
     else:
         L0 = ctx.voxelize(inst["grid"], ctrl=inst["ctrl"], fiber_offsets=inst["fiber_offsets"])
-    pyr = ctx.build_lod(L0, K=1)
+    pyr = ctx.build_lod(L0, K=K, dirs=dirs)
     torch.cuda.synchronize()
     return [L0.host()] + [p.host() for p in pyr]
 
 
-def check_batch(ctx, b, insts):
+def check_batch(ctx, b, insts, K=1, dirs=None):
     for i, inst in enumerate(insts):
-        ref = plain(ctx, inst)
+        ref = plain(ctx, inst, K, dirs)
         for l, r in enumerate(ref):
             g = b.level(i, l).host()
             for f in FIELDS:
@@ -74,5 +74,20 @@ def test_batch_capacity_overflow_is_reported():
     with pytest.raises(vx.VxError) as e:
         b.level(0, 0)
     assert e.value.status == 3
+    b.close()
+    ctx.close()
+
+
+def test_batch_with_sggx_h_matches_plain_instances(dirs5000):
+    """K = 4: every level above 0 clustered with SGGX-H inside the captured graph."""
+    ctx = vx.Context(DEV)
+    insts = instances(seed=6, n=8)
+    dirs = torch.from_numpy(dirs5000).to(DEV)
+    b = ctx.batch(insts, K=4, dirs=dirs)
+    b.run()
+    check_batch(ctx, b, insts, K=4, dirs=dirs)
+    b.run()          # graph replay
+    check_batch(ctx, b, insts, K=4, dirs=dirs)
+    assert any(int(b.level(i, 1).lobe_count.max()) > 1 for i in range(len(insts)))
     b.close()
     ctx.close()
