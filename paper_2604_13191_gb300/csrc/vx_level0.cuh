@@ -252,6 +252,7 @@ struct CapsuleTasks {
     uint32_t task[CT_TASKS];       // slot << 9 | sub-cell id
     float cap[CT_CAPS][8];         // a.xyz, b.xyz, r^2
     uint32_t mask[16];             // 512-bit mask, word w = lanes 2w (low half) and 2w+1
+    float q[32 * 7];               // w mu and w mu T(t) of up to 32 pairs (pair-major, stride 7)
 };
 
 // Step 3 of every pooled task whose sub-cell is not set yet (warp-collective); returns the
@@ -707,6 +708,23 @@ __device__ __forceinline__ void write_seg(SegOut out, uint32_t seg, uint32_t key
     }
 }
 
+// write_seg with the sums spread over lanes 0..6 (lane c holds component c)
+__device__ __forceinline__ void write_seg7(SegOut out, uint32_t seg, uint32_t key, uint32_t chunk, float accc) {
+    const int lane = threadIdx.x & 31;
+    uint64_t w = (uint64_t)chunk << (16 * (lane & 3));
+    w |= __shfl_down_sync(0xffffffffu, w, 1);
+    w |= __shfl_down_sync(0xffffffffu, w, 2);
+    const bool nz = __any_sync(0xffffffffu, chunk != 0);
+    if ((lane & 3) == 0) out.mask[(size_t)seg * 8 + (lane >> 2)] = w;
+    if (lane == 0) {
+        out.key[seg] = key;
+        out.mass[seg] = accc;
+        out.nonzero[seg] = nz ? 1u : 0u;
+    } else if (lane < 7) {
+        out.moment[(size_t)seg * 6 + lane - 1] = accc;
+    }
+}
+
 __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint32_t* __restrict__ keys,
                                                                   const uint32_t* __restrict__ prims,
                                                                   const uint32_t* __restrict__ starts,
@@ -737,10 +755,11 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
         uint32_t chunk = 0;
         bool full = false;
         int ntask = 0, ncap = 0;
-        float acc[7] = {0, 0, 0, 0, 0, 0, 0};
+        float accc = 0.0f;   // lane c < 7: component c of the mass / moment sums
         for (uint32_t base = beg; base < end; base += 32) {
             const uint32_t cnt = min(32u, end - base);
             float q[7] = {0, 0, 0, 0, 0, 0, 0};
+            __syncwarp();   // the previous batch's sums have read ct.q
             if (lane < cnt) {
                 const uint32_t p = prims[base + lane];
                 const float4 A = ra[p], B = rb[p];
@@ -759,10 +778,15 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                 q[4] = c * (t[0] * t[1]);
                 q[5] = c * (t[0] * t[2]);
                 q[6] = c * (t[1] * t[2]);
-            }
-            for (uint32_t j = 0; j < cnt; ++j) {
 #pragma unroll
-                for (int c = 0; c < 7; ++c) acc[c] = acc[c] + __shfl_sync(0xffffffffu, q[c], j);
+                for (int c = 0; c < 7; ++c) ct.q[lane * 7 + c] = q[c];
+            }
+            __syncwarp();
+            // sums in primitive order, one component per lane (the same sequence of FP32
+            // additions as a single running sum per component)
+            if (lane < 7)
+                for (uint32_t j = 0; j < cnt; ++j) accc = accc + ct.q[j * 7 + lane];
+            for (uint32_t j = 0; j < cnt; ++j) {
                 if (!full) {
                     const uint32_t p = prims[base + j];
                     const float4 A = ra[p], B = rb[p];
@@ -810,7 +834,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
             }
         }
         if (ntask > 0) chunk = capsule_step3_pool(ct, ntask, chunk);
-        write_seg(out, seg, key, chunk, acc);
+        write_seg7(out, seg, key, chunk, accc);
     }
 }
 
@@ -841,7 +865,6 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_tris(const uint32_t* 
                        iz = vx_compact1by2(key >> 2) + bz;
         uint32_t chunk = 0;
         bool full = false;
-        int ntask = 0, ncap = 0;
         float acc[7] = {0, 0, 0, 0, 0, 0, 0};
         for (uint32_t base = beg; base < end; base += 32) {
             const uint32_t cnt = min(32u, end - base);
