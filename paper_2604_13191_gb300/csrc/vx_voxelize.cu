@@ -321,41 +321,60 @@ __global__ void k_bcast(const uint32_t* __restrict__ excl, const uint32_t* __res
     }
 }
 
+// Per-segment constants of the fiber adjoint (grid units, FP64): endpoints, direction,
+// its length and reciprocal components, unit tangent, radius and weight.
+struct SegAdj {
+    double A[3], d[3], inv[3], t[3];
+    double dn, r, w;
+};
+__device__ __forceinline__ SegAdj seg_adj(float4 Af, float4 Bf) {
+    SegAdj g;
+    g.A[0] = Af.x; g.A[1] = Af.y; g.A[2] = Af.z;
+    g.d[0] = (double)Bf.x - Af.x; g.d[1] = (double)Bf.y - Af.y; g.d[2] = (double)Bf.z - Af.z;
+    g.dn = sqrt(g.d[0] * g.d[0] + g.d[1] * g.d[1] + g.d[2] * g.d[2]);
+    const double idn = g.dn > 0.0 ? 1.0 / g.dn : 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        g.inv[i] = g.d[i] != 0.0 ? 1.0 / g.d[i] : 0.0;
+        g.t[i] = g.d[i] * idn;
+    }
+    g.r = Af.w;
+    g.w = Bf.w;
+    return g;
+}
+
 // d/d(A, B, r, w) of  w * pi r^2 len * (gm + gM . T(t))  for one (segment, voxel) pair
 // (grid units); out: dA[3], dB[3], dr, dw.  FP64: the end-point terms of a piece that
 // crosses a plane almost parallel to it are large and cancel between the two voxels
 // sharing the plane, so FP32 would leave an error of a few 1e-6 of their size.
-__device__ __forceinline__ void pair_grad(float4 Af, float4 Bf, int vi, int vj, int vk, double gm, const double* gM,
+__device__ __forceinline__ void pair_grad(const SegAdj& g, int vi, int vj, int vk, double gm, const double* gM,
                                           double* out) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) out[c] = 0.0;
-    const double A[3] = {Af.x, Af.y, Af.z}, B[3] = {Bf.x, Bf.y, Bf.z};
-    const double a[3] = {A[0] - vi, A[1] - vj, A[2] - vk};
-    const double d[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+    const double a[3] = {g.A[0] - vi, g.A[1] - vj, g.A[2] - vk};
     double t0 = 0.0, t1 = 1.0;
     int ax0 = -1, ax1 = -1;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        if (d[i] == 0.0) {
+        if (g.d[i] == 0.0) {
             if (a[i] < 0.0 || a[i] > 1.0) return;
         } else {
-            const double ta = -a[i] / d[i], tb = (1.0 - a[i]) / d[i];
-            const double tn = d[i] > 0.0 ? ta : tb, tf = d[i] > 0.0 ? tb : ta;
+            const double ta = -a[i] * g.inv[i], tb = (1.0 - a[i]) * g.inv[i];
+            const double tn = g.d[i] > 0.0 ? ta : tb, tf = g.d[i] > 0.0 ? tb : ta;
             if (tn > t0) { t0 = tn; ax0 = i; }
             if (tf < t1) { t1 = tf; ax1 = i; }
         }
     }
     if (t1 <= t0) return;
-    const double r = Af.w, w = Bf.w;
     const double pi = 3.14159265358979323846;
-    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    const double t[3] = {d[0] / dn, d[1] / dn, d[2] / dn};
+    const double* t = g.t;
+    const double dn = g.dn;
     const double len = (t1 - t0) * dn;
-    const double mu = pi * r * r * len;
+    const double mu = pi * g.r * g.r * len;
     const double G = gm + gM[0] * t[0] * t[0] + gM[1] * t[1] * t[1] + gM[2] * t[2] * t[2] + gM[3] * t[0] * t[1] +
                      gM[4] * t[0] * t[2] + gM[5] * t[1] * t[2];
     out[7] = mu * G;                       // d/dw
-    out[6] = w * (2.0 * mu / r) * G;       // d/dr
+    out[6] = g.w * (2.0 * mu / g.r) * G;   // d/dr
     double cA[3] = {0.0, 0.0, 0.0}, cB[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -366,38 +385,40 @@ __device__ __forceinline__ void pair_grad(float4 Af, float4 Bf, int vi, int vj, 
         for (int k = 0; k < 3; ++k) {
             double gA = (1.0 - te) * t[k], gB = te * t[k];
             if (ax == k) {
-                gA -= (1.0 - te) * dn / d[k];
-                gB -= te * dn / d[k];
+                gA -= (1.0 - te) * dn * g.inv[k];
+                gB -= te * dn * g.inv[k];
             }
             cA[k] += sg * gA;
             cB[k] += sg * gB;
         }
     }
-    const double kmu = w * pi * r * r * G;
+    const double kmu = g.w * pi * g.r * g.r * G;
     double gt[3];
     gt[0] = 2.0 * gM[0] * t[0] + gM[3] * t[1] + gM[4] * t[2];
     gt[1] = gM[3] * t[0] + 2.0 * gM[1] * t[1] + gM[5] * t[2];
     gt[2] = gM[4] * t[0] + gM[5] * t[1] + 2.0 * gM[2] * t[2];
     const double tg = t[0] * gt[0] + t[1] * gt[1] + t[2] * gt[2];
-    const double wm = w * mu;
+    const double wmd = g.w * mu / dn;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const double gd = wm * (gt[k] - t[k] * tg) / dn;
+        const double gd = wmd * (gt[k] - t[k] * tg);
         out[k] = kmu * cA[k] - gd;
         out[3 + k] = kmu * cB[k] + gd;
     }
 }
 
-__device__ __forceinline__ int64_t find_key64(const uint64_t* __restrict__ keys, uint32_t n, uint64_t k) {
-    uint32_t lo = 0, hi = n;
+// first index in keys[lo, hi) whose key is >= k (hi when none)
+__device__ __forceinline__ uint32_t lower_key(const uint64_t* __restrict__ keys, uint32_t lo, uint32_t hi, uint64_t k) {
     while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
+        const uint32_t mid = (lo + hi) >> 1;
         if (keys[mid] < k) lo = mid + 1; else hi = mid;
     }
-    return (lo < n && keys[lo] == k) ? (int64_t)lo : -1;
+    return lo;
 }
 
-// warp per segment: sum of its pair gradients (lane j takes pairs j, j+32, ...; fixed tree)
+// warp per segment: sum of its pair gradients (lane j takes pairs j, j+32, ...; fixed tree).
+// The segment's candidate keys lie between their minimum and maximum, so the voxels are
+// looked up in the slice of keys0 between those two keys.
 __global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_fibers(const float4* __restrict__ ra,
                                                                     const float4* __restrict__ rb, uint32_t np,
                                                                     const uint32_t* __restrict__ offs,
@@ -410,21 +431,38 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_fibers(const float4
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * EMIT_WARPS;
     for (uint32_t p = blockIdx.x * EMIT_WARPS + (threadIdx.x >> 5); p < np; p += warps) {
-        const float4 A = ra[p], B = rb[p];
         const uint32_t beg = offs[p], n = cnt[p];
         double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (uint32_t j = lane; j < n; j += 32) {
-            const uint32_t key = pkeys[beg + j];
-            const int64_t v = find_key64(keys0, V0, (uint64_t)key);
-            if (v < 0) continue;
-            double g[8];
-            double gMv[6];
+        if (n > 0) {
+            const SegAdj g = seg_adj(ra[p], rb[p]);
+            uint32_t kmin = 0xffffffffu, kmax = 0u;
+            for (uint32_t j = lane; j < n; j += 32) {
+                const uint32_t key = pkeys[beg + j];
+                kmin = min(kmin, key);
+                kmax = max(kmax, key);
+            }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) gMv[c] = gM[(size_t)v * 6 + c];
-            pair_grad(A, B, (int)vx_compact1by2(key), (int)vx_compact1by2(key >> 1), (int)vx_compact1by2(key >> 2),
-                      gm[v], gMv, g);
+            for (int o = 16; o > 0; o >>= 1) {
+                kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+                kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+            }
+            uint32_t bound = 0;
+            if (lane == 0) bound = lower_key(keys0, 0, V0, (uint64_t)kmin);
+            if (lane == 1) bound = lower_key(keys0, 0, V0, (uint64_t)kmax + 1);
+            const uint32_t lo = __shfl_sync(0xffffffffu, bound, 0), hi = __shfl_sync(0xffffffffu, bound, 1);
+            for (uint32_t j = lane; j < n; j += 32) {
+                const uint32_t key = pkeys[beg + j];
+                const uint32_t v = lower_key(keys0, lo, hi, (uint64_t)key);
+                if (v >= hi || keys0[v] != (uint64_t)key) continue;
+                double gr[8];
+                double gMv[6];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] = acc[c] + g[c];
+                for (int c = 0; c < 6; ++c) gMv[c] = gM[(size_t)v * 6 + c];
+                pair_grad(g, (int)vx_compact1by2(key), (int)vx_compact1by2(key >> 1), (int)vx_compact1by2(key >> 2),
+                          gm[v], gMv, gr);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[c] = acc[c] + gr[c];
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
@@ -592,10 +630,26 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_tris(const float4* 
         const float4 A = r0[p], B = r1[p], Cv = r2[p];
         const uint32_t beg = offs[p], n = cnt[p];
         double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        // the triangle's voxels lie in the slice of keys0 between its smallest and largest key
+        uint32_t kmin = 0xffffffffu, kmax = 0u;
         for (uint32_t j = lane; j < n; j += 32) {
             const uint32_t key = pkeys[beg + j];
-            const int64_t v = find_key64(keys0, V0, (uint64_t)key);
-            if (v < 0) continue;
+            kmin = min(kmin, key);
+            kmax = max(kmax, key);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        }
+        uint32_t bound = 0;
+        if (n > 0 && lane == 0) bound = lower_key(keys0, 0, V0, (uint64_t)kmin);
+        if (n > 0 && lane == 1) bound = lower_key(keys0, 0, V0, (uint64_t)kmax + 1);
+        const uint32_t lo = __shfl_sync(0xffffffffu, bound, 0), hi = __shfl_sync(0xffffffffu, bound, 1);
+        for (uint32_t j = lane; j < n; j += 32) {
+            const uint32_t key = pkeys[beg + j];
+            const uint32_t v = lower_key(keys0, lo, hi, (uint64_t)key);
+            if (v >= hi || keys0[v] != (uint64_t)key) continue;
             double g[10];
             double gMv[6];
 #pragma unroll
