@@ -366,44 +366,48 @@ __device__ __forceinline__ void pair_grad(const SegAdj& g, int vi, int vj, int v
         }
     }
     if (t1 <= t0) return;
+    // (no bit-exact contract here: the multiply-adds are fused explicitly)
     const double pi = 3.14159265358979323846;
     const double* t = g.t;
     const double dn = g.dn;
     const double len = (t1 - t0) * dn;
-    const double mu = pi * g.r * g.r * len;
-    const double G = gm + gM[0] * t[0] * t[0] + gM[1] * t[1] * t[1] + gM[2] * t[2] * t[2] + gM[3] * t[0] * t[1] +
-                     gM[4] * t[0] * t[2] + gM[5] * t[1] * t[2];
+    const double pr2 = pi * g.r * g.r;
+    const double mu = pr2 * len;
+    double gt[3];
+    gt[0] = fma(2.0 * gM[0], t[0], fma(gM[3], t[1], gM[4] * t[2]));
+    gt[1] = fma(gM[3], t[0], fma(2.0 * gM[1], t[1], gM[5] * t[2]));
+    gt[2] = fma(gM[4], t[0], fma(gM[5], t[1], 2.0 * gM[2] * t[2]));
+    // gm + gM . T(t) = gm + (t . gt) / 2 (T(t) pairs each off-diagonal once)
+    const double tg = fma(t[0], gt[0], fma(t[1], gt[1], t[2] * gt[2]));
+    const double G = fma(0.5, tg, gm);
     out[7] = mu * G;                       // d/dw
     out[6] = g.w * (2.0 * mu / g.r) * G;   // d/dr
-    double cA[3] = {0.0, 0.0, 0.0}, cB[3] = {0.0, 0.0, 0.0};
+    // d len / d A, d B: the clipped ends (1 - t_e) A + t_e B move with both endpoints, and an
+    // end on a voxel plane also slides along the segment (its t_e depends on the endpoints)
+    double cA[3], cB[3];
+    const double dte = t1 - t0;
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const double te = e == 0 ? t0 : t1;
-        const int ax = e == 0 ? ax0 : ax1;
-        const double sg = e == 0 ? -1.0 : 1.0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            double gA = (1.0 - te) * t[k], gB = te * t[k];
-            if (ax == k) {
-                gA -= (1.0 - te) * dn * g.inv[k];
-                gB -= te * dn * g.inv[k];
-            }
-            cA[k] += sg * gA;
-            cB[k] += sg * gB;
-        }
+    for (int k = 0; k < 3; ++k) {
+        cA[k] = -dte * t[k];
+        cB[k] = dte * t[k];
     }
-    const double kmu = g.w * pi * g.r * g.r * G;
-    double gt[3];
-    gt[0] = 2.0 * gM[0] * t[0] + gM[3] * t[1] + gM[4] * t[2];
-    gt[1] = gM[3] * t[0] + 2.0 * gM[1] * t[1] + gM[5] * t[2];
-    gt[2] = gM[4] * t[0] + gM[5] * t[1] + 2.0 * gM[2] * t[2];
-    const double tg = t[0] * gt[0] + t[1] * gt[1] + t[2] * gt[2];
+    if (ax0 >= 0) {
+        const double f = dn * g.inv[ax0];
+        cA[ax0] = fma((1.0 - t0), f, cA[ax0]);
+        cB[ax0] = fma(t0, f, cB[ax0]);
+    }
+    if (ax1 >= 0) {
+        const double f = dn * g.inv[ax1];
+        cA[ax1] = fma(-(1.0 - t1), f, cA[ax1]);
+        cB[ax1] = fma(-t1, f, cB[ax1]);
+    }
+    const double kmu = g.w * pr2 * G;
     const double wmd = g.w * mu / dn;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const double gd = wmd * (gt[k] - t[k] * tg);
-        out[k] = kmu * cA[k] - gd;
-        out[3 + k] = kmu * cB[k] + gd;
+        const double gd = wmd * fma(-t[k], tg, gt[k]);
+        out[k] = fma(kmu, cA[k], -gd);
+        out[3 + k] = fma(kmu, cB[k], gd);
     }
 }
 
