@@ -119,10 +119,8 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_bcandidates(const float4* _
             bool hit = false;
             int vi = 0, vj = 0, vk = 0;
             if (idx < tot) {
-                const int ix = (int)(idx % rg.n[0]);
-                const long long t = idx / rg.n[0];
-                const int iy = (int)(t % rg.n[1]);
-                const int iz = (int)(t / rg.n[1]);
+                int ix, iy, iz;
+                voxel_of(idx, tot, rg, ix, iy, iz);
                 vi = rg.lo[0] + ix; vj = rg.lo[1] + iy; vk = rg.lo[2] + iz;
                 hit = FIBER ? capsule_voxel_candidate(a, b, vi, vj, vk) : tri_voxel_candidate(a, b, c, vi, vj, vk);
             }

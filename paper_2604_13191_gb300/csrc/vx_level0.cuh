@@ -566,6 +566,23 @@ __host__ __device__ inline Window full_window(int R) {
     for (int i = 0; i < 3; ++i) { w.lo[i] = 0; w.hi[i] = R - 1; }
     return w;
 }
+// (ix, iy, iz) of flat index idx < tot in a range (x fastest); 32-bit division when the
+// range holds fewer than 2^32 voxels (always inside a 1024^3 window)
+__device__ __forceinline__ void voxel_of(long long idx, long long tot, const Range& rg, int& ix, int& iy, int& iz) {
+    if (tot <= 0xffffffffll) {
+        const uint32_t i = (uint32_t)idx, n0 = (uint32_t)rg.n[0], n1 = (uint32_t)rg.n[1];
+        const uint32_t t = i / n0;
+        ix = (int)(i - t * n0);
+        iz = (int)(t / n1);
+        iy = (int)(t - (uint32_t)iz * n1);
+    } else {
+        const long long t = idx / rg.n[0];
+        ix = (int)(idx - t * rg.n[0]);
+        iz = (int)(t / rg.n[1]);
+        iy = (int)(t - (long long)iz * rg.n[1]);
+    }
+}
+
 __device__ __forceinline__ Range make_range(const float* mn, const float* mx, const Window& w) {
     Range r;
     r.total = 1;
@@ -653,10 +670,8 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_candidates(const float4* __
             bool hit = false;
             int vi = 0, vj = 0, vk = 0;
             if (idx < tot) {
-                int ix = (int)(idx % rg.n[0]);
-                long long t = idx / rg.n[0];
-                int iy = (int)(t % rg.n[1]);
-                int iz = (int)(t / rg.n[1]);
+                int ix, iy, iz;
+                voxel_of(idx, tot, rg, ix, iy, iz);
                 vi = rg.lo[0] + ix; vj = rg.lo[1] + iy; vk = rg.lo[2] + iz;
                 hit = FIBER ? capsule_voxel_candidate(a, b, vi, vj, vk) : tri_voxel_candidate(a, b, c, vi, vj, vk);
             }
