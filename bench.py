@@ -299,23 +299,14 @@ def main():
         h_out = torch.empty(sum(sizes) + 4096 * len(sizes), dtype=torch.uint8).pin_memory()
         h2d = h_ctrl.numel() * 4 + h_off.numel() * 8 + h_dirs.numel() * 4
 
-        copy_stream = torch.cuda.Stream(device=dev)
-
         def e2e_step():
             c = h_ctrl.to(dev, non_blocking=True)
             o = h_off.to(dev, non_blocking=True)
             d = h_dirs.to(dev, non_blocking=True)
             L0 = ctx.voxelize(w.grid, ctrl=c, fiber_offsets=o, num_prims=n_prims)
-            # level 0 goes down on a second stream while the pyramid is built
-            done0 = torch.cuda.Event()
-            done0.record()
-            n0 = L0.block.numel()
-            with torch.cuda.stream(copy_stream):
-                copy_stream.wait_event(done0)
-                h_out[:n0].copy_(L0.block, non_blocking=True)
             pyr = ctx.build_lod(L0, K=K_LOBES, dirs=d)
-            pos, nbytes = n0, n0
-            for lv in pyr:
+            pos, nbytes = 0, 0
+            for lv in [L0] + pyr:
                 n = lv.block.numel()
                 h_out[pos: pos + n].copy_(lv.block, non_blocking=True)
                 pos += n
