@@ -58,8 +58,9 @@ typedef struct {
 /* Cubic grid (Sec. 3.1: positions normalised to [0, Resolution) per axis).  Voxel (i,j,k)
  * covers origin + voxel_size * [i,i+1] x [j,j+1] x [k,k+1].  Grid coordinates are
  * u = (p - origin) * (1 / voxel_size), evaluated in FP32.
- * resolution: power of two, 1..2048 (1..1024 for vx_backward and batches).  sub_res: sub-cells per voxel edge; 8 (the paper's
- * third-level resolution, Sec. 3.1) is the supported value. */
+ * resolution: power of two, 1..2048 (1..1024 for vx_backward and batches).
+ * sub_res: sub-cells per voxel edge; 8 (the paper's third-level resolution, Sec. 3.1) is
+ * the supported value. */
 typedef struct {
     float origin[3];
     float voxel_size;
