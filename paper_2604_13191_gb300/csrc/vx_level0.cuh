@@ -448,25 +448,44 @@ __device__ __forceinline__ uint32_t tri_bits16(const float v[3][3], const float 
     return bits;
 }
 
-// Sutherland-Hodgman clip of a polygon against x_axis >= c (ge) or x_axis <= c
-__device__ __forceinline__ int clip_plane(const float (*in)[3], int n, float (*out)[3], int axis, float c, bool ge) {
+// Clipped-polygon buffers of the triangle measure: two polygons of up to 12 vertices per
+// thread, in shared memory with the thread index fastest (element (poly, vertex, coord) of
+// thread t at [((poly * 12 + vertex) * 3 + coord) * NT + t]), so the threads of a warp hit
+// 32 different banks.  NT = threads per block.
+template <int NT>
+struct PolyBuf {
+    float x[2 * 12 * 3 * NT];
+};
+
+// Sutherland-Hodgman clip of polygon `pi` (n vertices) against coord_axis >= c (ge) or
+// <= c into polygon `po`; returns the new vertex count.
+template <int NT>
+__device__ __forceinline__ int clip_plane_s(float* __restrict__ buf, int pi, int po, int n, int axis, float c, bool ge) {
+    const int t = threadIdx.x;
+    auto at = [&](int poly, int v, int j) -> float& { return buf[((poly * 12 + v) * 3 + j) * NT + t]; };
     int m = 0;
     for (int k = 0; k < n; ++k) {
-        const float* S = in[k];
-        const float* E = in[(k + 1) == n ? 0 : k + 1];
-        bool sin_ = ge ? (S[axis] >= c) : (S[axis] <= c);
-        bool ein = ge ? (E[axis] >= c) : (E[axis] <= c);
+        const int kn = (k + 1) == n ? 0 : k + 1;
+        const float Sa = at(pi, k, axis), Ea = at(pi, kn, axis);
+        const bool sin_ = ge ? (Sa >= c) : (Sa <= c);
+        const bool ein = ge ? (Ea >= c) : (Ea <= c);
         if (ein) {
             if (!sin_) {
-                float s = (c - S[axis]) / (E[axis] - S[axis]);
-                for (int j = 0; j < 3; ++j) out[m][j] = (j == axis) ? c : S[j] + s * (E[j] - S[j]);
+                const float sv = (c - Sa) / (Ea - Sa);
+                for (int j = 0; j < 3; ++j) {
+                    const float Sj = at(pi, k, j), Ej = at(pi, kn, j);
+                    at(po, m, j) = (j == axis) ? c : Sj + sv * (Ej - Sj);
+                }
                 ++m;
             }
-            for (int j = 0; j < 3; ++j) out[m][j] = E[j];
+            for (int j = 0; j < 3; ++j) at(po, m, j) = at(pi, kn, j);
             ++m;
         } else if (sin_) {
-            float s = (c - S[axis]) / (E[axis] - S[axis]);
-            for (int j = 0; j < 3; ++j) out[m][j] = (j == axis) ? c : S[j] + s * (E[j] - S[j]);
+            const float sv = (c - Sa) / (Ea - Sa);
+            for (int j = 0; j < 3; ++j) {
+                const float Sj = at(pi, k, j), Ej = at(pi, kn, j);
+                at(po, m, j) = (j == axis) ? c : Sj + sv * (Ej - Sj);
+            }
             ++m;
         }
     }
@@ -474,21 +493,27 @@ __device__ __forceinline__ int clip_plane(const float (*in)[3], int n, float (*o
 }
 
 // area (voxel units^2) of the triangle clipped to the voxel [0,1]^3
-__device__ __noinline__ float tri_measure(const float v[3][3]) {
-    float A[12][3], B[12][3];
-    int n = 3;
+template <int NT>
+__device__ float tri_measure(const float v[3][3], PolyBuf<NT>& pb) {
+    float* buf = pb.x;
+    const int t = threadIdx.x;
+    auto at = [&](int poly, int vv, int j) -> float& { return buf[((poly * 12 + vv) * 3 + j) * NT + t]; };
+#pragma unroll
     for (int k = 0; k < 3; ++k)
-        for (int j = 0; j < 3; ++j) A[k][j] = v[k][j];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) at(0, k, j) = v[k][j];
+    int n = 3;
     for (int axis = 0; axis < 3 && n > 0; ++axis) {
-        n = clip_plane(A, n, B, axis, 0.0f, true);
+        n = clip_plane_s<NT>(buf, 0, 1, n, axis, 0.0f, true);
         if (n == 0) break;
-        n = clip_plane(B, n, A, axis, 1.0f, false);
+        n = clip_plane_s<NT>(buf, 1, 0, n, axis, 1.0f, false);
     }
     if (n < 3) return 0.0f;
     float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+    const float a0 = at(0, 0, 0), a1 = at(0, 0, 1), a2 = at(0, 0, 2);
     for (int k = 1; k + 1 < n; ++k) {
-        float e1[3], e2[3];
-        for (int j = 0; j < 3; ++j) { e1[j] = A[k][j] - A[0][j]; e2[j] = A[k + 1][j] - A[0][j]; }
+        const float e1[3] = {at(0, k, 0) - a0, at(0, k, 1) - a1, at(0, k, 2) - a2};
+        const float e2[3] = {at(0, k + 1, 0) - a0, at(0, k + 1, 1) - a1, at(0, k + 1, 2) - a2};
         cx = cx + (e1[1] * e2[2] - e1[2] * e2[1]);
         cy = cy + (e1[2] * e2[0] - e1[0] * e2[2]);
         cz = cz + (e1[0] * e2[1] - e1[1] * e2[0]);
@@ -872,6 +897,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_tris(const uint32_t* 
         if (lane == 0) v = atomicAdd(next, 1u);
         return __shfl_sync(0xffffffffu, v, 0);
     };
+    __shared__ PolyBuf<RED_WARPS * 32> polys;
     for (uint32_t seg = next ? take() : blockIdx.x * RED_WARPS + (threadIdx.x >> 5); seg < nseg;
          seg = next ? take() : seg + warps) {
         const uint32_t beg = starts[seg], end = starts[seg + 1];
@@ -889,7 +915,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_tris(const uint32_t* 
                 const float4 a = r0[p], b = r1[p], c = r2[p];
                 float v[3][3], f[3][3];
                 tri_local(a, b, c, (int)ix, (int)iy, (int)iz, v, f);
-                float mu = tri_measure(v);
+                float mu = tri_measure<RED_WARPS * 32>(v, polys);
                 float n0 = f[0][1] * f[1][2] - f[0][2] * f[1][1];
                 float n1 = f[0][2] * f[1][0] - f[0][0] * f[1][2];
                 float n2 = f[0][0] * f[1][1] - f[0][1] * f[1][0];
