@@ -79,7 +79,9 @@ enum { VX_TRIANGLES = 0, VX_FIBERS = 1 };
  *   radius is the mean of its two control-point radii.  Primitive ids count segments
  *   fiber by fiber; num_prims must equal sum_f max(off[f+1]-off[f]-1, 0) (checked on the
  *   device; a mismatch returns VX_ERR_INVALID_ARG).
- * weights (device) [num_prims] float >= 0, or NULL for all ones. */
+ * weights (device) [num_prims] float >= 0, or NULL for all ones.
+ * Coordinates, radii and weights must be finite, radii and weights >= 0; a record that is
+ * not makes vx_voxelize / vx_backward return VX_ERR_INVALID_ARG. */
 typedef struct {
     int32_t kind;
     int64_t num_prims;

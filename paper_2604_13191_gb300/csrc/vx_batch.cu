@@ -62,6 +62,7 @@ __global__ void k_bprep_fibers(const float4* __restrict__ ctrl, const int64_t* _
     B.x = (pb.x - g.o[0]) * g.s; B.y = (pb.y - g.o[1]) * g.s; B.z = (pb.z - g.o[2]) * g.s;
     A.w = ((pa.w + pb.w) * 0.5f) * g.s;
     B.w = weights ? weights[p] : 1.0f;
+    if (bad_record(A, B)) atomicOr(err, 1u);
     ra[p] = A;
     rb[p] = B;
     inst_of[p] = (uint8_t)ii;
@@ -84,6 +85,7 @@ __global__ void k_bprep_tris(const float4* __restrict__ tv, const float* __restr
     a.w = weights ? weights[p] : 1.0f;
     b.w = 0.0f;
     c.w = 0.0f;
+    if (bad_record(a, b) || bad_record(c, c)) atomicOr(err, 1u);
     r0[p] = a; r1[p] = b; r2[p] = c;
     inst_of[p] = (uint8_t)ii;
 }

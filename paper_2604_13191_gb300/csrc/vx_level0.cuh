@@ -533,6 +533,14 @@ __global__ void k_fiber_seg_counts(const int64_t* __restrict__ off, int64_t F, u
 }
 
 // rec_a = (A.xyz, r_g), rec_b = (B.xyz, w) in grid coordinates
+// a record the method cannot use: a non-finite coordinate, radius or weight, or a negative
+// radius or weight
+__device__ __forceinline__ bool bad_record(float4 a, float4 b) {
+    const bool fin = isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(a.w) && isfinite(b.x) &&
+                     isfinite(b.y) && isfinite(b.z) && isfinite(b.w);
+    return !fin || a.w < 0.0f || b.w < 0.0f;
+}
+
 __global__ void k_prep_fibers(const float4* __restrict__ ctrl, const int64_t* __restrict__ off,
                               const uint32_t* __restrict__ seg_start, int64_t F, const uint32_t* __restrict__ seg_total,
                               const float* __restrict__ weights, uint32_t np, GridDev g, float4* __restrict__ ra,
@@ -556,13 +564,15 @@ __global__ void k_prep_fibers(const float4* __restrict__ ctrl, const int64_t* __
     B.x = (pb.x - g.o[0]) * g.s; B.y = (pb.y - g.o[1]) * g.s; B.z = (pb.z - g.o[2]) * g.s;
     A.w = ((pa.w + pb.w) * 0.5f) * g.s;
     B.w = weights ? weights[p] : 1.0f;
+    if (bad_record(A, B)) atomicOr(err, 1u);
     ra[p] = A;
     rb[p] = B;
 }
 
 // tri records: (U0, w), (U1, 0), (U2, 0)
 __global__ void k_prep_tris(const float4* __restrict__ tv, const float* __restrict__ weights, uint32_t np, GridDev g,
-                            float4* __restrict__ r0, float4* __restrict__ r1, float4* __restrict__ r2) {
+                            float4* __restrict__ r0, float4* __restrict__ r1, float4* __restrict__ r2,
+                            uint32_t* __restrict__ err) {
     uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     float4 v0 = tv[3 * (size_t)p], v1 = tv[3 * (size_t)p + 1], v2 = tv[3 * (size_t)p + 2];
@@ -573,6 +583,7 @@ __global__ void k_prep_tris(const float4* __restrict__ tv, const float* __restri
     a.w = weights ? weights[p] : 1.0f;
     b.w = 0.0f;
     c.w = 0.0f;
+    if (bad_record(a, b) || bad_record(c, c)) atomicOr(err, 1u);
     r0[p] = a; r1[p] = b; r2[p] = c;
 }
 
@@ -617,7 +628,8 @@ __device__ __forceinline__ Range make_range(const float* mn, const float* mx, co
         const int lo = fl < (float)w.lo[i] ? w.lo[i] : (fl > (float)w.hi[i] ? w.hi[i] + 1 : (int)fl);
         const int hi = fh < (float)w.lo[i] ? w.lo[i] - 1 : (fh > (float)w.hi[i] ? w.hi[i] : (int)fh);
         r.lo[i] = lo;
-        r.n[i] = hi >= lo ? hi - lo + 1 : 0;
+        // a NaN bound (rejected input, flagged by the prep kernels) gives an empty range
+        r.n[i] = (mn[i] <= mx[i] && hi >= lo) ? hi - lo + 1 : 0;
         r.total *= r.n[i];
     }
     return r;
@@ -731,24 +743,8 @@ __global__ void k_head_starts(const uint32_t* __restrict__ keys, uint32_t n, con
 // reduce: warp per candidate voxel
 // lane l owns sub-cells sz = l >> 2, sy = 2 (l & 3) + {0,1}, sx = 0..7 (16 bits)
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ void write_seg(SegOut out, uint32_t seg, uint32_t key, uint32_t chunk, const float* acc) {
-    const int lane = threadIdx.x & 31;
-    // word sz = lanes 4 sz .. 4 sz + 3, chunk q at bits 16 q
-    uint64_t w = (uint64_t)chunk << (16 * (lane & 3));
-    w |= __shfl_down_sync(0xffffffffu, w, 1);
-    w |= __shfl_down_sync(0xffffffffu, w, 2);
-    bool nz = __any_sync(0xffffffffu, chunk != 0);
-    if ((lane & 3) == 0) out.mask[(size_t)seg * 8 + (lane >> 2)] = w;
-    if (lane == 0) {
-        out.key[seg] = key;
-        out.mass[seg] = acc[0];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) out.moment[(size_t)seg * 6 + c] = acc[1 + c];
-        out.nonzero[seg] = nz ? 1u : 0u;
-    }
-}
-
-// write_seg with the sums spread over lanes 0..6 (lane c holds component c)
+// Writes one candidate voxel's outputs: its mask (lanes' 16-bit chunks gathered into the
+// 8 words), key, non-empty flag and the sums spread over lanes 0..6 (lane c: component c).
 __device__ __forceinline__ void write_seg7(SegOut out, uint32_t seg, uint32_t key, uint32_t chunk, float accc) {
     const int lane = threadIdx.x & 31;
     uint64_t w = (uint64_t)chunk << (16 * (lane & 3));
@@ -898,6 +894,8 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_tris(const uint32_t* 
         return __shfl_sync(0xffffffffu, v, 0);
     };
     __shared__ PolyBuf<RED_WARPS * 32> polys;
+    __shared__ float qs[RED_WARPS][32 * 7];       // per-pair w mu, w mu T(n) (pair-major)
+    float* const qw = qs[threadIdx.x >> 5];
     for (uint32_t seg = next ? take() : blockIdx.x * RED_WARPS + (threadIdx.x >> 5); seg < nseg;
          seg = next ? take() : seg + warps) {
         const uint32_t beg = starts[seg], end = starts[seg + 1];
@@ -906,10 +904,11 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_tris(const uint32_t* 
                        iz = vx_compact1by2(key >> 2) + bz;
         uint32_t chunk = 0;
         bool full = false;
-        float acc[7] = {0, 0, 0, 0, 0, 0, 0};
+        float accc = 0.0f;   // lane c < 7: component c of the mass / moment sums
         for (uint32_t base = beg; base < end; base += 32) {
             const uint32_t cnt = min(32u, end - base);
             float q[7] = {0, 0, 0, 0, 0, 0, 0};
+            __syncwarp();   // the previous batch's sums have read qw
             if (lane < cnt) {
                 const uint32_t p = prims[base + lane];
                 const float4 a = r0[p], b = r1[p], c = r2[p];
@@ -930,10 +929,14 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_tris(const uint32_t* 
                 q[4] = cc * (t[0] * t[1]);
                 q[5] = cc * (t[0] * t[2]);
                 q[6] = cc * (t[1] * t[2]);
-            }
-            for (uint32_t j = 0; j < cnt; ++j) {
 #pragma unroll
-                for (int c = 0; c < 7; ++c) acc[c] = acc[c] + __shfl_sync(0xffffffffu, q[c], j);
+                for (int c = 0; c < 7; ++c) qw[lane * 7 + c] = q[c];
+            }
+            __syncwarp();
+            // sums in primitive order, one component per lane (one FP32 running sum each)
+            if (lane < 7)
+                for (uint32_t j = 0; j < cnt; ++j) accc = accc + qw[j * 7 + lane];
+            for (uint32_t j = 0; j < cnt; ++j) {
                 if (!full) {
                     const uint32_t p = prims[base + j];
                     const float4 a = r0[p], b = r1[p], c = r2[p];
@@ -944,7 +947,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_tris(const uint32_t* 
                 }
             }
         }
-        write_seg(out, seg, key, chunk, acc);
+        write_seg7(out, seg, key, chunk, accc);
     }
 }
 

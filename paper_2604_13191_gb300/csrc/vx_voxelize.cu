@@ -205,7 +205,7 @@ extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, co
                                                          misc + 4, prims->weights, np, g, r0, r1, misc));
     } else {
         VX_LAUNCH(ctx, ST_PREP, s, k_prep_tris<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->tri_verts, prims->weights, np, g, r0,
-                                                       r1, r2));
+                                                       r1, r2, misc));
     }
     VX_CUDA_TRY(cudaGetLastError());
     vx_stage_units(ctx, ST_PREP, np);
@@ -764,7 +764,7 @@ extern "C" vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, co
         VX_TRY(vx_ws_ensure(ctx, WS_REC_C, (size_t)np * 16, s));
         r2 = (float4*)ctx->ws[WS_REC_C].p;
         VX_LAUNCH(ctx, ST_PREP, s, k_prep_tris<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->tri_verts,
-                                                                               prims->weights, np, g, r0, r1, r2));
+                                                                               prims->weights, np, g, r0, r1, r2, misc));
     }
     VX_TRY(vx_ws_ensure(ctx, WS_COUNT, (size_t)np * 4, s));
     VX_TRY(vx_ws_ensure(ctx, WS_OFFS, (size_t)np * 4, s));

@@ -229,6 +229,26 @@ def test_invalid_arguments(ctx):
     with pytest.raises(vx.VxError) as e:
         ctx.voxelize(synth.Grid((0.0, 0.0, 0.0), 1.0 / 4096, 4096), ctrl=ctrl, fiber_offsets=off)
     assert e.value.status == 6
+    # non-finite coordinates and negative weights or radii are rejected (the ranges of such
+    # records are empty, so nothing runs on them before the error is read back)
+    bad = ctrl.clone()
+    bad[1, 0] = float("nan")
+    with pytest.raises(vx.VxError) as e:
+        ctx.voxelize(grid, ctrl=bad, fiber_offsets=off)
+    assert e.value.status == 1
+    bad = ctrl.clone()
+    bad[2, 3] = -1.0
+    with pytest.raises(vx.VxError) as e:
+        ctx.voxelize(grid, ctrl=bad, fiber_offsets=off)
+    assert e.value.status == 1
+    tris = torch.full((2, 3, 4), 0.5, dtype=torch.float32, device=DEV)
+    with pytest.raises(vx.VxError) as e:
+        ctx.voxelize(grid, tri_verts=tris, weights=torch.tensor([1.0, -2.0], device=DEV))
+    assert e.value.status == 1
+    tris[1, 2, 1] = float("inf")
+    with pytest.raises(vx.VxError) as e:
+        ctx.voxelize(grid, tri_verts=tris)
+    assert e.value.status == 1
     L0 = ctx.voxelize(grid, ctrl=ctrl, fiber_offsets=off)
     with pytest.raises(vx.VxError) as e:
         ctx.build_lod(L0, K=9)
