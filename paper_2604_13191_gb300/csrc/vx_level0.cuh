@@ -796,11 +796,28 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
             const uint32_t cnt = min(32u, end - base);
             float q[7] = {0, 0, 0, 0, 0, 0, 0};
             __syncwarp();   // the previous batch's sums have read ct.q
+            // order of the mask tests: capsules whose axis passes deepest into the voxel first
+            // (they set the most bits, so later capsules find more lanes already full); the
+            // mask is an OR, so the order does not change it
+            uint32_t okey = 0xffffffe0u | (uint32_t)lane;
             if (lane < cnt) {
                 const uint32_t p = prims[base + lane];
                 const float4 A = ra[p], B = rb[p];
                 float a[3] = {A.x - fx, A.y - fy, A.z - fz};
                 float b[3] = {B.x - fx, B.y - fy, B.z - fz};
+                {
+                    // squared distance from the voxel centre to the axis, minus r^2
+                    const float e[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+                    const float w[3] = {0.5f - a[0], 0.5f - a[1], 0.5f - a[2]};
+                    const float ee = (e[0] * e[0] + e[1] * e[1]) + e[2] * e[2];
+                    float tt = ee > 0.0f ? ((w[0] * e[0] + w[1] * e[1]) + w[2] * e[2]) / ee : 0.0f;
+                    tt = fminf(fmaxf(tt, 0.0f), 1.0f);
+                    const float dx = w[0] - tt * e[0], dy = w[1] - tt * e[1], dz = w[2] - tt * e[2];
+                    const float v = ((dx * dx + dy * dy) + dz * dz) - A.w * A.w;
+                    uint32_t bits = __float_as_uint(v);
+                    bits ^= (bits >> 31) ? 0xffffffffu : 0x80000000u;   // order-preserving as unsigned
+                    okey = (min(bits, 0xffffffbfu) & 0xffffffe0u) | (uint32_t)lane;   // below the empty lanes
+                }
                 float mu = capsule_measure(a, b, A.w);
                 float dg[3] = {B.x - A.x, B.y - A.y, B.z - A.z};
                 float dn = sqrtf((dg[0] * dg[0] + dg[1] * dg[1]) + dg[2] * dg[2]);
@@ -822,9 +839,19 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
             // additions as a single running sum per component)
             if (lane < 7)
                 for (uint32_t j = 0; j < cnt; ++j) accc = accc + ct.q[j * 7 + lane];
+            // bitonic sort of the 32 keys over the warp (unique: the lane is the low 5 bits)
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                    const uint32_t other = __shfl_xor_sync(0xffffffffu, okey, jj);
+                    const bool keep_min = ((lane & k) == 0) == ((lane & jj) == 0);
+                    okey = keep_min ? min(okey, other) : max(okey, other);
+                }
+            }
             for (uint32_t j = 0; j < cnt; ++j) {
                 if (!full) {
-                    const uint32_t p = prims[base + j];
+                    const uint32_t p = prims[base + (__shfl_sync(0xffffffffu, okey, (int)j) & 31u)];
                     const float4 A = ra[p], B = rb[p];
                     float a[3] = {A.x - fx, A.y - fy, A.z - fz};
                     float b[3] = {B.x - fx, B.y - fy, B.z - fz};
