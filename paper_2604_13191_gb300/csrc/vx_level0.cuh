@@ -253,6 +253,7 @@ struct CapsuleTasks {
     float cap[CT_CAPS][8];         // a.xyz, b.xyz, r^2
     uint32_t mask[16];             // 512-bit mask, word w = lanes 2w (low half) and 2w+1
     float q[32 * 7];               // w mu and w mu T(t) of up to 32 pairs (pair-major, stride 7)
+    float4 batch[32][2];           // local a.xyz, b.xyz, r^2 of the batch's capsules (by lane)
 };
 
 // Step 3 of every pooled task whose sub-cell is not set yet (warp-collective); returns the
@@ -805,6 +806,8 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                 const float4 A = ra[p], B = rb[p];
                 float a[3] = {A.x - fx, A.y - fy, A.z - fz};
                 float b[3] = {B.x - fx, B.y - fy, B.z - fz};
+                ct.batch[lane][0] = make_float4(a[0], a[1], a[2], b[0]);
+                ct.batch[lane][1] = make_float4(b[1], b[2], A.w * A.w, 0.0f);
                 {
                     // squared distance from the voxel centre to the axis, minus r^2
                     const float e[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
@@ -851,11 +854,11 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
             }
             for (uint32_t j = 0; j < cnt; ++j) {
                 if (!full) {
-                    const uint32_t p = prims[base + (__shfl_sync(0xffffffffu, okey, (int)j) & 31u)];
-                    const float4 A = ra[p], B = rb[p];
-                    float a[3] = {A.x - fx, A.y - fy, A.z - fz};
-                    float b[3] = {B.x - fx, B.y - fy, B.z - fz};
-                    const float rr = A.w * A.w;
+                    const int slot = (int)(__shfl_sync(0xffffffffu, okey, (int)j) & 31u);
+                    const float4 c0 = ct.batch[slot][0], c1 = ct.batch[slot][1];
+                    const float a[3] = {c0.x, c0.y, c0.z};
+                    const float b[3] = {c0.w, c1.x, c1.y};
+                    const float rr = c1.z;
                     uint32_t und;
                     chunk = capsule_steps12(a, b, rr, sy0, sz, chunk, und);
                     // pool the undecided sub-cells as step-3 tasks of this capsule
