@@ -65,7 +65,13 @@ __device__ __forceinline__ float seg_g(const float* a, const float* d, float t, 
 // (Scalar code with explicit selects: no dynamically indexed local arrays.)
 __device__ __forceinline__ float sel3(int i, float x, float y, float z) { return i == 0 ? x : (i == 1 ? y : z); }
 
-__device__ __noinline__ float seg_box_min(const float* a, const float* d, const float* lo, const float* hi) {
+// Called out of line (it is the rare, long case) with scalar arguments, so that nothing of
+// it goes through local memory: the box is [lo, lo + ext] (exact for the voxel [0, 1]^3 and
+// for the sub-cells [k/8, (k+1)/8]).
+__device__ __noinline__ float seg_box_min(float ax, float ay, float az, float dx, float dy, float dz, float lx,
+                                          float ly, float lz, float ext) {
+    const float a[3] = {ax, ay, az}, d[3] = {dx, dy, dz};
+    const float lo[3] = {lx, ly, lz}, hi[3] = {lx + ext, ly + ext, lz + ext};
     float L = -INFINITY, U = INFINITY;
     int iL = -1, jU = -1, moving = 0;
     float plo0 = 0.0f, plo1 = 0.0f, plo2 = 0.0f, phi0 = 0.0f, phi1 = 0.0f, phi2 = 0.0f;
@@ -142,7 +148,7 @@ __device__ __forceinline__ bool capsule_box(const float* a, const float* b, floa
     if (G > rr) return false;
     if (sqdist_point_box(a[0], a[1], a[2], lo, hi) <= rr) return true;
     if (sqdist_point_box(b[0], b[1], b[2], lo, hi) <= rr) return true;
-    return seg_box_min(a, d, lo, hi) <= rr;
+    return seg_box_min(a[0], a[1], a[2], d[0], d[1], d[2], lo[0], lo[1], lo[2], hi[0] - lo[0]) <= rr;
 }
 
 // Per-axis terms of steps 1 and 2 for the sub-cell interval [k/8, (k+1)/8] of one axis.
@@ -272,12 +278,10 @@ __device__ __forceinline__ uint32_t capsule_step3_pool(CapsuleTasks& ct, int nta
         const uint32_t bit = 1u << (id & 31);
         if (ct.mask[id >> 5] & bit) continue;
         const float* c = ct.cap[task >> 9];
-        const float a[3] = {c[0], c[1], c[2]};
-        const float d[3] = {c[3] - c[0], c[4] - c[1], c[5] - c[2]};
         const int sx = id & 7, sy = (id >> 3) & 7, zz = id >> 6;
-        const float lo[3] = {(float)sx * 0.125f, (float)sy * 0.125f, (float)zz * 0.125f};
-        const float hi[3] = {(float)(sx + 1) * 0.125f, (float)(sy + 1) * 0.125f, (float)(zz + 1) * 0.125f};
-        if (seg_box_min(a, d, lo, hi) <= c[6]) atomicOr(&ct.mask[id >> 5], bit);
+        if (seg_box_min(c[0], c[1], c[2], c[3] - c[0], c[4] - c[1], c[5] - c[2], (float)sx * 0.125f,
+                        (float)sy * 0.125f, (float)zz * 0.125f, 0.125f) <= c[6])
+            atomicOr(&ct.mask[id >> 5], bit);
     }
     __syncwarp();
     const uint32_t w = ct.mask[lane >> 1];
