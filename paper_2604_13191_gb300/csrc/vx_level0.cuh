@@ -254,33 +254,98 @@ __device__ __forceinline__ uint32_t capsule_steps12(const float* a, const float*
 // a time, so that the exact minimum (the expensive case) runs with all lanes busy.
 constexpr int CT_TASKS = 512;
 constexpr int CT_CAPS = 32;
+// One capsule in voxel-local grid units: (a.xyz, r^2), (b.xyz, r + eta), (d = b - a, 1 / |d|^2)
+// with eta the margin of capsule_cell_separated.
+struct CapsuleLocal {
+    float4 a_rr, b_reta, d_idd;
+};
 struct CapsuleTasks {
     uint32_t task[CT_TASKS];       // slot << 9 | sub-cell id
-    float cap[CT_CAPS][8];         // a.xyz, b.xyz, r^2
+    CapsuleLocal cap[CT_CAPS];     // capsules of the pooled tasks
     uint32_t mask[16];             // 512-bit mask, word w = lanes 2w (low half) and 2w+1
     float q[32 * 7];               // w mu and w mu T(t) of up to 32 pairs (pair-major, stride 7)
-    float4 batch[32][2];           // local a.xyz, b.xyz, r^2 of the batch's capsules (by lane)
+    CapsuleLocal batch[32];        // the batch's capsules (by lane)
 };
+
+// Local capsule of endpoints a, b (voxel-local grid units) and radius r.  eta bounds, with
+// a wide factor, the FP32 error of the separation test below plus that of step 3: both
+// scale with the magnitude M of the local coordinates (and r), and sum to less than
+// 3e-6 (M + r + 3).
+__device__ __forceinline__ CapsuleLocal capsule_local(const float* a, const float* b, float r) {
+    const float d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const float dd = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+    const float M = fmaxf(fmaxf(fmaxf(fabsf(a[0]), fabsf(a[1])), fmaxf(fabsf(a[2]), fabsf(b[0]))),
+                          fmaxf(fabsf(b[1]), fabsf(b[2])));
+    const float eta = 2e-5f * ((M + r) + 3.0f);
+    CapsuleLocal c;
+    c.a_rr = make_float4(a[0], a[1], a[2], r * r);
+    c.b_reta = make_float4(b[0], b[1], b[2], r + eta);
+    c.d_idd = make_float4(d[0], d[1], d[2], dd > 0.0f ? 1.0f / dd : 0.0f);
+    return c;
+}
+
+// True when segment a-b is farther than r from sub-cell `id` by a margin that makes step 3
+// reject it too.  For a unit n, the distance between two convex sets is at least their
+// separation along n: here min(n.(a - c), n.(b - c)) - h |n|_1 for the sub-cell of centre c
+// and half-size h = 1/16.  n is taken along v = p - c, p the point of the segment nearest
+// to c (any v gives a bound; this one is nearly tight once the sub-cell is a few sub-cells
+// away).  The test s > (r + eta) |v|, s the separation times |v|, is done in squares.
+// Step 3's FP32 value is the squared distance of a point within ~1e-6 (M + 1) of the
+// segment, to relative 1e-6, so a sub-cell separated by more than r + eta has that value
+// above r^2: the task can be dropped without changing the mask.
+__device__ __forceinline__ bool capsule_cell_separated(const CapsuleLocal& c, int id) {
+    const float cx = (float)(id & 7) * 0.125f + 0.0625f;
+    const float cy = (float)((id >> 3) & 7) * 0.125f + 0.0625f;
+    const float cz = (float)(id >> 6) * 0.125f + 0.0625f;
+    const float Ax = c.a_rr.x - cx, Ay = c.a_rr.y - cy, Az = c.a_rr.z - cz;
+    const float Bx = c.b_reta.x - cx, By = c.b_reta.y - cy, Bz = c.b_reta.z - cz;
+    float tc = -((Ax * c.d_idd.x + Ay * c.d_idd.y) + Az * c.d_idd.z) * c.d_idd.w;
+    tc = fminf(fmaxf(tc, 0.0f), 1.0f);
+    const float vx = Ax + tc * c.d_idd.x, vy = Ay + tc * c.d_idd.y, vz = Az + tc * c.d_idd.z;
+    const float sa = (vx * Ax + vy * Ay) + vz * Az;
+    const float sb = (vx * Bx + vy * By) + vz * Bz;
+    const float sep = fminf(sa, sb) - 0.0625f * ((fabsf(vx) + fabsf(vy)) + fabsf(vz));
+    const float vv = (vx * vx + vy * vy) + vz * vz;
+    const float re = c.b_reta.w;
+    return sep > 0.0f && sep * sep > (re * re) * vv;
+}
 
 // Step 3 of every pooled task whose sub-cell is not set yet (warp-collective); returns the
 // lane's 16 bits of the updated mask.  A task skipped because an earlier task of the same
 // sub-cell set it would have returned a bit that is already 1, so the order of evaluation
-// does not change the mask.
+// does not change the mask.  Tasks whose sub-cell is separated from the capsule are dropped
+// first (compacting the rest in place), so that the exact minimum runs on full warps.
 __device__ __forceinline__ uint32_t capsule_step3_pool(CapsuleTasks& ct, int ntask, uint32_t chunk) {
     const int lane = threadIdx.x & 31;
     const uint32_t lo16 = __shfl_sync(0xffffffffu, chunk, (2 * lane) & 31);
     const uint32_t hi16 = __shfl_sync(0xffffffffu, chunk, (2 * lane + 1) & 31);
     if (lane < 16) ct.mask[lane] = lo16 | (hi16 << 16);
     __syncwarp();
-    for (int t = lane; t < ntask; t += 32) {
+    int nkeep = 0;
+    for (int t0 = 0; t0 < ntask; t0 += 32) {
+        const int t = t0 + lane;
+        uint32_t task = 0;
+        bool keep = false;
+        if (t < ntask) {
+            task = ct.task[t];
+            const int id = (int)(task & 511u);
+            keep = !(ct.mask[id >> 5] & (1u << (id & 31))) && !capsule_cell_separated(ct.cap[task >> 9], id);
+        }
+        const uint32_t kept = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();   // the chunk is read before any lane writes (writes land at or below it)
+        if (keep) ct.task[nkeep + __popc(kept & ((1u << lane) - 1u))] = task;
+        nkeep += __popc(kept);
+    }
+    __syncwarp();
+    for (int t = lane; t < nkeep; t += 32) {
         const uint32_t task = ct.task[t];
         const int id = (int)(task & 511u);
         const uint32_t bit = 1u << (id & 31);
         if (ct.mask[id >> 5] & bit) continue;
-        const float* c = ct.cap[task >> 9];
+        const CapsuleLocal& c = ct.cap[task >> 9];
         const int sx = id & 7, sy = (id >> 3) & 7, zz = id >> 6;
-        if (seg_box_min(c[0], c[1], c[2], c[3] - c[0], c[4] - c[1], c[5] - c[2], (float)sx * 0.125f,
-                        (float)sy * 0.125f, (float)zz * 0.125f, 0.125f) <= c[6])
+        if (seg_box_min(c.a_rr.x, c.a_rr.y, c.a_rr.z, c.d_idd.x, c.d_idd.y, c.d_idd.z, (float)sx * 0.125f,
+                        (float)sy * 0.125f, (float)zz * 0.125f, 0.125f) <= c.a_rr.w)
             atomicOr(&ct.mask[id >> 5], bit);
     }
     __syncwarp();
@@ -810,8 +875,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                 const float4 A = ra[p], B = rb[p];
                 float a[3] = {A.x - fx, A.y - fy, A.z - fz};
                 float b[3] = {B.x - fx, B.y - fy, B.z - fz};
-                ct.batch[lane][0] = make_float4(a[0], a[1], a[2], b[0]);
-                ct.batch[lane][1] = make_float4(b[1], b[2], A.w * A.w, 0.0f);
+                ct.batch[lane] = capsule_local(a, b, A.w);
                 {
                     // squared distance from the voxel centre to the axis, minus r^2
                     const float e[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
@@ -859,10 +923,10 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
             for (uint32_t j = 0; j < cnt; ++j) {
                 if (!full) {
                     const int slot = (int)(__shfl_sync(0xffffffffu, okey, (int)j) & 31u);
-                    const float4 c0 = ct.batch[slot][0], c1 = ct.batch[slot][1];
+                    const float4 c0 = ct.batch[slot].a_rr, c1 = ct.batch[slot].b_reta;
                     const float a[3] = {c0.x, c0.y, c0.z};
-                    const float b[3] = {c0.w, c1.x, c1.y};
-                    const float rr = c1.z;
+                    const float b[3] = {c1.x, c1.y, c1.z};
+                    const float rr = c0.w;
                     uint32_t und;
                     chunk = capsule_steps12(a, b, rr, sy0, sz, chunk, und);
                     // pool the undecided sub-cells as step-3 tasks of this capsule
@@ -880,14 +944,9 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                             ntask = 0;
                             ncap = 0;
                         }
-                        float cv = rr;
-                        cv = lane == 0 ? a[0] : cv;
-                        cv = lane == 1 ? a[1] : cv;
-                        cv = lane == 2 ? a[2] : cv;
-                        cv = lane == 3 ? b[0] : cv;
-                        cv = lane == 4 ? b[1] : cv;
-                        cv = lane == 5 ? b[2] : cv;
-                        if (lane < 7) ct.cap[ncap][lane] = cv;
+                        if (lane < 12)
+                            reinterpret_cast<float*>(&ct.cap[ncap])[lane] =
+                                reinterpret_cast<const float*>(&ct.batch[slot])[lane];
                         uint32_t pos = (uint32_t)ntask + off - n;
                         uint32_t u = und;
                         while (u) {
