@@ -135,6 +135,64 @@ def test_random_fibers(ctx, dirs5000, seed, R, rad, pts):
         compare_level(g, r, f"seed {seed} level {lvl}", mu_max=prim_measure_max(w))
 
 
+def _seg_box_dist(a, b, lo, hi):
+    """FP64 distance from segment a-b to box [lo, hi] (ternary search of a convex function)."""
+    def g(t):
+        p = a + t * (b - a)
+        e = np.maximum(np.maximum(lo - p, p - hi), 0.0)
+        return float(e @ e)
+    l, h = 0.0, 1.0
+    for _ in range(200):
+        m1, m2 = l + (h - l) / 3, h - (h - l) / 3
+        if g(m1) <= g(m2):
+            h = m2
+        else:
+            l = m1
+    return np.sqrt(g(0.5 * (l + h)))
+
+
+def test_grazing_capsules(ctx):
+    """Capsules whose radius is within a relative 3e-4 of the distance from their axis to
+    one sub-cell, whose nearest point lies inside the segment (so steps 1-2 leave it to the
+    exact minimum): the sub-cell decision sits at the edge of step 3 and inside the
+    margin of the separation test that drops step-3 work.  One capsule per 8^3 block of a
+    64^3 grid, so that no other capsule can set the grazed sub-cells."""
+    R = 64
+    grid = synth.Grid((0.0, 0.0, 0.0), 1.0 / R, R)
+    rng = np.random.default_rng(17)
+    eps = [-3e-4, -1e-4, -3e-5, -1e-5, -3e-6, -1e-6, -3e-7, -1e-7, 0.0, 1e-7, 3e-7, 1e-6, 3e-6, 1e-5, 3e-5,
+           1e-4, 3e-4]
+    ctrl = []
+    n = 0
+    for bx in range(8):
+        for by in range(8):
+            for bz in range(8):
+                base = np.array([bx, by, bz], np.float64) * 8 + 2.0
+                # a segment crossing the block's middle voxel, a target sub-cell beside its middle
+                d = rng.normal(size=3)
+                d /= np.linalg.norm(d)
+                L = rng.uniform(0.5, 3.0)
+                m = base + 2.0 + rng.uniform(-0.3, 0.3, 3)
+                a = np.float32(m - 0.5 * L * d).astype(np.float64)
+                b = np.float32(m + 0.5 * L * d).astype(np.float64)
+                side = np.cross(d, rng.normal(size=3))
+                side /= np.linalg.norm(side)
+                q = 0.5 * (a + b) + side * rng.uniform(0.3, 1.2)
+                lo = np.floor(q * 8) / 8
+                D = _seg_box_dist(a, b, lo, lo + 0.125)
+                if D < 0.05:
+                    continue
+                r = np.float32(D * (1.0 + eps[n % len(eps)]) / R)
+                n += 1
+                ctrl += [[*(a / R), r], [*(b / R), r]]
+    ctrl = np.array(ctrl, np.float32)
+    off = np.arange(0, ctrl.shape[0] + 1, 2, dtype=np.int64)
+    w = synth.Workload("graze", "fibers", grid, ctrl=ctrl, fiber_offsets=off, K=1)
+    got = run_gpu(ctx, w, lod=False)
+    compare_level(got[0], oracle.voxelize(w), "grazing", lobes=False, mu_max=prim_measure_max(w))
+    assert n > 400
+
+
 @pytest.mark.parametrize("seed,R,size", [(1, 16, (0.2, 3.0)), (2, 32, (0.05, 0.5)), (3, 64, (2.0, 12.0))])
 def test_random_triangles(ctx, dirs5000, seed, R, size):
     tris, grid = synth.random_triangles(60, R, seed=seed, size=size)
