@@ -80,6 +80,9 @@ static int popcount64(uint64_t v) { int c = 0; while (v) { v &= v - 1; ++c; } re
 /*   2. an endpoint within r of the box                                      */
 /*   3. min over t in [0,1] of squared distance from a + t d to the box,     */
 /*      evaluated at the stationary points of the active quadratic pieces.   */
+/* Steps 1 and 2 compare the x term with what r^2 leaves after the y and z   */
+/* terms, x^2 <= r^2 - (y^2 + z^2): the same inequality as the sum of the    */
+/* three squares <= r^2, in the FP32 form in which the kernels evaluate it.  */
 /* ------------------------------------------------------------------------- */
 static float box_sqdist_point(const float* p, const float* lo, const float* hi) {
     float e[3];
@@ -99,6 +102,17 @@ static float seg_box_g(const float* a, const float* d, float t, const float* lo,
     return box_sqdist_point(p, lo, hi);
 }
 
+/* squared distance from p to the box, compared with rr in the form x^2 <= rr - (y^2 + z^2) */
+static int box_point_within(const float* p, const float* lo, const float* hi, float rr) {
+    float e[3];
+    for (int i = 0; i < 3; ++i) {
+        if (p[i] < lo[i]) e[i] = lo[i] - p[i];
+        else if (p[i] > hi[i]) e[i] = p[i] - hi[i];
+        else e[i] = 0.0f;
+    }
+    return e[0] * e[0] <= rr - (e[1] * e[1] + e[2] * e[2]);
+}
+
 ORC_API int vxo_capsule_box(const float* a, const float* b, float rr, const float* lo, const float* hi) {
     float d[3];
     for (int i = 0; i < 3; ++i) d[i] = b[i] - a[i];
@@ -110,11 +124,10 @@ ORC_API int vxo_capsule_box(const float* a, const float* b, float rr, const floa
         else if (mn > hi[i]) g[i] = mn - hi[i];
         else g[i] = 0.0f;
     }
-    float G = (g[0] * g[0] + g[1] * g[1]) + g[2] * g[2];
-    if (G > rr) return 0;
+    if (g[0] * g[0] > rr - (g[1] * g[1] + g[2] * g[2])) return 0;
     /* step 2 */
-    if (box_sqdist_point(a, lo, hi) <= rr) return 1;
-    if (box_sqdist_point(b, lo, hi) <= rr) return 1;
+    if (box_point_within(a, lo, hi, rr)) return 1;
+    if (box_point_within(b, lo, hi, rr)) return 1;
     /* step 3 */
     float L = -INFINITY, U = INFINITY;
     int iL = -1, jU = -1, moving = 0;

@@ -193,27 +193,74 @@ __device__ __forceinline__ AxisBound axis_bound(float a, float b, float lo, floa
     return r;
 }
 
+// Per-warp pool of step-3 work of one voxel: (capsule slot, sub-cell) tasks left undecided
+// by steps 1-2 of the batch's capsules, those capsules, and the voxel's mask while the pool
+// is evaluated.  Tasks of many capsules are evaluated 32 at a time, so that the exact
+// minimum (the expensive case) runs with all lanes busy.
+constexpr int CT_TASKS = 512;
+// One capsule in voxel-local grid units: (a.xyz, r^2), (b.xyz, r + eta), (d = b - a, 1 / |d|^2)
+// with eta the margin of capsule_cell_separated.
+struct CapsuleLocal {
+    float4 a_rr, b_reta, d_idd;
+};
+// The x-axis terms of steps 1-2 for the 8 sub-cell columns sx = 0..7 (the same for every
+// lane): squared gap of the segment's extent, squared distances of the endpoints.
+struct CapsuleX {
+    float4 g2[2], ea2[2], eb2[2];
+};
+struct CapsuleTasks {
+    uint16_t task[CT_TASKS];       // batch slot << 9 | sub-cell id
+    uint32_t mask[16];             // 512-bit mask, word w = lanes 2w (low half) and 2w+1
+    float q[32 * 7];               // w mu and w mu T(t) of up to 32 pairs (pair-major, stride 7)
+    CapsuleLocal batch[32];        // the batch's capsules (by lane)
+    CapsuleX xt[32];               // their x-axis terms
+};
+
+__device__ __forceinline__ CapsuleX capsule_x(float a, float b) {
+    float g[8], ea[8], eb[8];
+#pragma unroll
+    for (int sx = 0; sx < 8; ++sx) {
+        const AxisTerms t = axis_terms(a, b, sx);
+        g[sx] = t.g2;
+        ea[sx] = t.ea2;
+        eb[sx] = t.eb2;
+    }
+    CapsuleX x;
+    x.g2[0] = make_float4(g[0], g[1], g[2], g[3]);
+    x.g2[1] = make_float4(g[4], g[5], g[6], g[7]);
+    x.ea2[0] = make_float4(ea[0], ea[1], ea[2], ea[3]);
+    x.ea2[1] = make_float4(ea[4], ea[5], ea[6], ea[7]);
+    x.eb2[0] = make_float4(eb[0], eb[1], eb[2], eb[3]);
+    x.eb2[1] = make_float4(eb[4], eb[5], eb[6], eb[7]);
+    return x;
+}
+
 // Steps 1-2 of the capsule test for the 16 sub-cells of one lane (sx = 0..7,
 // sy = sy0 + (0|1), sz); bit b = sx + 8 (sy - sy0), so lane L holds bits 16L .. 16L+15 of
 // the voxel's 512-bit mask (bit id sx + 8 sy + 64 sz).  Bits already set in `have` are
 // skipped (OR is idempotent).  Returns `have` plus the bits step 1-2 decide set; `und`
 // receives the sub-cells left for step 3.
-// A group of sub-cells (the lane's 16, or one row of 8) is decided at once when
-//   the sum of its per-axis gap bounds > r^2   -> every sub-cell fails step 1 (bits 0), or
-//   the sum of an endpoint's far bounds <= r^2 -> every sub-cell passes step 2 (bits 1)
-// (each sub-cell's step-1 sum is >= the group's and <= its step-2 sum, so the group result
-// equals the per-sub-cell definition bit for bit).
-__device__ __forceinline__ uint32_t capsule_steps12(const float* a, const float* b, float rr, int sy0, int sz,
+// Both steps compare the x term with what r^2 leaves after the y and z terms:
+//   step 1 fails  when  g_x^2 > r^2 - (g_y^2 + g_z^2),
+//   step 2 passes when  e_x^2 <= r^2 - (e_y^2 + e_z^2)  for endpoint a or b,
+// so a row's 8 sub-cells compare 8 x terms with one budget each.
+// A group of sub-cells (the lane's 16, or one row of 8) is decided at once when its per-axis
+// gap bounds fail step 1, or an endpoint's far bounds pass step 2: FP addition and
+// subtraction are monotone, so every sub-cell inside then fails (passes) too, and the group
+// result equals the per-sub-cell definition bit for bit.
+__device__ __forceinline__ uint32_t capsule_steps12(const CapsuleLocal& c, const CapsuleX& X, int sy0, int sz,
                                                     uint32_t have, uint32_t& und) {
     uint32_t bits = have;
     und = 0;
     if (have == 0xffffu) return bits;
+    const float a[3] = {c.a_rr.x, c.a_rr.y, c.a_rr.z}, b[3] = {c.b_reta.x, c.b_reta.y, c.b_reta.z};
+    const float rr = c.a_rr.w;
     const float zlo = (float)sz * 0.125f, zhi = (float)(sz + 1) * 0.125f;
     const AxisBound bz = axis_bound(a[2], b[2], zlo, zhi);
     const AxisBound bx = axis_bound(a[0], b[0], 0.0f, 1.0f);
     const AxisBound bb = axis_bound(a[1], b[1], (float)sy0 * 0.125f, (float)(sy0 + 2) * 0.125f);
-    if ((bx.g2 + bb.g2) + bz.g2 > rr) return bits;                       // all 16 fail step 1
-    if ((bx.fa2 + bb.fa2) + bz.fa2 <= rr || (bx.fb2 + bb.fb2) + bz.fb2 <= rr) return 0xffffu;
+    if (bx.g2 > rr - (bb.g2 + bz.g2)) return bits;                       // all 16 fail step 1
+    if (bx.fa2 <= rr - (bb.fa2 + bz.fa2) || bx.fb2 <= rr - (bb.fb2 + bz.fb2)) return 0xffffu;
     const AxisTerms tz = axis_terms(a[2], b[2], sz);
 #pragma unroll
     for (int yi = 0; yi < 2; ++yi) {
@@ -221,25 +268,28 @@ __device__ __forceinline__ uint32_t capsule_steps12(const float* a, const float*
         if ((bits & rowmask) == rowmask) continue;
         const float ylo = (float)(sy0 + yi) * 0.125f, yhi = (float)(sy0 + yi + 1) * 0.125f;
         const AxisBound by = axis_bound(a[1], b[1], ylo, yhi);
-        if ((bx.g2 + by.g2) + bz.g2 > rr) continue;
-        if ((bx.fa2 + by.fa2) + bz.fa2 <= rr || (bx.fb2 + by.fb2) + bz.fb2 <= rr) {
+        if (bx.g2 > rr - (by.g2 + bz.g2)) continue;
+        if (bx.fa2 <= rr - (by.fa2 + bz.fa2) || bx.fb2 <= rr - (by.fb2 + bz.fb2)) {
             bits |= rowmask;
             continue;
         }
         const AxisTerms ty = axis_terms(a[1], b[1], sy0 + yi);
+        const float TG = rr - (ty.g2 + tz.g2);
+        const float TA = rr - (ty.ea2 + tz.ea2);
+        const float TB = rr - (ty.eb2 + tz.eb2);
+        const float4 g0 = X.g2[0], g1 = X.g2[1], a0 = X.ea2[0], a1 = X.ea2[1], b0 = X.eb2[0], b1 = X.eb2[1];
+        const float xg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+        const float xa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float xb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
         // per sub-cell: set when an endpoint passes step 2, open (step 3) when it passes
-        // step 1 only.  EA, EB >= G (an endpoint is no closer to a sub-cell than the
-        // segment's extent, and FP addition is monotone), so min(EA, EB) <= r^2 implies
-        // G <= r^2; bits set before are dropped from `und` at the end.
+        // step 1 only.  e >= g on every axis (an endpoint is no closer to a sub-cell than the
+        // segment's extent) and the operations are monotone, so a set sub-cell is open too;
+        // bits set before are dropped from `und` at the end.
         uint32_t row_set = 0, row_open = 0;
 #pragma unroll
         for (int sx = 0; sx < 8; ++sx) {
-            const AxisTerms tx = axis_terms(a[0], b[0], sx);
-            const float G = (tx.g2 + ty.g2) + tz.g2;
-            const float EA = (tx.ea2 + ty.ea2) + tz.ea2;
-            const float EB = (tx.eb2 + ty.eb2) + tz.eb2;
-            row_set |= (fminf(EA, EB) <= rr ? 1u : 0u) << sx;
-            row_open |= (G <= rr ? 1u : 0u) << sx;
+            row_set |= ((xa[sx] <= TA) || (xb[sx] <= TB) ? 1u : 0u) << sx;
+            row_open |= (xg[sx] <= TG ? 1u : 0u) << sx;
         }
         bits |= row_set << (8 * yi);
         und |= row_open << (8 * yi);
@@ -247,25 +297,6 @@ __device__ __forceinline__ uint32_t capsule_steps12(const float* a, const float*
     und &= ~bits;
     return bits;
 }
-
-// Per-warp pool of step-3 work of one voxel: (capsule slot, sub-cell) tasks left undecided
-// by steps 1-2 of the voxel's capsules, the local endpoints and r^2 of those capsules, and
-// the voxel's mask while the pool is evaluated.  Tasks of many capsules are evaluated 32 at
-// a time, so that the exact minimum (the expensive case) runs with all lanes busy.
-constexpr int CT_TASKS = 512;
-constexpr int CT_CAPS = 32;
-// One capsule in voxel-local grid units: (a.xyz, r^2), (b.xyz, r + eta), (d = b - a, 1 / |d|^2)
-// with eta the margin of capsule_cell_separated.
-struct CapsuleLocal {
-    float4 a_rr, b_reta, d_idd;
-};
-struct CapsuleTasks {
-    uint32_t task[CT_TASKS];       // slot << 9 | sub-cell id
-    CapsuleLocal cap[CT_CAPS];     // capsules of the pooled tasks
-    uint32_t mask[16];             // 512-bit mask, word w = lanes 2w (low half) and 2w+1
-    float q[32 * 7];               // w mu and w mu T(t) of up to 32 pairs (pair-major, stride 7)
-    CapsuleLocal batch[32];        // the batch's capsules (by lane)
-};
 
 // Local capsule of endpoints a, b (voxel-local grid units) and radius r.  eta bounds, with
 // a wide factor, the FP32 error of the separation test below plus that of step 3: both
@@ -329,11 +360,11 @@ __device__ __forceinline__ uint32_t capsule_step3_pool(CapsuleTasks& ct, int nta
         if (t < ntask) {
             task = ct.task[t];
             const int id = (int)(task & 511u);
-            keep = !(ct.mask[id >> 5] & (1u << (id & 31))) && !capsule_cell_separated(ct.cap[task >> 9], id);
+            keep = !(ct.mask[id >> 5] & (1u << (id & 31))) && !capsule_cell_separated(ct.batch[task >> 9], id);
         }
         const uint32_t kept = __ballot_sync(0xffffffffu, keep);
         __syncwarp();   // the chunk is read before any lane writes (writes land at or below it)
-        if (keep) ct.task[nkeep + __popc(kept & ((1u << lane) - 1u))] = task;
+        if (keep) ct.task[nkeep + __popc(kept & ((1u << lane) - 1u))] = (uint16_t)task;
         nkeep += __popc(kept);
     }
     __syncwarp();
@@ -342,7 +373,7 @@ __device__ __forceinline__ uint32_t capsule_step3_pool(CapsuleTasks& ct, int nta
         const int id = (int)(task & 511u);
         const uint32_t bit = 1u << (id & 31);
         if (ct.mask[id >> 5] & bit) continue;
-        const CapsuleLocal& c = ct.cap[task >> 9];
+        const CapsuleLocal& c = ct.batch[task >> 9];
         const int sx = id & 7, sy = (id >> 3) & 7, zz = id >> 6;
         if (seg_box_min(c.a_rr.x, c.a_rr.y, c.a_rr.z, c.d_idd.x, c.d_idd.y, c.d_idd.z, (float)sx * 0.125f,
                         (float)sy * 0.125f, (float)zz * 0.125f, 0.125f) <= c.a_rr.w)
@@ -860,7 +891,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                     fz = (float)((int)vx_compact1by2(key >> 2) + bz);
         uint32_t chunk = 0;
         bool full = false;
-        int ntask = 0, ncap = 0;
+        int ntask = 0;
         float accc = 0.0f;   // lane c < 7: component c of the mass / moment sums
         for (uint32_t base = beg; base < end; base += 32) {
             const uint32_t cnt = min(32u, end - base);
@@ -876,6 +907,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                 float a[3] = {A.x - fx, A.y - fy, A.z - fz};
                 float b[3] = {B.x - fx, B.y - fy, B.z - fz};
                 ct.batch[lane] = capsule_local(a, b, A.w);
+                ct.xt[lane] = capsule_x(a[0], b[0]);
                 {
                     // squared distance from the voxel centre to the axis, minus r^2
                     const float e[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
@@ -923,12 +955,8 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
             for (uint32_t j = 0; j < cnt; ++j) {
                 if (!full) {
                     const int slot = (int)(__shfl_sync(0xffffffffu, okey, (int)j) & 31u);
-                    const float4 c0 = ct.batch[slot].a_rr, c1 = ct.batch[slot].b_reta;
-                    const float a[3] = {c0.x, c0.y, c0.z};
-                    const float b[3] = {c1.x, c1.y, c1.z};
-                    const float rr = c0.w;
                     uint32_t und;
-                    chunk = capsule_steps12(a, b, rr, sy0, sz, chunk, und);
+                    chunk = capsule_steps12(ct.batch[slot], ct.xt[slot], sy0, sz, chunk, und);
                     // pool the undecided sub-cells as step-3 tasks of this capsule
                     const uint32_t n = __popc(und);
                     uint32_t off = n;
@@ -939,30 +967,27 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                     }
                     const int total = (int)__shfl_sync(0xffffffffu, off, 31);
                     if (total > 0) {
-                        if (ntask + total > CT_TASKS || ncap == CT_CAPS) {
+                        if (ntask + total > CT_TASKS) {
                             chunk = capsule_step3_pool(ct, ntask, chunk);
                             ntask = 0;
-                            ncap = 0;
                         }
-                        if (lane < 12)
-                            reinterpret_cast<float*>(&ct.cap[ncap])[lane] =
-                                reinterpret_cast<const float*>(&ct.batch[slot])[lane];
                         uint32_t pos = (uint32_t)ntask + off - n;
                         uint32_t u = und;
                         while (u) {
                             const int bpos = __ffs(u) - 1;
                             u &= u - 1;
-                            ct.task[pos++] = ((uint32_t)ncap << 9) | (uint32_t)(16 * lane + bpos);
+                            ct.task[pos++] = (uint16_t)((slot << 9) | (16 * lane + bpos));
                         }
                         ntask += total;
-                        ++ncap;
                         __syncwarp();
                     }
                     full = __all_sync(0xffffffffu, chunk == 0xffffu);
                 }
             }
+            // the tasks refer to this batch's capsules: evaluate them before the next batch
+            if (ntask > 0 && !full) chunk = capsule_step3_pool(ct, ntask, chunk);
+            ntask = 0;
         }
-        if (ntask > 0) chunk = capsule_step3_pool(ct, ntask, chunk);
         write_seg7(out, seg, key, chunk, accc);
     }
 }
