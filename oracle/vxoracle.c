@@ -787,11 +787,12 @@ ORC_API void vxo_sqrtm3(const float* S, float* Rm) {
 }
 
 /* Histogram + empirical second moment of the N directions drawn from a lobe S.
- * omega_k = normalize(S'^(1/2) u_k), S' = S + 1e-6 tr(S) I, u_k the fixed direction set.
+ * omega_k = normalize(S'^(1/2) u_k), S' = S + 1e-6 tr(S) I, u_k the fixed direction set;
+ * the product S'^(1/2) u_k row by row as fmaf(R2, u2, fmaf(R1, u1, R0 u0)).
  * Histogram (5 bins per axis over [-1,1], omega and -omega both counted): stored as
  * hist[a] = #(omega_a^2 >= 0.36 |v|^2), hist[3+a] = #(omega_a^2 >= 0.04 |v|^2).
- * Second moment: each product omega_a omega_b rounded to the 2^-20 grid, summed exactly
- * in integers, divided by N. */
+ * Second moment: each product omega_a omega_b (= v_a v_b / |v|^2) rounded once to the
+ * 2^-20 grid, summed exactly in integers, divided by N. */
 ORC_API void vxo_sample_lobe(const float* S, const float* dirs, int N, int32_t* hist, float* Mhat) {
     float tr = (S[0] + S[1]) + S[2];
     float eps = 1e-6f * tr;
@@ -804,7 +805,7 @@ ORC_API void vxo_sample_lobe(const float* S, const float* dirs, int N, int32_t* 
     for (int k = 0; k < N; ++k) {
         const float* u = dirs + 3 * k;
         float v[3];
-        for (int i = 0; i < 3; ++i) v[i] = (Rm[3 * i] * u[0] + Rm[3 * i + 1] * u[1]) + Rm[3 * i + 2] * u[2];
+        for (int i = 0; i < 3; ++i) v[i] = fmaf(Rm[3 * i + 2], u[2], fmaf(Rm[3 * i + 1], u[1], Rm[3 * i] * u[0]));
         float n2 = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
         if (!(n2 > 0.0f)) continue;
         ++cnt;
@@ -818,8 +819,9 @@ ORC_API void vxo_sample_lobe(const float* S, const float* dirs, int N, int32_t* 
         float s20 = inv * 1048576.0f;
         static const int AB[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
         for (int c = 0; c < 6; ++c) {
-            float x = (v[AB[c][0]] * v[AB[c][1]]) * s20;
-            Q[c] += (int64_t)nearbyintf(x);
+            float p = v[AB[c][0]] * v[AB[c][1]];
+            /* the product p * s20 is exact in FP64 (24 + 24 bits); rounded once, half to even */
+            Q[c] += (int64_t)nearbyint((double)p * (double)s20);
         }
     }
     for (int c = 0; c < 6; ++c) hist[c] = h[c];

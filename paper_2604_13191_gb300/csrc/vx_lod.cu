@@ -11,9 +11,10 @@
 //
 // SGGX-H arithmetic: every lobe S is sampled with the N given unit directions u_k as
 // omega_k = normalize(S'^(1/2) u_k), S' = S + 1e-6 tr(S) I, S'^(1/2) by cyclic Jacobi
-// (FP32, 6 sweeps).  Histograms are integer counts; the sample second moment sums the
-// products omega_a omega_b rounded to the 2^-20 grid in integers.  Both are therefore
-// independent of the order in which the warp visits the samples.
+// (FP32, 6 sweeps); S'^(1/2) u_k is taken with fused multiply-adds.  Histograms are integer
+// counts; the sample second moment sums the products omega_a omega_b, each rounded once to
+// the 2^-20 grid, in integers.  Both are therefore independent of the order in which the
+// warp visits the samples.
 #include <math.h>
 
 #include <algorithm>
@@ -263,10 +264,11 @@ __device__ void sqrtm3(const float* S, float* Rm) {
 }
 
 
-// round-half-even to an integer for |x| < 2^22: adding 1.5 * 2^23 leaves the rounded
-// integer in the low mantissa bits (same value as __float2int_rn, at FP32-add cost)
-__device__ __forceinline__ int rint_small(float x) {
-    return __float_as_int(x + 12582912.0f) - 0x4B400000;
+// round-half-even of the exact product x * s to an integer, for |x s| < 2^22: the fused
+// x * s + 1.5 * 2^23 is rounded once, in a binade whose spacing is 1, so the integer lands
+// in the low mantissa bits (1.5 * 2^23 is even, so ties go to the even integer)
+__device__ __forceinline__ int rint_prod(float x, float s) {
+    return __float_as_int(__fmaf_rn(x, s, 12582912.0f)) - 0x4B400000;
 }
 
 // Histogram and sample second moment of lobe S, computed cooperatively by G warps
@@ -302,7 +304,7 @@ __device__ LobeOwn sample_lobe(const float* S, const float4* __restrict__ dirs, 
             const float u0 = u4.x, u1 = u4.y, u2 = u4.z;
             float v[3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) v[i] = (Rm[3 * i] * u0 + Rm[3 * i + 1] * u1) + Rm[3 * i + 2] * u2;
+            for (int i = 0; i < 3; ++i) v[i] = __fmaf_rn(Rm[3 * i + 2], u2, __fmaf_rn(Rm[3 * i + 1], u1, Rm[3 * i] * u0));
             const float c0 = v[0] * v[0], c1 = v[1] * v[1], c2 = v[2] * v[2];
             const float n2 = (c0 + c1) + c2;
             if (!(n2 > 0.0f)) continue;
@@ -316,12 +318,12 @@ __device__ LobeOwn sample_lobe(const float* S, const float4* __restrict__ dirs, 
             h[5] += (c2 >= t2) ? 1 : 0;
             const float inv = 1.0f / n2;
             const float s20 = inv * 1048576.0f;
-            q[0] += rint_small(c0 * s20);
-            q[1] += rint_small(c1 * s20);
-            q[2] += rint_small(c2 * s20);
-            q[3] += rint_small((v[0] * v[1]) * s20);
-            q[4] += rint_small((v[0] * v[2]) * s20);
-            q[5] += rint_small((v[1] * v[2]) * s20);
+            q[0] += rint_prod(c0, s20);
+            q[1] += rint_prod(c1, s20);
+            q[2] += rint_prod(c2, s20);
+            q[3] += rint_prod(v[0] * v[1], s20);
+            q[4] += rint_prod(v[0] * v[2], s20);
+            q[5] += rint_prod(v[1] * v[2], s20);
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c) Q[c] += q[c];
