@@ -906,14 +906,15 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                 const float4 A = ra[p], B = rb[p];
                 float a[3] = {A.x - fx, A.y - fy, A.z - fz};
                 float b[3] = {B.x - fx, B.y - fy, B.z - fz};
-                ct.batch[lane] = capsule_local(a, b, A.w);
+                const CapsuleLocal cl = capsule_local(a, b, A.w);
+                ct.batch[lane] = cl;
                 ct.xt[lane] = capsule_x(a[0], b[0]);
                 {
-                    // squared distance from the voxel centre to the axis, minus r^2
-                    const float e[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+                    // squared distance from the voxel centre to the axis, minus r^2 (an ordering
+                    // key only: any rounding of it leaves the outputs unchanged)
+                    const float e[3] = {cl.d_idd.x, cl.d_idd.y, cl.d_idd.z};
                     const float w[3] = {0.5f - a[0], 0.5f - a[1], 0.5f - a[2]};
-                    const float ee = (e[0] * e[0] + e[1] * e[1]) + e[2] * e[2];
-                    float tt = ee > 0.0f ? ((w[0] * e[0] + w[1] * e[1]) + w[2] * e[2]) / ee : 0.0f;
+                    float tt = ((w[0] * e[0] + w[1] * e[1]) + w[2] * e[2]) * cl.d_idd.w;
                     tt = fminf(fmaxf(tt, 0.0f), 1.0f);
                     const float dx = w[0] - tt * e[0], dy = w[1] - tt * e[1], dz = w[2] - tt * e[2];
                     const float v = ((dx * dx + dy * dy) + dz * dz) - A.w * A.w;

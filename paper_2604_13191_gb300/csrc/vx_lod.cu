@@ -218,8 +218,13 @@ __global__ void k_lod_reduce(LevelIn in, const uint32_t* __restrict__ starts, ui
 // ------------------------------------------------------------------------------------
 // SGGX-H
 // ------------------------------------------------------------------------------------
-// S'^(1/2) of a symmetric 3x3 matrix (packed xx,yy,zz,xy,xz,yz) by cyclic Jacobi
-__device__ void sqrtm3(const float* S, float* Rm) {
+// S'^(1/2) of a symmetric 3x3 matrix (packed xx,yy,zz,xy,xz,yz) by cyclic Jacobi.  Returns
+// true when the square root is well conditioned: smallest singular value above 1e-4 of the
+// largest, and the largest above 1e-15.  S' = S + 1e-6 tr(S) I bounds the ratio below by
+// ~1e-3 for any S with tr(S) > 0; the rounding of the FP32 Jacobi (orthogonality of the
+// rotations, the product R u) is ~1e-6 of the largest value, so for every unit u the FP32
+// v = R u then has |v| > 1e-4 sg_max (1 - 1e-2) and |v|^2 > 0.
+__device__ bool sqrtm3(const float* S, float* Rm) {
     float a[3][3] = {{S[0], S[3], S[4]}, {S[3], S[1], S[5]}, {S[4], S[5], S[2]}};
     float V[3][3] = {{1.0f, 0.0f, 0.0f}, {0.0f, 1.0f, 0.0f}, {0.0f, 0.0f, 1.0f}};
     for (int sweep = 0; sweep < 6; ++sweep) {
@@ -261,6 +266,46 @@ __device__ void sqrtm3(const float* S, float* Rm) {
 #pragma unroll
         for (int j = 0; j < 3; ++j)
             Rm[3 * i + j] = ((V[i][0] * sg[0]) * V[j][0] + (V[i][1] * sg[1]) * V[j][1]) + (V[i][2] * sg[2]) * V[j][2];
+    const float smax = fmaxf(fmaxf(sg[0], sg[1]), sg[2]), smin = fminf(fminf(sg[0], sg[1]), sg[2]);
+    return smax > 1e-15f && smin > 1e-4f * smax;
+}
+
+// a >= b as an integer mask (all ones or zero; zero when either is NaN)
+__device__ __forceinline__ uint32_t ge_mask(float a, float b) {
+    uint32_t m;
+    asm("set.ge.u32.f32 %0, %1, %2;" : "=r"(m) : "f"(a), "f"(b));
+    return m;
+}
+
+// One direction sample of a well-conditioned lobe (|v|^2 > 0): the six histogram masks and
+// the six moment terms as raw FP32 bit patterns (x * 2^20 / |v|^2 + 1.5 * 2^23, rounded once).
+struct SampleTerms {
+    uint32_t m[6];
+    uint32_t x[6];
+};
+__device__ __forceinline__ SampleTerms sample_terms(const float* Rm, float4 u4) {
+    float v[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        v[i] = __fmaf_rn(Rm[3 * i + 2], u4.z, __fmaf_rn(Rm[3 * i + 1], u4.y, Rm[3 * i] * u4.x));
+    const float c0 = v[0] * v[0], c1 = v[1] * v[1], c2 = v[2] * v[2];
+    const float n2 = (c0 + c1) + c2;
+    const float t6 = 0.36f * n2, t2 = 0.04f * n2;
+    SampleTerms r;
+    r.m[0] = ge_mask(c0, t6);
+    r.m[1] = ge_mask(c1, t6);
+    r.m[2] = ge_mask(c2, t6);
+    r.m[3] = ge_mask(c0, t2);
+    r.m[4] = ge_mask(c1, t2);
+    r.m[5] = ge_mask(c2, t2);
+    const float s20 = (1.0f / n2) * 1048576.0f;
+    r.x[0] = __float_as_uint(__fmaf_rn(c0, s20, 12582912.0f));
+    r.x[1] = __float_as_uint(__fmaf_rn(c1, s20, 12582912.0f));
+    r.x[2] = __float_as_uint(__fmaf_rn(c2, s20, 12582912.0f));
+    r.x[3] = __float_as_uint(__fmaf_rn(v[0] * v[1], s20, 12582912.0f));
+    r.x[4] = __float_as_uint(__fmaf_rn(v[0] * v[2], s20, 12582912.0f));
+    r.x[5] = __float_as_uint(__fmaf_rn(v[1] * v[2], s20, 12582912.0f));
+    return r;
 }
 
 
@@ -288,12 +333,42 @@ __device__ LobeOwn sample_lobe(const float* S, const float4* __restrict__ dirs, 
     const float eps = 1e-6f * tr;
     const float Sp[6] = {S[0] + eps, S[1] + eps, S[2] + eps, S[3], S[4], S[5]};
     float Rm[9];
-    sqrtm3(Sp, Rm);
+    const bool wellcond = sqrtm3(Sp, Rm);
     int32_t h[6] = {0, 0, 0, 0, 0, 0};
     long long Q[6] = {0, 0, 0, 0, 0, 0};
     int cnt = 0;
     const int tid = (G == 1) ? (threadIdx.x & 31) : (int)threadIdx.x;
     constexpr int STRIDE = 32 * G;
+    if (wellcond && N <= STRIDE * 1024) {
+        // every sample has |v|^2 > 0: no sample is skipped, so two samples are summed per step
+        // with three-input adds (histogram masks are -1 / 0; each moment term carries the
+        // constant 1.5 * 2^23, removed at the end: the sums wrap modulo 2^32, and the true sum
+        // of at most 1024 terms of magnitude <= 2^20 is recovered exactly)
+        uint32_t q[6] = {0, 0, 0, 0, 0, 0};
+        int k = tid;
+#pragma unroll 1
+        for (; k + STRIDE < N; k += 2 * STRIDE) {
+            const SampleTerms A = sample_terms(Rm, __ldg(dirs + k));
+            const SampleTerms B = sample_terms(Rm, __ldg(dirs + k + STRIDE));
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                h[c] = h[c] - (int32_t)A.m[c] - (int32_t)B.m[c];
+                q[c] = q[c] + A.x[c] + B.x[c];
+            }
+        }
+        if (k < N) {
+            const SampleTerms A = sample_terms(Rm, __ldg(dirs + k));
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                h[c] = h[c] - (int32_t)A.m[c];
+                q[c] = q[c] + A.x[c];
+            }
+        }
+        const uint32_t ns = tid < N ? (uint32_t)((N - 1 - tid) / STRIDE + 1) : 0u;
+        cnt = (int)ns;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) Q[c] = (int32_t)(q[c] - ns * 0x4B400000u);
+    } else
     // per-thread int32 partial sums (|term| <= 2^20), flushed to int64 every 1024 samples
     for (int k0 = tid; k0 < N; k0 += STRIDE * 1024) {
         int32_t q[6] = {0, 0, 0, 0, 0, 0};
@@ -417,7 +492,7 @@ constexpr int CL_BLOCK_WARPS = 8;
 constexpr int CL_WIDE_WARPS = 16;   // levels with at most one parent per SM
 
 template <int G>
-__global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32) k_sggx_cluster(
+__global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32, G == 1 ? 7 : 0) k_sggx_cluster(
     LevelIn in, const uint32_t* __restrict__ starts, const uint32_t* __restrict__ work,
     const uint32_t* __restrict__ nwork_p, vx_level out, int K, const float4* __restrict__ dirs, int N,
     const LobeStats* __restrict__ cst, LobeStats* __restrict__ pst, unsigned long long* __restrict__ nsampled) {
