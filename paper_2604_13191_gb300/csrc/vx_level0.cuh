@@ -132,25 +132,6 @@ __device__ __noinline__ float seg_box_min(float ax, float ay, float az, float dx
     return gmin;
 }
 
-// Full capsule-box predicate (used at voxel level with an inflated radius as a cull).
-__device__ __forceinline__ bool capsule_box(const float* a, const float* b, float rr, const float* lo,
-                                            const float* hi) {
-    float d[3], g[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        d[i] = b[i] - a[i];
-        float mn = fmin2(a[i], b[i]), mx = fmax2(a[i], b[i]);
-        if (lo[i] > mx) g[i] = lo[i] - mx;
-        else if (mn > hi[i]) g[i] = mn - hi[i];
-        else g[i] = 0.0f;
-    }
-    float G = (g[0] * g[0] + g[1] * g[1]) + g[2] * g[2];
-    if (G > rr) return false;
-    if (sqdist_point_box(a[0], a[1], a[2], lo, hi) <= rr) return true;
-    if (sqdist_point_box(b[0], b[1], b[2], lo, hi) <= rr) return true;
-    return seg_box_min(a[0], a[1], a[2], d[0], d[1], d[2], lo[0], lo[1], lo[2], hi[0] - lo[0]) <= rr;
-}
-
 // Per-axis terms of steps 1 and 2 for the sub-cell interval [k/8, (k+1)/8] of one axis.
 struct AxisTerms {
     float g2, ea2, eb2;
@@ -315,30 +296,35 @@ __device__ __forceinline__ CapsuleLocal capsule_local(const float* a, const floa
     return c;
 }
 
-// True when segment a-b is farther than r from sub-cell `id` by a margin that makes step 3
-// reject it too.  For a unit n, the distance between two convex sets is at least their
-// separation along n: here min(n.(a - c), n.(b - c)) - h |n|_1 for the sub-cell of centre c
-// and half-size h = 1/16.  n is taken along v = p - c, p the point of the segment nearest
-// to c (any v gives a bound; this one is nearly tight once the sub-cell is a few sub-cells
-// away).  The test s > (r + eta) |v|, s the separation times |v|, is done in squares.
-// Step 3's FP32 value is the squared distance of a point within ~1e-6 (M + 1) of the
-// segment, to relative 1e-6, so a sub-cell separated by more than r + eta has that value
-// above r^2: the task can be dropped without changing the mask.
-__device__ __forceinline__ bool capsule_cell_separated(const CapsuleLocal& c, int id) {
-    const float cx = (float)(id & 7) * 0.125f + 0.0625f;
-    const float cy = (float)((id >> 3) & 7) * 0.125f + 0.0625f;
-    const float cz = (float)(id >> 6) * 0.125f + 0.0625f;
-    const float Ax = c.a_rr.x - cx, Ay = c.a_rr.y - cy, Az = c.a_rr.z - cz;
-    const float Bx = c.b_reta.x - cx, By = c.b_reta.y - cy, Bz = c.b_reta.z - cz;
-    float tc = -((Ax * c.d_idd.x + Ay * c.d_idd.y) + Az * c.d_idd.z) * c.d_idd.w;
+// True when segment a-b (a, b - a, 1/|b - a|^2) is farther than re from the cube of centre
+// (cx, cy, cz) and half-size h.  For a unit n, the distance between two convex sets is at
+// least their separation along n: here min(n.(a - c), n.(b - c)) - h |n|_1.  n is taken along
+// v = p - c, p the point of the segment nearest to c (any v gives a bound; this one is
+// nearly tight once the box is a few box sizes away).  The test s > re |v|, s the separation
+// times |v|, is done in squares.
+__device__ __forceinline__ bool segment_box_separated(float4 a, float4 b, float4 d_idd, float cx, float cy, float cz,
+                                                      float h, float re) {
+    const float Ax = a.x - cx, Ay = a.y - cy, Az = a.z - cz;
+    const float Bx = b.x - cx, By = b.y - cy, Bz = b.z - cz;
+    float tc = -((Ax * d_idd.x + Ay * d_idd.y) + Az * d_idd.z) * d_idd.w;
     tc = fminf(fmaxf(tc, 0.0f), 1.0f);
-    const float vx = Ax + tc * c.d_idd.x, vy = Ay + tc * c.d_idd.y, vz = Az + tc * c.d_idd.z;
+    const float vx = Ax + tc * d_idd.x, vy = Ay + tc * d_idd.y, vz = Az + tc * d_idd.z;
     const float sa = (vx * Ax + vy * Ay) + vz * Az;
     const float sb = (vx * Bx + vy * By) + vz * Bz;
-    const float sep = fminf(sa, sb) - 0.0625f * ((fabsf(vx) + fabsf(vy)) + fabsf(vz));
+    const float sep = fminf(sa, sb) - h * ((fabsf(vx) + fabsf(vy)) + fabsf(vz));
     const float vv = (vx * vx + vy * vy) + vz * vz;
-    const float re = c.b_reta.w;
     return sep > 0.0f && sep * sep > (re * re) * vv;
+}
+
+// True when the capsule provably misses sub-cell `id` by more than the rounding of the
+// exact minimum: separated by more than r + eta, eta (per capsule) covering the FP32 errors
+// of this bound and of step 3.  Step 3's FP32 value is the squared distance of a point
+// within ~1e-6 (M + 1) of the segment, to relative 1e-6, so a sub-cell separated by more
+// than r + eta has that value above r^2: the task can be dropped without changing the mask.
+__device__ __forceinline__ bool capsule_cell_separated(const CapsuleLocal& c, int id) {
+    return segment_box_separated(c.a_rr, c.b_reta, c.d_idd, (float)(id & 7) * 0.125f + 0.0625f,
+                                 (float)((id >> 3) & 7) * 0.125f + 0.0625f, (float)(id >> 6) * 0.125f + 0.0625f,
+                                 0.0625f, c.b_reta.w);
 }
 
 // Step 3 of every pooled task whose sub-cell is not set yet (warp-collective); returns the
@@ -746,12 +732,22 @@ __device__ __forceinline__ Range capsule_range(float4 A, float4 B, const Window&
     return make_range(mn, mx, R);
 }
 
+// The voxel is kept unless steps 1-2 reject it at the inflated radius, or it is separated
+// from the segment by more than that radius plus the separation test's rounding margin.
 __device__ __forceinline__ bool capsule_voxel_candidate(float4 A, float4 B, int vi, int vj, int vk) {
-    float a[3] = {A.x - (float)vi, A.y - (float)vj, A.z - (float)vk};
-    float b[3] = {B.x - (float)vi, B.y - (float)vj, B.z - (float)vk};
-    float r = A.w + capsule_margin(A.w);
+    const float a[3] = {A.x - (float)vi, A.y - (float)vj, A.z - (float)vk};
+    const float b[3] = {B.x - (float)vi, B.y - (float)vj, B.z - (float)vk};
+    const float r = A.w + capsule_margin(A.w);
+    const float rr = r * r;
     const float lo[3] = {0.0f, 0.0f, 0.0f}, hi[3] = {1.0f, 1.0f, 1.0f};
-    return capsule_box(a, b, r * r, lo, hi);
+    float g[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) g[i] = gap3(0.0f, 1.0f, fmin2(a[i], b[i]), fmax2(a[i], b[i]));
+    if ((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2] > rr) return false;
+    if (sqdist_point_box(a[0], a[1], a[2], lo, hi) <= rr) return true;
+    if (sqdist_point_box(b[0], b[1], b[2], lo, hi) <= rr) return true;
+    const CapsuleLocal c = capsule_local(a, b, r);
+    return !segment_box_separated(c.a_rr, c.b_reta, c.d_idd, 0.5f, 0.5f, 0.5f, 0.5f, c.b_reta.w);
 }
 
 __device__ __forceinline__ Range tri_range(float4 a, float4 b, float4 c, const Window& R) {
