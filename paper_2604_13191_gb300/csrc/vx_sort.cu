@@ -141,21 +141,35 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const uint32_t* __r
     for (int d = threadIdx.x; d < RB; d += SORT_THREADS) hist[(size_t)d * nt + blockIdx.x] = h[d];
 }
 
+// Stable scatter of one tile.  Each element's rank inside the tile (digit-major, original
+// order within a digit) is found with per-warp running counters; the tile is then
+// rearranged into that order in shared memory and written out with consecutive threads on
+// consecutive elements, so that the writes of one digit's run are contiguous.
 template <bool LUT, int RB>
-__global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint32_t* __restrict__ keys,
+__global__ void __launch_bounds__(SORT_THREADS, 3) k_radix_scatter(const uint32_t* __restrict__ keys,
                                                                 const uint32_t* __restrict__ vals, uint32_t n,
                                                                 int shift, uint32_t dmask, uint32_t nt,
                                                                 const uint8_t* __restrict__ lut,
                                                                 const uint32_t* __restrict__ hist,
                                                                 uint32_t* __restrict__ okeys,
                                                                 uint32_t* __restrict__ ovals) {
-    __shared__ uint32_t wcnt[SORT_WARPS][RB];
-    __shared__ uint32_t gofs[RB];
+    static_assert(RB % SORT_THREADS == 0, "digits per thread");
+    union Stage {
+        uint32_t wcnt[SORT_WARPS][RB];           // ranking: per-warp counts, then warp offsets
+        struct {
+            uint32_t k[SORT_TILE], v[SORT_TILE];  // the tile in digit order
+        } t;
+    };
+    __shared__ Stage st;
+    __shared__ uint32_t gofs[RB];   // global start of the tile's run of each digit
+    __shared__ uint32_t tofs[RB];   // start of each digit's run inside the tile
+    __shared__ uint32_t scan_tmp[SORT_WARPS + 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < SORT_WARPS * RB; i += SORT_THREADS) (&wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < SORT_WARPS * RB; i += SORT_THREADS) (&st.wcnt[0][0])[i] = 0;
     for (int d = threadIdx.x; d < RB; d += SORT_THREADS) gofs[d] = hist[(size_t)d * nt + blockIdx.x];
     __syncthreads();
-    const size_t base = (size_t)blockIdx.x * SORT_TILE + (size_t)w * (32 * SORT_ITEMS);
+    const size_t tile0 = (size_t)blockIdx.x * SORT_TILE;
+    const size_t base = tile0 + (size_t)w * (32 * SORT_ITEMS);
     const uint32_t lt = (1u << lane) - 1u;
     uint32_t k[SORT_ITEMS], v[SORT_ITEMS], rk[SORT_ITEMS];
 #pragma unroll
@@ -167,32 +181,65 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint32_t* 
         uint32_t d = valid ? radix_digit<LUT>(k[j], v[j], shift, dmask, lut) : (uint32_t)RB;
         uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t r = 0;
-        if (valid) r = wcnt[w][d] + __popc(peers & lt);
+        if (valid) r = st.wcnt[w][d] + __popc(peers & lt);
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) wcnt[w][d] += __popc(peers);
+        if (valid && lane == __ffs(peers) - 1) st.wcnt[w][d] += __popc(peers);
         __syncwarp();
         rk[j] = r;
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < RB; d += SORT_THREADS) {
+    // warp offsets per digit (exclusive over warps) and the tile's count of each digit
+    constexpr int DPT = RB / SORT_THREADS;
+    uint32_t cnt[DPT];
+#pragma unroll
+    for (int i = 0; i < DPT; ++i) {
+        const int d = threadIdx.x * DPT + i;
         uint32_t run = 0;
 #pragma unroll
         for (int ww = 0; ww < SORT_WARPS; ++ww) {
-            uint32_t t = wcnt[ww][d];
-            wcnt[ww][d] = run;
+            const uint32_t t = st.wcnt[ww][d];
+            st.wcnt[ww][d] = run;
             run += t;
+        }
+        cnt[i] = run;
+    }
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < DPT; ++i) sum += cnt[i];
+    uint32_t total;
+    uint32_t ex = block_excl_scan(sum, scan_tmp, total);
+#pragma unroll
+    for (int i = 0; i < DPT; ++i) {
+        tofs[threadIdx.x * DPT + i] = ex;
+        ex += cnt[i];
+    }
+    __syncthreads();
+    // tile-local positions (the counters are read before the tile overwrites them)
+#pragma unroll
+    for (int j = 0; j < SORT_ITEMS; ++j) {
+        const size_t e = base + (size_t)j * 32 + lane;
+        if (e < n) {
+            const uint32_t d = radix_digit<LUT>(k[j], v[j], shift, dmask, lut);
+            rk[j] += tofs[d] + st.wcnt[w][d];
         }
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < SORT_ITEMS; ++j) {
-        size_t e = base + (size_t)j * 32 + lane;
+        const size_t e = base + (size_t)j * 32 + lane;
         if (e < n) {
-            uint32_t d = radix_digit<LUT>(k[j], v[j], shift, dmask, lut);
-            uint32_t pos = gofs[d] + wcnt[w][d] + rk[j];
-            okeys[pos] = k[j];
-            ovals[pos] = v[j];
+            st.t.k[rk[j]] = k[j];
+            st.t.v[rk[j]] = v[j];
         }
+    }
+    __syncthreads();
+    const uint32_t tn = (uint32_t)min((size_t)SORT_TILE, (size_t)n - tile0);
+    for (uint32_t i = threadIdx.x; i < tn; i += SORT_THREADS) {
+        const uint32_t kk = st.t.k[i], vv = st.t.v[i];
+        const uint32_t d = radix_digit<LUT>(kk, vv, shift, dmask, lut);
+        const uint32_t pos = gofs[d] + (i - tofs[d]);
+        okeys[pos] = kk;
+        ovals[pos] = vv;
     }
 }
 
