@@ -140,8 +140,14 @@ struct AxisTerms {
 // at most one of the two differences is positive, and a difference is positive exactly when
 // its comparison holds (FP subtraction of finite values), so the two forms round to the same
 // value up to the sign of a zero, which the square removes.  Likewise the endpoint distances.
+// max of three (one instruction on sm_100 and later; exact, like two two-input maxima)
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
 __device__ __forceinline__ float gap3(float lo, float hi, float mn, float mx) {
-    return fmaxf(fmaxf(lo - mx, mn - hi), 0.0f);
+    return fmax3(lo - mx, mn - hi, 0.0f);
 }
 __device__ __forceinline__ AxisTerms axis_terms(float a, float b, int k) {
     const float lo = (float)k * 0.125f, hi = (float)(k + 1) * 0.125f;
@@ -188,6 +194,7 @@ struct CapsuleLocal {
 // lane): squared gap of the segment's extent, squared distances of the endpoints.
 struct CapsuleX {
     float4 g2[2], ea2[2], eb2[2];
+    float4 bx;                     // the voxel's x interval [0, 1]: gap^2, far_a^2, far_b^2
 };
 struct CapsuleTasks {
     uint16_t task[CT_TASKS];       // batch slot << 9 | sub-cell id
@@ -213,6 +220,8 @@ __device__ __forceinline__ CapsuleX capsule_x(float a, float b) {
     x.ea2[1] = make_float4(ea[4], ea[5], ea[6], ea[7]);
     x.eb2[0] = make_float4(eb[0], eb[1], eb[2], eb[3]);
     x.eb2[1] = make_float4(eb[4], eb[5], eb[6], eb[7]);
+    const AxisBound bx = axis_bound(a, b, 0.0f, 1.0f);
+    x.bx = make_float4(bx.g2, bx.fa2, bx.fb2, 0.0f);
     return x;
 }
 
@@ -238,7 +247,8 @@ __device__ __forceinline__ uint32_t capsule_steps12(const CapsuleLocal& c, const
     const float rr = c.a_rr.w;
     const float zlo = (float)sz * 0.125f, zhi = (float)(sz + 1) * 0.125f;
     const AxisBound bz = axis_bound(a[2], b[2], zlo, zhi);
-    const AxisBound bx = axis_bound(a[0], b[0], 0.0f, 1.0f);
+    const float4 bxv = X.bx;
+    const AxisBound bx = {bxv.x, bxv.y, bxv.z};
     const AxisBound bb = axis_bound(a[1], b[1], (float)sy0 * 0.125f, (float)(sy0 + 2) * 0.125f);
     if (bx.g2 > rr - (bb.g2 + bz.g2)) return bits;                       // all 16 fail step 1
     if (bx.fa2 <= rr - (bb.fa2 + bz.fa2) || bx.fb2 <= rr - (bb.fb2 + bz.fb2)) return 0xffffu;
@@ -286,8 +296,8 @@ __device__ __forceinline__ uint32_t capsule_steps12(const CapsuleLocal& c, const
 __device__ __forceinline__ CapsuleLocal capsule_local(const float* a, const float* b, float r) {
     const float d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
     const float dd = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
-    const float M = fmaxf(fmaxf(fmaxf(fabsf(a[0]), fabsf(a[1])), fmaxf(fabsf(a[2]), fabsf(b[0]))),
-                          fmaxf(fabsf(b[1]), fabsf(b[2])));
+    const float M = fmax3(fmax3(fabsf(a[0]), fabsf(a[1]), fabsf(a[2])), fmax3(fabsf(b[0]), fabsf(b[1]), fabsf(b[2])),
+                          0.0f);
     const float eta = 2e-5f * ((M + r) + 3.0f);
     CapsuleLocal c;
     c.a_rr = make_float4(a[0], a[1], a[2], r * r);
@@ -955,15 +965,15 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                     uint32_t und;
                     chunk = capsule_steps12(ct.batch[slot], ct.xt[slot], sy0, sz, chunk, und);
                     // pool the undecided sub-cells as step-3 tasks of this capsule
-                    const uint32_t n = __popc(und);
-                    uint32_t off = n;
+                    if (__any_sync(0xffffffffu, und != 0u)) {
+                        const uint32_t n = __popc(und);
+                        uint32_t off = n;
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t t = __shfl_up_sync(0xffffffffu, off, o);
-                        if (lane >= o) off += t;
-                    }
-                    const int total = (int)__shfl_sync(0xffffffffu, off, 31);
-                    if (total > 0) {
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint32_t t = __shfl_up_sync(0xffffffffu, off, o);
+                            if (lane >= o) off += t;
+                        }
+                        const int total = (int)__shfl_sync(0xffffffffu, off, 31);
                         if (ntask + total > CT_TASKS) {
                             chunk = capsule_step3_pool(ct, ntask, chunk);
                             ntask = 0;
