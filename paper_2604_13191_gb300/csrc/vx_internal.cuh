@@ -107,6 +107,12 @@ vx_status vx_scan_u32(vx_context* ctx, const uint32_t* in, uint32_t* out, uint32
 vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, uint32_t** keys_alt,
                             uint32_t** vals_alt, uint32_t n, int bits, cudaStream_t s);
 
+// Starts of the runs of equal keys in the sorted keys[0, n): starts[r] = first index of run
+// r, starts[*nseg] = n; *nseg (device) receives the number of runs.  starts needs room for
+// the number of runs + 1 words.  Uses scan workspace slot WS_SCAN_TMP.
+vx_status vx_segment_starts(vx_context* ctx, const uint32_t* keys, uint32_t n, uint32_t* nseg, uint32_t* starts,
+                            cudaStream_t s);
+
 // Exclusive prefix sum with caller-provided partials (>= ceil(n / 2048) words).
 cudaError_t vx_scan_u32_scratch(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total,
                                 uint32_t* partials, cudaStream_t s);

@@ -834,18 +834,6 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_candidates(const float4* __
 // ------------------------------------------------------------------------------------
 // segments
 // ------------------------------------------------------------------------------------
-__global__ void k_head_flags(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ flags) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
-}
-
-__global__ void k_head_starts(const uint32_t* __restrict__ keys, uint32_t n, const uint32_t* __restrict__ idx,
-                              const uint32_t* __restrict__ nseg, uint32_t* __restrict__ starts) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && (i == 0 || keys[i] != keys[i - 1])) starts[idx[i]] = i;
-    if (i == 0) starts[*nseg] = n;
-}
-
 // ------------------------------------------------------------------------------------
 // reduce: warp per candidate voxel
 // lane l owns sub-cells sz = l >> 2, sy = 2 (l & 3) + {0,1}, sx = 0..7 (16 bits)

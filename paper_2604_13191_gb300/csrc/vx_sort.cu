@@ -111,6 +111,59 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* in, 
     }
 }
 
+// ---- segment starts ---------------------------------------------------------------
+// Heads of the runs of equal keys in a sorted array: element e is a head when e == 0 or
+// keys[e] != keys[e - 1].  A thread takes SCAN_ITEMS consecutive elements (as k_scan_down).
+__device__ __forceinline__ uint32_t head_bits(const uint32_t* __restrict__ keys, uint32_t n, size_t e0) {
+    static_assert(SCAN_ITEMS == 8, "two 16-byte loads per thread");
+    uint32_t k[SCAN_ITEMS];
+    if (e0 + SCAN_ITEMS <= n) {
+        // e0 is a multiple of 8 and the key arrays are 256-byte aligned
+        const uint4 x = __ldg(reinterpret_cast<const uint4*>(keys + e0));
+        const uint4 y = __ldg(reinterpret_cast<const uint4*>(keys + e0) + 1);
+        k[0] = x.x; k[1] = x.y; k[2] = x.z; k[3] = x.w;
+        k[4] = y.x; k[5] = y.y; k[6] = y.z; k[7] = y.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) k[j] = e0 + j < n ? keys[e0 + j] : 0u;
+    }
+    uint32_t prev = e0 > 0 && e0 - 1 < n ? keys[e0 - 1] : 0u;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        const size_t e = e0 + j;
+        if (e < n && (e == 0 || k[j] != prev)) bits |= 1u << j;
+        prev = k[j];
+    }
+    return bits;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_seg_count(const uint32_t* __restrict__ keys, uint32_t n,
+                                                            uint32_t* __restrict__ part) {
+    __shared__ uint32_t sm[SCAN_THREADS / 32 + 1];
+    const size_t e0 = (size_t)blockIdx.x * SCAN_TILE + (size_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t tot;
+    block_excl_scan(__popc(head_bits(keys, n, e0)), sm, tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_seg_starts(const uint32_t* __restrict__ keys, uint32_t n,
+                                                             const uint32_t* __restrict__ part,
+                                                             const uint32_t* __restrict__ nseg,
+                                                             uint32_t* __restrict__ starts) {
+    __shared__ uint32_t sm[SCAN_THREADS / 32 + 1];
+    const size_t e0 = (size_t)blockIdx.x * SCAN_TILE + (size_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t bits = head_bits(keys, n, e0);
+    uint32_t tot;
+    uint32_t idx = block_excl_scan(__popc(bits), sm, tot) + part[blockIdx.x];
+    while (bits) {
+        const int j = __ffs(bits) - 1;
+        bits &= bits - 1;
+        starts[idx++] = (uint32_t)(e0 + j);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) starts[*nseg] = n;
+}
+
 // ---- radix sort ----------------------------------------------------------------
 // Digit of an element: bits [shift, shift + 8) of its key, or (LUT pass) a digit looked
 // up from its value: lut[value], with 255 for the padding value 0xffffffff.
@@ -258,6 +311,23 @@ vx_status vx_scan_u32(vx_context* ctx, const uint32_t* in, uint32_t* out, uint32
     VX_LAUNCH(ctx, ST_SCAN, s, k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(in, n, part));
     VX_LAUNCH(ctx, ST_SCAN, s, k_scan_partials<<<1, SCAN_THREADS, 0, s>>>(part, nb, total));
     VX_LAUNCH(ctx, ST_SCAN, s, k_scan_down<<<nb, SCAN_THREADS, 0, s>>>(in, out, n, part));
+    VX_CUDA_TRY(cudaGetLastError());
+    return VX_OK;
+}
+
+vx_status vx_segment_starts(vx_context* ctx, const uint32_t* keys, uint32_t n, uint32_t* nseg, uint32_t* starts,
+                            cudaStream_t s) {
+    if (n == 0) {
+        VX_CUDA_TRY(cudaMemsetAsync(nseg, 0, 4, s));
+        VX_CUDA_TRY(cudaMemsetAsync(starts, 0, 4, s));
+        return VX_OK;
+    }
+    const uint32_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    VX_TRY(vx_ws_ensure(ctx, WS_SCAN_TMP, (size_t)nb * 4 + 256, s));
+    uint32_t* part = (uint32_t*)ctx->ws[WS_SCAN_TMP].p;
+    VX_LAUNCH(ctx, ST_HEADS, s, k_seg_count<<<nb, SCAN_THREADS, 0, s>>>(keys, n, part));
+    VX_LAUNCH(ctx, ST_HEADS, s, k_scan_partials<<<1, SCAN_THREADS, 0, s>>>(part, nb, nseg));
+    VX_LAUNCH(ctx, ST_HEADS, s, k_seg_starts<<<nb, SCAN_THREADS, 0, s>>>(keys, n, part, nseg, starts));
     VX_CUDA_TRY(cudaGetLastError());
     return VX_OK;
 }

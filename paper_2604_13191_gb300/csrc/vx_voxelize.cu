@@ -104,10 +104,7 @@ vx_status voxelize_window(vx_context* ctx, bool fiber, uint32_t np, const Window
     VX_TRY(vx_ws_ensure(ctx, WS_STARTS, (size_t)npairs * 4 + 8, s));
     uint32_t* flags = (uint32_t*)ctx->ws[WS_FLAGS].p;
     uint32_t* starts = (uint32_t*)ctx->ws[WS_STARTS].p;
-    VX_LAUNCH(ctx, ST_HEADS, s, k_head_flags<<<grid_for(npairs, 256), 256, 0, s>>>(k0, npairs, flags));
-    VX_TRY(vx_scan_u32(ctx, flags, flags, npairs, misc + 2, s));
-    VX_LAUNCH(ctx, ST_HEADS, s, k_head_starts<<<grid_for(npairs, 256), 256, 0, s>>>(k0, npairs, flags, misc + 2, starts));
-    VX_CUDA_TRY(cudaGetLastError());
+    VX_TRY(vx_segment_starts(ctx, k0, npairs, misc + 2, starts, s));
 
     VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc + 2, 4, cudaMemcpyDeviceToHost, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
