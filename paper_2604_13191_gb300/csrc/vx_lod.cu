@@ -465,9 +465,10 @@ struct ClusterView {
     float* Mh;
     int32_t* H;
     uint8_t* alive;
+    uint8_t* list;    // the alive slots in increasing order (rebuilt before each merge)
 };
 __host__ __device__ inline size_t cluster_bytes(int slots) {
-    return (((size_t)slots * 19 * 4 + (size_t)slots) + 15) & ~size_t(15);
+    return (((size_t)slots * 19 * 4 + (size_t)slots * 2) + 15) & ~size_t(15);
 }
 __device__ inline ClusterView cluster_view(unsigned char* base, int slots) {
     ClusterView v;
@@ -476,8 +477,22 @@ __device__ inline ClusterView cluster_view(unsigned char* base, int slots) {
     v.Mh = v.w + slots;
     v.H = (int32_t*)(v.Mh + (size_t)slots * 6);
     v.alive = (uint8_t*)(v.H + (size_t)slots * 6);
+    v.list = v.alive + slots;
     return v;
 }
+
+// q -> (a, b), a > b, ordered by a then b, for the pairs of up to 64 alive lobes
+struct PairTable {
+    uint16_t ab[64 * 63 / 2];
+};
+constexpr PairTable make_pair_table() {
+    PairTable t{};
+    int q = 0;
+    for (int a = 1; a < 64; ++a)
+        for (int b = 0; b < a; ++b) t.ab[q++] = (uint16_t)((a << 8) | b);
+    return t;
+}
+__device__ const PairTable kPairTable = make_pair_table();
 
 // float3 direction table -> float4 (one 16-byte load per sample)
 __global__ void k_pack_dirs(const float* __restrict__ d, int n, float4* __restrict__ out) {
@@ -572,19 +587,28 @@ __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32, G == 1 ? 7 : 
         gsync();
         int count = n, next = n;
         while (count > K) {
-            // argmin over alive pairs (i > j) of (distance, i, j)
+            // the alive slots in increasing order (count <= 8K <= 64 of them)
+            if (tid < 32) {
+                int base = 0;
+                for (int s0 = 0; s0 < next; s0 += 32) {
+                    const int sl = s0 + tid;
+                    const bool al = sl < next && sm.alive[sl];
+                    const uint32_t m = __ballot_sync(0xffffffffu, al);
+                    if (al) sm.list[base + __popc(m & ((1u << tid) - 1u))] = (uint8_t)sl;
+                    base += __popc(m);
+                }
+            }
+            gsync();
+            // argmin over alive pairs (i > j) of (distance, i, j); the distance is a sum of
+            // six histogram differences of at most N each, so it fits 32 bits
             unsigned long long best = ~0ull;
-            const int npairs = next * (next - 1) / 2;
+            const int npairs = count * (count - 1) / 2;
             for (int q = tid; q < npairs; q += NT) {
-                // q -> (i, j), i > j, ordered by i then j
-                int i = (int)((sqrtf(8.0f * (float)q + 1.0f) + 1.0f) * 0.5f);
-                while (i * (i - 1) / 2 > q) --i;
-                while ((i + 1) * i / 2 <= q) ++i;
-                const int j = q - i * (i - 1) / 2;
-                if (!sm.alive[i] || !sm.alive[j]) continue;
-                long long d = 0;
+                const uint32_t ab = kPairTable.ab[q];
+                const int i = sm.list[ab >> 8], j = sm.list[ab & 0xffu];
+                uint32_t d = 0;
 #pragma unroll
-                for (int c = 0; c < 6; ++c) d += llabs((long long)sm.H[i * 6 + c] - (long long)sm.H[j * 6 + c]);
+                for (int c = 0; c < 6; ++c) d = __sad(sm.H[i * 6 + c], sm.H[j * 6 + c], d);
                 unsigned long long key = ((unsigned long long)d << 16) | ((unsigned long long)i << 8) | (unsigned long long)j;
                 if (key < best) best = key;
             }
