@@ -531,11 +531,13 @@ def _source_hash(name):
 
 
 # FP32 operations the definition spends per unit of work:
-#   reduce_fibers: per (pair, sub-cell) decision, the step-1/2 test on precomputed per-axis
-#     terms: 3 x (2 adds + 1 compare) = 9, plus the per-axis terms amortised (~1) -> 10
-#   sggx_cluster: per sampled direction: mat-vec 15, norm 5, thresholds 2, compares 6,
-#     reciprocal 1, scale 1, products 9, roundings 12 -> 51
-ALU_OPS = {"reduce_fibers": 512 * 10, "sggx_cluster": N_SAMPLES * 51}
+#   reduce_fibers: per (pair, sub-cell) decision, the step-1/2 tests on precomputed per-axis
+#     terms, each x^2 against r^2 - (y^2 + z^2): 3 x (2 adds + 1 compare) = 9, plus the
+#     per-axis terms amortised (~1) -> 10
+#   sggx_cluster: per sampled direction: mat-vec 9 (3 multiplies, 6 fused), squares and norm
+#     5, thresholds 2, compares 6, reciprocal 1, scale 1, off-diagonal products 3, fused
+#     product-roundings 6, integer sums 12 -> 45
+ALU_OPS = {"reduce_fibers": 512 * 10, "sggx_cluster": N_SAMPLES * 45}
 # algorithmic HBM bytes per unit of work
 HBM_BYTES = {
     "sort_scatter": 16,          # per pair and pass: key + value read and written
