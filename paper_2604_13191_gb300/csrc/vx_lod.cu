@@ -100,7 +100,8 @@ __device__ __forceinline__ void downsample_into(const uint64_t* cm, int oct, uin
             b = (b | (b >> 2)) & 0x0fu;
             out |= (uint64_t)b << (4 * ox + 8 * (4 * oy + qy));
         }
-        pm[4 * oz + qz] |= out;
+        // (constant indices: the parent mask stays in registers)
+        if (oz) pm[4 + qz] |= out; else pm[qz] |= out;
     }
 }
 
@@ -141,8 +142,13 @@ __global__ void k_lod_reduce(LevelIn in, const uint32_t* __restrict__ starts, ui
 #pragma unroll
             for (int j = 0; j < 6; ++j) M[j] = M[j] + in.moment[(size_t)c * 6 + j];
             uint64_t cm[8];
+            const ulonglong2* cm2 = reinterpret_cast<const ulonglong2*>(in.mask + (size_t)c * 8);
 #pragma unroll
-            for (int w = 0; w < 8; ++w) cm[w] = in.mask[(size_t)c * 8 + w];
+            for (int w = 0; w < 4; ++w) {
+                const ulonglong2 x = cm2[w];
+                cm[2 * w] = x.x;
+                cm[2 * w + 1] = x.y;
+            }
             downsample_into(cm, (int)(in.keys[c] & 7ull), pm);
             ncand += in.lobe_count[c];
         }
@@ -150,8 +156,9 @@ __global__ void k_lod_reduce(LevelIn in, const uint32_t* __restrict__ starts, ui
         out.mass[p] = m;
 #pragma unroll
         for (int j = 0; j < 6; ++j) out.moment[(size_t)p * 6 + j] = M[j];
+        ulonglong2* pm2 = reinterpret_cast<ulonglong2*>(out.mask + (size_t)p * 8);
 #pragma unroll
-        for (int w = 0; w < 8; ++w) out.mask[(size_t)p * 8 + w] = pm[w];
+        for (int w = 0; w < 4; ++w) pm2[w] = make_ulonglong2(pm[2 * w], pm[2 * w + 1]);
         uint16_t occ;
         uint8_t pj[3];
         mask_counts(pm, occ, pj);
