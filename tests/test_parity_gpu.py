@@ -220,6 +220,20 @@ def test_yarn_reduced_sggx_h(ctx, dirs5000):
     assert clustered > 100
 
 
+def test_sggx_h_more_directions_than_one_pass(ctx):
+    """The same yarn with N = 33,000 directions: above 32 x 1024, so the warp tier (levels
+    1-2 here, over 2,432 parents) samples through its general loop with 64-bit partial sums,
+    while the block tiers keep the paired loop.  Lobes and counts must still match."""
+    w = synth.config2(fibers_per_ply=8, segments=500, R=128, K=4)
+    dirs = synth.sample_directions(33000)
+    got = run_gpu(ctx, w, dirs=dirs)
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, 128, 4, dirs)
+    assert refs[1]["keys"].shape[0] > 152 * 16
+    for lvl, (g, r) in enumerate(zip(got, refs)):
+        compare_level(g, r, f"level {lvl}", mu_max=prim_measure_max(w))
+
+
 # ----------------------------------------------------------------------------
 # edge cases
 # ----------------------------------------------------------------------------
