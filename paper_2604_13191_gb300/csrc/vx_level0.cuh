@@ -937,7 +937,9 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
             // additions as a single running sum per component)
             if (lane < 7)
                 for (uint32_t j = 0; j < cnt; ++j) accc = accc + ct.q[j * 7 + lane];
-            // bitonic sort of the 32 keys over the warp (unique: the lane is the low 5 bits)
+            // bitonic sort of the 32 keys over the warp (unique: the lane is the low 5 bits);
+            // after the stage of width k, lanes 0..k-1 hold their keys in ascending order, so
+            // the sort stops once k covers the batch
 #pragma unroll
             for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
@@ -946,6 +948,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                     const bool keep_min = ((lane & k) == 0) == ((lane & jj) == 0);
                     okey = keep_min ? min(okey, other) : max(okey, other);
                 }
+                if ((uint32_t)k >= cnt) break;
             }
             for (uint32_t j = 0; j < cnt; ++j) {
                 if (!full) {
