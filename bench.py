@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-splines", action="store_true")
     ap.add_argument("--woven", type=int, default=0,
                     help="also time the woven patch at 2048^3 with this many warp and weft yarns (16 = the "
                          "full patch)")
@@ -341,6 +342,11 @@ def main():
     if args.woven > 0:
         woven = woven_patch(ctx, dev, args.woven, dirs)
 
+    # ---- spline input (Catmull-Rom nodes tessellated on the device) --------------------------
+    splines = None
+    if not args.no_splines:
+        splines = spline_fibers(ctx, dev, args.steps, dirs)
+
     # ---- adjoint vs forward on the differentiation workload ---------------------------------
     adjoint = None
     if not args.no_adjoint:
@@ -377,6 +383,7 @@ def main():
         "e2e": e2e,
         "clocks": clk,
         "batched": batched,
+        "splines": splines,
         "adjoint": adjoint,
     }
     if woven is not None:
@@ -479,6 +486,41 @@ def woven_patch(ctx, dev, n_yarns, dirs):
             "prims": int(w.num_prims), "ms_per_step": statistics.mean(ms), "voxelize_ms": statistics.mean(vox),
             "lod_ms": statistics.mean(lod), "prims_per_s": w.num_prims / (statistics.mean(ms) * 1e-3),
             "candidate_pairs": int(pairs), "voxels_per_level": sizes}
+
+
+def spline_fibers(ctx, dev, steps, dirs):
+    """Spline input: the bench yarn's fibers given as Catmull-Rom splines through every 10th
+    node (401 nodes per fiber), tessellated on the device with 10 points per span (the same
+    768k capsules), then vx_voxelize + vx_build_lod, K = 4; CUDA events."""
+    import torch
+    w = synth.config2()
+    off = w.fiber_offsets
+    keep = [np.arange(off[f], off[f + 1], 10) for f in range(len(off) - 1)]
+    nodes = torch.from_numpy(np.concatenate([w.ctrl[k] for k in keep]).astype(np.float32)).to(dev)
+    noff = torch.from_numpy(np.concatenate([[0], np.cumsum([len(k) for k in keep])]).astype(np.int64)).to(dev)
+    S = 10
+    tess, total = [], []
+    for i in range(steps + 2):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        m = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctrl, coff = ctx.tessellate_catmull_rom(nodes, noff, S)
+        m.record()
+        L0 = ctx.voxelize(w.grid, ctrl=ctrl, fiber_offsets=coff)
+        pyr = ctx.build_lod(L0, K=K_LOBES, dirs=dirs)
+        b.record()
+        torch.cuda.synchronize()
+        if i >= 2:
+            tess.append(a.elapsed_time(m))
+            total.append(a.elapsed_time(b))
+        n_caps = int(ctrl.shape[0] - (coff.shape[0] - 1))
+        del L0, pyr, ctrl, coff
+    return {"workload": "the bench yarn as Catmull-Rom splines: 192 fibers x 401 nodes, 10 points per span "
+                        "(768k capsules), 512^3, K=4, N=5000",
+            "nodes": int(nodes.shape[0]), "subdiv": S, "prims": n_caps, "tessellate_ms": statistics.mean(tess),
+            "ms_per_step": statistics.mean(total), "prims_per_s": n_caps / (statistics.mean(total) * 1e-3)}
 
 
 def adjoint_vs_forward(ctx, dev, steps):

@@ -287,6 +287,35 @@ VX_API vx_status vx_batch_level(vx_batch* batch, int instance, int level, void* 
 /* Frees the batch's buffers and graph. */
 VX_API void vx_batch_destroy(vx_batch* batch);
 
+/* Catmull-Rom spline fibers tessellated into capsule control points (Sec. 3.2: the spline
+ * through its stored nodes, sampled at equally spaced t), for vx_voxelize with VX_FIBERS.
+ *   nodes       (device) [num_nodes][4] float xyz + radius, 16-byte aligned
+ *   offsets     (device) [num_splines + 1] int64: spline f has nodes offsets[f] ..
+ *               offsets[f+1]-1, at least one
+ *   subdiv      points per span (>= 1): span i (nodes i, i+1) gives t = j / subdiv,
+ *               j = 0..subdiv-1; the spline's last node closes it
+ *   out_ctrl    (device, caller-owned) [(num_nodes - num_splines) * subdiv + num_splines][4],
+ *               16-byte aligned
+ *   out_offsets (device, caller-owned) [num_splines + 1]: spline f's points start at
+ *               (offsets[f] - f) * subdiv + f
+ * Uniform Catmull-Rom through P0..P3 = nodes i-1 .. i+2 (an end node reflected through its
+ * neighbour past either end); radius interpolated linearly between nodes i and i+1.
+ * VX_ERR_INVALID_ARG for bad sizes or pointers, or a spline without nodes (found on the
+ * device: the call synchronises `stream` once). */
+VX_API vx_status vx_tessellate_catmull_rom(vx_context* ctx, const float* nodes, const int64_t* offsets,
+                                           int64_t num_splines, int64_t num_nodes, int subdiv, float* out_ctrl,
+                                           int64_t* out_offsets, void* stream);
+
+/* 8-bit compact SGGX export (Sec. 4.3, Eq. compact-sggx: one byte per
+ * parameter, 6 bytes per distribution).  For every lobe k < lobe_count[v] of the level:
+ *   sigma_x, sigma_y, sigma_z in [0, 1]  ->  q = round(255 * sigma)
+ *   r_xy, r_xz, r_yz in [-1, 1]          ->  q = round(127.5 * r + 127.5)
+ * evaluated in FP32, rounded to nearest with ties to even, clamped to [0, 255].  out
+ * (device, caller-owned) [num_voxels][K][6] bytes; lobes at or past lobe_count are zero.
+ * Enqueues one kernel on `stream`.  VX_ERR_INVALID_ARG on a NULL level, a NULL out with
+ * voxels to write, or K outside 1..8. */
+VX_API vx_status vx_export_compact8(const vx_level* level, uint8_t* out, void* stream);
+
 /* Returns a level's block to the context's allocator and clears the struct. */
 VX_API void vx_level_release(vx_context* ctx, vx_level* level, void* stream);
 

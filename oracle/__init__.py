@@ -75,6 +75,10 @@ def _load():
             lib.vxo_tri_measure64.argtypes = [P, C.c_int, C.c_int, C.c_int]
             lib.vxo_compact.restype = None
             lib.vxo_compact.argtypes = [P, P]
+            lib.vxo_compact8.restype = None
+            lib.vxo_compact8.argtypes = [P, C.c_int64, P]
+            lib.vxo_catmull_rom.restype = None
+            lib.vxo_catmull_rom.argtypes = [P, P, C.c_int64, C.c_int, P, P]
             lib.vxo_sqrtm3.restype = None
             lib.vxo_sqrtm3.argtypes = [P, P]
             lib.vxo_sample_lobe.restype = None
@@ -202,6 +206,31 @@ def compact(S) -> np.ndarray:
     o = np.zeros(6, dtype=np.float32)
     _load().vxo_compact(_ptr(S), _ptr(o))
     return o
+
+
+def catmull_rom(nodes, offsets, subdiv: int):
+    """Tessellated Catmull-Rom spline fibers (Sec. 3.2): (ctrl [P', 4] float32, offsets [F+1])
+    with (n_f - 1) * subdiv + 1 points per spline of n_f >= 1 nodes."""
+    nodes = _f32(nodes).reshape(-1, 4)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    F = off.shape[0] - 1
+    assert F >= 0 and np.all(np.diff(off) >= 1) and int(subdiv) >= 1
+    total = int((off[-1] - F) * subdiv + F)
+    out = np.zeros((max(total, 1), 4), dtype=np.float32)
+    out_off = np.zeros(F + 1, dtype=np.int64)
+    _load().vxo_catmull_rom(_ptr(nodes), _ptr(off), F, int(subdiv), _ptr(out), _ptr(out_off))
+    return out[:total], out_off
+
+
+def compact8(c) -> np.ndarray:
+    """8-bit compact SGGX of parameter sextuples c [..., 6] (Sec. 4.3): bytes [..., 6]."""
+    c = _f32(c)
+    shape = c.shape
+    flat = np.ascontiguousarray(c.reshape(-1, 6))
+    o = np.zeros(flat.shape, dtype=np.uint8)
+    if flat.shape[0]:
+        _load().vxo_compact8(_ptr(flat), flat.shape[0], _ptr(o))
+    return o.reshape(shape)
 
 
 def sqrtm3(S) -> np.ndarray:

@@ -536,6 +536,67 @@ ORC_API void vxo_compact(const float* S, float* out) {
     out[5] = pyz > 0.0f ? S[5] / sqrtf(pyz) : 0.0f;
 }
 
+/* Catmull-Rom spline fibers (Sec. 3.2: the spline through its stored nodes, sampled at
+ * equally spaced t).  Spline f has nodes off[f] .. off[f+1]-1 (at least one each).  Span i
+ * joins nodes i and i+1 and uses P0..P3 = nodes i-1, i, i+1, i+2; past either end the
+ * missing node is the end node reflected through its neighbour (2 P_0 - P_1, 2 P_n-1 -
+ * P_n-2), so that nodes on a line give points on it.  It gives S points at t = j / S,
+ * j = 0..S-1, from the uniform
+ * Catmull-Rom form
+ *     C(t) = 0.5 (2 P1 + t (a + t (b + t c))),  a = P2 - P0,
+ *     b = ((2 P0 - 5 P1) + 4 P2) - P3,  c = ((3 P1 - P0) - 3 P2) + P3,
+ * and the radius linearly, r1 + t (r2 - r1).  The spline's last node closes it.  Output
+ * spline f: (n_f - 1) S + 1 points from (off[f] - f) S + f.  FP32, in this order. */
+ORC_API void vxo_catmull_rom(const float* nodes, const int64_t* off, int64_t F, int S, float* out,
+                             int64_t* out_off) {
+    for (int64_t f = 0; f <= F; ++f) out_off[f] = (off[f] - f) * S + f;
+    for (int64_t f = 0; f < F; ++f) {
+        const int64_t b = off[f], n = off[f + 1] - off[f];
+        float* o = out + out_off[f] * 4;
+        for (int64_t i = 0; i + 1 < n; ++i) {
+            const float* P1 = nodes + (b + i) * 4;
+            const float* P2 = nodes + (b + i + 1) * 4;
+            float P0[3], P3[3];
+            for (int k = 0; k < 3; ++k) {
+                P0[k] = i > 0 ? nodes[(b + i - 1) * 4 + k] : 2.0f * P1[k] - P2[k];
+                P3[k] = i + 2 < n ? nodes[(b + i + 2) * 4 + k] : 2.0f * P2[k] - P1[k];
+            }
+            for (int j = 0; j < S; ++j) {
+                const float t = (float)j / (float)S;
+                float* q = o + (i * S + j) * 4;
+                for (int k = 0; k < 3; ++k) {
+                    const float a = P2[k] - P0[k];
+                    const float bb = ((2.0f * P0[k] - 5.0f * P1[k]) + 4.0f * P2[k]) - P3[k];
+                    const float c = ((3.0f * P1[k] - P0[k]) - 3.0f * P2[k]) + P3[k];
+                    q[k] = 0.5f * (2.0f * P1[k] + t * (a + t * (bb + t * c)));
+                }
+                q[3] = P1[3] + t * (P2[3] - P1[3]);
+            }
+        }
+        if (n > 0) {
+            const float* L = nodes + (b + n - 1) * 4;
+            float* q = o + (n - 1) * S * 4;
+            for (int k = 0; k < 4; ++k) q[k] = L[k];
+        }
+    }
+}
+
+/* 8-bit compact SGGX (Sec. 4.3, Eq. compact-sggx, one byte per parameter): sigma in [0, 1]
+ * -> round(255 sigma), r in [-1, 1] -> round(127.5 r + 127.5), FP32, ties to even, clamped
+ * to [0, 255].  c: n parameter sextuples; out: n * 6 bytes. */
+static uint8_t quant8(float x, float scale, float bias) {
+    float q = rintf(x * scale + bias);
+    if (q < 0.0f) q = 0.0f;
+    if (q > 255.0f) q = 255.0f;
+    return (uint8_t)q;
+}
+ORC_API void vxo_compact8(const float* c, int64_t n, uint8_t* out) {
+    for (int64_t i = 0; i < n; ++i) {
+        for (int j = 0; j < 3; ++j) out[i * 6 + j] = quant8(c[i * 6 + j], 255.0f, 0.0f);
+        for (int j = 3; j < 6; ++j) out[i * 6 + j] = quant8(c[i * 6 + j], 127.5f, 127.5f);
+    }
+}
+
 /* single normalised lobe from (m, M): S = M / m, weight m */
 static void single_lobe(vxo_level* L, int64_t v) {
     float m = L->mass[v];

@@ -62,7 +62,8 @@ class VxAllocator(C.Structure):
 EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_lod",
            "vx_level_release", "vx_status_string", "vx_last_cuda_error", "vx_profile_enable",
            "vx_profile_read", "vx_backward", "vx_backward_noalloc", "vx_batch_create", "vx_batch_run",
-           "vx_batch_level", "vx_batch_destroy", "vx_set_max_pairs_per_pass", "vx_batch_create_lod"]
+           "vx_batch_level", "vx_batch_destroy", "vx_set_max_pairs_per_pass", "vx_batch_create_lod",
+           "vx_export_compact8", "vx_tessellate_catmull_rom"]
 
 
 class VxInstance(C.Structure):
@@ -130,6 +131,10 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         lib.vx_batch_level.argtypes = [P, C.c_int, C.c_int, P, C.POINTER(VxLevel)]
         lib.vx_batch_destroy.restype = None
         lib.vx_batch_destroy.argtypes = [P]
+        lib.vx_tessellate_catmull_rom.restype = C.c_int
+        lib.vx_tessellate_catmull_rom.argtypes = [P, P, P, C.c_int64, C.c_int64, C.c_int, P, P, P]
+        lib.vx_export_compact8.restype = C.c_int
+        lib.vx_export_compact8.argtypes = [C.POINTER(VxLevel), P, P]
         lib.vx_backward_noalloc.restype = C.c_int
         lib.vx_backward_noalloc.argtypes = [C.POINTER(VxPrimitives), C.POINTER(VxGrid), P, C.c_int64, C.c_int,
                                             C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), P, P, P]
@@ -372,6 +377,35 @@ class Context:
                      lobe_count=v(L.lobe_count, n, torch.uint8, (n,)),
                      lobes=v(L.lobes, n * K * 28, torch.float32, (n, K, 7)),
                      compact=v(L.compact, n * K * 24, torch.float32, (n, K, 6)), block=None, _c=L)
+
+    def tessellate_catmull_rom(self, nodes: torch.Tensor, offsets: torch.Tensor, subdiv: int, stream=None):
+        """vx_tessellate_catmull_rom: spline nodes [P, 4] (xyz, radius) and offsets [F+1] ->
+        fiber control points [(P - F) * subdiv + F, 4] and their offsets [F+1]."""
+        nodes = nodes.contiguous()
+        offsets = offsets.contiguous()
+        _check(nodes, torch.float32, self.device, "nodes")
+        _check(offsets, torch.int64, self.device, "offsets")
+        F = offsets.shape[0] - 1
+        P = nodes.shape[0]
+        total = max((P - F) * int(subdiv) + F, 0)
+        out = torch.empty((max(total, 1), 4), dtype=torch.float32, device=self.device)
+        out_off = torch.empty((F + 1,), dtype=torch.int64, device=self.device)
+        st = self.lib.vx_tessellate_catmull_rom(self.h, C.c_void_p(nodes.data_ptr() if P else 0),
+                                                C.c_void_p(offsets.data_ptr()), F, P, int(subdiv),
+                                                C.c_void_p(out.data_ptr()), C.c_void_p(out_off.data_ptr()),
+                                                _stream(stream))
+        if st != 0:
+            raise self._err(st, "vx_tessellate_catmull_rom")
+        return out[:total], out_off
+
+    def export_compact8(self, level: Level, stream=None) -> torch.Tensor:
+        """vx_export_compact8: the level's lobes as 8-bit compact SGGX, uint8 [n, K, 6]."""
+        out = torch.zeros((max(level.num_voxels, 0), level.K, 6), dtype=torch.uint8, device=self.device)
+        st = self.lib.vx_export_compact8(C.byref(level._c), C.c_void_p(out.data_ptr() if out.numel() else 0),
+                                         _stream(stream))
+        if st != 0:
+            raise self._err(st, "vx_export_compact8")
+        return out
 
     def build_lod(self, level: Level, *, K: int = 1, dirs=None, num_levels: int = 0,
                   stream=None) -> list:

@@ -204,6 +204,44 @@ vx_status vx_profile_read(vx_context* ctx, vx_stage_time* out, int max_stages, i
     return VX_OK;
 }
 
+namespace {
+// one byte of the compact export: round-half-even of x * scale + bias, clamped to [0, 255]
+__device__ __forceinline__ uint8_t quantize8(float x, float scale, float bias) {
+    const float q = rintf(x * scale + bias);
+    return (uint8_t)fminf(fmaxf(q, 0.0f), 255.0f);
+}
+
+__global__ void k_export_compact8(const float* __restrict__ compact, const uint8_t* __restrict__ lobe_count,
+                                  int64_t n, int K, uint8_t* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // (voxel, lobe)
+    if (i >= n * K) return;
+    const int64_t v = i / K;
+    const int k = (int)(i - v * K);
+    uint8_t q[6] = {0, 0, 0, 0, 0, 0};
+    if (k < (int)lobe_count[v]) {
+        const float* c = compact + (size_t)i * 6;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) q[j] = quantize8(c[j], 255.0f, 0.0f);
+#pragma unroll
+        for (int j = 3; j < 6; ++j) q[j] = quantize8(c[j], 127.5f, 127.5f);
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) out[(size_t)i * 6 + j] = q[j];
+}
+}  // namespace
+
+vx_status vx_export_compact8(const vx_level* level, uint8_t* out, void* stream) {
+    if (!level) return VX_ERR_INVALID_ARG;
+    if (level->num_voxels == 0) return VX_OK;
+    if (!out || level->num_voxels < 0 || level->K < 1 || level->K > vx::kMaxK || !level->compact || !level->lobe_count)
+        return VX_ERR_INVALID_ARG;
+    const int64_t items = level->num_voxels * level->K;
+    const unsigned blocks = (unsigned)((items + 255) / 256);
+    k_export_compact8<<<blocks, 256, 0, (cudaStream_t)stream>>>(level->compact, level->lobe_count, level->num_voxels,
+                                                                level->K, out);
+    return cudaGetLastError() == cudaSuccess ? VX_OK : VX_ERR_CUDA;
+}
+
 void vx_level_release(vx_context* ctx, vx_level* level, void* stream) {
     if (!ctx || !level) return;
     if (level->block) vx_dev_free(ctx, level->block, (cudaStream_t)stream);

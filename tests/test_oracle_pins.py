@@ -460,3 +460,85 @@ def test_sggx_h_copies_when_few(dirs5000):
     out, merges = oracle.sggx_h(cand, 4, dirs5000)
     assert merges == []
     assert np.allclose(out[0], cand[1]) and np.allclose(out[1], cand[0])
+
+
+# ----------------------------------------------------------------------------
+# 8-bit compact SGGX (Sec. 4.3): closed-form byte values and the round-trip bound
+# ----------------------------------------------------------------------------
+def test_compact8_closed_form_values():
+    c = np.array([[0.0, 1.0, 0.5, -1.0, 1.0, 0.0],              # 0.5 * 255 = 127.5 -> 128 (even)
+                  [1.0 / 255, 2.0 / 255, 0.999, -0.5, 0.5, 1.0 / 127.5 - 1.0],
+                  [1.2, -0.1, 0.25, -1.3, 1.3, 0.3]], np.float32)  # clamped
+    q = oracle.compact8(c)
+    assert q.dtype == np.uint8
+    assert q[0].tolist() == [0, 255, 128, 0, 255, 128]            # 127.5 r + 127.5 at r = 0: 127.5 -> 128
+    assert q[1].tolist() == [1, 2, 255, 64, 191, 1]               # 63.75 -> 64, 191.25 -> 191
+    assert q[2].tolist() == [255, 0, 64, 0, 255, 166]             # 63.75 -> 64, 165.75 -> 166
+    # an isotropic lobe S = I/3: sigma = sqrt(1/3) -> 147.2 -> 147, r = 0 -> 128
+    iso = oracle.compact(np.array([1 / 3, 1 / 3, 1 / 3, 0, 0, 0], np.float32))
+    assert oracle.compact8(iso).tolist() == [147, 147, 147, 128, 128, 128]
+
+
+def test_compact8_round_trip_bound():
+    rng = np.random.default_rng(12)
+    c = np.concatenate([rng.uniform(0, 1, (5000, 3)), rng.uniform(-1, 1, (5000, 3))], axis=1).astype(np.float32)
+    q = oracle.compact8(c).astype(np.float64)
+    sig = q[:, :3] / 255.0
+    r = q[:, 3:] / 127.5 - 1.0
+    assert np.abs(sig - c[:, :3]).max() <= 0.5 / 255 + 1e-6
+    assert np.abs(r - c[:, 3:]).max() <= 0.5 / 127.5 + 1e-6
+
+
+# ----------------------------------------------------------------------------
+# Catmull-Rom spline fibers (Sec. 3.2): independent FP64 matrix form, linear precision
+# ----------------------------------------------------------------------------
+CR_BASIS = 0.5 * np.array([[0, 2, 0, 0], [-1, 0, 1, 0], [2, -5, 4, -1], [-1, 3, -3, 1]], np.float64)
+
+
+def cr_reference(nodes, S):
+    """FP64 reference: [1 t t^2 t^3] M [P0 P1 P2 P3]^T with reflected end nodes."""
+    P = nodes[:, :3].astype(np.float64)
+    n = P.shape[0]
+    ext = np.concatenate([2 * P[:1] - P[1:2], P, 2 * P[-1:] - P[-2:-1]]) if n > 1 else P
+    pts = []
+    for i in range(n - 1):
+        G = ext[i: i + 4]
+        for j in range(S):
+            t = j / S
+            pts.append(np.array([1, t, t * t, t ** 3]) @ CR_BASIS @ G)
+    pts.append(P[-1])
+    return np.array(pts)
+
+
+def test_catmull_rom_matches_matrix_form():
+    rng = np.random.default_rng(21)
+    sizes = [2, 3, 7, 1, 12]
+    nodes = np.concatenate([np.concatenate([rng.uniform(0, 4, (k, 3)), rng.uniform(0.1, 0.5, (k, 1))], 1)
+                            for k in sizes]).astype(np.float32)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    S = 6
+    ctrl, out_off = oracle.catmull_rom(nodes, off, S)
+    assert out_off.tolist() == [int((off[f] - f) * S + f) for f in range(len(sizes) + 1)]
+    for f, k in enumerate(sizes):
+        got = ctrl[out_off[f]: out_off[f + 1]]
+        assert got.shape[0] == (k - 1) * S + 1
+        ref = cr_reference(nodes[off[f]: off[f + 1]], S)
+        np.testing.assert_allclose(got[:, :3], ref, rtol=0, atol=1e-5)
+        # nodes are passed exactly (t = 0 of each span, and the closing node)
+        assert np.array_equal(got[::S, :3], nodes[off[f]: off[f + 1], :3])
+        # radius: linear between consecutive nodes
+        r = nodes[off[f]: off[f + 1], 3].astype(np.float64)
+        if k > 1:
+            t = (np.arange((k - 1) * S) % S) / S
+            i = np.arange((k - 1) * S) // S
+            np.testing.assert_allclose(got[:-1, 3], r[i] + t * (r[i + 1] - r[i]), rtol=1e-6)
+
+
+def test_catmull_rom_linear_precision():
+    # equally spaced nodes on a line: every sample is on the line at its uniform parameter
+    a = np.array([0.3, -1.2, 2.0]); d = np.array([0.7, 0.2, -0.4])
+    k, S = 9, 5
+    nodes = np.concatenate([a + np.arange(k)[:, None] * d, np.full((k, 1), 0.25)], 1).astype(np.float32)
+    ctrl, _ = oracle.catmull_rom(nodes, np.array([0, k]), S)
+    u = np.arange((k - 1) * S + 1) / S
+    np.testing.assert_allclose(ctrl[:, :3], a + u[:, None] * d, rtol=0, atol=2e-6)

@@ -234,6 +234,71 @@ def test_sggx_h_more_directions_than_one_pass(ctx):
         compare_level(g, r, f"level {lvl}", mu_max=prim_measure_max(w))
 
 
+def test_catmull_rom_splines(ctx, dirs5000):
+    """Spline fibers: the device tessellation equals the oracle's bit for bit, and the
+    tessellated fibers voxelize to the oracle's pyramid (a yarn whose polylines are
+    subsampled to every 8th node and re-tessellated with 8 points per span)."""
+    w = synth.config2(fibers_per_ply=6, segments=480, R=128, K=4)
+    off = w.fiber_offsets
+    keep = []
+    for f in range(len(off) - 1):
+        idx = np.arange(off[f], off[f + 1])
+        keep.append(np.unique(np.concatenate([idx[::8], idx[-1:]])))
+    nodes = np.concatenate([w.ctrl[k] for k in keep]).astype(np.float32)
+    noff = np.concatenate([[0], np.cumsum([len(k) for k in keep])]).astype(np.int64)
+    S = 8
+    ctrl_d, off_d = ctx.tessellate_catmull_rom(torch.from_numpy(nodes).to(DEV), torch.from_numpy(noff).to(DEV), S)
+    ctrl_o, off_o = oracle.catmull_rom(nodes, noff, S)
+    assert np.array_equal(off_d.cpu().numpy(), off_o)
+    assert np.array_equal(ctrl_d.cpu().numpy().view(np.uint32), ctrl_o.view(np.uint32))
+    ws = synth.Workload("spl", "fibers", w.grid, ctrl=ctrl_o, fiber_offsets=off_o, K=4)
+    L0 = ctx.voxelize(ws.grid, ctrl=ctrl_d, fiber_offsets=off_d)
+    pyr = ctx.build_lod(L0, K=4, dirs=torch.from_numpy(dirs5000).to(DEV))
+    torch.cuda.synchronize()
+    got = [L0.host()] + [p.host() for p in pyr]
+    ref0 = oracle.voxelize(ws)
+    refs = [ref0] + oracle.build_pyramid(ref0, 128, 4, dirs5000)
+    for lvl, (g, r) in enumerate(zip(got, refs)):
+        compare_level(g, r, f"splines level {lvl}", mu_max=prim_measure_max(ws))
+    # a spline without nodes is rejected
+    with pytest.raises(vx.VxError):
+        ctx.tessellate_catmull_rom(torch.from_numpy(nodes).to(DEV),
+                                   torch.tensor([0, 3, 3, len(nodes)], dtype=torch.int64, device=DEV), S)
+
+
+def test_export_compact8(ctx, dirs5000):
+    """8-bit compact SGGX export of every level of the K = 4 yarn pyramid against the
+    oracle's quantization of its own compact parameters.  Level 0 (S = M/m, bit-exact
+    inputs) must match byte for byte; on coarser levels the lobes agree to 1e-5, so a byte
+    may differ by one only where the oracle's scaled value lies within 1e-3 of a rounding
+    boundary.  Lobes past lobe_count are zero."""
+    w = synth.config2(fibers_per_ply=8, segments=500, R=128, K=4)
+    L0 = ctx.voxelize(w.grid, ctrl=torch.from_numpy(w.ctrl).to(DEV),
+                      fiber_offsets=torch.from_numpy(w.fiber_offsets).to(DEV))
+    pyr = ctx.build_lod(L0, K=4, dirs=torch.from_numpy(dirs5000).to(DEV))
+    got = [ctx.export_compact8(lv).cpu().numpy() for lv in [L0] + pyr]
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, 128, 4, dirs5000)
+    scale = np.array([255.0] * 3 + [127.5] * 3)
+    bias = np.array([0.0] * 3 + [127.5] * 3)
+    for lvl, (g, r) in enumerate(zip(got, refs)):
+        # (the oracle's level 0 is stored with the pyramid's K; it holds at most one lobe)
+        K = g.shape[1]
+        assert g.shape[0] == r["keys"].shape[0] and r["lobe_count"].max() <= K
+        comp = r["compact"][:, :K]
+        q = oracle.compact8(comp)
+        live = np.arange(K)[None, :] < r["lobe_count"][:, None]
+        q[~live] = 0
+        if lvl == 0:
+            assert np.array_equal(g, q), "level 0: bytes differ"
+            continue
+        x = comp.astype(np.float64) * scale + bias
+        near = np.abs(x - np.floor(x) - 0.5) < 1e-3
+        diff = g.astype(np.int32) - q.astype(np.int32)
+        assert np.abs(diff).max() <= 1, f"level {lvl}"
+        assert np.all((diff == 0) | (near & live[..., None])), f"level {lvl}: bytes differ away from a boundary"
+
+
 # ----------------------------------------------------------------------------
 # edge cases
 # ----------------------------------------------------------------------------
