@@ -165,11 +165,15 @@ VX_API vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, const 
  *   K: lobe cap per voxel, 1..8 (1 = the plain 2x2x2 moment aggregation of Sec. 4.3).
  *   n_samples, dirs: the N fixed unit directions (device, [n_samples][3] float) each SGGX
  *     lobe is sampled with for its histogram (Sec. 4.4, N = 5000 in the paper); only read
- *     when K > 1.  1 <= n_samples <= 65536. */
+ *     when K > 1.  1 <= n_samples <= 65536.
+ *   merge: the lobe a merge of SGGX-H creates (K > 1).  0: the second moment of the two
+ *     lobes' pooled samples, (M^_i + M^_j) / 2; 1: the moments weighted by the lobes'
+ *     masses, (w_i M^_i + w_j M^_j) / (w_i + w_j).  Other values: VX_ERR_INVALID_ARG. */
 typedef struct {
     int32_t num_levels;
     int32_t K;
     int32_t n_samples;
+    int32_t merge;
     const float* dirs;
 } vx_lod_params;
 

@@ -86,7 +86,7 @@ def _load():
             lib.vxo_hist_dist.restype = C.c_int64
             lib.vxo_hist_dist.argtypes = [P, P]
             lib.vxo_sggx_h.restype = C.c_int
-            lib.vxo_sggx_h.argtypes = [P, C.c_int, C.c_int, P, C.c_int, P, P]
+            lib.vxo_sggx_h.argtypes = [P, C.c_int, C.c_int, P, C.c_int, P, P, C.c_int]
             lib.vxo_voxelize_fibers.restype = C.c_int
             lib.vxo_voxelize_fibers.argtypes = [P, P, C.c_int64, P, C.POINTER(_Grid), C.c_int,
                                                 C.POINTER(_Level)]
@@ -94,7 +94,7 @@ def _load():
             lib.vxo_voxelize_tris.argtypes = [P, C.c_int64, P, C.POINTER(_Grid), C.c_int,
                                               C.POINTER(_Level)]
             lib.vxo_lod_step.restype = C.c_int
-            lib.vxo_lod_step.argtypes = [C.POINTER(_Level), C.c_int, P, C.c_int, C.POINTER(_Level)]
+            lib.vxo_lod_step.argtypes = [C.POINTER(_Level), C.c_int, P, C.c_int, C.POINTER(_Level), C.c_int]
             lib.vxo_level_free.restype = None
             lib.vxo_level_free.argtypes = [C.POINTER(_Level)]
             lib.vxo_fiber_voxels.restype = C.c_int
@@ -255,7 +255,7 @@ def hist_dist(a, b) -> int:
     return int(_load().vxo_hist_dist(_ptr(a), _ptr(b)))
 
 
-def sggx_h(cand, K, dirs):
+def sggx_h(cand, K, dirs, merge: int = 0):
     """cand [n,7] (S6 + weight) -> (lobes [m,7] sorted by weight desc, merges [(i,j)])."""
     cand = _f32(cand).reshape(-1, 7)
     n = int(cand.shape[0])
@@ -263,7 +263,7 @@ def sggx_h(cand, K, dirs):
     out = np.zeros((max(n, 1), 7), dtype=np.float32)
     merges = np.zeros((max(n, 1), 2), dtype=np.int32)
     m = _load().vxo_sggx_h(_ptr(cand), n, int(K), _ptr(dirs), int(dirs.shape[0]), _ptr(out),
-                           _ptr(merges))
+                           _ptr(merges), int(merge))
     return out[:m].copy(), [tuple(x) for x in merges[: max(0, n - m)]]
 
 
@@ -298,23 +298,24 @@ def voxelize(workload, K=None) -> dict:
     return voxelize_fibers(workload.ctrl, workload.fiber_offsets, workload.grid, workload.weights, K)
 
 
-def lod_step(level: dict, K: int, dirs) -> dict:
+def lod_step(level: dict, K: int, dirs, merge: int = 0) -> dict:
+    """One LoD level (Sec. 4.2-4.4); merge 0 = pooled-sample merge, 1 = mass-weighted."""
     keep = []
     Lin = _dict_to_level(level, keep)
     dirs = _f32(dirs).reshape(-1, 3)
     Lout = _Level()
-    _load().vxo_lod_step(C.byref(Lin), int(K), _ptr(dirs), int(dirs.shape[0]), C.byref(Lout))
+    _load().vxo_lod_step(C.byref(Lin), int(K), _ptr(dirs), int(dirs.shape[0]), C.byref(Lout), int(merge))
     d = _level_to_dict(Lout)
     _load().vxo_level_free(C.byref(Lout))
     return d
 
 
-def build_pyramid(level0: dict, resolution: int, K: int, dirs, num_levels: int = 0) -> list:
+def build_pyramid(level0: dict, resolution: int, K: int, dirs, num_levels: int = 0, merge: int = 0) -> list:
     """Levels 1..L (L = log2(resolution) when num_levels == 0)."""
     L = int(round(np.log2(resolution))) if num_levels == 0 else num_levels
     out, cur = [], level0
     for _ in range(L):
-        cur = lod_step(cur, K, dirs)
+        cur = lod_step(cur, K, dirs, merge)
         out.append(cur)
     return out
 

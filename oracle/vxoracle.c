@@ -899,9 +899,12 @@ ORC_API int64_t vxo_hist_dist(const int32_t* a, const int32_t* b) {
 
 /* Agglomerative SGGX-H of n candidate lobes (S6 + weight each, in candidate order) to at
  * most K lobes.  Output lobes sorted by weight (descending), ties by creation index.
- * Returns the output count; merges_out (optional) receives (i, j) creation ids per merge. */
+ * Returns the output count; merges_out (optional) receives (i, j) creation ids per merge.
+ * merge 0: the merged lobe is the second moment of the two lobes' pooled samples,
+ * (M^_i + M^_j) / 2; merge 1: the same moments weighted by the lobes' masses,
+ * (w_i M^_i + w_j M^_j) / (w_i + w_j). */
 ORC_API int vxo_sggx_h(const float* cand, int n, int K, const float* dirs, int N,
-                       float* out, int32_t* merges_out) {
+                       float* out, int32_t* merges_out, int merge) {
     int cap = 2 * n + 1;
     float* S = (float*)malloc(sizeof(float) * 6 * (size_t)cap);
     float* wgt = (float*)malloc(sizeof(float) * (size_t)cap);
@@ -927,7 +930,13 @@ ORC_API int vxo_sggx_h(const float* cand, int n, int K, const float* dirs, int N
                     if (bi < 0 || dd < best) { best = dd; bi = i; bj = j; }
                 }
             }
-            for (int c = 0; c < 6; ++c) S[6 * next + c] = (Mh[6 * bi + c] + Mh[6 * bj + c]) * 0.5f;
+            const float wi = wgt[bi], wj = wgt[bj], ws = wgt[bi] + wgt[bj];
+            for (int c = 0; c < 6; ++c) {
+                if (merge == 1 && ws > 0.0f)
+                    S[6 * next + c] = (wi * Mh[6 * bi + c] + wj * Mh[6 * bj + c]) / ws;
+                else
+                    S[6 * next + c] = (Mh[6 * bi + c] + Mh[6 * bj + c]) * 0.5f;
+            }
             wgt[next] = wgt[bi] + wgt[bj];
             vxo_sample_lobe(S + 6 * next, dirs, N, H + 6 * next, Mh + 6 * next);
             alive[bi] = 0; alive[bj] = 0; alive[next] = 1;
@@ -955,7 +964,7 @@ ORC_API int vxo_sggx_h(const float* cand, int n, int K, const float* dirs, int N
 /* ------------------------------------------------------------------------- */
 /* LoD: level l -> l+1 (Sec. 4.2 density by projection, 4.3 2x2x2, 4.4 SGGX-H) */
 /* ------------------------------------------------------------------------- */
-ORC_API int vxo_lod_step(const vxo_level* in, int K, const float* dirs, int N, vxo_level* out) {
+ORC_API int vxo_lod_step(const vxo_level* in, int K, const float* dirs, int N, vxo_level* out, int merge) {
     int64_t np = 0;
     for (int64_t i = 0; i < in->n; ++i)
         if (i == 0 || (in->keys[i] >> 3) != (in->keys[i - 1] >> 3)) ++np;
@@ -1007,7 +1016,7 @@ ORC_API int vxo_lod_step(const vxo_level* in, int K, const float* dirs, int N, v
             single_lobe(out, v);
         } else {
             float res[16 * 7];
-            int nl = vxo_sggx_h(cand, nc, K, dirs, N, res, NULL);
+            int nl = vxo_sggx_h(cand, nc, K, dirs, N, res, NULL, merge);
             float* lo = out->lobes + (size_t)v * K * 7;
             memcpy(lo, res, (size_t)nl * 7 * sizeof(float));
             for (int l = 0; l < nl; ++l) vxo_compact(lo + 7 * l, out->compact + ((size_t)v * K + l) * 6);

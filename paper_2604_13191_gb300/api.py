@@ -48,7 +48,7 @@ class VxLevel(C.Structure):
 
 class VxLodParams(C.Structure):
     _fields_ = [("num_levels", C.c_int32), ("K", C.c_int32), ("n_samples", C.c_int32),
-                ("dirs", C.c_void_p)]
+                ("merge", C.c_int32), ("dirs", C.c_void_p)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -348,12 +348,13 @@ class Context:
             raise self._err(st, "vx_backward")
         return g_ctrl, g_w
 
-    def batch(self, instances, *, K: int = 1, dirs=None, headroom: float = 0.125, stream=None) -> "Batch":
+    def batch(self, instances, *, K: int = 1, dirs=None, headroom: float = 0.125, merge: str = "pooled",
+              stream=None) -> "Batch":
         """vx_batch_create_lod: instances = list of dicts with kind ("triangles" | "fibers"),
         grid, and tri_verts [T,3,4] or ctrl [P,4] + fiber_offsets [F+1] (+ optional weights),
         CUDA tensors; K lobes per voxel above level 0 (dirs [N,3] when K > 1).  Returns a
         Batch whose run() replays one captured graph."""
-        return Batch(self, instances, headroom, stream, K=K, dirs=dirs)
+        return Batch(self, instances, headroom, stream, K=K, dirs=dirs, merge=merge)
 
     def _view_level(self, L: VxLevel, keep) -> Level:
         """Typed tensors over a level whose arrays live in blocks of this context's allocator."""
@@ -408,11 +409,13 @@ class Context:
         return out
 
     def build_lod(self, level: Level, *, K: int = 1, dirs=None, num_levels: int = 0,
-                  stream=None) -> list:
-        """vx_build_lod: levels level+1 .. level+L (L = num_levels, 0 = down to 1^3)."""
+                  merge: str = "pooled", stream=None) -> list:
+        """vx_build_lod: levels level+1 .. level+L (L = num_levels, 0 = down to 1^3).  merge:
+        "pooled" (the two lobes' pooled samples) or "mass" (their moments weighted by mass)."""
         prm = VxLodParams()
         prm.num_levels = int(num_levels)
         prm.K = int(K)
+        prm.merge = _merge_mode(merge)
         if dirs is not None:
             d = dirs.contiguous()
             _check(d, torch.float32, self.device, "dirs")
@@ -425,6 +428,13 @@ class Context:
         if st != 0:
             raise self._err(st, "vx_build_lod")
         return [self._wrap(outs[i]) for i in range(L)]
+
+
+def _merge_mode(merge) -> int:
+    modes = {"pooled": 0, "mass": 1}
+    if merge not in modes:
+        raise ValueError(f"merge: expected one of {sorted(modes)}, got {merge!r}")
+    return modes[merge]
 
 
 def _check(t, dtype, device, name):
@@ -533,7 +543,8 @@ class Batch:
     """A planned batch (vx_batch_*): one captured CUDA graph runs every instance from its
     primitives to all of its pyramid levels (K lobes per voxel above level 0)."""
 
-    def __init__(self, ctx: Context, instances, headroom=0.125, stream=None, K: int = 1, dirs=None):
+    def __init__(self, ctx: Context, instances, headroom=0.125, stream=None, K: int = 1, dirs=None,
+                 merge: str = "pooled"):
         self.ctx = ctx
         lib = ctx.lib
         tris = [i for i in instances if i["kind"] == "triangles"]
@@ -595,6 +606,7 @@ class Batch:
             fp.weights = None if fw is None else fw.data_ptr()
         lod = VxLodParams()
         lod.num_levels, lod.K, lod.n_samples, lod.dirs = 0, int(K), 0, None
+        lod.merge = _merge_mode(merge)
         if K > 1:
             if dirs is None:
                 raise ValueError("K > 1 needs the direction set (dirs [N,3])")

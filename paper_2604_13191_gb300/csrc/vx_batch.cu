@@ -293,6 +293,7 @@ struct vx_batch {
     float headroom = 0.125f;
     int K = 1;                              // lobes per voxel of the levels above 0
     int n_dirs = 0;
+    int merge = 0;                          // SGGX-H merge rule (vx_lod_params.merge)
     float4* dirs4 = nullptr;                // direction table of the lobe histograms (K > 1)
     cudaStream_t cap_stream = nullptr;
     cudaStream_t cap_stream2 = nullptr;     // the triangle branch of the captured graph
@@ -466,7 +467,7 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
         if (vx_lod_step_batched(&S.lv[l - 1], S.linst[l - 1], nprev, S.cap_v[l - 1], &S.lv[l], S.linst[l],
                                 C + C_LVL + l, S.cap_v[l], S.flags, S.idx, S.starts, S.part, C + C_LVL + 16 + l,
                                 C + C_ERR, b->dirs4, b->n_dirs, S.work[l], C + C_CLUSTER,
-                                l > 1 ? S.stats[l - 1] : nullptr, S.stats[l], s) != cudaSuccess)
+                                l > 1 ? S.stats[l - 1] : nullptr, S.stats[l], b->merge, s) != cudaSuccess)
             return VX_ERR_CUDA;
         k_inst_offsets<<<(S.ninst + 1 + 127) / 128, 128, 0, s>>>(S.linst[l], C + C_LVL + l, S.ninst,
                                                                  S.inst_start + (size_t)l * (S.ninst + 1));
@@ -495,6 +496,7 @@ extern "C" vx_status vx_batch_create_lod(vx_context* ctx, const vx_primitives* t
     if (K < 1 || K > vx::kMaxK) return VX_ERR_UNSUPPORTED;
     if (lod && lod->num_levels != 0) return VX_ERR_UNSUPPORTED;
     if (K > 1 && (!lod->dirs || lod->n_samples < 1 || lod->n_samples > 65536)) return VX_ERR_INVALID_ARG;
+    if (lod && lod->merge != 0 && lod->merge != 1) return VX_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     ctx->last_stream = s;
     vx_batch* b = new (std::nothrow) vx_batch();
@@ -550,6 +552,7 @@ extern "C" vx_status vx_batch_create_lod(vx_context* ctx, const vx_primitives* t
     if (K > 1) {
         // the direction table, copied once: runs use the directions given here
         b->n_dirs = lod->n_samples;
+        b->merge = lod->merge;
         if ((st = balloc(b, (void**)&b->dirs4, (size_t)lod->n_samples * 16, s)) != VX_OK) return fail(st);
         if (vx_lod_batched_prepare(K, lod->dirs, lod->n_samples, b->dirs4, s) != cudaSuccess) return fail(VX_ERR_CUDA);
     }

@@ -128,7 +128,7 @@ cudaError_t vx_lod_step_batched(const vx_level* in, const uint16_t* inst_in, con
                                 vx_level* out, uint16_t* inst_out, uint32_t* np_dev, uint32_t cap_out,
                                 uint32_t* flags, uint32_t* idx, uint32_t* starts, uint32_t* partials, uint32_t* tmp,
                                 uint32_t* err, const float4* dirs4, int n_dirs, uint32_t* work, uint32_t* wcnt,
-                                const void* cst, void* pst, cudaStream_t s);
+                                const void* cst, void* pst, int merge, cudaStream_t s);
 cudaError_t vx_lod_batched_prepare(int K, const float* dirs, int n, float4* dirs4, cudaStream_t s);
 constexpr size_t kLobeStatsBytes = 48;   // per-lobe histogram + sample moment kept between levels
 

@@ -517,7 +517,8 @@ template <int G>
 __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32, G == 1 ? 7 : 0) k_sggx_cluster(
     LevelIn in, const uint32_t* __restrict__ starts, const uint32_t* __restrict__ work,
     const uint32_t* __restrict__ nwork_p, vx_level out, int K, const float4* __restrict__ dirs, int N,
-    const LobeStats* __restrict__ cst, LobeStats* __restrict__ pst, unsigned long long* __restrict__ nsampled) {
+    const LobeStats* __restrict__ cst, LobeStats* __restrict__ pst, unsigned long long* __restrict__ nsampled,
+    int merge) {
     extern __shared__ unsigned char smem_raw[];
     constexpr int GROUPS = (G == 1) ? CL_WARPS : 1;
     const int group = (G == 1) ? (int)(threadIdx.x >> 5) : 0;
@@ -632,7 +633,13 @@ __global__ void __launch_bounds__(G == 1 ? CL_WARPS * 32 : G * 32, G == 1 ? 7 : 
                 __syncthreads();
             }
             const int bi = (int)((best >> 8) & 0xffull), bj = (int)(best & 0xffull);
-            if (tid < 6) sm.S[next * 6 + tid] = (sm.Mh[bi * 6 + tid] + sm.Mh[bj * 6 + tid]) * 0.5f;
+            // merge 0: pooled samples, (M^_i + M^_j) / 2; merge 1: mass-weighted moments
+            if (tid < 6) {
+                const float wi = sm.w[bi], wj = sm.w[bj], ws = wi + wj;
+                sm.S[next * 6 + tid] = (merge == 1 && ws > 0.0f)
+                                           ? (wi * sm.Mh[bi * 6 + tid] + wj * sm.Mh[bj * 6 + tid]) / ws
+                                           : (sm.Mh[bi * 6 + tid] + sm.Mh[bj * 6 + tid]) * 0.5f;
+            }
             if (tid == 0) {
                 sm.w[next] = sm.w[bi] + sm.w[bj];
                 sm.alive[bi] = 0;
@@ -702,19 +709,19 @@ cudaError_t cluster_set_smem(int K) {
 // wcnt[0] holds the number of listed parents and wcnt[1] (zero) the take counter.
 void launch_cluster(const LevelIn& li, const uint32_t* starts, const uint32_t* work, const uint32_t* wcnt,
                     const vx_level& out, int K, const float4* dirs4, int N, const LobeStats* cst, LobeStats* pst,
-                    unsigned long long* nsampled, uint32_t n, cudaStream_t s) {
+                    unsigned long long* nsampled, uint32_t n, int merge, cudaStream_t s) {
     if (n > (uint32_t)(vx::kSMs * 16)) {
         const unsigned cb = (unsigned)std::min<size_t>((n + CL_WARPS - 1) / CL_WARPS, (size_t)vx::kSMs * 7);
         k_sggx_cluster<1><<<cb, CL_WARPS * 32, cluster_smem(1, K), s>>>(li, starts, work, wcnt, out, K, dirs4, N,
-                                                                          cst, pst, nsampled);
+                                                                          cst, pst, nsampled, merge);
     } else if (n > (uint32_t)vx::kSMs) {
         const unsigned cb = (unsigned)std::max<uint32_t>(1u, std::min<uint32_t>(n, vx::kSMs * 4));
         k_sggx_cluster<CL_BLOCK_WARPS><<<cb, CL_BLOCK_WARPS * 32, cluster_smem(CL_BLOCK_WARPS, K), s>>>(
-            li, starts, work, wcnt, out, K, dirs4, N, cst, pst, nsampled);
+            li, starts, work, wcnt, out, K, dirs4, N, cst, pst, nsampled, merge);
     } else {
         const unsigned cb = (unsigned)std::max<uint32_t>(1u, n);
         k_sggx_cluster<CL_WIDE_WARPS><<<cb, CL_WIDE_WARPS * 32, cluster_smem(CL_WIDE_WARPS, K), s>>>(
-            li, starts, work, wcnt, out, K, dirs4, N, cst, pst, nsampled);
+            li, starts, work, wcnt, out, K, dirs4, N, cst, pst, nsampled, merge);
     }
 }
 
@@ -775,6 +782,7 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
     if (K < 1 || K > vx::kMaxK) return VX_ERR_UNSUPPORTED;
     if (in->K < 1 || in->K > vx::kMaxK) return VX_ERR_INVALID_ARG;
     if (K > 1 && (!params->dirs || params->n_samples < 1 || params->n_samples > 65536)) return VX_ERR_INVALID_ARG;
+    if (params->merge != 0 && params->merge != 1) return VX_ERR_INVALID_ARG;
     for (int l = 0; l < L; ++l) memset(&out[l], 0, sizeof(vx_level));
     if (L == 0) return VX_OK;
     const uint32_t n0 = (uint32_t)in->num_voxels;
@@ -844,7 +852,8 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
         if (K > 1) {
             unsigned long long* cnt_dev = ctx->prof ? ctx->dev_lobe_count : nullptr;
             VX_LAUNCH(ctx, ST_SGGX_CLUSTER, s, launch_cluster(li, starts, work, misc + 40, out[l - 1], K, dirs4,
-                                                              params->n_samples, cst, pst, cnt_dev, ncur, s));
+                                                              params->n_samples, cst, pst, cnt_dev, ncur,
+                                                              params->merge, s));
             VX_CUDA_TRY(cudaGetLastError());
         }
     }
@@ -872,7 +881,7 @@ cudaError_t vx_lod_step_batched(const vx_level* in, const uint16_t* inst_in, con
                                 vx_level* out, uint16_t* inst_out, uint32_t* np_dev, uint32_t cap_out,
                                 uint32_t* flags, uint32_t* idx, uint32_t* starts, uint32_t* partials, uint32_t* tmp,
                                 uint32_t* err, const float4* dirs4, int n_dirs, uint32_t* work, uint32_t* wcnt,
-                                const void* cst, void* pst, cudaStream_t s) {
+                                const void* cst, void* pst, int merge, cudaStream_t s) {
     const unsigned gb = (unsigned)std::min<size_t>(grid_for(cap_in, 256), (size_t)vx::kSMs * 16);
     k_bparent_flags<<<gb, 256, 0, s>>>(in->keys, inst_in, n_dev, cap_in, flags);
     cudaError_t e = vx_scan_u32_scratch(flags, idx, cap_in, tmp, partials, s);
@@ -892,7 +901,7 @@ cudaError_t vx_lod_step_batched(const vx_level* in, const uint16_t* inst_in, con
                                     (const LobeStats*)cst, (LobeStats*)pst);
     if (K > 1)
         launch_cluster(li, starts, work, wcnt, *out, K, dirs4, n_dirs, (const LobeStats*)cst, (LobeStats*)pst, nullptr,
-                       cap_out, s);
+                       cap_out, merge, s);
     k_bparent_inst<<<gb, 256, 0, s>>>(inst_in, starts, np_dev, inst_out);
     return cudaGetLastError();
 }

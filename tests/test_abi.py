@@ -57,7 +57,7 @@ int main(void) {
   printf("vx_lod_params %zu\n", sizeof(vx_lod_params));
   printf("vx_allocator %zu\n", sizeof(vx_allocator));
   P(vx_primitives, weights) P(vx_primitives, fiber_offsets) P(vx_level, compact) P(vx_level, block)
-  P(vx_level, num_voxels) P(vx_lod_params, dirs) P(vx_grid, resolution)
+  P(vx_level, num_voxels) P(vx_lod_params, dirs) P(vx_lod_params, merge) P(vx_grid, resolution)
   return 0;
 }
 """
@@ -79,6 +79,7 @@ int main(void) {
     assert int(got["vx_level.block"]) == api.VxLevel.block.offset
     assert int(got["vx_level.num_voxels"]) == api.VxLevel.num_voxels.offset
     assert int(got["vx_lod_params.dirs"]) == api.VxLodParams.dirs.offset
+    assert int(got["vx_lod_params.merge"]) == api.VxLodParams.merge.offset
     assert int(got["vx_grid.resolution"]) == api.VxGrid.resolution.offset
 
 

@@ -542,3 +542,25 @@ def test_catmull_rom_linear_precision():
     ctrl, _ = oracle.catmull_rom(nodes, np.array([0, k]), S)
     u = np.arange((k - 1) * S + 1) / S
     np.testing.assert_allclose(ctrl[:, :3], a + u[:, None] * d, rtol=0, atol=2e-6)
+
+
+# ----------------------------------------------------------------------------
+# SGGX-H merge rules (C12 and the mass-weighted option)
+# ----------------------------------------------------------------------------
+def test_sggx_h_merge_rules_two_lobes():
+    """Two lobes merged into one: the pooled rule gives (M^_1 + M^_2) / 2, the mass-weighted
+    rule (w_1 M^_1 + w_2 M^_2) / (w_1 + w_2), with M^ each lobe's own sample moment."""
+    dirs = synth.sample_directions(5000)
+    S1 = np.array([0.8, 0.15, 0.05, 0.1, 0.0, 0.02], np.float32)
+    S2 = np.array([0.1, 0.2, 0.7, 0.0, -0.05, 0.1], np.float32)
+    w1, w2 = 3.0, 0.5
+    cand = np.array([list(S1) + [w1], list(S2) + [w2]], np.float32)
+    _, M1 = oracle.sample_lobe(S1, dirs)
+    _, M2 = oracle.sample_lobe(S2, dirs)
+    pooled, _ = oracle.sggx_h(cand, 1, dirs, merge=0)
+    mass, _ = oracle.sggx_h(cand, 1, dirs, merge=1)
+    np.testing.assert_allclose(pooled[0, :6], (M1.astype(np.float64) + M2) / 2, rtol=0, atol=1e-7)
+    np.testing.assert_allclose(mass[0, :6], (w1 * M1.astype(np.float64) + w2 * M2) / (w1 + w2), rtol=0, atol=1e-6)
+    assert pooled[0, 6] == mass[0, 6] == np.float32(w1 + w2)
+    # the mass-weighted lobe leans towards the heavier lobe
+    assert abs(mass[0, 0] - M1[0]) < abs(pooled[0, 0] - M1[0])

@@ -220,6 +220,23 @@ def test_yarn_reduced_sggx_h(ctx, dirs5000):
     assert clustered > 100
 
 
+def test_sggx_h_mass_weighted_merge(ctx, dirs5000):
+    """The mass-weighted merge option on the reduced yarn: every level against the oracle
+    run with the same rule."""
+    w = synth.config2(fibers_per_ply=8, segments=500, R=128, K=4)
+    L0 = ctx.voxelize(w.grid, ctrl=torch.from_numpy(w.ctrl).to(DEV),
+                      fiber_offsets=torch.from_numpy(w.fiber_offsets).to(DEV))
+    pyr = ctx.build_lod(L0, K=4, dirs=torch.from_numpy(dirs5000).to(DEV), merge="mass")
+    torch.cuda.synchronize()
+    got = [L0.host()] + [p.host() for p in pyr]
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, 128, 4, dirs5000, merge=1)
+    for lvl, (g, r) in enumerate(zip(got, refs)):
+        compare_level(g, r, f"level {lvl}", mu_max=prim_measure_max(w))
+    with pytest.raises(ValueError):
+        ctx.build_lod(L0, K=4, dirs=torch.from_numpy(dirs5000).to(DEV), merge="median")
+
+
 def test_sggx_h_more_directions_than_one_pass(ctx):
     """The same yarn with N = 33,000 directions: above 32 x 1024, so the warp tier (levels
     1-2 here, over 2,432 parents) samples through its general loop with 64-bit partial sums,
