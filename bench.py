@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-splines", action="store_true")
+    ap.add_argument("--no-sampled", action="store_true")
     ap.add_argument("--woven", type=int, default=0,
                     help="also time the woven patch at 2048^3 with this many warp and weft yarns (16 = the "
                          "full patch)")
@@ -347,6 +348,11 @@ def main():
     if not args.no_splines:
         splines = spline_fibers(ctx, dev, args.steps, dirs)
 
+    # ---- the paper's sample-based level 0 against the exact one -----------------------------
+    sampled = None
+    if not args.no_sampled:
+        sampled = sampled_vs_exact(ctx, dev, args.steps)
+
     # ---- adjoint vs forward on the differentiation workload ---------------------------------
     adjoint = None
     if not args.no_adjoint:
@@ -384,6 +390,7 @@ def main():
         "clocks": clk,
         "batched": batched,
         "splines": splines,
+        "sampled": sampled,
         "adjoint": adjoint,
     }
     if woven is not None:
@@ -521,6 +528,40 @@ def spline_fibers(ctx, dev, steps, dirs):
                         "(768k capsules), 512^3, K=4, N=5000",
             "nodes": int(nodes.shape[0]), "subdiv": S, "prims": n_caps, "tessellate_ms": statistics.mean(tess),
             "ms_per_step": statistics.mean(total), "prims_per_s": n_caps / (statistics.mean(total) * 1e-3)}
+
+
+def sampled_vs_exact(ctx, dev, steps, samples=8):
+    """The paper's sample-based level 0 (axis samples per segment, Sec. 3.2-3.3) against the
+    exact level 0 on the bench yarn: time, and occupancy / voxel / mass totals relative to the
+    exact path (CUDA events; totals by tensor sums)."""
+    import torch
+    w = synth.config2()
+    ctrl = torch.from_numpy(w.ctrl).to(dev)
+    off = torch.from_numpy(w.fiber_offsets).to(dev)
+    ms = []
+    for i in range(steps + 2):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        Ls = ctx.voxelize_sampled(w.grid, ctrl=ctrl, fiber_offsets=off, samples=samples, num_prims=w.num_prims)
+        b.record()
+        torch.cuda.synchronize()
+        if i >= 2:
+            ms.append(a.elapsed_time(b))
+        if i < steps + 1:
+            del Ls
+    Le = ctx.voxelize(w.grid, ctrl=ctrl, fiber_offsets=off, num_prims=w.num_prims)
+    occ_s = int(Ls.occ.to(torch.int64).sum())
+    occ_e = int(Le.occ.to(torch.int64).sum())
+    out = {"workload": f"the bench yarn (768k capsules) at 512^3, {samples} axis samples per segment",
+           "samples_per_segment": samples, "ms": statistics.mean(ms),
+           "prims_per_s": w.num_prims / (statistics.mean(ms) * 1e-3),
+           "voxels": int(Ls.num_voxels), "voxels_exact": int(Le.num_voxels),
+           "occupied_subcells_ratio": occ_s / max(occ_e, 1),
+           "mass_ratio": float(Ls.mass.double().sum() / Le.mass.double().sum())}
+    del Ls, Le
+    return out
 
 
 def adjoint_vs_forward(ctx, dev, steps):

@@ -87,6 +87,9 @@ def _load():
             lib.vxo_hist_dist.argtypes = [P, P]
             lib.vxo_sggx_h.restype = C.c_int
             lib.vxo_sggx_h.argtypes = [P, C.c_int, C.c_int, P, C.c_int, P, P, C.c_int]
+            lib.vxo_voxelize_fibers_sampled.restype = C.c_int
+            lib.vxo_voxelize_fibers_sampled.argtypes = [P, P, C.c_int64, P, C.POINTER(_Grid), C.c_int,
+                                                        C.POINTER(_Level)]
             lib.vxo_voxelize_fibers.restype = C.c_int
             lib.vxo_voxelize_fibers.argtypes = [P, P, C.c_int64, P, C.POINTER(_Grid), C.c_int,
                                                 C.POINTER(_Level)]
@@ -275,6 +278,21 @@ def voxelize_fibers(ctrl, offsets, grid, weights=None, K=1) -> dict:
     G = _grid(grid)
     _load().vxo_voxelize_fibers(_ptr(ctrl), _ptr(offsets), int(offsets.shape[0] - 1), _ptr(w),
                                 C.byref(G), int(K), C.byref(L))
+    d = _level_to_dict(L)
+    _load().vxo_level_free(C.byref(L))
+    return d
+
+
+def voxelize_fibers_sampled(ctrl, offsets, grid, samples: int, weights=None) -> dict:
+    """Sample-based level 0 of fiber segments: `samples` axis samples per segment, each
+    marking one sub-cell and carrying 1/samples of the segment's measure (Sec. 3.2-3.3)."""
+    ctrl = _f32(ctrl).reshape(-1, 4)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    w = None if weights is None else _f32(weights)
+    L = _Level()
+    G = _grid(grid)
+    _load().vxo_voxelize_fibers_sampled(_ptr(ctrl), _ptr(offsets), int(offsets.shape[0] - 1), _ptr(w),
+                                        C.byref(G), int(samples), C.byref(L))
     d = _level_to_dict(L)
     _load().vxo_level_free(C.byref(L))
     return d

@@ -739,6 +739,68 @@ ORC_API int vxo_voxelize_fibers(const float* ctrl, const int64_t* offsets, int64
     return 0;
 }
 
+/* Sample-based voxelization of fiber segments (the paper's vertex-map sampling, Sec. 3.2-3.3,
+ * as a comparison workload): S samples per segment on its axis at t_j = (j + 1/2) / S, each
+ * carrying 1/S of the segment's measure.  A sample at grid point u = A + t_j (B - A) marks
+ * the sub-cell floor(8 (u - floor(u))) of voxel floor(u) (dropped outside [0, R)^3) and
+ * adds c = (w pi r^2 |B - A|) / S and c T(t) to that voxel, summed in sample order
+ * (segment-major).  FP32 in this order. */
+ORC_API int vxo_voxelize_fibers_sampled(const float* ctrl, const int64_t* offsets, int64_t F,
+                                        const float* weights, const vxo_grid* g, int S, vxo_level* out) {
+    const float s = 1.0f / g->voxel_size;
+    const int R = g->resolution;
+    recs_t recs = {0, 0, 0};
+    int64_t prim = 0;
+    for (int64_t f = 0; f < F; ++f) {
+        for (int64_t c = offsets[f]; c + 1 < offsets[f + 1]; ++c, ++prim) {
+            const float* pa = ctrl + 4 * c;
+            const float* pb = ctrl + 4 * (c + 1);
+            float A[3], B[3];
+            for (int i = 0; i < 3; ++i) {
+                A[i] = (pa[i] - g->origin[i]) * s;
+                B[i] = (pb[i] - g->origin[i]) * s;
+            }
+            const float rg = ((pa[3] + pb[3]) * 0.5f) * s;
+            const float w = weights ? weights[prim] : 1.0f;
+            const float d[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+            const float dn = sqrtf((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+            float t[3] = {0, 0, 0};
+            if (dn > 0.0f) { t[0] = d[0] / dn; t[1] = d[1] / dn; t[2] = d[2] / dn; }
+            const float mu = (3.14159265358979f * (rg * rg)) * dn;
+            const float cs = (w * mu) / (float)S;
+            const double cs64 = (double)w * (3.141592653589793 * (double)rg * (double)rg) *
+                                sqrt((double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2]) / S;
+            for (int j = 0; j < S; ++j) {
+                const float tj = ((float)j + 0.5f) / (float)S;
+                float u[3];
+                int v[3], sc[3], inside = 1;
+                for (int i = 0; i < 3; ++i) {
+                    u[i] = A[i] + tj * d[i];
+                    const float fl = floorf(u[i]);
+                    if (!(u[i] >= 0.0f) || !(u[i] < (float)R)) inside = 0;
+                    v[i] = (int)fl;
+                    int k = (int)((u[i] - fl) * 8.0f);
+                    sc[i] = k > 7 ? 7 : k;
+                }
+                if (!inside) continue;
+                rec_t x;
+                memset(x.mask, 0, sizeof(x.mask));
+                mask_set(x.mask, sc[0], sc[1], sc[2]);
+                x.key = vxo_morton((uint32_t)v[0], (uint32_t)v[1], (uint32_t)v[2]);
+                x.prim = prim * S + j;
+                x.c = cs;
+                x.dir[0] = t[0]; x.dir[1] = t[1]; x.dir[2] = t[2];
+                x.c64 = cs64;
+                x.dir64[0] = t[0]; x.dir64[1] = t[1]; x.dir64[2] = t[2];
+                recs_push(&recs, &x);
+            }
+        }
+    }
+    reduce_records(&recs, out, 1);
+    free(recs.r);
+    return 0;
+}
+
 /* Triangles: tri [T][3][4] (xyz, w unused). */
 ORC_API int vxo_voxelize_tris(const float* tri, int64_t T, const float* weights,
                               const vxo_grid* g, int K, vxo_level* out) {

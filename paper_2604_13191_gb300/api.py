@@ -63,7 +63,7 @@ EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_l
            "vx_level_release", "vx_status_string", "vx_last_cuda_error", "vx_profile_enable",
            "vx_profile_read", "vx_backward", "vx_backward_noalloc", "vx_batch_create", "vx_batch_run",
            "vx_batch_level", "vx_batch_destroy", "vx_set_max_pairs_per_pass", "vx_batch_create_lod",
-           "vx_export_compact8", "vx_tessellate_catmull_rom"]
+           "vx_export_compact8", "vx_tessellate_catmull_rom", "vx_voxelize_sampled"]
 
 
 class VxInstance(C.Structure):
@@ -131,6 +131,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         lib.vx_batch_level.argtypes = [P, C.c_int, C.c_int, P, C.POINTER(VxLevel)]
         lib.vx_batch_destroy.restype = None
         lib.vx_batch_destroy.argtypes = [P]
+        lib.vx_voxelize_sampled.restype = C.c_int
+        lib.vx_voxelize_sampled.argtypes = [P, C.POINTER(VxPrimitives), C.POINTER(VxGrid), C.c_int, P,
+                                            C.POINTER(VxLevel)]
         lib.vx_tessellate_catmull_rom.restype = C.c_int
         lib.vx_tessellate_catmull_rom.argtypes = [P, P, P, C.c_int64, C.c_int64, C.c_int, P, P, P]
         lib.vx_export_compact8.restype = C.c_int
@@ -289,6 +292,19 @@ class Context:
         st = self.lib.vx_voxelize(self.h, C.byref(P), C.byref(G), s, C.byref(L))
         if st != 0:
             raise self._err(st, "vx_voxelize")
+        return self._wrap(L)
+
+    def voxelize_sampled(self, grid, *, ctrl, fiber_offsets, samples: int, weights=None, num_prims=None,
+                         stream=None) -> Level:
+        """vx_voxelize_sampled: the sample-based level 0 of fibers (`samples` axis samples per
+        segment), for comparison with voxelize()."""
+        keep = []
+        P = self._prims(None, ctrl, fiber_offsets, weights, num_prims, keep)
+        G = _grid(grid)
+        L = VxLevel()
+        st = self.lib.vx_voxelize_sampled(self.h, C.byref(P), C.byref(G), int(samples), _stream(stream), C.byref(L))
+        if st != 0:
+            raise self._err(st, "vx_voxelize_sampled")
         return self._wrap(L)
 
     def _prims(self, tri_verts, ctrl, fiber_offsets, weights, num_prims, keep):

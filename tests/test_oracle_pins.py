@@ -564,3 +564,34 @@ def test_sggx_h_merge_rules_two_lobes():
     assert pooled[0, 6] == mass[0, 6] == np.float32(w1 + w2)
     # the mass-weighted lobe leans towards the heavier lobe
     assert abs(mass[0, 0] - M1[0]) < abs(pooled[0, 0] - M1[0])
+
+
+# ----------------------------------------------------------------------------
+# Sample-based voxelization (Sec. 3.2-3.3, comparison workload)
+# ----------------------------------------------------------------------------
+def test_sampled_fibers_closed_form_and_subset_of_exact():
+    grid = synth.Grid((0.0, 0.0, 0.0), 1.0 / 8, 8)
+    # a segment along x through voxel centres (y = z = 0.5 voxel), 4 voxels long, 16 samples:
+    # 4 samples per voxel at x = 1/8, 3/8, 5/8, 7/8 -> sub-cells sx = 1, 3, 5, 7 of row (4, 4)
+    r = 0.01
+    ctrl = np.array([[0.0, 0.5 / 8, 0.5 / 8, r], [4.0 / 8, 0.5 / 8, 0.5 / 8, r]], np.float32)
+    L = oracle.voxelize_fibers_sampled(ctrl, np.array([0, 2]), grid, 16)
+    assert L["keys"].tolist() == [oracle.morton(i, 0, 0) for i in range(4)]
+    assert L["occ"].tolist() == [4, 4, 4, 4]
+    row = sum(1 << (sx + 8 * 4) for sx in (1, 3, 5, 7))
+    assert all(int(m[4]) == row and int(m[:4].sum()) == 0 for m in L["mask"])
+    mu = np.pi * (r * 8) ** 2 * 4.0
+    np.testing.assert_allclose(L["mass"], mu / 4, rtol=1e-6)
+    np.testing.assert_allclose(L["moment"][:, 0], mu / 4, rtol=1e-6)        # t = x: only xx
+    assert np.abs(L["moment"][:, 1:]).max() == 0.0
+    # random fibers: the mass of the samples inside the grid, and every sampled sub-cell is one
+    # the exact capsule test sets (a sample lies on the axis, inside the capsule)
+    ctrl, off, grid = synth.random_segments(6, 12, 16, seed=4, radius=(0.2, 1.0), step=(0.3, 2.0))
+    S = 6
+    Ls = oracle.voxelize_fibers_sampled(ctrl, off, grid, S)
+    Le = oracle.voxelize(synth.Workload("e", "fibers", grid, ctrl=ctrl, fiber_offsets=off))
+    idx = {int(k): i for i, k in enumerate(Le["keys"])}
+    for k, m in zip(Ls["keys"], Ls["mask"]):
+        e = Le["mask"][idx[int(k)]]
+        assert np.all((m & ~e) == 0)
+    assert Ls["occ"].sum() < Le["occ"].sum()

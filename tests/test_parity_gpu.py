@@ -283,6 +283,24 @@ def test_catmull_rom_splines(ctx, dirs5000):
                                    torch.tensor([0, 3, 3, len(nodes)], dtype=torch.int64, device=DEV), S)
 
 
+def test_sampled_fibers(ctx):
+    """The sample-based level 0 (4 axis samples per segment) of the reduced yarn against the
+    oracle's, and its sub-cells inside the exact path's (a sample lies inside its capsule)."""
+    w = synth.config2(fibers_per_ply=8, segments=500, R=128, K=1)
+    ctrl = torch.from_numpy(w.ctrl).to(DEV)
+    off = torch.from_numpy(w.fiber_offsets).to(DEV)
+    Ls = ctx.voxelize_sampled(w.grid, ctrl=ctrl, fiber_offsets=off, samples=4)
+    Le = ctx.voxelize(w.grid, ctrl=ctrl, fiber_offsets=off)
+    torch.cuda.synchronize()
+    gs, ge = Ls.host(), Le.host()
+    rs = oracle.voxelize_fibers_sampled(w.ctrl, w.fiber_offsets, w.grid, 4)
+    compare_level(gs, rs, "sampled", mu_max=prim_measure_max(w))
+    pos = np.searchsorted(ge["keys"], gs["keys"])
+    assert np.array_equal(ge["keys"][pos], gs["keys"])
+    assert np.all((gs["mask"] & ~ge["mask"][pos]) == 0)
+    assert gs["occ"].sum() < ge["occ"].sum()
+
+
 def test_export_compact8(ctx, dirs5000):
     """8-bit compact SGGX export of every level of the K = 4 yarn pyramid against the
     oracle's quantization of its own compact parameters.  Level 0 (S = M/m, bit-exact
