@@ -291,14 +291,19 @@ VX_API vx_status vx_batch_level(vx_batch* batch, int instance, int level, void* 
 /* Frees the batch's buffers and graph. */
 VX_API void vx_batch_destroy(vx_batch* batch);
 
-/* Sample-based level 0 of fiber segments: the paper's vertex-map sampling (Sec. 3.2-3.3,
- * equally spaced samples along t gathered per voxel), a comparison workload for the exact
- * path of vx_voxelize.  Each segment gives samples_per_segment samples on its axis at
- * t_j = (j + 1/2) / S; a sample marks the sub-cell of its point in its voxel (samples outside
- * [0, R)^3 are dropped) and carries 1/S of the segment's measure w pi r^2 |B - A| and the
- * matching share of the moment.  out0 is a level like vx_voxelize's (K = 1), summed in sample
- * order.  Fibers only, R <= 1024 (VX_ERR_UNSUPPORTED otherwise); num_prims *
- * samples_per_segment < 2^31 (VX_ERR_CAPACITY).  Synchronises the stream once. */
+/* Sample-based level 0: the paper's vertex-map sampling (Sec. 3.2-3.3, samples generated
+ * from kernel indices and gathered per voxel), a comparison workload for the exact path of
+ * vx_voxelize.  S = samples_per_segment.
+ *   fibers:    S samples per segment on its axis at t_j = (j + 1/2) / S, each carrying 1/S of
+ *              w pi r^2 |B - A|;
+ *   triangles: max(1, ceil(S a / a_max)) samples per triangle of area a (a_max the largest),
+ *              on a rank-1 lattice mapped into the triangle by Heitz's square-to-triangle
+ *              map, each carrying w a / (its count).
+ * A sample marks the sub-cell of its point in its voxel (samples outside [0, R)^3 are
+ * dropped) and adds its measure and the matching moment.  out0 is a level like
+ * vx_voxelize's (K = 1), summed in sample order.  R <= 1024 (VX_ERR_UNSUPPORTED otherwise);
+ * num_prims * S < 2^31 (VX_ERR_CAPACITY).  Synchronises the stream once (twice for
+ * triangles). */
 VX_API vx_status vx_voxelize_sampled(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
                                      int samples_per_segment, void* stream, vx_level* out0);
 

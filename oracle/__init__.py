@@ -87,6 +87,8 @@ def _load():
             lib.vxo_hist_dist.argtypes = [P, P]
             lib.vxo_sggx_h.restype = C.c_int
             lib.vxo_sggx_h.argtypes = [P, C.c_int, C.c_int, P, C.c_int, P, P, C.c_int]
+            lib.vxo_voxelize_tris_sampled.restype = C.c_int
+            lib.vxo_voxelize_tris_sampled.argtypes = [P, C.c_int64, P, C.POINTER(_Grid), C.c_int, C.POINTER(_Level)]
             lib.vxo_voxelize_fibers_sampled.restype = C.c_int
             lib.vxo_voxelize_fibers_sampled.argtypes = [P, P, C.c_int64, P, C.POINTER(_Grid), C.c_int,
                                                         C.POINTER(_Level)]
@@ -293,6 +295,19 @@ def voxelize_fibers_sampled(ctrl, offsets, grid, samples: int, weights=None) -> 
     G = _grid(grid)
     _load().vxo_voxelize_fibers_sampled(_ptr(ctrl), _ptr(offsets), int(offsets.shape[0] - 1), _ptr(w),
                                         C.byref(G), int(samples), C.byref(L))
+    d = _level_to_dict(L)
+    _load().vxo_level_free(C.byref(L))
+    return d
+
+
+def voxelize_tris_sampled(tris, grid, samples: int, weights=None) -> dict:
+    """Sample-based level 0 of triangles: up to `samples` per triangle by area relative to the
+    largest, placed by Heitz's square-to-triangle map (Sec. 3.2-3.3)."""
+    tris = _f32(tris).reshape(-1, 3, 4)
+    w = None if weights is None else _f32(weights)
+    L = _Level()
+    G = _grid(grid)
+    _load().vxo_voxelize_tris_sampled(_ptr(tris), int(tris.shape[0]), _ptr(w), C.byref(G), int(samples), C.byref(L))
     d = _level_to_dict(L)
     _load().vxo_level_free(C.byref(L))
     return d

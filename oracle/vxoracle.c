@@ -801,6 +801,81 @@ ORC_API int vxo_voxelize_fibers_sampled(const float* ctrl, const int64_t* offset
     return 0;
 }
 
+/* Sample-based voxelization of triangles (Sec. 3.2-3.3: sample counts by area relative to the
+ * largest triangle, points from Heitz's square-to-triangle map): triangle p of area a gets
+ * M_p = max(1, ceil(S a / a_max)) (at most S) samples; sample j is the lattice point
+ * (x, y) = ((j + 1/2) / M_p, frac((j + 1/2) 0.6180339887)), mapped to barycentrics by
+ * y > x: b0 = x/2, b1 = y - b0; else b1 = y/2, b0 = x - b1; the point is
+ * (b0 U0 + b1 U1) + (1 - b0 - b1) U2, carrying (w a) / M_p and the normal's moment. */
+ORC_API int vxo_voxelize_tris_sampled(const float* tri, int64_t T, const float* weights, const vxo_grid* g, int S,
+                                      vxo_level* out) {
+    const float s = 1.0f / g->voxel_size;
+    const int R = g->resolution;
+    float* U = (float*)malloc(sizeof(float) * 9 * (size_t)(T > 0 ? T : 1));
+    float* area = (float*)malloc(sizeof(float) * (size_t)(T > 0 ? T : 1));
+    float* nrm = (float*)malloc(sizeof(float) * 3 * (size_t)(T > 0 ? T : 1));
+    float amax = 0.0f;
+    for (int64_t p = 0; p < T; ++p) {
+        for (int k = 0; k < 3; ++k)
+            for (int i = 0; i < 3; ++i) U[9 * p + 3 * k + i] = (tri[12 * p + 4 * k + i] - g->origin[i]) * s;
+        const float* u = U + 9 * p;
+        float f0[3], f1[3];
+        for (int i = 0; i < 3; ++i) { f0[i] = u[3 + i] - u[i]; f1[i] = u[6 + i] - u[3 + i]; }
+        const float n0 = f0[1] * f1[2] - f0[2] * f1[1];
+        const float n1 = f0[2] * f1[0] - f0[0] * f1[2];
+        const float n2 = f0[0] * f1[1] - f0[1] * f1[0];
+        const float nn = sqrtf((n0 * n0 + n1 * n1) + n2 * n2);
+        nrm[3 * p] = nrm[3 * p + 1] = nrm[3 * p + 2] = 0.0f;
+        if (nn > 0.0f) { nrm[3 * p] = n0 / nn; nrm[3 * p + 1] = n1 / nn; nrm[3 * p + 2] = n2 / nn; }
+        area[p] = 0.5f * nn;
+        if (area[p] > amax) amax = area[p];
+    }
+    recs_t recs = {0, 0, 0};
+    for (int64_t p = 0; p < T; ++p) {
+        const float* u = U + 9 * p;
+        const float w = weights ? weights[p] : 1.0f;
+        uint32_t m = 1;
+        if (amax > 0.0f) {
+            const float x = (float)S * (area[p] / amax);
+            m = (uint32_t)ceilf(x);
+            if (m < 1) m = 1;
+            if (m > (uint32_t)S) m = (uint32_t)S;
+        }
+        const float cs = (w * area[p]) / (float)m;
+        for (uint32_t j = 0; j < m; ++j) {
+            const float x = ((float)j + 0.5f) / (float)m;
+            const float yy = ((float)j + 0.5f) * 0.6180339887f;
+            const float y = yy - floorf(yy);
+            float b0, b1;
+            if (y > x) { b0 = x * 0.5f; b1 = y - b0; } else { b1 = y * 0.5f; b0 = x - b1; }
+            const float b2 = (1.0f - b0) - b1;
+            float q[3];
+            int v[3], sc[3], inside = 1;
+            for (int i = 0; i < 3; ++i) {
+                q[i] = (b0 * u[i] + b1 * u[3 + i]) + b2 * u[6 + i];
+                const float fl = floorf(q[i]);
+                if (!(q[i] >= 0.0f) || !(q[i] < (float)R)) inside = 0;
+                v[i] = (int)fl;
+                int k = (int)((q[i] - fl) * 8.0f);
+                sc[i] = k > 7 ? 7 : k;
+            }
+            if (!inside) continue;
+            rec_t x_;
+            memset(x_.mask, 0, sizeof(x_.mask));
+            mask_set(x_.mask, sc[0], sc[1], sc[2]);
+            x_.key = vxo_morton((uint32_t)v[0], (uint32_t)v[1], (uint32_t)v[2]);
+            x_.prim = p * S + (int64_t)j;
+            x_.c = cs;
+            for (int i = 0; i < 3; ++i) { x_.dir[i] = nrm[3 * p + i]; x_.dir64[i] = nrm[3 * p + i]; }
+            x_.c64 = (double)cs;
+            recs_push(&recs, &x_);
+        }
+    }
+    reduce_records(&recs, out, 1);
+    free(recs.r); free(U); free(area); free(nrm);
+    return 0;
+}
+
 /* Triangles: tri [T][3][4] (xyz, w unused). */
 ORC_API int vxo_voxelize_tris(const float* tri, int64_t T, const float* weights,
                               const vxo_grid* g, int K, vxo_level* out) {

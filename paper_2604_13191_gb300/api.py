@@ -294,12 +294,13 @@ class Context:
             raise self._err(st, "vx_voxelize")
         return self._wrap(L)
 
-    def voxelize_sampled(self, grid, *, ctrl, fiber_offsets, samples: int, weights=None, num_prims=None,
-                         stream=None) -> Level:
+    def voxelize_sampled(self, grid, *, samples: int, tri_verts=None, ctrl=None, fiber_offsets=None, weights=None,
+                         num_prims=None, stream=None) -> Level:
         """vx_voxelize_sampled: the sample-based level 0 of fibers (`samples` axis samples per
-        segment), for comparison with voxelize()."""
+        segment) or triangles (up to `samples` per triangle, by area), for comparison with
+        voxelize()."""
         keep = []
-        P = self._prims(None, ctrl, fiber_offsets, weights, num_prims, keep)
+        P = self._prims(tri_verts, ctrl, fiber_offsets, weights, num_prims, keep)
         G = _grid(grid)
         L = VxLevel()
         st = self.lib.vx_voxelize_sampled(self.h, C.byref(P), C.byref(G), int(samples), _stream(stream), C.byref(L))

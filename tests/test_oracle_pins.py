@@ -595,3 +595,33 @@ def test_sampled_fibers_closed_form_and_subset_of_exact():
         e = Le["mask"][idx[int(k)]]
         assert np.all((m & ~e) == 0)
     assert Ls["occ"].sum() < Le["occ"].sum()
+
+
+def test_sampled_triangles_counts_mass_and_subset():
+    grid = synth.Grid((0.0, 0.0, 0.0), 1.0, 16)
+    # two right triangles in the plane z = 2.5: legs 4 (area 8) and legs 2.19 (area ~2.4, 0.3 of
+    # the largest), far apart; S = 10 -> 10 and ceil(3.0) = 3 samples
+    big = np.array([[1.0, 1.0, 2.5, 0], [5.0, 1.0, 2.5, 0], [1.0, 5.0, 2.5, 0]], np.float32)
+    leg = np.float32(np.sqrt(2 * 8 * 0.3))
+    small = np.array([[9.0, 9.0, 2.5, 0], [9.0 + leg, 9.0, 2.5, 0], [9.0, 9.0 + leg, 2.5, 0]], np.float32)
+    tris = np.stack([big, small])
+    L = oracle.voxelize_tris_sampled(tris, grid, 10)
+    keys = L["keys"]
+    def x_of(k):   # x bits of a Morton key (bit 0 of every triple)
+        return sum(((int(k) >> (3 * i)) & 1) << i for i in range(21))
+    x = np.array([x_of(k) for k in keys])
+    small_sel = x >= 8
+    assert L["occ"][small_sel].sum() <= 3 and L["occ"][~small_sel].sum() <= 10
+    area_small = 0.5 * float(leg) * float(leg)
+    np.testing.assert_allclose(L["mass"][small_sel].sum(), area_small, rtol=1e-5)
+    np.testing.assert_allclose(L["mass"][~small_sel].sum(), 8.0, rtol=1e-6)
+    # the normal moment: plane z = const -> only zz
+    np.testing.assert_allclose(L["moment"][:, 2], L["mass"], rtol=1e-6)
+    assert np.abs(L["moment"][:, [0, 1, 3, 4, 5]]).max() == 0.0
+    # every sampled sub-cell is one the exact test sets (the sample lies on the triangle)
+    tris, grid = synth.random_triangles(60, 16, seed=2, size=(0.5, 4.0))
+    Ls = oracle.voxelize_tris_sampled(tris, grid, 24)
+    Le = oracle.voxelize(synth.Workload("t", "triangles", grid, tri_verts=tris))
+    pos = np.searchsorted(Le["keys"], Ls["keys"])
+    assert np.array_equal(Le["keys"][pos], Ls["keys"])
+    assert np.all((Ls["mask"] & ~Le["mask"][pos]) == 0)

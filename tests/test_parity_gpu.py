@@ -301,6 +301,22 @@ def test_sampled_fibers(ctx):
     assert gs["occ"].sum() < ge["occ"].sum()
 
 
+def test_sampled_triangles(ctx):
+    """The sample-based level 0 of the heightfield (up to 16 samples per triangle by area)
+    against the oracle's, and inside the exact path's sub-cells."""
+    w = synth.config1()
+    tv = torch.from_numpy(w.tri_verts).to(DEV)
+    Ls = ctx.voxelize_sampled(w.grid, tri_verts=tv, samples=16)
+    Le = ctx.voxelize(w.grid, tri_verts=tv)
+    torch.cuda.synchronize()
+    gs, ge = Ls.host(), Le.host()
+    rs = oracle.voxelize_tris_sampled(w.tri_verts, w.grid, 16)
+    compare_level(gs, rs, "sampled triangles", mu_max=prim_measure_max(w))
+    pos = np.searchsorted(ge["keys"], gs["keys"])
+    assert np.array_equal(ge["keys"][pos], gs["keys"])
+    assert np.all((gs["mask"] & ~ge["mask"][pos]) == 0)
+
+
 def test_export_compact8(ctx, dirs5000):
     """8-bit compact SGGX export of every level of the K = 4 yarn pyramid against the
     oracle's quantization of its own compact parameters.  Level 0 (S = M/m, bit-exact
