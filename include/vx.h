@@ -336,6 +336,17 @@ VX_API vx_status vx_tessellate_catmull_rom(vx_context* ctx, const float* nodes, 
  * voxels to write, or K outside 1..8. */
 VX_API vx_status vx_export_compact8(const vx_level* level, uint8_t* out, void* stream);
 
+/* OpenVDB-style leaf table of a level (the paper exports its volumes to OpenVDB, Sec. 5.1):
+ * the level's voxels grouped into 8^3 leaf nodes.  Leaf l covers the voxels
+ * leaf_first[l] .. leaf_first[l+1]-1 of the level (in key order); leaf_keys[l] is the
+ * Morton key of the leaf (voxel key >> 9: the leaf origin is 8 times its decoded
+ * coordinates); leaf_masks[l][8] is the value mask of the leaf in VDB's x-major order, bit
+ * (x & 7) * 64 + (y & 7) * 8 + (z & 7) set for every voxel present.  Buffers are device,
+ * caller-owned, with room for num_voxels leaves (+1 for leaf_first); *num_leaves (host)
+ * receives the count.  R <= 2048.  Synchronises `stream` once. */
+VX_API vx_status vx_export_leaves(vx_context* ctx, const vx_level* level, uint64_t* leaf_keys, uint64_t* leaf_masks,
+                                  uint32_t* leaf_first, int64_t* num_leaves, void* stream);
+
 /* Returns a level's block to the context's allocator and clears the struct. */
 VX_API void vx_level_release(vx_context* ctx, vx_level* level, void* stream);
 

@@ -167,6 +167,16 @@ def _dict_to_level(d: dict, keep: list) -> _Level:
 # ----------------------------------------------------------------------------
 # public wrappers
 # ----------------------------------------------------------------------------
+def demorton(k: int):
+    """(x, y, z) of a Morton key (x in bit 0 of every triple)."""
+    x = y = z = 0
+    for i in range(21):
+        x |= ((k >> (3 * i)) & 1) << i
+        y |= ((k >> (3 * i + 1)) & 1) << i
+        z |= ((k >> (3 * i + 2)) & 1) << i
+    return x, y, z
+
+
 def morton(x: int, y: int, z: int) -> int:
     return int(_load().vxo_morton(x, y, z))
 
@@ -225,6 +235,25 @@ def catmull_rom(nodes, offsets, subdiv: int):
     out_off = np.zeros(F + 1, dtype=np.int64)
     _load().vxo_catmull_rom(_ptr(nodes), _ptr(off), F, int(subdiv), _ptr(out), _ptr(out_off))
     return out[:total], out_off
+
+
+def vdb_leaves(keys):
+    """OpenVDB-style 8^3 leaf table of a level's sorted Morton keys: (leaf keys = key >> 9,
+    value masks [L, 8] uint64 with bit (x & 7) * 64 + (y & 7) * 8 + (z & 7) per voxel, first
+    voxel index of each leaf [L + 1])."""
+    keys = np.asarray(keys, dtype=np.uint64)
+    leaf = keys >> np.uint64(9)
+    if keys.size == 0:
+        return np.zeros(0, np.uint64), np.zeros((0, 8), np.uint64), np.zeros(1, np.int64)
+    head = np.concatenate([[True], leaf[1:] != leaf[:-1]])
+    first = np.concatenate([np.nonzero(head)[0], [keys.size]]).astype(np.int64)
+    masks = np.zeros((first.size - 1, 8), dtype=np.uint64)
+    for l in range(first.size - 1):
+        for i in range(first[l], first[l + 1]):
+            x, y, z = demorton(int(keys[i]) & 511)
+            bit = x * 64 + y * 8 + z
+            masks[l, bit >> 6] |= np.uint64(1) << np.uint64(bit & 63)
+    return leaf[head], masks, first
 
 
 def compact8(c) -> np.ndarray:

@@ -63,7 +63,7 @@ EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_l
            "vx_level_release", "vx_status_string", "vx_last_cuda_error", "vx_profile_enable",
            "vx_profile_read", "vx_backward", "vx_backward_noalloc", "vx_batch_create", "vx_batch_run",
            "vx_batch_level", "vx_batch_destroy", "vx_set_max_pairs_per_pass", "vx_batch_create_lod",
-           "vx_export_compact8", "vx_tessellate_catmull_rom", "vx_voxelize_sampled"]
+           "vx_export_compact8", "vx_tessellate_catmull_rom", "vx_voxelize_sampled", "vx_export_leaves"]
 
 
 class VxInstance(C.Structure):
@@ -131,6 +131,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         lib.vx_batch_level.argtypes = [P, C.c_int, C.c_int, P, C.POINTER(VxLevel)]
         lib.vx_batch_destroy.restype = None
         lib.vx_batch_destroy.argtypes = [P]
+        lib.vx_export_leaves.restype = C.c_int
+        lib.vx_export_leaves.argtypes = [P, C.POINTER(VxLevel), P, P, P, C.POINTER(C.c_int64), P]
         lib.vx_voxelize_sampled.restype = C.c_int
         lib.vx_voxelize_sampled.argtypes = [P, C.POINTER(VxPrimitives), C.POINTER(VxGrid), C.c_int, P,
                                             C.POINTER(VxLevel)]
@@ -415,6 +417,23 @@ class Context:
         if st != 0:
             raise self._err(st, "vx_tessellate_catmull_rom")
         return out[:total], out_off
+
+    def export_leaves(self, level: Level, stream=None):
+        """vx_export_leaves: the level's OpenVDB-style 8^3 leaf table: (leaf_keys int64 [L],
+        value masks int64 [L, 8] (uint64 bit patterns, x-major bit order), first voxel of each
+        leaf int32 [L + 1])."""
+        n = max(level.num_voxels, 0)
+        keys = torch.empty((max(n, 1),), dtype=torch.int64, device=self.device)
+        masks = torch.empty((max(n, 1), 8), dtype=torch.int64, device=self.device)
+        first = torch.empty((n + 1,), dtype=torch.int32, device=self.device)
+        nl = C.c_int64(0)
+        st = self.lib.vx_export_leaves(self.h, C.byref(level._c), C.c_void_p(keys.data_ptr()),
+                                       C.c_void_p(masks.data_ptr()), C.c_void_p(first.data_ptr()), C.byref(nl),
+                                       _stream(stream))
+        if st != 0:
+            raise self._err(st, "vx_export_leaves")
+        L = int(nl.value)
+        return keys[:L], masks[:L], first[: L + 1]
 
     def export_compact8(self, level: Level, stream=None) -> torch.Tensor:
         """vx_export_compact8: the level's lobes as 8-bit compact SGGX, uint8 [n, K, 6]."""

@@ -230,6 +230,64 @@ __global__ void k_export_compact8(const float* __restrict__ compact, const uint8
 }
 }  // namespace
 
+namespace {
+// leaf (8^3 block) of each voxel: its Morton key >> 9
+__global__ void k_leaf_ids(const uint64_t* __restrict__ keys, int64_t n, uint32_t* __restrict__ leaf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) leaf[i] = (uint32_t)(keys[i] >> 9);
+}
+
+// thread per leaf: its key and the value mask of its voxels, in the leaf's x-major order
+// (bit (x & 7) * 64 + (y & 7) * 8 + (z & 7))
+__global__ void k_leaf_masks(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ first,
+                             const uint32_t* __restrict__ nleaf_p, uint64_t* __restrict__ leaf_keys,
+                             uint64_t* __restrict__ leaf_masks) {
+    const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= *nleaf_p) return;
+    uint64_t m[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const uint32_t b = first[l], e = first[l + 1];
+    for (uint32_t i = b; i < e; ++i) {
+        const uint32_t k = (uint32_t)(keys[i] & 511u);
+        const uint32_t x = vx_compact1by2(k), y = vx_compact1by2(k >> 1), z = vx_compact1by2(k >> 2);
+        const uint32_t bit = (x << 6) | (y << 3) | z;
+        m[bit >> 6] |= 1ull << (bit & 63u);
+    }
+    leaf_keys[l] = keys[b] >> 9;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) leaf_masks[(size_t)l * 8 + w] = m[w];
+}
+}  // namespace
+
+vx_status vx_export_leaves(vx_context* ctx, const vx_level* level, uint64_t* leaf_keys, uint64_t* leaf_masks,
+                           uint32_t* leaf_first, int64_t* num_leaves, void* stream) {
+    if (!ctx || !level || !num_leaves) return VX_ERR_INVALID_ARG;
+    *num_leaves = 0;
+    const int64_t n = level->num_voxels;
+    if (n < 0 || n > 0xfffffffell) return VX_ERR_INVALID_ARG;
+    if (!leaf_first) return VX_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        VX_CUDA_TRY(cudaMemsetAsync(leaf_first, 0, 4, s));
+        return VX_OK;
+    }
+    if (!level->keys || !leaf_keys || !leaf_masks) return VX_ERR_INVALID_ARG;
+    if (level->resolution > 2048) return VX_ERR_UNSUPPORTED;
+    VX_TRY(vx_ws_ensure(ctx, WS_LOD_IDX, (size_t)n * 4, s));
+    VX_TRY(vx_ws_ensure(ctx, WS_MISC, 256, s));
+    uint32_t* leaf = (uint32_t*)ctx->ws[WS_LOD_IDX].p;
+    uint32_t* misc = (uint32_t*)ctx->ws[WS_MISC].p;
+    k_leaf_ids<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(level->keys, n, leaf);
+    VX_CUDA_TRY(cudaGetLastError());
+    VX_TRY(vx_segment_starts(ctx, leaf, (uint32_t)n, misc + 10, leaf_first, s));
+    k_leaf_masks<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(level->keys, leaf_first, misc + 10, leaf_keys,
+                                                             leaf_masks);
+    VX_CUDA_TRY(cudaGetLastError());
+    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc + 10, 4, cudaMemcpyDeviceToHost, s));
+    VX_CUDA_TRY(cudaStreamSynchronize(s));
+    *num_leaves = ((const uint32_t*)ctx->host_pin)[0];
+    return VX_OK;
+}
+
 vx_status vx_export_compact8(const vx_level* level, uint8_t* out, void* stream) {
     if (!level) return VX_ERR_INVALID_ARG;
     if (level->num_voxels == 0) return VX_OK;

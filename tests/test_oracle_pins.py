@@ -625,3 +625,16 @@ def test_sampled_triangles_counts_mass_and_subset():
     pos = np.searchsorted(Le["keys"], Ls["keys"])
     assert np.array_equal(Le["keys"][pos], Ls["keys"])
     assert np.all((Ls["mask"] & ~Le["mask"][pos]) == 0)
+
+
+def test_vdb_leaves_hand_made():
+    # voxels (0,0,0), (1,0,0), (7,7,7) in leaf 0; (8,0,0) in leaf 1; (0,9,0) in leaf 2
+    pts = [(0, 0, 0), (1, 0, 0), (7, 7, 7), (8, 0, 0), (0, 9, 0)]
+    keys = np.array(sorted(oracle.morton(*p) for p in pts), np.uint64)
+    lk, masks, first = oracle.vdb_leaves(keys)
+    assert lk.tolist() == [0, 1, 2]              # Morton keys of leaves (0,0,0), (1,0,0), (0,1,0)
+    assert first.tolist() == [0, 3, 4, 5]
+    assert int(masks[0, 0]) == 1 | (1 << 0) and int(masks[0, 1]) == (1 << 0)   # x=1 -> bit 64
+    assert int(masks[0, 7]) == 1 << 63                                       # (7,7,7) -> bit 511
+    assert int(masks[1, 0]) == 1 and int(masks[2, 0]) == 1 << 8              # (0,9,0) -> y & 7 = 1
+    assert oracle.demorton(oracle.morton(5, 3, 6)) == (5, 3, 6)

@@ -317,6 +317,23 @@ def test_sampled_triangles(ctx):
     assert np.all((gs["mask"] & ~ge["mask"][pos]) == 0)
 
 
+def test_export_vdb_leaves(ctx, dirs5000):
+    """OpenVDB-style leaf tables of the reduced yarn's level 0 and level 2 against the oracle's
+    tables of its own levels."""
+    w = synth.config2(fibers_per_ply=8, segments=500, R=128, K=1)
+    L0 = ctx.voxelize(w.grid, ctrl=torch.from_numpy(w.ctrl).to(DEV),
+                      fiber_offsets=torch.from_numpy(w.fiber_offsets).to(DEV))
+    pyr = ctx.build_lod(L0, K=1, num_levels=2)
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, 128, 1, dirs5000, num_levels=2)
+    for lvl, lv in ((0, L0), (2, pyr[1])):
+        k, m, f = ctx.export_leaves(lv)
+        rk, rm, rf = oracle.vdb_leaves(refs[lvl]["keys"])
+        assert np.array_equal(k.cpu().numpy().view(np.uint64), rk), f"level {lvl}: leaf keys"
+        assert np.array_equal(m.cpu().numpy().view(np.uint64), rm), f"level {lvl}: value masks"
+        assert np.array_equal(f.cpu().numpy().astype(np.int64), rf), f"level {lvl}: first voxels"
+
+
 def test_export_compact8(ctx, dirs5000):
     """8-bit compact SGGX export of every level of the K = 4 yarn pyramid against the
     oracle's quantization of its own compact parameters.  Level 0 (S = M/m, bit-exact
