@@ -336,7 +336,8 @@ VX_API vx_status vx_tessellate_catmull_rom(vx_context* ctx, const float* nodes, 
  * voxels to write, or K outside 1..8. */
 VX_API vx_status vx_export_compact8(const vx_level* level, uint8_t* out, void* stream);
 
-/* OpenVDB-style leaf table of a level (the paper exports its volumes to OpenVDB, Sec. 5.1):
+/* OpenVDB-style leaf table of a level (the paper times its voxelization with the export to
+ * OpenVDB, Sec. 5 table of insertion times):
  * the level's voxels grouped into 8^3 leaf nodes.  Leaf l covers the voxels
  * leaf_first[l] .. leaf_first[l+1]-1 of the level (in key order); leaf_keys[l] is the
  * Morton key of the leaf (voxel key >> 9: the leaf origin is 8 times its decoded

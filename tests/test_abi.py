@@ -90,3 +90,21 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "vxoracle" not in txt
+
+
+def test_merge_mode_names():
+    from paper_2604_13191_gb300 import api
+    assert api._merge_mode("pooled") == 0 and api._merge_mode("mass") == 1
+    with pytest.raises(ValueError):
+        api._merge_mode("median")
+
+
+def test_new_entry_points_reject_bad_arguments_without_gpu():
+    """Argument checks that return before any device work (NULL context or level)."""
+    import paper_2604_13191_gb300 as vx
+    lib = vx.load()
+    assert lib.vx_export_compact8(None, None, None) == 1                 # VX_ERR_INVALID_ARG
+    n = C.c_int64(5)
+    assert lib.vx_export_leaves(None, None, None, None, None, C.byref(n), None) == 1
+    assert lib.vx_tessellate_catmull_rom(None, None, None, 0, 0, 1, None, None, None) == 1
+    assert lib.vx_voxelize_sampled(None, None, None, 4, None, None) == 1
