@@ -185,10 +185,24 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const uint32_t* __r
     for (int d = threadIdx.x; d < RB; d += SORT_THREADS) h[d] = 0;
     __syncthreads();
     const size_t base = (size_t)blockIdx.x * SORT_TILE;
+    if (!LUT && base + SORT_TILE <= n) {
+        // a full tile: four consecutive keys per 16-byte load (the key arrays are 256-byte
+        // aligned and a tile starts at a multiple of 4096 keys)
+        const uint4* k4 = reinterpret_cast<const uint4*>(keys + base);
+#pragma unroll
+        for (int j = 0; j < SORT_ITEMS / 4; ++j) {
+            const uint4 q = __ldg(k4 + (size_t)j * SORT_THREADS + threadIdx.x);
+            atomicAdd(&h[(q.x >> shift) & dmask], 1u);
+            atomicAdd(&h[(q.y >> shift) & dmask], 1u);
+            atomicAdd(&h[(q.z >> shift) & dmask], 1u);
+            atomicAdd(&h[(q.w >> shift) & dmask], 1u);
+        }
+    } else {
 #pragma unroll 4
-    for (int j = 0; j < SORT_ITEMS; ++j) {
-        size_t e = base + (size_t)j * SORT_THREADS + threadIdx.x;
-        if (e < n) atomicAdd(&h[radix_digit<LUT>(LUT ? 0u : keys[e], LUT ? vals[e] : 0u, shift, dmask, lut)], 1u);
+        for (int j = 0; j < SORT_ITEMS; ++j) {
+            size_t e = base + (size_t)j * SORT_THREADS + threadIdx.x;
+            if (e < n) atomicAdd(&h[radix_digit<LUT>(LUT ? 0u : keys[e], LUT ? vals[e] : 0u, shift, dmask, lut)], 1u);
+        }
     }
     __syncthreads();
     for (int d = threadIdx.x; d < RB; d += SORT_THREADS) hist[(size_t)d * nt + blockIdx.x] = h[d];
