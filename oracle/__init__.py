@@ -6,7 +6,14 @@ written from the paper's definitions (see the header of that file), compiled
 with `-ffp-contract=off` so that FP32 decisions are taken in the same precision
 and operation order as the kernels.  It shares no code with the CUDA library.
 
-Parity unpinned: none (every function is pinned by tests/test_oracle_pins.py).
+The exact-EMD option of SGGX-H (the unsliced reading of Eq. similarity) lives in
+`oracle/emd.py`, in Python with scipy's LP solver, for tiny cross-checks only.
+
+Parity unpinned: none.  Every function is pinned by tests/test_oracle_pins.py,
+tests/test_oracle_adjoint_pins.py and tests/test_oracle_emd.py; the lobe sampling,
+its six-count histogram encoding and the integer distance are pinned against a
+literal 125-bin FP64 histogram and its sliced Wasserstein distance, and the whole
+SGGX-H loop against an FP64 restatement (oracle/emd.py, distance "sliced").
 """
 from __future__ import annotations
 

@@ -638,3 +638,108 @@ def test_vdb_leaves_hand_made():
     assert int(masks[0, 7]) == 1 << 63                                       # (7,7,7) -> bit 511
     assert int(masks[1, 0]) == 1 and int(masks[2, 0]) == 1 << 8              # (0,9,0) -> y & 7 = 1
     assert oracle.demorton(oracle.morton(5, 3, 6)) == (5, 3, 6)
+
+
+# ----------------------------------------------------------------------------
+# SGGX-H statistics against a literal FP64 restatement (Sec. 4.4, Eq. similarity)
+# ----------------------------------------------------------------------------
+def _fp64_lobe_directions(s6, dirs):
+    """omega_k = normalize(S'^(1/2) u_k) in FP64 with numpy's eigh, S' = S + 1e-6 tr(S) I
+    (the regularised lobe, its diagonal formed in FP32 as the method forms it)."""
+    s6 = np.asarray(s6, np.float32)
+    tr = np.float32(np.float32(s6[0] + s6[1]) + s6[2])
+    eps = np.float32(1e-6) * tr
+    S = np.array([[s6[0] + eps, s6[3], s6[4]], [s6[3], s6[1] + eps, s6[5]], [s6[4], s6[5], s6[2] + eps]],
+                 np.float32).astype(np.float64)
+    w, U = np.linalg.eigh(S)
+    R = U @ np.diag(np.sqrt(np.maximum(w, 0.0))) @ U.T
+    v = np.asarray(dirs, np.float64) @ R.T
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def _literal_histogram(om):
+    """The 5 x 5 x 5 histogram over [-1, 1]^3 of the 2N entries omega and -omega, bin
+    min(4, floor((c + 1) * 2.5)) per axis, normalised to 1."""
+    pts = np.concatenate([om, -om])
+    b = np.minimum(4, np.floor((pts + 1.0) * 2.5).astype(np.int64))
+    H = np.zeros((5, 5, 5))
+    np.add.at(H, (b[:, 0], b[:, 1], b[:, 2]), 1.0)
+    return H / pts.shape[0]
+
+
+def _sliced_w1(Ha, Hb):
+    """Sum over the three axes of the Wasserstein-1 distance between the axis marginals
+    (bin width 0.4): sum_a sum_k |CDF_a(k) - CDF_b(k)| * 0.4."""
+    d = 0.0
+    for ax in range(3):
+        other = tuple(i for i in range(3) if i != ax)
+        ca = np.cumsum(Ha.sum(axis=other))
+        cb = np.cumsum(Hb.sum(axis=other))
+        d += 0.4 * np.abs(ca - cb)[:4].sum()
+    return d
+
+
+def _near_edges(om, tol=1e-5):
+    """Samples whose |omega_a| is within tol of a bin edge (0.2 or 0.6): FP32 and FP64 may
+    bin them differently."""
+    c = np.abs(om)
+    return ((np.abs(c - 0.6) < tol) | (np.abs(c - 0.2) < tol)).sum(axis=0)
+
+
+def _random_lobes(rng, n):
+    out = []
+    for t in range(n):
+        Q = rng.standard_normal((3, 3))
+        lam = rng.uniform(0, 1, 3) ** (1 + 3 * (t % 3))     # isotropic to nearly rank 1
+        V, _ = np.linalg.qr(Q)
+        S = V @ np.diag(lam) @ V.T
+        S /= np.trace(S)
+        out.append(np.array([S[0, 0], S[1, 1], S[2, 2], S[0, 1], S[0, 2], S[1, 2]], np.float32))
+    return out
+
+
+def test_sample_lobe_matches_fp64_directions(dirs5000):
+    """The oracle's histogram counts and sample second moment against directions computed in
+    FP64 with numpy's eigh: counts exact (up to samples within 1e-5 of a bin edge), M^ within
+    1e-6 (measured worst case 5.6e-7, for nearly rank-1 lobes)."""
+    rng = np.random.default_rng(11)
+    for s6 in _random_lobes(rng, 15):
+        h, M = oracle.sample_lobe(s6, dirs5000)
+        om = _fp64_lobe_directions(s6, dirs5000)
+        c = np.abs(om)
+        near = _near_edges(om)
+        assert np.all(np.abs(h[:3] - (c >= 0.6).sum(axis=0)) <= near)
+        assert np.all(np.abs(h[3:] - (c >= 0.2).sum(axis=0)) <= near)
+        Mref = np.array([np.mean(om[:, a] * om[:, b]) for a, b in ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))])
+        assert np.max(np.abs(M - Mref)) <= 1e-6
+
+
+def test_hist_dist_equals_sliced_wasserstein_of_literal_histogram(dirs5000):
+    """The oracle stores a lobe's 5^3 histogram as six counts and its distance as an integer
+    sum of count differences, in units of 0.4 / N.  Against the literal statement (the
+    125-bin histogram of omega and -omega, the Wasserstein-1 distance of each axis marginal,
+    summed over the axes) the two agree up to samples within 1e-5 of a bin edge.  A wrong
+    edge, a wrong weight on the middle band or a dropped factor for the +-omega doubling
+    moves the distance by far more than that tolerance (asserted below)."""
+    rng = np.random.default_rng(12)
+    lobes = _random_lobes(rng, 10)
+    N = dirs5000.shape[0]
+    oms = [_fp64_lobe_directions(s6, dirs5000) for s6 in lobes]
+    Hs = [_literal_histogram(om) for om in oms]
+    hs = [oracle.sample_lobe(s6, dirs5000)[0] for s6 in lobes]
+    for H in Hs:
+        # the symmetric histogram: each marginal is mirror-symmetric
+        for ax in range(3):
+            m = H.sum(axis=tuple(i for i in range(3) if i != ax))
+            assert np.allclose(m, m[::-1], atol=1e-12)
+    checked = 0
+    for i in range(len(lobes)):
+        for j in range(len(lobes)):
+            lit = _sliced_w1(Hs[i], Hs[j])
+            orc = oracle.hist_dist(hs[i], hs[j]) * 0.4 / N
+            tol = 0.4 / N * (int(_near_edges(oms[i]).sum()) + int(_near_edges(oms[j]).sum())) * 2 + 1e-12
+            assert abs(lit - orc) <= tol, (i, j, lit, orc)
+            if i != j:
+                assert lit > 50 * tol   # the pin can see a factor of 2 or a moved edge
+                checked += 1
+    assert checked == 90
