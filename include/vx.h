@@ -77,8 +77,10 @@ enum { VX_TRIANGLES = 0, VX_FIBERS = 1 };
  *   fiber_offsets (device) [num_fibers+1] int64, fiber f owns ctrl[off[f] .. off[f+1]-1];
  *   segment s of fiber f joins ctrl[off[f]+s] and ctrl[off[f]+s+1] and is a capsule whose
  *   radius is the mean of its two control-point radii.  Primitive ids count segments
- *   fiber by fiber; num_prims must equal sum_f max(off[f+1]-off[f]-1, 0) (checked on the
- *   device; a mismatch returns VX_ERR_INVALID_ARG).
+ *   fiber by fiber; num_prims must equal sum_f max(off[f+1]-off[f]-1, 0), and every
+ *   segment's control points must lie in ctrl[0, num_ctrl) (both checked on the device;
+ *   a mismatch, or a negative or decreasing offset, returns VX_ERR_INVALID_ARG and no
+ *   control point outside the array is read).
  * weights (device) [num_prims] float >= 0, or NULL for all ones.
  * Coordinates, radii and weights must be finite, radii and weights >= 0; a record that is
  * not makes vx_voxelize / vx_backward return VX_ERR_INVALID_ARG. */
@@ -220,16 +222,20 @@ VX_API vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, const 
                              const float* const* grad_mass, const float* const* grad_moment,
                              void* stream, float* grad_ctrl, float* grad_weights);
 
-/* vx_backward for callers that cannot allocate device memory: for example code running
- * inside a host application or memory manager that owns all device memory and forbids
- * cudaMalloc, or a loop in which an allocation would stall the device.  Same arguments
- * and results as vx_backward (no context: nothing is allocated, not even through an
- * allocator).  There is no counterpart in the paper.
+/* vx_backward for FIBERS ONLY, for callers that cannot allocate device memory: for
+ * example code running inside a host application or memory manager that owns all device
+ * memory and forbids cudaMalloc, or a loop in which an allocation would stall the device.
+ * The arguments and results are those of vx_backward with prims->kind == VX_FIBERS (no
+ * context: nothing is allocated, not even through an allocator); triangles return
+ * VX_ERR_UNSUPPORTED.  There is no counterpart in the paper.
  * Scratch: one fixed array of about 39 MB inside the library (a file-scope device
  * array), which every GPU that loads the library holds until the process exits.
  * Limits: at most 65,536 segments, 8,192 fibers, 262,144 level-0 voxels and 2,097,152
- * candidate (voxel, segment) pairs; larger inputs return VX_ERR_CAPACITY (the pair limit
- * is checked after the candidates are counted, before any gradient is written).
+ * candidate (voxel, segment) pairs; larger inputs return VX_ERR_CAPACITY.  The pair limit
+ * is checked after the candidates are counted; grad_ctrl and grad_weights are written
+ * (zeroed, then accumulated) only after every limit has passed, so an error return
+ * leaves them as they were (except for num_prims == 0, where grad_ctrl is zeroed).
+ * `stream` must belong to the current device (VX_ERR_INVALID_ARG otherwise).
  * The first call on a device looks up the array's device address and caches it: make
  * that first call before any stream capture on that device.  Every call uses the same
  * array, which keeps the previous call's contents (the call clears what must start at
@@ -311,7 +317,8 @@ VX_API vx_status vx_voxelize_sampled(vx_context* ctx, const vx_primitives* prims
  * through its stored nodes, sampled at equally spaced t), for vx_voxelize with VX_FIBERS.
  *   nodes       (device) [num_nodes][4] float xyz + radius, 16-byte aligned
  *   offsets     (device) [num_splines + 1] int64: spline f has nodes offsets[f] ..
- *               offsets[f+1]-1, at least one
+ *               offsets[f+1]-1, at least one; offsets[0] = 0, offsets[num_splines] =
+ *               num_nodes (checked on the device: VX_ERR_INVALID_ARG)
  *   subdiv      points per span (>= 1): span i (nodes i, i+1) gives t = j / subdiv,
  *               j = 0..subdiv-1; the spline's last node closes it
  *   out_ctrl    (device, caller-owned) [(num_nodes - num_splines) * subdiv + num_splines][4],

@@ -542,6 +542,40 @@ def backward_noalloc(grid, *, ctrl, fiber_offsets, keys0, grad_mass, grad_moment
     """vx_backward_noalloc: the gradients of Context.backward written into the caller's
     grad_ctrl [P,4] (and grad_weights [N]) with no device allocation (fixed library
     scratch; limits in NOALLOC_LIMITS).  Calls that overlap on the GPU race."""
+    # the library writes num_ctrl * 16 bytes into grad_ctrl and num_prims * 4 into
+    # grad_weights: their shapes, types, devices and layouts are checked before any call
+    dev = ctrl.device
+    _check(ctrl, torch.float32, dev, "ctrl")
+    _check(fiber_offsets, torch.int64, dev, "fiber_offsets")
+    if ctrl.dim() != 2 or ctrl.shape[1] != 4:
+        raise ValueError(f"ctrl: expected shape (P, 4), got {tuple(ctrl.shape)}")
+    if fiber_offsets.dim() != 1 or fiber_offsets.shape[0] < 2:
+        raise ValueError("fiber_offsets: expected shape (F + 1,) with F >= 1")
+    if not isinstance(grad_ctrl, torch.Tensor):
+        raise TypeError("grad_ctrl: expected a tensor")
+    _check(grad_ctrl, torch.float32, dev, "grad_ctrl")
+    if tuple(grad_ctrl.shape) != (ctrl.shape[0], 4) or not grad_ctrl.is_contiguous():
+        raise ValueError(f"grad_ctrl: expected a contiguous ({ctrl.shape[0]}, 4) tensor, got "
+                         f"{tuple(grad_ctrl.shape)}{'' if grad_ctrl.is_contiguous() else ' (non-contiguous)'}")
+    if len(grad_mass) != len(grad_moment) or len(grad_mass) < 1:
+        raise ValueError("grad_mass / grad_moment: one tensor per level, the same number of each")
+    for g in list(grad_mass) + list(grad_moment):
+        _check(g, torch.float32, dev, "grad")
+    _check(keys0, torch.int64, dev, "keys0")
+    if num_prims is None:
+        oc = fiber_offsets.cpu()
+        num_prims = int(torch.clamp(oc[1:] - oc[:-1] - 1, min=0).sum())
+    if grad_weights is not None:
+        _check(grad_weights, torch.float32, dev, "grad_weights")
+        if tuple(grad_weights.shape) != (int(num_prims),) or not grad_weights.is_contiguous():
+            raise ValueError(f"grad_weights: expected a contiguous ({int(num_prims)},) tensor, got "
+                             f"{tuple(grad_weights.shape)}")
+    if weights is not None:
+        _check(weights, torch.float32, dev, "weights")
+        if tuple(weights.shape) != (int(num_prims),):
+            raise ValueError(f"weights: expected shape ({int(num_prims)},), got {tuple(weights.shape)}")
+    if dev.type != "cuda":
+        raise ValueError(f"backward_noalloc: tensors must be on a CUDA device, got {dev}")
     lib = load()
     keep = []
     c = ctrl.contiguous()
@@ -552,9 +586,6 @@ def backward_noalloc(grid, *, ctrl, fiber_offsets, keys0, grad_mass, grad_moment
     P.num_ctrl = c.shape[0]
     P.fiber_offsets = o.data_ptr()
     P.num_fibers = o.shape[0] - 1
-    if num_prims is None:
-        oc = o.cpu()
-        num_prims = int(torch.clamp(oc[1:] - oc[:-1] - 1, min=0).sum())
     P.num_prims = int(num_prims)
     if weights is not None:
         wt = weights.contiguous()

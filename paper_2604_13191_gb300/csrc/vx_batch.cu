@@ -39,7 +39,7 @@ __device__ __forceinline__ int find_inst(const BInst* __restrict__ inst, int nin
     return lo - 1;
 }
 
-__global__ void k_bprep_fibers(const float4* __restrict__ ctrl, const int64_t* __restrict__ off,
+__global__ void k_bprep_fibers(const float4* __restrict__ ctrl, int64_t num_ctrl, const int64_t* __restrict__ off,
                                const uint32_t* __restrict__ seg_start, int64_t F, const float* __restrict__ weights,
                                uint32_t np, const BInst* __restrict__ inst, int ninst, float4* __restrict__ ra,
                                float4* __restrict__ rb, uint8_t* __restrict__ inst_of, uint32_t* __restrict__ err) {
@@ -53,8 +53,9 @@ __global__ void k_bprep_fibers(const float4* __restrict__ ctrl, const int64_t* _
     const int64_t f = lo - 1;
     const int ii = find_inst(inst, ninst, p);
     if (f < 0 || ii < 0 || p >= inst[ii].prim_begin + inst[ii].num_prims) { atomicOr(err, 1u); return; }
-    const int64_t c = off[f] + (int64_t)(p - seg_start[f]);
-    if (c + 1 >= off[f + 1]) { atomicOr(err, 1u); return; }
+    const int64_t o0 = off[f];
+    const int64_t c = o0 + (int64_t)(p - seg_start[f]);
+    if (o0 < 0 || c < 0 || c + 1 >= off[f + 1] || c + 1 >= num_ctrl) { atomicOr(err, 1u); return; }
     const BInst g = inst[ii];
     const float4 pa = ctrl[c], pb = ctrl[c + 1];
     float4 A, B;
@@ -264,6 +265,7 @@ struct SubBatch {
     int key_bits = 0;
     const float* tri = nullptr;
     const float* ctrl = nullptr;
+    int64_t num_ctrl = 0;
     const int64_t* off = nullptr;
     const float* weights = nullptr;
     std::vector<BInst> hinst;
@@ -340,9 +342,9 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
     ++*nl;
     // ---- prep -------------------------------------------------------------------------
     if (S.fiber) {
-        k_fiber_seg_counts<<<gf((size_t)S.F, 256, 1u << 30), 256, 0, s>>>(S.off, S.F, S.fs);
+        k_fiber_seg_counts<<<gf((size_t)S.F, 256, 1u << 30), 256, 0, s>>>(S.off, S.F, S.num_ctrl, S.fs, C + C_ERR);
         if (vx_scan_u32_scratch(S.fs, S.fs, (uint32_t)S.F, C + C_SEGTOT, S.part, s) != cudaSuccess) return VX_ERR_CUDA;
-        k_bprep_fibers<<<gf(S.np, 256, 1u << 30), 256, 0, s>>>((const float4*)S.ctrl, S.off, S.fs, S.F, S.weights,
+        k_bprep_fibers<<<gf(S.np, 256, 1u << 30), 256, 0, s>>>((const float4*)S.ctrl, S.num_ctrl, S.off, S.fs, S.F, S.weights,
                                                                S.np, S.dinst, S.ninst, S.r0, S.r1, S.inst_of,
                                                                C + C_ERR);
         *nl += 5;
@@ -563,6 +565,7 @@ extern "C" vx_status vx_batch_create_lod(vx_context* ctx, const vx_primitives* t
         if (S.np == 0) continue;
         if (S.fiber) {
             S.ctrl = fibers->ctrl;
+            S.num_ctrl = fibers->num_ctrl;
             S.off = fibers->fiber_offsets;
             S.F = fibers->num_fibers;
             S.weights = fibers->weights;

@@ -621,10 +621,14 @@ __device__ float tri_measure(const float v[3][3], PolyBuf<NT>& pb) {
 // ------------------------------------------------------------------------------------
 // prep kernels
 // ------------------------------------------------------------------------------------
-__global__ void k_fiber_seg_counts(const int64_t* __restrict__ off, int64_t F, uint32_t* __restrict__ cnt) {
+// Segments per fiber; offsets that are negative, decrease, or pass num_ctrl are flagged.
+__global__ void k_fiber_seg_counts(const int64_t* __restrict__ off, int64_t F, int64_t num_ctrl,
+                                   uint32_t* __restrict__ cnt, uint32_t* __restrict__ err) {
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f < F) {
-        int64_t c = off[f + 1] - off[f] - 1;
+        const int64_t a = off[f], b = off[f + 1];
+        if (a < 0 || b < a || b > num_ctrl) atomicOr(err, 1u);
+        int64_t c = b - a - 1;
         cnt[f] = (uint32_t)(c > 0 ? c : 0);
     }
 }
@@ -638,7 +642,9 @@ __device__ __forceinline__ bool bad_record(float4 a, float4 b) {
     return !fin || a.w < 0.0f || b.w < 0.0f;
 }
 
-__global__ void k_prep_fibers(const float4* __restrict__ ctrl, const int64_t* __restrict__ off,
+// A segment whose control points fall outside ctrl[0, num_ctrl) (malformed offsets: negative,
+// past the end, or decreasing) is flagged and not read.
+__global__ void k_prep_fibers(const float4* __restrict__ ctrl, int64_t num_ctrl, const int64_t* __restrict__ off,
                               const uint32_t* __restrict__ seg_start, int64_t F, const uint32_t* __restrict__ seg_total,
                               const float* __restrict__ weights, uint32_t np, GridDev g, float4* __restrict__ ra,
                               float4* __restrict__ rb, uint32_t* __restrict__ err) {
@@ -653,8 +659,9 @@ __global__ void k_prep_fibers(const float4* __restrict__ ctrl, const int64_t* __
     }
     int64_t f = lo - 1;
     if (f < 0) { atomicOr(err, 1u); return; }
-    int64_t c = off[f] + (int64_t)(p - seg_start[f]);
-    if (c + 1 >= off[f + 1]) { atomicOr(err, 1u); return; }
+    const int64_t o0 = off[f];
+    int64_t c = o0 + (int64_t)(p - seg_start[f]);
+    if (o0 < 0 || c < 0 || c + 1 >= off[f + 1] || c + 1 >= num_ctrl) { atomicOr(err, 1u); return; }
     float4 pa = ctrl[c], pb = ctrl[c + 1];
     float4 A, B;
     A.x = (pa.x - g.o[0]) * g.s; A.y = (pa.y - g.o[1]) * g.s; A.z = (pa.z - g.o[2]) * g.s;

@@ -767,6 +767,11 @@ inline unsigned grid_for(size_t n, int threads) {
 
 }  // namespace
 
+namespace {
+vx_status build_levels(vx_context* ctx, const vx_level* in, const vx_lod_params* params, cudaStream_t s,
+                       vx_level* out, int L, const uint32_t* counts, uint32_t* misc);
+}  // namespace
+
 extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_lod_params* params, void* stream,
                                   vx_level* out) {
     if (!ctx || !in || !params || !out) return VX_ERR_INVALID_ARG;
@@ -806,6 +811,18 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
             return st;
         }
     }
+    // an error past this point returns every level to the allocator (outputs unallocated)
+    const vx_status st = build_levels(ctx, in, params, s, out, L, counts, misc);
+    if (st != VX_OK)
+        for (int l = 0; l < L; ++l) vx_level_release(ctx, &out[l], s);
+    return st;
+}
+
+namespace {
+vx_status build_levels(vx_context* ctx, const vx_level* in, const vx_lod_params* params, cudaStream_t s,
+                       vx_level* out, int L, const uint32_t* counts, uint32_t* misc) {
+    const int K = params->K;
+    const uint32_t n0 = (uint32_t)in->num_voxels;
     // ---- per level ------------------------------------------------------------------------
     VX_TRY(vx_ws_ensure(ctx, WS_LOD_FLAGS, (size_t)std::max<uint32_t>(n0, 1) * 4, s));
     VX_TRY(vx_ws_ensure(ctx, WS_LOD_STARTS, (size_t)std::max<uint32_t>(n0, 1) * 4 + 8, s));
@@ -859,6 +876,7 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
     }
     return VX_OK;
 }
+}  // namespace
 
 // Direction table and shared-memory limits of batched clustering with K lobes (host side,
 // before any capture): dirs [n][3] -> dirs4 [n] float4.

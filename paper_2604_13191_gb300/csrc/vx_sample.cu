@@ -272,9 +272,9 @@ extern "C" vx_status vx_voxelize_sampled(vx_context* ctx, const vx_primitives* p
         VX_TRY(vx_ws_ensure(ctx, WS_FIBER_START, (size_t)F * 4 + 256, s));
         uint32_t* fs = (uint32_t*)ctx->ws[WS_FIBER_START].p;
         VX_LAUNCH(ctx, ST_PREP, s, k_fiber_seg_counts<<<grid_for((size_t)F, 256), 256, 0, s>>>(prims->fiber_offsets, F,
-                                                                                              fs));
+                                                                                              prims->num_ctrl, fs, misc));
         VX_TRY(vx_scan_u32(ctx, fs, fs, (uint32_t)F, misc + 4, s));
-        VX_LAUNCH(ctx, ST_PREP, s, k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl,
+        VX_LAUNCH(ctx, ST_PREP, s, k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl, prims->num_ctrl,
                                                          prims->fiber_offsets, fs, F, misc + 4, prims->weights, np, g,
                                                          r0, r1, misc));
         n = np * (uint32_t)S;

@@ -14,12 +14,15 @@
 
 namespace {
 
-__global__ void k_spline_offsets(const int64_t* __restrict__ off, int64_t F, int S, int64_t* __restrict__ out_off,
-                                 uint32_t* __restrict__ err) {
+// Output offsets; the node offsets must run from 0 to num_nodes and increase strictly
+// (every spline has a node), else the error flag is set and no node is read.
+__global__ void k_spline_offsets(const int64_t* __restrict__ off, int64_t F, int64_t num_nodes, int S,
+                                 int64_t* __restrict__ out_off, uint32_t* __restrict__ err) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f > F) return;
     out_off[f] = (off[f] - f) * S + f;
     if (f < F && off[f + 1] <= off[f]) atomicOr(err, 1u);
+    if ((f == 0 && off[0] != 0) || (f == F && off[F] != num_nodes)) atomicOr(err, 1u);
 }
 
 __global__ void k_spline_points(const float4* __restrict__ nodes, const int64_t* __restrict__ off,
@@ -83,7 +86,7 @@ vx_status vx_tessellate_catmull_rom(vx_context* ctx, const float* nodes, const i
     uint32_t* err = (uint32_t*)ctx->ws[WS_MISC].p;
     VX_CUDA_TRY(cudaMemsetAsync(err, 0, 4, s));
     const int64_t F = num_splines;
-    k_spline_offsets<<<(unsigned)((F + 1 + 255) / 256), 256, 0, s>>>(offsets, F, subdiv, out_offsets, err);
+    k_spline_offsets<<<(unsigned)((F + 1 + 255) / 256), 256, 0, s>>>(offsets, F, num_nodes, subdiv, out_offsets, err);
     VX_CUDA_TRY(cudaGetLastError());
     VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, err, 4, cudaMemcpyDeviceToHost, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));

@@ -196,9 +196,9 @@ extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, co
         if (F > 0x7fffffff) return VX_ERR_CAPACITY;
         VX_TRY(vx_ws_ensure(ctx, WS_FIBER_START, (size_t)F * 4 + 256, s));
         uint32_t* fs = (uint32_t*)ctx->ws[WS_FIBER_START].p;
-        VX_LAUNCH(ctx, ST_PREP, s, k_fiber_seg_counts<<<grid_for((size_t)F, 256), 256, 0, s>>>(prims->fiber_offsets, F, fs));
+        VX_LAUNCH(ctx, ST_PREP, s, k_fiber_seg_counts<<<grid_for((size_t)F, 256), 256, 0, s>>>(prims->fiber_offsets, F, prims->num_ctrl, fs, misc));
         VX_TRY(vx_scan_u32(ctx, fs, fs, (uint32_t)F, misc + 4, s));
-        VX_LAUNCH(ctx, ST_PREP, s, k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl, prims->fiber_offsets, fs, F,
+        VX_LAUNCH(ctx, ST_PREP, s, k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl, prims->num_ctrl, prims->fiber_offsets, fs, F,
                                                          misc + 4, prims->weights, np, g, r0, r1, misc));
     } else {
         VX_LAUNCH(ctx, ST_PREP, s, k_prep_tris<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->tri_verts, prims->weights, np, g, r0,
@@ -230,7 +230,10 @@ extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, co
             parts.emplace_back();
             st = voxelize_window(ctx, fiber, np, win, w.lg, key_hi, (int)R, (uint32_t)total, r0, r1, r2, misc, s,
                                  &parts.back());
-            if (st != VX_OK) parts.pop_back();
+            if (st != VX_OK) {
+                vx_level_release(ctx, &parts.back(), s);   // allocated before a later step failed
+                parts.pop_back();
+            }
             continue;
         }
         if (w.lg == 0) { st = VX_ERR_CAPACITY; break; }      // one voxel over the limit
@@ -701,6 +704,9 @@ extern "C" vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, co
     if (R == 0 || (R & (R - 1)) != 0) return VX_ERR_INVALID_ARG;
     if (R > 1024 || grid->sub_res != 8) return VX_ERR_UNSUPPORTED;
     if (num_voxels0 < 0 || num_voxels0 > 0xffffffffll || num_levels < 0 || num_levels > 11) return VX_ERR_INVALID_ARG;
+    if ((num_voxels0 > 0 && !keys0) || !(grid->voxel_size > 0.0f) || !isfinite(grid->voxel_size))
+        return VX_ERR_INVALID_ARG;
+    if (fiber && prims->num_ctrl < 0) return VX_ERR_INVALID_ARG;
     if (prims->num_prims < 0 || prims->num_prims > 0xfffffffell) return VX_ERR_CAPACITY;
     if (((uintptr_t)grad_ctrl & 15) != 0) return VX_ERR_INVALID_ARG;
     if (fiber && (!prims->ctrl || !prims->fiber_offsets || prims->num_fibers <= 0 || ((uintptr_t)prims->ctrl & 15) != 0))
@@ -752,9 +758,9 @@ extern "C" vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, co
         if (F > 0x7fffffff) return VX_ERR_CAPACITY;
         VX_TRY(vx_ws_ensure(ctx, WS_FIBER_START, (size_t)F * 4 + 256, s));
         fs = (uint32_t*)ctx->ws[WS_FIBER_START].p;
-        VX_LAUNCH(ctx, ST_PREP, s, k_fiber_seg_counts<<<grid_for((size_t)F, 256), 256, 0, s>>>(prims->fiber_offsets, F, fs));
+        VX_LAUNCH(ctx, ST_PREP, s, k_fiber_seg_counts<<<grid_for((size_t)F, 256), 256, 0, s>>>(prims->fiber_offsets, F, prims->num_ctrl, fs, misc));
         VX_TRY(vx_scan_u32(ctx, fs, fs, (uint32_t)F, misc + 4, s));
-        VX_LAUNCH(ctx, ST_PREP, s, k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl,
+        VX_LAUNCH(ctx, ST_PREP, s, k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl, prims->num_ctrl,
                                                                                  prims->fiber_offsets, fs, F, misc + 4,
                                                                                  prims->weights, np, g, r0, r1, misc));
     } else {
@@ -775,11 +781,16 @@ extern "C" vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, co
         VX_LAUNCH(ctx, ST_COUNT, s, k_candidates<false, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
                                         r0, r1, r2, np, full_window((int)R), cnt, nullptr, nullptr, nullptr));
     VX_TRY(vx_scan_u32(ctx, cnt, offs, np, misc + 1, s));
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 8, cudaMemcpyDeviceToHost, s));
+    // the exact 64-bit total: the 32-bit scan total wraps
+    unsigned long long* t64 = (unsigned long long*)(misc + 8);
+    VX_LAUNCH(ctx, ST_COUNT, s, k_sum_u64<<<(unsigned)std::min<size_t>(grid_for(np, 256), (size_t)vx::kSMs * 8), 256, 0, s>>>(
+                                    cnt, np, t64));
+    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 48, cudaMemcpyDeviceToHost, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     if (((uint32_t*)ctx->host_pin)[0]) return VX_ERR_INVALID_ARG;
-    const uint32_t npairs = ((uint32_t*)ctx->host_pin)[1];
-    if (npairs >= 0x80000000u) return VX_ERR_CAPACITY;
+    const uint64_t npairs64 = ((const uint64_t*)ctx->host_pin)[4];
+    if (npairs64 >= 0x80000000ull) return VX_ERR_CAPACITY;
+    const uint32_t npairs = (uint32_t)npairs64;
     VX_TRY(vx_ws_ensure(ctx, WS_KEYS0, (size_t)std::max<uint32_t>(npairs, 1) * 4, s));
     VX_TRY(vx_ws_ensure(ctx, WS_VALS0, (size_t)std::max<uint32_t>(npairs, 1) * 4, s));
     uint32_t* k0 = (uint32_t*)ctx->ws[WS_KEYS0].p;
@@ -851,10 +862,13 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 std::mutex g_na_mutex;
 unsigned char* g_na_ptr[256] = {};
 
-// device address of the scratch array on the current device (set up on first use)
-vx_status na_scratch(unsigned char** out) {
-    int dev = 0;
+// device address of the scratch array on the current device (set up on first use); the
+// stream must belong to that device, or the address would be another device's
+vx_status na_scratch(cudaStream_t s, unsigned char** out) {
+    int dev = 0, sdev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return VX_ERR_CUDA;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) return VX_ERR_INVALID_ARG;
+    if (sdev != dev) return VX_ERR_INVALID_ARG;
     if (dev < 0 || dev >= 256) return VX_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_na_mutex);
     if (!g_na_ptr[dev]) {
@@ -883,7 +897,9 @@ extern "C" vx_status vx_backward_noalloc(const vx_primitives* prims, const vx_gr
     const uint32_t R = grid->resolution;
     if (R == 0 || (R & (R - 1)) != 0) return VX_ERR_INVALID_ARG;
     if (R > 1024 || grid->sub_res != 8) return VX_ERR_UNSUPPORTED;
-    if (num_voxels0 < 0 || num_levels < 0 || num_levels > 11 || prims->num_prims < 0 || prims->num_fibers <= 0)
+    if (num_voxels0 < 0 || num_levels < 0 || num_levels > 11 || prims->num_prims < 0 || prims->num_fibers <= 0 ||
+        prims->num_ctrl < 0 || (num_voxels0 > 0 && !keys0) || !(grid->voxel_size > 0.0f) ||
+        !isfinite(grid->voxel_size))
         return VX_ERR_INVALID_ARG;
     if (prims->num_prims > (int64_t)NA_MAX_PRIMS || prims->num_fibers > (int64_t)NA_MAX_FIBERS ||
         num_voxels0 > (int64_t)NA_MAX_VOXELS)
@@ -894,7 +910,7 @@ extern "C" vx_status vx_backward_noalloc(const vx_primitives* prims, const vx_gr
     for (int l = 0; l <= num_levels; ++l)
         if (!grad_mass[l] || !grad_moment[l]) return VX_ERR_INVALID_ARG;
     unsigned char* base = nullptr;
-    VX_TRY(na_scratch(&base));
+    VX_TRY(na_scratch(s, &base));
     const uint32_t np = (uint32_t)prims->num_prims;
     const uint32_t V0 = (uint32_t)num_voxels0;
     const int64_t P = prims->num_ctrl, F = prims->num_fibers;
@@ -919,9 +935,10 @@ extern "C" vx_status vx_backward_noalloc(const vx_primitives* prims, const vx_gr
 
     // the array keeps the previous call's contents: clear the counters and error flag
     NA_TRY(cudaMemsetAsync(misc, 0, 64, s));
-    NA_TRY(cudaMemsetAsync(grad_ctrl, 0, (size_t)P * 16, s));
-    if (grad_weights && np) NA_TRY(cudaMemsetAsync(grad_weights, 0, (size_t)np * 4, s));
-    if (np == 0) return VX_OK;
+    if (np == 0) {
+        if (P) NA_TRY(cudaMemsetAsync(grad_ctrl, 0, (size_t)P * 16, s));
+        return VX_OK;
+    }
 
     // level-0 adjoints (coarse adjoints broadcast down)
     if (V0) {
@@ -933,20 +950,28 @@ extern "C" vx_status vx_backward_noalloc(const vx_primitives* prims, const vx_gr
         }
     }
     // candidate pairs, primitive-major
-    k_fiber_seg_counts<<<grid_for((size_t)F, 256), 256, 0, s>>>(prims->fiber_offsets, F, fs);
+    k_fiber_seg_counts<<<grid_for((size_t)F, 256), 256, 0, s>>>(prims->fiber_offsets, F, prims->num_ctrl, fs, misc);
     NA_TRY(vx_scan_u32_scratch(fs, fs, (uint32_t)F, misc + 4, part, s));
-    k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl, prims->fiber_offsets, fs, F, misc + 4,
+    k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl, prims->num_ctrl, prims->fiber_offsets, fs, F, misc + 4,
                                                      prims->weights, np, g, r0, r1, misc);
     const unsigned cblocks = (unsigned)std::min<size_t>((np + EMIT_WARPS - 1) / EMIT_WARPS, (size_t)vx::kSMs * 64);
     k_candidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, nullptr, np, full_window((int)R), cnt,
                                                                   nullptr, nullptr, nullptr);
     NA_TRY(vx_scan_u32_scratch(cnt, offs, np, misc + 1, part, s));
-    uint32_t host[2] = {0, 0};
-    NA_TRY(cudaMemcpyAsync(host, misc, 8, cudaMemcpyDeviceToHost, s));
+    // the exact 64-bit total (the 32-bit scan total wraps)
+    k_sum_u64<<<(unsigned)std::min<size_t>(grid_for(np, 256), (size_t)vx::kSMs * 8), 256, 0, s>>>(
+        cnt, np, (unsigned long long*)(misc + 8));
+    uint32_t host[12] = {0};
+    NA_TRY(cudaMemcpyAsync(host, misc, 48, cudaMemcpyDeviceToHost, s));
     NA_TRY(cudaStreamSynchronize(s));
     if (host[0]) return VX_ERR_INVALID_ARG;
-    const uint32_t npairs = host[1];
-    if (npairs > NA_MAX_PAIRS) return VX_ERR_CAPACITY;
+    uint64_t npairs64 = 0;
+    memcpy(&npairs64, host + 8, 8);
+    if (npairs64 > NA_MAX_PAIRS) return VX_ERR_CAPACITY;
+    const uint32_t npairs = (uint32_t)npairs64;
+    // the caller's outputs are written only once every limit has passed
+    NA_TRY(cudaMemsetAsync(grad_ctrl, 0, (size_t)P * 16, s));
+    if (grad_weights) NA_TRY(cudaMemsetAsync(grad_weights, 0, (size_t)np * 4, s));
     if (npairs)
         k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, nullptr, np, full_window((int)R), nullptr,
                                                                      offs, k0, v0);

@@ -108,3 +108,37 @@ def test_new_entry_points_reject_bad_arguments_without_gpu():
     assert lib.vx_export_leaves(None, None, None, None, None, C.byref(n), None) == 1
     assert lib.vx_tessellate_catmull_rom(None, None, None, 0, 0, 1, None, None, None) == 1
     assert lib.vx_voxelize_sampled(None, None, None, 4, None, None) == 1
+
+
+def test_backward_noalloc_checks_output_shapes_before_any_call():
+    """The allocation-free adjoint writes num_ctrl * 16 bytes into grad_ctrl and num_prims * 4
+    into grad_weights: a buffer of the wrong shape, type or layout is refused on the host."""
+    import torch
+
+    from paper_2604_13191_gb300 import api
+    import synth
+    w = synth.config2(fibers_per_ply=2, segments=20, R=32, K=1)
+    ctrl = torch.from_numpy(w.ctrl)
+    off = torch.from_numpy(w.fiber_offsets)
+    keys = torch.zeros(4, dtype=torch.int64)
+    gm, gM = [torch.zeros(4)], [torch.zeros(4, 6)]
+    good_w = torch.zeros(w.num_prims)
+    kw = dict(ctrl=ctrl, fiber_offsets=off, keys0=keys, grad_mass=gm, grad_moment=gM)
+    with pytest.raises(ValueError, match="grad_ctrl"):
+        api.backward_noalloc(w.grid, grad_ctrl=torch.zeros(ctrl.shape[0] - 1, 4), **kw)
+    with pytest.raises(ValueError, match="grad_ctrl"):
+        api.backward_noalloc(w.grid, grad_ctrl=torch.zeros(4, ctrl.shape[0]).t(), **kw)
+    with pytest.raises(TypeError, match="grad_ctrl"):
+        api.backward_noalloc(w.grid, grad_ctrl=torch.zeros(ctrl.shape[0], 4, dtype=torch.float64), **kw)
+    with pytest.raises(ValueError, match="grad_weights"):
+        api.backward_noalloc(w.grid, grad_ctrl=torch.zeros(ctrl.shape[0], 4),
+                             grad_weights=torch.zeros(w.num_prims + 1), **kw)
+    with pytest.raises(ValueError, match="grad_weights"):
+        api.backward_noalloc(w.grid, grad_ctrl=torch.zeros(ctrl.shape[0], 4),
+                             grad_weights=torch.zeros(2 * w.num_prims)[::2], **kw)
+    with pytest.raises(TypeError, match="grad"):
+        api.backward_noalloc(w.grid, ctrl=ctrl, fiber_offsets=off, keys0=keys, grad_mass=[torch.zeros(4).double()],
+                             grad_moment=gM, grad_ctrl=torch.zeros(ctrl.shape[0], 4), grad_weights=good_w)
+    # well-formed buffers get as far as the device check (no GPU here)
+    with pytest.raises(ValueError, match="CUDA"):
+        api.backward_noalloc(w.grid, grad_ctrl=torch.zeros(ctrl.shape[0], 4), grad_weights=good_w, **kw)

@@ -91,3 +91,51 @@ def test_batch_with_sggx_h_matches_plain_instances(dirs5000):
     assert any(int(b.level(i, 1).lobe_count.max()) > 1 for i in range(len(insts)))
     b.close()
     ctx.close()
+
+
+def _oracle_instances():
+    """Two heightfields (512 and 2,048 triangles at 64^3 and 128^3) and two yarn patches
+    (1,200 and 1,080 segments, fibers 1.5 voxels thick, at 64^3 and 32^3): sizes the oracle
+    finishes in seconds, with clustered parents at every level above 0."""
+    ws = []
+    for n, R, seed in ((17, 64, 1), (33, 128, 2)):
+        ws.append(synth.Workload(f"hf{n}", "triangles", synth.Grid((0.0, 0.0, -0.5), 1.0 / R, R),
+                                 tri_verts=synth.heightfield(n, seed), K=1))
+    for fpp, segs, R, seed in ((2, 200, 64, 3), (3, 120, 32, 4)):
+        c, o = synth.yarn(3, fpp, segs, fiber_radius=1.5 / R, seed=seed)
+        ws.append(synth.Workload(f"yarn{fpp}", "fibers", synth.Grid((0.0, 0.0, 0.0), 1.0 / R, R), ctrl=c,
+                                 fiber_offsets=o, K=1))
+    return ws
+
+
+def _as_instance(w):
+    if w.kind == "triangles":
+        return {"kind": "triangles", "grid": w.grid, "tri_verts": torch.from_numpy(w.tri_verts).to(DEV)}
+    return {"kind": "fibers", "grid": w.grid, "ctrl": torch.from_numpy(w.ctrl).to(DEV),
+            "fiber_offsets": torch.from_numpy(w.fiber_offsets).to(DEV)}
+
+
+@pytest.mark.parametrize("K,which", [(1, (0, 3)), (4, (0, 1, 2, 3))])
+def test_batch_matches_oracle(K, which, dirs5000):
+    """Each batched instance against the CPU oracle directly (not through the plain CUDA
+    path): keys, masks, occupancy, projections and the FP32 sums bit-exact, the FP64
+    tolerance of the parity tests, and the SGGX-H lobes within 1e-5 (K = 4)."""
+    import oracle
+    from test_parity_gpu import compare_level, prim_measure_max
+    ws = [_oracle_instances()[i] for i in which]
+    ctx = vx.Context(DEV)
+    dirs = torch.from_numpy(dirs5000).to(DEV) if K > 1 else None
+    b = ctx.batch([_as_instance(w) for w in ws], K=K, dirs=dirs)
+    refs = []
+    for w in ws:
+        ref0 = oracle.voxelize(w, K=1)
+        refs.append([ref0] + oracle.build_pyramid(ref0, w.grid.resolution, K, dirs5000))
+    for rep in range(2):      # first run, then a graph replay
+        b.run()
+        torch.cuda.synchronize()
+        for i, w in enumerate(ws):
+            for l, r in enumerate(refs[i]):
+                compare_level(b.level(i, l).host(), r, f"{w.name} K={K} level {l} run {rep}",
+                              mu_max=prim_measure_max(w))
+    b.close()
+    ctx.close()

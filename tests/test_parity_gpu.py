@@ -11,6 +11,8 @@ The absolute floor covers FP32 clipping: a clip parameter carries an absolute er
 few 2^-24 of the primitive's parameter range, so a clipped piece's measure is exact only
 to ~1e-7 of the whole primitive's measure, whatever the size of the piece.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -277,10 +279,13 @@ def test_catmull_rom_splines(ctx, dirs5000):
     refs = [ref0] + oracle.build_pyramid(ref0, 128, 4, dirs5000)
     for lvl, (g, r) in enumerate(zip(got, refs)):
         compare_level(g, r, f"splines level {lvl}", mu_max=prim_measure_max(ws))
-    # a spline without nodes is rejected
-    with pytest.raises(vx.VxError):
-        ctx.tessellate_catmull_rom(torch.from_numpy(nodes).to(DEV),
-                                   torch.tensor([0, 3, 3, len(nodes)], dtype=torch.int64, device=DEV), S)
+    # a spline without nodes is rejected, and so are offsets that do not run from 0 to the
+    # node count (the last spline would read past the nodes)
+    for bad in ([0, 3, 3, len(nodes)], [0, 3, len(nodes) + 2], [1, 3, len(nodes)]):
+        with pytest.raises(vx.VxError) as e:
+            ctx.tessellate_catmull_rom(torch.from_numpy(nodes).to(DEV),
+                                       torch.tensor(bad, dtype=torch.int64, device=DEV), S)
+        assert e.value.status == 1
 
 
 def test_sampled_fibers(ctx):
@@ -454,6 +459,20 @@ def test_invalid_arguments(ctx):
     with pytest.raises(vx.VxError) as e:
         ctx.voxelize(grid, tri_verts=tris)
     assert e.value.status == 1
+    # offsets that reach past ctrl[num_ctrl - 1], or start below 0, are flagged before any
+    # control point outside the array is read (the buffer is sliced so that the bytes past
+    # num_ctrl exist and belong to this test)
+    big = torch.zeros((8, 4), dtype=torch.float32, device=DEV)
+    P = vx.api.VxPrimitives()
+    P.kind, P.num_prims, P.ctrl, P.num_ctrl = vx.api.VX_FIBERS, 4, big.data_ptr(), 4
+    for bad_off in ([0, 5], [-1, 4], [3, 1, 4]):
+        o = torch.tensor(bad_off, dtype=torch.int64, device=DEV)
+        P.fiber_offsets, P.num_fibers = o.data_ptr(), len(bad_off) - 1
+        P.num_prims = sum(max(b - a - 1, 0) for a, b in zip(bad_off[:-1], bad_off[1:]))
+        out = vx.api.VxLevel()
+        st = ctx.lib.vx_voxelize(ctx.h, C.byref(P), C.byref(vx.api._grid(grid)), vx.api._stream(None),
+                                 C.byref(out))
+        assert st == 1, bad_off
     L0 = ctx.voxelize(grid, ctrl=ctrl, fiber_offsets=off)
     with pytest.raises(vx.VxError) as e:
         ctx.build_lod(L0, K=9)
