@@ -56,9 +56,9 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-splines", action="store_true")
     ap.add_argument("--no-sampled", action="store_true")
-    ap.add_argument("--woven", type=int, default=0,
+    ap.add_argument("--woven", type=int, default=16,
                     help="also time the woven patch at 2048^3 with this many warp and weft yarns (16 = the "
-                         "full patch)")
+                         "full patch, 0 = skip)")
     ap.add_argument("--fibers-per-ply", type=int, default=64,
                     help="smaller yarns for profiling captures (64 = the benchmark workload)")
     return ap.parse_args()
@@ -94,29 +94,60 @@ def replica_throughput(ws, prims_per_rank, steps, total_ms):
 # ----------------------------------------------------------------------------------
 # CPU oracle timings (the reference arm and the cpu_baseline leg)
 # ----------------------------------------------------------------------------------
-def oracle_sample(w, n_fibers=None, n_segments=None):
-    off = w.fiber_offsets
-    if n_fibers is not None:
-        o = off[: n_fibers + 1].copy()
-    else:
-        o = np.array([0, n_segments + 1], np.int64)
-    return w.ctrl[: o[-1]], o
+SEGMENTS_PER_PROC = 1000
 
 
-def time_oracle(w, ctrl, off, dirs):
+def usable_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_worker(args):
+    """One oracle process: voxelize + full LoD of its fibers (segments, seconds)."""
+    ctrl, off, grid, barrier = args
     import oracle
+    dirs = synth.sample_directions(N_SAMPLES)
+    barrier.wait()
     t = time.perf_counter()
-    L0 = oracle.voxelize_fibers(ctrl, off, w.grid, K=1)
-    oracle.build_pyramid(L0, w.grid.resolution, K_LOBES, dirs)
-    return time.perf_counter() - t, synth.fiber_segment_count(off)
+    L0 = oracle.voxelize_fibers(ctrl, off, grid, K=1)
+    oracle.build_pyramid(L0, grid.resolution, K_LOBES, dirs)
+    return synth.fiber_segment_count(off), time.perf_counter() - t
 
 
-def cpu_baseline(w, dirs):
-    ctrl, off = oracle_sample(w, n_fibers=2)
-    secs, n = time_oracle(w, ctrl, off, dirs)
-    return {"value": n / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first 2 of 192 fibers ({n} segments) of the same yarn, voxelize + full LoD "
-                      f"K={K_LOBES}, N={N_SAMPLES}; single-threaded C oracle, {secs:.1f} s"}
+def time_oracle_parallel(w, procs):
+    """The oracle as it stands (single-threaded C) run as `procs` concurrent processes, one
+    per usable host core, process p on the first 1,000 segments of fiber p of the yarn:
+    voxelize + full LoD with K = 4, N = 5000.  Returns (segments, wall seconds of the slowest
+    process, processes).  Processes are spawned (never forked after CUDA is initialised)."""
+    import multiprocessing as mp
+    mpc = mp.get_context("spawn")
+    off = w.fiber_offsets
+    procs = max(1, min(procs, len(off) - 1))
+    with mpc.Manager() as m:
+        barrier = m.Barrier(procs)
+        jobs = []
+        for p in range(procs):
+            c0 = int(off[p])
+            jobs.append((w.ctrl[c0: c0 + SEGMENTS_PER_PROC + 1].copy(), np.array([0, SEGMENTS_PER_PROC + 1], np.int64),
+                         w.grid, barrier))
+        with mpc.Pool(procs) as pool:
+            res = pool.map(_oracle_worker, jobs)
+    return sum(r[0] for r in res), max(r[1] for r in res), procs
+
+
+def cpu_sample_text(procs, n, secs):
+    return (f"{procs} concurrent oracle processes (one per usable host core), process p on the first "
+            f"{SEGMENTS_PER_PROC} segments of fiber p of the same yarn ({n} segments in all), voxelize + full LoD "
+            f"K={K_LOBES}, N={N_SAMPLES}, 512^3; single-threaded C oracle per process; wall {secs:.1f} s of the "
+            f"slowest")
+
+
+def cpu_baseline(w, dirs=None):
+    n, secs, procs = time_oracle_parallel(w, usable_cores())
+    return {"value": n / secs, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": cpu_sample_text(procs, n, secs)}
 
 
 def run_reference(args):
@@ -124,23 +155,23 @@ def run_reference(args):
     if rank != 0:
         return
     w = synth.config2()
-    dirs = synth.sample_directions(N_SAMPLES)
-    ctrl, off = oracle_sample(w, n_segments=1000)
+    cores = usable_cores()
     for _ in range(args.warmup):
-        time_oracle(w, ctrl, off, dirs)
+        time_oracle_parallel(w, cores)
     tot, n = 0.0, 0
+    procs = 1
     for _ in range(args.steps):
-        s, k = time_oracle(w, ctrl, off, dirs)
-        tot += s
+        k, secs, procs = time_oracle_parallel(w, cores)
+        tot += secs
         n += k
     value = n / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "first 1000 segments of fiber 0 per step, voxelize + full LoD "
-                                       f"K={K_LOBES}, N={N_SAMPLES}; single-threaded C oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": cpu_sample_text(procs, n // max(args.steps, 1), tot / max(args.steps, 1)) +
+                             " (per step)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -367,7 +398,7 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        cpu = cpu_baseline(w, dirs_np)
+        cpu = cpu_baseline(w)
     stages = {k: {"launches": v[0] // args.steps, "ms_per_step": v[1] / args.steps,
                   "units_per_step": v[2] // args.steps}
               for k, v in prof.items() if v[0]}
@@ -459,40 +490,74 @@ def batched_vs_plain(ctx, dev, steps):
             "note": "batched = one captured graph per run; plain = per-instance vx_voxelize + vx_build_lod"}
 
 
-def woven_patch(ctx, dev, n_yarns, dirs):
-    """The woven patch (n_yarns warp x n_yarns weft yarns of 3 x 80 fibers, r = 0.002) at
-    2048^3, K = 4: vx_voxelize + vx_build_lod, one warm-up and two timed steps."""
+VOX_STAGES = ("prep", "candidates_count", "candidates_emit", "scan", "sort_hist", "sort_scatter", "segment_heads",
+              "reduce_fibers", "reduce_tris", "finalize")
+LOD_STAGES = ("lod_counts", "lod_heads", "lod_reduce", "sggx_cluster")
+
+
+def woven_patch(ctx, dev, n_yarns, dirs, window_log2=9, steps=2):
+    """The woven patch (n_yarns warp x n_yarns weft yarns of 3 x 80 fibers, 2,000 segments
+    per span, r = 0.002) at 2048^3 with K = 4, through vx_voxelize_lod_windowed (512^3
+    windows: the pyramid of the full patch does not fit in device memory at once).  Each
+    window's levels are handed to a callback that drops them.  One warm-up step, `steps`
+    timed steps (CUDA events around the call), then one step with per-stage event timing
+    for the voxelize / LoD split; peak device memory from torch's allocator."""
     import torch
+    import paper_2604_13191_gb300 as vx
     w = synth.config3(n_yarns=n_yarns)
     ctrl = torch.from_numpy(w.ctrl).to(dev)
     off = torch.from_numpy(w.fiber_offsets).to(dev)
-    ctx.profile(True)
-    ms, vox, lod = [], [], []
-    for i in range(3):
+    info = {"windows": 0, "voxels": [0] * window_log2}
+    # a context of its own, so that the peak below includes the workspace the call grows
+    ctx = vx.Context(dev)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(dev)
+    base = torch.cuda.memory_allocated(dev)
+
+    def on_window(win, levels):
+        info["windows"] += 1
+        for l, lv in enumerate(levels):
+            info["voxels"][l] += lv.num_voxels
+
+    def step():
+        info["windows"] = 0
+        info["voxels"] = [0] * window_log2
+        top = ctx.voxelize_lod_windowed(w.grid, window_log2=window_log2, on_window=on_window, K=K_LOBES, dirs=dirs,
+                                        ctrl=ctrl, fiber_offsets=off, num_prims=w.num_prims)
+        return info["voxels"] + [t.num_voxels for t in top]
+
+    step()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
-        m = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
-        L0 = ctx.voxelize(w.grid, ctrl=ctrl, fiber_offsets=off, num_prims=w.num_prims)
-        m.record()
-        pyr = ctx.build_lod(L0, K=K_LOBES, dirs=dirs)
+        sizes = step()
         b.record()
         torch.cuda.synchronize()
-        if i > 0:
-            ms.append(a.elapsed_time(b))
-            vox.append(a.elapsed_time(m))
-            lod.append(m.elapsed_time(b))
-        sizes = [L0.num_voxels] + [p.num_voxels for p in pyr]
-        del L0, pyr
+        ms.append(a.elapsed_time(b))
+    peak = torch.cuda.max_memory_allocated(dev) - base
+    ctx.profile(True)
+    step()
     prof = ctx.profile_read()
     ctx.profile(False)
-    pairs = prof.get("reduce_fibers", (0, 0.0, 0))[2] // 3
+    ctx.close()
+    vox_ms = sum(prof[k][1] for k in VOX_STAGES if k in prof)
+    lod_ms = sum(prof[k][1] for k in LOD_STAGES if k in prof)
+    pairs = prof.get("reduce_fibers", (0, 0.0, 0))[2]
+    t = statistics.mean(ms)
     return {"workload": f"woven patch {n_yarns}x{n_yarns} yarns x 3 plies x 80 fibers x 2000 segments "
-                        f"({w.num_prims} capsules, r = 0.002), 2048^3, K=4, N=5000",
-            "prims": int(w.num_prims), "ms_per_step": statistics.mean(ms), "voxelize_ms": statistics.mean(vox),
-            "lod_ms": statistics.mean(lod), "prims_per_s": w.num_prims / (statistics.mean(ms) * 1e-3),
-            "candidate_pairs": int(pairs), "voxels_per_level": sizes}
+                        f"({w.num_prims} capsules, r = 0.002), 2048^3, K=4, N=5000, windows of "
+                        f"{1 << window_log2}^3 (vx_voxelize_lod_windowed, every window's levels dropped by the "
+                        f"callback)",
+            "prims": int(w.num_prims), "ms_per_step": t, "prims_per_s": w.num_prims / (t * 1e-3),
+            "voxelize_ms": vox_ms, "lod_ms": lod_ms, "stage_split_note": "device time of the library's "
+            "voxelize and LoD stages in one extra step with per-launch event timing",
+            "windows": info["windows"], "candidate_pairs": int(pairs), "voxels_per_level": sizes,
+            "peak_device_bytes": int(peak), "peak_note": "device memory the call held at its peak (levels, "
+            "workspace), over the inputs already resident", "steps": steps}
 
 
 def spline_fibers(ctx, dev, steps, dirs):

@@ -153,14 +153,35 @@ VX_API vx_status vx_set_max_pairs_per_pass(vx_context* ctx, int64_t max_pairs);
  * Windows: the candidate (voxel, primitive) pairs are counted over the whole grid; a window
  * wider than 1024 voxels (keys of one pass are 30-bit) or holding more pairs than the
  * per-pass limit (vx_set_max_pairs_per_pass) is split into its eight octants, recursively,
- * in Morton order; each window is voxelized on its own and the windows' voxels are
- * concatenated, which keeps the key order.  Synchronises the stream once per counted
- * window and three times per processed window to size its outputs.
+ * in Morton order; each window is voxelized on its own and its voxels are written in
+ * key order.  With several windows a first pass counts each window's candidate voxels
+ * (emit, sort, heads) so that the level is allocated once and every window is reduced
+ * straight into its rows (the block may hold a few unused rows past num_voxels).
+ * Synchronises the stream once per counted window and twice (three times with several
+ * windows) per processed window.
  * Errors: VX_ERR_INVALID_ARG, VX_ERR_UNSUPPORTED (resolution > 2048 or sub_res != 8),
  * VX_ERR_OUT_OF_MEMORY, VX_ERR_CAPACITY (a single voxel over the per-pass limit),
  * VX_ERR_CUDA. */
 VX_API vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
                       void* stream, vx_level* out0);
+
+/* ---- windowed pyramid (grids whose pyramid does not fit in device memory at once) ------ */
+
+/* One window of the grid: voxels [lo, lo + 2^log2_size) per axis; index counts the
+ * non-empty windows in Morton order. */
+typedef struct {
+    int32_t lo[3];
+    int32_t log2_size;
+    int64_t index;
+} vx_window;
+
+/* Receives the levels 0 .. num_levels-1 of one window (rows of that window only, global
+ * keys, each level a block of the context's allocator).  Ownership passes to the callee,
+ * which releases each level with vx_level_release (at once or later).  Work on `stream`
+ * that produced them may still be in flight: order any use after it on that stream.
+ * Returning a status other than VX_OK stops vx_voxelize_lod_windowed, which returns it. */
+typedef vx_status (*vx_window_fn)(void* user, const vx_window* window, vx_level* levels, int num_levels,
+                                  void* stream);
 
 /* LoD parameters (Sec. 4.2-4.4).
  *   num_levels: number of coarser levels to build; 0 = down to 1^3 (log2 resolution).
@@ -191,6 +212,25 @@ typedef struct {
  * VX_ERR_CUDA. */
 VX_API vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_lod_params* params,
                        void* stream, vx_level* out);
+
+/* Voxelization and the whole pyramid, window by window, for grids whose pyramid does
+ * not fit in device memory at once (the paper processes the grid in blocks, Sec. 3.1-3.3).
+ * The grid is cut into windows of 2^w voxels per side (w = window_log2, 1 <= w <= log2
+ * resolution, at most 2^21 windows).  For each window that holds voxels, in Morton order:
+ * its level 0 (vx_voxelize restricted to the window; a window over the per-pass pair limit
+ * is split further inside) and its levels 1 .. w (vx_build_lod with lod->K, lod->dirs,
+ * lod->n_samples, lod->merge); levels 0 .. w-1 go to on_window, and the window's level-w
+ * voxel (its root) is kept.  Then top[0] is level w (the roots of all windows, in key
+ * order) and top[1 .. log2 R - w] the levels above it, built from top[0]; *num_top
+ * receives log2 R - w + 1.  The union of the windows' levels and top is the pyramid of
+ * vx_voxelize + vx_build_lod, bit for bit.  Peak memory: one window's pyramid (plus what
+ * the callee keeps) and the workspace of its largest pass.
+ * lod->num_levels must be 0.  Errors: as vx_voxelize and vx_build_lod, VX_ERR_INVALID_ARG
+ * (w out of range, NULL callback), VX_ERR_UNSUPPORTED (more than 2^21 windows), or the
+ * callee's status. */
+VX_API vx_status vx_voxelize_lod_windowed(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
+                                          const vx_lod_params* lod, int window_log2, vx_window_fn on_window,
+                                          void* user, void* stream, vx_level* top, int* num_top);
 
 /* Adjoint (reverse mode) of a linear loss on the per-voxel mass and second moments of
  * level 0 and the L coarser levels built from it:

@@ -51,6 +51,11 @@ class VxLodParams(C.Structure):
                 ("merge", C.c_int32), ("dirs", C.c_void_p)]
 
 
+class VxWindow(C.Structure):
+    _fields_ = [("lo", C.c_int32 * 3), ("log2_size", C.c_int32), ("index", C.c_int64)]
+
+
+WINDOW_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(VxWindow), C.POINTER(VxLevel), C.c_int, C.c_void_p)
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
@@ -63,7 +68,8 @@ EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_l
            "vx_level_release", "vx_status_string", "vx_last_cuda_error", "vx_profile_enable",
            "vx_profile_read", "vx_backward", "vx_backward_noalloc", "vx_batch_create", "vx_batch_run",
            "vx_batch_level", "vx_batch_destroy", "vx_set_max_pairs_per_pass", "vx_batch_create_lod",
-           "vx_export_compact8", "vx_tessellate_catmull_rom", "vx_voxelize_sampled", "vx_export_leaves"]
+           "vx_export_compact8", "vx_tessellate_catmull_rom", "vx_voxelize_sampled", "vx_export_leaves",
+           "vx_voxelize_lod_windowed"]
 
 
 class VxInstance(C.Structure):
@@ -140,6 +146,10 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         lib.vx_tessellate_catmull_rom.argtypes = [P, P, P, C.c_int64, C.c_int64, C.c_int, P, P, P]
         lib.vx_export_compact8.restype = C.c_int
         lib.vx_export_compact8.argtypes = [C.POINTER(VxLevel), P, P]
+        lib.vx_voxelize_lod_windowed.restype = C.c_int
+        lib.vx_voxelize_lod_windowed.argtypes = [P, C.POINTER(VxPrimitives), C.POINTER(VxGrid),
+                                                 C.POINTER(VxLodParams), C.c_int, WINDOW_FN, P, P,
+                                                 C.POINTER(VxLevel), C.POINTER(C.c_int)]
         lib.vx_backward_noalloc.restype = C.c_int
         lib.vx_backward_noalloc.argtypes = [C.POINTER(VxPrimitives), C.POINTER(VxGrid), P, C.c_int64, C.c_int,
                                             C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), P, P, P]
@@ -340,6 +350,51 @@ class Context:
             keep.append(w)
             P.weights = w.data_ptr()
         return P
+
+    def voxelize_lod_windowed(self, grid, *, window_log2: int, on_window, K: int = 1, dirs=None,
+                              merge: str = "pooled", tri_verts=None, ctrl=None, fiber_offsets=None, weights=None,
+                              num_prims=None, stream=None) -> list:
+        """vx_voxelize_lod_windowed: the pyramid window by window.  on_window(window, levels)
+        is called for every non-empty window of 2^window_log2 voxels per side (window: dict
+        with lo, log2_size, index; levels: its levels 0 .. window_log2 - 1 as Level objects,
+        which it may keep or drop).  Returns the levels window_log2 .. log2 R built from the
+        windows' roots."""
+        keep = []
+        P = self._prims(tri_verts, ctrl, fiber_offsets, weights, num_prims, keep)
+        G = _grid(grid)
+        prm = VxLodParams()
+        prm.num_levels = 0
+        prm.K = int(K)
+        prm.merge = _merge_mode(merge)
+        if dirs is not None:
+            d = dirs.contiguous()
+            _check(d, torch.float32, self.device, "dirs")
+            keep.append(d)
+            prm.dirs = d.data_ptr()
+            prm.n_samples = d.shape[0]
+        failure = []
+
+        def cb(user, win, levels, n, stream_):
+            try:
+                w = win.contents
+                lv = [self._wrap(levels[i]) for i in range(n)]
+                on_window({"lo": tuple(w.lo), "log2_size": int(w.log2_size), "index": int(w.index)}, lv)
+                return 0
+            except BaseException as e:       # stop the call; re-raised below
+                failure.append(e)
+                return 1
+        fn = WINDOW_FN(cb)
+        R = int(G.resolution)
+        L = R.bit_length() - 1
+        top = (VxLevel * (max(L - int(window_log2), 0) + 1))()
+        ntop = C.c_int(0)
+        st = self.lib.vx_voxelize_lod_windowed(self.h, C.byref(P), C.byref(G), C.byref(prm), int(window_log2), fn,
+                                               None, _stream(stream), top, C.byref(ntop))
+        if failure:
+            raise failure[0]
+        if st != 0:
+            raise self._err(st, "vx_voxelize_lod_windowed")
+        return [self._wrap(top[i]) for i in range(ntop.value)]
 
     def backward(self, grid, *, keys0, grad_mass, grad_moment, tri_verts=None, ctrl=None, fiber_offsets=None,
                  weights=None, num_prims=None, stream=None):

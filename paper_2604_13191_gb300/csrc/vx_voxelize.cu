@@ -65,56 +65,76 @@ vx_status count_window(vx_context* ctx, bool fiber, uint32_t np, const Window& w
     return VX_OK;
 }
 
-// One counted window (count_window ran on it and its total fits 31 bits): emit, sort,
-// segments, reduction and compaction into a new level block (*out).  Keys of the block
-// are key_hi | the Morton key relative to the window's corner (3 * bits bits).
-vx_status voxelize_window(vx_context* ctx, bool fiber, uint32_t np, const Window& win, int bits, uint64_t key_hi,
-                          int res, uint32_t npairs, float4* r0, float4* r1, float4* r2, uint32_t* misc,
-                          cudaStream_t s, vx_level* out) {
-    const int bx = win.lo[0], by = win.lo[1], bz = win.lo[2];
+// A window of the grid in the planning of a voxelization: its corner and size (2^lg voxels
+// per side) and, once counted, its candidate-pair total.
+struct Leaf {
+    int lo[3];
+    int lg;
+    uint64_t pairs;
+};
+
+inline Window window_of(const Leaf& w) {
+    Window win;
+    for (int i = 0; i < 3; ++i) { win.lo[i] = w.lo[i]; win.hi[i] = w.lo[i] + (1 << w.lg) - 1; }
+    return win;
+}
+
+inline uint64_t key_hi_of(const Leaf& w) {
+    return vx_morton3_64((uint32_t)(w.lo[0] >> w.lg), (uint32_t)(w.lo[1] >> w.lg), (uint32_t)(w.lo[2] >> w.lg))
+           << (3 * w.lg);
+}
+
+// Emit, sort and segment heads of one window whose candidate counts and offsets are in
+// WS_COUNT / WS_OFFS (count_window ran on it last) and whose pair total fits 31 bits.  On
+// return the sorted keys / primitive ids are in *k0 / *v0, the run starts in WS_STARTS and
+// the number of candidate voxels in *nseg.  Synchronises the stream once.
+vx_status window_segments(vx_context* ctx, bool fiber, uint32_t np, const Window& win, int bits, uint32_t npairs,
+                          float4* r0, float4* r1, float4* r2, uint32_t* misc, cudaStream_t s, uint32_t** k0,
+                          uint32_t** v0, uint32_t** k1, uint32_t** v1, uint32_t* nseg) {
     uint32_t* offs = (uint32_t*)ctx->ws[WS_OFFS].p;
     const unsigned cblocks = (unsigned)std::min<size_t>((np + EMIT_WARPS - 1) / EMIT_WARPS, (size_t)vx::kSMs * 64);
-    vx_stage_units(ctx, ST_COUNT, npairs);
-    vx_stage_units(ctx, ST_EMIT, npairs);
-    vx_stage_units(ctx, ST_SORT_SCATTER, npairs);
-    vx_stage_units(ctx, ST_SORT_HIST, npairs);
-    vx_stage_units(ctx, ST_REDUCE_FIBERS + (fiber ? 0 : 1), npairs);
-    if (npairs == 0) return vx_level_alloc(ctx, out, 0, 1, 0, res, s);
-
-    // ---- emit + sort ------------------------------------------------------------------
     VX_TRY(vx_ws_ensure(ctx, WS_KEYS0, (size_t)npairs * 4, s));
     VX_TRY(vx_ws_ensure(ctx, WS_VALS0, (size_t)npairs * 4, s));
     VX_TRY(vx_ws_ensure(ctx, WS_KEYS1, (size_t)npairs * 4, s));
     VX_TRY(vx_ws_ensure(ctx, WS_VALS1, (size_t)npairs * 4, s));
-    uint32_t* k0 = (uint32_t*)ctx->ws[WS_KEYS0].p;
-    uint32_t* v0 = (uint32_t*)ctx->ws[WS_VALS0].p;
-    uint32_t* k1 = (uint32_t*)ctx->ws[WS_KEYS1].p;
-    uint32_t* v1 = (uint32_t*)ctx->ws[WS_VALS1].p;
+    *k0 = (uint32_t*)ctx->ws[WS_KEYS0].p;
+    *v0 = (uint32_t*)ctx->ws[WS_VALS0].p;
+    *k1 = (uint32_t*)ctx->ws[WS_KEYS1].p;
+    *v1 = (uint32_t*)ctx->ws[WS_VALS1].p;
     if (fiber)
         VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                       r0, r1, r2, np, win, nullptr, offs, k0, v0));
+                                       r0, r1, r2, np, win, nullptr, offs, *k0, *v0));
     else
         VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<false, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                       r0, r1, r2, np, win, nullptr, offs, k0, v0));
+                                       r0, r1, r2, np, win, nullptr, offs, *k0, *v0));
     VX_CUDA_TRY(cudaGetLastError());
-    VX_TRY(vx_radix_sort_u32(ctx, &k0, &v0, &k1, &v1, npairs, 3 * bits, s));
-
-    // ---- segments ---------------------------------------------------------------------
+    VX_TRY(vx_radix_sort_u32(ctx, k0, v0, k1, v1, npairs, 3 * bits, s));
     VX_TRY(vx_ws_ensure(ctx, WS_FLAGS, (size_t)npairs * 4, s));
     VX_TRY(vx_ws_ensure(ctx, WS_STARTS, (size_t)npairs * 4 + 8, s));
-    uint32_t* flags = (uint32_t*)ctx->ws[WS_FLAGS].p;
     uint32_t* starts = (uint32_t*)ctx->ws[WS_STARTS].p;
-    VX_TRY(vx_segment_starts(ctx, k0, npairs, misc + 2, starts, s));
-
+    VX_TRY(vx_segment_starts(ctx, *k0, npairs, misc + 2, starts, s));
     VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc + 2, 4, cudaMemcpyDeviceToHost, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
-    const uint32_t nseg = ((uint32_t*)ctx->host_pin)[0];
-    vx_stage_units(ctx, ST_FINALIZE, nseg);
+    *nseg = ((uint32_t*)ctx->host_pin)[0];
+    return VX_OK;
+}
 
-    // ---- per-voxel reduction ----------------------------------------------------------
+// Per-voxel reduction and compaction of one window after window_segments: the non-empty
+// voxels are written to `dst`, a level or a view into one at the window's first row, with
+// room for at least nseg rows (dst == NULL: a new level block of exactly the window's
+// voxels is allocated into *alloc_out).  *nvox receives the window's voxel count.
+// Keys are key_hi | the Morton key relative to the window's corner.  Synchronises once.
+vx_status window_reduce(vx_context* ctx, bool fiber, uint32_t np, uint32_t nseg, uint64_t key_hi, int res,
+                        uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const Window& win, float4* r0,
+                        float4* r1, float4* r2, uint32_t* misc, cudaStream_t s, const vx_level* dst,
+                        vx_level* alloc_out, uint32_t* nvox_out) {
+    const int bx = win.lo[0], by = win.lo[1], bz = win.lo[2];
+    uint32_t* flags = (uint32_t*)ctx->ws[WS_FLAGS].p;
+    uint32_t* starts = (uint32_t*)ctx->ws[WS_STARTS].p;
+    vx_stage_units(ctx, ST_FINALIZE, nseg);
     // temp outputs per candidate voxel: mask 64 + mass 4 + moment 24 bytes; the sort's
     // alternate buffers are free now and hold the key and the non-empty flag.
-    VX_TRY(vx_ws_ensure(ctx, WS_SEG_OUT, (size_t)nseg * (64 + 4 + 24), s));
+    VX_TRY(vx_ws_ensure(ctx, WS_SEG_OUT, (size_t)std::max<uint32_t>(nseg, 1) * (64 + 4 + 24), s));
     char* so = (char*)ctx->ws[WS_SEG_OUT].p;
     SegOut seg;
     seg.mask = (uint64_t*)so;
@@ -123,41 +143,63 @@ vx_status voxelize_window(vx_context* ctx, bool fiber, uint32_t np, const Window
     seg.key = k1;
     seg.nonzero = v1;
     const unsigned rblocks = (unsigned)std::min<size_t>((nseg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 32);
+    VX_CUDA_TRY(cudaMemsetAsync(misc + 6, 0, 4, s));
     if (fiber) {
         // resident blocks (7 per SM) taking voxels from a counter
-        VX_CUDA_TRY(cudaMemsetAsync(misc + 6, 0, 4, s));
         const unsigned fblocks = (unsigned)std::min<size_t>((nseg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 7);
         VX_LAUNCH(ctx, ST_REDUCE_FIBERS, s, k_reduce_fibers<<<fblocks, RED_WARPS * 32, 0, s>>>(
                                                 k0, v0, starts, misc + 2, r0, r1, seg, bx, by, bz, misc + 6));
     } else {
-        VX_CUDA_TRY(cudaMemsetAsync(misc + 6, 0, 4, s));
         VX_LAUNCH(ctx, ST_REDUCE_TRIS, s, k_reduce_tris<<<rblocks, RED_WARPS * 32, 0, s>>>(
                                               k0, v0, starts, misc + 2, r0, r1, r2, seg, bx, by, bz, misc + 6));
     }
     VX_CUDA_TRY(cudaGetLastError());
-
-    // ---- compaction: dst = exclusive scan of the non-empty flags ----------------------------
-    uint32_t* dst = flags;   // the head flags are no longer needed
-    VX_TRY(vx_scan_u32(ctx, seg.nonzero, dst, nseg, misc + 3, s));
+    // compaction: dst index = exclusive scan of the non-empty flags (the head flags are free)
+    VX_TRY(vx_scan_u32(ctx, seg.nonzero, flags, nseg, misc + 3, s));
     VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc + 3, 4, cudaMemcpyDeviceToHost, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     const uint32_t nvox = ((uint32_t*)ctx->host_pin)[0];
-    VX_TRY(vx_level_alloc(ctx, out, nvox, 1, 0, res, s));
+    *nvox_out = nvox;
+    vx_level view;
+    if (dst) {
+        view = *dst;
+    } else {
+        VX_TRY(vx_level_alloc(ctx, alloc_out, nvox, 1, 0, res, s));
+        view = *alloc_out;
+    }
     if (nvox > 0) {
-        VX_LAUNCH(ctx, ST_FINALIZE, s, k_finalize<<<grid_for(nseg, 256), 256, 0, s>>>(seg, misc + 2, dst, *out, key_hi));
+        VX_LAUNCH(ctx, ST_FINALIZE, s, k_finalize<<<grid_for(nseg, 256), 256, 0, s>>>(seg, misc + 2, flags, view, key_hi));
         VX_CUDA_TRY(cudaGetLastError());
     }
     return VX_OK;
 }
 
-}  // namespace
+// The level arrays of L from row `at` on (a view for k_finalize; K = 1 rows).
+inline vx_level level_view(const vx_level& L, int64_t at) {
+    vx_level v = L;
+    v.keys += at;
+    v.mask += (size_t)at * 8;
+    v.mass += at;
+    v.moment += (size_t)at * 6;
+    v.occ += at;
+    v.occ_proj += (size_t)at * 3;
+    v.lobe_count += at;
+    v.lobes += (size_t)at * 7 * L.K;
+    v.compact += (size_t)at * 6 * L.K;
+    return v;
+}
 
-extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
-                                 void* stream, vx_level* out0) {
-    if (!ctx || !prims || !grid || !out0) return VX_ERR_INVALID_ARG;
-    memset(out0, 0, sizeof(*out0));
-    cudaStream_t s = (cudaStream_t)stream;
-    ctx->last_stream = s;
+// Prepared primitives of one voxelization: records in grid coordinates (WS_REC_A/B/C).
+struct Prepared {
+    bool fiber;
+    uint32_t np;
+    int bits_R;
+    int R;
+    float4 *r0, *r1, *r2;
+    uint32_t* misc;
+};
+
+vx_status prepare(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid, cudaStream_t s, Prepared* P) {
     const uint32_t R = grid->resolution;
     if (R == 0 || (R & (R - 1)) != 0) return VX_ERR_INVALID_ARG;
     if (R > 2048 || grid->sub_res != 8) return VX_ERR_UNSUPPORTED;
@@ -166,22 +208,25 @@ extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, co
     const bool fiber = prims->kind == VX_FIBERS;
     if (!fiber && prims->kind != VX_TRIANGLES) return VX_ERR_INVALID_ARG;
     const uint32_t np = (uint32_t)prims->num_prims;
-    int bits_R = 0;
-    while ((1u << bits_R) < R) ++bits_R;
-    GridDev g;
-    g.o[0] = grid->origin[0]; g.o[1] = grid->origin[1]; g.o[2] = grid->origin[2];
-    g.s = 1.0f / grid->voxel_size;
-    g.R = (int)R;
-
-    if (np == 0) return vx_level_alloc(ctx, out0, 0, 1, 0, (int)R, s);
+    P->fiber = fiber;
+    P->np = np;
+    P->R = (int)R;
+    P->bits_R = 0;
+    while ((1u << P->bits_R) < R) ++P->bits_R;
+    P->r0 = P->r1 = P->r2 = nullptr;
+    P->misc = nullptr;
+    if (np == 0) return VX_OK;
     if (fiber) {
-        if (!prims->ctrl || !prims->fiber_offsets || prims->num_fibers <= 0) return VX_ERR_INVALID_ARG;
+        if (!prims->ctrl || !prims->fiber_offsets || prims->num_fibers <= 0 || prims->num_ctrl < 0)
+            return VX_ERR_INVALID_ARG;
         if (((uintptr_t)prims->ctrl & 15) != 0) return VX_ERR_INVALID_ARG;
     } else {
         if (!prims->tri_verts || ((uintptr_t)prims->tri_verts & 15) != 0) return VX_ERR_INVALID_ARG;
     }
-
-    // ---- prep -----------------------------------------------------------------------
+    GridDev g;
+    g.o[0] = grid->origin[0]; g.o[1] = grid->origin[1]; g.o[2] = grid->origin[2];
+    g.s = 1.0f / grid->voxel_size;
+    g.R = (int)R;
     VX_TRY(vx_ws_ensure(ctx, WS_REC_A, (size_t)np * 16, s));
     VX_TRY(vx_ws_ensure(ctx, WS_REC_B, (size_t)np * 16, s));
     if (!fiber) VX_TRY(vx_ws_ensure(ctx, WS_REC_C, (size_t)np * 16, s));
@@ -206,39 +251,41 @@ extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, co
     }
     VX_CUDA_TRY(cudaGetLastError());
     vx_stage_units(ctx, ST_PREP, np);
+    P->r0 = r0; P->r1 = r1; P->r2 = r2; P->misc = misc;
+    return VX_OK;
+}
 
-    // ---- windows: the whole grid, split into octants (Morton order) while a window is
-    // wider than 1024 voxels (30-bit keys) or holds more candidate pairs than one pass may
-    std::vector<vx_level> parts;
-    vx_status st = VX_OK;
+// Windows of the region [lo, lo + 2^lg)^3 in Morton order: a window is split into its
+// eight octants while it is wider than 2^max_lg voxels (max_lg <= 10: keys of one pass are
+// 30-bit) or holds more candidate pairs than one pass may; octants without pairs are
+// dropped.  Each window is counted (one synchronisation); the list holds every window that
+// is kept, with its pair total.  VX_ERR_CAPACITY when a single voxel is over the limit.
+// *counted (optional) receives the index of the leaf whose counts and offsets are still in
+// the workspace (the last window counted was that leaf), or -1.
+vx_status plan_windows(vx_context* ctx, const Prepared& P, const int lo[3], int lg, int max_lg, cudaStream_t s,
+                       std::vector<Leaf>* leaves, int* counted) {
+    if (counted) *counted = -1;
     struct Pending { int lo[3]; int lg; };
     std::vector<Pending> stack;
-    stack.push_back(Pending{{0, 0, 0}, bits_R});
-    while (!stack.empty() && st == VX_OK) {
+    stack.push_back(Pending{{lo[0], lo[1], lo[2]}, lg});
+    const uint64_t limit = (uint64_t)std::min<int64_t>(ctx->max_pairs, 0x7fffffffll);
+    while (!stack.empty()) {
         const Pending w = stack.back();
         stack.pop_back();
-        Window win;
-        for (int i = 0; i < 3; ++i) { win.lo[i] = w.lo[i]; win.hi[i] = w.lo[i] + (1 << w.lg) - 1; }
+        Leaf leaf{{w.lo[0], w.lo[1], w.lo[2]}, w.lg, 0};
         uint64_t total = 0;
-        st = count_window(ctx, fiber, np, win, r0, r1, r2, misc, s, &total);
-        if (st != VX_OK) break;
-        if (total == 0 && w.lg < bits_R) continue;            // an empty octant adds nothing
-        const uint64_t limit = (uint64_t)std::min<int64_t>(ctx->max_pairs, 0x7fffffffll);
-        if (w.lg <= 10 && total <= limit) {
-            const uint64_t key_hi = vx_morton3_64((uint32_t)(w.lo[0] >> w.lg), (uint32_t)(w.lo[1] >> w.lg),
-                                               (uint32_t)(w.lo[2] >> w.lg)) << (3 * w.lg);
-            parts.emplace_back();
-            st = voxelize_window(ctx, fiber, np, win, w.lg, key_hi, (int)R, (uint32_t)total, r0, r1, r2, misc, s,
-                                 &parts.back());
-            if (st != VX_OK) {
-                vx_level_release(ctx, &parts.back(), s);   // allocated before a later step failed
-                parts.pop_back();
-            }
+        VX_TRY(count_window(ctx, P.fiber, P.np, window_of(leaf), P.r0, P.r1, P.r2, P.misc, s, &total));
+        if (counted) *counted = -1;
+        if (total == 0) continue;                                 // an empty window adds nothing
+        if (w.lg <= max_lg && total <= limit) {
+            leaf.pairs = total;
+            leaves->push_back(leaf);
+            if (counted) *counted = (int)leaves->size() - 1;
             continue;
         }
-        if (w.lg == 0) { st = VX_ERR_CAPACITY; break; }      // one voxel over the limit
+        if (w.lg == 0) return VX_ERR_CAPACITY;                    // one voxel over the limit
         const int half = 1 << (w.lg - 1);
-        for (int o = 7; o >= 0; --o) {                          // pushed in reverse: popped in Morton order
+        for (int o = 7; o >= 0; --o) {                            // pushed in reverse: popped in Morton order
             Pending c;
             c.lg = w.lg - 1;
             c.lo[0] = w.lo[0] + ((o & 1) ? half : 0);
@@ -247,50 +294,194 @@ extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, co
             stack.push_back(c);
         }
     }
-    if (st != VX_OK) {
-        for (auto& P : parts) vx_level_release(ctx, &P, s);
+    return VX_OK;
+}
+
+// Level 0 of the planned windows (Morton order), as one level block.  One window: its
+// pipeline allocates the block.  Several: a first pass counts each window's candidate
+// voxels (emit, sort, heads), one block is allocated for their sum, and a second pass
+// reduces every window straight into its rows, so that no window is held twice.
+// `counted`: index of the leaf whose counts and offsets are in the workspace (or -1).
+vx_status voxelize_leaves(vx_context* ctx, const Prepared& P, const std::vector<Leaf>& leaves, int counted,
+                          cudaStream_t s, vx_level* out0) {
+    const int res = P.R;
+    uint32_t *k0, *v0, *k1, *v1;
+    for (const Leaf& w : leaves) {
+        vx_stage_units(ctx, ST_COUNT, (int64_t)w.pairs);
+        vx_stage_units(ctx, ST_EMIT, (int64_t)w.pairs);
+        vx_stage_units(ctx, ST_SORT_SCATTER, (int64_t)w.pairs);
+        vx_stage_units(ctx, ST_SORT_HIST, (int64_t)w.pairs);
+        vx_stage_units(ctx, ST_REDUCE_FIBERS + (P.fiber ? 0 : 1), (int64_t)w.pairs);
+    }
+    if (leaves.empty()) return vx_level_alloc(ctx, out0, 0, 1, 0, res, s);
+    if (leaves.size() == 1) {
+        const Leaf& w = leaves[0];
+        const Window win = window_of(w);
+        uint64_t total = w.pairs;
+        if (counted != 0) VX_TRY(count_window(ctx, P.fiber, P.np, win, P.r0, P.r1, P.r2, P.misc, s, &total));
+        uint32_t nseg = 0, nvox = 0;
+        VX_TRY(window_segments(ctx, P.fiber, P.np, win, w.lg, (uint32_t)total, P.r0, P.r1, P.r2, P.misc, s, &k0, &v0,
+                               &k1, &v1, &nseg));
+        vx_status st = window_reduce(ctx, P.fiber, P.np, nseg, key_hi_of(w), res, k0, v0, k1, v1, win, P.r0, P.r1,
+                                     P.r2, P.misc, s, nullptr, out0, &nvox);
+        if (st != VX_OK) vx_level_release(ctx, out0, s);
         return st;
     }
-    if (parts.size() == 1) {
-        *out0 = parts[0];
-        return VX_OK;
+    // pass 1: candidate voxels per window (an upper bound of its voxels)
+    std::vector<uint32_t> nsegs(leaves.size());
+    int64_t cap = 0;
+    for (size_t i = 0; i < leaves.size(); ++i) {
+        const Window win = window_of(leaves[i]);
+        uint64_t total = leaves[i].pairs;
+        if (counted != (int)i) VX_TRY(count_window(ctx, P.fiber, P.np, win, P.r0, P.r1, P.r2, P.misc, s, &total));
+        counted = (int)i;
+        VX_TRY(window_segments(ctx, P.fiber, P.np, win, leaves[i].lg, (uint32_t)total, P.r0, P.r1, P.r2, P.misc, s,
+                               &k0, &v0, &k1, &v1, &nsegs[i]));
+        cap += nsegs[i];
     }
-    int64_t total = 0;
-    for (auto& P : parts) total += P.num_voxels;
-    const size_t ntiles = parts.size();
-    if (st == VX_OK) st = vx_level_alloc(ctx, out0, total, 1, 0, (int)R, s);
+    VX_TRY(vx_level_alloc(ctx, out0, cap, 1, 0, res, s));
+    // pass 2: every window reduced into its rows
     int64_t at = 0;
-    for (size_t t = 0; t < ntiles && st == VX_OK; ++t) {
-        const vx_level& P = parts[t];
-        const size_t n = (size_t)P.num_voxels;
-        if (n) {
-            const cudaError_t e =
-                [&]() {
-                    cudaError_t r = cudaSuccess;
-                    auto cp = [&](void* d, const void* src, size_t bytes) {
-                        if (r == cudaSuccess) r = cudaMemcpyAsync(d, src, bytes, cudaMemcpyDeviceToDevice, s);
-                    };
-                    cp(out0->keys + at, P.keys, n * 8);
-                    cp(out0->mask + (size_t)at * 8, P.mask, n * 64);
-                    cp(out0->mass + at, P.mass, n * 4);
-                    cp(out0->moment + (size_t)at * 6, P.moment, n * 24);
-                    cp(out0->occ + at, P.occ, n * 2);
-                    cp(out0->occ_proj + (size_t)at * 3, P.occ_proj, n * 3);
-                    cp(out0->lobe_count + at, P.lobe_count, n);
-                    cp(out0->lobes + (size_t)at * 7, P.lobes, n * 28);
-                    cp(out0->compact + (size_t)at * 6, P.compact, n * 24);
-                    return r;
-                }();
-            if (e != cudaSuccess) {
-                vx_record_cuda_error(ctx, e, "cudaMemcpyAsync");
-                st = VX_ERR_CUDA;
-            }
+    vx_status st = VX_OK;
+    for (size_t i = 0; i < leaves.size() && st == VX_OK; ++i) {
+        const Window win = window_of(leaves[i]);
+        uint64_t total = leaves[i].pairs;
+        uint32_t nseg = 0, nvox = 0;
+        if (counted != (int)i) st = count_window(ctx, P.fiber, P.np, win, P.r0, P.r1, P.r2, P.misc, s, &total);
+        counted = (int)i;
+        if (st == VX_OK)
+            st = window_segments(ctx, P.fiber, P.np, win, leaves[i].lg, (uint32_t)total, P.r0, P.r1, P.r2, P.misc, s,
+                                 &k0, &v0, &k1, &v1, &nseg);
+        if (st == VX_OK && nseg != nsegs[i]) st = VX_ERR_CUDA;    // the two passes must agree
+        if (st == VX_OK) {
+            const vx_level view = level_view(*out0, at);
+            st = window_reduce(ctx, P.fiber, P.np, nseg, key_hi_of(leaves[i]), res, k0, v0, k1, v1, win, P.r0, P.r1,
+                               P.r2, P.misc, s, &view, nullptr, &nvox);
         }
-        at += (int64_t)n;
+        at += nvox;
     }
-    for (size_t t = 0; t < ntiles; ++t) vx_level_release(ctx, &parts[t], s);
-    if (st != VX_OK) vx_level_release(ctx, out0, s);
-    return st;
+    if (st != VX_OK) {
+        vx_level_release(ctx, out0, s);
+        return st;
+    }
+    out0->num_voxels = at;
+    return VX_OK;
+}
+
+}  // namespace
+
+extern "C" vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
+                                 void* stream, vx_level* out0) {
+    if (!ctx || !prims || !grid || !out0) return VX_ERR_INVALID_ARG;
+    memset(out0, 0, sizeof(*out0));
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    Prepared P;
+    VX_TRY(prepare(ctx, prims, grid, s, &P));
+    if (P.np == 0) return vx_level_alloc(ctx, out0, 0, 1, 0, P.R, s);
+    std::vector<Leaf> leaves;
+    const int lo[3] = {0, 0, 0};
+    int counted = -1;
+    VX_TRY(plan_windows(ctx, P, lo, P.bits_R, 10, s, &leaves, &counted));
+    return voxelize_leaves(ctx, P, leaves, counted, s, out0);
+}
+
+// Copies row 0 of `src` (one voxel) into row i of `dst` (same K).
+static vx_status copy_root(vx_context* ctx, const vx_level& src, const vx_level& dst, int64_t i, cudaStream_t s) {
+    const int K = src.K;
+    VX_CUDA_TRY(cudaMemcpyAsync(dst.keys + i, src.keys, 8, cudaMemcpyDeviceToDevice, s));
+    VX_CUDA_TRY(cudaMemcpyAsync(dst.mask + (size_t)i * 8, src.mask, 64, cudaMemcpyDeviceToDevice, s));
+    VX_CUDA_TRY(cudaMemcpyAsync(dst.mass + i, src.mass, 4, cudaMemcpyDeviceToDevice, s));
+    VX_CUDA_TRY(cudaMemcpyAsync(dst.moment + (size_t)i * 6, src.moment, 24, cudaMemcpyDeviceToDevice, s));
+    VX_CUDA_TRY(cudaMemcpyAsync(dst.occ + i, src.occ, 2, cudaMemcpyDeviceToDevice, s));
+    VX_CUDA_TRY(cudaMemcpyAsync(dst.occ_proj + (size_t)i * 3, src.occ_proj, 3, cudaMemcpyDeviceToDevice, s));
+    VX_CUDA_TRY(cudaMemcpyAsync(dst.lobe_count + i, src.lobe_count, 1, cudaMemcpyDeviceToDevice, s));
+    VX_CUDA_TRY(cudaMemcpyAsync(dst.lobes + (size_t)i * 7 * K, src.lobes, (size_t)28 * K, cudaMemcpyDeviceToDevice, s));
+    VX_CUDA_TRY(cudaMemcpyAsync(dst.compact + (size_t)i * 6 * K, src.compact, (size_t)24 * K, cudaMemcpyDeviceToDevice,
+                                s));
+    return VX_OK;
+}
+
+extern "C" vx_status vx_voxelize_lod_windowed(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
+                                              const vx_lod_params* lod, int window_log2, vx_window_fn on_window,
+                                              void* user, void* stream, vx_level* top, int* num_top) {
+    if (!ctx || !prims || !grid || !lod || !on_window || !top || !num_top) return VX_ERR_INVALID_ARG;
+    *num_top = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    Prepared P;
+    VX_TRY(prepare(ctx, prims, grid, s, &P));
+    const int L = P.bits_R, w = window_log2;
+    if (w < 1 || w > L) return VX_ERR_INVALID_ARG;
+    if (lod->num_levels != 0) return VX_ERR_INVALID_ARG;
+    if (lod->K < 1 || lod->K > vx::kMaxK) return VX_ERR_UNSUPPORTED;
+    if (3 * (L - w) > 21) return VX_ERR_UNSUPPORTED;              // at most 2^21 windows
+    const int K = lod->K;
+    for (int l = 0; l <= L - w; ++l) memset(&top[l], 0, sizeof(vx_level));
+    // the window roots (level w) are gathered here, one row per non-empty window
+    vx_level roots;
+    VX_TRY(vx_level_alloc(ctx, &roots, P.np ? (int64_t)1 << (3 * (L - w)) : 0, K, w, P.R >> w, s));
+    vx_status st = VX_OK;
+    int64_t nroots = 0;
+    std::vector<Leaf> leaves;
+    if (P.np) {
+        const int lo[3] = {0, 0, 0};
+        st = plan_windows(ctx, P, lo, P.bits_R, std::min(w, 10), s, &leaves, nullptr);
+    }
+    // leaves are in Morton order, so the leaves of one 2^w window are contiguous
+    size_t i = 0;
+    int64_t index = 0;
+    while (st == VX_OK && i < leaves.size()) {
+        const int sh = w;
+        size_t j = i;
+        while (j < leaves.size() && (leaves[j].lo[0] >> sh) == (leaves[i].lo[0] >> sh) &&
+               (leaves[j].lo[1] >> sh) == (leaves[i].lo[1] >> sh) && (leaves[j].lo[2] >> sh) == (leaves[i].lo[2] >> sh))
+            ++j;
+        const std::vector<Leaf> group(leaves.begin() + i, leaves.begin() + j);
+        vx_window info;
+        for (int a = 0; a < 3; ++a) info.lo[a] = (leaves[i].lo[a] >> sh) << sh;
+        info.log2_size = w;
+        info.index = index++;
+        vx_level lv[12];
+        memset(lv, 0, sizeof(lv));
+        st = voxelize_leaves(ctx, P, group, -1, s, &lv[0]);
+        if (st == VX_OK && lv[0].num_voxels > 0) {
+            vx_lod_params wp = *lod;
+            wp.num_levels = w;
+            st = vx_build_lod(ctx, &lv[0], &wp, stream, &lv[1]);
+            if (st == VX_OK) st = copy_root(ctx, lv[w], roots, nroots, s);
+            if (st == VX_OK) {
+                ++nroots;
+                vx_level_release(ctx, &lv[w], s);
+                // ownership of levels 0 .. w-1 passes to the callee
+                st = on_window(user, &info, lv, w, stream);
+                if (st != VX_OK)
+                    for (int l = 0; l < w; ++l) vx_level_release(ctx, &lv[l], s);
+            } else {
+                for (int l = 0; l <= w; ++l) vx_level_release(ctx, &lv[l], s);
+            }
+        } else {
+            vx_level_release(ctx, &lv[0], s);
+        }
+        i = j;
+    }
+    if (st != VX_OK) {
+        vx_level_release(ctx, &roots, s);
+        return st;
+    }
+    roots.num_voxels = nroots;
+    top[0] = roots;
+    if (L > w) {
+        vx_lod_params tp = *lod;
+        tp.num_levels = L - w;
+        st = vx_build_lod(ctx, &roots, &tp, stream, &top[1]);
+        if (st != VX_OK) {
+            vx_level_release(ctx, &top[0], s);
+            return st;
+        }
+    }
+    *num_top = L - w + 1;
+    return VX_OK;
 }
 
 // =====================================================================================

@@ -203,3 +203,81 @@ def test_woven_2048_pyramid_properties(woven_run):
         assert float(P.mass.double().sum()) == pytest.approx(tot, rel=1e-5)
         assert bool((P.lobe_count <= 4).all())
         prev = P
+
+
+# ----------------------------------------------------------------------------
+# the full woven patch (16 warp x 16 weft yarns, 15.36M capsules, r = 0.002) at 2048^3 with
+# K = 4, built window by window (vx_voxelize_lod_windowed, 512^3 windows): the pyramid does
+# not fit in device memory at once.  Samples of every window's level 0 and level 1 are
+# gathered in the callback, and the levels are dropped.
+# ----------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def woven_full(dirs5000):
+    w = synth.config3()
+    ctx = vx.Context(DEV)
+    rng = np.random.default_rng(50)
+    stats = {"windows": 0, "count": [0] * 9, "mass": [0.0] * 9, "l0": [], "l1": [], "sorted": True}
+
+    def on_window(win, levels):
+        stats["windows"] += 1
+        for l, lv in enumerate(levels):
+            stats["count"][l] += lv.num_voxels
+            stats["mass"][l] += float(lv.mass.double().sum())
+            stats["sorted"] &= bool((lv.keys[1:] > lv.keys[:-1]).all())
+        if win["index"] % 4 == 0:
+            L0 = levels[0]
+            idx = np.sort(rng.choice(L0.num_voxels, 6, replace=False))
+            stats["l0"].append(_rows(L0, idx))
+            P = levels[1]
+            cl = torch.nonzero(P.lobe_count == 4).flatten().cpu().numpy()
+            if cl.size:
+                stats["l1"].append(_rows(P, np.array([rng.choice(cl)])))
+
+    top = ctx.voxelize_lod_windowed(w.grid, window_log2=9, on_window=on_window, K=4,
+                                    dirs=torch.from_numpy(dirs5000).to(DEV),
+                                    ctrl=torch.from_numpy(w.ctrl).to(DEV),
+                                    fiber_offsets=torch.from_numpy(w.fiber_offsets).to(DEV), num_prims=w.num_prims)
+    torch.cuda.synchronize()
+    top_mass = [float(t.mass.double().sum()) for t in top]
+    top_n = [t.num_voxels for t in top]
+    yield w, stats, top_mass, top_n
+    del top
+    ctx.close()
+
+
+def test_woven_full_patch_windows_and_mass(woven_full):
+    w, stats, top_mass, top_n = woven_full
+    assert w.num_prims == 15_360_000
+    assert stats["windows"] >= 16 and stats["sorted"]
+    assert stats["count"][0] > 500_000_000
+    assert top_n[0] == stats["windows"] and top_n[-1] == 1
+    tot = stats["mass"][0]
+    for m in stats["mass"][1:] + top_mass:
+        assert m == pytest.approx(tot, rel=1e-5)
+
+
+def test_woven_full_patch_sampled_level0(woven_full):
+    w, stats, _, _ = woven_full
+    got = {k: np.concatenate([r[k] for r in stats["l0"]]) for k in stats["l0"][0]}
+    assert got["keys"].size >= 40
+    ref = oracle.fiber_voxels(w.ctrl, w.fiber_offsets, w.grid, got["keys"])
+    assert np.array_equal(ref["mask"], got["mask"])
+    assert np.array_equal(ref["mass"].view(np.uint32), got["mass"].view(np.uint32))
+    assert np.array_equal(ref["moment"].view(np.uint32), got["moment"].view(np.uint32))
+
+
+def test_woven_full_patch_sampled_parents(woven_full, dirs5000):
+    w, stats, _, _ = woven_full
+    rows = stats["l1"][:3]
+    assert len(rows) == 3
+    for got in rows:
+        pk = np.uint64(got["keys"][0])
+        child_keys = (pk << np.uint64(3)) | np.arange(8, dtype=np.uint64)
+        vox = oracle.fiber_voxels(w.ctrl, w.fiber_offsets, w.grid, child_keys)
+        cur = oracle.lod_step(oracle.level_from_voxels(child_keys, vox), 4, dirs5000)
+        assert cur["keys"].shape[0] == 1 and cur["keys"][0] == pk
+        assert np.array_equal(cur["mask"][0], got["mask"][0])
+        assert cur["mass"][0].view(np.uint32) == got["mass"][0].view(np.uint32)
+        c = int(cur["lobe_count"][0])
+        assert c == int(got["lobe_count"][0]) == 4
+        assert np.max(np.abs(cur["lobes"][0, :c] - got["lobes"][0, :c])) <= 1e-5

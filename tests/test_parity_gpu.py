@@ -545,3 +545,67 @@ def test_windows_split_by_pair_limit(ctx, dirs5000, kind):
         for k in ("keys", "mask", "mass", "moment", "lobes", "lobe_count", "compact"):
             assert np.array_equal(np.asarray(a[k]).view(np.uint8), np.asarray(b[k]).view(np.uint8)), (lvl, k)
         compare_level(b, r, f"level {lvl}", mu_max=prim_measure_max(w))
+
+
+# ----------------------------------------------------------------------------
+# the windowed pyramid (vx_voxelize_lod_windowed) against the whole one
+# ----------------------------------------------------------------------------
+FIELDS = ("keys", "mask", "mass", "moment", "occ", "proj", "lobe_count", "lobes", "compact")
+
+
+def _cat_levels(parts):
+    out = {}
+    for f in FIELDS:
+        out[f] = np.concatenate([p[f] for p in parts]) if parts else None
+    return out
+
+
+@pytest.mark.parametrize("kind,w_log2,K", [("fibers", 4, 4), ("fibers", 6, 1), ("triangles", 5, 1),
+                                           ("triangles", 3, 4)])
+def test_windowed_pyramid_equals_whole(ctx, dirs5000, kind, w_log2, K):
+    """Every window's levels 0 .. w-1, concatenated in window order, and the levels built
+    from the windows' roots equal vx_voxelize + vx_build_lod bit for bit (all fields)."""
+    if kind == "fibers":
+        w = synth.config2(fibers_per_ply=6, segments=480, R=128, K=K)
+        geom = dict(ctrl=torch.from_numpy(w.ctrl).to(DEV), fiber_offsets=torch.from_numpy(w.fiber_offsets).to(DEV))
+    else:
+        w = synth.config1()
+        geom = dict(tri_verts=torch.from_numpy(w.tri_verts).to(DEV))
+    dirs = torch.from_numpy(dirs5000).to(DEV) if K > 1 else None
+    L0 = ctx.voxelize(w.grid, **geom)
+    whole = [L0.host()] + [p.host() for p in ctx.build_lod(L0, K=K, dirs=dirs)]
+    per_level = [[] for _ in range(w_log2)]
+    seen = []
+
+    def on_window(win, levels):
+        assert len(levels) == w_log2 and win["log2_size"] == w_log2
+        seen.append(win)
+        for l, lv in enumerate(levels):
+            per_level[l].append(lv.host())
+
+    top = ctx.voxelize_lod_windowed(w.grid, window_log2=w_log2, on_window=on_window, K=K, dirs=dirs, **geom)
+    torch.cuda.synchronize()
+    assert len(seen) > 1 and [s["index"] for s in seen] == list(range(len(seen)))
+    assert len(top) == len(whole) - w_log2
+    got = [_cat_levels(p) for p in per_level] + [t.host() for t in top]
+    for l, (g, r) in enumerate(zip(got, whole)):
+        for f in FIELDS:
+            assert np.array_equal(np.asarray(g[f]).view(np.uint8), np.asarray(r[f]).view(np.uint8)), (l, f)
+
+
+def test_windowed_callback_error_stops_the_call(ctx):
+    w = synth.config2(fibers_per_ply=2, segments=200, R=64, K=1)
+    geom = dict(ctrl=torch.from_numpy(w.ctrl).to(DEV), fiber_offsets=torch.from_numpy(w.fiber_offsets).to(DEV))
+    calls = []
+
+    def on_window(win, levels):
+        calls.append(win["index"])
+        if len(calls) == 2:
+            raise KeyError("stop")
+
+    with pytest.raises(KeyError):
+        ctx.voxelize_lod_windowed(w.grid, window_log2=3, on_window=on_window, **geom)
+    assert calls == [0, 1]
+    with pytest.raises(vx.VxError) as e:
+        ctx.voxelize_lod_windowed(w.grid, window_log2=7, on_window=on_window, **geom)   # w > log2 R
+    assert e.value.status == 1
