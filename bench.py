@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-splines", action="store_true")
+    ap.add_argument("--no-heightfield", action="store_true")
     ap.add_argument("--no-sampled", action="store_true")
     ap.add_argument("--woven", type=int, default=16,
                     help="also time the woven patch at 2048^3 with this many warp and weft yarns (16 = the "
@@ -367,12 +368,17 @@ def main():
     # ---- batched path vs per-instance plain calls (64 instances of uneven size) ------------
     batched = None
     if not args.no_batched:
-        batched = batched_vs_plain(ctx, dev, args.steps)
+        batched = batched_vs_plain(ctx, dev, args.steps, dirs)
 
     # ---- the woven patch at 2048^3 (optional) ---------------------------------------------
     woven = None
     if args.woven > 0:
         woven = woven_patch(ctx, dev, args.woven, dirs)
+
+    # ---- the triangle path (heightfields) ----------------------------------------------------
+    heightfield = None
+    if not args.no_heightfield:
+        heightfield = heightfield_record(ctx, dev, args.steps)
 
     # ---- spline input (Catmull-Rom nodes tessellated on the device) --------------------------
     splines = None
@@ -420,6 +426,7 @@ def main():
         "e2e": e2e,
         "clocks": clk,
         "batched": batched,
+        "heightfield": heightfield,
         "splines": splines,
         "sampled": sampled,
         "adjoint": adjoint,
@@ -434,16 +441,16 @@ def main():
 # ----------------------------------------------------------------------------------
 ADJ_WORKLOAD = ("yarn 3x64 fibers x 4000 segments (768k capsules) at 256^3, level 0 + 4 LoD levels (K=1); "
                 "loss = sum of U(-1,1) weights times every level's m and M")
-BATCH_WORKLOAD = ("64 instances: 32 heightfields of 2k-200k triangles and 32 yarn patches of 10k-400k "
-                  "segments (log-uniform), grids 64^3-1024^3, all LoD levels, K=1")
+BATCH_WORKLOAD = ("64 instances: 32 heightfields of 2k-2M triangles and 32 yarn patches of 10k-4M "
+                  "segments (log-uniform), grids 64^3-1024^3, all LoD levels, K=4, N=5000")
 
 
-def batched_vs_plain(ctx, dev, steps):
+def batched_vs_plain(ctx, dev, steps, dirs):
     """One graph replay of the batched path against a loop of plain vx_voxelize +
-    vx_build_lod calls over the same instances (same GPU, CUDA events)."""
+    vx_build_lod calls over the same instances (same GPU, CUDA events), K = 4 on every
+    level; the plan's groups and the launch shapes its autotuner picked are reported."""
     import torch
-    ws = synth.config4(seed=4, n_instances=64, min_tris=2000, max_tris=200_000, min_segs=10_000,
-                       max_segs=400_000)
+    ws = synth.config4(seed=4, n_instances=64)
     insts = []
     for w in ws:
         if w.kind == "triangles":
@@ -453,7 +460,11 @@ def batched_vs_plain(ctx, dev, steps):
                           "fiber_offsets": torch.from_numpy(w.fiber_offsets).to(dev),
                           "num_prims": w.num_prims})
     nprims = sum(w.num_prims for w in ws)
-    b = ctx.batch(insts)
+    t0 = time.perf_counter()
+    b = ctx.batch(insts, K=K_LOBES, dirs=dirs)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    plan = b.query()
 
     def run_batch():
         b.run()
@@ -466,7 +477,7 @@ def batched_vs_plain(ctx, dev, steps):
             else:
                 L0 = ctx.voxelize(inst["grid"], ctrl=inst["ctrl"], fiber_offsets=inst["fiber_offsets"],
                                   num_prims=inst["num_prims"])
-            outs.append((L0, ctx.build_lod(L0, K=1)))
+            outs.append((L0, ctx.build_lod(L0, K=K_LOBES, dirs=dirs)))
         return outs
 
     def timed(fn, n):
@@ -485,9 +496,16 @@ def batched_vs_plain(ctx, dev, steps):
     tb = timed(run_batch, steps)
     tp = timed(run_plain, steps)
     b.close()
-    return {"workload": BATCH_WORKLOAD, "prims": int(nprims), "batched_ms": tb, "plain_ms": tp,
-            "speedup": tp / tb, "batched_prims_per_s": nprims / (tb * 1e-3),
-            "note": "batched = one captured graph per run; plain = per-instance vx_voxelize + vx_build_lod"}
+    for k in plan.values():
+        k.pop("cluster_ms", None)
+    return {"workload": BATCH_WORKLOAD, "prims": int(nprims),
+            "triangles": int(sum(w.num_prims for w in ws if w.kind == "triangles")),
+            "segments": int(sum(w.num_prims for w in ws if w.kind == "fibers")),
+            "batched_ms": tb, "plain_ms": tp, "speedup": tp / tb, "batched_prims_per_s": nprims / (tb * 1e-3),
+            "plan_s": plan_s, "plan": plan,
+            "note": "batched = one captured graph per run (groups of instances whose pairs fit one pass, run in "
+                    "sequence per kind, the two kinds on two branches); plain = per-instance vx_voxelize + "
+                    "vx_build_lod; plan_s includes the autotuner's timing runs"}
 
 
 VOX_STAGES = ("prep", "candidates_count", "candidates_emit", "scan", "sort_hist", "sort_scatter", "segment_heads",
@@ -558,6 +576,54 @@ def woven_patch(ctx, dev, n_yarns, dirs, window_log2=9, steps=2):
             "windows": info["windows"], "candidate_pairs": int(pairs), "voxels_per_level": sizes,
             "peak_device_bytes": int(peak), "peak_note": "device memory the call held at its peak (levels, "
             "workspace), over the inputs already resident", "steps": steps}
+
+
+def heightfield_record(ctx, dev, steps):
+    """The triangle path: vx_voxelize + vx_build_lod (K = 1) of the config-1 heightfield
+    (64 x 64 vertices, 7,938 triangles, 128^3) and of a 1024 x 1024-vertex heightfield
+    (2,093,058 triangles, the largest size of the batching workload) at 1024^3; CUDA events
+    over `steps` steps after 2 warm-up steps, per-stage device times from one profiled step;
+    k_reduce_tris's pairs per second (its pipe and issue fractions are ncu counters, in the
+    profile summary of that kernel)."""
+    import torch
+    out = {}
+    for name, n, R in (("config1_128", 64, 128), ("hf1024_1024", 1024, 1024)):
+        tris = synth.heightfield(n, 1)
+        grid = synth.Grid((0.0, 0.0, -0.5), 1.0 / R, R)
+        tv = torch.from_numpy(tris).to(dev)
+
+        def step():
+            L0 = ctx.voxelize(grid, tri_verts=tv)
+            pyr = ctx.build_lod(L0, K=1)
+            return L0, pyr
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            L0, pyr = step()
+        e.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e) / steps
+        nvox = L0.num_voxels
+        del L0, pyr
+        ctx.profile(True)
+        step()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        red = prof.get("reduce_tris", (0, 0.0, 0))
+        lod_ms = sum(prof[k][1] for k in LOD_STAGES if k in prof)
+        vox_ms = sum(prof[k][1] for k in VOX_STAGES if k in prof)
+        out[name] = {"triangles": int(tris.shape[0]), "resolution": R, "ms_per_step": ms,
+                     "prims_per_s": tris.shape[0] / (ms * 1e-3), "voxelize_ms": vox_ms, "lod_ms": lod_ms,
+                     "level0_voxels": int(nvox), "candidate_pairs": int(red[2]), "reduce_tris_ms": red[1],
+                     "reduce_tris_pairs_per_s": red[2] / (red[1] * 1e-3) if red[1] > 0 else None}
+    out["note"] = ("voxelize + full LoD K=1; stage times from one extra step with per-launch event timing; "
+                   "k_reduce_tris's FP32-pipe and issue fractions are ncu counters "
+                   "(profiles/k_reduce_tris_heightfield.md)")
+    return out
 
 
 def spline_fibers(ctx, dev, steps, dirs):

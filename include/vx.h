@@ -42,7 +42,8 @@ typedef enum {
     VX_ERR_OUT_OF_MEMORY = 2, /* the allocator returned NULL                           */
     VX_ERR_CAPACITY = 3,      /* an internal 32-bit index range would overflow         */
     VX_ERR_CUDA = 4,          /* a CUDA runtime call failed (see vx_last_cuda_error)   */
-    VX_ERR_TIMEOUT = 5,       /* a bounded wait gave up                                */
+    VX_ERR_TIMEOUT = 5,       /* a bounded wait on the device gave up (the radix sort's
+                                 copy pipeline; the outputs of that call are not valid) */
     VX_ERR_UNSUPPORTED = 6    /* a parameter outside the supported range               */
 } vx_status;
 
@@ -138,10 +139,11 @@ VX_API vx_status vx_context_create(const vx_allocator* alloc, vx_context** out);
 /* Releases the workspace and the context (after synchronising its last stream). */
 VX_API void vx_context_destroy(vx_context* ctx);
 
-/* Per-pass limit on candidate (voxel, primitive) pairs of vx_voxelize (default and
- * maximum 2^31 - 1).  Each pass holds about 24 bytes of workspace per pair, so a lower
- * limit bounds the workspace; a window over the limit is split into octants.  The split
- * does not change any output.  Errors: VX_ERR_INVALID_ARG (ctx NULL or max_pairs < 1). */
+/* Per-pass limit on candidate (voxel, primitive) pairs (default and maximum 2^31 - 1).
+ * vx_voxelize and vx_voxelize_lod_windowed split a window over the limit into octants; a
+ * batch groups its instances so that each group's pairs fit it.  Each pass holds about 24
+ * bytes of workspace per pair, so a lower limit bounds the workspace.  The split does not
+ * change any output.  Errors: VX_ERR_INVALID_ARG (ctx NULL or max_pairs < 1). */
 VX_API vx_status vx_set_max_pairs_per_pass(vx_context* ctx, int64_t max_pairs);
 
 /* Sparse voxelization (Sec. 3.1-3.5, Sec. 4.1): level 0 of the pyramid.
@@ -311,8 +313,10 @@ typedef struct vx_batch vx_batch;
  * pipeline once, synchronising after each counting stage, and sizes every buffer at
  * (1 + headroom) times the measured count; a later run whose counts exceed them is
  * clamped and reported as VX_ERR_CAPACITY by vx_batch_level.  At most 255 instances of
- * each kind.  Errors: VX_ERR_INVALID_ARG, VX_ERR_UNSUPPORTED, VX_ERR_OUT_OF_MEMORY,
- * VX_ERR_CAPACITY, VX_ERR_CUDA. */
+ * each kind.  Instances are grouped so that each group's candidate pairs fit one pass, and
+ * launch shapes are tuned on the planning run (vx_batch_query).  An instance whose pairs
+ * alone exceed one pass returns VX_ERR_CAPACITY.  Errors: VX_ERR_INVALID_ARG,
+ * VX_ERR_UNSUPPORTED, VX_ERR_OUT_OF_MEMORY, VX_ERR_CAPACITY, VX_ERR_CUDA. */
 VX_API vx_status vx_batch_create(vx_context* ctx, const vx_primitives* tris, const vx_primitives* fibers,
                                  const vx_instance* instances, int num_instances, float headroom, void* stream,
                                  vx_batch** out);
@@ -333,6 +337,31 @@ VX_API vx_status vx_batch_run(vx_batch* batch, void* stream);
  * buffers (block = NULL, owned by the batch, valid until the next run).  Synchronises
  * `stream` on the first call after a run.  VX_ERR_CAPACITY if that run overflowed. */
 VX_API vx_status vx_batch_level(vx_batch* batch, int instance, int level, void* stream, vx_level* view);
+
+/* What planning chose for a batch (no counterpart in the paper).  Instances of a kind are
+ * split into groups whose candidate pairs fit one pass (vx_set_max_pairs_per_pass, with the
+ * headroom); the groups of a kind run one after the other and share one set of pair
+ * buffers.  Launch shapes are picked by an autotuner while the batch is planned: every
+ * candidate is timed (CUDA events, two runs each) on the planning run's own data and the
+ * fastest is kept; all candidates give the same outputs.  Per kind ([0] triangles,
+ * [1] fibers), for its largest group:
+ *   reduce_blocks_per_sm  resident blocks per SM of the per-voxel reduce (candidates
+ *                         fibers 3..7, triangles 4, 8, 16, 24, 32), reduce_ms their times;
+ *   cluster_tier[l]       SGGX-H tier of level l (0: a warp per parent, 1: a block of 8
+ *                         warps, 2: a block of 16 warps; -1: not tuned, K = 1 or level 0),
+ *                         cluster_ms[l][t] the time of tier t. */
+typedef struct {
+    int32_t num_groups[2];
+    int64_t max_group_pairs[2];
+    int32_t reduce_blocks_per_sm[2];
+    int32_t reduce_candidates[2][5];
+    float reduce_ms[2][5];
+    int32_t cluster_tier[2][12];
+    float cluster_ms[2][12][3];
+} vx_batch_info;
+
+/* Fills *info from the batch's plan.  Errors: VX_ERR_INVALID_ARG (NULL argument). */
+VX_API vx_status vx_batch_query(const vx_batch* batch, vx_batch_info* info);
 
 /* Frees the batch's buffers and graph. */
 VX_API void vx_batch_destroy(vx_batch* batch);

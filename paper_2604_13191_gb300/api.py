@@ -69,12 +69,19 @@ EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_l
            "vx_profile_read", "vx_backward", "vx_backward_noalloc", "vx_batch_create", "vx_batch_run",
            "vx_batch_level", "vx_batch_destroy", "vx_set_max_pairs_per_pass", "vx_batch_create_lod",
            "vx_export_compact8", "vx_tessellate_catmull_rom", "vx_voxelize_sampled", "vx_export_leaves",
-           "vx_voxelize_lod_windowed"]
+           "vx_voxelize_lod_windowed", "vx_batch_query"]
 
 
 class VxInstance(C.Structure):
     _fields_ = [("kind", C.c_int32), ("grid", VxGrid), ("prim_begin", C.c_int64), ("num_prims", C.c_int64),
                 ("fiber_begin", C.c_int64), ("num_fibers", C.c_int64)]
+
+
+class VxBatchInfo(C.Structure):
+    _fields_ = [("num_groups", C.c_int32 * 2), ("max_group_pairs", C.c_int64 * 2),
+                ("reduce_blocks_per_sm", C.c_int32 * 2), ("reduce_candidates", (C.c_int32 * 5) * 2),
+                ("reduce_ms", (C.c_float * 5) * 2), ("cluster_tier", (C.c_int32 * 12) * 2),
+                ("cluster_ms", ((C.c_float * 3) * 12) * 2)]
 
 
 class VxStageTime(C.Structure):
@@ -135,6 +142,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         lib.vx_batch_run.argtypes = [P, P]
         lib.vx_batch_level.restype = C.c_int
         lib.vx_batch_level.argtypes = [P, C.c_int, C.c_int, P, C.POINTER(VxLevel)]
+        lib.vx_batch_query.restype = C.c_int
+        lib.vx_batch_query.argtypes = [P, C.POINTER(VxBatchInfo)]
         lib.vx_batch_destroy.restype = None
         lib.vx_batch_destroy.argtypes = [P]
         lib.vx_export_leaves.restype = C.c_int
@@ -756,6 +765,25 @@ class Batch:
         if st != 0:
             raise self.ctx._err(st, "vx_batch_level")
         return self.ctx._view_level(L, self.keep)
+
+    def query(self) -> dict:
+        """vx_batch_query: the plan's groups per kind and the launch shapes its autotuner
+        picked (with the candidates' planning-run times)."""
+        info = VxBatchInfo()
+        st = self.ctx.lib.vx_batch_query(self.h, C.byref(info))
+        if st != 0:
+            raise self.ctx._err(st, "vx_batch_query")
+        out = {}
+        for k, name in enumerate(("triangles", "fibers")):
+            out[name] = {
+                "groups": int(info.num_groups[k]), "max_group_pairs": int(info.max_group_pairs[k]),
+                "reduce_blocks_per_sm": int(info.reduce_blocks_per_sm[k]),
+                "reduce_ms": {int(info.reduce_candidates[k][c]): float(info.reduce_ms[k][c]) for c in range(5)
+                              if info.reduce_candidates[k][c]},
+                "cluster_tier": {l: int(info.cluster_tier[k][l]) for l in range(12) if info.cluster_tier[k][l] >= 0},
+                "cluster_ms": {l: [float(x) for x in info.cluster_ms[k][l]] for l in range(12)
+                               if info.cluster_tier[k][l] >= 0}}
+        return out
 
     def close(self):
         if getattr(self, "h", None):

@@ -242,6 +242,17 @@ __global__ void k_bparent_count_flags(const uint64_t* __restrict__ keys, const u
         flags[i] = (i < n && (i == 0 || inst[i] != inst[i - 1] || (keys[i] >> 3) != (keys[i - 1] >> 3))) ? 1u : 0u;
 }
 
+// exact 64-bit candidate-pair total of every instance (block per instance)
+__global__ void k_inst_pair_totals(const uint32_t* __restrict__ cnt, const BInst* __restrict__ inst,
+                                   unsigned long long* __restrict__ out) {
+    const BInst I = inst[blockIdx.x];
+    unsigned long long acc = 0;
+    for (uint32_t p = threadIdx.x; p < I.num_prims; p += blockDim.x) acc += cnt[I.prim_begin + p];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out + blockIdx.x, acc);
+}
+
 inline unsigned gf(size_t n, int threads, size_t cap_blocks) {
     size_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -256,6 +267,18 @@ enum {
     C_CLUSTER = 50  // [50] parents listed for clustering, [51] their take counter
 };
 
+// Buffers of the pair stages (candidate pairs, sort, segments, per-voxel temporaries and
+// the LoD scratch), shared by the groups of one primitive kind: the groups run one after
+// the other on that kind's stream.  Grown while the groups are planned.
+struct Pool {
+    uint32_t *k0 = nullptr, *v0 = nullptr, *k1 = nullptr, *v1 = nullptr, *flags = nullptr, *idx = nullptr;
+    uint32_t* hist = nullptr;
+    char* so = nullptr;                                   // mask 64 + mass 4 + moment 24 per segment
+    uint32_t *seg_key = nullptr, *seg_nonzero = nullptr, *dst = nullptr, *starts = nullptr;
+    size_t pairs = 0, hist_words = 0, segs = 0;           // capacities
+};
+
+// One group of instances of one kind: planned, captured and replayed as one pipeline.
 struct SubBatch {
     bool fiber = false;
     int ninst = 0;
@@ -269,14 +292,13 @@ struct SubBatch {
     const int64_t* off = nullptr;
     const float* weights = nullptr;
     std::vector<BInst> hinst;
+    std::vector<uint32_t> host_counts, host_starts;
+    Pool* pool = nullptr;
     BInst* dinst = nullptr;
     uint8_t* inst_of = nullptr;
     float4 *r0 = nullptr, *r1 = nullptr, *r2 = nullptr;
     uint32_t *cnt = nullptr, *offs = nullptr, *fs = nullptr;
-    uint32_t *k0 = nullptr, *v0 = nullptr, *k1 = nullptr, *v1 = nullptr;
-    uint32_t *hist = nullptr, *part = nullptr, *flags = nullptr, *idx = nullptr, *starts = nullptr;
-    SegOut seg{};
-    uint32_t* dst = nullptr;
+    uint32_t* part = nullptr;
     uint32_t* counters = nullptr;           // 64 words
     uint32_t* inst_start = nullptr;         // [(Lmax + 1)][ninst + 1]
     vx_level lv[kMaxLevels + 1];
@@ -284,13 +306,24 @@ struct SubBatch {
     void* stats[kMaxLevels + 1] = {};      // K > 1: lobe statistics of each level (none for 0)
     uint32_t* work[kMaxLevels + 1] = {};   // K > 1: parents listed for clustering
     uint32_t cap_pairs = 0, cap_seg = 0, cap_v[kMaxLevels + 1];
+    uint32_t plan_pairs = 0;                   // candidate pairs measured by the planning run
+    // launch shapes picked by timing candidates on the planning run (autotuner)
+    int red_bpsm = 0;                          // reduce kernel: resident blocks per SM
+    int red_cand[5] = {};                      // the candidates timed, and their times
+    float red_ms[5] = {};
+    int tier[kMaxLevels + 1];                  // clustering tier per level (-1: by parent count)
+    float tier_ms[kMaxLevels + 1][3] = {};
+    SubBatch() {
+        for (int& t : tier) t = -1;
+    }
 };
 
 }  // namespace
 
 struct vx_batch {
     vx_context* ctx = nullptr;
-    SubBatch sb[2];          // 0: triangles, 1: fibers
+    std::vector<SubBatch> groups[2];   // per kind (0: triangles, 1: fibers), instances in order
+    Pool pool[2];
     std::vector<void*> allocs;
     float headroom = 0.125f;
     int K = 1;                              // lobes per voxel of the levels above 0
@@ -303,9 +336,7 @@ struct vx_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int num_instances = 0;
-    std::vector<int> kind_of, local_of;   // instance -> (sub-batch, index in it)
-    std::vector<uint32_t> host_counts[2];
-    std::vector<uint32_t> host_starts[2];
+    std::vector<int> kind_of, group_of, local_of;   // instance -> (kind, group, index in the group)
     bool host_valid = false;
     int64_t launches_per_run = 0;
 };
@@ -319,9 +350,138 @@ vx_status balloc(vx_batch* b, void** p, size_t bytes, cudaStream_t s) {
     return VX_OK;
 }
 
+// Grows a pool buffer to at least `bytes` (its previous contents are not kept).
+vx_status pool_grow(vx_batch* b, void** p, size_t bytes, cudaStream_t s) {
+    if (*p) vx_dev_free(b->ctx, *p, s);
+    *p = vx_dev_alloc(b->ctx, bytes, s);
+    return *p ? VX_OK : VX_ERR_OUT_OF_MEMORY;
+}
+
+vx_status pool_pairs(vx_batch* b, Pool& P, size_t pairs, size_t hist_words, cudaStream_t s) {
+    if (pairs > P.pairs) {
+        for (uint32_t** q : {&P.k0, &P.v0, &P.k1, &P.v1, &P.flags, &P.idx})
+            VX_TRY(pool_grow(b, (void**)q, pairs * 4, s));
+        P.pairs = pairs;
+    }
+    if (hist_words > P.hist_words) {
+        VX_TRY(pool_grow(b, (void**)&P.hist, hist_words * 4, s));
+        P.hist_words = hist_words;
+    }
+    return VX_OK;
+}
+
+vx_status pool_segs(vx_batch* b, Pool& P, size_t segs, cudaStream_t s) {
+    if (segs <= P.segs) return VX_OK;
+    VX_TRY(pool_grow(b, (void**)&P.so, segs * (64 + 4 + 24), s));
+    for (uint32_t** q : {&P.seg_key, &P.seg_nonzero, &P.dst}) VX_TRY(pool_grow(b, (void**)q, segs * 4, s));
+    VX_TRY(pool_grow(b, (void**)&P.starts, (segs + 2) * 4, s));
+    P.segs = segs;
+    return VX_OK;
+}
+
+SegOut pool_segout(const Pool& P) {
+    SegOut o;
+    o.mask = (uint64_t*)P.so;
+    o.moment = (float*)(P.so + P.segs * 64);
+    o.mass = (float*)(P.so + P.segs * 88);
+    o.key = P.seg_key;
+    o.nonzero = P.seg_nonzero;
+    return o;
+}
+
 uint32_t with_headroom(uint32_t n, float h) {
     double x = (double)n * (1.0 + (double)h) + 1024.0;
     return x > 4.0e9 ? 0xffffffffu : (uint32_t)x;
+}
+
+// Mean device time of `reps` runs of fn() on stream s (CUDA events; synchronises).
+template <class F>
+vx_status time_launches(cudaStream_t s, int reps, F fn, float* ms) {
+    cudaEvent_t a = nullptr, e = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&e) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return VX_ERR_CUDA;
+    }
+    cudaError_t r = cudaEventRecord(a, s);
+    for (int i = 0; i < reps && r == cudaSuccess; ++i) r = fn();
+    if (r == cudaSuccess) r = cudaEventRecord(e, s);
+    if (r == cudaSuccess) r = cudaEventSynchronize(e);
+    if (r == cudaSuccess) r = cudaEventElapsedTime(ms, a, e);
+    cudaEventDestroy(a);
+    cudaEventDestroy(e);
+    if (r != cudaSuccess) return VX_ERR_CUDA;
+    *ms /= (float)reps;
+    return VX_OK;
+}
+
+// Candidate pairs of every instance of one kind (prep and count over all of its primitives,
+// in temporary buffers), for grouping the instances into passes.  Synchronises the stream.
+vx_status instance_pairs(vx_batch* b, bool fiber, const vx_primitives* prims, const std::vector<BInst>& inst,
+                         uint32_t np, int64_t F, cudaStream_t s, std::vector<uint64_t>* pairs) {
+    vx_context* ctx = b->ctx;
+    const int ninst = (int)inst.size();
+    std::vector<void*> tmp;
+    vx_status st = VX_OK;
+    auto get = [&](size_t bytes) -> void* {
+        void* p = vx_dev_alloc(ctx, bytes, s);
+        if (p) tmp.push_back(p); else st = VX_ERR_OUT_OF_MEMORY;
+        return p;
+    };
+    BInst* dinst = (BInst*)get(sizeof(BInst) * ninst);
+    uint8_t* inst_of = (uint8_t*)get((size_t)np + 16);
+    float4* r0 = (float4*)get((size_t)np * 16);
+    float4* r1 = (float4*)get((size_t)np * 16);
+    float4* r2 = fiber ? nullptr : (float4*)get((size_t)np * 16);
+    uint32_t* cnt = (uint32_t*)get((size_t)np * 4);
+    uint32_t* fs = (uint32_t*)get((size_t)(fiber ? F : 1) * 4 + 16);
+    uint32_t* part = (uint32_t*)get((std::max<size_t>(np, (size_t)(fiber ? F : 1)) / 2048 + 64) * 4);
+    uint32_t* C = (uint32_t*)get(64 * 4);
+    unsigned long long* tot = (unsigned long long*)get((size_t)ninst * 8);
+    cudaError_t e = cudaSuccess;
+    if (st == VX_OK) {
+        e = cudaMemcpyAsync(dinst, inst.data(), sizeof(BInst) * ninst, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(C, 0, 64 * 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(tot, 0, (size_t)ninst * 8, s);
+        if (e == cudaSuccess && fiber) {
+            k_fiber_seg_counts<<<gf((size_t)F, 256, 1u << 30), 256, 0, s>>>(prims->fiber_offsets, F, prims->num_ctrl, fs,
+                                                                             C + C_ERR);
+            e = vx_scan_u32_scratch(fs, fs, (uint32_t)F, C + C_SEGTOT, part, s);
+            if (e == cudaSuccess)
+                k_bprep_fibers<<<gf(np, 256, 1u << 30), 256, 0, s>>>((const float4*)prims->ctrl, prims->num_ctrl,
+                                                                     prims->fiber_offsets, fs, F, prims->weights, np,
+                                                                     dinst, ninst, r0, r1, inst_of, C + C_ERR);
+        } else if (e == cudaSuccess) {
+            k_bprep_tris<<<gf(np, 256, 1u << 30), 256, 0, s>>>((const float4*)prims->tri_verts, prims->weights, np,
+                                                               dinst, ninst, r0, r1, r2, inst_of, C + C_ERR);
+        }
+        const unsigned cblocks = (unsigned)std::min<size_t>((np + EMIT_WARPS - 1) / EMIT_WARPS, (size_t)vx::kSMs * 64);
+        if (e == cudaSuccess) {
+            if (fiber)
+                k_bcandidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, r2, np, dinst, inst_of, cnt,
+                                                                               nullptr, 0, nullptr, nullptr);
+            else
+                k_bcandidates<false, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, r2, np, dinst, inst_of, cnt,
+                                                                                nullptr, 0, nullptr, nullptr);
+            k_inst_pair_totals<<<ninst, 256, 0, s>>>(cnt, dinst, tot);
+            e = cudaGetLastError();
+        }
+        std::vector<unsigned long long> h(ninst);
+        uint32_t err = 0, segtot = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), tot, (size_t)ninst * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&err, C + C_ERR, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&segtot, C + C_SEGTOT, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            vx_record_cuda_error(ctx, e, "instance pair counts");
+            st = VX_ERR_CUDA;
+        } else if (err || (fiber && segtot != np)) {
+            st = VX_ERR_INVALID_ARG;
+        } else {
+            pairs->assign(h.begin(), h.end());
+        }
+    }
+    for (void* p : tmp) vx_dev_free(ctx, p, s);
+    return st;
 }
 
 // Enqueue the pipeline of one sub-batch.  plan: synchronise after each counting stage,
@@ -330,6 +490,7 @@ uint32_t with_headroom(uint32_t n, float h) {
 vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* nl) {
     if (S.np == 0) return VX_OK;
     vx_context* ctx = b->ctx;
+    Pool& PL = *S.pool;
     uint32_t* C = S.counters;
     uint32_t* host = (uint32_t*)ctx->host_pin;
     const unsigned blk = vx::kSMs * 16;
@@ -368,16 +529,11 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
         if (err) return VX_ERR_INVALID_ARG;
         const uint32_t np = readback(C_PAIRS_TOT);
         if (np >= 0x80000000u) return VX_ERR_CAPACITY;
+        S.plan_pairs = np;
         S.cap_pairs = with_headroom(np, b->headroom);
         const uint32_t nt = (S.cap_pairs + 4095) / 4096;
         const size_t hn = (size_t)256 * nt;
-        VX_TRY(balloc(b, (void**)&S.k0, (size_t)S.cap_pairs * 4, s));
-        VX_TRY(balloc(b, (void**)&S.v0, (size_t)S.cap_pairs * 4, s));
-        VX_TRY(balloc(b, (void**)&S.k1, (size_t)S.cap_pairs * 4, s));
-        VX_TRY(balloc(b, (void**)&S.v1, (size_t)S.cap_pairs * 4, s));
-        VX_TRY(balloc(b, (void**)&S.hist, hn * 4, s));
-        VX_TRY(balloc(b, (void**)&S.flags, (size_t)S.cap_pairs * 4, s));
-        VX_TRY(balloc(b, (void**)&S.idx, (size_t)S.cap_pairs * 4, s));
+        VX_TRY(pool_pairs(b, PL, S.cap_pairs, hn, s));
         // scan partials: the largest scanned array is max(hist, pairs)
         const size_t mx = std::max<size_t>(hn, S.cap_pairs);
         VX_TRY(balloc(b, (void**)&S.part, (mx / 2048 + 64) * 4, s));
@@ -385,53 +541,68 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
     k_clamp<<<1, 1, 0, s>>>(C + C_PAIRS_TOT, S.cap_pairs, C + C_PAIRS, C + C_ERR);
     if (S.fiber)
         k_bcandidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(S.r0, S.r1, S.r2, S.np, S.dinst, S.inst_of,
-                                                                      nullptr, S.offs, S.cap_pairs, S.k0, S.v0);
+                                                                      nullptr, S.offs, S.cap_pairs, PL.k0, PL.v0);
     else
         k_bcandidates<false, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(S.r0, S.r1, S.r2, S.np, S.dinst, S.inst_of,
-                                                                       nullptr, S.offs, S.cap_pairs, S.k0, S.v0);
-    k_pad<<<blk, 256, 0, s>>>(S.k0, S.v0, C + C_PAIRS, S.cap_pairs);
+                                                                       nullptr, S.offs, S.cap_pairs, PL.k0, PL.v0);
+    k_pad<<<blk, 256, 0, s>>>(PL.k0, PL.v0, C + C_PAIRS, S.cap_pairs);
     *nl += 3;
     // ---- sort by (instance, key) ------------------------------------------------------------
-    uint32_t *k0 = S.k0, *v0 = S.v0, *k1 = S.k1, *v1 = S.v1;
-    if (vx_radix_sort_u32_scratch(&k0, &v0, &k1, &v1, S.cap_pairs, S.key_bits, S.inst_of, S.hist, S.part, s) !=
+    uint32_t *k0 = PL.k0, *v0 = PL.v0, *k1 = PL.k1, *v1 = PL.v1;
+    if (vx_radix_sort_u32_scratch(&k0, &v0, &k1, &v1, S.cap_pairs, S.key_bits, S.inst_of, PL.hist, S.part, s) !=
         cudaSuccess)
         return VX_ERR_CUDA;
     *nl += 5 * ((S.key_bits + 7) / 8 + 1);
     // ---- segments ---------------------------------------------------------------------------
-    k_bhead_flags<<<gf(S.cap_pairs, 256, blk), 256, 0, s>>>(k0, v0, S.inst_of, C + C_PAIRS, S.cap_pairs, S.flags);
-    if (vx_scan_u32_scratch(S.flags, S.idx, S.cap_pairs, C + C_SEG_TOT, S.part, s) != cudaSuccess) return VX_ERR_CUDA;
+    k_bhead_flags<<<gf(S.cap_pairs, 256, blk), 256, 0, s>>>(k0, v0, S.inst_of, C + C_PAIRS, S.cap_pairs, PL.flags);
+    if (vx_scan_u32_scratch(PL.flags, PL.idx, S.cap_pairs, C + C_SEG_TOT, S.part, s) != cudaSuccess) return VX_ERR_CUDA;
     *nl += 4;
     if (plan) {
         const uint32_t ns = readback(C_SEG_TOT);
         S.cap_seg = std::min(with_headroom(ns, b->headroom), S.cap_pairs);
-        VX_TRY(balloc(b, (void**)&S.starts, ((size_t)S.cap_seg + 2) * 4, s));
-        char* so = nullptr;
-        VX_TRY(balloc(b, (void**)&so, (size_t)S.cap_seg * (64 + 4 + 24), s));
-        S.seg.mask = (uint64_t*)so;
-        S.seg.mass = (float*)(so + (size_t)S.cap_seg * 64);
-        S.seg.moment = (float*)(so + (size_t)S.cap_seg * 68);
-        VX_TRY(balloc(b, (void**)&S.seg.key, (size_t)S.cap_seg * 4, s));
-        VX_TRY(balloc(b, (void**)&S.seg.nonzero, (size_t)S.cap_seg * 4, s));
-        VX_TRY(balloc(b, (void**)&S.dst, (size_t)S.cap_seg * 4, s));
+        VX_TRY(pool_segs(b, PL, S.cap_seg, s));
     }
+    const SegOut seg = pool_segout(PL);
     k_clamp<<<1, 1, 0, s>>>(C + C_SEG_TOT, S.cap_seg, C + C_SEG, C + C_ERR);
-    k_bhead_starts<<<gf(S.cap_pairs, 256, blk), 256, 0, s>>>(k0, v0, S.inst_of, C + C_PAIRS, S.idx, C + C_SEG_TOT,
-                                                             S.cap_seg, S.starts);
+    k_bhead_starts<<<gf(S.cap_pairs, 256, blk), 256, 0, s>>>(k0, v0, S.inst_of, C + C_PAIRS, PL.idx, C + C_SEG_TOT,
+                                                             S.cap_seg, PL.starts);
     // ---- per-voxel reduction ------------------------------------------------------------------
     // resident blocks taking voxels from a counter (zeroed by a node of the graph)
-    if (cudaMemsetAsync(C + C_TAKE, 0, 4, s) != cudaSuccess) return VX_ERR_CUDA;
-    if (S.fiber) {
-        const unsigned rblocks = (unsigned)std::min<size_t>((S.cap_seg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 7);
-        k_reduce_fibers<<<rblocks, RED_WARPS * 32, 0, s>>>(k0, v0, S.starts, C + C_SEG, S.r0, S.r1, S.seg, 0, 0, 0,
-                                                          C + C_TAKE);
-    } else {
-        const unsigned rblocks = (unsigned)std::min<size_t>((S.cap_seg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 32);
-        k_reduce_tris<<<rblocks, RED_WARPS * 32, 0, s>>>(k0, v0, S.starts, C + C_SEG, S.r0, S.r1, S.r2, S.seg, 0, 0,
-                                                         0, C + C_TAKE);
+    auto launch_reduce = [&](int bpsm) -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(C + C_TAKE, 0, 4, s);
+        if (e != cudaSuccess) return e;
+        const unsigned rblocks =
+            (unsigned)std::min<size_t>((S.cap_seg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * bpsm);
+        if (S.fiber)
+            k_reduce_fibers<<<std::max(rblocks, 1u), RED_WARPS * 32, 0, s>>>(k0, v0, PL.starts, C + C_SEG, S.r0, S.r1,
+                                                                              seg, 0, 0, 0, C + C_TAKE);
+        else
+            k_reduce_tris<<<std::max(rblocks, 1u), RED_WARPS * 32, 0, s>>>(k0, v0, PL.starts, C + C_SEG, S.r0, S.r1,
+                                                                            S.r2, seg, 0, 0, 0, C + C_TAKE);
+        return cudaGetLastError();
+    };
+    if (S.red_bpsm == 0) S.red_bpsm = S.fiber ? 7 : 32;
+    if (launch_reduce(S.red_bpsm) != cudaSuccess) return VX_ERR_CUDA;
+    if (plan) {
+        // autotuner: time the reduce at each candidate grid on the planning run's pairs (every
+        // grid gives the same outputs) and keep the fastest
+        static const int fib_c[5] = {3, 4, 5, 6, 7}, tri_c[5] = {4, 8, 16, 24, 32};
+        const int* cand = S.fiber ? fib_c : tri_c;
+        float best = 0.0f;
+        for (int c = 0; c < 5; ++c) {
+            float ms = 0.0f;
+            VX_TRY(time_launches(s, 2, [&]() { return launch_reduce(cand[c]); }, &ms));
+            S.red_cand[c] = cand[c];
+            S.red_ms[c] = ms;
+            if (c == 0 || ms < best) {
+                best = ms;
+                S.red_bpsm = cand[c];
+            }
+        }
     }
     // non-empty flags beyond the clamped segment count read as zero in the compaction scan
-    k_zero_tail<<<blk, 256, 0, s>>>(S.seg.nonzero, C + C_SEG, S.cap_seg);
-    if (vx_scan_u32_scratch(S.seg.nonzero, S.dst, S.cap_seg, C + C_VOX_TOT, S.part, s) != cudaSuccess)
+    k_zero_tail<<<blk, 256, 0, s>>>(seg.nonzero, C + C_SEG, S.cap_seg);
+    if (vx_scan_u32_scratch(seg.nonzero, PL.dst, S.cap_seg, C + C_VOX_TOT, S.part, s) != cudaSuccess)
         return VX_ERR_CUDA;
     *nl += 5;
     // ---- level 0 ------------------------------------------------------------------------------
@@ -443,7 +614,7 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
         VX_TRY(balloc(b, (void**)&S.linst[0], (size_t)S.cap_v[0] * 2 + 16, s));
     }
     k_clamp<<<1, 1, 0, s>>>(C + C_VOX_TOT, S.cap_v[0], C + C_VOX, C + C_ERR);
-    k_bfinalize<<<gf(S.cap_seg, 256, blk), 256, 0, s>>>(S.seg, C + C_SEG, S.dst, S.cap_v[0], S.starts, v0, S.inst_of,
+    k_bfinalize<<<gf(S.cap_seg, 256, blk), 256, 0, s>>>(seg, C + C_SEG, PL.dst, S.cap_v[0], PL.starts, v0, S.inst_of,
                                                         S.lv[0], S.linst[0]);
     k_inst_offsets<<<(S.ninst + 1 + 127) / 128, 128, 0, s>>>(S.linst[0], C + C_VOX, S.ninst, S.inst_start);
     *nl += 3;
@@ -453,8 +624,8 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
         if (plan) {
             // exact parent count of this level: run the flag scan once to measure it
             k_bparent_count_flags<<<gf(S.cap_v[l - 1], 256, blk), 256, 0, s>>>(S.lv[l - 1].keys, S.linst[l - 1], nprev,
-                                                                               S.cap_v[l - 1], S.flags);
-            if (vx_scan_u32_scratch(S.flags, S.idx, S.cap_v[l - 1], C + C_LVL + 16 + l, S.part, s) != cudaSuccess)
+                                                                               S.cap_v[l - 1], PL.flags);
+            if (vx_scan_u32_scratch(PL.flags, PL.idx, S.cap_v[l - 1], C + C_LVL + 16 + l, S.part, s) != cudaSuccess)
                 return VX_ERR_CUDA;
             const uint32_t np = readback(C_LVL + 16 + l);
             S.cap_v[l] = with_headroom(np, b->headroom);
@@ -467,10 +638,27 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
             }
         }
         if (vx_lod_step_batched(&S.lv[l - 1], S.linst[l - 1], nprev, S.cap_v[l - 1], &S.lv[l], S.linst[l],
-                                C + C_LVL + l, S.cap_v[l], S.flags, S.idx, S.starts, S.part, C + C_LVL + 16 + l,
+                                C + C_LVL + l, S.cap_v[l], PL.flags, PL.idx, PL.starts, S.part, C + C_LVL + 16 + l,
                                 C + C_ERR, b->dirs4, b->n_dirs, S.work[l], C + C_CLUSTER,
-                                l > 1 ? S.stats[l - 1] : nullptr, S.stats[l], b->merge, s) != cudaSuccess)
+                                l > 1 ? S.stats[l - 1] : nullptr, S.stats[l], b->merge, S.tier[l], s) != cudaSuccess)
             return VX_ERR_CUDA;
+        if (plan && b->K > 1) {
+            // autotuner: time the three clustering tiers on this level's parents (same result)
+            float best = 0.0f;
+            for (int t = 0; t < 3; ++t) {
+                float ms = 0.0f;
+                VX_TRY(time_launches(s, 2, [&]() {
+                    return vx_lod_cluster_batched(&S.lv[l - 1], &S.lv[l], PL.starts, S.work[l], C + C_CLUSTER,
+                                                  b->dirs4, b->n_dirs, l > 1 ? S.stats[l - 1] : nullptr, S.stats[l],
+                                                  S.cap_v[l], b->merge, t, s);
+                }, &ms));
+                S.tier_ms[l][t] = ms;
+                if (t == 0 || ms < best) {
+                    best = ms;
+                    S.tier[l] = t;
+                }
+            }
+        }
         k_inst_offsets<<<(S.ninst + 1 + 127) / 128, 128, 0, s>>>(S.linst[l], C + C_LVL + l, S.ninst,
                                                                  S.inst_start + (size_t)l * (S.ninst + 1));
         *nl += 9;
@@ -508,6 +696,7 @@ extern "C" vx_status vx_batch_create_lod(vx_context* ctx, const vx_primitives* t
     b->K = K;
     b->num_instances = num_instances;
     b->kind_of.resize(num_instances);
+    b->group_of.resize(num_instances);
     b->local_of.resize(num_instances);
     vx_status st = VX_OK;
     auto fail = [&](vx_status e) {
@@ -517,6 +706,9 @@ extern "C" vx_status vx_batch_create_lod(vx_context* ctx, const vx_primitives* t
     // instance tables per kind, checked on the host (ranges contiguous and in order)
     uint32_t next[2] = {0, 0};
     int64_t next_fiber = 0;
+    std::vector<BInst> kinst[2];
+    std::vector<int64_t> kfib[2];                 // fibers: first fiber of each instance
+    std::vector<int> kidx[2];                     // batch index of each instance of a kind
     for (int i = 0; i < num_instances; ++i) {
         const vx_instance& I = instances[i];
         const int k = I.kind == VX_FIBERS ? 1 : 0;
@@ -525,9 +717,9 @@ extern "C" vx_status vx_batch_create_lod(vx_context* ctx, const vx_primitives* t
         if (R == 0 || (R & (R - 1)) != 0 || !(I.grid.voxel_size > 0.0f)) return fail(VX_ERR_INVALID_ARG);
         if (R > 1024 || I.grid.sub_res != 8) return fail(VX_ERR_UNSUPPORTED);
         if (I.prim_begin != (int64_t)next[k] || I.num_prims < 0) return fail(VX_ERR_INVALID_ARG);
+        if ((int64_t)next[k] + I.num_prims > 0xffffffffll) return fail(VX_ERR_CAPACITY);
         if (k == 1 && (I.fiber_begin != next_fiber || I.num_fibers < 0)) return fail(VX_ERR_INVALID_ARG);
-        SubBatch& S = b->sb[k];
-        if (S.ninst >= 255) return fail(VX_ERR_UNSUPPORTED);
+        if (kinst[k].size() >= 255) return fail(VX_ERR_UNSUPPORTED);
         BInst bi;
         bi.o[0] = I.grid.origin[0]; bi.o[1] = I.grid.origin[1]; bi.o[2] = I.grid.origin[2];
         bi.s = 1.0f / I.grid.voxel_size;
@@ -537,11 +729,10 @@ extern "C" vx_status vx_batch_create_lod(vx_context* ctx, const vx_primitives* t
         bi.L = L;
         bi.prim_begin = (uint32_t)I.prim_begin;
         bi.num_prims = (uint32_t)I.num_prims;
-        S.hinst.push_back(bi);
-        S.Lmax = std::max(S.Lmax, L);
-        S.key_bits = std::max(S.key_bits, 3 * L);
+        kinst[k].push_back(bi);
+        kfib[k].push_back(I.fiber_begin);
+        kidx[k].push_back(i);
         b->kind_of[i] = k;
-        b->local_of[i] = S.ninst++;
         next[k] += (uint32_t)I.num_prims;
         if (k == 1) next_fiber += I.num_fibers;
     }
@@ -558,39 +749,85 @@ extern "C" vx_status vx_batch_create_lod(vx_context* ctx, const vx_primitives* t
         if ((st = balloc(b, (void**)&b->dirs4, (size_t)lod->n_samples * 16, s)) != VX_OK) return fail(st);
         if (vx_lod_batched_prepare(K, lod->dirs, lod->n_samples, b->dirs4, s) != cudaSuccess) return fail(VX_ERR_CUDA);
     }
+    // Groups: consecutive instances of a kind whose candidate pairs fit one pass (with the
+    // headroom), measured by counting every instance once.
+    const uint64_t pass_limit = (uint64_t)std::min<int64_t>(ctx->max_pairs, 0x7fffffffll);
+    const uint64_t group_limit =
+        (uint64_t)std::max(0.0, ((double)pass_limit - 1024.0) / (1.0 + (double)headroom));
     for (int k = 0; k < 2; ++k) {
-        SubBatch& S = b->sb[k];
-        S.fiber = k == 1;
-        S.np = next[k];
-        if (S.np == 0) continue;
-        if (S.fiber) {
-            S.ctrl = fibers->ctrl;
-            S.num_ctrl = fibers->num_ctrl;
-            S.off = fibers->fiber_offsets;
-            S.F = fibers->num_fibers;
-            S.weights = fibers->weights;
-        } else {
-            S.tri = tris->tri_verts;
-            S.weights = tris->weights;
-        }
-        if ((st = balloc(b, (void**)&S.dinst, sizeof(BInst) * S.ninst, s)) != VX_OK) return fail(st);
-        if (cudaMemcpyAsync(S.dinst, S.hinst.data(), sizeof(BInst) * S.ninst, cudaMemcpyHostToDevice, s) != cudaSuccess)
-            return fail(VX_ERR_CUDA);
-        if ((st = balloc(b, (void**)&S.inst_of, (size_t)S.np + 16, s)) != VX_OK) return fail(st);
-        if ((st = balloc(b, (void**)&S.r0, (size_t)S.np * 16, s)) != VX_OK) return fail(st);
-        if ((st = balloc(b, (void**)&S.r1, (size_t)S.np * 16, s)) != VX_OK) return fail(st);
-        if (!S.fiber && (st = balloc(b, (void**)&S.r2, (size_t)S.np * 16, s)) != VX_OK) return fail(st);
-        if ((st = balloc(b, (void**)&S.cnt, (size_t)S.np * 4, s)) != VX_OK) return fail(st);
-        if ((st = balloc(b, (void**)&S.offs, (size_t)S.np * 4, s)) != VX_OK) return fail(st);
-        if ((st = balloc(b, (void**)&S.fs, (size_t)(S.fiber ? S.F : 1) * 4 + 16, s)) != VX_OK) return fail(st);
-        if ((st = balloc(b, (void**)&S.counters, 64 * 4, s)) != VX_OK) return fail(st);
-        if ((st = balloc(b, (void**)&S.inst_start, (size_t)(kMaxLevels + 1) * (S.ninst + 1) * 4, s)) != VX_OK)
+        const int ninst = (int)kinst[k].size();
+        if (next[k] == 0 || ninst == 0) continue;
+        std::vector<uint64_t> pairs;
+        if ((st = instance_pairs(b, k == 1, k == 1 ? fibers : tris, kinst[k], next[k], k == 1 ? next_fiber : 0, s,
+                                 &pairs)) != VX_OK)
             return fail(st);
-        // partials for the scans before the pair buffers exist (largest: primitives or fibers)
-        const size_t pre = std::max<size_t>(S.np, (size_t)(S.fiber ? S.F : 1));
-        if ((st = balloc(b, (void**)&S.part, (pre / 2048 + 64) * 4, s)) != VX_OK) return fail(st);
-        int64_t nl = 0;
-        if ((st = enqueue(b, S, s, true, &nl)) != VX_OK) return fail(st);
+        std::vector<std::pair<int, int>> ranges;   // [first, last) instance of each group
+        int first = 0;
+        uint64_t acc = 0;
+        for (int i = 0; i < ninst; ++i) {
+            if (pairs[i] > group_limit) return fail(VX_ERR_CAPACITY);   // one instance over one pass
+            if (i > first && acc + pairs[i] > group_limit) {
+                ranges.push_back({first, i});
+                first = i;
+                acc = 0;
+            }
+            acc += pairs[i];
+        }
+        ranges.push_back({first, ninst});
+        b->groups[k].resize(ranges.size());
+        for (size_t g = 0; g < ranges.size(); ++g) {
+            SubBatch& S = b->groups[k][g];
+            S.fiber = k == 1;
+            S.pool = &b->pool[k];
+            const int i0 = ranges[g].first, i1 = ranges[g].second;
+            const uint32_t pbase = kinst[k][i0].prim_begin;
+            for (int i = i0; i < i1; ++i) {
+                BInst bi = kinst[k][i];
+                bi.prim_begin -= pbase;
+                S.hinst.push_back(bi);
+                S.Lmax = std::max(S.Lmax, bi.L);
+                S.key_bits = std::max(S.key_bits, 3 * bi.L);
+                S.np += bi.num_prims;
+                b->group_of[kidx[k][i]] = (int)g;
+                b->local_of[kidx[k][i]] = S.ninst++;
+            }
+            if (S.fiber) {
+                const int64_t f0 = kfib[k][i0];
+                const int64_t f1 = (i1 < ninst) ? kfib[k][i1] : next_fiber;
+                S.ctrl = fibers->ctrl;
+                S.num_ctrl = fibers->num_ctrl;
+                S.off = fibers->fiber_offsets + f0;
+                S.F = f1 - f0;
+                S.weights = fibers->weights ? fibers->weights + pbase : nullptr;
+            } else {
+                S.tri = tris->tri_verts + (size_t)pbase * 12;
+                S.weights = tris->weights ? tris->weights + pbase : nullptr;
+            }
+        }
+    }
+    for (int k = 0; k < 2; ++k) {
+        for (SubBatch& S : b->groups[k]) {
+            if (S.np == 0) continue;
+            if ((st = balloc(b, (void**)&S.dinst, sizeof(BInst) * S.ninst, s)) != VX_OK) return fail(st);
+            if (cudaMemcpyAsync(S.dinst, S.hinst.data(), sizeof(BInst) * S.ninst, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess)
+                return fail(VX_ERR_CUDA);
+            if ((st = balloc(b, (void**)&S.inst_of, (size_t)S.np + 16, s)) != VX_OK) return fail(st);
+            if ((st = balloc(b, (void**)&S.r0, (size_t)S.np * 16, s)) != VX_OK) return fail(st);
+            if ((st = balloc(b, (void**)&S.r1, (size_t)S.np * 16, s)) != VX_OK) return fail(st);
+            if (!S.fiber && (st = balloc(b, (void**)&S.r2, (size_t)S.np * 16, s)) != VX_OK) return fail(st);
+            if ((st = balloc(b, (void**)&S.cnt, (size_t)S.np * 4, s)) != VX_OK) return fail(st);
+            if ((st = balloc(b, (void**)&S.offs, (size_t)S.np * 4, s)) != VX_OK) return fail(st);
+            if ((st = balloc(b, (void**)&S.fs, (size_t)(S.fiber ? S.F : 1) * 4 + 16, s)) != VX_OK) return fail(st);
+            if ((st = balloc(b, (void**)&S.counters, 64 * 4, s)) != VX_OK) return fail(st);
+            if ((st = balloc(b, (void**)&S.inst_start, (size_t)(kMaxLevels + 1) * (S.ninst + 1) * 4, s)) != VX_OK)
+                return fail(st);
+            // partials for the scans before the pair buffers exist (largest: primitives or fibers)
+            const size_t pre = std::max<size_t>(S.np, (size_t)(S.fiber ? S.F : 1));
+            if ((st = balloc(b, (void**)&S.part, (pre / 2048 + 64) * 4, s)) != VX_OK) return fail(st);
+            int64_t nl = 0;
+            if ((st = enqueue(b, S, s, true, &nl)) != VX_OK) return fail(st);
+        }
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(VX_ERR_CUDA);
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(VX_ERR_CUDA);
@@ -615,8 +852,10 @@ extern "C" vx_status vx_batch_run(vx_batch* b, void* stream) {
         if (cudaEventRecord(b->fork, b->cap_stream) != cudaSuccess ||
             cudaStreamWaitEvent(b->cap_stream2, b->fork, 0) != cudaSuccess)
             st = VX_ERR_CUDA;
-        if (st == VX_OK) st = enqueue(b, b->sb[0], b->cap_stream2, false, &nl);
-        if (st == VX_OK) st = enqueue(b, b->sb[1], b->cap_stream, false, &nl);
+        for (SubBatch& S : b->groups[0])
+            if (st == VX_OK) st = enqueue(b, S, b->cap_stream2, false, &nl);
+        for (SubBatch& S : b->groups[1])
+            if (st == VX_OK) st = enqueue(b, S, b->cap_stream, false, &nl);
         if (cudaEventRecord(b->join, b->cap_stream2) != cudaSuccess ||
             cudaStreamWaitEvent(b->cap_stream, b->join, 0) != cudaSuccess)
             st = st == VX_OK ? VX_ERR_CUDA : st;
@@ -664,28 +903,29 @@ extern "C" vx_status vx_batch_level(vx_batch* b, int instance, int level, void* 
     if (!b || !view || instance < 0 || instance >= b->num_instances || level < 0) return VX_ERR_INVALID_ARG;
     memset(view, 0, sizeof(*view));
     const int k = b->kind_of[instance], li = b->local_of[instance];
-    SubBatch& S = b->sb[k];
+    SubBatch& S = b->groups[k][b->group_of[instance]];
     const BInst& I = S.hinst[li];
     if (level > I.L) return VX_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (!b->host_valid) {
         for (int kk = 0; kk < 2; ++kk) {
-            SubBatch& T = b->sb[kk];
-            b->host_counts[kk].assign(64, 0);
-            b->host_starts[kk].assign((size_t)(kMaxLevels + 1) * (T.ninst + 1), 0);
-            if (T.np == 0) continue;
-            if (cudaMemcpyAsync(b->host_counts[kk].data(), T.counters, 64 * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaMemcpyAsync(b->host_starts[kk].data(), T.inst_start, b->host_starts[kk].size() * 4,
-                                cudaMemcpyDeviceToHost, s) != cudaSuccess)
-                return VX_ERR_CUDA;
+            for (SubBatch& T : b->groups[kk]) {
+                T.host_counts.assign(64, 0);
+                T.host_starts.assign((size_t)(kMaxLevels + 1) * (T.ninst + 1), 0);
+                if (T.np == 0) continue;
+                if (cudaMemcpyAsync(T.host_counts.data(), T.counters, 64 * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaMemcpyAsync(T.host_starts.data(), T.inst_start, T.host_starts.size() * 4,
+                                    cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                    return VX_ERR_CUDA;
+            }
         }
         if (cudaStreamSynchronize(s) != cudaSuccess) return VX_ERR_CUDA;
         b->host_valid = true;
     }
-    const uint32_t err = b->host_counts[k][C_ERR];
+    const uint32_t err = S.host_counts[C_ERR];
     if (err & 2u) return VX_ERR_CAPACITY;
     if (err & 1u) return VX_ERR_INVALID_ARG;
-    const uint32_t* st = b->host_starts[k].data() + (size_t)level * (S.ninst + 1);
+    const uint32_t* st = S.host_starts.data() + (size_t)level * (S.ninst + 1);
     const uint32_t beg = st[li], end = st[li + 1];
     const vx_level& L = S.lv[level];
     view->level = level;
@@ -705,6 +945,30 @@ extern "C" vx_status vx_batch_level(vx_batch* b, int instance, int level, void* 
     return VX_OK;
 }
 
+extern "C" vx_status vx_batch_query(const vx_batch* b, vx_batch_info* info) {
+    if (!b || !info) return VX_ERR_INVALID_ARG;
+    memset(info, 0, sizeof(*info));
+    for (int k = 0; k < 2; ++k) {
+        info->num_groups[k] = (int32_t)b->groups[k].size();
+        for (int l = 0; l < 12; ++l) info->cluster_tier[k][l] = -1;
+        const SubBatch* big = nullptr;
+        for (const SubBatch& S : b->groups[k])
+            if (!big || S.cap_pairs > big->cap_pairs) big = &S;
+        if (!big) continue;
+        info->max_group_pairs[k] = big->plan_pairs;
+        info->reduce_blocks_per_sm[k] = big->red_bpsm;
+        for (int c = 0; c < 5; ++c) {
+            info->reduce_candidates[k][c] = big->red_cand[c];
+            info->reduce_ms[k][c] = big->red_ms[c];
+        }
+        for (int l = 0; l <= kMaxLevels && l < 12; ++l) {
+            info->cluster_tier[k][l] = big->tier[l];
+            for (int t = 0; t < 3; ++t) info->cluster_ms[k][l][t] = big->tier_ms[l][t];
+        }
+    }
+    return VX_OK;
+}
+
 extern "C" void vx_batch_destroy(vx_batch* b) {
     if (!b) return;
     cudaStream_t s = b->ctx->last_stream;
@@ -716,6 +980,11 @@ extern "C" void vx_batch_destroy(vx_batch* b) {
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->join) cudaEventDestroy(b->join);
     for (void* p : b->allocs) vx_dev_free(b->ctx, p, s);
+    for (Pool& P : b->pool)
+        for (void* p : {(void*)P.k0, (void*)P.v0, (void*)P.k1, (void*)P.v1, (void*)P.flags, (void*)P.idx,
+                        (void*)P.hist, (void*)P.so, (void*)P.seg_key, (void*)P.seg_nonzero, (void*)P.dst,
+                        (void*)P.starts})
+            if (p) vx_dev_free(b->ctx, p, s);
     cudaStreamSynchronize(s);
     delete b;
 }

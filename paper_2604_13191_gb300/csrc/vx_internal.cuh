@@ -103,9 +103,10 @@ vx_status vx_scan_u32(vx_context* ctx, const uint32_t* in, uint32_t* out, uint32
                       uint32_t* total, cudaStream_t s);
 // Stable LSD radix sort of (key, value) uint32 pairs on the low `bits` bits.  The
 // function ping-pongs between the two buffer pairs and leaves *keys / *vals pointing
-// at the sorted data.
+// at the sorted data.  err (device): bit 4 is set when a bounded wait of the scatter's
+// copy pipeline gave up (the result is then incomplete; report VX_ERR_TIMEOUT).
 vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, uint32_t** keys_alt,
-                            uint32_t** vals_alt, uint32_t n, int bits, cudaStream_t s);
+                            uint32_t** vals_alt, uint32_t n, int bits, cudaStream_t s, uint32_t* err);
 
 // Starts of the runs of equal keys in the sorted keys[0, n): starts[r] = first index of run
 // r, starts[*nseg] = n; *nseg (device) receives the number of runs.  starts needs room for
@@ -128,7 +129,13 @@ cudaError_t vx_lod_step_batched(const vx_level* in, const uint16_t* inst_in, con
                                 vx_level* out, uint16_t* inst_out, uint32_t* np_dev, uint32_t cap_out,
                                 uint32_t* flags, uint32_t* idx, uint32_t* starts, uint32_t* partials, uint32_t* tmp,
                                 uint32_t* err, const float4* dirs4, int n_dirs, uint32_t* work, uint32_t* wcnt,
-                                const void* cst, void* pst, int merge, cudaStream_t s);
+                                const void* cst, void* pst, int merge, int tier, cudaStream_t s);
+// The clustering of a batched LoD step again, alone, with a given tier (0 warp per parent,
+// 1 block of 8 warps, 2 block of 16 warps): for timing the tiers while a batch is planned.
+cudaError_t vx_lod_cluster_batched(const vx_level* in, const vx_level* out, const uint32_t* starts,
+                                   const uint32_t* work, uint32_t* wcnt, const float4* dirs4, int n_dirs,
+                                   const void* cst, void* pst, uint32_t cap_out, int merge, int tier,
+                                   cudaStream_t s);
 cudaError_t vx_lod_batched_prepare(int K, const float* dirs, int n, float4* dirs4, cudaStream_t s);
 constexpr size_t kLobeStatsBytes = 48;   // per-lobe histogram + sample moment kept between levels
 

@@ -1134,18 +1134,28 @@ __global__ void k_finalize(SegOut in, const uint32_t* __restrict__ nseg_p, const
         if (!in.nonzero[s]) continue;
         const uint32_t o = dst[s];
         L.keys[o] = key_hi | (uint64_t)in.key[s];
+        // 16-byte mask and 8-byte moment accesses (mask rows are 64-byte aligned, moment
+        // rows 8-byte aligned in both the temporaries and the level block)
         uint64_t m[8];
+        const uint4* mi = reinterpret_cast<const uint4*>(in.mask + (size_t)s * 8);
+        uint4* mo = reinterpret_cast<uint4*>(L.mask + (size_t)o * 8);
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            m[w] = in.mask[(size_t)s * 8 + w];
-            L.mask[(size_t)o * 8 + w] = m[w];
+        for (int w = 0; w < 4; ++w) {
+            const uint4 q = mi[w];
+            mo[w] = q;
+            m[2 * w] = ((uint64_t)q.y << 32) | q.x;
+            m[2 * w + 1] = ((uint64_t)q.w << 32) | q.z;
         }
         float mass = in.mass[s];
         float M[6];
+        const float2* Mi = reinterpret_cast<const float2*>(in.moment + (size_t)s * 6);
+        float2* Mo = reinterpret_cast<float2*>(L.moment + (size_t)o * 6);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            M[c] = in.moment[(size_t)s * 6 + c];
-            L.moment[(size_t)o * 6 + c] = M[c];
+        for (int c = 0; c < 3; ++c) {
+            const float2 q = Mi[c];
+            Mo[c] = q;
+            M[2 * c] = q.x;
+            M[2 * c + 1] = q.y;
         }
         L.mass[o] = mass;
         uint16_t occ;

@@ -704,22 +704,25 @@ cudaError_t cluster_set_smem(int K) {
     return e;
 }
 
-// Clustering of one level.  n, the level's parent count (or an upper bound of it), picks
-// the tier: a warp per parent on wide levels, a block of 8 or 16 warps on narrow ones.
-// wcnt[0] holds the number of listed parents and wcnt[1] (zero) the take counter.
+// Clustering of one level.  tier: 0 a warp per parent (resident blocks of 4 warps), 1 a
+// block of 8 warps, 2 a block of 16 warps per parent; -1 picks by n, the level's parent
+// count (or an upper bound of it): warps on wide levels, blocks on narrow ones.  Every
+// tier gives the same result.  wcnt[0] holds the number of listed parents and wcnt[1]
+// (zero) the take counter.
 void launch_cluster(const LevelIn& li, const uint32_t* starts, const uint32_t* work, const uint32_t* wcnt,
                     const vx_level& out, int K, const float4* dirs4, int N, const LobeStats* cst, LobeStats* pst,
-                    unsigned long long* nsampled, uint32_t n, int merge, cudaStream_t s) {
-    if (n > (uint32_t)(vx::kSMs * 16)) {
+                    unsigned long long* nsampled, uint32_t n, int merge, cudaStream_t s, int tier = -1) {
+    if (tier < 0) tier = n > (uint32_t)(vx::kSMs * 16) ? 0 : (n > (uint32_t)vx::kSMs ? 1 : 2);
+    if (tier == 0) {
         const unsigned cb = (unsigned)std::min<size_t>((n + CL_WARPS - 1) / CL_WARPS, (size_t)vx::kSMs * 7);
         k_sggx_cluster<1><<<cb, CL_WARPS * 32, cluster_smem(1, K), s>>>(li, starts, work, wcnt, out, K, dirs4, N,
                                                                           cst, pst, nsampled, merge);
-    } else if (n > (uint32_t)vx::kSMs) {
+    } else if (tier == 1) {
         const unsigned cb = (unsigned)std::max<uint32_t>(1u, std::min<uint32_t>(n, vx::kSMs * 4));
         k_sggx_cluster<CL_BLOCK_WARPS><<<cb, CL_BLOCK_WARPS * 32, cluster_smem(CL_BLOCK_WARPS, K), s>>>(
             li, starts, work, wcnt, out, K, dirs4, N, cst, pst, nsampled, merge);
     } else {
-        const unsigned cb = (unsigned)std::max<uint32_t>(1u, n);
+        const unsigned cb = (unsigned)std::max<uint32_t>(1u, std::min<uint32_t>(n, vx::kSMs * 2));
         k_sggx_cluster<CL_WIDE_WARPS><<<cb, CL_WIDE_WARPS * 32, cluster_smem(CL_WIDE_WARPS, K), s>>>(
             li, starts, work, wcnt, out, K, dirs4, N, cst, pst, nsampled, merge);
     }
@@ -899,7 +902,7 @@ cudaError_t vx_lod_step_batched(const vx_level* in, const uint16_t* inst_in, con
                                 vx_level* out, uint16_t* inst_out, uint32_t* np_dev, uint32_t cap_out,
                                 uint32_t* flags, uint32_t* idx, uint32_t* starts, uint32_t* partials, uint32_t* tmp,
                                 uint32_t* err, const float4* dirs4, int n_dirs, uint32_t* work, uint32_t* wcnt,
-                                const void* cst, void* pst, int merge, cudaStream_t s) {
+                                const void* cst, void* pst, int merge, int tier, cudaStream_t s) {
     const unsigned gb = (unsigned)std::min<size_t>(grid_for(cap_in, 256), (size_t)vx::kSMs * 16);
     k_bparent_flags<<<gb, 256, 0, s>>>(in->keys, inst_in, n_dev, cap_in, flags);
     cudaError_t e = vx_scan_u32_scratch(flags, idx, cap_in, tmp, partials, s);
@@ -919,7 +922,24 @@ cudaError_t vx_lod_step_batched(const vx_level* in, const uint16_t* inst_in, con
                                     (const LobeStats*)cst, (LobeStats*)pst);
     if (K > 1)
         launch_cluster(li, starts, work, wcnt, *out, K, dirs4, n_dirs, (const LobeStats*)cst, (LobeStats*)pst, nullptr,
-                       cap_out, merge, s);
+                       cap_out, merge, s, tier);
     k_bparent_inst<<<gb, 256, 0, s>>>(inst_in, starts, np_dev, inst_out);
+    return cudaGetLastError();
+}
+
+// The clustering of a batched LoD step run again on its own with the given tier (the
+// step's parents, work list and statistics are still in place): for timing the tiers
+// while a batch is planned.  The outputs are rewritten with the same values.
+cudaError_t vx_lod_cluster_batched(const vx_level* in, const vx_level* out, const uint32_t* starts,
+                                   const uint32_t* work, uint32_t* wcnt, const float4* dirs4, int n_dirs,
+                                   const void* cst, void* pst, uint32_t cap_out, int merge, int tier,
+                                   cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(wcnt + 1, 0, 4, s);
+    if (e != cudaSuccess) return e;
+    LevelIn li;
+    li.keys = in->keys; li.mask = in->mask; li.mass = in->mass; li.moment = in->moment;
+    li.lobe_count = in->lobe_count; li.lobes = in->lobes; li.K = in->K;
+    launch_cluster(li, starts, work, wcnt, *out, out->K, dirs4, n_dirs, (const LobeStats*)cst, (LobeStats*)pst,
+                   nullptr, cap_out, merge, s, tier);
     return cudaGetLastError();
 }

@@ -313,7 +313,7 @@ extern "C" vx_status vx_voxelize_sampled(vx_context* ctx, const vx_primitives* p
                                        r0, r1, r2, np, S, (int)R, kbits, cnt, (const uint32_t*)ctx->ws[WS_OFFS].p, k0,
                                        v0));
     VX_CUDA_TRY(cudaGetLastError());
-    VX_TRY(vx_radix_sort_u32(ctx, &k0, &v0, &k1, &v1, n, kbits + 1, s));
+    VX_TRY(vx_radix_sort_u32(ctx, &k0, &v0, &k1, &v1, n, kbits + 1, s, misc));
     VX_TRY(vx_ws_ensure(ctx, WS_STARTS, (size_t)n * 4 + 8, s));
     uint32_t* starts = (uint32_t*)ctx->ws[WS_STARTS].p;
     VX_TRY(vx_segment_starts(ctx, k0, n, misc + 2, starts, s));
@@ -321,6 +321,7 @@ extern "C" vx_status vx_voxelize_sampled(vx_context* ctx, const vx_primitives* p
     VX_CUDA_TRY(cudaMemcpyAsync((uint32_t*)ctx->host_pin + 4, k0 + (n - 1), 4, cudaMemcpyDeviceToHost, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     const uint32_t* hp = (const uint32_t*)ctx->host_pin;
+    if (hp[0] & 4u) return VX_ERR_TIMEOUT;   // a bounded wait of the sort gave up
     if (hp[0]) return VX_ERR_INVALID_ARG;
     // the run of samples outside the grid (key 1 << kbits) sorts last and is not a voxel
     const uint32_t nvox = hp[2] - (hp[4] == (1u << kbits) ? 1u : 0u);

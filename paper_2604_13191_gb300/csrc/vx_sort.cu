@@ -3,6 +3,8 @@
 // The sort orders candidate (voxel key, primitive id) pairs by Morton key, keeping
 // primitive-id order inside each key (stability), which is what makes the per-voxel
 // reductions order-deterministic (the paper sorts samples by block id, Sec. 3.3).
+#include <algorithm>
+
 #include "vx_internal.cuh"
 
 namespace {
@@ -310,6 +312,196 @@ __global__ void __launch_bounds__(SORT_THREADS, 3) k_radix_scatter(const uint32_
     }
 }
 
+// ---- persistent scatter with double-buffered bulk copies ------------------------------
+// A resident block takes tiles t, t + grid, ...; while it ranks and writes one tile, the next
+// tile's keys and values stream into the other half of its shared memory through 1-D bulk
+// async copies (cp.async.bulk, completion on an mbarrier).  Each wait is bounded: a wait that
+// gives up sets bit 4 of *err, waits (bounded) for the block's own copies still in flight,
+// and ends the block (the host then reports VX_ERR_TIMEOUT).
+constexpr uint32_t PIPE_SPIN_LIMIT = 1u << 22;   // try_wait polls before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// bounded wait for phase `parity` of the barrier; false when it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < PIPE_SPIN_LIMIT; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// global -> shared bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+constexpr size_t pipe_smem(int rb) {
+    return (size_t)2 * 2 * SORT_TILE * 4                 // two stages of keys + values
+           + (size_t)SORT_WARPS * rb * 4                 // per-warp digit counters
+           + (size_t)2 * rb * 4                          // gofs, tofs
+           + 64;                                         // scan scratch, barriers
+}
+
+template <int RB>
+__global__ void __launch_bounds__(SORT_THREADS, 2) k_radix_scatter_pipe(const uint32_t* __restrict__ keys,
+                                                                      const uint32_t* __restrict__ vals, uint32_t n,
+                                                                      int shift, uint32_t dmask, uint32_t nt,
+                                                                      const uint32_t* __restrict__ hist,
+                                                                      uint32_t* __restrict__ okeys,
+                                                                      uint32_t* __restrict__ ovals,
+                                                                      uint32_t* __restrict__ err) {
+    static_assert(RB % SORT_THREADS == 0, "digits per thread");
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    // stage s: keys at sm + 2 s TILE, values right after them
+    uint32_t* const stage0 = (uint32_t*)sm_raw;
+    uint32_t (*wcnt)[RB] = reinterpret_cast<uint32_t (*)[RB]>((uint32_t*)sm_raw + 4 * SORT_TILE);
+    uint32_t* gofs = (uint32_t*)sm_raw + 4 * SORT_TILE + SORT_WARPS * RB;
+    uint32_t* tofs = gofs + RB;
+    uint32_t* scan_tmp = tofs + RB;                       // SORT_WARPS + 1 words
+    uint64_t* bar = reinterpret_cast<uint64_t*>(scan_tmp + 12);   // 8-byte aligned: two barriers
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    // a tile is loaded by bulk copies when it is whole (the last one may be short, and its
+    // byte count a multiple of 4 only): else by the threads
+    auto bulk_ok = [&](uint32_t t) { return (size_t)(t + 1) * SORT_TILE <= n; };
+    auto issue = [&](uint32_t t, int st) {
+        const size_t e0 = (size_t)t * SORT_TILE;
+        uint32_t* sk = stage0 + (size_t)st * 2 * SORT_TILE;
+        mbar_expect_tx(&bar[st], 2u * SORT_TILE * 4u);
+        bulk_load(sk, keys + e0, SORT_TILE * 4u, &bar[st]);
+        bulk_load(sk + SORT_TILE, vals + e0, SORT_TILE * 4u, &bar[st]);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t phase = 0u, pending = 0u;   // bit s: the parity to wait for / a copy in flight, stage s
+    if (threadIdx.x == 0 && blockIdx.x < nt && bulk_ok(blockIdx.x)) issue(blockIdx.x, 0);
+    if (blockIdx.x < nt && bulk_ok(blockIdx.x)) pending |= 1u;
+    bool lost = false;
+    int st = 0;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x, st ^= 1) {
+        // the next tile streams into the other stage (its last reader finished: the loop ends
+        // with a barrier); generic writes to that stage are ordered before the async copy
+        const uint32_t tn = t + gridDim.x;
+        if (tn < nt && bulk_ok(tn)) {
+            if (threadIdx.x == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(tn, st ^ 1);
+            }
+            pending |= 1u << (st ^ 1);
+        }
+        const size_t tile0 = (size_t)t * SORT_TILE;
+        const uint32_t tn_items = (uint32_t)min((size_t)SORT_TILE, (size_t)n - tile0);
+        uint32_t* const sk = stage0 + (size_t)st * 2 * SORT_TILE;
+        uint32_t* const sv = sk + SORT_TILE;
+        if ((pending >> st) & 1u) {
+            if (!mbar_wait(&bar[st], (phase >> st) & 1u)) {
+                lost = true;
+                break;
+            }
+            phase ^= 1u << st;
+            pending &= ~(1u << st);
+        } else {
+            for (uint32_t i = threadIdx.x; i < tn_items; i += SORT_THREADS) {
+                sk[i] = keys[tile0 + i];
+                sv[i] = vals[tile0 + i];
+            }
+        }
+        for (int i = threadIdx.x; i < SORT_WARPS * RB; i += SORT_THREADS) (&wcnt[0][0])[i] = 0;
+        for (int d = threadIdx.x; d < RB; d += SORT_THREADS) gofs[d] = hist[(size_t)d * nt + t];
+        __syncthreads();
+        // rank: per-warp running counters (stable within the tile)
+        uint32_t k[SORT_ITEMS], v[SORT_ITEMS], rk[SORT_ITEMS];
+        const uint32_t lb = (uint32_t)w * (32 * SORT_ITEMS);
+#pragma unroll
+        for (int j = 0; j < SORT_ITEMS; ++j) {
+            const uint32_t e = lb + (uint32_t)j * 32 + lane;
+            const bool valid = e < tn_items;
+            k[j] = valid ? sk[e] : 0u;
+            v[j] = valid ? sv[e] : 0u;
+            const uint32_t d = valid ? ((k[j] >> shift) & dmask) : (uint32_t)RB;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            uint32_t r = 0;
+            if (valid) r = wcnt[w][d] + __popc(peers & lt);
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) wcnt[w][d] += __popc(peers);
+            __syncwarp();
+            rk[j] = r;
+        }
+        __syncthreads();
+        constexpr int DPT = RB / SORT_THREADS;
+        uint32_t cnt[DPT];
+#pragma unroll
+        for (int i = 0; i < DPT; ++i) {
+            const int d = threadIdx.x * DPT + i;
+            uint32_t run = 0;
+#pragma unroll
+            for (int ww = 0; ww < SORT_WARPS; ++ww) {
+                const uint32_t c = wcnt[ww][d];
+                wcnt[ww][d] = run;
+                run += c;
+            }
+            cnt[i] = run;
+        }
+        uint32_t sum = 0;
+#pragma unroll
+        for (int i = 0; i < DPT; ++i) sum += cnt[i];
+        uint32_t total;
+        uint32_t ex = block_excl_scan(sum, scan_tmp, total);
+#pragma unroll
+        for (int i = 0; i < DPT; ++i) {
+            tofs[threadIdx.x * DPT + i] = ex;
+            ex += cnt[i];
+        }
+        __syncthreads();
+        // the tile in digit order, over the stage it was read from (every item is in registers)
+#pragma unroll
+        for (int j = 0; j < SORT_ITEMS; ++j) {
+            const uint32_t e = lb + (uint32_t)j * 32 + lane;
+            if (e < tn_items) {
+                const uint32_t d = (k[j] >> shift) & dmask;
+                const uint32_t pos = rk[j] + tofs[d] + wcnt[w][d];
+                sk[pos] = k[j];
+                sv[pos] = v[j];
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < tn_items; i += SORT_THREADS) {
+            const uint32_t kk = sk[i], vv = sv[i];
+            const uint32_t d = (kk >> shift) & dmask;
+            const uint32_t pos = gofs[d] + (i - tofs[d]);
+            okeys[pos] = kk;
+            ovals[pos] = vv;
+        }
+        __syncthreads();
+    }
+    if (lost) {
+        if (threadIdx.x == 0) atomicOr(err, 4u);
+        // the block's own copies still in flight land before it exits (bounded)
+        for (int s2 = 0; s2 < 2; ++s2)
+            if ((pending >> s2) & 1u) mbar_wait(&bar[s2], (phase >> s2) & 1u);
+    }
+}
+
 }  // namespace
 
 vx_status vx_scan_u32(vx_context* ctx, const uint32_t* in, uint32_t* out, uint32_t n,
@@ -347,7 +539,7 @@ vx_status vx_segment_starts(vx_context* ctx, const uint32_t* keys, uint32_t n, u
 }
 
 vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, uint32_t** keys_alt,
-                            uint32_t** vals_alt, uint32_t n, int bits, cudaStream_t s) {
+                            uint32_t** vals_alt, uint32_t n, int bits, cudaStream_t s, uint32_t* err) {
     if (n <= 1 || bits <= 0) return VX_OK;
     // as few passes as 9-bit digits allow, digits as even as possible; 512 buckets when a
     // digit is wider than 8 bits (27-bit keys: three passes of 9 instead of four of 8)
@@ -359,6 +551,15 @@ vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, u
     if (hn > 0xffffffffull) return VX_ERR_CAPACITY;
     VX_TRY(vx_ws_ensure(ctx, WS_SORT_HIST, hn * 4, s));
     uint32_t* hist = (uint32_t*)ctx->ws[WS_SORT_HIST].p;
+    static bool attr_set = false;   // dynamic shared memory of the scatter, once per process
+    if (!attr_set) {
+        VX_CUDA_TRY(cudaFuncSetAttribute(k_radix_scatter_pipe<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pipe_smem(512)));
+        VX_CUDA_TRY(cudaFuncSetAttribute(k_radix_scatter_pipe<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pipe_smem(256)));
+        attr_set = true;
+    }
+    const unsigned sblocks = (unsigned)std::min<uint32_t>(nt, (uint32_t)vx::kSMs * 2);
     for (int shift = 0; shift < bits; shift += width) {
         int nb = bits - shift < width ? bits - shift : width;
         uint32_t dmask = (1u << nb) - 1u;
@@ -370,11 +571,11 @@ vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, u
                                                 *keys, *vals, n, shift, dmask, nt, nullptr, hist)));
         VX_TRY(vx_scan_u32(ctx, hist, hist, (uint32_t)hn, nullptr, s));
         if (rb == 512u)
-            VX_LAUNCH(ctx, ST_SORT_SCATTER, s, (k_radix_scatter<false, 512><<<nt, SORT_THREADS, 0, s>>>(
-                                                   *keys, *vals, n, shift, dmask, nt, nullptr, hist, *keys_alt, *vals_alt)));
+            VX_LAUNCH(ctx, ST_SORT_SCATTER, s, (k_radix_scatter_pipe<512><<<sblocks, SORT_THREADS, pipe_smem(512), s>>>(
+                                                   *keys, *vals, n, shift, dmask, nt, hist, *keys_alt, *vals_alt, err)));
         else
-            VX_LAUNCH(ctx, ST_SORT_SCATTER, s, (k_radix_scatter<false, 256><<<nt, SORT_THREADS, 0, s>>>(
-                                                   *keys, *vals, n, shift, dmask, nt, nullptr, hist, *keys_alt, *vals_alt)));
+            VX_LAUNCH(ctx, ST_SORT_SCATTER, s, (k_radix_scatter_pipe<256><<<sblocks, SORT_THREADS, pipe_smem(256), s>>>(
+                                                   *keys, *vals, n, shift, dmask, nt, hist, *keys_alt, *vals_alt, err)));
         VX_CUDA_TRY(cudaGetLastError());
         uint32_t* t = *keys; *keys = *keys_alt; *keys_alt = t;
         t = *vals; *vals = *vals_alt; *vals_alt = t;

@@ -65,6 +65,9 @@ vx_status count_window(vx_context* ctx, bool fiber, uint32_t np, const Window& w
     return VX_OK;
 }
 
+// Candidate pairs of one pass at most (31-bit pair indices).
+constexpr int64_t kMaxPassPairs = 0x7fffffffll;
+
 // A window of the grid in the planning of a voxelization: its corner and size (2^lg voxels
 // per side) and, once counted, its candidate-pair total.
 struct Leaf {
@@ -108,14 +111,15 @@ vx_status window_segments(vx_context* ctx, bool fiber, uint32_t np, const Window
         VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<false, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
                                        r0, r1, r2, np, win, nullptr, offs, *k0, *v0));
     VX_CUDA_TRY(cudaGetLastError());
-    VX_TRY(vx_radix_sort_u32(ctx, k0, v0, k1, v1, npairs, 3 * bits, s));
+    VX_TRY(vx_radix_sort_u32(ctx, k0, v0, k1, v1, npairs, 3 * bits, s, misc));
     VX_TRY(vx_ws_ensure(ctx, WS_FLAGS, (size_t)npairs * 4, s));
     VX_TRY(vx_ws_ensure(ctx, WS_STARTS, (size_t)npairs * 4 + 8, s));
     uint32_t* starts = (uint32_t*)ctx->ws[WS_STARTS].p;
     VX_TRY(vx_segment_starts(ctx, *k0, npairs, misc + 2, starts, s));
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc + 2, 4, cudaMemcpyDeviceToHost, s));
+    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 12, cudaMemcpyDeviceToHost, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
-    *nseg = ((uint32_t*)ctx->host_pin)[0];
+    if (((uint32_t*)ctx->host_pin)[0] & 4u) return VX_ERR_TIMEOUT;   // a bounded wait of the sort gave up
+    *nseg = ((uint32_t*)ctx->host_pin)[2];
     return VX_OK;
 }
 
@@ -138,8 +142,8 @@ vx_status window_reduce(vx_context* ctx, bool fiber, uint32_t np, uint32_t nseg,
     char* so = (char*)ctx->ws[WS_SEG_OUT].p;
     SegOut seg;
     seg.mask = (uint64_t*)so;
-    seg.mass = (float*)(so + (size_t)nseg * 64);
-    seg.moment = (float*)(so + (size_t)nseg * 68);
+    seg.moment = (float*)(so + (size_t)nseg * 64);   // 8-byte aligned rows
+    seg.mass = (float*)(so + (size_t)nseg * 88);
     seg.key = k1;
     seg.nonzero = v1;
     const unsigned rblocks = (unsigned)std::min<size_t>((nseg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 32);
@@ -268,7 +272,7 @@ vx_status plan_windows(vx_context* ctx, const Prepared& P, const int lo[3], int 
     struct Pending { int lo[3]; int lg; };
     std::vector<Pending> stack;
     stack.push_back(Pending{{lo[0], lo[1], lo[2]}, lg});
-    const uint64_t limit = (uint64_t)std::min<int64_t>(ctx->max_pairs, 0x7fffffffll);
+    const uint64_t limit = (uint64_t)std::min<int64_t>(ctx->max_pairs, kMaxPassPairs);
     while (!stack.empty()) {
         const Pending w = stack.back();
         stack.pop_back();

@@ -57,6 +57,8 @@ int main(void) {
   printf("vx_lod_params %zu\n", sizeof(vx_lod_params));
   printf("vx_allocator %zu\n", sizeof(vx_allocator));
   printf("vx_window %zu\n", sizeof(vx_window));
+  printf("vx_batch_info %zu\n", sizeof(vx_batch_info));
+  P(vx_batch_info, cluster_ms) P(vx_batch_info, reduce_ms)
   P(vx_window, log2_size) P(vx_window, index)
   P(vx_primitives, weights) P(vx_primitives, fiber_offsets) P(vx_level, compact) P(vx_level, block)
   P(vx_level, num_voxels) P(vx_lod_params, dirs) P(vx_lod_params, merge) P(vx_grid, resolution)
@@ -76,6 +78,9 @@ int main(void) {
     assert int(got["vx_lod_params"]) == C.sizeof(api.VxLodParams)
     assert int(got["vx_allocator"]) == C.sizeof(api.VxAllocator)
     assert int(got["vx_window"]) == C.sizeof(api.VxWindow)
+    assert int(got["vx_batch_info"]) == C.sizeof(api.VxBatchInfo)
+    assert int(got["vx_batch_info.cluster_ms"]) == api.VxBatchInfo.cluster_ms.offset
+    assert int(got["vx_batch_info.reduce_ms"]) == api.VxBatchInfo.reduce_ms.offset
     assert int(got["vx_window.log2_size"]) == api.VxWindow.log2_size.offset
     assert int(got["vx_window.index"]) == api.VxWindow.index.offset
     assert int(got["vx_primitives.weights"]) == api.VxPrimitives.weights.offset

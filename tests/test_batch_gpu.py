@@ -139,3 +139,65 @@ def test_batch_matches_oracle(K, which, dirs5000):
                               mu_max=prim_measure_max(w))
     b.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("K", [1, 4])
+def test_batch_groups_by_pass_limit(K, dirs5000):
+    """With a per-pass pair limit below a kind's total, its instances run as several
+    consecutive groups sharing one set of pair buffers; every instance still equals the plain
+    path bit for bit, on the first run and on a replay.  An instance that alone is over the
+    limit is reported (VX_ERR_CAPACITY)."""
+    ctx = vx.Context(DEV)
+    insts = instances(seed=7, n=10)
+    dirs = torch.from_numpy(dirs5000).to(DEV) if K > 1 else None
+    ref = vx.Context(DEV)
+    refs = [plain(ref, inst, K, dirs) for inst in insts]
+    whole = ctx.batch(insts, K=K, dirs=dirs).query()
+    total = max(whole["fibers"]["max_group_pairs"], whole["triangles"]["max_group_pairs"])
+    assert whole["fibers"]["groups"] == 1 and whole["triangles"]["groups"] == 1
+    b = None
+    for frac in (0.8, 0.65, 0.5):
+        ctx.set_max_pairs_per_pass(int(frac * total))
+        try:
+            b = ctx.batch(insts, K=K, dirs=dirs)
+        except vx.VxError as e:          # one instance over this limit: try a larger one
+            assert e.status == 3
+            continue
+        break
+    assert b is not None
+    q = b.query()
+    assert max(q["fibers"]["groups"], q["triangles"]["groups"]) > 1, q
+    for _ in range(2):
+        b.run()
+        for i in range(len(insts)):
+            for l, r in enumerate(refs[i]):
+                g = b.level(i, l).host()
+                for f in FIELDS:
+                    assert np.array_equal(np.asarray(g[f]).view(np.uint8), np.asarray(r[f]).view(np.uint8)), (i, l, f)
+    b.close()
+    ctx.set_max_pairs_per_pass(20_000)
+    with pytest.raises(vx.VxError) as e:
+        ctx.batch(insts, K=K, dirs=dirs)
+    assert e.value.status == 3
+    ctx.close()
+    ref.close()
+
+
+def test_batch_autotuner_records_its_choices(dirs5000):
+    """The plan times every candidate launch shape on its own data and keeps the fastest:
+    the reduce grid per kind and the clustering tier per level (K = 4)."""
+    ctx = vx.Context(DEV)
+    insts = instances(seed=6, n=8)
+    b = ctx.batch(insts, K=4, dirs=torch.from_numpy(dirs5000).to(DEV))
+    q = b.query()
+    for kind in ("triangles", "fibers"):
+        r = q[kind]
+        assert r["groups"] == 1 and r["max_group_pairs"] > 0
+        assert len(r["reduce_ms"]) == 5 and all(v > 0 for v in r["reduce_ms"].values())
+        assert r["reduce_ms"][r["reduce_blocks_per_sm"]] == min(r["reduce_ms"].values())
+        assert r["cluster_tier"] and all(t in (0, 1, 2) for t in r["cluster_tier"].values())
+        for l, t in r["cluster_tier"].items():
+            assert r["cluster_ms"][l][t] == min(r["cluster_ms"][l])
+    print(q)
+    b.close()
+    ctx.close()
