@@ -997,7 +997,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
     }
 }
 
-__global__ void __launch_bounds__(RED_WARPS * 32) k_reduce_tris(const uint32_t* __restrict__ keys,
+__global__ void __launch_bounds__(RED_WARPS * 32, 5) k_reduce_tris(const uint32_t* __restrict__ keys,
                                                                 const uint32_t* __restrict__ prims,
                                                                 const uint32_t* __restrict__ starts,
                                                                 const uint32_t* __restrict__ nseg_p,
