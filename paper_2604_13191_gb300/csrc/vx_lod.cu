@@ -139,8 +139,14 @@ __global__ void k_lod_reduce(LevelIn in, const uint32_t* __restrict__ starts, ui
         int ncand = 0;
         for (uint32_t c = beg; c < end; ++c) {
             m = m + in.mass[c];
+            // moments as 8-byte pairs (rows are 24 bytes, 8-byte aligned)
+            const float2* m2 = reinterpret_cast<const float2*>(in.moment + (size_t)c * 6);
 #pragma unroll
-            for (int j = 0; j < 6; ++j) M[j] = M[j] + in.moment[(size_t)c * 6 + j];
+            for (int j = 0; j < 3; ++j) {
+                const float2 q = m2[j];
+                M[2 * j] = M[2 * j] + q.x;
+                M[2 * j + 1] = M[2 * j + 1] + q.y;
+            }
             uint64_t cm[8];
             const ulonglong2* cm2 = reinterpret_cast<const ulonglong2*>(in.mask + (size_t)c * 8);
 #pragma unroll
@@ -154,8 +160,9 @@ __global__ void k_lod_reduce(LevelIn in, const uint32_t* __restrict__ starts, ui
         }
         out.keys[p] = in.keys[beg] >> 3;
         out.mass[p] = m;
+        float2* Mo = reinterpret_cast<float2*>(out.moment + (size_t)p * 6);
 #pragma unroll
-        for (int j = 0; j < 6; ++j) out.moment[(size_t)p * 6 + j] = M[j];
+        for (int j = 0; j < 3; ++j) Mo[j] = make_float2(M[2 * j], M[2 * j + 1]);
         ulonglong2* pm2 = reinterpret_cast<ulonglong2*>(out.mask + (size_t)p * 8);
 #pragma unroll
         for (int w = 0; w < 4; ++w) pm2[w] = make_ulonglong2(pm[2 * w], pm[2 * w + 1]);
@@ -244,9 +251,9 @@ __device__ bool sqrtm3(const float* S, float* Rm) {
             if (apq == 0.0f) continue;
             const float app = a[p][p], aqq = a[q][q];
             const float theta = (aqq - app) / (2.0f * apq);
-            float t = 1.0f / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+            float t = __frcp_rn(fabsf(theta) + sqrtf(theta * theta + 1.0f));
             if (theta < 0.0f) t = -t;
-            const float c = 1.0f / sqrtf(t * t + 1.0f);
+            const float c = __frcp_rn(sqrtf(t * t + 1.0f));
             const float sn = t * c;
             a[p][p] = app - t * apq;
             a[q][q] = aqq + t * apq;
@@ -305,7 +312,7 @@ __device__ __forceinline__ SampleTerms sample_terms(const float* Rm, float4 u4) 
     r.m[3] = ge_mask(c0, t2);
     r.m[4] = ge_mask(c1, t2);
     r.m[5] = ge_mask(c2, t2);
-    const float s20 = (1.0f / n2) * 1048576.0f;
+    const float s20 = __frcp_rn(n2) * 1048576.0f;
     r.x[0] = __float_as_uint(__fmaf_rn(c0, s20, 12582912.0f));
     r.x[1] = __float_as_uint(__fmaf_rn(c1, s20, 12582912.0f));
     r.x[2] = __float_as_uint(__fmaf_rn(c2, s20, 12582912.0f));
@@ -398,7 +405,7 @@ __device__ LobeOwn sample_lobe(const float* S, const float4* __restrict__ dirs, 
             h[3] += (c0 >= t2) ? 1 : 0;
             h[4] += (c1 >= t2) ? 1 : 0;
             h[5] += (c2 >= t2) ? 1 : 0;
-            const float inv = 1.0f / n2;
+            const float inv = __frcp_rn(n2);
             const float s20 = inv * 1048576.0f;
             q[0] += rint_prod(c0, s20);
             q[1] += rint_prod(c1, s20);
