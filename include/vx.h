@@ -445,6 +445,15 @@ typedef struct {
 VX_API vx_status vx_profile_enable(vx_context* ctx, int enable);
 VX_API vx_status vx_profile_read(vx_context* ctx, vx_stage_time* out, int max_stages, int* num_stages);
 
+/* Self-test of the device-side bounded waits (no counterpart in the paper).  The radix
+ * sort's copy pipeline waits on mbarriers with an iteration limit, and gives up with
+ * VX_ERR_TIMEOUT instead of hanging.  This call runs one such wait on a barrier that no copy
+ * will complete, so it must give up after `polls` polls: it returns VX_ERR_TIMEOUT when it
+ * did (the expected result) and VX_OK if the barrier had completed.  Nothing stays in
+ * flight, and the context stays usable.  Synchronises `stream`.  Errors:
+ * VX_ERR_INVALID_ARG (ctx NULL or polls < 1), VX_ERR_CUDA. */
+VX_API vx_status vx_selftest_bounded_wait(vx_context* ctx, int polls, void* stream);
+
 /* Static description of a status code. */
 VX_API const char* vx_status_string(vx_status s);
 

@@ -69,7 +69,7 @@ EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_l
            "vx_profile_read", "vx_backward", "vx_backward_noalloc", "vx_batch_create", "vx_batch_run",
            "vx_batch_level", "vx_batch_destroy", "vx_set_max_pairs_per_pass", "vx_batch_create_lod",
            "vx_export_compact8", "vx_tessellate_catmull_rom", "vx_voxelize_sampled", "vx_export_leaves",
-           "vx_voxelize_lod_windowed", "vx_batch_query"]
+           "vx_voxelize_lod_windowed", "vx_batch_query", "vx_selftest_bounded_wait"]
 
 
 class VxInstance(C.Structure):
@@ -142,6 +142,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         lib.vx_batch_run.argtypes = [P, P]
         lib.vx_batch_level.restype = C.c_int
         lib.vx_batch_level.argtypes = [P, C.c_int, C.c_int, P, C.POINTER(VxLevel)]
+        lib.vx_selftest_bounded_wait.restype = C.c_int
+        lib.vx_selftest_bounded_wait.argtypes = [P, C.c_int, P]
         lib.vx_batch_query.restype = C.c_int
         lib.vx_batch_query.argtypes = [P, C.POINTER(VxBatchInfo)]
         lib.vx_batch_destroy.restype = None

@@ -330,9 +330,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-// bounded wait for phase `parity` of the barrier; false when it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < PIPE_SPIN_LIMIT; ++i) {
+// bounded wait for phase `parity` of the barrier; false when it gave up after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = PIPE_SPIN_LIMIT) {
+    for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -502,6 +502,20 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_radix_scatter_pipe(const ui
     }
 }
 
+// Self-test of the bounded wait: a barrier that expects bytes no copy will deliver, so the
+// wait must give up after `limit` polls; *flag receives 4 (the sort's timeout bit) when it
+// did, 1 when the barrier completed (which would be an error).  No copy is issued, so nothing
+// is in flight when the kernel returns.
+__global__ void k_selftest_wait(uint32_t limit, uint32_t* flag) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect_tx(&bar, 16u);
+        *flag = mbar_wait(&bar, 0u, limit) ? 1u : 4u;
+    }
+}
+
 }  // namespace
 
 vx_status vx_scan_u32(vx_context* ctx, const uint32_t* in, uint32_t* out, uint32_t n,
@@ -628,4 +642,20 @@ cudaError_t vx_radix_sort_u32_scratch(uint32_t** keys, uint32_t** vals, uint32_t
         t = *vals; *vals = *vals_alt; *vals_alt = t;
     }
     return cudaGetLastError();
+}
+
+// Runs the bounded-wait self-test (k_selftest_wait) on `stream` and returns VX_ERR_TIMEOUT
+// when the wait gave up as it must (see vx.h).
+extern "C" vx_status vx_selftest_bounded_wait(vx_context* ctx, int polls, void* stream) {
+    if (!ctx || polls < 1) return VX_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    VX_TRY(vx_ws_ensure(ctx, WS_MISC, 256, s));
+    uint32_t* flag = (uint32_t*)ctx->ws[WS_MISC].p;
+    VX_CUDA_TRY(cudaMemsetAsync(flag, 0, 4, s));
+    k_selftest_wait<<<1, 32, 0, s>>>((uint32_t)polls, flag);
+    VX_CUDA_TRY(cudaGetLastError());
+    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, flag, 4, cudaMemcpyDeviceToHost, s));
+    VX_CUDA_TRY(cudaStreamSynchronize(s));
+    const uint32_t f = ((uint32_t*)ctx->host_pin)[0];
+    return f == 4u ? VX_ERR_TIMEOUT : (f == 1u ? VX_OK : VX_ERR_CUDA);
 }

@@ -89,3 +89,22 @@ def test_out_of_memory_is_reported_and_recoverable(frac, dirs5000):
     # vx_context_destroy returns the workspace; a level block lost by a failed call would remain
     assert not ctx.alloc.live, f"{len(ctx.alloc.live)} blocks still held after vx_context_destroy"
     assert not probe.alloc.live
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """The device waits of the sort's copy pipeline are bounded.  A wait on a barrier that no
+    copy completes must give up (VX_ERR_TIMEOUT) rather than hang; afterwards the same
+    context voxelizes as before."""
+    ctx = vx.Context(DEV)
+    w = synth.config2(fibers_per_ply=2, segments=200, R=64, K=1)
+    ctrl = torch.from_numpy(w.ctrl).to(DEV)
+    off = torch.from_numpy(w.fiber_offsets).to(DEV)
+    ref = ctx.voxelize(w.grid, ctrl=ctrl, fiber_offsets=off).host()
+    for polls in (1, 64, 4096):
+        st = ctx.lib.vx_selftest_bounded_wait(ctx.h, polls, api._stream(None))
+        assert st == 5, st                       # VX_ERR_TIMEOUT
+    assert ctx.lib.vx_selftest_bounded_wait(ctx.h, 0, api._stream(None)) == 1
+    got = ctx.voxelize(w.grid, ctrl=ctrl, fiber_offsets=off).host()
+    for k in ("keys", "mask", "mass", "moment"):
+        assert np.array_equal(got[k], ref[k])
+    ctx.close()

@@ -609,3 +609,30 @@ def test_windowed_callback_error_stops_the_call(ctx):
     with pytest.raises(vx.VxError) as e:
         ctx.voxelize_lod_windowed(w.grid, window_log2=7, on_window=on_window, **geom)   # w > log2 R
     assert e.value.status == 1
+
+
+def test_windowed_pyramid_with_split_windows_equals_whole(ctx, dirs5000):
+    """A pass limit below a window's pairs splits each window further inside the windowed
+    call (its level 0 then takes the two-pass path); the result is still the whole pyramid."""
+    w = synth.config2(fibers_per_ply=6, segments=480, R=128, K=4)
+    geom = dict(ctrl=torch.from_numpy(w.ctrl).to(DEV), fiber_offsets=torch.from_numpy(w.fiber_offsets).to(DEV))
+    dirs = torch.from_numpy(dirs5000).to(DEV)
+    L0 = ctx.voxelize(w.grid, **geom)
+    whole = [L0.host()] + [p.host() for p in ctx.build_lod(L0, K=4, dirs=dirs)]
+    per_level = [[] for _ in range(5)]
+
+    def on_window(win, levels):
+        for l, lv in enumerate(levels):
+            per_level[l].append(lv.host())
+
+    ctx.set_max_pairs_per_pass(20_000)
+    try:
+        top = ctx.voxelize_lod_windowed(w.grid, window_log2=5, on_window=on_window, K=4, dirs=dirs, **geom)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_max_pairs_per_pass(2**31 - 1)
+    got = [_cat_levels(p) for p in per_level] + [t.host() for t in top]
+    assert len(got) == len(whole)
+    for l, (g, r) in enumerate(zip(got, whole)):
+        for f in FIELDS:
+            assert np.array_equal(np.asarray(g[f]).view(np.uint8), np.asarray(r[f]).view(np.uint8)), (l, f)
