@@ -59,7 +59,7 @@ typedef struct {
 /* Cubic grid (Sec. 3.1: positions normalised to [0, Resolution) per axis).  Voxel (i,j,k)
  * covers origin + voxel_size * [i,i+1] x [j,j+1] x [k,k+1].  Grid coordinates are
  * u = (p - origin) * (1 / voxel_size), evaluated in FP32.
- * resolution: power of two, 1..2048 (1..1024 for vx_backward and batches).
+ * resolution: power of two, 1..2048 (1..1024 for batches and vx_backward_noalloc).
  * sub_res: sub-cells per voxel edge; 8 (the paper's third-level resolution, Sec. 3.1) is
  * the supported value. */
 typedef struct {
@@ -247,8 +247,10 @@ VX_API vx_status vx_voxelize_lod_windowed(vx_context* ctx, const vx_primitives* 
  *     weight (n the unit normal; the clipped polygon's edges on voxel planes carry the
  *     derivative of the area).
  * Sub-cell occupancy and the key set are piecewise constant and carry no gradient.
- * Candidate pairs are recomputed, not stored.
- *   prims: the forward's primitives; grid: the forward's grid (resolution <= 1024).
+ * Candidate pairs are recomputed, not stored, window by window as in vx_voxelize (windows
+ * at most 1024 voxels wide and one pass of pairs each); every window adds its terms to the
+ * per-primitive FP64 gradients.
+ *   prims: the forward's primitives; grid: the forward's grid (resolution <= 2048).
  *   keys0 (device) [num_voxels0]: level-0 keys of the forward (sorted).
  *   grad_mass, grad_moment: HOST arrays of num_levels+1 device pointers; level l has
  *     as many rows as there are distinct keys0 >> 3l ([V_l] and [V_l][6] floats).
@@ -257,8 +259,8 @@ VX_API vx_status vx_voxelize_lod_windowed(vx_context* ctx, const vx_primitives* 
  *     triangles: [num_prims][3][4], d loss / d (x, y, z) of every vertex, w = 0.
  *   grad_weights (device) [num_prims] or NULL.
  * Deterministic (fixed summation order, no atomics).  Errors: VX_ERR_INVALID_ARG,
- * VX_ERR_UNSUPPORTED (resolution > 1024), VX_ERR_OUT_OF_MEMORY, VX_ERR_CAPACITY,
- * VX_ERR_CUDA. */
+ * VX_ERR_UNSUPPORTED (resolution > 2048), VX_ERR_OUT_OF_MEMORY, VX_ERR_CAPACITY (a single
+ * voxel over the per-pass pair limit), VX_ERR_CUDA. */
 VX_API vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, const vx_grid* grid,
                              const uint64_t* keys0, int64_t num_voxels0, int num_levels,
                              const float* const* grad_mass, const float* const* grad_moment,

@@ -618,6 +618,14 @@ __device__ __forceinline__ uint32_t lower_key(const uint64_t* __restrict__ keys,
 // warp per segment: sum of its pair gradients (lane j takes pairs j, j+32, ...; fixed tree).
 // The segment's candidate keys lie between their minimum and maximum, so the voxels are
 // looked up in the slice of keys0 between those two keys.
+// The window of one pass of the adjoint: pair keys are relative to its corner (wx, wy, wz),
+// global keys are key_hi | key; per-primitive gradients are added to (accumulate) or written.
+struct AdjWin {
+    uint64_t key_hi;
+    int wx, wy, wz;
+    int accumulate;
+};
+
 __global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_fibers(const float4* __restrict__ ra,
                                                                     const float4* __restrict__ rb, uint32_t np,
                                                                     const uint32_t* __restrict__ offs,
@@ -626,7 +634,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_fibers(const float4
                                                                     const uint64_t* __restrict__ keys0, uint32_t V0,
                                                                     const double* __restrict__ gm,
                                                                     const double* __restrict__ gM,
-                                                                    double* __restrict__ seg_grad) {
+                                                                    double* __restrict__ seg_grad, AdjWin W) {
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * EMIT_WARPS;
     for (uint32_t p = blockIdx.x * EMIT_WARPS + (threadIdx.x >> 5); p < np; p += warps) {
@@ -646,19 +654,20 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_fibers(const float4
                 kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
             }
             uint32_t bound = 0;
-            if (lane == 0) bound = lower_key(keys0, 0, V0, (uint64_t)kmin);
-            if (lane == 1) bound = lower_key(keys0, 0, V0, (uint64_t)kmax + 1);
+            if (lane == 0) bound = lower_key(keys0, 0, V0, W.key_hi | kmin);
+            if (lane == 1) bound = lower_key(keys0, 0, V0, (W.key_hi | kmax) + 1);
             const uint32_t lo = __shfl_sync(0xffffffffu, bound, 0), hi = __shfl_sync(0xffffffffu, bound, 1);
             for (uint32_t j = lane; j < n; j += 32) {
                 const uint32_t key = pkeys[beg + j];
-                const uint32_t v = lower_key(keys0, lo, hi, (uint64_t)key);
-                if (v >= hi || keys0[v] != (uint64_t)key) continue;
+                const uint64_t gk = W.key_hi | key;
+                const uint32_t v = lower_key(keys0, lo, hi, gk);
+                if (v >= hi || keys0[v] != gk) continue;
                 double gr[8];
                 double gMv[6];
 #pragma unroll
                 for (int c = 0; c < 6; ++c) gMv[c] = gM[(size_t)v * 6 + c];
-                pair_grad(g, (int)vx_compact1by2(key), (int)vx_compact1by2(key >> 1), (int)vx_compact1by2(key >> 2),
-                          gm[v], gMv, gr);
+                pair_grad(g, W.wx + (int)vx_compact1by2(key), W.wy + (int)vx_compact1by2(key >> 1),
+                          W.wz + (int)vx_compact1by2(key >> 2), gm[v], gMv, gr);
 #pragma unroll
                 for (int c = 0; c < 8; ++c) acc[c] = acc[c] + gr[c];
             }
@@ -667,7 +676,10 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_fibers(const float4
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[c] = acc[c] + __shfl_xor_sync(0xffffffffu, acc[c], o);
-        if (lane < 8) seg_grad[(size_t)p * 8 + lane] = acc[lane];
+        if (lane < 8) {
+            double* o = seg_grad + (size_t)p * 8 + lane;
+            *o = W.accumulate ? *o + acc[lane] : acc[lane];
+        }
     }
 }
 
@@ -822,7 +834,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_tris(const float4* 
                                                                   const uint64_t* __restrict__ keys0, uint32_t V0,
                                                                   const double* __restrict__ gm,
                                                                   const double* __restrict__ gM,
-                                                                  double* __restrict__ tri_grad) {
+                                                                  double* __restrict__ tri_grad, AdjWin W) {
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * EMIT_WARPS;
     for (uint32_t p = blockIdx.x * EMIT_WARPS + (threadIdx.x >> 5); p < np; p += warps) {
@@ -842,19 +854,20 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_tris(const float4* 
             kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
         }
         uint32_t bound = 0;
-        if (n > 0 && lane == 0) bound = lower_key(keys0, 0, V0, (uint64_t)kmin);
-        if (n > 0 && lane == 1) bound = lower_key(keys0, 0, V0, (uint64_t)kmax + 1);
+        if (n > 0 && lane == 0) bound = lower_key(keys0, 0, V0, W.key_hi | kmin);
+        if (n > 0 && lane == 1) bound = lower_key(keys0, 0, V0, (W.key_hi | kmax) + 1);
         const uint32_t lo = __shfl_sync(0xffffffffu, bound, 0), hi = __shfl_sync(0xffffffffu, bound, 1);
         for (uint32_t j = lane; j < n; j += 32) {
             const uint32_t key = pkeys[beg + j];
-            const uint32_t v = lower_key(keys0, lo, hi, (uint64_t)key);
-            if (v >= hi || keys0[v] != (uint64_t)key) continue;
+            const uint64_t gk = W.key_hi | key;
+            const uint32_t v = lower_key(keys0, lo, hi, gk);
+            if (v >= hi || keys0[v] != gk) continue;
             double g[10];
             double gMv[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c) gMv[c] = gM[(size_t)v * 6 + c];
-            tri_pair_grad(A, B, Cv, (int)vx_compact1by2(key), (int)vx_compact1by2(key >> 1),
-                          (int)vx_compact1by2(key >> 2), gm[v], gMv, g);
+            tri_pair_grad(A, B, Cv, W.wx + (int)vx_compact1by2(key), W.wy + (int)vx_compact1by2(key >> 1),
+                          W.wz + (int)vx_compact1by2(key >> 2), gm[v], gMv, g);
 #pragma unroll
             for (int c = 0; c < 10; ++c) acc[c] = acc[c] + g[c];
         }
@@ -862,7 +875,10 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_adjoint_tris(const float4* 
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
             for (int c = 0; c < 10; ++c) acc[c] = acc[c] + __shfl_xor_sync(0xffffffffu, acc[c], o);
-        if (lane < 10) tri_grad[(size_t)p * 10 + lane] = acc[lane];
+        if (lane < 10) {
+            double* o = tri_grad + (size_t)p * 10 + lane;
+            *o = W.accumulate ? *o + acc[lane] : acc[lane];
+        }
     }
 }
 
@@ -897,7 +913,7 @@ extern "C" vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, co
     if (!fiber && prims->kind != VX_TRIANGLES) return VX_ERR_INVALID_ARG;
     const uint32_t R = grid->resolution;
     if (R == 0 || (R & (R - 1)) != 0) return VX_ERR_INVALID_ARG;
-    if (R > 1024 || grid->sub_res != 8) return VX_ERR_UNSUPPORTED;
+    if (R > 2048 || grid->sub_res != 8) return VX_ERR_UNSUPPORTED;
     if (num_voxels0 < 0 || num_voxels0 > 0xffffffffll || num_levels < 0 || num_levels > 11) return VX_ERR_INVALID_ARG;
     if ((num_voxels0 > 0 && !keys0) || !(grid->voxel_size > 0.0f) || !isfinite(grid->voxel_size))
         return VX_ERR_INVALID_ARG;
@@ -939,83 +955,65 @@ extern "C" vx_status vx_backward(vx_context* ctx, const vx_primitives* prims, co
                                                                                      grad_moment[l], 0, gm, gM));
         }
     }
-    // ---- recompute the candidate pairs (primitive-major order) --------------------------
-    VX_TRY(vx_ws_ensure(ctx, WS_REC_A, (size_t)np * 16, s));
-    VX_TRY(vx_ws_ensure(ctx, WS_REC_B, (size_t)np * 16, s));
-    VX_TRY(vx_ws_ensure(ctx, WS_MISC, 256, s));
-    uint32_t* misc = (uint32_t*)ctx->ws[WS_MISC].p;
-    VX_CUDA_TRY(cudaMemsetAsync(misc, 0, 64, s));
-    float4* r0 = (float4*)ctx->ws[WS_REC_A].p;
-    float4* r1 = (float4*)ctx->ws[WS_REC_B].p;
-    float4* r2 = nullptr;
-    uint32_t* fs = nullptr;
-    if (fiber) {
-        if (F > 0x7fffffff) return VX_ERR_CAPACITY;
-        VX_TRY(vx_ws_ensure(ctx, WS_FIBER_START, (size_t)F * 4 + 256, s));
-        fs = (uint32_t*)ctx->ws[WS_FIBER_START].p;
-        VX_LAUNCH(ctx, ST_PREP, s, k_fiber_seg_counts<<<grid_for((size_t)F, 256), 256, 0, s>>>(prims->fiber_offsets, F, prims->num_ctrl, fs, misc));
-        VX_TRY(vx_scan_u32(ctx, fs, fs, (uint32_t)F, misc + 4, s));
-        VX_LAUNCH(ctx, ST_PREP, s, k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl, prims->num_ctrl,
-                                                                                 prims->fiber_offsets, fs, F, misc + 4,
-                                                                                 prims->weights, np, g, r0, r1, misc));
-    } else {
-        VX_TRY(vx_ws_ensure(ctx, WS_REC_C, (size_t)np * 16, s));
-        r2 = (float4*)ctx->ws[WS_REC_C].p;
-        VX_LAUNCH(ctx, ST_PREP, s, k_prep_tris<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->tri_verts,
-                                                                               prims->weights, np, g, r0, r1, r2, misc));
-    }
-    VX_TRY(vx_ws_ensure(ctx, WS_COUNT, (size_t)np * 4, s));
-    VX_TRY(vx_ws_ensure(ctx, WS_OFFS, (size_t)np * 4, s));
-    uint32_t* cnt = (uint32_t*)ctx->ws[WS_COUNT].p;
-    uint32_t* offs = (uint32_t*)ctx->ws[WS_OFFS].p;
+    // ---- recompute the candidate pairs (primitive-major order), window by window ----------
+    // Windows as in vx_voxelize: at most 1024 voxels wide and one pass of pairs each.  Every
+    // window adds its pairs' terms to the per-primitive gradients (FP64).
+    Prepared Pp;
+    VX_TRY(prepare(ctx, prims, grid, s, &Pp));
+    std::vector<Leaf> leaves;
+    int counted = -1;
+    const int lo0[3] = {0, 0, 0};
+    VX_TRY(plan_windows(ctx, Pp, lo0, Pp.bits_R, 10, s, &leaves, &counted));
+    float4 *r0 = Pp.r0, *r1 = Pp.r1, *r2 = Pp.r2;
+    uint32_t* misc = Pp.misc;
+    uint32_t* fs = fiber ? (uint32_t*)ctx->ws[WS_FIBER_START].p : nullptr;
+    const size_t per_prim = fiber ? 64 : 80;
+    VX_TRY(vx_ws_ensure(ctx, WS_SEG_OUT, (size_t)np * per_prim, s));
+    double* pgrad = (double*)ctx->ws[WS_SEG_OUT].p;
+    VX_CUDA_TRY(cudaMemsetAsync(pgrad, 0, (size_t)np * per_prim, s));
     const unsigned cblocks = (unsigned)std::min<size_t>((np + EMIT_WARPS - 1) / EMIT_WARPS, (size_t)vx::kSMs * 64);
-    if (fiber)
-        VX_LAUNCH(ctx, ST_COUNT, s, k_candidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                        r0, r1, nullptr, np, full_window((int)R), cnt, nullptr, nullptr, nullptr));
-    else
-        VX_LAUNCH(ctx, ST_COUNT, s, k_candidates<false, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                        r0, r1, r2, np, full_window((int)R), cnt, nullptr, nullptr, nullptr));
-    VX_TRY(vx_scan_u32(ctx, cnt, offs, np, misc + 1, s));
-    // the exact 64-bit total: the 32-bit scan total wraps
-    unsigned long long* t64 = (unsigned long long*)(misc + 8);
-    VX_LAUNCH(ctx, ST_COUNT, s, k_sum_u64<<<(unsigned)std::min<size_t>(grid_for(np, 256), (size_t)vx::kSMs * 8), 256, 0, s>>>(
-                                    cnt, np, t64));
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 48, cudaMemcpyDeviceToHost, s));
-    VX_CUDA_TRY(cudaStreamSynchronize(s));
-    if (((uint32_t*)ctx->host_pin)[0]) return VX_ERR_INVALID_ARG;
-    const uint64_t npairs64 = ((const uint64_t*)ctx->host_pin)[4];
-    if (npairs64 >= 0x80000000ull) return VX_ERR_CAPACITY;
-    const uint32_t npairs = (uint32_t)npairs64;
-    VX_TRY(vx_ws_ensure(ctx, WS_KEYS0, (size_t)std::max<uint32_t>(npairs, 1) * 4, s));
-    VX_TRY(vx_ws_ensure(ctx, WS_VALS0, (size_t)std::max<uint32_t>(npairs, 1) * 4, s));
-    uint32_t* k0 = (uint32_t*)ctx->ws[WS_KEYS0].p;
-    uint32_t* v0 = (uint32_t*)ctx->ws[WS_VALS0].p;
-    if (npairs && fiber)
-        VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                       r0, r1, nullptr, np, full_window((int)R), nullptr, offs, k0, v0));
-    if (npairs && !fiber)
-        VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<false, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                       r0, r1, r2, np, full_window((int)R), nullptr, offs, k0, v0));
+    for (size_t i = 0; i < leaves.size(); ++i) {
+        const Leaf& w = leaves[i];
+        const Window win = window_of(w);
+        uint64_t total = w.pairs;
+        if (counted != (int)i) VX_TRY(count_window(ctx, fiber, np, win, r0, r1, r2, misc, s, &total));
+        counted = (int)i;
+        const uint32_t npairs = (uint32_t)total;
+        uint32_t* cnt = (uint32_t*)ctx->ws[WS_COUNT].p;
+        uint32_t* offs = (uint32_t*)ctx->ws[WS_OFFS].p;
+        VX_TRY(vx_ws_ensure(ctx, WS_KEYS0, (size_t)std::max<uint32_t>(npairs, 1) * 4, s));
+        VX_TRY(vx_ws_ensure(ctx, WS_VALS0, (size_t)std::max<uint32_t>(npairs, 1) * 4, s));
+        uint32_t* k0 = (uint32_t*)ctx->ws[WS_KEYS0].p;
+        uint32_t* v0 = (uint32_t*)ctx->ws[WS_VALS0].p;
+        AdjWin W;
+        W.key_hi = key_hi_of(w);
+        W.wx = w.lo[0]; W.wy = w.lo[1]; W.wz = w.lo[2];
+        W.accumulate = 1;
+        if (fiber) {
+            VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                           r0, r1, nullptr, np, win, nullptr, offs, k0, v0));
+            VX_LAUNCH(ctx, ST_REDUCE_FIBERS, s, k_adjoint_fibers<<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                                    r0, r1, np, offs, cnt, k0, keys0, V0, gm, gM, pgrad, W));
+        } else {
+            VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<false, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                           r0, r1, r2, np, win, nullptr, offs, k0, v0));
+            VX_LAUNCH(ctx, ST_REDUCE_TRIS, s, k_adjoint_tris<<<cblocks, EMIT_WARPS * 32, 0, s>>>(
+                                                  r0, r1, r2, np, offs, cnt, k0, keys0, V0, gm, gM, pgrad, W));
+        }
+        VX_CUDA_TRY(cudaGetLastError());
+    }
     if (!fiber) {
-        // ---- per-triangle gradients (no sharing between triangles: no scatter) ---------------
-        VX_TRY(vx_ws_ensure(ctx, WS_SEG_OUT, (size_t)np * 80, s));
-        double* tri_grad = (double*)ctx->ws[WS_SEG_OUT].p;
-        VX_LAUNCH(ctx, ST_REDUCE_TRIS, s, k_adjoint_tris<<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                              r0, r1, r2, np, offs, cnt, k0, keys0, V0, gm, gM, tri_grad));
+        // per-triangle gradients (no sharing between triangles: no scatter)
         VX_LAUNCH(ctx, ST_FINALIZE, s, k_adjoint_tri_out<<<grid_for(np, 256), 256, 0, s>>>(
-                                           tri_grad, np, g.s, (float4*)grad_ctrl, grad_weights));
+                                           pgrad, np, g.s, (float4*)grad_ctrl, grad_weights));
         VX_CUDA_TRY(cudaGetLastError());
         return VX_OK;
     }
-    // ---- per-segment gradients, then the control-point scatter ---------------------------
-    VX_TRY(vx_ws_ensure(ctx, WS_SEG_OUT, (size_t)np * 64, s));
-    double* seg_grad = (double*)ctx->ws[WS_SEG_OUT].p;
-    VX_LAUNCH(ctx, ST_REDUCE_FIBERS, s, k_adjoint_fibers<<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                            r0, r1, np, offs, cnt, k0, keys0, V0, gm, gM, seg_grad));
+    // per-segment gradients, then the control-point scatter
     VX_LAUNCH(ctx, ST_FINALIZE, s, k_adjoint_ctrl<<<grid_for((size_t)P, 256), 256, 0, s>>>(
-                                       prims->fiber_offsets, F, fs, P, seg_grad, g.s, (float4*)grad_ctrl));
+                                       prims->fiber_offsets, F, fs, P, pgrad, g.s, (float4*)grad_ctrl));
     if (grad_weights)
-        VX_LAUNCH(ctx, ST_FINALIZE, s, k_adjoint_weights<<<grid_for(np, 256), 256, 0, s>>>(seg_grad, np, grad_weights));
+        VX_LAUNCH(ctx, ST_FINALIZE, s, k_adjoint_weights<<<grid_for(np, 256), 256, 0, s>>>(pgrad, np, grad_weights));
     VX_CUDA_TRY(cudaGetLastError());
     return VX_OK;
 }
@@ -1170,7 +1168,11 @@ extern "C" vx_status vx_backward_noalloc(const vx_primitives* prims, const vx_gr
     if (npairs)
         k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, nullptr, np, full_window((int)R), nullptr,
                                                                      offs, k0, v0);
-    k_adjoint_fibers<<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, np, offs, cnt, k0, keys0, V0, gm, gM, seg_grad);
+    AdjWin W0;
+    W0.key_hi = 0;
+    W0.wx = W0.wy = W0.wz = 0;
+    W0.accumulate = 0;
+    k_adjoint_fibers<<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, np, offs, cnt, k0, keys0, V0, gm, gM, seg_grad, W0);
     k_adjoint_ctrl<<<grid_for((size_t)P, 256), 256, 0, s>>>(prims->fiber_offsets, F, fs, P, seg_grad, g.s,
                                                              (float4*)grad_ctrl);
     if (grad_weights) k_adjoint_weights<<<grid_for(np, 256), 256, 0, s>>>(seg_grad, np, grad_weights);

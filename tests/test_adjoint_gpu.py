@@ -276,3 +276,58 @@ def test_tri_adjoint_finite_differences_heightfield(heightfield_grads):
         checked += 1
     print(f"FD checked {checked}, stencils across a kink skipped {kinks}, worst rel {worst:.2e}; "
           f"{floored} within 1e-4 only through the floor, worst relative to |FD| {worst_fd:.2e}")
+
+
+def _fiber_grads(ctx, ctrl, off, grid, weights, levels):
+    """GPU forward, the loss weights of every level, and vx_backward's gradients."""
+    c = torch.from_numpy(ctrl).to(DEV)
+    o = torch.from_numpy(off).to(DEV)
+    wt = torch.from_numpy(weights).to(DEV)
+    L0 = ctx.voxelize(grid, ctrl=c, fiber_offsets=o, weights=wt)
+    pyr = ctx.build_lod(L0, K=1, num_levels=levels)
+    keys = [lv.keys.cpu().numpy().view(np.uint64) for lv in [L0] + pyr]
+    ab = [synth.loss_weights(k, l) for l, k in enumerate(keys)]
+    gm = [torch.from_numpy(a).to(DEV) for a, _ in ab]
+    gM = [torch.from_numpy(b).to(DEV) for _, b in ab]
+    g_c, g_w = ctx.backward(grid, ctrl=c, fiber_offsets=o, keys0=L0.keys, grad_mass=gm, grad_moment=gM,
+                            weights=wt)
+    torch.cuda.synchronize()
+    return g_c.cpu().numpy(), g_w.cpu().numpy(), keys, ab
+
+
+def test_adjoint_windows_match_one_pass(ctx):
+    """Windows forced by a low pass limit (several octant windows, each adding its pairs' terms)
+    give the gradients of one pass up to the FP64 summation order."""
+    w = synth.config2(fibers_per_ply=4, segments=300, R=64, K=1)
+    rng = np.random.default_rng(54)
+    weights = rng.uniform(0.5, 2.0, w.num_prims).astype(np.float32)
+    ref_c, ref_w, _, _ = _fiber_grads(ctx, w.ctrl, w.fiber_offsets, w.grid, weights, 3)
+    ctx.set_max_pairs_per_pass(5_000)
+    try:
+        got_c, got_w, _, _ = _fiber_grads(ctx, w.ctrl, w.fiber_offsets, w.grid, weights, 3)
+    finally:
+        ctx.set_max_pairs_per_pass(2**31 - 1)
+    sc = np.max(np.abs(ref_c))
+    assert np.max(np.abs(got_c - ref_c)) <= 1e-6 * sc
+    assert np.max(np.abs(got_w - ref_w)) <= 1e-6 * np.max(np.abs(ref_w))
+
+
+def test_adjoint_at_2048_matches_oracle_gradient(ctx):
+    """A 2048^3 grid (the fibers cross the 1024^3 windows' planes): vx_backward, window by
+    window, against the oracle's FP64 analytic gradient, tolerance of the 64^3 test."""
+    ctrl, off, grid = synth.random_segments(10, 30, 2048, seed=55, radius=(0.3, 1.5), step=(0.5, 2.0))
+    # move the walks onto the window corner (1024, 1024, 1024) so that they cross its planes
+    shift = np.float32(1024.0 / 2048.0) - ctrl[:, :3].mean(axis=0)
+    ctrl = ctrl.copy()
+    ctrl[:, :3] += shift
+    nseg = synth.fiber_segment_count(off)
+    weights = np.random.default_rng(56).uniform(0.5, 2.0, nseg).astype(np.float32)
+    g_c, g_w, keys, ab = _fiber_grads(ctx, ctrl, off, grid, weights, 2)
+    assert len(np.unique(keys[0] >> np.uint64(30))) > 1          # voxels in several 1024^3 windows
+    ref0 = oracle.voxelize_fibers(ctrl, off, grid, weights)
+    assert np.array_equal(ref0["keys"], keys[0])
+    gm0, gM0 = oracle.broadcast_adjoints(ref0["keys"], keys, [a for a, _ in ab], [b for _, b in ab])
+    _, d_ctrl, d_w = oracle.fiber_adjoint(ctrl, off, grid, ref0["keys"], gm0, gM0, weights=weights)
+    for got, ref in ((g_c[:, :3], d_ctrl[:, :3]), (g_c[:, 3], d_ctrl[:, 3]), (g_w, d_w)):
+        scale = np.median(np.abs(ref))
+        assert np.all(np.abs(got - ref) <= 1e-4 * np.maximum(np.abs(ref), scale))
