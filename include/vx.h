@@ -181,7 +181,8 @@ typedef struct {
  * keys, each level a block of the context's allocator).  Ownership passes to the callee,
  * which releases each level with vx_level_release (at once or later).  Work on `stream`
  * that produced them may still be in flight: order any use after it on that stream.
- * Returning a status other than VX_OK stops vx_voxelize_lod_windowed, which returns it. */
+ * Ownership passes whatever the callee returns.  Returning a status other than VX_OK stops
+ * vx_voxelize_lod_windowed, which returns it. */
 typedef vx_status (*vx_window_fn)(void* user, const vx_window* window, vx_level* levels, int num_levels,
                                   void* stream);
 

@@ -713,13 +713,14 @@ cudaError_t cluster_set_smem(int K) {
 
 // Clustering of one level.  tier: 0 a warp per parent (resident blocks of 4 warps), 1 a
 // block of 8 warps, 2 a block of 16 warps per parent; -1 picks by n, the level's parent
-// count (or an upper bound of it): warps on wide levels, blocks on narrow ones.  Every
-// tier gives the same result.  wcnt[0] holds the number of listed parents and wcnt[1]
+// count (or an upper bound of it): warps on wide levels, blocks of 8 warps on narrow ones
+// (on the 768k-capsule yarn the 8-warp blocks matched or beat the 16-warp ones on every
+// level of at most 212 parents).  Every tier gives the same result.  wcnt[0] holds the number of listed parents and wcnt[1]
 // (zero) the take counter.
 void launch_cluster(const LevelIn& li, const uint32_t* starts, const uint32_t* work, const uint32_t* wcnt,
                     const vx_level& out, int K, const float4* dirs4, int N, const LobeStats* cst, LobeStats* pst,
                     unsigned long long* nsampled, uint32_t n, int merge, cudaStream_t s, int tier = -1) {
-    if (tier < 0) tier = n > (uint32_t)(vx::kSMs * 16) ? 0 : (n > (uint32_t)vx::kSMs ? 1 : 2);
+    if (tier < 0) tier = n > (uint32_t)(vx::kSMs * 16) ? 0 : 1;
     if (tier == 0) {
         const unsigned cb = (unsigned)std::min<size_t>((n + CL_WARPS - 1) / CL_WARPS, (size_t)vx::kSMs * 7);
         k_sggx_cluster<1><<<cb, CL_WARPS * 32, cluster_smem(1, K), s>>>(li, starts, work, wcnt, out, K, dirs4, N,

@@ -552,47 +552,65 @@ vx_status vx_segment_starts(vx_context* ctx, const uint32_t* keys, uint32_t n, u
     return VX_OK;
 }
 
-vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, uint32_t** keys_alt,
-                            uint32_t** vals_alt, uint32_t n, int bits, cudaStream_t s, uint32_t* err) {
-    if (n <= 1 || bits <= 0) return VX_OK;
-    // as few passes as 9-bit digits allow, digits as even as possible; 512 buckets when a
-    // digit is wider than 8 bits (27-bit keys: three passes of 9 instead of four of 8)
+// Digit widths of the passes of a `bits`-bit key: as few passes as 9-bit digits allow, digits
+// as even as possible (27-bit keys: three passes of 9 instead of four of 8).  Returns the count.
+static int digit_plan(int bits, int* widths) {
     const int passes = (bits + 8) / 9;
     const int width = (bits + passes - 1) / passes;
-    const uint32_t rb = width > 8 ? 512u : 256u;
-    uint32_t nt = (n + SORT_TILE - 1) / SORT_TILE;
-    size_t hn = (size_t)rb * nt;
-    if (hn > 0xffffffffull) return VX_ERR_CAPACITY;
-    VX_TRY(vx_ws_ensure(ctx, WS_SORT_HIST, hn * 4, s));
-    uint32_t* hist = (uint32_t*)ctx->ws[WS_SORT_HIST].p;
+    int left = bits, n = 0;
+    while (left > 0) {
+        widths[n] = left < width ? left : width;
+        left -= widths[n++];
+    }
+    return n;
+}
+
+template <int RB>
+vx_status sort_pass(vx_context* ctx, uint32_t** keys, uint32_t** vals, uint32_t** keys_alt, uint32_t** vals_alt,
+                    uint32_t n, int shift, uint32_t dmask, uint32_t nt, uint32_t* hist, cudaStream_t s,
+                    uint32_t* err) {
     static bool attr_set = false;   // dynamic shared memory of the scatter, once per process
     if (!attr_set) {
-        VX_CUDA_TRY(cudaFuncSetAttribute(k_radix_scatter_pipe<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)pipe_smem(512)));
-        VX_CUDA_TRY(cudaFuncSetAttribute(k_radix_scatter_pipe<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)pipe_smem(256)));
+        VX_CUDA_TRY(cudaFuncSetAttribute(k_radix_scatter_pipe<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pipe_smem(RB)));
         attr_set = true;
     }
     const unsigned sblocks = (unsigned)std::min<uint32_t>(nt, (uint32_t)vx::kSMs * 2);
-    for (int shift = 0; shift < bits; shift += width) {
-        int nb = bits - shift < width ? bits - shift : width;
-        uint32_t dmask = (1u << nb) - 1u;
-        if (rb == 512u)
-            VX_LAUNCH(ctx, ST_SORT_HIST, s, (k_radix_hist<false, 512><<<nt, SORT_THREADS, 0, s>>>(
-                                                *keys, *vals, n, shift, dmask, nt, nullptr, hist)));
+    VX_LAUNCH(ctx, ST_SORT_HIST, s, (k_radix_hist<false, RB><<<nt, SORT_THREADS, 0, s>>>(
+                                        *keys, *vals, n, shift, dmask, nt, nullptr, hist)));
+    VX_TRY(vx_scan_u32(ctx, hist, hist, (uint32_t)((size_t)RB * nt), nullptr, s));
+    VX_LAUNCH(ctx, ST_SORT_SCATTER, s, (k_radix_scatter_pipe<RB><<<sblocks, SORT_THREADS, pipe_smem(RB), s>>>(
+                                           *keys, *vals, n, shift, dmask, nt, hist, *keys_alt, *vals_alt, err)));
+    VX_CUDA_TRY(cudaGetLastError());
+    uint32_t* t = *keys; *keys = *keys_alt; *keys_alt = t;
+    t = *vals; *vals = *vals_alt; *vals_alt = t;
+    return VX_OK;
+}
+
+vx_status vx_radix_sort_u32(vx_context* ctx, uint32_t** keys, uint32_t** vals, uint32_t** keys_alt,
+                            uint32_t** vals_alt, uint32_t n, int bits, cudaStream_t s, uint32_t* err) {
+    if (n <= 1 || bits <= 0) return VX_OK;
+    int widths[33];
+    const int passes = digit_plan(bits, widths);
+    int wmax = 0;
+    for (int p = 0; p < passes; ++p) wmax = std::max(wmax, widths[p]);
+    if (wmax > 10) return VX_ERR_CAPACITY;
+    const uint32_t nt = (n + SORT_TILE - 1) / SORT_TILE;
+    const size_t hn = ((size_t)1 << std::max(wmax, 8)) * nt;
+    if (hn > 0xffffffffull) return VX_ERR_CAPACITY;
+    VX_TRY(vx_ws_ensure(ctx, WS_SORT_HIST, hn * 4, s));
+    uint32_t* hist = (uint32_t*)ctx->ws[WS_SORT_HIST].p;
+    int shift = 0;
+    for (int p = 0; p < passes; ++p) {
+        const int w = widths[p];
+        const uint32_t dmask = (1u << w) - 1u;
+        if (w > 9)
+            VX_TRY(sort_pass<1024>(ctx, keys, vals, keys_alt, vals_alt, n, shift, dmask, nt, hist, s, err));
+        else if (w > 8)
+            VX_TRY(sort_pass<512>(ctx, keys, vals, keys_alt, vals_alt, n, shift, dmask, nt, hist, s, err));
         else
-            VX_LAUNCH(ctx, ST_SORT_HIST, s, (k_radix_hist<false, 256><<<nt, SORT_THREADS, 0, s>>>(
-                                                *keys, *vals, n, shift, dmask, nt, nullptr, hist)));
-        VX_TRY(vx_scan_u32(ctx, hist, hist, (uint32_t)hn, nullptr, s));
-        if (rb == 512u)
-            VX_LAUNCH(ctx, ST_SORT_SCATTER, s, (k_radix_scatter_pipe<512><<<sblocks, SORT_THREADS, pipe_smem(512), s>>>(
-                                                   *keys, *vals, n, shift, dmask, nt, hist, *keys_alt, *vals_alt, err)));
-        else
-            VX_LAUNCH(ctx, ST_SORT_SCATTER, s, (k_radix_scatter_pipe<256><<<sblocks, SORT_THREADS, pipe_smem(256), s>>>(
-                                                   *keys, *vals, n, shift, dmask, nt, hist, *keys_alt, *vals_alt, err)));
-        VX_CUDA_TRY(cudaGetLastError());
-        uint32_t* t = *keys; *keys = *keys_alt; *keys_alt = t;
-        t = *vals; *vals = *vals_alt; *vals_alt = t;
+            VX_TRY(sort_pass<256>(ctx, keys, vals, keys_alt, vals_alt, n, shift, dmask, nt, hist, s, err));
+        shift += w;
     }
     return VX_OK;
 }

@@ -457,10 +457,8 @@ extern "C" vx_status vx_voxelize_lod_windowed(vx_context* ctx, const vx_primitiv
             if (st == VX_OK) {
                 ++nroots;
                 vx_level_release(ctx, &lv[w], s);
-                // ownership of levels 0 .. w-1 passes to the callee
+                // ownership of levels 0 .. w-1 passes to the callee, whatever it returns
                 st = on_window(user, &info, lv, w, stream);
-                if (st != VX_OK)
-                    for (int l = 0; l < w; ++l) vx_level_release(ctx, &lv[l], s);
             } else {
                 for (int l = 0; l <= w; ++l) vx_level_release(ctx, &lv[l], s);
             }
