@@ -170,7 +170,7 @@ VX_API vx_status vx_voxelize(vx_context* ctx, const vx_primitives* prims, const 
 /* ---- windowed pyramid (grids whose pyramid does not fit in device memory at once) ------ */
 
 /* One window of the grid: voxels [lo, lo + 2^log2_size) per axis; index counts the
- * non-empty windows in Morton order. */
+ * non-empty windows in Morton order and is the window's row in the returned top[0]. */
 typedef struct {
     int32_t lo[3];
     int32_t log2_size;

@@ -413,13 +413,14 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_radix_scatter_pipe(const ui
         const uint32_t tn_items = (uint32_t)min((size_t)SORT_TILE, (size_t)n - tile0);
         uint32_t* const sk = stage0 + (size_t)st * 2 * SORT_TILE;
         uint32_t* const sv = sk + SORT_TILE;
+        bool gave_up = false;
         if ((pending >> st) & 1u) {
-            if (!mbar_wait(&bar[st], (phase >> st) & 1u)) {
-                lost = true;
-                break;
+            if (mbar_wait(&bar[st], (phase >> st) & 1u)) {
+                phase ^= 1u << st;
+                pending &= ~(1u << st);
+            } else {
+                gave_up = true;
             }
-            phase ^= 1u << st;
-            pending &= ~(1u << st);
         } else {
             for (uint32_t i = threadIdx.x; i < tn_items; i += SORT_THREADS) {
                 sk[i] = keys[tile0 + i];
@@ -428,7 +429,11 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_radix_scatter_pipe(const ui
         }
         for (int i = threadIdx.x; i < SORT_WARPS * RB; i += SORT_THREADS) (&wcnt[0][0])[i] = 0;
         for (int d = threadIdx.x; d < RB; d += SORT_THREADS) gofs[d] = hist[(size_t)d * nt + t];
-        __syncthreads();
+        // the whole block leaves together when any thread's wait gave up
+        if (__syncthreads_or(gave_up)) {
+            lost = true;
+            break;
+        }
         // rank: per-warp running counters (stable within the tile)
         uint32_t k[SORT_ITEMS], v[SORT_ITEMS], rk[SORT_ITEMS];
         const uint32_t lb = (uint32_t)w * (32 * SORT_ITEMS);
@@ -496,7 +501,8 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_radix_scatter_pipe(const ui
     }
     if (lost) {
         if (threadIdx.x == 0) atomicOr(err, 4u);
-        // the block's own copies still in flight land before it exits (bounded)
+        // the block's own copies still in flight land before it exits (bounded; a thread
+        // whose wait succeeded has already cleared that stage's bit)
         for (int s2 = 0; s2 < 2; ++s2)
             if ((pending >> s2) & 1u) mbar_wait(&bar[s2], (phase >> s2) & 1u);
     }

@@ -419,6 +419,8 @@ extern "C" vx_status vx_voxelize_lod_windowed(vx_context* ctx, const vx_primitiv
     if (w < 1 || w > L) return VX_ERR_INVALID_ARG;
     if (lod->num_levels != 0) return VX_ERR_INVALID_ARG;
     if (lod->K < 1 || lod->K > vx::kMaxK) return VX_ERR_UNSUPPORTED;
+    if (lod->K > 1 && (!lod->dirs || lod->n_samples < 1 || lod->n_samples > 65536)) return VX_ERR_INVALID_ARG;
+    if (lod->merge != 0 && lod->merge != 1) return VX_ERR_INVALID_ARG;
     if (3 * (L - w) > 21) return VX_ERR_UNSUPPORTED;              // at most 2^21 windows
     const int K = lod->K;
     for (int l = 0; l <= L - w; ++l) memset(&top[l], 0, sizeof(vx_level));
@@ -445,7 +447,7 @@ extern "C" vx_status vx_voxelize_lod_windowed(vx_context* ctx, const vx_primitiv
         vx_window info;
         for (int a = 0; a < 3; ++a) info.lo[a] = (leaves[i].lo[a] >> sh) << sh;
         info.log2_size = w;
-        info.index = index++;
+        info.index = index;
         vx_level lv[12];
         memset(lv, 0, sizeof(lv));
         st = voxelize_leaves(ctx, P, group, -1, s, &lv[0]);
@@ -456,6 +458,7 @@ extern "C" vx_status vx_voxelize_lod_windowed(vx_context* ctx, const vx_primitiv
             if (st == VX_OK) st = copy_root(ctx, lv[w], roots, nroots, s);
             if (st == VX_OK) {
                 ++nroots;
+                ++index;
                 vx_level_release(ctx, &lv[w], s);
                 // ownership of levels 0 .. w-1 passes to the callee, whatever it returns
                 st = on_window(user, &info, lv, w, stream);

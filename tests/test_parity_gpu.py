@@ -588,6 +588,11 @@ def test_windowed_pyramid_equals_whole(ctx, dirs5000, kind, w_log2, K):
     assert len(seen) > 1 and [s["index"] for s in seen] == list(range(len(seen)))
     assert len(top) == len(whole) - w_log2
     got = [_cat_levels(p) for p in per_level] + [t.host() for t in top]
+    roots = np.asarray(got[w_log2]["keys"]).astype(np.uint64)
+    assert len(roots) == len(seen)
+    for win in seen:   # a window's index is its root's row in the top level
+        finest = np.asarray(per_level[w_log2 - 1][win["index"]]["keys"]).astype(np.uint64)
+        assert np.all((finest >> np.uint64(3)) == roots[win["index"]])
     for l, (g, r) in enumerate(zip(got, whole)):
         for f in FIELDS:
             assert np.array_equal(np.asarray(g[f]).view(np.uint8), np.asarray(r[f]).view(np.uint8)), (l, f)
