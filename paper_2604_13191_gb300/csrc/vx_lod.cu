@@ -61,47 +61,32 @@ __global__ void k_parent_starts(const uint64_t* __restrict__ keys, uint32_t n, c
     if (i == 0) starts[np] = n;
 }
 
-__device__ __forceinline__ void mask_counts(const uint64_t* m, uint16_t& occ, uint8_t* proj) {
-    int o = 0, yz = 0, xz = 0;
-    uint64_t orz = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        uint64_t x = m[w];
-        o += __popcll(x);
-        orz |= x;
-        uint64_t t = x | (x >> 4);
-        t |= t >> 2;
-        t |= t >> 1;
-        yz += __popcll(t & 0x0101010101010101ull);
-        uint64_t r = x | (x >> 32);
-        r |= r >> 16;
-        r |= r >> 8;
-        xz += __popc((uint32_t)(r & 0xffu));
-    }
-    occ = (uint16_t)o;
-    proj[0] = (uint8_t)yz;
-    proj[1] = (uint8_t)xz;
-    proj[2] = (uint8_t)__popcll(orz);
+// 2x2x2 OR-downsample of two z-slabs a, b of a child mask (bit x + 8 y) into the parent word of
+// its octant (ox, oy): the 4 x 4 result lands at bit 4 ox + qx + 8 (4 oy + qy).  The folds run on
+// 32-bit halves (rows 0-3 low, 4-7 high): z, then the row pairs (2qy, 2qy + 1), then the x pairs;
+// one byte permute gathers the even rows and two steps compact their even bits to nibbles.
+__device__ __forceinline__ uint64_t downsample_word(uint64_t a, uint64_t b, int ox, int oy) {
+    uint32_t lo = (uint32_t)a | (uint32_t)b;
+    uint32_t hi = (uint32_t)(a >> 32) | (uint32_t)(b >> 32);
+    lo |= lo >> 8;
+    hi |= hi >> 8;
+    lo |= lo >> 1;
+    hi |= hi >> 1;
+    uint32_t x = __byte_perm(lo, hi, 0x6420) & 0x55555555u;   // byte qy: rows 2qy | 2qy + 1
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0f0f0f0fu;
+    return (uint64_t)(x << (4 * ox)) << (32 * oy);
 }
 
-// 2x2x2 OR-downsample of a child mask into octant (ox,oy,oz) of the parent mask
+// the child's 2x2x2-downsampled mask ORed into octant (ox, oy, oz) of the parent mask pm
 __device__ __forceinline__ void downsample_into(const uint64_t* cm, int oct, uint64_t* pm) {
     const int ox = oct & 1, oy = (oct >> 1) & 1, oz = (oct >> 2) & 1;
 #pragma unroll
     for (int qz = 0; qz < 4; ++qz) {
-        uint64_t f = cm[2 * qz] | cm[2 * qz + 1];        // fold z pairs
-        f |= f >> 8;                                      // fold y pairs (rows 2qy, 2qy+1)
-        f |= f >> 1;                                      // fold x pairs
-        uint64_t out = 0;
-#pragma unroll
-        for (int qy = 0; qy < 4; ++qy) {
-            uint32_t b = (uint32_t)(f >> (16 * qy)) & 0x55u;  // bits 0,2,4,6
-            b = (b | (b >> 1)) & 0x33u;
-            b = (b | (b >> 2)) & 0x0fu;
-            out |= (uint64_t)b << (4 * ox + 8 * (4 * oy + qy));
-        }
+        const uint64_t w = downsample_word(cm[2 * qz], cm[2 * qz + 1], ox, oy);
         // (constant indices: the parent mask stays in registers)
-        if (oz) pm[4 + qz] |= out; else pm[qz] |= out;
+        pm[qz] |= oz ? 0ull : w;
+        pm[4 + qz] |= oz ? w : 0ull;
     }
 }
 
@@ -115,7 +100,6 @@ __device__ __forceinline__ void compact_params(const float* S, float* c) {
     c[5] = pyz > 0.0f ? S[5] / sqrtf(pyz) : 0.0f;
 }
 
-// thread per parent (np_dev, when given, overrides np with a device-side count)
 // Histogram counts and sample second moment of one lobe (Sec. 4.4), 48 bytes.  Kept per
 // output lobe of a level so that the next level's clustering does not sample it again
 // (the statistics are a deterministic function of the lobe's stored S); h[0] < 0 marks a
@@ -126,107 +110,225 @@ struct LobeStats {
 };
 static_assert(sizeof(LobeStats) == kLobeStatsBytes, "lobe statistics record");
 
-__global__ void k_lod_reduce(LevelIn in, const uint32_t* __restrict__ starts, uint32_t np, vx_level out, int K,
-                             uint32_t* __restrict__ work, uint32_t* __restrict__ nwork,
-                             const uint32_t* __restrict__ np_dev, const LobeStats* __restrict__ cst,
-                             LobeStats* __restrict__ pst) {
+// One of the six moment components (or the mass, c = 6) picked by a lane index without a
+// dynamically indexed array (which would go through local memory).
+__device__ __forceinline__ float pick7(const float* M, float m, int c) {
+    float r = m;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) r = (c == k) ? M[k] : r;
+    return r;
+}
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint32_t m, uint64_t v, int o) {
+    const uint32_t lo = __shfl_xor_sync(m, (uint32_t)v, o, 8);
+    const uint32_t hi = __shfl_xor_sync(m, (uint32_t)(v >> 32), o, 8);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// A group of 8 lanes reduces one parent p: its children are in[starts[p] .. starts[p+1]) in
+// key order, at most 8 of them in a level of unique keys (one per octant), and lane j of the
+// group reads children beg + j, beg + j + 8, ...  All children's records are read at once.
+//   - mass and moment: the sequential FP32 chain in child order of the definition; the
+//     children's values are broadcast in the group and every lane folds them in that order;
+//   - mask: the OR of the children's 2x2x2-downsampled masks (exact in any order);
+//   - lobes (Sec. 4.3-4.4): K = 1 gives S = M / m; K > 1 copies at most K candidate lobes by
+//     weight, a lane per child; more candidates go to the SGGX-H work list.
+// (np_dev, when given, overrides np with a device-side count.)
+constexpr int LR_BLOCK = 256;
+
+__global__ void __launch_bounds__(LR_BLOCK, 4) k_lod_reduce(LevelIn in, const uint32_t* __restrict__ starts, uint32_t np,
+                                                         vx_level out, int K, uint32_t* __restrict__ work,
+                                                         uint32_t* __restrict__ nwork,
+                                                         const uint32_t* __restrict__ np_dev,
+                                                         const LobeStats* __restrict__ cst,
+                                                         LobeStats* __restrict__ pst) {
     if (np_dev) np = *np_dev;
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-        const uint32_t beg = starts[p], end = starts[p + 1];
-        float m = 0.0f;
-        float M[6] = {0, 0, 0, 0, 0, 0};
-        uint64_t pm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        int ncand = 0;
-        for (uint32_t c = beg; c < end; ++c) {
-            m = m + in.mass[c];
-            // moments as 8-byte pairs (rows are 24 bytes, 8-byte aligned)
-            const float2* m2 = reinterpret_cast<const float2*>(in.moment + (size_t)c * 6);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const float2 q = m2[j];
-                M[2 * j] = M[2 * j] + q.x;
-                M[2 * j + 1] = M[2 * j + 1] + q.y;
-            }
-            uint64_t cm[8];
-            const ulonglong2* cm2 = reinterpret_cast<const ulonglong2*>(in.mask + (size_t)c * 8);
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                const ulonglong2 x = cm2[w];
-                cm[2 * w] = x.x;
-                cm[2 * w + 1] = x.y;
-            }
-            downsample_into(cm, (int)(in.keys[c] & 7ull), pm);
-            ncand += in.lobe_count[c];
+    const int lane = threadIdx.x & 31;
+    const int j = lane & 7;
+    const uint32_t gm = 0xffu << (lane & 24);      // the lanes of this group
+    const uint32_t groups = gridDim.x * (LR_BLOCK / 8);
+    // the trip count is the same for the whole warp (full-warp ballot below); each iteration
+    // loads the next one's child range while it works
+    uint32_t base = (blockIdx.x * LR_BLOCK + (threadIdx.x & ~31u)) >> 3;
+    uint32_t nbeg = 0, nend = 0;
+    if (base + (uint32_t)(lane >> 3) < np) {
+        nbeg = starts[base + (lane >> 3)];
+        nend = starts[base + (lane >> 3) + 1];
+    }
+    for (; base < np; base += groups) {
+        const uint32_t p = base + (uint32_t)(lane >> 3);
+        const uint32_t beg = nbeg, end = nend;
+        const uint32_t pn = p + groups;
+        if (pn < np) {
+            nbeg = starts[pn];
+            nend = starts[pn + 1];
         }
-        out.keys[p] = in.keys[beg] >> 3;
-        out.mass[p] = m;
-        float2* Mo = reinterpret_cast<float2*>(out.moment + (size_t)p * 6);
+        bool cluster = false;
+        if (p < np) {
+            float m = 0.0f;
+            float M[6] = {0, 0, 0, 0, 0, 0};
+            uint64_t pm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            int ncand = 0;
+            for (uint32_t c0 = beg; c0 < end; c0 += 8) {
+                const uint32_t c = c0 + (uint32_t)j;
+                float cmass = 0.0f;
+                float cmo[6] = {0, 0, 0, 0, 0, 0};
+                if (c < end) {
+                    cmass = in.mass[c];
+                    // moments as 8-byte pairs (rows are 24 bytes, 8-byte aligned)
+                    const float2* m2 = reinterpret_cast<const float2*>(in.moment + (size_t)c * 6);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) Mo[j] = make_float2(M[2 * j], M[2 * j + 1]);
-        ulonglong2* pm2 = reinterpret_cast<ulonglong2*>(out.mask + (size_t)p * 8);
-#pragma unroll
-        for (int w = 0; w < 4; ++w) pm2[w] = make_ulonglong2(pm[2 * w], pm[2 * w + 1]);
-        uint16_t occ;
-        uint8_t pj[3];
-        mask_counts(pm, occ, pj);
-        out.occ[p] = occ;
-        out.occ_proj[(size_t)p * 3 + 0] = pj[0];
-        out.occ_proj[(size_t)p * 3 + 1] = pj[1];
-        out.occ_proj[(size_t)p * 3 + 2] = pj[2];
-        float* lo = out.lobes + (size_t)p * K * 7;
-        float* co = out.compact + (size_t)p * K * 6;
-        if (K == 1) {
-            if (m > 0.0f) {
-                float S[6];
-#pragma unroll
-                for (int j = 0; j < 6; ++j) S[j] = M[j] / m;
-#pragma unroll
-                for (int j = 0; j < 6; ++j) lo[j] = S[j];
-                lo[6] = m;
-                compact_params(S, co);
-                out.lobe_count[p] = 1;
-            } else {
-#pragma unroll
-                for (int j = 0; j < 7; ++j) lo[j] = 0.0f;
-#pragma unroll
-                for (int j = 0; j < 6; ++j) co[j] = 0.0f;
-                out.lobe_count[p] = 0;
-            }
-        } else if (ncand <= K) {
-            // copy the children's lobes, ordered by weight (descending), ties by candidate order
-            for (int j = 0; j < K * 7; ++j) lo[j] = 0.0f;
-            for (int j = 0; j < K * 6; ++j) co[j] = 0.0f;
-            int idx = 0;
-            for (uint32_t c = beg; c < end; ++c) {
-                for (int l = 0; l < in.lobe_count[c]; ++l, ++idx) {
-                    const float* src = in.lobes + ((size_t)c * in.K + l) * 7;
-                    const float wx = src[6];
-                    int rank = 0, idy = 0;
-                    for (uint32_t c2 = beg; c2 < end; ++c2)
-                        for (int l2 = 0; l2 < in.lobe_count[c2]; ++l2, ++idy) {
-                            const float wy = in.lobes[((size_t)c2 * in.K + l2) * 7 + 6];
-                            if (wy > wx || (wy == wx && idy < idx)) ++rank;
-                        }
-                    for (int j = 0; j < 7; ++j) lo[rank * 7 + j] = src[j];
-                    compact_params(src, co + rank * 6);
-                    if (pst) {
-                        LobeStats st;
-                        if (cst) {
-                            st = cst[(size_t)c * in.K + l];
-                        } else {
-                            st.h[0] = -1;
-                        }
-                        pst[(size_t)p * K + rank] = st;
+                    for (int k = 0; k < 3; ++k) {
+                        const float2 q = m2[k];
+                        cmo[2 * k] = q.x;
+                        cmo[2 * k + 1] = q.y;
                     }
+                    uint64_t cm[8];
+                    const ulonglong2* cm2 = reinterpret_cast<const ulonglong2*>(in.mask + (size_t)c * 8);
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const ulonglong2 x = cm2[w];
+                        cm[2 * w] = x.x;
+                        cm[2 * w + 1] = x.y;
+                    }
+                    downsample_into(cm, (int)(in.keys[c] & 7ull), pm);
+                    ncand += in.lobe_count[c];
+                }
+                const int nc = (int)min(8u, end - c0);   // the same in the whole group
+                for (int i = 0; i < nc; ++i) {
+                    const float mi = __shfl_sync(gm, cmass, i, 8);
+                    float Mi[6];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) Mi[k] = __shfl_sync(gm, cmo[k], i, 8);
+                    m = m + mi;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) M[k] = M[k] + Mi[k];
                 }
             }
-            out.lobe_count[p] = (uint8_t)ncand;
-        } else {
-            out.lobe_count[p] = 0;
-            uint32_t slot = atomicAdd(nwork, 1u);
-            work[slot] = p;
+            // the group's OR of the mask words, scattered so that lane j keeps word j: each step
+            // keeps the half of the words its lane-index bit selects and ORs in the partner's copy
+            uint64_t h4[4], h2[2];
+            {
+                const bool up = (j & 4) != 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint64_t keep = up ? pm[4 + q] : pm[q], give = up ? pm[q] : pm[4 + q];
+                    h4[q] = keep | shfl_xor_u64(gm, give, 4);
+                }
+            }
+            {
+                const bool up = (j & 2) != 0;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const uint64_t keep = up ? h4[2 + q] : h4[q], give = up ? h4[q] : h4[2 + q];
+                    h2[q] = keep | shfl_xor_u64(gm, give, 2);
+                }
+            }
+            const bool up1 = (j & 1) != 0;
+            const uint64_t word = (up1 ? h2[1] : h2[0]) | shfl_xor_u64(gm, up1 ? h2[0] : h2[1], 1);
+            // occupancy counts of word j (the z-slab j), summed over the group
+            int o = __popcll(word);
+            uint64_t t = word | (word >> 4);
+            t |= t >> 2;
+            t |= t >> 1;
+            int yz = __popcll(t & 0x0101010101010101ull);
+            uint64_t rr = word | (word >> 32);
+            rr |= rr >> 16;
+            rr |= rr >> 8;
+            int xz = __popc((uint32_t)(rr & 0xffu));
+            uint64_t orz = word;
+#pragma unroll
+            for (int sh = 4; sh > 0; sh >>= 1) {
+                o += __shfl_xor_sync(gm, o, sh, 8);
+                yz += __shfl_xor_sync(gm, yz, sh, 8);
+                xz += __shfl_xor_sync(gm, xz, sh, 8);
+                orz |= shfl_xor_u64(gm, orz, sh);
+                ncand += __shfl_xor_sync(gm, ncand, sh, 8);
+            }
+            const size_t pb = (size_t)p;
+            out.mask[pb * 8 + j] = word;
+            if (j < 6) out.moment[pb * 6 + j] = pick7(M, m, j);
+            if (j == 0) {
+                out.keys[pb] = in.keys[beg] >> 3;
+                out.mass[pb] = m;
+                out.occ[pb] = (uint16_t)o;
+                out.occ_proj[pb * 3 + 0] = (uint8_t)yz;
+                out.occ_proj[pb * 3 + 1] = (uint8_t)xz;
+                out.occ_proj[pb * 3 + 2] = (uint8_t)__popcll(orz);
+            }
+            float* lo = out.lobes + pb * K * 7;
+            float* co = out.compact + pb * K * 6;
+            if (K == 1) {
+                if (m > 0.0f) {
+                    float S[6], cc[6];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) S[k] = M[k] / m;
+                    compact_params(S, cc);
+                    if (j < 7) lo[j] = pick7(S, m, j);
+                    if (j < 6) co[j] = pick7(cc, 0.0f, j);
+                    if (j == 0) out.lobe_count[pb] = 1;
+                } else {
+                    if (j < 7) lo[j] = 0.0f;
+                    if (j < 6) co[j] = 0.0f;
+                    if (j == 0) out.lobe_count[pb] = 0;
+                }
+            } else if (ncand <= K) {
+                // the children's lobes ordered by weight (descending), ties by candidate order;
+                // each lane places the lobes of its own children, the slots past ncand are zero
+                for (int r = ncand + j; r < K; r += 8) {
+                    for (int k = 0; k < 7; ++k) lo[r * 7 + k] = 0.0f;
+                    for (int k = 0; k < 6; ++k) co[r * 6 + k] = 0.0f;
+                }
+                for (uint32_t c = beg + (uint32_t)j; c < end; c += 8) {
+                    int idx = 0;   // candidate index of the child's first lobe
+                    for (uint32_t c2 = beg; c2 < c; ++c2) idx += in.lobe_count[c2];
+                    const int nl = in.lobe_count[c];
+                    for (int l = 0; l < nl; ++l, ++idx) {
+                        const float* src = in.lobes + ((size_t)c * in.K + l) * 7;
+                        const float wx = src[6];
+                        int rank = 0, idy = 0;
+                        for (uint32_t c2 = beg; c2 < end; ++c2)
+                            for (int l2 = 0; l2 < in.lobe_count[c2]; ++l2, ++idy) {
+                                const float wy = in.lobes[((size_t)c2 * in.K + l2) * 7 + 6];
+                                if (wy > wx || (wy == wx && idy < idx)) ++rank;
+                            }
+                        for (int k = 0; k < 7; ++k) lo[rank * 7 + k] = src[k];
+                        compact_params(src, co + rank * 6);
+                        if (pst) {
+                            LobeStats st;
+                            if (cst) {
+                                st = cst[(size_t)c * in.K + l];
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < 6; ++k) { st.h[k] = 0; st.Mh[k] = 0.0f; }
+                                st.h[0] = -1;   // never sampled
+                            }
+                            pst[pb * K + rank] = st;
+                        }
+                    }
+                }
+                if (j == 0) out.lobe_count[pb] = (uint8_t)ncand;
+            } else {
+                if (j == 0) {
+                    out.lobe_count[pb] = 0;
+                    cluster = true;
+                }
+            }
+        }
+        // parents left for SGGX-H go to the work list with one atomic per warp (the list's
+        // order does not change any output: each parent is clustered on its own)
+        const uint32_t want = __ballot_sync(0xffffffffu, cluster);
+        if (want) {
+            uint32_t wbase = 0;
+            if (lane == 0) wbase = atomicAdd(nwork, (uint32_t)__popc(want));
+            wbase = __shfl_sync(0xffffffffu, wbase, 0);
+            if (cluster) work[wbase + __popc(want & ((1u << lane) - 1u))] = p;
         }
     }
+}
+
+// grid of the LoD reduce: 8 lanes per parent, at most the 4 blocks per SM that are resident
+inline unsigned lod_reduce_grid(size_t np) {
+    return (unsigned)std::max<size_t>(1, std::min<size_t>((np * 8 + LR_BLOCK - 1) / LR_BLOCK, (size_t)vx::kSMs * 4));
 }
 
 // ------------------------------------------------------------------------------------
@@ -874,7 +976,7 @@ vx_status build_levels(vx_context* ctx, const vx_level* in, const vx_lod_params*
         // statistics kept by the child level (none for the input level) and by this one
         const LobeStats* cst = (K > 1 && l > 1) ? stats[l & 1] : nullptr;
         LobeStats* pst = (K > 1) ? stats[(l + 1) & 1] : nullptr;
-        VX_LAUNCH(ctx, ST_LOD_REDUCE, s, k_lod_reduce<<<(unsigned)std::min<size_t>(grid_for(ncur, 128), (size_t)vx::kSMs * 32), 128, 0, s>>>(
+        VX_LAUNCH(ctx, ST_LOD_REDUCE, s, k_lod_reduce<<<lod_reduce_grid(ncur), LR_BLOCK, 0, s>>>(
             li, starts, ncur, out[l - 1], K, work, misc + 40, nullptr, cst, pst));
         VX_CUDA_TRY(cudaGetLastError());
         if (K > 1) {
@@ -920,13 +1022,13 @@ cudaError_t vx_lod_step_batched(const vx_level* in, const uint16_t* inst_in, con
     LevelIn li;
     li.keys = in->keys; li.mask = in->mask; li.mass = in->mass; li.moment = in->moment;
     li.lobe_count = in->lobe_count; li.lobes = in->lobes; li.K = in->K;
-    const unsigned rb = (unsigned)std::min<size_t>(grid_for(cap_out, 128), (size_t)vx::kSMs * 32);
+    const unsigned rb = lod_reduce_grid(cap_out);
     const int K = out->K;
     if (K > 1) {
         cudaError_t e2 = cudaMemsetAsync(wcnt, 0, 8, s);
         if (e2 != cudaSuccess) return e2;
     }
-    k_lod_reduce<<<rb, 128, 0, s>>>(li, starts, 0u, *out, K, K > 1 ? work : nullptr, K > 1 ? wcnt : nullptr, np_dev,
+    k_lod_reduce<<<rb, LR_BLOCK, 0, s>>>(li, starts, 0u, *out, K, K > 1 ? work : nullptr, K > 1 ? wcnt : nullptr, np_dev,
                                     (const LobeStats*)cst, (LobeStats*)pst);
     if (K > 1)
         launch_cluster(li, starts, work, wcnt, *out, K, dirs4, n_dirs, (const LobeStats*)cst, (LobeStats*)pst, nullptr,
