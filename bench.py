@@ -719,22 +719,27 @@ def adjoint_vs_forward(ctx, dev, steps):
                             num_prims=w.num_prims)
 
     def timed(fn, n):
+        # the median of three timed blocks of n calls (one disturbed block does not set it)
         for _ in range(2):
             fn()
         torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(n):
-            fn()
-        e.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(e) / n
+        blocks = []
+        for _ in range(3):
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(n):
+                fn()
+            e.record()
+            torch.cuda.synchronize()
+            blocks.append(a.elapsed_time(e) / n)
+        return sorted(blocks)[1], blocks
 
-    tf = timed(fwd, steps)
-    tb = timed(bwd, steps)
+    tf, tf_blocks = timed(fwd, steps)
+    tb, tb_blocks = timed(bwd, steps)
     return {"workload": ADJ_WORKLOAD, "prims": int(w.num_prims), "forward_ms": tf, "backward_ms": tb,
-            "backward_over_forward": tb / tf}
+            "backward_over_forward": tb / tf, "forward_blocks_ms": tf_blocks, "backward_blocks_ms": tb_blocks,
+            "timing": "median of three blocks of the step count, CUDA events"}
 
 
 def _source_hash(name):
