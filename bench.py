@@ -781,6 +781,7 @@ def roofline(prof, w, level_sizes, steps):
     avg_ms = ms / max(nl, 1)
     units_per_launch = units / max(nl, 1)
     traffic = None
+    issue = None   # ncu's issue-slot figures of the same capture (ALU-bound kernels)
     tfile = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tfile):
         try:
@@ -788,15 +789,24 @@ def roofline(prof, w, level_sizes, steps):
             ent = t.get(stage)
             if ent and ent.get("source_hash") == _source_hash(ent["source"]):
                 traffic = ent["bytes_per_launch"] * units_per_launch / ent["units_per_launch"]
+                if "issue_active" in ent:
+                    issue = {"issue_active": ent["issue_active"],
+                             "lanes_active_per_inst": ent.get("lanes_active_per_inst"),
+                             "alu_pipe_active": ent.get("alu_pipe_active"),
+                             "source": "ncu capture of the same kernel source (profiles/ncu_traffic.json)"}
         except Exception:
             traffic = None
+            issue = None
     if stage in ALU_OPS:
         ops = units_per_launch * ALU_OPS[stage]
         ach = ops / (avg_ms * 1e-3) / 1e12
         return {"kernel": stage, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s",
                 "frac": ach / alu_peak, "traffic": traffic, "avg_launch_ms": avg_ms,
                 "launches_per_step": nl // steps, "units_per_launch": units_per_launch,
-                "ops_per_unit": ALU_OPS[stage],
+                "ops_per_unit": ALU_OPS[stage], "issue_slots": issue,
+                "ops_note": "ops_per_unit counts the definition's FP32 operations (512 sub-cell tests of 10 "
+                            "operations per pair); the kernel skips most of them with exact group tests, so "
+                            "issue_slots says how busy the SM is",
                 "peak_source": f"152 SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz (max SM clock, MEASURED_PEAKS)"}
     per_unit = HBM_BYTES.get(stage)
     ach = None if per_unit is None else units_per_launch * per_unit / (avg_ms * 1e-3) / 1e9
