@@ -942,8 +942,10 @@ ORC_API int vxo_voxelize_tris(const float* tri, int64_t T, const float* weights,
 /* ------------------------------------------------------------------------- */
 
 /* Symmetric square root of a 3x3 SPD matrix by cyclic Jacobi rotations (FP32,
- * 6 sweeps over the pairs (0,1),(0,2),(1,2)); S packed xx,yy,zz,xy,xz,yz,
- * R full row-major 3x3. */
+ * at most 6 sweeps over the pairs (0,1),(0,2),(1,2); a rotation is skipped when its
+ * off-diagonal is zero or negligible against both diagonals); S packed
+ * xx,yy,zz,xy,xz,yz, R full row-major 3x3.  Sec. 4.4 samples a lobe through its square
+ * root and fixes no method for computing it. */
 ORC_API void vxo_sqrtm3(const float* S, float* Rm) {
     float a[3][3] = {{S[0], S[3], S[4]}, {S[3], S[1], S[5]}, {S[4], S[5], S[2]}};
     float V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
@@ -954,6 +956,14 @@ ORC_API void vxo_sqrtm3(const float* S, float* Rm) {
             float apq = a[p][q];
             if (apq == 0.0f) continue;
             float app = a[p][p], aqq = a[q][q];
+            /* an off-diagonal negligible against both diagonals (adding 100 |apq|
+             * changes neither in FP32) is set to zero instead of rotated */
+            float g = 100.0f * fabsf(apq);
+            if (fabsf(app) + g == fabsf(app) && fabsf(aqq) + g == fabsf(aqq)) {
+                a[p][q] = 0.0f;
+                a[q][p] = 0.0f;
+                continue;
+            }
             float theta = (aqq - app) / (2.0f * apq);
             float t = 1.0f / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
             if (theta < 0.0f) t = -t;

@@ -334,7 +334,8 @@ inline unsigned lod_reduce_grid(size_t np) {
 // ------------------------------------------------------------------------------------
 // SGGX-H
 // ------------------------------------------------------------------------------------
-// S'^(1/2) of a symmetric 3x3 matrix (packed xx,yy,zz,xy,xz,yz) by cyclic Jacobi.  Returns
+// S'^(1/2) of a symmetric 3x3 matrix (packed xx,yy,zz,xy,xz,yz) by cyclic Jacobi (at most 6
+// sweeps; a rotation is skipped when its off-diagonal is zero or negligible).  Returns
 // true when the square root is well conditioned: smallest singular value above 1e-4 of the
 // largest, and the largest above 1e-15.  S' = S + 1e-6 tr(S) I bounds the ratio below by
 // ~1e-3 for any S with tr(S) > 0; the rounding of the FP32 Jacobi (orthogonality of the
@@ -352,6 +353,14 @@ __device__ bool sqrtm3(const float* S, float* Rm) {
             const float apq = a[p][q];
             if (apq == 0.0f) continue;
             const float app = a[p][p], aqq = a[q][q];
+            // an off-diagonal negligible against both diagonals (adding 100 |apq| changes
+            // neither in FP32) is set to zero instead of rotated
+            const float g = 100.0f * fabsf(apq);
+            if (fabsf(app) + g == fabsf(app) && fabsf(aqq) + g == fabsf(aqq)) {
+                a[p][q] = 0.0f;
+                a[q][p] = 0.0f;
+                continue;
+            }
             const float theta = (aqq - app) / (2.0f * apq);
             float t = __frcp_rn(fabsf(theta) + sqrtf(theta * theta + 1.0f));
             if (theta < 0.0f) t = -t;
@@ -435,7 +444,7 @@ __device__ __forceinline__ int rint_prod(float x, float s) {
 // Histogram and sample second moment of lobe S, computed cooperatively by G warps
 // (G = 1: one warp; G > 1: the whole block, `red` is G * 13 words of shared memory).
 // Every count and sum is an integer, so the result is independent of G and of the order
-// in which the threads visit the samples.  Result valid in every participating thread.
+// in which the threads visit the samples.  Threads tid < 6 receive the result.
 // The part of a lobe's statistics one thread keeps: component `tid` of the histogram and
 // of M^ (threads tid < 6 of the group hold the six components).
 struct LobeOwn {
@@ -540,32 +549,31 @@ __device__ LobeOwn sample_lobe(const float* S, const float4* __restrict__ dirs, 
             }
         }
         __syncthreads();
-        long long tc = 0, th[6] = {0, 0, 0, 0, 0, 0}, tq[6] = {0, 0, 0, 0, 0, 0};
-        for (int ww = 0; ww < G; ++ww) {
-            tc += red[ww * 13];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                th[c] += red[ww * 13 + 1 + c];
-                tq[c] += red[ww * 13 + 7 + c];
+        // thread c < 6 keeps component c only (the result below reads nothing else)
+        if (tid < 6) {
+            long long tc = 0, th = 0, tq = 0;
+            for (int ww = 0; ww < G; ++ww) {
+                tc += red[ww * 13];
+                th += red[ww * 13 + 1 + tid];
+                tq += red[ww * 13 + 7 + tid];
             }
+            cnt = (int)tc;
+            h[0] = (int32_t)th;
+            Q[0] = tq;
         }
         __syncthreads();
-        cnt = (int)tc;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            h[c] = (int32_t)th[c];
-            Q[c] = tq[c];
-        }
     }
     // component `tid` (tid < 6) of the histogram and of M^ (one FP64 division per thread)
     LobeOwn own;
     own.h = h[0];
     long long q = Q[0];
+    if (G == 1) {
 #pragma unroll
-    for (int c = 1; c < 6; ++c) {
-        if (tid == c) {
-            own.h = h[c];
-            q = Q[c];
+        for (int c = 1; c < 6; ++c) {
+            if (tid == c) {
+                own.h = h[c];
+                q = Q[c];
+            }
         }
     }
     own.mh = 0.0f;
