@@ -951,6 +951,7 @@ ORC_API void vxo_sqrtm3(const float* S, float* Rm) {
     float V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     static const int PQ[3][2] = {{0, 1}, {0, 2}, {1, 2}};
     for (int sweep = 0; sweep < 6; ++sweep) {
+        int rotated = 0;
         for (int r = 0; r < 3; ++r) {
             int p = PQ[r][0], q = PQ[r][1];
             float apq = a[p][q];
@@ -964,10 +965,13 @@ ORC_API void vxo_sqrtm3(const float* S, float* Rm) {
                 a[q][p] = 0.0f;
                 continue;
             }
-            float theta = (aqq - app) / (2.0f * apq);
-            float t = 1.0f / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
-            if (theta < 0.0f) t = -t;
+            /* tan of the rotation angle: the smaller root of t^2 + 2 t d / (2 apq) - 1 = 0,
+             * d = aqq - app, written sgn(d) 2 apq / (|d| + sqrt(d^2 + 4 apq^2)) */
+            float d = aqq - app, e = 2.0f * apq;
+            float t = e / (fabsf(d) + sqrtf(d * d + e * e));
+            if (d < 0.0f) t = -t;
             float c = 1.0f / sqrtf(t * t + 1.0f);
+            rotated = 1;
             float sn = t * c;
             a[p][p] = app - t * apq;
             a[q][q] = aqq + t * apq;
@@ -985,6 +989,7 @@ ORC_API void vxo_sqrtm3(const float* S, float* Rm) {
                 V[i][q] = sn * vp + c * vq;
             }
         }
+        if (!rotated) break; /* every off-diagonal is zero */
     }
     float sg[3];
     for (int i = 0; i < 3; ++i) sg[i] = sqrtf(a[i][i] > 0.0f ? a[i][i] : 0.0f);

@@ -345,6 +345,7 @@ __device__ bool sqrtm3(const float* S, float* Rm) {
     float a[3][3] = {{S[0], S[3], S[4]}, {S[3], S[1], S[5]}, {S[4], S[5], S[2]}};
     float V[3][3] = {{1.0f, 0.0f, 0.0f}, {0.0f, 1.0f, 0.0f}, {0.0f, 0.0f, 1.0f}};
     for (int sweep = 0; sweep < 6; ++sweep) {
+        bool rotated = false;
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             const int p = (r == 2) ? 1 : 0;
@@ -361,10 +362,13 @@ __device__ bool sqrtm3(const float* S, float* Rm) {
                 a[q][p] = 0.0f;
                 continue;
             }
-            const float theta = (aqq - app) / (2.0f * apq);
-            float t = __frcp_rn(fabsf(theta) + sqrtf(theta * theta + 1.0f));
-            if (theta < 0.0f) t = -t;
+            // tan of the rotation angle, sgn(d) 2 apq / (|d| + sqrt(d^2 + 4 apq^2)) with
+            // d = aqq - app (the smaller root of t^2 + 2 t d / (2 apq) - 1 = 0)
+            const float d = aqq - app, e = 2.0f * apq;
+            float t = e / (fabsf(d) + sqrtf(d * d + e * e));
+            if (d < 0.0f) t = -t;
             const float c = __frcp_rn(sqrtf(t * t + 1.0f));
+            rotated = true;
             const float sn = t * c;
             a[p][p] = app - t * apq;
             a[q][q] = aqq + t * apq;
@@ -382,6 +386,7 @@ __device__ bool sqrtm3(const float* S, float* Rm) {
                 V[i][q] = sn * vp + c * vq;
             }
         }
+        if (!rotated) break;   // every off-diagonal is zero
     }
     float sg[3];
 #pragma unroll
