@@ -19,6 +19,10 @@
  *     outputs are left unallocated (block == NULL).
  *   - Calls are deterministic: the same inputs give bit-identical outputs.
  *   - A context is not thread-safe: use one context per host thread / stream.
+ *   - Where a call synchronises its stream to size an output, the few words it reads
+ *     back are stored by a kernel into the context's mapped pinned buffer, not copied by
+ *     a copy engine: the call does not wait behind the caller's transfers on other
+ *     streams (e.g. downloading level 0 while vx_build_lod runs on it).
  */
 #ifndef VX_H_
 #define VX_H_

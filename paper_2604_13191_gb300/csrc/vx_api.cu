@@ -9,7 +9,30 @@
 const char* const kStageNames[ST_NSTAGES] = {
     "prep", "candidates_count", "candidates_emit", "scan", "sort_hist", "sort_scatter", "segment_heads",
     "reduce_fibers", "reduce_tris", "finalize", "lod_counts", "lod_heads", "lod_reduce", "sggx_cluster",
-    "batched_graph"};
+    "batched_graph", "readback"};
+
+namespace {
+__global__ void k_readback(const uint32_t* __restrict__ src, uint32_t n, uint32_t* dst) {
+    const uint32_t i = threadIdx.x;
+    if (i < n) dst[i] = src[i];
+}
+}  // namespace
+
+vx_status vx_readback_async(vx_context* ctx, size_t off, const void* src, size_t bytes, cudaStream_t s) {
+    if ((bytes & 3) || (off & 3) || off + bytes > 64 * sizeof(uint64_t) || ((uintptr_t)src & 3) || !src)
+        return VX_ERR_INVALID_ARG;
+    const uint32_t n = (uint32_t)(bytes / 4);
+    if (n == 0) return VX_OK;
+    VX_LAUNCH(ctx, ST_READBACK, s,
+              k_readback<<<1, 128, 0, s>>>((const uint32_t*)src, n,
+                                           (uint32_t*)((char*)ctx->host_pin_dev + off)));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        vx_record_cuda_error(ctx, e, "k_readback");
+        return VX_ERR_CUDA;
+    }
+    return VX_OK;
+}
 
 static void vx_prof_drain(vx_context* ctx) {
     for (int i = 0; i < ctx->nev; ++i) {
@@ -114,9 +137,13 @@ vx_status vx_context_create(const vx_allocator* alloc, vx_context** out) {
         memset(&ctx->alloc, 0, sizeof(ctx->alloc));
         ctx->own_alloc = true;
     }
-    cudaError_t e = cudaMallocHost((void**)&ctx->host_pin, 64 * sizeof(uint64_t));
+    // the readback buffer is mapped: small results are stored into it by a kernel (see
+    // vx_readback_async), not copied by a copy engine
+    cudaError_t e = cudaHostAlloc((void**)&ctx->host_pin, 64 * sizeof(uint64_t), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&ctx->host_pin_dev, ctx->host_pin, 0);
     if (e != cudaSuccess) {
-        vx_record_cuda_error(ctx, e, "cudaMallocHost");
+        vx_record_cuda_error(ctx, e, "cudaHostAlloc");
+        if (ctx->host_pin) cudaFreeHost(ctx->host_pin);
         delete ctx;
         return VX_ERR_CUDA;
     }
@@ -282,7 +309,7 @@ vx_status vx_export_leaves(vx_context* ctx, const vx_level* level, uint64_t* lea
     k_leaf_masks<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(level->keys, leaf_first, misc + 10, leaf_keys,
                                                              leaf_masks);
     VX_CUDA_TRY(cudaGetLastError());
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc + 10, 4, cudaMemcpyDeviceToHost, s));
+    VX_TRY(vx_readback_async(ctx, 0, misc + 10, 4, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     *num_leaves = ((const uint32_t*)ctx->host_pin)[0];
     return VX_OK;

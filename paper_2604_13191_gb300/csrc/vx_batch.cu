@@ -495,7 +495,7 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
     uint32_t* host = (uint32_t*)ctx->host_pin;
     const unsigned blk = vx::kSMs * 16;
     auto readback = [&](int word) -> uint32_t {
-        if (cudaMemcpyAsync(host, C + word, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return 0xffffffffu;
+        if (vx_readback_async(ctx, 0, C + word, 4, s) != VX_OK) return 0xffffffffu;
         if (cudaStreamSynchronize(s) != cudaSuccess) return 0xffffffffu;
         return host[0];
     };

@@ -40,7 +40,7 @@ struct Buf {
 enum VxStage {
     ST_PREP = 0, ST_COUNT, ST_EMIT, ST_SCAN, ST_SORT_HIST, ST_SORT_SCATTER, ST_HEADS,
     ST_REDUCE_FIBERS, ST_REDUCE_TRIS, ST_FINALIZE, ST_LOD_COUNTS, ST_LOD_HEADS, ST_LOD_REDUCE,
-    ST_SGGX_CLUSTER, ST_BATCH, ST_NSTAGES
+    ST_SGGX_CLUSTER, ST_BATCH, ST_READBACK, ST_NSTAGES
 };
 extern const char* const kStageNames[ST_NSTAGES];
 
@@ -59,7 +59,8 @@ struct vx_context {
     char last_err[256] = {0};
     // workspace slots (grow-only)
     vx::Buf ws[32];
-    uint64_t* host_pin = nullptr; // pinned readback buffer (64 words)
+    uint64_t* host_pin = nullptr; // pinned readback buffer (64 words), mapped
+    uint64_t* host_pin_dev = nullptr;   // its device address
     // profiling
     bool prof = false;
     int64_t launches[ST_NSTAGES] = {0};
@@ -92,6 +93,12 @@ enum WsSlot {
 static_assert(WS_NSLOTS <= 32, "workspace slot table");
 
 void vx_record_cuda_error(vx_context* ctx, cudaError_t e, const char* what);
+// Copies `bytes` (a multiple of 4; src 4-byte aligned) of device memory into the context's
+// pinned readback buffer at byte offset `off` (off + bytes <= 512), with a one-block kernel
+// that stores into the mapped buffer.  No copy engine is involved, so the readback does not
+// queue behind the caller's large transfers on other streams.  The buffer holds the values
+// once `s` is synchronised.
+vx_status vx_readback_async(vx_context* ctx, size_t off, const void* src, size_t bytes, cudaStream_t s);
 vx_status vx_ws_ensure(vx_context* ctx, int slot, size_t bytes, cudaStream_t s);
 void* vx_dev_alloc(vx_context* ctx, size_t bytes, cudaStream_t s);
 void vx_dev_free(vx_context* ctx, void* p, cudaStream_t s);

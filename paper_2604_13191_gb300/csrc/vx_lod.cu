@@ -926,7 +926,7 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
         VX_LAUNCH(ctx, ST_LOD_COUNTS, s, k_level_counts<<<(unsigned)std::min<size_t>(grid_for(n0, 256), (size_t)vx::kSMs * 16), 256, 0, s>>>(
             in->keys, n0, L, misc));
     VX_CUDA_TRY(cudaGetLastError());
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 4 * (L + 1), cudaMemcpyDeviceToHost, s));
+    VX_TRY(vx_readback_async(ctx, 0, misc, 4 * (L + 1), s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     uint32_t counts[32];
     memcpy(counts, ctx->host_pin, 4 * (L + 1));

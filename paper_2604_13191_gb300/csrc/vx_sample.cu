@@ -289,10 +289,11 @@ extern "C" vx_status vx_voxelize_sampled(vx_context* ctx, const vx_primitives* p
         VX_LAUNCH(ctx, ST_PREP, s, k_tri_sample_counts<<<grid_for(np, 256), 256, 0, s>>>(r0, r1, r2, np, S, misc + 3,
                                                                                          cnt));
         VX_TRY(vx_scan_u32(ctx, cnt, offs, np, misc + 1, s));
-        VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 8, cudaMemcpyDeviceToHost, s));
+        VX_TRY(vx_readback_async(ctx, 0, misc, 8, s));
         VX_CUDA_TRY(cudaStreamSynchronize(s));
         if (((const uint32_t*)ctx->host_pin)[0]) return VX_ERR_INVALID_ARG;
         n = ((const uint32_t*)ctx->host_pin)[1];
+        if (n == 0) return vx_level_alloc(ctx, out0, 0, 1, 0, (int)R, s);   // no sample lands anywhere
     }
     VX_CUDA_TRY(cudaGetLastError());
 
@@ -317,8 +318,8 @@ extern "C" vx_status vx_voxelize_sampled(vx_context* ctx, const vx_primitives* p
     VX_TRY(vx_ws_ensure(ctx, WS_STARTS, (size_t)n * 4 + 8, s));
     uint32_t* starts = (uint32_t*)ctx->ws[WS_STARTS].p;
     VX_TRY(vx_segment_starts(ctx, k0, n, misc + 2, starts, s));
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 16, cudaMemcpyDeviceToHost, s));
-    VX_CUDA_TRY(cudaMemcpyAsync((uint32_t*)ctx->host_pin + 4, k0 + (n - 1), 4, cudaMemcpyDeviceToHost, s));
+    VX_TRY(vx_readback_async(ctx, 0, misc, 16, s));
+    VX_TRY(vx_readback_async(ctx, 16, k0 + (n - 1), 4, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     const uint32_t* hp = (const uint32_t*)ctx->host_pin;
     if (hp[0] & 4u) return VX_ERR_TIMEOUT;   // a bounded wait of the sort gave up

@@ -678,7 +678,7 @@ extern "C" vx_status vx_selftest_bounded_wait(vx_context* ctx, int polls, void* 
     VX_CUDA_TRY(cudaMemsetAsync(flag, 0, 4, s));
     k_selftest_wait<<<1, 32, 0, s>>>((uint32_t)polls, flag);
     VX_CUDA_TRY(cudaGetLastError());
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, flag, 4, cudaMemcpyDeviceToHost, s));
+    VX_TRY(vx_readback_async(ctx, 0, flag, 4, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     const uint32_t f = ((uint32_t*)ctx->host_pin)[0];
     return f == 4u ? VX_ERR_TIMEOUT : (f == 1u ? VX_OK : VX_ERR_CUDA);

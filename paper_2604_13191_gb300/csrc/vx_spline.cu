@@ -88,7 +88,7 @@ vx_status vx_tessellate_catmull_rom(vx_context* ctx, const float* nodes, const i
     const int64_t F = num_splines;
     k_spline_offsets<<<(unsigned)((F + 1 + 255) / 256), 256, 0, s>>>(offsets, F, num_nodes, subdiv, out_offsets, err);
     VX_CUDA_TRY(cudaGetLastError());
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, err, 4, cudaMemcpyDeviceToHost, s));
+    VX_TRY(vx_readback_async(ctx, 0, err, 4, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     if (((uint32_t*)ctx->host_pin)[0]) return VX_ERR_INVALID_ARG;
     const int64_t total = (num_nodes - F) * (int64_t)subdiv + F;

@@ -58,7 +58,7 @@ vx_status count_window(vx_context* ctx, bool fiber, uint32_t np, const Window& w
     VX_CUDA_TRY(cudaMemsetAsync(t64, 0, 8, s));
     VX_LAUNCH(ctx, ST_COUNT, s, k_sum_u64<<<(unsigned)std::min<size_t>(grid_for(np, 256), (size_t)vx::kSMs * 8), 256, 0, s>>>(
                                     cnt, np, t64));
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 48, cudaMemcpyDeviceToHost, s));
+    VX_TRY(vx_readback_async(ctx, 0, misc, 48, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     if (((uint32_t*)ctx->host_pin)[0]) return VX_ERR_INVALID_ARG;
     *total = ((const uint64_t*)ctx->host_pin)[4];
@@ -116,7 +116,7 @@ vx_status window_segments(vx_context* ctx, bool fiber, uint32_t np, const Window
     VX_TRY(vx_ws_ensure(ctx, WS_STARTS, (size_t)npairs * 4 + 8, s));
     uint32_t* starts = (uint32_t*)ctx->ws[WS_STARTS].p;
     VX_TRY(vx_segment_starts(ctx, *k0, npairs, misc + 2, starts, s));
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc, 12, cudaMemcpyDeviceToHost, s));
+    VX_TRY(vx_readback_async(ctx, 0, misc, 12, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     if (((uint32_t*)ctx->host_pin)[0] & 4u) return VX_ERR_TIMEOUT;   // a bounded wait of the sort gave up
     *nseg = ((uint32_t*)ctx->host_pin)[2];
@@ -160,7 +160,7 @@ vx_status window_reduce(vx_context* ctx, bool fiber, uint32_t np, uint32_t nseg,
     VX_CUDA_TRY(cudaGetLastError());
     // compaction: dst index = exclusive scan of the non-empty flags (the head flags are free)
     VX_TRY(vx_scan_u32(ctx, seg.nonzero, flags, nseg, misc + 3, s));
-    VX_CUDA_TRY(cudaMemcpyAsync(ctx->host_pin, misc + 3, 4, cudaMemcpyDeviceToHost, s));
+    VX_TRY(vx_readback_async(ctx, 0, misc + 3, 4, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     const uint32_t nvox = ((uint32_t*)ctx->host_pin)[0];
     *nvox_out = nvox;

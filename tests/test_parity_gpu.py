@@ -641,3 +641,31 @@ def test_windowed_pyramid_with_split_windows_equals_whole(ctx, dirs5000):
     for l, (g, r) in enumerate(zip(got, whole)):
         for f in FIELDS:
             assert np.array_equal(np.asarray(g[f]).view(np.uint8), np.asarray(r[f]).view(np.uint8)), (l, f)
+
+
+def test_build_lod_while_level0_downloads(ctx, dirs5000):
+    """vx_build_lod's sizing readback is a kernel store into mapped memory, so the call runs
+    beside a large download of its input on another stream; the pyramid and the downloaded
+    level are unchanged by the overlap."""
+    w = synth.config2(fibers_per_ply=6, segments=480, R=128, K=4)
+    geom = dict(ctrl=torch.from_numpy(w.ctrl).to(DEV), fiber_offsets=torch.from_numpy(w.fiber_offsets).to(DEV))
+    dirs = torch.from_numpy(dirs5000).to(DEV)
+    L0 = ctx.voxelize(w.grid, **geom)
+    ref = [p.host() for p in ctx.build_lod(L0, K=4, dirs=dirs)]
+    torch.cuda.synchronize()
+    host = torch.empty(L0.block.numel(), dtype=torch.uint8).pin_memory()
+    side = torch.cuda.Stream(DEV)
+    ev = torch.cuda.Event()
+    ev.record()
+    with torch.cuda.stream(side):
+        side.wait_event(ev)
+        host.copy_(L0.block, non_blocking=True)
+    got = [p.host() for p in ctx.build_lod(L0, K=4, dirs=dirs)]
+    torch.cuda.synchronize()
+    assert torch.equal(host, L0.block.cpu())
+    assert len(got) == len(ref)
+    for l, (g, r) in enumerate(zip(got, ref)):
+        for f in FIELDS:
+            assert np.array_equal(np.asarray(g[f]).view(np.uint8), np.asarray(r[f]).view(np.uint8)), (l, f)
+    prof_names = ctx.profile_read().keys()
+    assert "readback" in prof_names
