@@ -333,6 +333,7 @@ def main():
         h_out = torch.empty(sum(sizes) + 4096 * len(sizes), dtype=torch.uint8).pin_memory()
         h2d = h_ctrl.numel() * 4 + h_off.numel() * 8 + h_dirs.numel() * 4
         side = torch.cuda.Stream(dev)
+        level_done = [torch.cuda.Event() for _ in sizes[1:]]
 
         def e2e_step():
             c = h_ctrl.to(dev, non_blocking=True)
@@ -346,13 +347,16 @@ def main():
             with torch.cuda.stream(side):
                 side.wait_event(done0)
                 h_out[0: n0].copy_(L0.block, non_blocking=True)
-            pyr = ctx.build_lod(L0, K=K_LOBES, dirs=d)
+            # every coarser level downloads on the second stream as soon as it is complete
+            pyr = ctx.build_lod(L0, K=K_LOBES, dirs=d, events=level_done)
             pos, nbytes = n0, n0
-            for lv in pyr:
-                n = lv.block.numel()
-                h_out[pos: pos + n].copy_(lv.block, non_blocking=True)
-                pos += n
-                nbytes += n
+            with torch.cuda.stream(side):
+                for lv, ev in zip(pyr, level_done):
+                    side.wait_event(ev)
+                    n = lv.block.numel()
+                    h_out[pos: pos + n].copy_(lv.block, non_blocking=True)
+                    pos += n
+                    nbytes += n
             torch.cuda.synchronize()
             return nbytes
 
@@ -373,7 +377,8 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": etot / args.steps,
                "note": "inputs uploaded from pinned host memory, every level downloaded to pinned host "
-                       "memory; level 0 downloads on a second stream while the pyramid is built"}
+                       "memory on a second stream: level 0 while the pyramid is built, every coarser level "
+                       "once its event (vx_build_lod_events) is recorded"}
 
     # ---- batched path vs per-instance plain calls (64 instances of uneven size) ------------
     batched = None
@@ -426,7 +431,9 @@ def main():
                    f"{WORKLOAD} [profiling variant: {args.fibers_per_ply} fibers per ply]", "prims": n_prims, "resolution": w.grid.resolution,
                    "K": K_LOBES, "n_samples": N_SAMPLES, "levels": len(level_sizes),
                    "voxels_per_level": level_sizes, "parallelism": f"replicas x{ws}",
-                   "l2": "flushed between timed steps (256 MiB write)"},
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "timing": "the timed steps carry a CUDA event pair around every library launch (the "
+                             "stage times and the roofline's launch durations); e2e runs without them"},
         "lod_ms": sum(v["ms_per_step"] for k, v in stages.items() if k.startswith(("lod", "sggx"))),
         "voxelize": voxelize,
         "stages": stages,

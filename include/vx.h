@@ -220,6 +220,16 @@ typedef struct {
 VX_API vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_lod_params* params,
                        void* stream, vx_level* out);
 
+/* vx_build_lod that also records events[l] (a cudaEvent_t created by the caller, passed as
+ * void*; entries l >= num_events or NULL are skipped) on `stream` once out[l] is complete,
+ * so that work on other streams (a download of that level) can start while the coarser
+ * levels are built.  A level is complete once its reduce and its SGGX-H clustering
+ * have run; later work only reads it.  The call returns when all work is enqueued.  Same
+ * arguments, results and errors as vx_build_lod; num_events < 0, or events == NULL with
+ * num_events > 0: VX_ERR_INVALID_ARG.  On an error the events' state is unspecified. */
+VX_API vx_status vx_build_lod_events(vx_context* ctx, const vx_level* in, const vx_lod_params* params,
+                              void* stream, vx_level* out, void* const* events, int num_events);
+
 /* Voxelization and the whole pyramid, window by window, for grids whose pyramid does
  * not fit in device memory at once (the paper processes the grid in blocks, Sec. 3.1-3.3).
  * The grid is cut into windows of 2^w voxels per side (w = window_log2, 1 <= w <= log2

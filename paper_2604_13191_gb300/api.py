@@ -69,7 +69,7 @@ EXPORTS = ["vx_context_create", "vx_context_destroy", "vx_voxelize", "vx_build_l
            "vx_profile_read", "vx_backward", "vx_backward_noalloc", "vx_batch_create", "vx_batch_run",
            "vx_batch_level", "vx_batch_destroy", "vx_set_max_pairs_per_pass", "vx_batch_create_lod",
            "vx_export_compact8", "vx_tessellate_catmull_rom", "vx_voxelize_sampled", "vx_export_leaves",
-           "vx_voxelize_lod_windowed", "vx_batch_query", "vx_selftest_bounded_wait"]
+           "vx_voxelize_lod_windowed", "vx_batch_query", "vx_selftest_bounded_wait", "vx_build_lod_events"]
 
 
 class VxInstance(C.Structure):
@@ -116,6 +116,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         lib.vx_voxelize.argtypes = [P, C.POINTER(VxPrimitives), C.POINTER(VxGrid), P, C.POINTER(VxLevel)]
         lib.vx_build_lod.restype = C.c_int
         lib.vx_build_lod.argtypes = [P, C.POINTER(VxLevel), C.POINTER(VxLodParams), P, C.POINTER(VxLevel)]
+        lib.vx_build_lod_events.restype = C.c_int
+        lib.vx_build_lod_events.argtypes = [P, C.POINTER(VxLevel), C.POINTER(VxLodParams), P, C.POINTER(VxLevel),
+                                            C.POINTER(C.c_void_p), C.c_int]
         lib.vx_level_release.restype = None
         lib.vx_level_release.argtypes = [P, C.POINTER(VxLevel), P]
         lib.vx_status_string.restype = C.c_char_p
@@ -511,9 +514,11 @@ class Context:
         return out
 
     def build_lod(self, level: Level, *, K: int = 1, dirs=None, num_levels: int = 0,
-                  merge: str = "pooled", stream=None) -> list:
+                  merge: str = "pooled", stream=None, events=None) -> list:
         """vx_build_lod: levels level+1 .. level+L (L = num_levels, 0 = down to 1^3).  merge:
-        "pooled" (the two lobes' pooled samples) or "mass" (their moments weighted by mass)."""
+        "pooled" (the two lobes' pooled samples) or "mass" (their moments weighted by mass).
+        events: torch.cuda.Event objects; events[l] is recorded on the stream once level
+        l of the result is complete (vx_build_lod_events)."""
         prm = VxLodParams()
         prm.num_levels = int(num_levels)
         prm.K = int(K)
@@ -526,7 +531,17 @@ class Context:
         R = level.resolution
         L = int(num_levels) if num_levels else int(R).bit_length() - 1
         outs = (VxLevel * max(L, 1))()
-        st = self.lib.vx_build_lod(self.h, C.byref(level._c), C.byref(prm), _stream(stream), outs)
+        if events is None:
+            st = self.lib.vx_build_lod(self.h, C.byref(level._c), C.byref(prm), _stream(stream), outs)
+        else:
+            handles = []
+            for ev in events:
+                if ev.cuda_event == 0:   # a torch event is created by its first record
+                    ev.record(torch.cuda.current_stream(self.device))
+                handles.append(ev.cuda_event)
+            arr = (C.c_void_p * max(len(handles), 1))(*handles)
+            st = self.lib.vx_build_lod_events(self.h, C.byref(level._c), C.byref(prm), _stream(stream), outs,
+                                              arr, len(handles))
         if st != 0:
             raise self._err(st, "vx_build_lod")
         return [self._wrap(outs[i]) for i in range(L)]

@@ -895,11 +895,25 @@ inline unsigned grid_for(size_t n, int threads) {
 
 namespace {
 vx_status build_levels(vx_context* ctx, const vx_level* in, const vx_lod_params* params, cudaStream_t s,
-                       vx_level* out, int L, const uint32_t* counts, uint32_t* misc);
+                       vx_level* out, int L, const uint32_t* counts, uint32_t* misc, void* const* events, int nev);
+vx_status build_lod(vx_context* ctx, const vx_level* in, const vx_lod_params* params, void* stream, vx_level* out,
+                    void* const* events, int nev);
 }  // namespace
 
 extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_lod_params* params, void* stream,
                                   vx_level* out) {
+    return build_lod(ctx, in, params, stream, out, nullptr, 0);
+}
+
+extern "C" vx_status vx_build_lod_events(vx_context* ctx, const vx_level* in, const vx_lod_params* params,
+                                         void* stream, vx_level* out, void* const* events, int num_events) {
+    if (num_events < 0 || (num_events > 0 && !events)) return VX_ERR_INVALID_ARG;
+    return build_lod(ctx, in, params, stream, out, events, num_events);
+}
+
+namespace {
+vx_status build_lod(vx_context* ctx, const vx_level* in, const vx_lod_params* params, void* stream, vx_level* out,
+                    void* const* events, int nev) {
     if (!ctx || !in || !params || !out) return VX_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     ctx->last_stream = s;
@@ -938,15 +952,19 @@ extern "C" vx_status vx_build_lod(vx_context* ctx, const vx_level* in, const vx_
         }
     }
     // an error past this point returns every level to the allocator (outputs unallocated)
-    const vx_status st = build_levels(ctx, in, params, s, out, L, counts, misc);
+    const vx_status st = build_levels(ctx, in, params, s, out, L, counts, misc, events, nev);
     if (st != VX_OK)
         for (int l = 0; l < L; ++l) vx_level_release(ctx, &out[l], s);
     return st;
 }
 
-namespace {
 vx_status build_levels(vx_context* ctx, const vx_level* in, const vx_lod_params* params, cudaStream_t s,
-                       vx_level* out, int L, const uint32_t* counts, uint32_t* misc) {
+                       vx_level* out, int L, const uint32_t* counts, uint32_t* misc, void* const* events, int nev) {
+    // the caller's event for out[l - 1], recorded once that level is complete
+    auto level_done = [&](int l) -> cudaError_t {
+        if (events && l - 1 < nev && events[l - 1]) return cudaEventRecord((cudaEvent_t)events[l - 1], s);
+        return cudaSuccess;
+    };
     const int K = params->K;
     const uint32_t n0 = (uint32_t)in->num_voxels;
     // ---- per level ------------------------------------------------------------------------
@@ -977,7 +995,10 @@ vx_status build_levels(vx_context* ctx, const vx_level* in, const vx_lod_params*
     for (int l = 1; l <= L; ++l) {
         const vx_level* prev = (l == 1) ? in : &out[l - 2];
         const uint32_t nprev = (uint32_t)prev->num_voxels, ncur = counts[l];
-        if (ncur == 0) continue;
+        if (ncur == 0) {
+            VX_CUDA_TRY(level_done(l));
+            continue;
+        }
         LevelIn li;
         li.keys = prev->keys; li.mask = prev->mask; li.mass = prev->mass; li.moment = prev->moment;
         li.lobe_count = prev->lobe_count; li.lobes = prev->lobes; li.K = prev->K;
@@ -999,6 +1020,7 @@ vx_status build_levels(vx_context* ctx, const vx_level* in, const vx_lod_params*
                                                               params->merge, s));
             VX_CUDA_TRY(cudaGetLastError());
         }
+        VX_CUDA_TRY(level_done(l));
     }
     return VX_OK;
 }

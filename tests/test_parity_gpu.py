@@ -669,3 +669,17 @@ def test_build_lod_while_level0_downloads(ctx, dirs5000):
             assert np.array_equal(np.asarray(g[f]).view(np.uint8), np.asarray(r[f]).view(np.uint8)), (l, f)
     prof_names = ctx.profile_read().keys()
     assert "readback" in prof_names
+    # the levels downloaded on the side stream, each after its completion event
+    evs = [torch.cuda.Event() for _ in ref]
+    lv = ctx.build_lod(L0, K=4, dirs=dirs, events=evs)
+    hosts = [torch.empty(x.block.numel(), dtype=torch.uint8).pin_memory() for x in lv]
+    with torch.cuda.stream(side):
+        for x, h, ev in zip(lv, hosts, evs):
+            side.wait_event(ev)
+            h.copy_(x.block, non_blocking=True)
+    torch.cuda.synchronize()
+    for l, (x, h, r) in enumerate(zip(lv, hosts, ref)):
+        assert torch.equal(h, x.block.cpu()), l
+        g = x.host()
+        for f in FIELDS:
+            assert np.array_equal(np.asarray(g[f]).view(np.uint8), np.asarray(r[f]).view(np.uint8)), (l, f)
