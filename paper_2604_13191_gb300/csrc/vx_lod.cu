@@ -35,8 +35,14 @@ struct LevelIn {
     int K;
 };
 
+// Parents per level l = 1..L (L < 32): a key starts a parent of level l when its bits above
+// 3 l differ from the previous key's.  Warps add their counts in shared memory, and each
+// block adds its totals to counts[] once per level.
 __global__ void k_level_counts(const uint64_t* __restrict__ keys, uint32_t n, int L, uint32_t* __restrict__ counts) {
+    __shared__ uint32_t blk[32];
     const int lane = threadIdx.x & 31;
+    for (int l = threadIdx.x; l < 32; l += blockDim.x) blk[l] = 0;
+    __syncthreads();
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         uint32_t i = base + threadIdx.x;
         uint64_t k = (i < n) ? keys[i] : 0ull;
@@ -44,9 +50,12 @@ __global__ void k_level_counts(const uint64_t* __restrict__ keys, uint32_t n, in
         for (int l = 1; l <= L; ++l) {
             bool head = (i < n) && (i == 0 || (k >> (3 * l)) != (kp >> (3 * l)));
             uint32_t b = __ballot_sync(0xffffffffu, head);
-            if (lane == 0 && b) atomicAdd(&counts[l], (uint32_t)__popc(b));
+            if (lane == 0 && b) atomicAdd(&blk[l], (uint32_t)__popc(b));
         }
     }
+    __syncthreads();
+    for (int l = 1 + threadIdx.x; l <= L; l += blockDim.x)
+        if (blk[l]) atomicAdd(&counts[l], blk[l]);
 }
 
 __global__ void k_parent_flags(const uint64_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ flags) {
