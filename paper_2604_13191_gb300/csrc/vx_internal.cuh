@@ -61,6 +61,11 @@ struct vx_context {
     vx::Buf ws[32];
     uint64_t* host_pin = nullptr; // pinned readback buffer (64 words), mapped
     uint64_t* host_pin_dev = nullptr;   // its device address
+    // hit ballots stored by the last candidate count pass: the buffer (NULL: none stored),
+    // its primitive count and window (lo xyz, hi xyz); an emit pass uses them only on a match
+    uint32_t* ballots = nullptr;
+    uint32_t ballots_np = 0;
+    int ballots_win[6] = {0, 0, 0, 0, 0, 0};
     // profiling
     bool prof = false;
     int64_t launches[ST_NSTAGES] = {0};
@@ -87,7 +92,7 @@ enum WsSlot {
     WS_REC_A = 0, WS_REC_B, WS_REC_C, WS_COUNT, WS_OFFS, WS_SCAN_TMP,
     WS_KEYS0, WS_VALS0, WS_KEYS1, WS_VALS1, WS_SORT_HIST,
     WS_FLAGS, WS_SEGIDX, WS_STARTS, WS_SEG_OUT, WS_MISC, WS_FIBER_START,
-    WS_LOD_FLAGS, WS_LOD_IDX, WS_LOD_STARTS, WS_LOD_WORK, WS_LOD_TMP, WS_LOD_STATS0, WS_LOD_STATS1,
+    WS_LOD_FLAGS, WS_LOD_IDX, WS_LOD_STARTS, WS_LOD_WORK, WS_LOD_TMP, WS_LOD_STATS0, WS_LOD_STATS1, WS_BALLOTS,
     WS_NSLOTS
 };
 static_assert(WS_NSLOTS <= 32, "workspace slot table");

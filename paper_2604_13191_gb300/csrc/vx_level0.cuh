@@ -706,10 +706,20 @@ __host__ __device__ inline Window full_window(int R) {
     for (int i = 0; i < 3; ++i) { w.lo[i] = 0; w.hi[i] = R - 1; }
     return w;
 }
-// (ix, iy, iz) of flat index idx < tot in a range (x fastest); 32-bit division when the
-// range holds fewer than 2^32 voxels (always inside a 1024^3 window)
+// (ix, iy, iz) of flat index idx < tot in a range (x fastest).  Ranges of at most 2^16
+// voxels divide by the correctly rounded FP32 reciprocal: (i + 0.5) fl(1/n), rounded, is
+// within i / n (1 + 2^-23) of the quotient plus 0.5 / n, so its integer part is floor(i / n)
+// (checked for every n and i below 2^16).  Larger ranges use 32-bit division when they hold
+// fewer than 2^32 voxels (always inside a 1024^3 window).
 __device__ __forceinline__ void voxel_of(long long idx, long long tot, const Range& rg, int& ix, int& iy, int& iz) {
-    if (tot <= 0xffffffffll) {
+    if (tot <= 65536) {
+        const float r0 = __frcp_rn((float)rg.n[0]), r1 = __frcp_rn((float)rg.n[1]);
+        const int i = (int)idx;
+        const int t = (int)(((float)i + 0.5f) * r0);
+        ix = i - t * rg.n[0];
+        iz = (int)(((float)t + 0.5f) * r1);
+        iy = t - iz * rg.n[1];
+    } else if (tot <= 0xffffffffll) {
         const uint32_t i = (uint32_t)idx, n0 = (uint32_t)rg.n[0], n1 = (uint32_t)rg.n[1];
         const uint32_t t = i / n0;
         ix = (int)(i - t * n0);
@@ -794,6 +804,12 @@ __device__ __forceinline__ bool tri_voxel_candidate(float4 a, float4 b, float4 c
 // ------------------------------------------------------------------------------------
 // count / emit: warp per primitive over its voxel range
 // ------------------------------------------------------------------------------------
+// With `ballots`, the count pass stores each primitive's hit ballots (one word per 32 voxels
+// of its range, ranges of at most 32 * CAND_BALLOTS voxels) and the emit pass of the same
+// window reads them instead of testing again; larger ranges are tested in both passes.
+// The ballots are the same bits either way, so the emitted order does not change.
+constexpr int CAND_BALLOTS = 8;
+
 template <bool FIBER, bool EMIT>
 __global__ void __launch_bounds__(EMIT_WARPS * 32) k_candidates(const float4* __restrict__ r0,
                                                                 const float4* __restrict__ r1,
@@ -801,7 +817,8 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_candidates(const float4* __
                                                                 uint32_t* __restrict__ counts,
                                                                 const uint32_t* __restrict__ offs,
                                                                 uint32_t* __restrict__ keys,
-                                                                uint32_t* __restrict__ vals) {
+                                                                uint32_t* __restrict__ vals,
+                                                                uint32_t* __restrict__ ballots = nullptr) {
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * EMIT_WARPS;
     for (uint32_t p = blockIdx.x * EMIT_WARPS + (threadIdx.x >> 5); p < np; p += warps) {
@@ -816,17 +833,34 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_candidates(const float4* __
         uint32_t n = 0;
         uint32_t base = EMIT ? offs[p] : 0u;
         const long long tot = rg.total;
+        const bool stored = ballots != nullptr && tot <= 32ll * CAND_BALLOTS;
+        uint32_t* const pb = stored ? ballots + (size_t)p * CAND_BALLOTS : nullptr;
+        // emit: the primitive's stored words, one per lane, broadcast per step below
+        uint32_t words = 0;
+        if (EMIT && stored && (long long)lane * 32 < tot) words = pb[lane];
         for (long long idx0 = 0; idx0 < tot; idx0 += 32) {
             long long idx = idx0 + lane;
             bool hit = false;
             int vi = 0, vj = 0, vk = 0;
-            if (idx < tot) {
-                int ix, iy, iz;
-                voxel_of(idx, tot, rg, ix, iy, iz);
-                vi = rg.lo[0] + ix; vj = rg.lo[1] + iy; vk = rg.lo[2] + iz;
-                hit = FIBER ? capsule_voxel_candidate(a, b, vi, vj, vk) : tri_voxel_candidate(a, b, c, vi, vj, vk);
+            uint32_t bal;
+            if (EMIT && stored) {
+                bal = __shfl_sync(0xffffffffu, words, (int)(idx0 >> 5));
+                hit = (bal >> lane) & 1u;
+                if (hit) {
+                    int ix, iy, iz;
+                    voxel_of(idx, tot, rg, ix, iy, iz);
+                    vi = rg.lo[0] + ix; vj = rg.lo[1] + iy; vk = rg.lo[2] + iz;
+                }
+            } else {
+                if (idx < tot) {
+                    int ix, iy, iz;
+                    voxel_of(idx, tot, rg, ix, iy, iz);
+                    vi = rg.lo[0] + ix; vj = rg.lo[1] + iy; vk = rg.lo[2] + iz;
+                    hit = FIBER ? capsule_voxel_candidate(a, b, vi, vj, vk) : tri_voxel_candidate(a, b, c, vi, vj, vk);
+                }
+                bal = __ballot_sync(0xffffffffu, hit);
+                if (!EMIT && stored && lane == 0) pb[idx0 >> 5] = bal;
             }
-            uint32_t bal = __ballot_sync(0xffffffffu, hit);
             if (EMIT && hit) {
                 uint32_t pos = base + n + __popc(bal & ((1u << lane) - 1u));
                 keys[pos] = vx_morton3((uint32_t)(vi - R.lo[0]), (uint32_t)(vj - R.lo[1]), (uint32_t)(vk - R.lo[2]));

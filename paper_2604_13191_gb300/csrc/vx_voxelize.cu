@@ -38,21 +38,38 @@ __global__ void k_sum_u64(const uint32_t* __restrict__ cnt, uint32_t n, unsigned
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
 }
 
-// Candidate counts and offsets of the primitives over one window (WS_COUNT, WS_OFFS); the
-// exact total goes to *total.  Synchronises the stream once.
+// The count pass's ballot store (WS_BALLOTS, CAND_BALLOTS words per primitive), or NULL when
+// it would take more than 256 MB (the emit pass then tests every voxel again).
+uint32_t* window_ballots(vx_context* ctx, uint32_t np, cudaStream_t s) {
+    const size_t bytes = (size_t)np * CAND_BALLOTS * 4;
+    if (bytes > ((size_t)256 << 20)) return nullptr;
+    if (vx_ws_ensure(ctx, WS_BALLOTS, bytes, s) != VX_OK) return nullptr;
+    return (uint32_t*)ctx->ws[WS_BALLOTS].p;
+}
+
+// Candidate counts and offsets of the primitives over one window (WS_COUNT, WS_OFFS), and
+// the hit ballots of their ranges (WS_BALLOTS, see window_ballots); the exact total goes to
+// *total.  Synchronises the stream once.
 vx_status count_window(vx_context* ctx, bool fiber, uint32_t np, const Window& win, float4* r0, float4* r1,
                        float4* r2, uint32_t* misc, cudaStream_t s, uint64_t* total) {
     VX_TRY(vx_ws_ensure(ctx, WS_COUNT, (size_t)np * 4, s));
     VX_TRY(vx_ws_ensure(ctx, WS_OFFS, (size_t)np * 4, s));
     uint32_t* cnt = (uint32_t*)ctx->ws[WS_COUNT].p;
     uint32_t* offs = (uint32_t*)ctx->ws[WS_OFFS].p;
+    uint32_t* ballots = window_ballots(ctx, np, s);
+    ctx->ballots = ballots;
+    ctx->ballots_np = np;
+    for (int i = 0; i < 3; ++i) {
+        ctx->ballots_win[i] = win.lo[i];
+        ctx->ballots_win[3 + i] = win.hi[i];
+    }
     const unsigned cblocks = (unsigned)std::min<size_t>((np + EMIT_WARPS - 1) / EMIT_WARPS, (size_t)vx::kSMs * 64);
     if (fiber)
         VX_LAUNCH(ctx, ST_COUNT, s, k_candidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                        r0, r1, r2, np, win, cnt, nullptr, nullptr, nullptr));
+                                        r0, r1, r2, np, win, cnt, nullptr, nullptr, nullptr, ballots));
     else
         VX_LAUNCH(ctx, ST_COUNT, s, k_candidates<false, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                        r0, r1, r2, np, win, cnt, nullptr, nullptr, nullptr));
+                                        r0, r1, r2, np, win, cnt, nullptr, nullptr, nullptr, ballots));
     VX_TRY(vx_scan_u32(ctx, cnt, offs, np, misc + 1, s));
     unsigned long long* t64 = (unsigned long long*)(misc + 8);
     VX_CUDA_TRY(cudaMemsetAsync(t64, 0, 8, s));
@@ -104,12 +121,17 @@ vx_status window_segments(vx_context* ctx, bool fiber, uint32_t np, const Window
     *v0 = (uint32_t*)ctx->ws[WS_VALS0].p;
     *k1 = (uint32_t*)ctx->ws[WS_KEYS1].p;
     *v1 = (uint32_t*)ctx->ws[WS_VALS1].p;
+    // the ballots the count pass of this window stored, if it stored any
+    bool same = ctx->ballots != nullptr && ctx->ballots_np == np;
+    for (int i = 0; i < 3; ++i)
+        same = same && ctx->ballots_win[i] == win.lo[i] && ctx->ballots_win[3 + i] == win.hi[i];
+    uint32_t* ballots = same ? ctx->ballots : nullptr;
     if (fiber)
         VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                       r0, r1, r2, np, win, nullptr, offs, *k0, *v0));
+                                       r0, r1, r2, np, win, nullptr, offs, *k0, *v0, ballots));
     else
         VX_LAUNCH(ctx, ST_EMIT, s, k_candidates<false, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(
-                                       r0, r1, r2, np, win, nullptr, offs, *k0, *v0));
+                                       r0, r1, r2, np, win, nullptr, offs, *k0, *v0, ballots));
     VX_CUDA_TRY(cudaGetLastError());
     VX_TRY(vx_radix_sort_u32(ctx, k0, v0, k1, v1, npairs, 3 * bits, s, misc));
     VX_TRY(vx_ws_ensure(ctx, WS_FLAGS, (size_t)npairs * 4, s));
