@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_bcandidates(const float4* _
                                                                  const uint8_t* __restrict__ inst_of,
                                                                  uint32_t* __restrict__ counts,
                                                                  const uint32_t* __restrict__ offs, uint32_t cap,
-                                                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                                                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                                 uint32_t* __restrict__ ballots) {
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * EMIT_WARPS;
     for (uint32_t p = blockIdx.x * EMIT_WARPS + (threadIdx.x >> 5); p < np; p += warps) {
@@ -117,17 +118,34 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_bcandidates(const float4* _
         uint32_t n = 0;
         const uint32_t base = EMIT ? offs[p] : 0u;
         const long long tot = rg.total;
+        // hit ballots stored by the count pass for the emit pass (as k_candidates)
+        const bool stored = ballots != nullptr && tot <= 32ll * CAND_BALLOTS;
+        uint32_t* const pb = stored ? ballots + (size_t)p * CAND_BALLOTS : nullptr;
+        uint32_t words = 0;
+        if (EMIT && stored && (long long)lane * 32 < tot) words = pb[lane];
         for (long long idx0 = 0; idx0 < tot; idx0 += 32) {
             const long long idx = idx0 + lane;
             bool hit = false;
             int vi = 0, vj = 0, vk = 0;
-            if (idx < tot) {
-                int ix, iy, iz;
-                voxel_of(idx, tot, rg, ix, iy, iz);
-                vi = rg.lo[0] + ix; vj = rg.lo[1] + iy; vk = rg.lo[2] + iz;
-                hit = FIBER ? capsule_voxel_candidate(a, b, vi, vj, vk) : tri_voxel_candidate(a, b, c, vi, vj, vk);
+            uint32_t bal;
+            if (EMIT && stored) {
+                bal = __shfl_sync(0xffffffffu, words, (int)(idx0 >> 5));
+                hit = (bal >> lane) & 1u;
+                if (hit) {
+                    int ix, iy, iz;
+                    voxel_of(idx, tot, rg, ix, iy, iz);
+                    vi = rg.lo[0] + ix; vj = rg.lo[1] + iy; vk = rg.lo[2] + iz;
+                }
+            } else {
+                if (idx < tot) {
+                    int ix, iy, iz;
+                    voxel_of(idx, tot, rg, ix, iy, iz);
+                    vi = rg.lo[0] + ix; vj = rg.lo[1] + iy; vk = rg.lo[2] + iz;
+                    hit = FIBER ? capsule_voxel_candidate(a, b, vi, vj, vk) : tri_voxel_candidate(a, b, c, vi, vj, vk);
+                }
+                bal = __ballot_sync(0xffffffffu, hit);
+                if (!EMIT && stored && lane == 0) pb[idx0 >> 5] = bal;
             }
-            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
             if (EMIT && hit) {
                 const uint32_t pos = base + n + __popc(bal & ((1u << lane) - 1u));
                 if (pos < cap) {
@@ -298,6 +316,7 @@ struct SubBatch {
     uint8_t* inst_of = nullptr;
     float4 *r0 = nullptr, *r1 = nullptr, *r2 = nullptr;
     uint32_t *cnt = nullptr, *offs = nullptr, *fs = nullptr;
+    uint32_t* ballots = nullptr;            // the count pass's hit ballots (NULL: emit tests again)
     uint32_t* part = nullptr;
     uint32_t* counters = nullptr;           // 64 words
     uint32_t* inst_start = nullptr;         // [(Lmax + 1)][ninst + 1]
@@ -458,10 +477,10 @@ vx_status instance_pairs(vx_batch* b, bool fiber, const vx_primitives* prims, co
         if (e == cudaSuccess) {
             if (fiber)
                 k_bcandidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, r2, np, dinst, inst_of, cnt,
-                                                                               nullptr, 0, nullptr, nullptr);
+                                                                               nullptr, 0, nullptr, nullptr, nullptr);
             else
                 k_bcandidates<false, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(r0, r1, r2, np, dinst, inst_of, cnt,
-                                                                                nullptr, 0, nullptr, nullptr);
+                                                                                nullptr, 0, nullptr, nullptr, nullptr);
             k_inst_pair_totals<<<ninst, 256, 0, s>>>(cnt, dinst, tot);
             e = cudaGetLastError();
         }
@@ -518,10 +537,10 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
     const unsigned cblocks = (unsigned)std::min<size_t>((S.np + EMIT_WARPS - 1) / EMIT_WARPS, (size_t)vx::kSMs * 64);
     if (S.fiber)
         k_bcandidates<true, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(S.r0, S.r1, S.r2, S.np, S.dinst, S.inst_of,
-                                                                       S.cnt, nullptr, 0, nullptr, nullptr);
+                                                                       S.cnt, nullptr, 0, nullptr, nullptr, S.ballots);
     else
         k_bcandidates<false, false><<<cblocks, EMIT_WARPS * 32, 0, s>>>(S.r0, S.r1, S.r2, S.np, S.dinst, S.inst_of,
-                                                                        S.cnt, nullptr, 0, nullptr, nullptr);
+                                                                        S.cnt, nullptr, 0, nullptr, nullptr, S.ballots);
     if (vx_scan_u32_scratch(S.cnt, S.offs, S.np, C + C_PAIRS_TOT, S.part, s) != cudaSuccess) return VX_ERR_CUDA;
     *nl += 4;
     if (plan) {
@@ -541,10 +560,12 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
     k_clamp<<<1, 1, 0, s>>>(C + C_PAIRS_TOT, S.cap_pairs, C + C_PAIRS, C + C_ERR);
     if (S.fiber)
         k_bcandidates<true, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(S.r0, S.r1, S.r2, S.np, S.dinst, S.inst_of,
-                                                                      nullptr, S.offs, S.cap_pairs, PL.k0, PL.v0);
+                                                                      nullptr, S.offs, S.cap_pairs, PL.k0, PL.v0,
+                                                                      S.ballots);
     else
         k_bcandidates<false, true><<<cblocks, EMIT_WARPS * 32, 0, s>>>(S.r0, S.r1, S.r2, S.np, S.dinst, S.inst_of,
-                                                                       nullptr, S.offs, S.cap_pairs, PL.k0, PL.v0);
+                                                                       nullptr, S.offs, S.cap_pairs, PL.k0, PL.v0,
+                                                                       S.ballots);
     k_pad<<<blk, 256, 0, s>>>(PL.k0, PL.v0, C + C_PAIRS, S.cap_pairs);
     *nl += 3;
     // ---- sort by (instance, key) ------------------------------------------------------------
@@ -818,6 +839,10 @@ extern "C" vx_status vx_batch_create_lod(vx_context* ctx, const vx_primitives* t
             if (!S.fiber && (st = balloc(b, (void**)&S.r2, (size_t)S.np * 16, s)) != VX_OK) return fail(st);
             if ((st = balloc(b, (void**)&S.cnt, (size_t)S.np * 4, s)) != VX_OK) return fail(st);
             if ((st = balloc(b, (void**)&S.offs, (size_t)S.np * 4, s)) != VX_OK) return fail(st);
+            // ballots for the emit pass, when they take at most 2 GB
+            if ((size_t)S.np * CAND_BALLOTS * 4 <= ((size_t)2 << 30) &&
+                (st = balloc(b, (void**)&S.ballots, (size_t)S.np * CAND_BALLOTS * 4, s)) != VX_OK)
+                return fail(st);
             if ((st = balloc(b, (void**)&S.fs, (size_t)(S.fiber ? S.F : 1) * 4 + 16, s)) != VX_OK) return fail(st);
             if ((st = balloc(b, (void**)&S.counters, 64 * 4, s)) != VX_OK) return fail(st);
             if ((st = balloc(b, (void**)&S.inst_start, (size_t)(kMaxLevels + 1) * (S.ninst + 1) * 4, s)) != VX_OK)
