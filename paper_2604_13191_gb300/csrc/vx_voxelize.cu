@@ -38,13 +38,16 @@ __global__ void k_sum_u64(const uint32_t* __restrict__ cnt, uint32_t n, unsigned
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
 }
 
-// The count pass's ballot store (WS_BALLOTS, CAND_BALLOTS words per primitive), or NULL when
-// it would take more than 256 MB (the emit pass then tests every voxel again).
-uint32_t* window_ballots(vx_context* ctx, uint32_t np, cudaStream_t s) {
+// The count pass's ballot store (WS_BALLOTS, CAND_BALLOTS words per primitive) in *out, or
+// NULL when it would take more than 256 MB (the emit pass then tests every voxel again).
+// Errors: VX_ERR_OUT_OF_MEMORY, as for any workspace.
+vx_status window_ballots(vx_context* ctx, uint32_t np, cudaStream_t s, uint32_t** out) {
+    *out = nullptr;
     const size_t bytes = (size_t)np * CAND_BALLOTS * 4;
-    if (bytes > ((size_t)256 << 20)) return nullptr;
-    if (vx_ws_ensure(ctx, WS_BALLOTS, bytes, s) != VX_OK) return nullptr;
-    return (uint32_t*)ctx->ws[WS_BALLOTS].p;
+    if (bytes > ((size_t)256 << 20)) return VX_OK;
+    VX_TRY(vx_ws_ensure(ctx, WS_BALLOTS, bytes, s));
+    *out = (uint32_t*)ctx->ws[WS_BALLOTS].p;
+    return VX_OK;
 }
 
 // Candidate counts and offsets of the primitives over one window (WS_COUNT, WS_OFFS), and
@@ -56,7 +59,9 @@ vx_status count_window(vx_context* ctx, bool fiber, uint32_t np, const Window& w
     VX_TRY(vx_ws_ensure(ctx, WS_OFFS, (size_t)np * 4, s));
     uint32_t* cnt = (uint32_t*)ctx->ws[WS_COUNT].p;
     uint32_t* offs = (uint32_t*)ctx->ws[WS_OFFS].p;
-    uint32_t* ballots = window_ballots(ctx, np, s);
+    ctx->ballots = nullptr;
+    uint32_t* ballots = nullptr;
+    VX_TRY(window_ballots(ctx, np, s, &ballots));
     ctx->ballots = ballots;
     ctx->ballots_np = np;
     for (int i = 0; i < 3; ++i) {

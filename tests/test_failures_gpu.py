@@ -108,3 +108,28 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable():
     for k in ("keys", "mask", "mass", "moment"):
         assert np.array_equal(got[k], ref[k])
     ctx.close()
+
+
+def test_build_lod_events_rejects_bad_event_arguments():
+    """vx_build_lod_events checks its event arguments before any work: a negative count, or
+    no array for a positive count, is VX_ERR_INVALID_ARG with nothing allocated; an empty
+    list of events gives the result of vx_build_lod."""
+    ctx = vx.Context(DEV)
+    w = synth.config2(fibers_per_ply=2, segments=200, R=64, K=1)
+    L0 = ctx.voxelize(w.grid, ctrl=torch.from_numpy(w.ctrl).to(DEV),
+                      fiber_offsets=torch.from_numpy(w.fiber_offsets).to(DEV))
+    prm = api.VxLodParams()
+    prm.num_levels, prm.K, prm.n_samples, prm.merge = 0, 1, 0, 0
+    outs = (api.VxLevel * 8)()
+    live = len(ctx.alloc.live)
+    for arr, n in ((None, 2), (None, -1), ((C.c_void_p * 1)(), -3)):
+        st = ctx.lib.vx_build_lod_events(ctx.h, C.byref(L0._c), C.byref(prm), api._stream(None), outs, arr, n)
+        assert st == 1, (n, st)
+    assert len(ctx.alloc.live) == live
+    ref = [p.host() for p in ctx.build_lod(L0, K=1)]
+    got = [p.host() for p in ctx.build_lod(L0, K=1, events=[])]
+    assert len(ref) == len(got)
+    for a, b in zip(ref, got):
+        for k in ("keys", "mask", "mass", "moment", "occ", "proj", "lobe_count", "lobes"):
+            assert np.array_equal(a[k], b[k]), k
+    ctx.close()
