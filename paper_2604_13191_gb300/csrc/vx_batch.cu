@@ -527,7 +527,8 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
         k_bprep_fibers<<<gf(S.np, 256, 1u << 30), 256, 0, s>>>((const float4*)S.ctrl, S.num_ctrl, S.off, S.fs, S.F, S.weights,
                                                                S.np, S.dinst, S.ninst, S.r0, S.r1, S.inst_of,
                                                                C + C_ERR);
-        *nl += 5;
+        k_tangent_terms<<<gf(S.np, 256, 1u << 30), 256, 0, s>>>(S.r0, S.r1, S.np, S.r2);
+        *nl += 6;
     } else {
         k_bprep_tris<<<gf(S.np, 256, 1u << 30), 256, 0, s>>>((const float4*)S.tri, S.weights, S.np, S.dinst,
                                                              S.ninst, S.r0, S.r1, S.r2, S.inst_of, C + C_ERR);
@@ -596,7 +597,7 @@ vx_status enqueue(vx_batch* b, SubBatch& S, cudaStream_t s, bool plan, int64_t* 
             (unsigned)std::min<size_t>((S.cap_seg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * bpsm);
         if (S.fiber)
             k_reduce_fibers<<<std::max(rblocks, 1u), RED_WARPS * 32, 0, s>>>(k0, v0, PL.starts, C + C_SEG, S.r0, S.r1,
-                                                                              seg, 0, 0, 0, C + C_TAKE);
+                                                                              S.r2, seg, 0, 0, 0, C + C_TAKE);
         else
             k_reduce_tris<<<std::max(rblocks, 1u), RED_WARPS * 32, 0, s>>>(k0, v0, PL.starts, C + C_SEG, S.r0, S.r1,
                                                                             S.r2, seg, 0, 0, 0, C + C_TAKE);
@@ -836,7 +837,8 @@ extern "C" vx_status vx_batch_create_lod(vx_context* ctx, const vx_primitives* t
             if ((st = balloc(b, (void**)&S.inst_of, (size_t)S.np + 16, s)) != VX_OK) return fail(st);
             if ((st = balloc(b, (void**)&S.r0, (size_t)S.np * 16, s)) != VX_OK) return fail(st);
             if ((st = balloc(b, (void**)&S.r1, (size_t)S.np * 16, s)) != VX_OK) return fail(st);
-            if (!S.fiber && (st = balloc(b, (void**)&S.r2, (size_t)S.np * 16, s)) != VX_OK) return fail(st);
+            // triangles: the third vertex records; fibers: the tangent terms (two float4 each)
+            if ((st = balloc(b, (void**)&S.r2, (size_t)S.np * (S.fiber ? 32 : 16), s)) != VX_OK) return fail(st);
             if ((st = balloc(b, (void**)&S.cnt, (size_t)S.np * 4, s)) != VX_OK) return fail(st);
             if ((st = balloc(b, (void**)&S.offs, (size_t)S.np * 4, s)) != VX_OK) return fail(st);
             // ballots for the emit pass, when they take at most 2 GB

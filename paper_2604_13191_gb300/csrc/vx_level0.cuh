@@ -673,6 +673,23 @@ __global__ void k_prep_fibers(const float4* __restrict__ ctrl, int64_t num_ctrl,
     rb[p] = B;
 }
 
+// The tangent terms of each capsule's moment, T = (t_x^2, t_y^2, t_z^2, t_x t_y, t_x t_z,
+// t_y t_z) with t = (B - A) / |B - A| (zero for a degenerate segment), as two float4 per
+// primitive (the last two lanes zero).  These are the operations the reduce applied to every
+// candidate pair; they depend on the primitive only, so they run once per primitive.
+__global__ void k_tangent_terms(const float4* __restrict__ ra, const float4* __restrict__ rb, uint32_t np,
+                                float4* __restrict__ rt) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const float4 A = ra[p], B = rb[p];
+    const float dg[3] = {B.x - A.x, B.y - A.y, B.z - A.z};
+    const float dn = sqrtf((dg[0] * dg[0] + dg[1] * dg[1]) + dg[2] * dg[2]);
+    float t[3] = {0.0f, 0.0f, 0.0f};
+    if (dn > 0.0f) { t[0] = dg[0] / dn; t[1] = dg[1] / dn; t[2] = dg[2] / dn; }
+    rt[2 * (size_t)p] = make_float4(t[0] * t[0], t[1] * t[1], t[2] * t[2], t[0] * t[1]);
+    rt[2 * (size_t)p + 1] = make_float4(t[0] * t[2], t[1] * t[2], 0.0f, 0.0f);
+}
+
 // tri records: (U0, w), (U1, 0), (U2, 0)
 __global__ void k_prep_tris(const float4* __restrict__ tv, const float* __restrict__ weights, uint32_t np, GridDev g,
                             float4* __restrict__ r0, float4* __restrict__ r1, float4* __restrict__ r2,
@@ -902,7 +919,8 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                                                                   const uint32_t* __restrict__ starts,
                                                                   const uint32_t* __restrict__ nseg_p,
                                                                   const float4* __restrict__ ra,
-                                                                  const float4* __restrict__ rb, SegOut out,
+                                                                  const float4* __restrict__ rb,
+                                                                  const float4* __restrict__ rt, SegOut out,
                                                                   int bx, int by, int bz,
                                                                   uint32_t* __restrict__ next) {
     const int lane = threadIdx.x & 31;
@@ -958,18 +976,16 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                     okey = (min(bits, 0xffffffbfu) & 0xffffffe0u) | (uint32_t)lane;   // below the empty lanes
                 }
                 float mu = capsule_measure(a, b, A.w);
-                float dg[3] = {B.x - A.x, B.y - A.y, B.z - A.z};
-                float dn = sqrtf((dg[0] * dg[0] + dg[1] * dg[1]) + dg[2] * dg[2]);
-                float t[3] = {0.0f, 0.0f, 0.0f};
-                if (dn > 0.0f) { t[0] = dg[0] / dn; t[1] = dg[1] / dn; t[2] = dg[2] / dn; }
+                // w mu and w mu T(t), T the primitive's tangent terms (k_tangent_terms)
+                const float4 T0 = rt[2 * (size_t)p], T1 = rt[2 * (size_t)p + 1];
                 float c = B.w * mu;
                 q[0] = c;
-                q[1] = c * (t[0] * t[0]);
-                q[2] = c * (t[1] * t[1]);
-                q[3] = c * (t[2] * t[2]);
-                q[4] = c * (t[0] * t[1]);
-                q[5] = c * (t[0] * t[2]);
-                q[6] = c * (t[1] * t[2]);
+                q[1] = c * T0.x;
+                q[2] = c * T0.y;
+                q[3] = c * T0.z;
+                q[4] = c * T0.w;
+                q[5] = c * T1.x;
+                q[6] = c * T1.y;
 #pragma unroll
                 for (int c = 0; c < 7; ++c) ct.q[lane * 7 + c] = q[c];
             }

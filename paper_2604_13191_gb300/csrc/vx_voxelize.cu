@@ -179,7 +179,7 @@ vx_status window_reduce(vx_context* ctx, bool fiber, uint32_t np, uint32_t nseg,
         // resident blocks (7 per SM) taking voxels from a counter
         const unsigned fblocks = (unsigned)std::min<size_t>((nseg + RED_WARPS - 1) / RED_WARPS, (size_t)vx::kSMs * 7);
         VX_LAUNCH(ctx, ST_REDUCE_FIBERS, s, k_reduce_fibers<<<fblocks, RED_WARPS * 32, 0, s>>>(
-                                                k0, v0, starts, misc + 2, r0, r1, seg, bx, by, bz, misc + 6));
+                                                k0, v0, starts, misc + 2, r0, r1, r2, seg, bx, by, bz, misc + 6));
     } else {
         VX_LAUNCH(ctx, ST_REDUCE_TRIS, s, k_reduce_tris<<<rblocks, RED_WARPS * 32, 0, s>>>(
                                               k0, v0, starts, misc + 2, r0, r1, r2, seg, bx, by, bz, misc + 6));
@@ -226,7 +226,7 @@ struct Prepared {
     uint32_t np;
     int bits_R;
     int R;
-    float4 *r0, *r1, *r2;
+    float4 *r0, *r1, *r2;   // r2: triangles' third records, fibers' tangent terms
     uint32_t* misc;
 };
 
@@ -260,13 +260,14 @@ vx_status prepare(vx_context* ctx, const vx_primitives* prims, const vx_grid* gr
     g.R = (int)R;
     VX_TRY(vx_ws_ensure(ctx, WS_REC_A, (size_t)np * 16, s));
     VX_TRY(vx_ws_ensure(ctx, WS_REC_B, (size_t)np * 16, s));
-    if (!fiber) VX_TRY(vx_ws_ensure(ctx, WS_REC_C, (size_t)np * 16, s));
+    // triangles: the third vertex records; fibers: the tangent terms (two float4 each)
+    VX_TRY(vx_ws_ensure(ctx, WS_REC_C, (size_t)np * (fiber ? 32 : 16), s));
     VX_TRY(vx_ws_ensure(ctx, WS_MISC, 256, s));
     uint32_t* misc = (uint32_t*)ctx->ws[WS_MISC].p;   // [0] err, [1] npairs, [2] nseg, [3] nvox, [4] segtotal
     VX_CUDA_TRY(cudaMemsetAsync(misc, 0, 64, s));
     float4* r0 = (float4*)ctx->ws[WS_REC_A].p;
     float4* r1 = (float4*)ctx->ws[WS_REC_B].p;
-    float4* r2 = fiber ? nullptr : (float4*)ctx->ws[WS_REC_C].p;
+    float4* r2 = (float4*)ctx->ws[WS_REC_C].p;
     if (fiber) {
         const int64_t F = prims->num_fibers;
         if (F > 0x7fffffff) return VX_ERR_CAPACITY;
@@ -276,6 +277,7 @@ vx_status prepare(vx_context* ctx, const vx_primitives* prims, const vx_grid* gr
         VX_TRY(vx_scan_u32(ctx, fs, fs, (uint32_t)F, misc + 4, s));
         VX_LAUNCH(ctx, ST_PREP, s, k_prep_fibers<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->ctrl, prims->num_ctrl, prims->fiber_offsets, fs, F,
                                                          misc + 4, prims->weights, np, g, r0, r1, misc));
+        VX_LAUNCH(ctx, ST_PREP, s, k_tangent_terms<<<grid_for(np, 256), 256, 0, s>>>(r0, r1, np, r2));
     } else {
         VX_LAUNCH(ctx, ST_PREP, s, k_prep_tris<<<grid_for(np, 256), 256, 0, s>>>((const float4*)prims->tri_verts, prims->weights, np, g, r0,
                                                        r1, r2, misc));
