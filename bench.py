@@ -512,6 +512,12 @@ def batched_vs_plain(ctx, dev, steps, dirs):
 
     tb = timed(run_batch, steps)
     tp = timed(run_plain, steps)
+    # kernels per replay: the kernel nodes of the captured graph (the library's launch count)
+    ctx.profile(True)
+    b.run()
+    torch.cuda.synchronize()
+    graph_kernels = ctx.profile_read().get("batched_graph", (0, 0.0, 0))[0]
+    ctx.profile(False)
     b.close()
     for k in plan.values():
         k.pop("cluster_ms", None)
@@ -519,7 +525,7 @@ def batched_vs_plain(ctx, dev, steps, dirs):
             "triangles": int(sum(w.num_prims for w in ws if w.kind == "triangles")),
             "segments": int(sum(w.num_prims for w in ws if w.kind == "fibers")),
             "batched_ms": tb, "plain_ms": tp, "speedup": tp / tb, "batched_prims_per_s": nprims / (tb * 1e-3),
-            "plan_s": plan_s, "plan": plan,
+            "plan_s": plan_s, "plan": plan, "graph_kernels": int(graph_kernels),
             "note": "batched = one captured graph per run (groups of instances whose pairs fit one pass, run in "
                     "sequence per kind, the two kinds on two branches); plain = per-instance vx_voxelize + "
                     "vx_build_lod; plan_s includes the autotuner's timing runs"}
