@@ -398,6 +398,13 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_radix_scatter_pipe(const ui
     if (blockIdx.x < nt && bulk_ok(blockIdx.x)) pending |= 1u;
     bool lost = false;
     int st = 0;
+    // this thread's digits' global offsets for the tile in hand, loaded one tile ahead (the
+    // digit-major histogram puts a tile's offsets a stride nt apart)
+    constexpr int DPG = RB / SORT_THREADS;
+    uint32_t gcur[DPG];
+#pragma unroll
+    for (int i = 0; i < DPG; ++i)
+        gcur[i] = blockIdx.x < nt ? hist[(size_t)(threadIdx.x + i * SORT_THREADS) * nt + blockIdx.x] : 0u;
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x, st ^= 1) {
         // the next tile streams into the other stage (its last reader finished: the loop ends
         // with a barrier); generic writes to that stage are ordered before the async copy
@@ -409,6 +416,10 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_radix_scatter_pipe(const ui
             }
             pending |= 1u << (st ^ 1);
         }
+        uint32_t gnxt[DPG];
+#pragma unroll
+        for (int i = 0; i < DPG; ++i)
+            gnxt[i] = tn < nt ? hist[(size_t)(threadIdx.x + i * SORT_THREADS) * nt + tn] : 0u;
         const size_t tile0 = (size_t)t * SORT_TILE;
         const uint32_t tn_items = (uint32_t)min((size_t)SORT_TILE, (size_t)n - tile0);
         uint32_t* const sk = stage0 + (size_t)st * 2 * SORT_TILE;
@@ -428,7 +439,8 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_radix_scatter_pipe(const ui
             }
         }
         for (int i = threadIdx.x; i < SORT_WARPS * RB; i += SORT_THREADS) (&wcnt[0][0])[i] = 0;
-        for (int d = threadIdx.x; d < RB; d += SORT_THREADS) gofs[d] = hist[(size_t)d * nt + t];
+#pragma unroll
+        for (int i = 0; i < DPG; ++i) gofs[threadIdx.x + i * SORT_THREADS] = gcur[i];
         // the whole block leaves together when any thread's wait gave up
         if (__syncthreads_or(gave_up)) {
             lost = true;
@@ -497,6 +509,8 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_radix_scatter_pipe(const ui
             okeys[pos] = kk;
             ovals[pos] = vv;
         }
+#pragma unroll
+        for (int i = 0; i < DPG; ++i) gcur[i] = gnxt[i];
         __syncthreads();
     }
     if (lost) {
