@@ -914,6 +914,107 @@ __device__ __forceinline__ void write_seg7(SegOut out, uint32_t seg, uint32_t ke
     }
 }
 
+// Batch slot `lane` of a voxel at (fx, fy, fz): capsule p's local record, the x terms of its
+// steps 1-2 and its w mu, w mu T(t) moment terms, in the warp's shared state.  Returns the
+// key that orders the mask tests: capsules whose axis passes deepest into the voxel first
+// (they set the most bits, so later capsules find more lanes already full).  The mask is an
+// OR, so the order does not change it.
+__device__ __forceinline__ uint32_t capsule_slot_setup(CapsuleTasks& ct, int lane, uint32_t p, float fx, float fy,
+                                                       float fz, const float4* __restrict__ ra,
+                                                       const float4* __restrict__ rb,
+                                                       const float4* __restrict__ rt) {
+    const float4 A = ra[p], B = rb[p];
+    float a[3] = {A.x - fx, A.y - fy, A.z - fz};
+    float b[3] = {B.x - fx, B.y - fy, B.z - fz};
+    const CapsuleLocal cl = capsule_local(a, b, A.w);
+    ct.batch[lane] = cl;
+    ct.xt[lane] = capsule_x(a[0], b[0]);
+    uint32_t okey;
+    {
+        // squared distance from the voxel centre to the axis, minus r^2 (an ordering key only:
+        // any rounding of it leaves the outputs unchanged)
+        const float e[3] = {cl.d_idd.x, cl.d_idd.y, cl.d_idd.z};
+        const float w[3] = {0.5f - a[0], 0.5f - a[1], 0.5f - a[2]};
+        float tt = ((w[0] * e[0] + w[1] * e[1]) + w[2] * e[2]) * cl.d_idd.w;
+        tt = fminf(fmaxf(tt, 0.0f), 1.0f);
+        const float dx = w[0] - tt * e[0], dy = w[1] - tt * e[1], dz = w[2] - tt * e[2];
+        const float v = ((dx * dx + dy * dy) + dz * dz) - A.w * A.w;
+        uint32_t bits = __float_as_uint(v);
+        bits ^= (bits >> 31) ? 0xffffffffu : 0x80000000u;   // order-preserving as unsigned
+        okey = (min(bits, 0xffffffbfu) & 0xffffffe0u) | (uint32_t)lane;   // below the empty lanes
+    }
+    const float mu = capsule_measure(a, b, A.w);
+    // w mu and w mu T(t), T the primitive's tangent terms (k_tangent_terms)
+    const float4 T0 = rt[2 * (size_t)p], T1 = rt[2 * (size_t)p + 1];
+    const float c = B.w * mu;
+    float* q = ct.q + lane * 7;
+    q[0] = c;
+    q[1] = c * T0.x;
+    q[2] = c * T0.y;
+    q[3] = c * T0.z;
+    q[4] = c * T0.w;
+    q[5] = c * T1.x;
+    q[6] = c * T1.y;
+    return okey;
+}
+
+// Steps 1-3 of the `cnt` capsules of one voxel whose ordering keys sit at lanes src0,
+// src0 + dir, ... of `okey` (the batch slot is a key's low 5 bits), on top of the lane's
+// 16-bit chunk of the mask.  The pooled step-3 tasks refer to this batch's slots, so they
+// are evaluated before the function returns.
+__device__ __forceinline__ uint32_t voxel_mask(CapsuleTasks& ct, uint32_t okey, uint32_t cnt, int src0, int dir,
+                                               int sy0, int sz, uint32_t chunk, bool& full) {
+    const int lane = threadIdx.x & 31;
+    int ntask = 0;
+    for (uint32_t j = 0; j < cnt; ++j) {
+        if (full) break;
+        const int slot = (int)(__shfl_sync(0xffffffffu, okey, src0 + dir * (int)j) & 31u);
+        uint32_t und;
+        chunk = capsule_steps12(ct.batch[slot], ct.xt[slot], sy0, sz, chunk, und);
+        // pool the undecided sub-cells as step-3 tasks of this capsule
+        if (__any_sync(0xffffffffu, und != 0u)) {
+            const uint32_t n = __popc(und);
+            uint32_t off = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, off, o);
+                if (lane >= o) off += t;
+            }
+            const int total = (int)__shfl_sync(0xffffffffu, off, 31);
+            if (ntask + total > CT_TASKS) {
+                chunk = capsule_step3_pool(ct, ntask, chunk);
+                ntask = 0;
+            }
+            uint32_t pos = (uint32_t)ntask + off - n;
+            uint32_t u = und;
+            while (u) {
+                const int bpos = __ffs(u) - 1;
+                u &= u - 1;
+                ct.task[pos++] = (uint16_t)((slot << 9) | (16 * lane + bpos));
+            }
+            ntask += total;
+            __syncwarp();
+        }
+        full = __all_sync(0xffffffffu, chunk == 0xffffu);
+    }
+    if (ntask > 0 && !full) chunk = capsule_step3_pool(ct, ntask, chunk);
+    return chunk;
+}
+
+// Voxel origin (grid units) of a window-relative Morton key.
+__device__ __forceinline__ void voxel_origin(uint32_t key, int bx, int by, int bz, float& fx, float& fy, float& fz) {
+    fx = (float)((int)vx_compact1by2(key) + bx);
+    fy = (float)((int)vx_compact1by2(key >> 1) + by);
+    fz = (float)((int)vx_compact1by2(key >> 2) + bz);
+}
+
+// Warp per candidate voxel, two voxels per step: the segments s0 and s0 + 1 are taken
+// together.  When both hold at most 16 capsules (pair mode) one setup serves both: lanes 0-15
+// prepare A's capsules (batch slots 0-15) and lanes 16-31 B's (slots 16-31), the sums run
+// on lanes 0-6 (A) and 7-13 (B) at once and the ordering sort runs in each half; then the
+// mask steps run for A and for B.  Otherwise each voxel runs alone, its capsules in batches
+// of 32.  The setup and the mask steps each have one call site (the loop below walks the
+// voxels and batches), so that the kernel holds one copy of them.
 __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint32_t* __restrict__ keys,
                                                                   const uint32_t* __restrict__ prims,
                                                                   const uint32_t* __restrict__ starts,
@@ -929,121 +1030,97 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
     const uint32_t warps = gridDim.x * RED_WARPS;
     __shared__ CapsuleTasks pool[RED_WARPS];
     CapsuleTasks& ct = pool[threadIdx.x >> 5];
-    // voxels are taken from the counter `next` one per warp when it is given (a grid of
+    // voxels are taken two at a time from the counter `next` when it is given (a grid of
     // resident blocks), else in a fixed grid stride
     auto take = [&]() -> uint32_t {
         uint32_t v = 0;
-        if (lane == 0) v = atomicAdd(next, 1u);
+        if (lane == 0) v = atomicAdd(next, 2u);
         return __shfl_sync(0xffffffffu, v, 0);
     };
-    for (uint32_t seg = next ? take() : blockIdx.x * RED_WARPS + (threadIdx.x >> 5); seg < nseg;
-         seg = next ? take() : seg + warps) {
-        const uint32_t beg = starts[seg], end = starts[seg + 1];
-        const uint32_t key = keys[beg];
-        const float fx = (float)((int)vx_compact1by2(key) + bx), fy = (float)((int)vx_compact1by2(key >> 1) + by),
-                    fz = (float)((int)vx_compact1by2(key >> 2) + bz);
-        uint32_t chunk = 0;
-        bool full = false;
-        int ntask = 0;
-        float accc = 0.0f;   // lane c < 7: component c of the mass / moment sums
-        for (uint32_t base = beg; base < end; base += 32) {
-            const uint32_t cnt = min(32u, end - base);
-            float q[7] = {0, 0, 0, 0, 0, 0, 0};
-            __syncwarp();   // the previous batch's sums have read ct.q
-            // order of the mask tests: capsules whose axis passes deepest into the voxel first
-            // (they set the most bits, so later capsules find more lanes already full); the
-            // mask is an OR, so the order does not change it
-            uint32_t okey = 0xffffffe0u | (uint32_t)lane;
-            if (lane < cnt) {
-                const uint32_t p = prims[base + lane];
-                const float4 A = ra[p], B = rb[p];
-                float a[3] = {A.x - fx, A.y - fy, A.z - fz};
-                float b[3] = {B.x - fx, B.y - fy, B.z - fz};
-                const CapsuleLocal cl = capsule_local(a, b, A.w);
-                ct.batch[lane] = cl;
-                ct.xt[lane] = capsule_x(a[0], b[0]);
-                {
-                    // squared distance from the voxel centre to the axis, minus r^2 (an ordering
-                    // key only: any rounding of it leaves the outputs unchanged)
-                    const float e[3] = {cl.d_idd.x, cl.d_idd.y, cl.d_idd.z};
-                    const float w[3] = {0.5f - a[0], 0.5f - a[1], 0.5f - a[2]};
-                    float tt = ((w[0] * e[0] + w[1] * e[1]) + w[2] * e[2]) * cl.d_idd.w;
-                    tt = fminf(fmaxf(tt, 0.0f), 1.0f);
-                    const float dx = w[0] - tt * e[0], dy = w[1] - tt * e[1], dz = w[2] - tt * e[2];
-                    const float v = ((dx * dx + dy * dy) + dz * dz) - A.w * A.w;
-                    uint32_t bits = __float_as_uint(v);
-                    bits ^= (bits >> 31) ? 0xffffffffu : 0x80000000u;   // order-preserving as unsigned
-                    okey = (min(bits, 0xffffffbfu) & 0xffffffe0u) | (uint32_t)lane;   // below the empty lanes
+    for (uint32_t s0 = next ? take() : 2u * (blockIdx.x * RED_WARPS + (threadIdx.x >> 5)); s0 < nseg;
+         s0 = next ? take() : s0 + 2u * warps) {
+        const bool two = s0 + 1 < nseg;
+        const uint32_t begA = starts[s0], begB = starts[s0 + 1];
+        const uint32_t endB = two ? starts[s0 + 2] : begB;
+        const uint32_t cntA = begB - begA, cntB = endB - begB;
+        const bool pair = two && cntA <= 16 && cntB <= 16;
+        const uint32_t keyA = keys[begA], keyB = two ? keys[begB] : 0u;
+        uint32_t seg = s0, base = begA, end = begB, key = keyA;
+        uint32_t chunk = 0, okey = 0, cnt = 0;
+        bool full = false, second = false;
+        float accc = 0.0f;   // lane c < 7: component c of the sums (pair mode: lane 7 + c, B's)
+        int src0 = 0, dir = 1;
+        for (;;) {
+            if (!second) {
+                // set up a batch: both voxels of a pair, or the next 32 capsules of `seg`
+                const bool hi = pair && lane >= 16;
+                const uint32_t li = pair ? (uint32_t)(lane & 15) : (uint32_t)lane;
+                cnt = pair ? cntA : min(32u, end - base);
+                const uint32_t mine = pair ? (hi ? cntB : cntA) : cnt;
+                float fx, fy, fz;
+                voxel_origin(hi ? keyB : key, bx, by, bz, fx, fy, fz);
+                __syncwarp();   // the previous batch's sums have read ct.q
+                okey = 0xffffffe0u | (uint32_t)lane;
+                if (li < mine)
+                    okey = capsule_slot_setup(ct, lane, prims[(pair ? (hi ? begB : begA) : base) + li], fx, fy, fz,
+                                              ra, rb, rt);
+                __syncwarp();
+                // sums in primitive order, one component per lane (the same sequence of FP32
+                // additions as a single running sum per component)
+                if (lane < 7) {
+                    for (uint32_t j = 0; j < cnt; ++j) accc = accc + ct.q[j * 7 + lane];
+                } else if (pair && lane < 14) {
+                    for (uint32_t j = 0; j < cntB; ++j) accc = accc + ct.q[(16 + j) * 7 + (lane - 7)];
                 }
-                float mu = capsule_measure(a, b, A.w);
-                // w mu and w mu T(t), T the primitive's tangent terms (k_tangent_terms)
-                const float4 T0 = rt[2 * (size_t)p], T1 = rt[2 * (size_t)p + 1];
-                float c = B.w * mu;
-                q[0] = c;
-                q[1] = c * T0.x;
-                q[2] = c * T0.y;
-                q[3] = c * T0.z;
-                q[4] = c * T0.w;
-                q[5] = c * T1.x;
-                q[6] = c * T1.y;
+                // bitonic sort of the keys (unique: the lane is the low 5 bits); after the
+                // stage of width k, lanes 0..k-1 hold their keys in ascending order, so the sort
+                // stops once k covers the batch.  A pair sorts within its halves (k <= 16):
+                // B's keys end ascending from lane 16 below width 16, descending from lane 31
+                // at width 16.
+                const uint32_t target = pair ? max(cntA, cntB) : cnt;
+                int kf = 2;
 #pragma unroll
-                for (int c = 0; c < 7; ++c) ct.q[lane * 7 + c] = q[c];
-            }
-            __syncwarp();
-            // sums in primitive order, one component per lane (the same sequence of FP32
-            // additions as a single running sum per component)
-            if (lane < 7)
-                for (uint32_t j = 0; j < cnt; ++j) accc = accc + ct.q[j * 7 + lane];
-            // bitonic sort of the 32 keys over the warp (unique: the lane is the low 5 bits);
-            // after the stage of width k, lanes 0..k-1 hold their keys in ascending order, so
-            // the sort stops once k covers the batch
+                for (int k = 2; k <= 32; k <<= 1) {
+                    if (pair && k > 16) break;
+                    kf = k;
 #pragma unroll
-            for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-                for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                    const uint32_t other = __shfl_xor_sync(0xffffffffu, okey, jj);
-                    const bool keep_min = ((lane & k) == 0) == ((lane & jj) == 0);
-                    okey = keep_min ? min(okey, other) : max(okey, other);
-                }
-                if ((uint32_t)k >= cnt) break;
-            }
-            for (uint32_t j = 0; j < cnt; ++j) {
-                if (!full) {
-                    const int slot = (int)(__shfl_sync(0xffffffffu, okey, (int)j) & 31u);
-                    uint32_t und;
-                    chunk = capsule_steps12(ct.batch[slot], ct.xt[slot], sy0, sz, chunk, und);
-                    // pool the undecided sub-cells as step-3 tasks of this capsule
-                    if (__any_sync(0xffffffffu, und != 0u)) {
-                        const uint32_t n = __popc(und);
-                        uint32_t off = n;
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const uint32_t t = __shfl_up_sync(0xffffffffu, off, o);
-                            if (lane >= o) off += t;
-                        }
-                        const int total = (int)__shfl_sync(0xffffffffu, off, 31);
-                        if (ntask + total > CT_TASKS) {
-                            chunk = capsule_step3_pool(ct, ntask, chunk);
-                            ntask = 0;
-                        }
-                        uint32_t pos = (uint32_t)ntask + off - n;
-                        uint32_t u = und;
-                        while (u) {
-                            const int bpos = __ffs(u) - 1;
-                            u &= u - 1;
-                            ct.task[pos++] = (uint16_t)((slot << 9) | (16 * lane + bpos));
-                        }
-                        ntask += total;
-                        __syncwarp();
+                    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                        const uint32_t other = __shfl_xor_sync(0xffffffffu, okey, jj);
+                        const bool keep_min = ((lane & k) == 0) == ((lane & jj) == 0);
+                        okey = keep_min ? min(okey, other) : max(okey, other);
                     }
-                    full = __all_sync(0xffffffffu, chunk == 0xffffu);
+                    if ((uint32_t)k >= target) break;
+                }
+                src0 = 0;
+                dir = 1;
+                if (pair) {   // where B's keys will be read (kept for its turn)
+                    base = kf == 16 ? 31u : 16u;
+                    end = kf == 16 ? 1u : 0u;
                 }
             }
-            // the tasks refer to this batch's capsules: evaluate them before the next batch
-            if (ntask > 0 && !full) chunk = capsule_step3_pool(ct, ntask, chunk);
-            ntask = 0;
+            chunk = voxel_mask(ct, okey, cnt, src0, dir, sy0, sz, chunk, full);
+            if (!pair) {
+                base += cnt;
+                if (base < end) continue;   // the voxel's next batch
+            }
+            write_seg7(out, seg, key, chunk, __shfl_down_sync(0xffffffffu, accc, second ? 7 : 0));
+            if (seg != s0 || !two) break;
+            // the second voxel of the two
+            seg = s0 + 1;
+            key = keyB;
+            chunk = 0;
+            full = false;
+            if (pair) {
+                second = true;
+                cnt = cntB;
+                src0 = (int)base;
+                dir = end ? -1 : 1;
+            } else {
+                base = begB;
+                end = endB;
+                accc = 0.0f;
+            }
         }
-        write_seg7(out, seg, key, chunk, accc);
     }
 }
 
