@@ -1009,12 +1009,13 @@ __device__ __forceinline__ void voxel_origin(uint32_t key, int bx, int by, int b
 }
 
 // Warp per candidate voxel, two voxels per step: the segments s0 and s0 + 1 are taken
-// together.  When both hold at most 16 capsules (pair mode) one setup serves both: lanes 0-15
-// prepare A's capsules (batch slots 0-15) and lanes 16-31 B's (slots 16-31), the sums run
-// on lanes 0-6 (A) and 7-13 (B) at once and the ordering sort runs in each half; then the
-// mask steps run for A and for B.  Otherwise each voxel runs alone, its capsules in batches
-// of 32.  The setup and the mask steps each have one call site (the loop below walks the
-// voxels and batches), so that the kernel holds one copy of them.
+// together.  When their capsules fit one batch (at most 32 together; pack mode) one setup
+// serves both: lanes 0 .. nA-1 prepare A's capsules and lanes nA .. nA+nB-1 B's (batch slots
+// by lane), the sums run on lanes 0-6 (A) and 7-13 (B) at once, and one ordering sort with
+// the voxel as its top key bit leaves A's keys first and B's after them; then the mask steps
+// run for A and for B.  Otherwise each voxel runs alone, its capsules in batches of 32.  The
+// setup and the mask steps each have one call site (the loop below walks the voxels and
+// batches), so that the kernel holds one copy of them.
 __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint32_t* __restrict__ keys,
                                                                   const uint32_t* __restrict__ prims,
                                                                   const uint32_t* __restrict__ starts,
@@ -1043,63 +1044,54 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
         const uint32_t begA = starts[s0], begB = starts[s0 + 1];
         const uint32_t endB = two ? starts[s0 + 2] : begB;
         const uint32_t cntA = begB - begA, cntB = endB - begB;
-        const bool pair = two && cntA <= 16 && cntB <= 16;
+        const bool pack = two && cntA + cntB <= 32;
         const uint32_t keyA = keys[begA], keyB = two ? keys[begB] : 0u;
         uint32_t seg = s0, base = begA, end = begB, key = keyA;
         uint32_t chunk = 0, okey = 0, cnt = 0;
         bool full = false, second = false;
-        float accc = 0.0f;   // lane c < 7: component c of the sums (pair mode: lane 7 + c, B's)
-        int src0 = 0, dir = 1;
+        float accc = 0.0f;   // lane c < 7: component c of the sums (pack mode: lane 7 + c, B's)
+        int src0 = 0;
         for (;;) {
             if (!second) {
-                // set up a batch: both voxels of a pair, or the next 32 capsules of `seg`
-                const bool hi = pair && lane >= 16;
-                const uint32_t li = pair ? (uint32_t)(lane & 15) : (uint32_t)lane;
-                cnt = pair ? cntA : min(32u, end - base);
-                const uint32_t mine = pair ? (hi ? cntB : cntA) : cnt;
+                // set up a batch: both voxels of a pack, or the next 32 capsules of `seg`
+                const bool inB = pack && (uint32_t)lane >= cntA;
+                cnt = pack ? cntA : min(32u, end - base);
+                const uint32_t nset = pack ? cntA + cntB : cnt;
                 float fx, fy, fz;
-                voxel_origin(hi ? keyB : key, bx, by, bz, fx, fy, fz);
+                voxel_origin(inB ? keyB : key, bx, by, bz, fx, fy, fz);
                 __syncwarp();   // the previous batch's sums have read ct.q
                 okey = 0xffffffe0u | (uint32_t)lane;
-                if (li < mine)
-                    okey = capsule_slot_setup(ct, lane, prims[(pair ? (hi ? begB : begA) : base) + li], fx, fy, fz,
-                                              ra, rb, rt);
+                if ((uint32_t)lane < nset) {
+                    okey = capsule_slot_setup(ct, lane, prims[(pack ? (inB ? begB - cntA : begA) : base) + lane], fx,
+                                              fy, fz, ra, rb, rt);
+                    // the voxel above the distance key (still below the empty lanes' keys)
+                    if (pack) okey = (inB ? 0x80000000u : 0u) | ((okey >> 1) & 0x7fffffe0u) | (uint32_t)lane;
+                }
                 __syncwarp();
                 // sums in primitive order, one component per lane (the same sequence of FP32
                 // additions as a single running sum per component)
                 if (lane < 7) {
                     for (uint32_t j = 0; j < cnt; ++j) accc = accc + ct.q[j * 7 + lane];
-                } else if (pair && lane < 14) {
-                    for (uint32_t j = 0; j < cntB; ++j) accc = accc + ct.q[(16 + j) * 7 + (lane - 7)];
+                } else if (pack && lane < 14) {
+                    for (uint32_t j = 0; j < cntB; ++j) accc = accc + ct.q[(cntA + j) * 7 + (lane - 7)];
                 }
                 // bitonic sort of the keys (unique: the lane is the low 5 bits); after the
                 // stage of width k, lanes 0..k-1 hold their keys in ascending order, so the sort
-                // stops once k covers the batch.  A pair sorts within its halves (k <= 16):
-                // B's keys end ascending from lane 16 below width 16, descending from lane 31
-                // at width 16.
-                const uint32_t target = pair ? max(cntA, cntB) : cnt;
-                int kf = 2;
+                // stops once k covers the batch
 #pragma unroll
                 for (int k = 2; k <= 32; k <<= 1) {
-                    if (pair && k > 16) break;
-                    kf = k;
 #pragma unroll
                     for (int jj = k >> 1; jj > 0; jj >>= 1) {
                         const uint32_t other = __shfl_xor_sync(0xffffffffu, okey, jj);
                         const bool keep_min = ((lane & k) == 0) == ((lane & jj) == 0);
                         okey = keep_min ? min(okey, other) : max(okey, other);
                     }
-                    if ((uint32_t)k >= target) break;
+                    if ((uint32_t)k >= nset) break;
                 }
                 src0 = 0;
-                dir = 1;
-                if (pair) {   // where B's keys will be read (kept for its turn)
-                    base = kf == 16 ? 31u : 16u;
-                    end = kf == 16 ? 1u : 0u;
-                }
             }
-            chunk = voxel_mask(ct, okey, cnt, src0, dir, sy0, sz, chunk, full);
-            if (!pair) {
+            chunk = voxel_mask(ct, okey, cnt, src0, 1, sy0, sz, chunk, full);
+            if (!pack) {
                 base += cnt;
                 if (base < end) continue;   // the voxel's next batch
             }
@@ -1110,11 +1102,10 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
             key = keyB;
             chunk = 0;
             full = false;
-            if (pair) {
+            if (pack) {   // B's keys follow A's
                 second = true;
                 cnt = cntB;
-                src0 = (int)base;
-                dir = end ? -1 : 1;
+                src0 = (int)cntA;
             } else {
                 base = begB;
                 end = endB;
