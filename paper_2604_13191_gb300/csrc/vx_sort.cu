@@ -113,6 +113,36 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* in, 
     }
 }
 
+// Single-block exclusive scan of a short array (a few tiles): the tiles in order with a
+// running carry, each thread on SCAN_ITEMS consecutive elements (in place allowed: a thread
+// reads its elements before it writes them); *total (optional) receives the sum.
+constexpr uint32_t SCAN_SMALL_TILES = 16;
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_small(const uint32_t* in, uint32_t* out, uint32_t n,
+                                                             uint32_t* total) {
+    __shared__ uint32_t sm[SCAN_THREADS / 32 + 1];
+    uint32_t carry = 0;
+    for (uint32_t b = 0; b < n; b += SCAN_TILE) {
+        uint32_t v[SCAN_ITEMS];
+        uint32_t s = 0;
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) {
+            const uint32_t e = b + threadIdx.x * SCAN_ITEMS + j;
+            v[j] = (e < n) ? in[e] : 0u;
+            s += v[j];
+        }
+        uint32_t tot;
+        uint32_t run = carry + block_excl_scan(s, sm, tot);
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) {
+            const uint32_t e = b + threadIdx.x * SCAN_ITEMS + j;
+            if (e < n) out[e] = run;
+            run += v[j];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
 // ---- segment starts ---------------------------------------------------------------
 // Heads of the runs of equal keys in a sorted array: element e is a head when e == 0 or
 // keys[e] != keys[e - 1].  A thread takes SCAN_ITEMS consecutive elements (as k_scan_down).
@@ -548,6 +578,11 @@ vx_status vx_scan_u32(vx_context* ctx, const uint32_t* in, uint32_t* out, uint32
         if (total) VX_CUDA_TRY(cudaMemsetAsync(total, 0, 4, s));
         return VX_OK;
     }
+    if (nb <= SCAN_SMALL_TILES) {   // one launch for a short array
+        VX_LAUNCH(ctx, ST_SCAN, s, k_scan_small<<<1, SCAN_THREADS, 0, s>>>(in, out, n, total));
+        VX_CUDA_TRY(cudaGetLastError());
+        return VX_OK;
+    }
     VX_LAUNCH(ctx, ST_SCAN, s, k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(in, n, part));
     VX_LAUNCH(ctx, ST_SCAN, s, k_scan_partials<<<1, SCAN_THREADS, 0, s>>>(part, nb, total));
     VX_LAUNCH(ctx, ST_SCAN, s, k_scan_down<<<nb, SCAN_THREADS, 0, s>>>(in, out, n, part));
@@ -641,6 +676,10 @@ cudaError_t vx_scan_u32_scratch(const uint32_t* in, uint32_t* out, uint32_t n, u
                                 uint32_t* partials, cudaStream_t s) {
     if (n == 0) return total ? cudaMemsetAsync(total, 0, 4, s) : cudaSuccess;
     const uint32_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb <= SCAN_SMALL_TILES) {   // one launch for a short array
+        k_scan_small<<<1, SCAN_THREADS, 0, s>>>(in, out, n, total);
+        return cudaGetLastError();
+    }
     k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(in, n, partials);
     k_scan_partials<<<1, SCAN_THREADS, 0, s>>>(partials, nb, total);
     k_scan_down<<<nb, SCAN_THREADS, 0, s>>>(in, out, n, partials);
