@@ -726,7 +726,7 @@ __host__ __device__ inline Window full_window(int R) {
 // (ix, iy, iz) of flat index idx < tot in a range (x fastest).  Ranges of at most 2^16
 // voxels divide by the correctly rounded FP32 reciprocal: (i + 0.5) fl(1/n), rounded, is
 // within i / n (1 + 2^-23) of the quotient plus 0.5 / n, so its integer part is floor(i / n)
-// (checked for every n and i below 2^16).  Larger ranges use 32-bit division when they hold
+// (checked for every n and i below 2^16; tests/test_host_arith.py keeps every n up to 4096).  Larger ranges use 32-bit division when they hold
 // fewer than 2^32 voxels (always inside a 1024^3 window).
 __device__ __forceinline__ void voxel_of(long long idx, long long tot, const Range& rg, int& ix, int& iy, int& iz) {
     if (tot <= 65536) {
