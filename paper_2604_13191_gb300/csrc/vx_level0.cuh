@@ -1008,14 +1008,14 @@ __device__ __forceinline__ void voxel_origin(uint32_t key, int bx, int by, int b
     fz = (float)((int)vx_compact1by2(key >> 2) + bz);
 }
 
-// Warp per candidate voxel, two voxels per step: the segments s0 and s0 + 1 are taken
-// together.  When their capsules fit one batch (at most 32 together; pack mode) one setup
-// serves both: lanes 0 .. nA-1 prepare A's capsules and lanes nA .. nA+nB-1 B's (batch slots
-// by lane), the sums run on lanes 0-6 (A) and 7-13 (B) at once, and one ordering sort with
-// the voxel as its top key bit leaves A's keys first and B's after them; then the mask steps
-// run for A and for B.  Otherwise each voxel runs alone, its capsules in batches of 32.  The
-// setup and the mask steps each have one call site (the loop below walks the voxels and
-// batches), so that the kernel holds one copy of them.
+// Warp per candidate voxel, four voxels per step.  The step's voxels form groups of
+// consecutive voxels whose capsules fit one batch (at most 32 together), and one setup serves
+// a group: lane l takes the group's l-th capsule (the capsules of consecutive voxels are
+// consecutive in the sorted pairs), the sums of voxel u run on lanes 7u .. 7u+6, and one
+// ordering sort with the voxel above the distance key leaves each voxel's capsules together,
+// in voxel order; then the mask steps run voxel by voxel.  A voxel of more than 32 capsules
+// is a group of its own and runs in batches of 32.  The setup, the mask steps and the output
+// each have one call site, so that the kernel holds one copy of them.
 __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint32_t* __restrict__ keys,
                                                                   const uint32_t* __restrict__ prims,
                                                                   const uint32_t* __restrict__ starts,
@@ -1025,55 +1025,59 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                                                                   const float4* __restrict__ rt, SegOut out,
                                                                   int bx, int by, int bz,
                                                                   uint32_t* __restrict__ next) {
+    constexpr uint32_t STEP = 4;   // voxels per warp step (a group's voxel index takes 2 bits)
     const int lane = threadIdx.x & 31;
     const uint32_t nseg = *nseg_p;
     const int sz = lane >> 2, sy0 = (lane & 3) * 2;
     const uint32_t warps = gridDim.x * RED_WARPS;
     __shared__ CapsuleTasks pool[RED_WARPS];
     CapsuleTasks& ct = pool[threadIdx.x >> 5];
-    // voxels are taken two at a time from the counter `next` when it is given (a grid of
+    // voxels are taken STEP at a time from the counter `next` when it is given (a grid of
     // resident blocks), else in a fixed grid stride
     auto take = [&]() -> uint32_t {
         uint32_t v = 0;
-        if (lane == 0) v = atomicAdd(next, 2u);
+        if (lane == 0) v = atomicAdd(next, STEP);
         return __shfl_sync(0xffffffffu, v, 0);
     };
-    for (uint32_t s0 = next ? take() : 2u * (blockIdx.x * RED_WARPS + (threadIdx.x >> 5)); s0 < nseg;
-         s0 = next ? take() : s0 + 2u * warps) {
-        const bool two = s0 + 1 < nseg;
-        const uint32_t begA = starts[s0], begB = starts[s0 + 1];
-        const uint32_t endB = two ? starts[s0 + 2] : begB;
-        const uint32_t cntA = begB - begA, cntB = endB - begB;
-        const bool pack = two && cntA + cntB <= 32;
-        const uint32_t keyA = keys[begA], keyB = two ? keys[begB] : 0u;
-        uint32_t seg = s0, base = begA, end = begB, key = keyA;
-        uint32_t chunk = 0, okey = 0, cnt = 0;
-        bool full = false, second = false;
-        float accc = 0.0f;   // lane c < 7: component c of the sums (pack mode: lane 7 + c, B's)
-        int src0 = 0;
-        for (;;) {
-            if (!second) {
-                // set up a batch: both voxels of a pack, or the next 32 capsules of `seg`
-                const bool inB = pack && (uint32_t)lane >= cntA;
-                cnt = pack ? cntA : min(32u, end - base);
-                const uint32_t nset = pack ? cntA + cntB : cnt;
+    for (uint32_t s0 = next ? take() : STEP * (blockIdx.x * RED_WARPS + (threadIdx.x >> 5)); s0 < nseg;
+         s0 = next ? take() : s0 + STEP * warps) {
+        const uint32_t s_end = min(s0 + STEP, nseg);
+        for (uint32_t g = s0; g < s_end;) {
+            // the group [g, g + m): consecutive voxels of at most 32 capsules together, or one voxel
+            const uint32_t gbeg = starts[g];
+            uint32_t m = 1, gend = starts[g + 1];
+            while (g + m < s_end) {
+                const uint32_t nx = starts[g + m + 1];
+                if (nx - gbeg > 32u) break;
+                gend = nx;
+                ++m;
+            }
+            uint32_t chunk = 0;
+            bool full = false;
+            float accc = 0.0f;   // lane 7u + c: component c of voxel u's sums
+            for (uint32_t base = gbeg; base < gend; base += 32) {
+                const uint32_t cnt = min(32u, gend - base);
+                // the lane's voxel in the group, and its origin
+                uint32_t v = 0;
+                for (uint32_t t = 1; t < m; ++t) v += (base + (uint32_t)lane >= starts[g + t]) ? 1u : 0u;
                 float fx, fy, fz;
-                voxel_origin(inB ? keyB : key, bx, by, bz, fx, fy, fz);
+                voxel_origin(keys[starts[g + v]], bx, by, bz, fx, fy, fz);
                 __syncwarp();   // the previous batch's sums have read ct.q
-                okey = 0xffffffe0u | (uint32_t)lane;
-                if ((uint32_t)lane < nset) {
-                    okey = capsule_slot_setup(ct, lane, prims[(pack ? (inB ? begB - cntA : begA) : base) + lane], fx,
-                                              fy, fz, ra, rb, rt);
+                uint32_t okey = 0xffffffe0u | (uint32_t)lane;
+                if ((uint32_t)lane < cnt) {
+                    okey = capsule_slot_setup(ct, lane, prims[base + lane], fx, fy, fz, ra, rb, rt);
                     // the voxel above the distance key (still below the empty lanes' keys)
-                    if (pack) okey = (inB ? 0x80000000u : 0u) | ((okey >> 1) & 0x7fffffe0u) | (uint32_t)lane;
+                    if (m > 1) okey = (v << 30) | ((okey >> 2) & 0x3fffffc0u) | (uint32_t)lane;
                 }
                 __syncwarp();
                 // sums in primitive order, one component per lane (the same sequence of FP32
-                // additions as a single running sum per component)
-                if (lane < 7) {
-                    for (uint32_t j = 0; j < cnt; ++j) accc = accc + ct.q[j * 7 + lane];
-                } else if (pack && lane < 14) {
-                    for (uint32_t j = 0; j < cntB; ++j) accc = accc + ct.q[(cntA + j) * 7 + (lane - 7)];
+                // additions as a single running sum per component); all voxels at once
+                if ((uint32_t)lane < 7u * m) {
+                    const uint32_t u = (uint32_t)lane / 7u;
+                    const uint32_t ub = m > 1 ? starts[g + u] - base : 0u;
+                    const uint32_t un = m > 1 ? starts[g + u + 1] - starts[g + u] : cnt;
+                    const float* q = ct.q + ub * 7 + ((uint32_t)lane - 7u * u);
+                    for (uint32_t j = 0; j < un; ++j) accc = accc + q[j * 7];
                 }
                 // bitonic sort of the keys (unique: the lane is the low 5 bits); after the
                 // stage of width k, lanes 0..k-1 hold their keys in ascending order, so the sort
@@ -1086,31 +1090,22 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 7) k_reduce_fibers(const uint3
                         const bool keep_min = ((lane & k) == 0) == ((lane & jj) == 0);
                         okey = keep_min ? min(okey, other) : max(okey, other);
                     }
-                    if ((uint32_t)k >= nset) break;
+                    if ((uint32_t)k >= cnt) break;
                 }
-                src0 = 0;
+                // the mask steps, voxel by voxel; a voxel's outputs once its last batch is in
+                for (uint32_t u = 0; u < m; ++u) {
+                    const uint32_t ub = m > 1 ? starts[g + u] - base : 0u;
+                    const uint32_t un = m > 1 ? starts[g + u + 1] - starts[g + u] : cnt;
+                    chunk = voxel_mask(ct, okey, un, (int)ub, 1, sy0, sz, chunk, full);
+                    if (m > 1 || base + cnt >= gend) {
+                        write_seg7(out, g + u, keys[starts[g + u]], chunk,
+                                   __shfl_down_sync(0xffffffffu, accc, 7 * u));
+                        chunk = 0;
+                        full = false;
+                    }
+                }
             }
-            chunk = voxel_mask(ct, okey, cnt, src0, 1, sy0, sz, chunk, full);
-            if (!pack) {
-                base += cnt;
-                if (base < end) continue;   // the voxel's next batch
-            }
-            write_seg7(out, seg, key, chunk, __shfl_down_sync(0xffffffffu, accc, second ? 7 : 0));
-            if (seg != s0 || !two) break;
-            // the second voxel of the two
-            seg = s0 + 1;
-            key = keyB;
-            chunk = 0;
-            full = false;
-            if (pack) {   // B's keys follow A's
-                second = true;
-                cnt = cntB;
-                src0 = (int)cntA;
-            } else {
-                base = begB;
-                end = endB;
-                accc = 0.0f;
-            }
+            g += m;
         }
     }
 }
