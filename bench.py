@@ -199,6 +199,13 @@ class ClockSampler:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
                                        "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.fh, stderr=subprocess.DEVNULL)
+            # the sampler's own start (driver and NVML initialisation) stays out of the timed
+            # region: wait, at most 3 s, for its first sample before the steps begin
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 3.0 and self.p.poll() is None:
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.02)
         except Exception:
             self.p = None
 
