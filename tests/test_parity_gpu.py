@@ -137,6 +137,45 @@ def test_random_fibers(ctx, dirs5000, seed, R, rad, pts):
         compare_level(g, r, f"seed {seed} level {lvl}", mu_max=prim_measure_max(w))
 
 
+def test_dense_bundle_batches_and_voxel_groups(ctx, dirs5000):
+    """A bundle of 72 thick parallel fibers through one region: voxels near its axis hold over
+    a hundred capsules (several batches of 32 in the reduce), voxels at its rim a few (packed
+    several to a batch).  Every level equals the oracle's, bit for bit."""
+    R = 32
+    h = 1.0 / R
+    rng = np.random.default_rng(21)
+    ctrl, off = [], [0]
+    for f in range(72):
+        y0, z0 = 16.0 + rng.uniform(-1.5, 1.5), 16.0 + rng.uniform(-1.5, 1.5)
+        r = rng.uniform(0.6, 1.6)
+        for k in range(41):
+            x = 4.0 + 0.5 * k + rng.uniform(-0.05, 0.05)
+            y, z = y0 + rng.uniform(-0.1, 0.1), z0 + rng.uniform(-0.1, 0.1)
+            ctrl.append([x * h, y * h, z * h, r * h])
+        off.append(len(ctrl))
+    ctrl = np.asarray(ctrl, np.float32)
+    off = np.asarray(off, np.int64)
+    n = synth.fiber_segment_count(off)
+    w = synth.Workload("bundle", "fibers", synth.Grid((0.0, 0.0, 0.0), h, R), ctrl=ctrl, fiber_offsets=off,
+                       weights=rng.uniform(0.5, 2.0, n).astype(np.float32), K=4)
+    got = run_gpu(ctx, w, dirs=dirs5000)
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, R, 4, dirs5000)
+    # the case reaches what it is for: voxels of more than 32 capsules next to small ones
+    # (capsules counted by their midpoint within r + 1 of the voxel centre)
+    A = np.concatenate([ctrl[off[f]:off[f + 1] - 1, :3] for f in range(len(off) - 1)]) * R
+    B = np.concatenate([ctrl[off[f] + 1:off[f + 1], :3] for f in range(len(off) - 1)]) * R
+    rr = np.concatenate([0.5 * (ctrl[off[f]:off[f + 1] - 1, 3] + ctrl[off[f] + 1:off[f + 1], 3])
+                         for f in range(len(off) - 1)]) * R
+    mid = 0.5 * (A + B)
+    vox = np.stack(np.meshgrid(np.arange(R), np.arange(R), np.arange(R), indexing="ij"), -1).reshape(-1, 3) + 0.5
+    near = vox[(np.abs(vox[:, 1] - 16) < 4) & (np.abs(vox[:, 2] - 16) < 4) & (vox[:, 0] > 6) & (vox[:, 0] < 22)]
+    counts = np.array([(np.linalg.norm(mid - c, axis=1) < rr + 1.0).sum() for c in near])
+    assert counts.max() > 32 and (counts[counts > 0] <= 16).any()
+    for lvl, (g, r) in enumerate(zip(got, refs)):
+        compare_level(g, r, f"bundle level {lvl}", mu_max=prim_measure_max(w))
+
+
 def _seg_box_dist(a, b, lo, hi):
     """FP64 distance from segment a-b to box [lo, hi] (ternary search of a convex function)."""
     def g(t):
