@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(LR_BLOCK, 4) k_lod_reduce(LevelIn in, const ui
             float M[6] = {0, 0, 0, 0, 0, 0};
             uint64_t pm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             int ncand = 0;
+            uint32_t lcj = 0;   // lobe count of this lane's child (last chunk read)
             for (uint32_t c0 = beg; c0 < end; c0 += 8) {
                 const uint32_t c = c0 + (uint32_t)j;
                 float cmass = 0.0f;
@@ -200,7 +201,8 @@ __global__ void __launch_bounds__(LR_BLOCK, 4) k_lod_reduce(LevelIn in, const ui
                         cm[2 * w + 1] = x.y;
                     }
                     downsample_into(cm, (int)(in.keys[c] & 7ull), pm);
-                    ncand += in.lobe_count[c];
+                    lcj = in.lobe_count[c];
+                    ncand += (int)lcj;
                 }
                 const int nc = (int)min(8u, end - c0);   // the same in the whole group
                 for (int i = 0; i < nc; ++i) {
@@ -212,6 +214,17 @@ __global__ void __launch_bounds__(LR_BLOCK, 4) k_lod_reduce(LevelIn in, const ui
 #pragma unroll
                     for (int k = 0; k < 6; ++k) M[k] = M[k] + Mi[k];
                 }
+            }
+            // a parent of at most 8 children, each with at most one lobe (every parent of level 1):
+            // the lane's child's lobe row, read now so that it arrives during the mask reduction
+            const bool one_chunk = end - beg <= 8u;
+            const uint32_t cj = beg + (uint32_t)j;
+            const bool has1 = K > 1 && one_chunk && cj < end && lcj == 1u;
+            float row[7] = {0, 0, 0, 0, 0, 0, 0};
+            if (has1) {
+                const float* src = in.lobes + (size_t)cj * in.K * 7;
+#pragma unroll
+                for (int k = 0; k < 7; ++k) row[k] = src[k];
             }
             // the group's OR of the mask words, scattered so that lane j keeps word j: each step
             // keeps the half of the words its lane-index bit selects and ORs in the partner's copy
@@ -287,6 +300,36 @@ __global__ void __launch_bounds__(LR_BLOCK, 4) k_lod_reduce(LevelIn in, const ui
                     for (int k = 0; k < 7; ++k) lo[r * 7 + k] = 0.0f;
                     for (int k = 0; k < 6; ++k) co[r * 6 + k] = 0.0f;
                 }
+                const bool fast = one_chunk && __all_sync(gm, !(cj < end && lcj > 1u));
+                if (fast) {
+                    // the ranks from the group's weights: candidate order is child order
+                    const uint32_t hb = (__ballot_sync(gm, has1) >> (lane & 24)) & 0xffu;
+                    const int idx = __popc(hb & ((1u << j) - 1u));
+                    const float wx = row[6];
+                    int rank = 0;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float wy = __shfl_sync(gm, wx, i, 8);
+                        const int idy = __popc(hb & ((1u << i) - 1u));
+                        if (((hb >> i) & 1u) && (wy > wx || (wy == wx && idy < idx))) ++rank;
+                    }
+                    if (has1) {
+#pragma unroll
+                        for (int k = 0; k < 7; ++k) lo[rank * 7 + k] = row[k];
+                        compact_params(row, co + rank * 6);
+                        if (pst) {
+                            LobeStats st;
+                            if (cst) {
+                                st = cst[(size_t)cj * in.K];
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < 6; ++k) { st.h[k] = 0; st.Mh[k] = 0.0f; }
+                                st.h[0] = -1;   // never sampled
+                            }
+                            pst[pb * K + rank] = st;
+                        }
+                    }
+                } else
                 for (uint32_t c = beg + (uint32_t)j; c < end; c += 8) {
                     int idx = 0;   // candidate index of the child's first lobe
                     for (uint32_t c2 = beg; c2 < c; ++c2) idx += in.lobe_count[c2];
