@@ -380,9 +380,19 @@ def main():
             e_ms.append(1e3 * (time.perf_counter() - t0))
         barrier()
         etot = max_over_ranks(sum(e_ms), ws, dev)
+        # this box's device-to-host rate, for reading the e2e time (one level-0 download alone,
+        # after the timed steps)
+        L0x = ctx.voxelize(w.grid, ctrl=ctrl, fiber_offsets=off, num_prims=n_prims)
+        torch.cuda.synchronize()
+        nx = L0x.block.numel()
+        ta = time.perf_counter()
+        h_out[0: nx].copy_(L0x.block, non_blocking=True)
+        torch.cuda.synchronize()
+        d2h_gbs = nx / (time.perf_counter() - ta) / 1e9
+        del L0x
         e2e = {"value": replica_throughput(ws, n_prims, args.steps, etot), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": etot / args.steps,
+               "ms_per_step": etot / args.steps, "d2h_gbs": d2h_gbs,
                "note": "inputs uploaded from pinned host memory, every level downloaded to pinned host "
                        "memory on a second stream: level 0 while the pyramid is built, every coarser level "
                        "once its event (vx_build_lod_events) is recorded"}
