@@ -218,9 +218,16 @@ class ClockSampler:
         except Exception:
             self.p.kill()
         self.fh.close()
+        with open(self.path) as fh:
+            return self.summarize(fh)
+
+    @staticmethod
+    def summarize(lines):
+        """Median SM clock, the maximum clock and the throttle reasons seen active in
+        nvidia-smi CSV lines (the FIELDS order); None without a sample."""
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
