@@ -768,7 +768,7 @@ extern "C" vx_status vx_batch_create_lod(vx_context* ctx, const vx_primitives* t
         // the direction table, copied once: runs use the directions given here
         b->n_dirs = lod->n_samples;
         b->merge = lod->merge;
-        if ((st = balloc(b, (void**)&b->dirs4, (size_t)lod->n_samples * 16, s)) != VX_OK) return fail(st);
+        if ((st = balloc(b, (void**)&b->dirs4, vx_dirs_bytes(lod->n_samples), s)) != VX_OK) return fail(st);
         if (vx_lod_batched_prepare(K, lod->dirs, lod->n_samples, b->dirs4, s) != cudaSuccess) return fail(VX_ERR_CUDA);
     }
     // Groups: consecutive instances of a kind whose candidate pairs fit one pass (with the

@@ -150,6 +150,9 @@ cudaError_t vx_lod_cluster_batched(const vx_level* in, const vx_level* out, cons
                                    cudaStream_t s);
 cudaError_t vx_lod_batched_prepare(int K, const float* dirs, int n, float4* dirs4, cudaStream_t s);
 constexpr size_t kLobeStatsBytes = 48;   // per-lobe histogram + sample moment kept between levels
+// Direction table of the lobe sampling: n float4 directions, then the whole pairs of them
+// ({x0, x1, y0, y1}, {z0, z1, 0, 0} for directions 2j, 2j + 1) for the packed FP32 loop.
+inline size_t vx_dirs_bytes(int n) { return (size_t)n * 16 + (size_t)(n / 2) * 32; }
 
 // ---- Morton ------------------------------------------------------------------
 __host__ __device__ inline uint32_t vx_part1by2(uint32_t x) {

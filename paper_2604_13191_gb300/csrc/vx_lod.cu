@@ -459,6 +459,33 @@ __device__ __forceinline__ uint32_t ge_mask(float a, float b) {
     return m;
 }
 
+// Two FP32 values packed in a 64-bit register (low half first) and the packed FP32 operations
+// on them; each half is rounded to nearest even, exactly as the scalar operation.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // One direction sample of a well-conditioned lobe (|v|^2 > 0): the six histogram masks and
 // the six moment terms as raw FP32 bit patterns (x * 2^20 / |v|^2 + 1.5 * 2^23, rounded once).
 struct SampleTerms {
@@ -522,31 +549,70 @@ __device__ LobeOwn sample_lobe(const float* S, const float4* __restrict__ dirs, 
     const int tid = (G == 1) ? (threadIdx.x & 31) : (int)threadIdx.x;
     constexpr int STRIDE = 32 * G;
     if (wellcond && N <= STRIDE * 1024) {
-        // every sample has |v|^2 > 0: no sample is skipped, so two samples are summed per step
-        // with three-input adds (histogram masks are -1 / 0; each moment term carries the
-        // constant 1.5 * 2^23, removed at the end: the sums wrap modulo 2^32, and the true sum
-        // of at most 1024 terms of magnitude <= 2^20 is recovered exactly)
-        uint32_t q[6] = {0, 0, 0, 0, 0, 0};
-        int k = tid;
-#pragma unroll 1
-        for (; k + STRIDE < N; k += 2 * STRIDE) {
-            const SampleTerms A = sample_terms(Rm, __ldg(dirs + k));
-            const SampleTerms B = sample_terms(Rm, __ldg(dirs + k + STRIDE));
+        // every sample has |v|^2 > 0: no sample is skipped.  Two samples (a whole pair of the
+        // pair table) per step, their FP32 arithmetic as packed pairs: each half of a packed
+        // operation rounds as the scalar one would, so the terms are those of sample_terms.
+        // Histogram masks are -1 / 0; each moment term carries the constant 1.5 * 2^23, removed
+        // at the end: the sums wrap modulo 2^32, and the true sum of at most 1025 terms of
+        // magnitude <= 2^20 is recovered exactly.
+        f2 R2[9];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                h[c] = h[c] - (int32_t)A.m[c] - (int32_t)B.m[c];
-                q[c] = q[c] + A.x[c] + B.x[c];
-            }
+        for (int i = 0; i < 9; ++i) R2[i] = f2_pack(Rm[i], Rm[i]);
+        const f2 k36 = f2_pack(0.36f, 0.36f), k04 = f2_pack(0.04f, 0.04f);
+        const f2 k20 = f2_pack(1048576.0f, 1048576.0f), koff = f2_pack(12582912.0f, 12582912.0f);
+        const int NP = N >> 1;
+        const ulonglong2* __restrict__ pr = reinterpret_cast<const ulonglong2*>(dirs + N);
+        uint32_t q[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 1
+        for (int j = tid; j < NP; j += STRIDE) {
+            const ulonglong2 xy = __ldg(pr + 2 * j);
+            const f2 z = __ldg(reinterpret_cast<const unsigned long long*>(pr + 2 * j + 1));
+            f2 v[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                v[i] = f2_fma(R2[3 * i + 2], z, f2_fma(R2[3 * i + 1], xy.y, f2_mul(R2[3 * i], xy.x)));
+            const f2 c0 = f2_mul(v[0], v[0]), c1 = f2_mul(v[1], v[1]), c2 = f2_mul(v[2], v[2]);
+            const f2 n2 = f2_add(f2_add(c0, c1), c2);
+            const f2 t6 = f2_mul(k36, n2), t2 = f2_mul(k04, n2);
+            float a0, b0, a1, b1, a2, b2, a6, b6, a4, b4, an, bn;
+            f2_unpack(c0, a0, b0);
+            f2_unpack(c1, a1, b1);
+            f2_unpack(c2, a2, b2);
+            f2_unpack(t6, a6, b6);
+            f2_unpack(t2, a4, b4);
+            f2_unpack(n2, an, bn);
+            h[0] = h[0] - (int32_t)ge_mask(a0, a6) - (int32_t)ge_mask(b0, b6);
+            h[1] = h[1] - (int32_t)ge_mask(a1, a6) - (int32_t)ge_mask(b1, b6);
+            h[2] = h[2] - (int32_t)ge_mask(a2, a6) - (int32_t)ge_mask(b2, b6);
+            h[3] = h[3] - (int32_t)ge_mask(a0, a4) - (int32_t)ge_mask(b0, b4);
+            h[4] = h[4] - (int32_t)ge_mask(a1, a4) - (int32_t)ge_mask(b1, b4);
+            h[5] = h[5] - (int32_t)ge_mask(a2, a4) - (int32_t)ge_mask(b2, b4);
+            const f2 s20 = f2_mul(f2_pack(__frcp_rn(an), __frcp_rn(bn)), k20);
+            // each term is folded into its sum as soon as it is formed (short live ranges)
+            f2 x = f2_fma(c0, s20, koff);
+            q[0] = q[0] + (uint32_t)x + (uint32_t)(x >> 32);
+            x = f2_fma(c1, s20, koff);
+            q[1] = q[1] + (uint32_t)x + (uint32_t)(x >> 32);
+            x = f2_fma(c2, s20, koff);
+            q[2] = q[2] + (uint32_t)x + (uint32_t)(x >> 32);
+            x = f2_fma(f2_mul(v[0], v[1]), s20, koff);
+            q[3] = q[3] + (uint32_t)x + (uint32_t)(x >> 32);
+            x = f2_fma(f2_mul(v[0], v[2]), s20, koff);
+            q[4] = q[4] + (uint32_t)x + (uint32_t)(x >> 32);
+            x = f2_fma(f2_mul(v[1], v[2]), s20, koff);
+            q[5] = q[5] + (uint32_t)x + (uint32_t)(x >> 32);
         }
-        if (k < N) {
-            const SampleTerms A = sample_terms(Rm, __ldg(dirs + k));
+        // an odd N leaves one sample, taken by the thread next in line
+        const bool last = (N & 1) && tid == NP % STRIDE;
+        if (last) {
+            const SampleTerms A = sample_terms(Rm, __ldg(dirs + N - 1));
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
                 h[c] = h[c] - (int32_t)A.m[c];
                 q[c] = q[c] + A.x[c];
             }
         }
-        const uint32_t ns = tid < N ? (uint32_t)((N - 1 - tid) / STRIDE + 1) : 0u;
+        const uint32_t ns = 2u * (tid < NP ? (uint32_t)((NP - 1 - tid) / STRIDE + 1) : 0u) + (last ? 1u : 0u);
         cnt = (int)ns;
 #pragma unroll
         for (int c = 0; c < 6; ++c) Q[c] = (int32_t)(q[c] - ns * 0x4B400000u);
@@ -675,10 +741,18 @@ constexpr PairTable make_pair_table() {
 }
 __device__ const PairTable kPairTable = make_pair_table();
 
-// float3 direction table -> float4 (one 16-byte load per sample)
+// float3 direction table -> float4 (one 16-byte load per sample), followed by the table of
+// whole pairs: directions 2j and 2j + 1 as {x0, x1, y0, y1} and {z0, z1, 0, 0}, so that each
+// coordinate of the two loads as one packed FP32 pair
 __global__ void k_pack_dirs(const float* __restrict__ d, int n, float4* __restrict__ out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) out[k] = make_float4(d[3 * k], d[3 * k + 1], d[3 * k + 2], 0.0f);
+    if (k < n / 2) {
+        float4* pr = out + n;
+        const float* a = d + 6 * k;
+        pr[2 * k] = make_float4(a[0], a[3], a[1], a[4]);
+        pr[2 * k + 1] = make_float4(a[2], a[5], 0.0f, 0.0f);
+    }
 }
 
 // One parent listed in `work` per group of G warps (G = 1: a warp per parent, for levels
@@ -1038,7 +1112,7 @@ vx_status build_levels(vx_context* ctx, const vx_level* in, const vx_lod_params*
     }
     float4* dirs4 = nullptr;
     if (K > 1) {
-        VX_TRY(vx_ws_ensure(ctx, WS_LOD_TMP, (size_t)params->n_samples * 16, s));
+        VX_TRY(vx_ws_ensure(ctx, WS_LOD_TMP, vx_dirs_bytes(params->n_samples), s));
         dirs4 = (float4*)ctx->ws[WS_LOD_TMP].p;
         VX_LAUNCH(ctx, ST_LOD_HEADS, s, k_pack_dirs<<<(params->n_samples + 255) / 256, 256, 0, s>>>(
                                             params->dirs, params->n_samples, dirs4));
@@ -1079,7 +1153,7 @@ vx_status build_levels(vx_context* ctx, const vx_level* in, const vx_lod_params*
 }  // namespace
 
 // Direction table and shared-memory limits of batched clustering with K lobes (host side,
-// before any capture): dirs [n][3] -> dirs4 [n] float4.
+// before any capture): dirs [n][3] -> the direction table (vx_dirs_bytes(n) bytes at dirs4).
 cudaError_t vx_lod_batched_prepare(int K, const float* dirs, int n, float4* dirs4, cudaStream_t s) {
     if (K <= 1) return cudaSuccess;
     k_pack_dirs<<<(n + 255) / 256, 256, 0, s>>>(dirs, n, dirs4);

@@ -292,6 +292,20 @@ def test_sggx_h_more_directions_than_one_pass(ctx):
         compare_level(g, r, f"level {lvl}", mu_max=prim_measure_max(w))
 
 
+@pytest.mark.parametrize("n_dirs", [4999, 33001])
+def test_sggx_h_odd_direction_count(ctx, n_dirs):
+    """An odd number of directions: the paired sampling loop leaves one sample over, taken
+    by a single thread.  4,999 puts every tier on the paired loop; 33,001 puts the warp tier
+    on its general loop and the block tiers on the paired loop.  Lobes and counts must match."""
+    w = synth.config2(fibers_per_ply=8, segments=500, R=128, K=4)
+    dirs = synth.sample_directions(n_dirs)
+    got = run_gpu(ctx, w, dirs=dirs)
+    ref0 = oracle.voxelize(w)
+    refs = [ref0] + oracle.build_pyramid(ref0, 128, 4, dirs)
+    for lvl, (g, r) in enumerate(zip(got, refs)):
+        compare_level(g, r, f"level {lvl}", mu_max=prim_measure_max(w))
+
+
 def test_catmull_rom_splines(ctx, dirs5000):
     """Spline fibers: the device tessellation equals the oracle's bit for bit, and the
     tessellated fibers voxelize to the oracle's pyramid (a yarn whose polylines are
